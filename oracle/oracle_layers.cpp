@@ -1,0 +1,281 @@
+// oracle_layers.cpp - the paper's multi-ciphertext layer algorithms on the
+// CPU oracle: encrypted matrix multiplication (n ciphertexts per operand),
+// convolution over the column-wise image layout (w ciphertexts of h pixels),
+// square activation and the fully connected layer.
+//
+// TEST INFRASTRUCTURE ONLY (see oracle_internal.h).
+//
+// The paper states the multi-ciphertext layouts (abstract; contributions in
+// Sec. I-C) and says the single-ciphertext algorithms carry over by
+// partitioning and linearity (Sec. IV-A, IV-B); it prints no algorithm for
+// them. The readings written out here:
+//
+// Matmul (Alg. 3 with the operands split into n ciphertexts):
+//   A_k holds column k of A at slots i < m; B~_k holds row k of B tiled with
+//   period p over all slots (the tiling of tau_b, Sec. III-A, over the whole
+//   ring). Because p divides the slot count, RowShifter (Alg. 2) applied idx
+//   times is exactly Rot(B~_k, idx) (the m mod p = 0 case, Sec. III-B). Round
+//   idx computes D_idx = sum_k A_k (x) Rot(B~_k, idx): the SumColVec of Alg. 3
+//   over the n columns becomes n - 1 ciphertext additions, and slot i of
+//   D_idx is C[i][(i + idx) mod p]. The rotations of each B~_k share one
+//   ModUp; the n products of a round are summed as three-component tensors and
+//   relinearised once, then rescaled.
+//
+// Convolution (Alg. 4 over the column layout, channels summed as in Sec. IV-B):
+//   X_{c,j} holds column j of channel c, row r at slot g*r (row gap g) within
+//   blocks of H slots, one image per block. Column offsets b of the kernel
+//   select ciphertexts; row offsets a are rotations by g*a (the row pass of
+//   SumForConv, Alg. 1). Output (o, j') is
+//       bias_o + sum_c sum_b sum_a K[o][c][a][b] * Rot(X_{c, s j' + b}, g a),
+//   then rescaled; the output row gap is g*s. Scalars are integers
+//   round(K * q_l), q_l the prime the following rescale drops, so the scale is
+//   unchanged by the layer; the bias is added after the rescale as
+//   round(bias * scale).
+//
+// Fully connected layer: Z_o = sum_{c,j} pt_{o,c,j} (x) X_{c,j}, pt_{o,c,j}
+//   holding W[o][c][i][j] at slots b*H + g*i; rescale; sum inside each block by
+//   rotate-and-add over g, 2g, ..., H/2 (SumRowVec-style, Sec. II-B); add the
+//   bias. The logit o of image b is at slot b*H of Z_o.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "oracle_internal.h"
+
+namespace oracle {
+Ct ct_from(const Ctx& C, const u64* p, int n_polys, int limbs);
+void ct_to(const Ctx& C, const Ct& ct, u64* p);
+
+// D_idx, idx < p, from A_k, B~_k (k < n), all at the same level.
+static std::vector<Ct> matmul(Ctx& C, const std::vector<Ct>& A, const std::vector<Ct>& B, int p) {
+  const int n = (int)A.size();
+  std::vector<long> steps(p);
+  for (int idx = 0; idx < p; idx++) steps[idx] = idx;
+  std::vector<std::vector<Ct>> R(n);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < n; k++) R[k] = ct_rotate_hoisted(C, B[k], steps);
+  std::vector<Ct> D(p);
+#pragma omp parallel for schedule(dynamic)
+  for (int idx = 0; idx < p; idx++) {
+    Ct T = ct_tensor(C, A[0], R[0][idx]);
+    for (int k = 1; k < n; k++) T = ct_add(C, T, ct_tensor(C, A[k], R[k][idx]));
+    D[idx] = ct_rescale(C, ct_relin(C, T));
+  }
+  return D;
+}
+
+static i64 quantise(double w, u64 q) { return std::llround(w * (double)q); }
+
+// Convolution outputs sel = [(o, j')] from inputs X[c][j].
+// schedule 0: rotate the inputs, then multiply-accumulate (the canonical one).
+// schedule 1: multiply-accumulate per row offset a, then rotate the partial
+//             sums by g*a and add (the SumForConv order of Alg. 1 / Alg. 4).
+static std::vector<Ct> conv2d(Ctx& C, const std::vector<std::vector<Ct>>& X, int gap, const double* Kw,
+                              const double* bias, int c_out, int k, int stride, double scale,
+                              const std::vector<std::pair<int, int>>& sel, int schedule) {
+  const int c_in = (int)X.size();
+  const int lp = X[0][0].limbs();
+  const u64 ql = C.q[lp - 1];
+  auto kw = [&](int o, int c, int a, int b) { return Kw[((o * c_in + c) * k + a) * k + b]; };
+  std::vector<Ct> out(sel.size());
+  if (schedule == 0) {
+    std::set<std::pair<int, int>> need;
+    for (auto& s : sel)
+      for (int c = 0; c < c_in; c++)
+        for (int b = 0; b < k; b++) need.insert({c, stride * s.second + b});
+    std::vector<std::pair<int, int>> needv(need.begin(), need.end());
+    std::vector<long> steps(k);
+    for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
+    std::vector<std::vector<Ct>> rot(needv.size());
+#pragma omp parallel for schedule(dynamic)
+    for (size_t t = 0; t < needv.size(); t++) rot[t] = ct_rotate_hoisted(C, X[needv[t].first][needv[t].second], steps);
+    std::map<std::pair<int, int>, size_t> where;
+    for (size_t t = 0; t < needv.size(); t++) where[needv[t]] = t;
+#pragma omp parallel for schedule(dynamic)
+    for (size_t t = 0; t < sel.size(); t++) {
+      const int o = sel[t].first, jp = sel[t].second;
+      Ct acc;
+      bool first = true;
+      for (int c = 0; c < c_in; c++)
+        for (int b = 0; b < k; b++)
+          for (int a = 0; a < k; a++) {
+            Ct term = ct_mul_scalar(C, rot[where.at({c, stride * jp + b})][a], quantise(kw(o, c, a, b), ql));
+            acc = first ? term : ct_add(C, acc, term);
+            first = false;
+          }
+      Ct r = ct_rescale(C, acc);
+      if (bias) r = ct_add_const(C, r, std::llround(bias[o] * scale));
+      out[t] = r;
+    }
+  } else {
+#pragma omp parallel for schedule(dynamic)
+    for (size_t t = 0; t < sel.size(); t++) {
+      const int o = sel[t].first, jp = sel[t].second;
+      Ct acc;
+      for (int a = 0; a < k; a++) {
+        Ct part;
+        bool first = true;
+        for (int c = 0; c < c_in; c++)
+          for (int b = 0; b < k; b++) {
+            Ct term = ct_mul_scalar(C, X[c][stride * jp + b], quantise(kw(o, c, a, b), ql));
+            part = first ? term : ct_add(C, part, term);
+            first = false;
+          }
+        Ct rotated = ct_rotate_hoisted(C, part, {(long)gap * a})[0];
+        acc = a == 0 ? rotated : ct_add(C, acc, rotated);
+      }
+      Ct r = ct_rescale(C, acc);
+      if (bias) r = ct_add_const(C, r, std::llround(bias[o] * scale));
+      out[t] = r;
+    }
+  }
+  return out;
+}
+
+// Square activation: tensor, relinearise, rescale.
+static Ct square(Ctx& C, const Ct& x) { return ct_rescale(C, ct_relin(C, ct_tensor(C, x, x))); }
+
+// Plaintext of FC weights for output o, input column (c, j): W[o][c][i][j] at
+// slot b*H + g*i for every block b < B and valid row i < hv, zero elsewhere,
+// encoded at scale q_l.
+static std::vector<i64> fc_plaintext(const Ctx& C, const double* W, int o, int c, int j, int c_in, int hv,
+                                     int w_in, int gap, int H, int B, u64 ql) {
+  std::vector<double> z(C.N / 2, 0.0);
+  const size_t row = (size_t)c_in * hv * w_in;
+  for (int b = 0; b < B; b++)
+    for (int i = 0; i < hv; i++) z[(size_t)b * H + (size_t)gap * i] = W[(size_t)o * row + ((size_t)c * hv + i) * w_in + j];
+  return encode(C, z.data(), z.size(), (double)ql);
+}
+
+static Ct fc_output(Ctx& C, const std::vector<std::vector<Ct>>& X, const std::vector<std::vector<i64>>& pts /* [c*w+j] */,
+                    int gap, int H, double bias_o, bool has_bias, double scale) {
+  const int c_in = (int)X.size(), w_in = (int)X[0].size();
+  const int lp = X[0][0].limbs();
+  // sum_{c,j} pt (x) X, each product a negacyclic product per limb
+  Ct acc;
+  acc.c.assign(2, RnsPoly(lp, Poly(C.N, 0)));
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < lp; i++) {
+    const u64 q = C.q[i];
+    for (int t = 0; t < 2; t++) {
+      Poly sum(C.N, 0), x(C.N), y(C.N);
+      for (int c = 0; c < c_in; c++)
+        for (int j = 0; j < w_in; j++) {
+          const std::vector<i64>& pt = pts[(size_t)c * w_in + j];
+          for (size_t n = 0; n < C.N; n++) y[n] = reduce_signed(pt[n], q);
+          x = X[c][j].c[t][i];
+          ntt_fwd(C, i, x.data());
+          ntt_fwd(C, i, y.data());
+          for (size_t n = 0; n < C.N; n++) sum[n] = addmod(sum[n], mulmod(x[n], y[n], q), q);
+        }
+      ntt_inv(C, i, sum.data());
+      acc.c[t][i] = sum;
+    }
+  }
+  C.cnt.ct_plain += (long)c_in * w_in;
+  Ct z = ct_rescale(C, acc);
+  for (int t = gap; t < H; t *= 2) z = ct_add(C, z, ct_rotate_hoisted(C, z, {(long)t})[0]);
+  if (has_bias) z = ct_add_const(C, z, std::llround(bias_o * scale));
+  return z;
+}
+
+}  // namespace oracle
+
+using namespace oracle;
+
+static thread_local std::string g_lerr;
+#define OL_TRY(...)                    \
+  try {                                \
+    __VA_ARGS__;                       \
+    return 0;                          \
+  } catch (const std::exception& e) {  \
+    g_lerr = e.what();                 \
+    return -1;                         \
+  }
+
+static std::vector<Ct> cts_from(const Ctx& C, const uint64_t* p, int n, int limbs) {
+  std::vector<Ct> v(n);
+  for (int t = 0; t < n; t++) v[t] = ct_from(C, p + (size_t)t * 2 * limbs * C.N, 2, limbs);
+  return v;
+}
+static void cts_to(const Ctx& C, const std::vector<Ct>& v, uint64_t* p) {
+  for (size_t t = 0; t < v.size(); t++) ct_to(C, v[t], p + t * 2 * v[t].limbs() * C.N);
+}
+
+extern "C" {
+
+const char* ol_last_error() { return g_lerr.c_str(); }
+
+// A [n][2][lp][N], B [n][2][lp][N] -> D [p][2][lp-1][N]
+int oc_matmul(void* h, const uint64_t* A, const uint64_t* B, int n, int p, int lp, uint64_t* D) {
+  OL_TRY(Ctx* C = (Ctx*)h; std::vector<Ct> d = matmul(*C, cts_from(*C, A, n, lp), cts_from(*C, B, n, lp), p);
+         cts_to(*C, d, D));
+}
+
+// X [c_in][w_in][2][lp][N]; K [c_out][c_in][k][k]; bias [c_out] or NULL;
+// sel [n_sel][2] = (o, j'); out [n_sel][2][lp-1][N].
+int oc_conv2d(void* h, const uint64_t* X, int lp, int c_in, int w_in, int gap, const double* K, const double* bias,
+              int c_out, int k, int stride, double scale, int n_sel, const int* sel, int schedule, uint64_t* out) {
+  OL_TRY(Ctx* C = (Ctx*)h; std::vector<std::vector<Ct>> x(c_in);
+         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * 2 * lp * C->N, w_in, lp);
+         std::vector<std::pair<int, int>> s(n_sel);
+         for (int t = 0; t < n_sel; t++) {
+           s[t] = {sel[2 * t], sel[2 * t + 1]};
+           if (s[t].first < 0 || s[t].first >= c_out || stride * s[t].second + k > w_in) throw std::runtime_error("bad output index");
+         }
+         std::vector<Ct> r = conv2d(*C, x, gap, K, bias, c_out, k, stride, scale, s, schedule);
+         cts_to(*C, r, out));
+}
+
+// x [n][2][lp][N] -> [n][2][lp-1][N]
+int oc_square(void* h, const uint64_t* X, int n, int lp, uint64_t* out) {
+  try {
+    Ctx* C = (Ctx*)h;
+    std::vector<Ct> x = cts_from(*C, X, n, lp);
+    std::vector<Ct> r(n);
+    for (int t = 0; t < n; t++) r[t] = square(*C, x[t]);
+    cts_to(*C, r, out);
+    return 0;
+  } catch (const std::exception& e) {
+    g_lerr = e.what();
+    return -1;
+  }
+}
+
+// FC plaintexts for outputs sel_o: pts [n_sel][c_in][w_in][N] (int64 coefficients)
+int oc_fc_plaintexts(void* h, int lp, int c_in, int hv, int w_in, int gap, int H, int B, const double* W, int n_sel,
+                     const int* sel_o, int64_t* pts) {
+  Ctx* C = (Ctx*)h;
+  const u64 ql = C->q[lp - 1];
+  const long tot = (long)n_sel * c_in * w_in;
+#pragma omp parallel for schedule(dynamic)
+  for (long t = 0; t < tot; t++) {
+    const int s = (int)(t / ((long)c_in * w_in)), rem = (int)(t % ((long)c_in * w_in));
+    std::vector<i64> pt = fc_plaintext(*C, W, sel_o[s], rem / w_in, rem % w_in, c_in, hv, w_in, gap, H, B, ql);
+    std::memcpy(pts + (size_t)t * C->N, pt.data(), C->N * 8);
+  }
+  return 0;
+}
+
+// X [c_in][w_in][2][lp][N]; pts [n_sel][c_in][w_in][N] from oc_fc_plaintexts;
+// bias [out] or NULL; out [n_sel][2][lp-1][N].
+int oc_fc(void* h, const uint64_t* X, int lp, int c_in, int w_in, int gap, int H, const int64_t* pts,
+          const double* bias, double scale, int n_sel, const int* sel_o, uint64_t* out) {
+  OL_TRY(Ctx* C = (Ctx*)h; std::vector<std::vector<Ct>> x(c_in);
+         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * 2 * lp * C->N, w_in, lp);
+         for (int s = 0; s < n_sel; s++) {
+           std::vector<std::vector<i64>> p((size_t)c_in * w_in);
+           for (size_t t = 0; t < p.size(); t++) {
+             const int64_t* src = pts + ((size_t)s * c_in * w_in + t) * C->N;
+             p[t].assign(src, src + C->N);
+           }
+           Ct z = fc_output(*C, x, p, gap, H, bias ? bias[sel_o[s]] : 0.0, bias != nullptr, scale);
+           ct_to(*C, z, out + (size_t)s * 2 * (lp - 1) * C->N);
+         });
+}
+
+}  // extern "C"

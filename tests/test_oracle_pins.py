@@ -1,0 +1,490 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+These run without a GPU. Each test checks the oracle against something other
+than itself: textbook definitions evaluated with Python integers (schoolbook
+negacyclic product, the NTT's defining sum, CRT lifts), closed forms (the
+canonical-embedding sum), invariants (rotation = slot shift after decryption,
+automorphisms are ring maps), the paper's worked examples
+(tests/golden/*.txt) and the FP64 results the encrypted layers must decrypt to.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import sympy
+
+from inputs import synthetic
+from oracle import Oracle, fp64_ref, layouts, slot_sim
+from tests.conftest import golden_path
+
+
+def brv(x: int, bits: int) -> int:
+    return int(format(x, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+@pytest.fixture(scope="module")
+def small():
+    o = Oracle(5, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=11)
+    o.keygen([1, 2, 3, 5, -1, 7])
+    return o
+
+
+@pytest.fixture(scope="module")
+def hybrid():
+    # two special primes, digits of two primes (the CNN parameter shape), small ring
+    o = Oracle(6, (60, 45, 45, 45, 45), 2, 60, 2, 45.0, seed=5)
+    o.keygen([1, 2, 4])
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Prime chain and roots
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("log_n,q_bits,K,sb", [(13, (60, 40, 40), 1, 60), (16, (60,) + (45,) * 12, 2, 60),
+                                               (15, (60,) + (40,) * 8, 1, 60)])
+def test_prime_chain_rule(log_n, q_bits, K, sb):
+    o = Oracle(log_n, q_bits, K, sb, 1 if K == 1 else 2, 40.0)
+    two_n = 2 * (1 << log_n)
+    assert len(set(o.primes)) == len(o.primes)
+    for q, b in zip(o.primes, list(q_bits) + [sb] * K):
+        assert sympy.isprime(q)
+        assert q % two_n == 1
+        assert q.bit_length() == b
+    # the specials are the largest candidates of their size, q_0 the next one
+    cands = [(1 << sb) - t * two_n + 1 for t in range(1, 2000)]
+    primes_sb = [c for c in cands if sympy.isprime(c)]
+    assert o.p == primes_sb[:K]
+    if q_bits[0] == sb:
+        assert o.q[0] == primes_sb[K]
+    # q_1..q_L: the largest unused candidates of their size, in order
+    b = q_bits[1]
+    cands_b = [c for c in ((1 << b) - t * two_n + 1 for t in range(1, 4000)) if sympy.isprime(c)]
+    same = [q for q, bb in zip(o.q[1:], q_bits[1:]) if bb == b]
+    assert b != sb and same == cands_b[: len(same)]
+
+
+def test_psi_is_primitive_2n_root(small):
+    for pi, q in enumerate(small.primes):
+        psi = small.psi(pi)
+        assert pow(psi, small.N, q) == q - 1
+        # the root comes from the smallest quadratic non-residue
+        x = next(x for x in range(2, 1000) if pow(x, (q - 1) // 2, q) == q - 1)
+        assert psi == pow(x, (q - 1) // (2 * small.N), q)
+
+
+# ---------------------------------------------------------------------------
+# P1: NTT against its defining sum and against the schoolbook product
+# ---------------------------------------------------------------------------
+def test_ntt_matches_definition(small):
+    rng = np.random.default_rng(0)
+    N, bits = small.N, small.log_n
+    for pi, q in enumerate(small.primes):
+        a = [int(x) for x in rng.integers(0, q, N, dtype=np.uint64)]
+        psi = small.psi(pi)
+        ref = [sum(a[i] * pow(psi, (2 * brv(j, bits) + 1) * i, q) for i in range(N)) % q for j in range(N)]
+        got = small.ntt(np.array(a, dtype=np.uint64), pi)
+        assert [int(x) for x in got] == ref
+        assert [int(x) for x in small.ntt(got, pi, inverse=True)] == a
+
+
+def schoolbook_negacyclic(a, b, q):
+    N = len(a)
+    r = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                r[k] += a[i] * b[j]
+            else:
+                r[k - N] -= a[i] * b[j]
+    return [x % q for x in r]
+
+
+@pytest.mark.parametrize("log_n", [4, 6])
+def test_polymul_matches_schoolbook(log_n):
+    o = Oracle(log_n, (60, 40, 45), 2, 60, 1, 40.0)
+    rng = np.random.default_rng(log_n)
+    for pi, q in enumerate(o.primes):
+        a = [int(x) for x in rng.integers(0, q, o.N, dtype=np.uint64)]
+        b = [int(x) for x in rng.integers(0, q, o.N, dtype=np.uint64)]
+        got = o.polymul(np.array(a, dtype=np.uint64), np.array(b, dtype=np.uint64), pi)
+        assert [int(x) for x in got] == schoolbook_negacyclic(a, b, q)
+
+
+def test_automorphism_is_ring_map(small):
+    rng = np.random.default_rng(3)
+    q = small.q[1]
+    a = rng.integers(0, q, small.N, dtype=np.uint64)
+    b = rng.integers(0, q, small.N, dtype=np.uint64)
+    for step in (1, 2, 5):
+        k = small.galois_elt(step)
+        assert k == pow(5, step, 2 * small.N)
+        lhs = small.automorph(small.polymul(a, b, 1), k, 1)
+        rhs = small.polymul(small.automorph(a, k, 1), small.automorph(b, k, 1), 1)
+        assert np.array_equal(lhs, rhs)
+    k1, k2 = small.galois_elt(1), small.galois_elt(2)
+    assert np.array_equal(small.automorph(small.automorph(a, k1, 1), k2, 1),
+                          small.automorph(a, (k1 * k2) % (2 * small.N), 1))
+    # definition on X: X -> X^k, with X^N = -1
+    x = np.zeros(small.N, np.uint64)
+    x[1] = 1
+    k = small.galois_elt(3)
+    e = k % (2 * small.N)
+    y = small.automorph(x, k, 1)
+    exp = np.zeros(small.N, np.uint64)
+    if e < small.N:
+        exp[e] = 1
+    else:
+        exp[e - small.N] = q - 1
+    assert np.array_equal(y, exp)
+
+
+# ---------------------------------------------------------------------------
+# P2: base conversion, ModDown and rescale against big-integer CRT lifts
+# ---------------------------------------------------------------------------
+def crt(res, mods):
+    M = math.prod(mods)
+    x = 0
+    for r, m in zip(res, mods):
+        Mi = M // m
+        x += int(r) * Mi * pow(Mi, -1, m)
+    return x % M
+
+
+def test_modup_is_crt_lift_plus_small_multiple(hybrid):
+    o = hybrid
+    rng = np.random.default_rng(7)
+    lp = 4  # three digits at alpha = 2: {q0,q1}, {q2,q3}
+    x = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.q[:lp]])
+    basis = o.q[:lp] + o.p
+    for j in range(2):
+        I = list(range(2 * j, min(2 * j + 2, lp)))
+        D = math.prod(o.q[i] for i in I)
+        ext = o.modup(x, j)
+        for n in range(0, o.N, 7):
+            X = crt([x[i][n] for i in I], [o.q[i] for i in I])
+            ok = False
+            for u in range(len(I)):
+                if all(int(ext[pos][n]) == (X + u * D) % t for pos, t in enumerate(basis)):
+                    ok = True
+            assert ok, (j, n)
+
+
+def test_moddown_is_division_by_p(hybrid):
+    o = hybrid
+    rng = np.random.default_rng(8)
+    lp = 3
+    basis = o.q[:lp] + o.p
+    u = np.stack([rng.integers(0, t, o.N, dtype=np.uint64) for t in basis])
+    out = o.moddown(u)
+    Q = math.prod(o.q[:lp])
+    P = math.prod(o.p)
+    for n in range(0, o.N, 5):
+        U = crt([u[i][n] for i in range(len(basis))], basis)
+        UP = U % P
+        ok = False
+        for e in range(o.K):
+            V = ((U - UP) // P - e) % Q
+            if all(int(out[i][n]) == V % q for i, q in enumerate(o.q[:lp])):
+                ok = True
+        assert ok, n
+
+
+def test_rescale_rounds_half_up(small):
+    o = small
+    rng = np.random.default_rng(9)
+    lp = 4
+    ct = np.stack([np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.q[:lp]]) for _ in range(2)])
+    out = o.rescale(ct)
+    ql = o.q[lp - 1]
+    Q = math.prod(o.q[:lp])
+    for t in range(2):
+        for n in range(o.N):
+            X = crt([ct[t][i][n] for i in range(lp)], o.q[:lp])
+            V = ((X + ql // 2) // ql) % (Q // ql)
+            assert [int(out[t][i][n]) for i in range(lp - 1)] == [V % q for q in o.q[: lp - 1]]
+
+
+# ---------------------------------------------------------------------------
+# P3: encoding (canonical embedding) and encryption
+# ---------------------------------------------------------------------------
+def test_encode_matches_embedding_sum():
+    o = Oracle(5, (60, 40), 1, 60, 1, 30.0)
+    N, S = o.N, o.slots
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-1, 1, S)
+    m = o.encode(z)
+    zeta = np.exp(1j * np.pi / N)
+    e = [pow(5, j, 2 * N) for j in range(S)]
+    for k in range(N):
+        val = o.scale * (2.0 / N) * sum(z[j] * zeta ** (-e[j] * k) for j in range(S)).real
+        assert abs(m[k] - val) <= 0.5 + 1e-6
+    # m(zeta^(5^j)) = scale * z_j
+    for j in range(S):
+        ev = sum(int(m[k]) * zeta ** (e[j] * k) for k in range(N))
+        assert abs(ev / o.scale - z[j]) < 1e-8
+
+
+def test_decode_inverts_encode():
+    o = Oracle(12, (60, 40), 1, 60, 1, 40.0)
+    z = np.random.default_rng(2).uniform(-1, 1, o.slots)
+    assert np.abs(o.decode(o.encode(z).astype(float)) - z).max() < 1e-9
+
+
+def test_secret_is_ternary(small):
+    s = small.secret()
+    assert set(np.unique(s)).issubset({-1, 0, 1})
+    counts = [int((s == v).sum()) for v in (-1, 0, 1)]
+    assert min(counts) > 0
+
+
+def test_encrypt_decrypt(small):
+    z = np.random.default_rng(3).uniform(-1, 1, small.slots)
+    m = small.encode(z)
+    for limbs in (4, 2, 1):
+        ct = small.encrypt(m, limbs, ct_id=limbs)
+        assert np.abs(small.decrypt(ct) - z).max() < 1e-6
+        # the error in the coefficient domain is small and not zero
+        err = small.decrypt_coeffs(ct) - m
+        assert 0 < np.abs(err).max() < 200
+    # distinct ciphertext ids draw distinct randomness
+    a, b = small.encrypt(m, 4, 1), small.encrypt(m, 4, 2)
+    assert not np.array_equal(a, b)
+    assert np.array_equal(a, small.encrypt(m, 4, 1))
+
+
+# ---------------------------------------------------------------------------
+# P4 / P5: Rot, key switching, Mul, cMul (Sec. II-A)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fx", ["small", "hybrid"])
+def test_rotation_is_left_shift(fx, request):
+    o = request.getfixturevalue(fx)
+    z = np.random.default_rng(4).uniform(-1, 1, o.slots)
+    ct = o.encrypt(o.encode(z), ct_id=3)
+    steps = [0, 1, 2] if fx == "hybrid" else [0, 1, 3, 5, -1, 7]
+    r = o.rotate(ct, steps)
+    for t, s in enumerate(steps):
+        assert np.abs(o.decrypt(r[t]) - np.roll(z, -s)).max() < 1e-6, s
+    # a wrong direction would fail
+    assert np.abs(o.decrypt(r[1]) - np.roll(z, steps[1])).max() > 1e-2
+
+
+@pytest.mark.parametrize("fx", ["small", "hybrid"])
+def test_keyswitch_noise_is_small(fx, request):
+    o = request.getfixturevalue(fx)
+    rng = np.random.default_rng(6)
+    for lp in (o.L1, 2):
+        x = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.q[:lp]])
+        negx = np.stack([(np.uint64(q) - x[i]) % np.uint64(q) for i, q in enumerate(o.q[:lp])])
+        v = o.keyswitch(x, 0)
+        e = o.decrypt_coeffs(np.stack([v[0], v[1], negx]))  # v0 + v1 s - x s^2
+        assert np.abs(e).max() < 2000
+
+
+def test_tensor_relin_rescale(small):
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(-1, 1, small.slots), rng.uniform(-1, 1, small.slots)
+    a = small.encrypt(small.encode(x), ct_id=10)
+    b = small.encrypt(small.encode(y), ct_id=11)
+    d = small.tensor(a, b)
+    assert np.abs(small.decrypt(d, small.scale ** 2) - x * y).max() < 1e-6
+    r = small.relin(d)
+    assert np.abs(small.decrypt(r, small.scale ** 2) - x * y).max() < 1e-6
+    s = small.rescale(r)
+    assert np.abs(small.decrypt(s, small.scale ** 2 / small.q[-1]) - x * y).max() < 1e-6
+    # Add
+    assert np.abs(small.decrypt(small.add(a, b)) - (x + y)).max() < 1e-6
+
+
+def test_cmul_scalar_and_plain(small):
+    rng = np.random.default_rng(12)
+    x, w = rng.uniform(-1, 1, small.slots), rng.uniform(-1, 1, small.slots)
+    a = small.encrypt(small.encode(x), ct_id=20)
+    ql = small.q[-1]
+    r = small.rescale(small.mul_scalar(a, round(0.37 * ql)))
+    assert np.abs(small.decrypt(r) - 0.37 * x).max() < 1e-6
+    r = small.rescale(small.mul_plain(a, small.encode(w, float(ql))))
+    assert np.abs(small.decrypt(r) - w * x).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Paper's worked examples in the plaintext slot simulator (P8, P9)
+# ---------------------------------------------------------------------------
+def read_blocks(name):
+    blocks, cur, tag = [], None, None
+    for line in open(golden_path(name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line in ("matrix", "bias"):
+            cur = []
+            blocks.append((line, cur))
+            continue
+        row = [int(v) for v in line.split()]
+        if cur is None:
+            cur = []
+            blocks.append(("matrix", cur))
+        cur.append(row)
+    return [(t, np.array(m)) for t, m in blocks]
+
+
+def test_sumforconv_worked_example():
+    flags = read_blocks("sumforconv_h4_w4_k3.txt")[0][1]
+    Z = np.random.default_rng(0).uniform(-1, 1, (4, 4))
+    got = (slot_sim.sum_for_conv(Z.reshape(-1), 4, 4, 3) * slot_sim.valid_mask(4, 4, 3)).reshape(4, 4)
+    for i in range(4):
+        for j in range(4):
+            exp = Z[i:i + 3, j:j + 3].sum() if flags[i, j] else 0.0
+            assert abs(got[i, j] - exp) < 1e-12
+    # the literal text (row pass on the input) does not give the printed box sums
+    lit = (slot_sim.sum_for_conv(Z.reshape(-1), 4, 4, 3, separable=False) * slot_sim.valid_mask(4, 4, 3)).reshape(4, 4)
+    assert abs(lit[0, 0] - Z[0:3, 0:3].sum()) > 1e-6
+
+
+def test_kernelspanner_worked_example():
+    blocks = read_blocks("kernelspanner_h4_w4_k2.txt")
+    kv = {1: 2.0, 2: 3.0, 3: 5.0, 4: 7.0, 5: 11.0}
+    K = np.array([[kv[1], kv[2]], [kv[3], kv[4]]])
+    sim = slot_sim.kernelspanner(K, 4, 4)
+    expect = [np.vectorize(lambda e: kv.get(e, 0.0))(m) for t, m in blocks if t == "matrix"]
+    assert len(expect) == len(sim) == 4
+    for E in expect:
+        assert any(np.array_equal(E, P) for P in sim.values())
+    bias = [np.vectorize(lambda e: kv.get(e, 0.0))(m) for t, m in blocks if t == "bias"][0]
+    assert np.array_equal(slot_sim.bias_block(kv[5], 4, 4, 2), bias)
+
+
+@pytest.mark.parametrize("h,w,k", [(4, 4, 2), (6, 5, 3), (7, 7, 3), (9, 8, 4)])
+def test_alg4_slot_simulation_is_convolution(h, w, k):
+    rng = np.random.default_rng(h * 100 + w * 10 + k)
+    I = rng.uniform(0, 1, (h, w))
+    K = rng.normal(0, 1, (k, k))
+    out = slot_sim.conv_alg4(I, K, 0.3)
+    ref = fp64_ref.conv2d(I[None, None], K[None, None], [0.3], 1)[0, 0]
+    assert np.abs(out[: h - k + 1, : w - k + 1] - ref).max() < 1e-12
+    assert np.abs(out[h - k + 1:, :]).max() == 0 and np.abs(out[:, w - k + 1:]).max() == 0
+
+
+def test_multi_ct_layouts_in_slot_simulator():
+    rng = np.random.default_rng(2)
+    A = rng.uniform(-1, 1, (6, 5))
+    Bm = rng.uniform(-1, 1, (5, 4))
+    D = slot_sim.matmul_multi_ct(A, Bm, 64)
+    assert np.abs(layouts.matmul_from_diagonals(D, 6, 4) - A @ Bm).max() < 1e-12
+    imgs = rng.uniform(0, 1, (2, 3, 11, 9))
+    K = rng.normal(0, 1, (4, 3, 3, 3))
+    bias = rng.normal(0, 1, 4)
+    for stride in (1, 2):
+        Y = slot_sim.conv_columns(imgs, K, bias, stride, 64, 16)
+        ref = fp64_ref.conv2d(imgs, K, bias, stride)
+        got = np.moveaxis(layouts.image_from_columns(Y, 2, 16, stride, ref.shape[2]), 0, 1)
+        # [O][B][h][w] -> [B][O][h][w]
+        assert np.abs(got - ref).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P6 / P7: encrypted layers decrypt to the FP64 results
+# ---------------------------------------------------------------------------
+def test_matmul_config_small_matches_fp64():
+    pre = synthetic.MATMUL_SMALL
+    o = Oracle.from_preset(pre, seed=101)
+    A, Bm = synthetic.matmul_operands(4, 8, 4, seed=101)
+    o.keygen(list(range(1, 4)))
+    Ac = np.stack([o.encrypt(o.encode(v), ct_id=i) for i, v in enumerate(layouts.matrix_a_columns(A, o.slots))])
+    Bc = np.stack([o.encrypt(o.encode(v), ct_id=100 + i) for i, v in enumerate(layouts.matrix_b_rows(Bm, o.slots))])
+    o.reset_counters()
+    D = o.matmul(Ac, Bc, 4)
+    sc = o.scale ** 2 / o.q[-1]
+    C = layouts.matmul_from_diagonals(np.stack([o.decrypt(d, sc) for d in D]), 4, 4)
+    assert np.abs(C - A @ Bm).max() < 1e-4
+    assert np.abs(C - A @ Bm).max() < 1e-6
+    # P10: n (p-1) rotations from n hoisted ModUps, n p tensors, p relins, p rescales
+    c = o.counters()
+    assert c["rotations"] == 8 * 3 and c["tensors"] == 32 and c["relins"] == 4 and c["rescales"] == 4
+    assert c["modups"] == 8 + 4  # one per B~_k, one per relinearisation
+
+
+def test_matmul_rectangular_detects_transposition():
+    o = Oracle(8, (60, 40, 40), 1, 60, 1, 40.0, seed=3)
+    o.keygen(list(range(1, 8)))
+    rng = np.random.default_rng(4)
+    A, Bm = rng.uniform(-1, 1, (5, 3)), rng.uniform(-1, 1, (3, 8))
+    Ac = np.stack([o.encrypt(o.encode(v), ct_id=i) for i, v in enumerate(layouts.matrix_a_columns(A, o.slots))])
+    Bc = np.stack([o.encrypt(o.encode(v), ct_id=50 + i) for i, v in enumerate(layouts.matrix_b_rows(Bm, o.slots))])
+    D = o.matmul(Ac, Bc, 8)
+    C = layouts.matmul_from_diagonals(np.stack([o.decrypt(d, o.scale ** 2 / o.q[-1]) for d in D]), 5, 8)
+    assert np.abs(C - A @ Bm).max() < 1e-6
+
+
+def encrypt_images(o, imgs, H, limbs=None, base_id=0):
+    """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
+    Bn, C, h, w = imgs.shape
+    out = []
+    for c in range(C):
+        z = layouts.image_columns(imgs[:, c], o.slots, H)
+        out.append(np.stack([o.encrypt(o.encode(z[j]), limbs, base_id + c * w + j) for j in range(w)]))
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("stride,c_in", [(1, 1), (2, 2)])
+def test_conv2d_matches_fp64_and_schedules_agree(stride, c_in):
+    o = Oracle(8, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=21)
+    k, c_out, H = 3, 2, 16
+    o.keygen([1, 2])
+    rng = np.random.default_rng(stride)
+    imgs = rng.uniform(0, 1, (3, c_in, 9, 8))
+    K = rng.normal(0, 0.3, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.3, c_out)
+    X = encrypt_images(o, imgs, H)
+    o.reset_counters()
+    Y = o.conv2d(X, 1, K, bias, stride, o.scale)
+    c = o.counters()
+    w_out = (8 - k) // stride + 1
+    ref = fp64_ref.conv2d(imgs, K, bias, stride)
+    z = np.stack([o.decrypt(y) for y in Y]).reshape(c_out, w_out, o.slots)
+    got = np.moveaxis(layouts.image_from_columns(z, 3, H, stride, ref.shape[2]), 0, 1)
+    assert np.abs(got - ref).max() < 1e-6
+    # P10: (k-1) rotations of every used input column, one ModUp each
+    used = min(8, stride * (w_out - 1) + k)
+    assert c["rotations"] == c_in * used * (k - 1) and c["modups"] == c_in * used
+    assert c["rescales"] == c_out * w_out and c["ct_scalar"] == c_out * w_out * c_in * k * k
+    # P12: the SumForConv order (multiply, then rotate partial sums) decrypts the same
+    Y2 = o.conv2d(X, 1, K, bias, stride, o.scale, schedule=1)
+    z2 = np.stack([o.decrypt(y) for y in Y2]).reshape(c_out, w_out, o.slots)
+    got2 = np.moveaxis(layouts.image_from_columns(z2, 3, H, stride, ref.shape[2]), 0, 1)
+    assert np.abs(got2 - got).max() < 1e-6
+    assert not np.array_equal(Y, Y2)  # different key switches, same decryption
+
+
+def test_cnn_small_matches_fp64():
+    """conv(5x5,s2) -> x^2 -> conv(3x3,s2) -> x^2 -> FC on a reduced ring and image."""
+    o = Oracle(9, (60,) + (45,) * 6, 2, 60, 2, 45.0, seed=31)
+    side, H, Bn = 17, 32, 2
+    h1 = (side - 5) // 2 + 1   # 7
+    h2 = (h1 - 3) // 2 + 1     # 3
+    rng = np.random.default_rng(31)
+    imgs = rng.uniform(0, 1, (Bn, side, side))
+    c1w, c1b = rng.normal(0, 0.2, (2, 1, 5, 5)), rng.normal(0, 0.2, 2)
+    c2w, c2b = rng.normal(0, 0.2, (3, 2, 3, 3)), rng.normal(0, 0.2, 3)
+    fw, fb = rng.normal(0, 0.2, (4, 3 * h2 * h2)), rng.normal(0, 0.2, 4)
+    o.keygen([1, 2, 3, 4, 6, 8, 16])
+    X = encrypt_images(o, imgs[:, None], H)
+    sc = o.scale
+    Y = o.conv2d(X, 1, c1w, c1b, 2, sc).reshape(2, h1, 2, -1, o.N)
+    Y = o.square(Y.reshape(-1, 2, Y.shape[-2], o.N)).reshape(2, h1, 2, -1, o.N)
+    sc = sc * sc / o.q[X.shape[3] - 2]
+    Y = o.conv2d(Y, 2, c2w, c2b, 2, sc).reshape(3, h2, 2, -1, o.N)
+    lp = Y.shape[3]
+    Y = o.square(Y.reshape(-1, 2, lp, o.N)).reshape(3, h2, 2, lp - 1, o.N)
+    sc = sc * sc / o.q[lp - 1]
+    pts = o.fc_plaintexts(lp - 1, 3, h2, h2, 4, H, Bn, fw, list(range(4)))
+    Z = o.fc(Y, 4, H, pts, fb, sc, list(range(4)))
+    z = np.stack([o.decrypt(zz, sc) for zz in Z])
+    logits = layouts.logits_from_fc(z, Bn, H)
+    x = imgs[:, None]
+    x = fp64_ref.conv2d(x, c1w, c1b, 2) ** 2
+    x = fp64_ref.conv2d(x, c2w, c2b, 2) ** 2
+    ref = fp64_ref.dense(x, fw, fb)
+    assert np.abs(logits - ref).max() < 1e-4
