@@ -1,0 +1,277 @@
+/*
+ * he_gb300.h - C ABI of the GB300 (sm_103a) RNS-CKKS engine for encrypted
+ * matrix multiplication and convolution over the multi-ciphertext layouts of
+ * "Volley Revolver: A Novel Matrix-Encoding Method for Privacy-Preserving
+ * Deep Learning (Inference++)" (arXiv 2512.18646).
+ *
+ * The paper (Sec. II-A) uses the CKKS primitives Enc, Dec, Add, Mul, cMul and
+ * Rot, and (abstract, Sec. I-C) encrypts an m x n by n x p matrix product as n
+ * ciphertexts per operand and an h x w image as w ciphertexts of h column
+ * pixels. This library evaluates those layouts with RNS-CKKS on the GPU:
+ * negacyclic NTTs over word-size primes, hybrid key switching with keys
+ * resident in device memory, and rescaling after every multiplication.
+ *
+ * Conventions for every entry point:
+ *  - Return value: HE_OK (0) or one of the HE_E_* codes below. On error the
+ *    outputs are left unset (no partially built handle is returned) and
+ *    he_last_error() gives a message for the calling thread.
+ *  - Handles (he_ctx, he_ctset, he_ptset, he_server) are created and owned by
+ *    the library; release them with the matching *_free / *_destroy call.
+ *    Destroying a context invalidates every handle made from it.
+ *  - Pointer arguments without further note are HOST pointers, borrowed for
+ *    the duration of the call. Arrays are C-contiguous, row-major.
+ *  - Work is enqueued on the context's CUDA stream. Calls that return host
+ *    data (decrypt, export, info that needs device state) synchronise that
+ *    stream; the others may return before the GPU finishes.
+ *  - A ciphertext set (he_ctset) is n ciphertexts at one level (number of Q
+ *    limbs) and one scale, held in device memory in the NTT domain as
+ *    [n][2][limbs][N] 64-bit residues.
+ *  - Rotation steps follow Rot(ct, l) of Sec. II-A: a left rotation of the
+ *    N/2 slots by l.
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HE_OK 0
+#define HE_E_ARG 1      /* invalid argument (size, shape, null pointer)        */
+#define HE_E_LEVEL 2    /* not enough levels left for the operation            */
+#define HE_E_NOKEY 3    /* a needed rotation key was not generated             */
+#define HE_E_SCALE 4    /* operands at different scales or levels              */
+#define HE_E_OOM 5      /* device allocation failed                            */
+#define HE_E_TIMEOUT 6  /* a bounded wait expired                              */
+#define HE_E_CUDA 7     /* a CUDA call failed                                  */
+#define HE_E_UNIMPL 8   /* operation not supported for these arguments         */
+#define HE_E_STATE 9    /* handle in the wrong state (e.g. no keys yet)        */
+
+typedef struct he_ctx he_ctx;       /* parameters, NTT tables, keys, stream      */
+typedef struct he_ctset he_ctset;   /* n ciphertexts at one level and scale      */
+typedef struct he_ptset he_ptset;   /* encoded plaintexts prepared on the device */
+
+/*
+ * Scheme parameters. Primes: the n_special primes of P take the largest
+ * special_bits-bit values of the form 2^b - t 2N + 1 (t = 1, 2, ...) that are
+ * prime; then q_0, q_1, ..., q_L take, in order, the largest unused such
+ * prime of q_bits[i] bits. Key switching uses digits of `alpha` consecutive
+ * Q primes (dnum = ceil(n_q / alpha) digits at the top level).
+ */
+typedef struct {
+  int log_n;           /* ring degree N = 2^log_n, 4 <= log_n <= 16           */
+  int n_q;             /* number of Q primes (levels + 1), 1..32             */
+  const int* q_bits;   /* n_q bit sizes, each in [20, 61]                     */
+  int n_special;       /* K >= 1 special primes                               */
+  int special_bits;    /* bit size of each special prime, in [20, 61]         */
+  int alpha;           /* primes per key-switching digit, >= 1                */
+  double log_scale;    /* encoding scale = 2^log_scale                        */
+  double sigma;        /* Gaussian error parameter (3.2)                      */
+} he_params_desc;
+
+/*
+ * he_ctx_create: build the prime chain, the NTT tables and the constants of
+ * base conversion and rescaling, on the GPU that is current for the calling
+ * thread. `seed` names every random stream keygen and encryption draw
+ * (inputs/he_random.h). `cuda_stream` is a cudaStream_t or NULL for the
+ * default stream. Errors: HE_E_ARG on invalid parameters, HE_E_CUDA /
+ * HE_E_OOM on device failures.
+ */
+int he_ctx_create(const he_params_desc* desc, uint64_t seed, void* cuda_stream, he_ctx** out);
+void he_ctx_destroy(he_ctx* ctx);
+
+/* The n_q + n_special primes, Q then P, into out[n] (n >= their count). */
+int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n);
+
+/* Ring degree exponent, prime counts, digit size, scale. Any pointer may be NULL. */
+int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* alpha, double* scale);
+
+/*
+ * he_keygen: draw the ternary secret s, the public key (-a s + e, a) over Q,
+ * the relinearisation key (s^2 -> s) and one Galois key per rotation step
+ * (phi_{5^l}(s) -> s), as hybrid key-switching keys over Q*P (Sec. II-A says
+ * the library provides these keys). All keys stay in device memory. The
+ * secret is kept in the context for decryption (the context is the key
+ * owner's). Steps are reduced mod N/2; 0 is ignored. May be called again to
+ * add rotation keys. Errors: HE_E_ARG, HE_E_OOM, HE_E_CUDA.
+ */
+int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps);
+
+/* ---- encryption into the paper's layouts (Enc_pk, Sec. II-A) ---- */
+
+/*
+ * he_encrypt_image: column-wise image layout (abstract; Sec. I-C). px is
+ * [batch][h][w] doubles. Output: w ciphertexts at the top level and scale
+ * 2^log_scale; ciphertext j holds column j, image b's row i at slot
+ * b * block_stride + i. block_stride is a power of two >= h with
+ * batch * block_stride <= N/2 (one image per block, the virtual ciphertexts
+ * of Sec. III-D). Ciphertext ids (the randomness streams) are ct_id_base + j.
+ */
+int he_encrypt_image(he_ctx* ctx, const double* px, int batch, int h, int w, int block_stride,
+                     uint64_t ct_id_base, he_ctset** out);
+
+/* A [m][n] -> n ciphertexts; ciphertext k holds column k of A at slots i < m
+ * (abstract; Sec. I-C: n ciphertexts per operand). Ids ct_id_base + k. */
+int he_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out);
+
+/* B [n][p] -> n ciphertexts; ciphertext k holds row k of B tiled with period p
+ * over every slot (the tiling of tau_b, Sec. III-A). p must divide N/2. */
+int he_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out);
+
+/*
+ * he_encrypt_coeffs: encrypt already-encoded plaintexts. m is [n_ct][N]
+ * signed integer coefficients; the result has `limbs` Q limbs and the given
+ * scale. Ciphertext i uses randomness id ct_id_base + i. Used to start two
+ * implementations from the same integer plaintexts.
+ */
+int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double scale, uint64_t ct_id_base,
+                      he_ctset** out);
+
+/* ---- evaluation (all operands in device memory) ---- */
+
+/*
+ * he_matmul: encrypted C = A B (Alg. 3 over n ciphertexts per operand, Sec.
+ * IV-A). A from he_encrypt_matrix_a (m x n), B from he_encrypt_matrix_b
+ * (n x p), same level and scale. Result: p ciphertexts at one level lower;
+ * ciphertext idx holds C[i][(i + idx) mod p] at slot i < m (decode with
+ * he_decrypt_matrix). Needs rotation keys for steps 1..p-1.
+ * Errors: HE_E_ARG (shape), HE_E_SCALE, HE_E_LEVEL, HE_E_NOKEY.
+ */
+int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C);
+
+/*
+ * he_matmul_batched: `count` independent products A[i] B[i] (each as in
+ * he_matmul, shapes m[i], p[i]) evaluated together; C[i] receives each
+ * result.
+ */
+int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
+                      const int* p, he_ctset** C);
+
+/*
+ * he_conv2d: valid 2-D convolution (cross-correlation, no kernel flip) over
+ * the column layout (Alg. 4 with channels summed as in Sec. IV-B). `in` holds
+ * c_in * w_in ciphertexts, channel-major ([c][j]), rows at gap `gap` (1 for an
+ * input image). weights [c_out][c_in][k][k], bias [c_out] or NULL. Output:
+ * c_out * w_out ciphertexts ([o][j']), w_out = (w_in - k) / stride + 1, row
+ * gap gap * stride, one level lower, same scale. Needs rotation keys for
+ * steps gap * a, a = 1..k-1.
+ */
+int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* weights, const double* bias,
+              int c_out, int k, int stride, he_ctset** out);
+
+/*
+ * he_poly_act: polynomial activation in place. Supported: degree 2 with
+ * coeffs {0, 0, 1} (x -> x^2: tensor, relinearise, rescale). Other
+ * polynomials return HE_E_UNIMPL.
+ */
+int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree);
+
+/*
+ * he_fc_prepare: encode dense-layer weights for inputs in the column layout:
+ * W [out_dim][c_in * h_valid * w_in] in (channel, row, column) order; for
+ * output o and input column (c, j) a plaintext with W[o][c][i][j] at slot
+ * b * block_stride + gap * i for every block b < batch. Plaintexts are
+ * encoded at scale q_l (the prime dropped after the product) at `limbs`
+ * limbs, and kept on the device.
+ */
+int he_fc_prepare(he_ctx* ctx, const double* W, int out_dim, int c_in, int h_valid, int w_in, int gap,
+                  int block_stride, int batch, int limbs, he_ptset** out);
+
+/* Same, from integer coefficients pts [out_dim][c_in][w_in][N] encoded elsewhere. */
+int he_fc_prepare_coeffs(he_ctx* ctx, const int64_t* pts, int out_dim, int c_in, int w_in, int gap,
+                         int block_stride, int limbs, he_ptset** out);
+void he_ptset_free(he_ptset* pts);
+
+/*
+ * he_fc_apply: Z_o = sum_{c,j} pt_{o,c,j} (x) in_{c,j}, rescale, then sum
+ * inside each block by rotate-and-add over gap, 2 gap, ..., block_stride / 2,
+ * then add bias[o] (NULL for none). Logit o of image b is at slot
+ * b * block_stride of output o (he_decrypt_slots). Needs rotation keys for
+ * those steps.
+ */
+int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const double* bias, he_ctset** out);
+
+/* he_fc: he_fc_prepare + he_fc_apply + he_ptset_free. */
+int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int out_dim, int c_in, int h_valid,
+          int w_in, int gap, int block_stride, int batch, he_ctset** out);
+
+/* ---- primitives (Sec. II-A), for composition and testing ---- */
+
+/* Rot(ct, l) for every ciphertext of `in` and every step: one ModUp per
+ * ciphertext shared by its steps (hoisting). out has n * n_steps
+ * ciphertexts, [ct][step]. */
+int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps, he_ctset** out);
+
+/* Mul(a_i, b_i) pairwise: tensor product, relinearisation, rescale. */
+int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out);
+
+/* Drop the last prime: round(x / q_l) in every limb; scale /= q_l. */
+int he_rescale(he_ctx* ctx, he_ctset* inout);
+
+/* Add(a_i, b_i) pairwise (same level and scale). */
+int he_add(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out);
+
+/* ---- decryption (Dec_sk, Sec. II-A) ---- */
+
+/*
+ * he_decrypt_slots: out [n][N/2] real slot values. Decryption computes
+ * c0 + c1 s on the device and reads the q_0 limb: valid while |message +
+ * noise| < q_0 / 2, which the parameter sets keep (q_0 is the large base
+ * prime).
+ */
+int he_decrypt_slots(he_ctx* ctx, const he_ctset* in, double* out, size_t out_len);
+
+/* he_decrypt_matrix: C [m][p] from he_matmul's p diagonal ciphertexts. */
+int he_decrypt_matrix(he_ctx* ctx, const he_ctset* C, int m, int p, double* C_out);
+
+/* he_decrypt_image: [batch][n_ct][h_valid] column values, row i of image b
+ * read at slot b * block_stride + gap * i of each ciphertext. */
+int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_stride, int gap, int h_valid,
+                     double* out, size_t out_len);
+
+/* ---- ciphertext sets ---- */
+
+/* Copy out as coefficient-domain limbs [n][2][limbs][N] (inverse NTT on the
+ * device). n_words must be at least n * 2 * limbs * N. Synchronises. */
+int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words);
+
+/* Build a set from coefficient-domain limbs [n][2][limbs][N] (residues < q_i). */
+int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
+
+/* Number of ciphertexts, limbs (level + 1), scale. Any pointer may be NULL. */
+int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale);
+
+/* Device address of the residues, [n][2][limbs][N] uint64 in the NTT domain. */
+int he_ctset_device_ptr(const he_ctset* set, uint64_t** dptr);
+
+/* A set of n ciphertexts taken from `set` starting at ciphertext `first`
+ * (a copy). */
+int he_ctset_slice(he_ctx* ctx, const he_ctset* set, int first, int n, he_ctset** out);
+
+/* Concatenate sets of equal level and scale (a copy). */
+int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_ctset** out);
+
+void he_ctset_free(he_ctset* set);
+
+/* ---- transforms (testing) ---- */
+
+/*
+ * he_ntt: negacyclic NTT of host data [n_polys][limbs][N] in place, limb i
+ * modulo q_i (prime index `first_prime` + i). Forward: out[j] =
+ * sum_i a_i psi^((2 brv(j) + 1) i) mod q with psi = x^((q-1)/2N) for the
+ * smallest quadratic non-residue x of q; inverse undoes it.
+ */
+int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* he_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HE_GB300_H */

@@ -1,0 +1,101 @@
+"""ctypes binding of libhegb300.so (the C ABI in include/he_gb300.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Loading fails loudly if the library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhegb300.so")
+
+HE_OK, HE_E_ARG, HE_E_LEVEL, HE_E_NOKEY, HE_E_SCALE, HE_E_OOM, HE_E_TIMEOUT, HE_E_CUDA, HE_E_UNIMPL, HE_E_STATE = range(10)
+ERROR_NAMES = {1: "HE_E_ARG", 2: "HE_E_LEVEL", 3: "HE_E_NOKEY", 4: "HE_E_SCALE", 5: "HE_E_OOM", 6: "HE_E_TIMEOUT",
+               7: "HE_E_CUDA", 8: "HE_E_UNIMPL", 9: "HE_E_STATE"}
+
+
+class HeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ParamsDesc(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_int), ("n_q", ctypes.c_int), ("q_bits", ctypes.POINTER(ctypes.c_int)),
+                ("n_special", ctypes.c_int), ("special_bits", ctypes.c_int), ("alpha", ctypes.c_int),
+                ("log_scale", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+V = ctypes.c_void_p
+PV = ctypes.POINTER(ctypes.c_void_p)
+I = ctypes.c_int
+U64 = ctypes.c_uint64
+D = ctypes.c_double
+SZ = ctypes.c_size_t
+P_U64 = ctypes.POINTER(ctypes.c_uint64)
+P_I64 = ctypes.POINTER(ctypes.c_int64)
+P_I32 = ctypes.POINTER(ctypes.c_int32)
+P_I = ctypes.POINTER(ctypes.c_int)
+P_D = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); every entry point declared in include/he_gb300.h
+SIGNATURES = {
+    "he_ctx_create": (I, [ctypes.POINTER(ParamsDesc), U64, V, PV]),
+    "he_ctx_destroy": (None, [V]),
+    "he_ctx_primes": (I, [V, P_U64, I]),
+    "he_ctx_info": (I, [V, P_I, P_I, P_I, P_I, P_D]),
+    "he_keygen": (I, [V, P_I32, I]),
+    "he_encrypt_image": (I, [V, P_D, I, I, I, I, U64, PV]),
+    "he_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
+    "he_encrypt_matrix_b": (I, [V, P_D, I, I, U64, PV]),
+    "he_encrypt_coeffs": (I, [V, P_I64, I, I, D, U64, PV]),
+    "he_matmul": (I, [V, V, V, I, I, PV]),
+    "he_matmul_batched": (I, [V, I, PV, PV, P_I, P_I, PV]),
+    "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
+    "he_poly_act": (I, [V, V, P_D, I]),
+    "he_fc_prepare": (I, [V, P_D, I, I, I, I, I, I, I, I, PV]),
+    "he_fc_prepare_coeffs": (I, [V, P_I64, I, I, I, I, I, I, PV]),
+    "he_ptset_free": (None, [V]),
+    "he_fc_apply": (I, [V, V, V, P_D, PV]),
+    "he_fc": (I, [V, V, P_D, P_D, I, I, I, I, I, I, I, PV]),
+    "he_rotate": (I, [V, V, P_I32, I, PV]),
+    "he_mul": (I, [V, V, V, PV]),
+    "he_rescale": (I, [V, V]),
+    "he_add": (I, [V, V, V, PV]),
+    "he_decrypt_slots": (I, [V, V, P_D, SZ]),
+    "he_decrypt_matrix": (I, [V, V, I, I, P_D]),
+    "he_decrypt_image": (I, [V, V, I, I, I, I, P_D, SZ]),
+    "he_ctset_export": (I, [V, P_U64, SZ]),
+    "he_ctset_import": (I, [V, P_U64, I, I, D, PV]),
+    "he_ctset_info": (I, [V, P_I, P_I, P_D]),
+    "he_ctset_device_ptr": (I, [V, ctypes.POINTER(P_U64)]),
+    "he_ctset_slice": (I, [V, V, I, I, PV]),
+    "he_ctset_concat": (I, [V, PV, I, PV]),
+    "he_ctset_free": (None, [V]),
+    "he_ntt": (I, [V, P_U64, I, I, I, I]),
+    "he_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (once). Raises if it is missing: there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libhegb300.so not built at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(rc: int):
+    if rc != HE_OK:
+        raise HeError(rc, (load().he_last_error() or b"").decode())

@@ -1,0 +1,248 @@
+"""Python face of the C ABI (include/he_gb300.h): same operations, numpy in
+and out, handles freed when their Python objects die. Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from ._lib import P_D, P_I, P_I32, P_I64, P_U64, ParamsDesc, check, load
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class CtSet:
+    """n ciphertexts at one level and scale, in device memory (NTT domain)."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.h = ctypes.c_void_p(handle)
+
+    def free(self):
+        if self.h:
+            load().he_ctset_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n, limbs, sc = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(load().he_ctset_info(self.h, ctypes.byref(n), ctypes.byref(limbs), ctypes.byref(sc)))
+        return n.value, limbs.value, sc.value
+
+    @property
+    def n(self):
+        return self.info()[0]
+
+    @property
+    def limbs(self):
+        return self.info()[1]
+
+    @property
+    def scale(self):
+        return self.info()[2]
+
+    def export(self) -> np.ndarray:
+        """Coefficient-domain limbs [n][2][limbs][N] (uint64)."""
+        n, limbs, _ = self.info()
+        out = np.zeros((n, 2, limbs, self.ctx.N), np.uint64)
+        check(load().he_ctset_export(self.h, _ptr(out, P_U64), out.size))
+        return out
+
+    def device_ptr(self) -> int:
+        p = P_U64()
+        check(load().he_ctset_device_ptr(self.h, ctypes.byref(p)))
+        return ctypes.cast(p, ctypes.c_void_p).value
+
+    def slice(self, first: int, n: int) -> "CtSet":
+        out = ctypes.c_void_p()
+        check(load().he_ctset_slice(self.ctx.h, self.h, first, n, ctypes.byref(out)))
+        return CtSet(self.ctx, out.value)
+
+
+class PtSet:
+    def __init__(self, handle: int):
+        self.h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        try:
+            if self.h:
+                load().he_ptset_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Context:
+    """he_ctx: parameters, NTT tables and keys on the current CUDA device."""
+
+    def __init__(self, log_n: int, q_bits: Sequence[int], n_special: int, special_bits: int, alpha: int,
+                 log_scale: float, sigma: float = 3.2, seed: int = 1, stream: Optional[int] = None):
+        lib = load()
+        qb = (ctypes.c_int * len(q_bits))(*q_bits)
+        self._qb = qb
+        d = ParamsDesc(log_n, len(q_bits), qb, n_special, special_bits, alpha, float(log_scale), float(sigma))
+        h = ctypes.c_void_p()
+        check(lib.he_ctx_create(ctypes.byref(d), seed, ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        self.log_n = log_n
+        self.N = 1 << log_n
+        self.slots = self.N // 2
+        self.L1 = len(q_bits)
+        self.K = n_special
+        self.alpha = alpha
+        self.scale = float(2.0 ** log_scale)
+        pr = np.zeros(self.L1 + self.K, np.uint64)
+        check(lib.he_ctx_primes(h, _ptr(pr, P_U64), pr.size))
+        self.primes = [int(x) for x in pr]
+        self.q = self.primes[: self.L1]
+        self.p = self.primes[self.L1:]
+
+    @classmethod
+    def from_preset(cls, preset, seed: int = 1, stream: Optional[int] = None):
+        return cls(preset.log_n, preset.q_bits, preset.n_special, preset.special_bits, preset.alpha,
+                   preset.log_scale, preset.sigma, seed, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().he_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _set(self, fn, *args) -> CtSet:
+        out = ctypes.c_void_p()
+        check(fn(*args, ctypes.byref(out)))
+        return CtSet(self, out.value)
+
+    # ---- keys / encryption ----
+    def keygen(self, steps: Sequence[int] = ()):
+        st = (ctypes.c_int32 * max(1, len(steps)))(*steps)
+        check(load().he_keygen(self.h, st, len(steps)))
+
+    def encrypt_image(self, px, block_stride: int, ct_id_base: int = 0) -> CtSet:
+        px = _f64(px)
+        b, h, w = px.shape
+        return self._set(load().he_encrypt_image, self.h, _ptr(px, P_D), b, h, w, block_stride, ct_id_base)
+
+    def encrypt_matrix_a(self, A, ct_id_base: int = 0) -> CtSet:
+        A = _f64(A)
+        return self._set(load().he_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)
+
+    def encrypt_matrix_b(self, B, ct_id_base: int = 0) -> CtSet:
+        B = _f64(B)
+        return self._set(load().he_encrypt_matrix_b, self.h, _ptr(B, P_D), B.shape[0], B.shape[1], ct_id_base)
+
+    def encrypt_coeffs(self, m, limbs: Optional[int] = None, scale: Optional[float] = None,
+                       ct_id_base: int = 0) -> CtSet:
+        m = np.ascontiguousarray(m, dtype=np.int64).reshape(-1, self.N)
+        return self._set(load().he_encrypt_coeffs, self.h, _ptr(m, P_I64), m.shape[0],
+                         self.L1 if limbs is None else limbs, self.scale if scale is None else scale, ct_id_base)
+
+    def import_coeffs(self, host, scale: float) -> CtSet:
+        host = np.ascontiguousarray(host, dtype=np.uint64)
+        n, _, limbs, _ = host.shape
+        return self._set(load().he_ctset_import, self.h, _ptr(host, P_U64), n, limbs, scale)
+
+    # ---- evaluation ----
+    def matmul(self, A: CtSet, B: CtSet, m: int, p: int) -> CtSet:
+        return self._set(load().he_matmul, self.h, A.h, B.h, m, p)
+
+    def matmul_batched(self, As, Bs, ms, ps):
+        n = len(As)
+        arrA = (ctypes.c_void_p * n)(*[a.h.value for a in As])
+        arrB = (ctypes.c_void_p * n)(*[b.h.value for b in Bs])
+        mm = (ctypes.c_int * n)(*ms)
+        pp = (ctypes.c_int * n)(*ps)
+        out = (ctypes.c_void_p * n)()
+        check(load().he_matmul_batched(self.h, n, arrA, arrB, mm, pp, out))
+        return [CtSet(self, out[i]) for i in range(n)]
+
+    def conv2d(self, x: CtSet, c_in: int, gap: int, W, bias, stride: int) -> CtSet:
+        W = _f64(W)
+        c_out, _, k, _ = W.shape
+        b = None if bias is None else _f64(bias)
+        return self._set(load().he_conv2d, self.h, x.h, c_in, gap, _ptr(W, P_D), None if b is None else _ptr(b, P_D),
+                         c_out, k, stride)
+
+    def poly_act(self, x: CtSet, coeffs: Sequence[float]):
+        c = _f64(coeffs)
+        check(load().he_poly_act(self.h, x.h, _ptr(c, P_D), len(coeffs) - 1))
+        return x
+
+    def square(self, x: CtSet) -> CtSet:
+        return self.poly_act(x, [0.0, 0.0, 1.0])
+
+    def fc_prepare(self, W, c_in: int, h_valid: int, w_in: int, gap: int, block_stride: int, batch: int,
+                   limbs: int) -> PtSet:
+        W = _f64(W)
+        out = ctypes.c_void_p()
+        check(load().he_fc_prepare(self.h, _ptr(W, P_D), W.shape[0], c_in, h_valid, w_in, gap, block_stride, batch,
+                                   limbs, ctypes.byref(out)))
+        return PtSet(out.value)
+
+    def fc_prepare_coeffs(self, pts, gap: int, block_stride: int, limbs: int) -> PtSet:
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        out_dim, c_in, w_in, _ = pts.shape
+        out = ctypes.c_void_p()
+        check(load().he_fc_prepare_coeffs(self.h, _ptr(pts, P_I64), out_dim, c_in, w_in, gap, block_stride, limbs,
+                                          ctypes.byref(out)))
+        return PtSet(out.value)
+
+    def fc_apply(self, x: CtSet, pts: PtSet, bias) -> CtSet:
+        b = None if bias is None else _f64(bias)
+        return self._set(load().he_fc_apply, self.h, x.h, pts.h, None if b is None else _ptr(b, P_D))
+
+    def rotate(self, x: CtSet, steps: Sequence[int]) -> CtSet:
+        st = (ctypes.c_int32 * len(steps))(*steps)
+        return self._set(load().he_rotate, self.h, x.h, st, len(steps))
+
+    def mul(self, a: CtSet, b: CtSet) -> CtSet:
+        return self._set(load().he_mul, self.h, a.h, b.h)
+
+    def add(self, a: CtSet, b: CtSet) -> CtSet:
+        return self._set(load().he_add, self.h, a.h, b.h)
+
+    def rescale(self, x: CtSet) -> CtSet:
+        check(load().he_rescale(self.h, x.h))
+        return x
+
+    # ---- decryption ----
+    def decrypt_slots(self, x: CtSet) -> np.ndarray:
+        n = x.n
+        out = np.zeros((n, self.slots), np.float64)
+        check(load().he_decrypt_slots(self.h, x.h, _ptr(out, P_D), out.size))
+        return out
+
+    def decrypt_matrix(self, C: CtSet, m: int, p: int) -> np.ndarray:
+        out = np.zeros((m, p), np.float64)
+        check(load().he_decrypt_matrix(self.h, C.h, m, p, _ptr(out, P_D)))
+        return out
+
+    def decrypt_image(self, x: CtSet, batch: int, block_stride: int, gap: int, h_valid: int) -> np.ndarray:
+        """[batch][n_ct][h_valid]: per ciphertext (column), the valid rows."""
+        out = np.zeros((batch, x.n, h_valid), np.float64)
+        check(load().he_decrypt_image(self.h, x.h, batch, block_stride, gap, h_valid, _ptr(out, P_D), out.size))
+        return out
+
+    def ntt(self, host, first_prime: int = 0, inverse: bool = False) -> np.ndarray:
+        a = np.ascontiguousarray(host, dtype=np.uint64).copy()
+        shp = a.shape
+        a3 = a.reshape(-1, shp[-2] if a.ndim >= 2 else 1, self.N)
+        check(load().he_ntt(self.h, _ptr(a3, P_U64), a3.shape[0], a3.shape[1], first_prime, int(inverse)))
+        return a3.reshape(shp)

@@ -1,0 +1,452 @@
+// capi.cpp - the extern "C" entry points declared in include/he_gb300.h.
+// Argument checking, the paper's slot layouts (image columns, matrix
+// columns / tiled rows, diagonal matmul output), and translation of internal
+// errors into status codes; all arithmetic runs in the kernels.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/he_gb300.h"
+#include "he_internal.h"
+
+using namespace he;
+
+static thread_local std::string g_err;
+
+template <class F>
+static int guard(F f) {
+  try {
+    f();
+    g_err.clear();
+    return HE_OK;
+  } catch (const Error& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return HE_E_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return HE_E_CUDA;
+  }
+}
+
+#define REQUIRE(cond, code, msg) \
+  do {                           \
+    if (!(cond)) throw Error((code), (msg)); \
+  } while (0)
+
+static bool pow2(long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+template <class F>
+static void host_parallel(size_t n, F f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 16) nt = 16;
+  if (n < 2 || nt == 1) {
+    for (size_t i = 0; i < n; i++) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; t++)
+    th.emplace_back([&, t] {
+      for (size_t i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Encode slot vectors z [n][M] (host) at scale and encrypt at the top level.
+static std::unique_ptr<CtSet> encrypt_slots(Ctx& C, const std::vector<double>& z, int n, u64 id_base) {
+  const size_t M = C.N / 2;
+  std::vector<int64_t> m((size_t)n * C.N);
+  host_parallel((size_t)n, [&](size_t c) { encode_real(C, z.data() + c * M, M, C.scale0, m.data() + c * C.N); });
+  return encrypt_coeffs(C, m.data(), n, C.L1, C.scale0, id_base);
+}
+
+static he_ctset* wrap(std::unique_ptr<CtSet> s) {
+  he_ctset* h = new he_ctset;
+  h->s = std::move(s);
+  return h;
+}
+
+extern "C" {
+
+const char* he_last_error(void) { return g_err.c_str(); }
+
+int he_ctx_create(const he_params_desc* d, uint64_t seed, void* cuda_stream, he_ctx** out) {
+  return guard([&] {
+    REQUIRE(d && out && d->q_bits, HE_E_ARG, "null argument");
+    REQUIRE(d->n_q >= 1 && d->n_q <= 32, HE_E_ARG, "n_q must be in [1, 32]");
+    std::vector<int> qb(d->q_bits, d->q_bits + d->n_q);
+    auto* h = new he_ctx;
+    try {
+      ctx_init(h->c, d->log_n, qb, d->n_special, d->special_bits, d->alpha, d->log_scale, d->sigma, seed,
+               (cudaStream_t)cuda_stream);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+void he_ctx_destroy(he_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->c.stream);
+  delete ctx;
+}
+
+int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n) {
+  return guard([&] {
+    REQUIRE(ctx && out, HE_E_ARG, "null argument");
+    REQUIRE(n >= ctx->c.np(), HE_E_ARG, "output too small");
+    for (int i = 0; i < ctx->c.np(); i++) out[i] = ctx->c.q[i];
+  });
+}
+
+int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* alpha, double* scale) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    if (log_n) *log_n = ctx->c.log_n;
+    if (n_q) *n_q = ctx->c.L1;
+    if (n_special) *n_special = ctx->c.K;
+    if (alpha) *alpha = ctx->c.alpha;
+    if (scale) *scale = ctx->c.scale0;
+  });
+}
+
+int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps) {
+  return guard([&] {
+    REQUIRE(ctx && n_steps >= 0 && (n_steps == 0 || rot_steps), HE_E_ARG, "bad arguments");
+    std::vector<long> st(rot_steps, rot_steps + n_steps);
+    keygen(ctx->c, st);
+  });
+}
+
+int he_encrypt_image(he_ctx* ctx, const double* px, int batch, int h, int w, int block_stride, uint64_t ct_id_base,
+                     he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && px && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long M = (long)C.N / 2;
+    REQUIRE(batch >= 1 && h >= 1 && w >= 1, HE_E_ARG, "empty image");
+    REQUIRE(pow2(block_stride) && block_stride >= h, HE_E_ARG, "block_stride must be a power of two >= h");
+    REQUIRE((long)batch * block_stride <= M, HE_E_ARG, "batch * block_stride exceeds the slot count");
+    std::vector<double> z((size_t)w * M, 0.0);
+    for (int b = 0; b < batch; b++)
+      for (int i = 0; i < h; i++)
+        for (int j = 0; j < w; j++) z[(size_t)j * M + (size_t)b * block_stride + i] = px[((size_t)b * h + i) * w + j];
+    *out = wrap(encrypt_slots(C, z, w, ct_id_base));
+  });
+}
+
+int he_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long M = (long)C.N / 2;
+    REQUIRE(m >= 1 && n >= 1 && m <= M, HE_E_ARG, "bad matrix shape");
+    std::vector<double> z((size_t)n * M, 0.0);
+    for (int k = 0; k < n; k++)
+      for (int i = 0; i < m; i++) z[(size_t)k * M + i] = A[(size_t)i * n + k];
+    *out = wrap(encrypt_slots(C, z, n, ct_id_base));
+  });
+}
+
+int he_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && B && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long M = (long)C.N / 2;
+    REQUIRE(n >= 1 && p >= 1 && M % p == 0, HE_E_ARG, "p must divide the slot count");
+    std::vector<double> z((size_t)n * M);
+    for (int k = 0; k < n; k++)
+      for (long s = 0; s < M; s++) z[(size_t)k * M + s] = B[(size_t)k * p + (s % p)];
+    *out = wrap(encrypt_slots(C, z, n, ct_id_base));
+  });
+}
+
+int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double scale, uint64_t ct_id_base,
+                      he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && m && out, HE_E_ARG, "null argument");
+    REQUIRE(scale > 0, HE_E_ARG, "scale must be positive");
+    *out = wrap(encrypt_coeffs(ctx->c, m, n_ct, limbs, scale, ct_id_base));
+  });
+}
+
+int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C_out) {
+  return guard([&] {
+    REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
+    REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
+    REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
+    *C_out = wrap(matmul(ctx->c, *A->s, *B->s, p));
+  });
+}
+
+int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
+                      const int* p, he_ctset** C_out) {
+  return guard([&] {
+    REQUIRE(ctx && A && B && m && p && C_out && count >= 0, HE_E_ARG, "null argument");
+    std::vector<std::unique_ptr<CtSet>> res(count);
+    for (int i = 0; i < count; i++) {
+      REQUIRE(A[i] && B[i], HE_E_ARG, "null operand");
+      REQUIRE(A[i]->s->scale == B[i]->s->scale, HE_E_SCALE, "operands at different scales");
+      res[i] = matmul(ctx->c, *A[i]->s, *B[i]->s, p[i]);
+    }
+    for (int i = 0; i < count; i++) C_out[i] = wrap(std::move(res[i]));
+  });
+}
+
+int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* weights, const double* bias, int c_out,
+              int k, int stride, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && weights && out, HE_E_ARG, "null argument");
+    *out = wrap(conv2d(ctx->c, *in->s, c_in, gap, weights, bias, c_out, k, stride));
+  });
+}
+
+int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) {
+  return guard([&] {
+    REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");
+    REQUIRE(degree == 2 && coeffs[0] == 0.0 && coeffs[1] == 0.0 && coeffs[2] == 1.0, HE_E_UNIMPL,
+            "only x -> x^2 is supported");
+    inout->s = square(ctx->c, *inout->s);
+  });
+}
+
+int he_fc_prepare(he_ctx* ctx, const double* W, int out_dim, int c_in, int h_valid, int w_in, int gap,
+                  int block_stride, int batch, int limbs, he_ptset** out) {
+  return guard([&] {
+    REQUIRE(ctx && W && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long M = (long)C.N / 2;
+    REQUIRE(out_dim >= 1 && c_in >= 1 && h_valid >= 1 && w_in >= 1 && gap >= 1, HE_E_ARG, "bad shape");
+    REQUIRE(pow2(block_stride) && pow2(gap) && (long)gap * (h_valid - 1) < block_stride, HE_E_ARG,
+            "rows do not fit the blocks");
+    REQUIRE(batch >= 1 && (long)batch * block_stride <= M, HE_E_ARG, "batch * block_stride exceeds the slot count");
+    REQUIRE(limbs >= 2 && limbs <= C.L1, HE_E_LEVEL, "bad level");
+    const int n_in = c_in * w_in;
+    const double ql = (double)C.q[limbs - 1];
+    std::vector<int64_t> pts((size_t)out_dim * n_in * C.N);
+    const size_t row = (size_t)c_in * h_valid * w_in;
+    host_parallel((size_t)out_dim * n_in, [&](size_t t) {
+      const int o = (int)(t / n_in), cj = (int)(t % n_in), c = cj / w_in, j = cj % w_in;
+      std::vector<double> z(M, 0.0);
+      for (int b = 0; b < batch; b++)
+        for (int i = 0; i < h_valid; i++)
+          z[(size_t)b * block_stride + (size_t)gap * i] = W[(size_t)o * row + ((size_t)c * h_valid + i) * w_in + j];
+      encode_real(C, z.data(), M, ql, pts.data() + t * C.N);
+    });
+    auto* h = new he_ptset;
+    h->ctx = &C;
+    h->out_dim = out_dim; h->n_in = n_in; h->limbs = limbs; h->gap = gap; h->block_stride = block_stride;
+    try {
+      h->buf = fc_prepare(C, pts.data(), out_dim, n_in, limbs);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+int he_fc_prepare_coeffs(he_ctx* ctx, const int64_t* pts, int out_dim, int c_in, int w_in, int gap, int block_stride,
+                         int limbs, he_ptset** out) {
+  return guard([&] {
+    REQUIRE(ctx && pts && out, HE_E_ARG, "null argument");
+    REQUIRE(out_dim >= 1 && c_in >= 1 && w_in >= 1, HE_E_ARG, "bad shape");
+    REQUIRE(pow2(block_stride) && pow2(gap), HE_E_ARG, "gap and block_stride must be powers of two");
+    REQUIRE(limbs >= 2 && limbs <= ctx->c.L1, HE_E_LEVEL, "bad level");
+    auto* h = new he_ptset;
+    h->ctx = &ctx->c;
+    h->out_dim = out_dim; h->n_in = c_in * w_in; h->limbs = limbs; h->gap = gap; h->block_stride = block_stride;
+    try {
+      h->buf = fc_prepare(ctx->c, pts, out_dim, c_in * w_in, limbs);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+void he_ptset_free(he_ptset* pts) { delete pts; }
+
+int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const double* bias, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && pts && out, HE_E_ARG, "null argument");
+    REQUIRE(in->s->n == pts->n_in, HE_E_ARG, "input size does not match the prepared weights");
+    REQUIRE(in->s->limbs == pts->limbs, HE_E_LEVEL, "input level does not match the prepared weights");
+    *out = wrap(fc_apply(ctx->c, *in->s, pts->buf.p, pts->out_dim, pts->gap, pts->block_stride, bias));
+  });
+}
+
+int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int out_dim, int c_in, int h_valid,
+          int w_in, int gap, int block_stride, int batch, he_ctset** out) {
+  he_ptset* pts = nullptr;
+  int rc = he_fc_prepare(ctx, W, out_dim, c_in, h_valid, w_in, gap, block_stride, batch, in ? in->s->limbs : 0, &pts);
+  if (rc != HE_OK) return rc;
+  rc = he_fc_apply(ctx, in, pts, b, out);
+  he_ptset_free(pts);
+  return rc;
+}
+
+int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && steps && out && n_steps >= 1, HE_E_ARG, "bad arguments");
+    std::vector<long> st(steps, steps + n_steps);
+    *out = wrap(rotate(ctx->c, *in->s, st));
+  });
+}
+
+int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && a && b && out, HE_E_ARG, "null argument");
+    *out = wrap(mul(ctx->c, *a->s, *b->s));
+  });
+}
+
+int he_rescale(he_ctx* ctx, he_ctset* inout) {
+  return guard([&] {
+    REQUIRE(ctx && inout, HE_E_ARG, "null argument");
+    rescale_inplace(ctx->c, *inout->s);
+  });
+}
+
+int he_add(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && a && b && out, HE_E_ARG, "null argument");
+    *out = wrap(add(ctx->c, *a->s, *b->s));
+  });
+}
+
+int he_decrypt_slots(he_ctx* ctx, const he_ctset* in, double* out, size_t out_len) {
+  return guard([&] {
+    REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
+    REQUIRE(out_len >= (size_t)in->s->n * (ctx->c.N / 2), HE_E_ARG, "output too small");
+    decrypt_slots(ctx->c, *in->s, out);
+  });
+}
+
+int he_decrypt_matrix(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_out) {
+  return guard([&] {
+    REQUIRE(ctx && Cs && C_out, HE_E_ARG, "null argument");
+    REQUIRE(Cs->s->n == p && m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "shape does not match");
+    const size_t M = ctx->c.N / 2;
+    std::vector<double> z((size_t)p * M);
+    decrypt_slots(ctx->c, *Cs->s, z.data());
+    for (int idx = 0; idx < p; idx++)
+      for (int i = 0; i < m; i++) C_out[(size_t)i * p + (i + idx) % p] = z[(size_t)idx * M + i];
+  });
+}
+
+int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_stride, int gap, int h_valid, double* out,
+                     size_t out_len) {
+  return guard([&] {
+    REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
+    const size_t M = ctx->c.N / 2;
+    const int n = in->s->n;
+    REQUIRE(batch >= 1 && h_valid >= 1 && gap >= 1 && (size_t)batch * block_stride <= M &&
+                (long)gap * (h_valid - 1) < block_stride,
+            HE_E_ARG, "layout does not fit");
+    REQUIRE(out_len >= (size_t)batch * n * h_valid, HE_E_ARG, "output too small");
+    std::vector<double> z((size_t)n * M);
+    decrypt_slots(ctx->c, *in->s, z.data());
+    for (int b = 0; b < batch; b++)
+      for (int c = 0; c < n; c++)
+        for (int i = 0; i < h_valid; i++)
+          out[((size_t)b * n + c) * h_valid + i] = z[(size_t)c * M + (size_t)b * block_stride + (size_t)gap * i];
+  });
+}
+
+int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words) {
+  return guard([&] {
+    REQUIRE(set && host, HE_E_ARG, "null argument");
+    REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
+    export_coeffs(*set->s->ctx, *set->s, host);
+  });
+}
+
+int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
+    *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale));
+  });
+}
+
+int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale) {
+  return guard([&] {
+    REQUIRE(set, HE_E_ARG, "null set");
+    if (n_ct) *n_ct = set->s->n;
+    if (limbs) *limbs = set->s->limbs;
+    if (scale) *scale = set->s->scale;
+  });
+}
+
+int he_ctset_device_ptr(const he_ctset* set, uint64_t** dptr) {
+  return guard([&] {
+    REQUIRE(set && dptr, HE_E_ARG, "null argument");
+    *dptr = set->s->buf.p;
+  });
+}
+
+int he_ctset_slice(he_ctx* ctx, const he_ctset* set, int first, int n, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && set && out, HE_E_ARG, "null argument");
+    const CtSet& s = *set->s;
+    REQUIRE(first >= 0 && n >= 1 && first + n <= s.n, HE_E_ARG, "slice out of range");
+    auto r = new_set(ctx->c, n, s.polys, s.limbs, s.scale);
+    HE_CUDA(cudaMemcpyAsync(r->buf.p, s.ct(first), (size_t)n * s.ct_words() * 8, cudaMemcpyDeviceToDevice,
+                            ctx->c.stream));
+    *out = wrap(std::move(r));
+  });
+}
+
+int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && sets && out && n_sets >= 1, HE_E_ARG, "null argument");
+    int total = 0;
+    for (int i = 0; i < n_sets; i++) {
+      REQUIRE(sets[i], HE_E_ARG, "null set");
+      REQUIRE(sets[i]->s->limbs == sets[0]->s->limbs && sets[i]->s->polys == sets[0]->s->polys, HE_E_LEVEL,
+              "sets at different levels");
+      REQUIRE(sets[i]->s->scale == sets[0]->s->scale, HE_E_SCALE, "sets at different scales");
+      total += sets[i]->s->n;
+    }
+    const CtSet& s0 = *sets[0]->s;
+    auto r = new_set(ctx->c, total, s0.polys, s0.limbs, s0.scale);
+    size_t off = 0;
+    for (int i = 0; i < n_sets; i++) {
+      const size_t w = sets[i]->s->buf.words;
+      HE_CUDA(cudaMemcpyAsync(r->buf.p + off, sets[i]->s->buf.p, w * 8, cudaMemcpyDeviceToDevice, ctx->c.stream));
+      off += w;
+    }
+    *out = wrap(std::move(r));
+  });
+}
+
+void he_ctset_free(he_ctset* set) { delete set; }
+
+int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse) {
+  return guard([&] {
+    REQUIRE(ctx && host && n_polys >= 1 && limbs >= 1, HE_E_ARG, "bad arguments");
+    Ctx& C = ctx->c;
+    REQUIRE(first_prime >= 0 && first_prime + limbs <= C.np(), HE_E_ARG, "prime range out of bounds");
+    const size_t words = (size_t)n_polys * limbs * C.N;
+    for (size_t idx = 0; idx < words; idx++)
+      REQUIRE(host[idx] < C.q[first_prime + (int)((idx / C.N) % limbs)], HE_E_ARG, "residue out of range");
+    DevBuf d(words, C.stream);
+    HE_CUDA(cudaMemcpyAsync(d.p, host, words * 8, cudaMemcpyHostToDevice, C.stream));
+    LimbMap lm;
+    lm.lpp = limbs; lm.split = limbs; lm.base0 = first_prime; lm.base1 = 0; lm.poly_stride = (size_t)limbs * C.N;
+    if (inverse) ntt_inverse(C, d.p, n_polys, lm);
+    else ntt_forward(C, d.p, n_polys, lm);
+    HE_CUDA(cudaMemcpyAsync(host, d.p, words * 8, cudaMemcpyDeviceToHost, C.stream));
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
+
+}  // extern "C"

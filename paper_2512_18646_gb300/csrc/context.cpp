@@ -1,0 +1,522 @@
+// context.cpp - parameters, device tables, key generation, encryption and
+// decryption of the GB300 RNS-CKKS engine.
+//
+// Scheme (Sec. II-A lists Enc_pk, Dec_sk and the evaluation keys the CKKS
+// library provides; the RNS form is the standard full-RNS CKKS):
+//   secret s ternary; public key (b, a) = (-a s + e, a) over Q;
+//   key-switching key from s' to s, digit j of alpha primes:
+//     (-a_j s + e_j + P g_j s', a_j) over Q*P, g_j = 1 mod the primes of
+//     digit j and 0 mod the other primes of Q;
+//   Enc(m) = (v b + e0 + m, v a + e1), v ternary, e0, e1 Gaussian;
+//   Dec(c0, c1) = c0 + c1 s.
+// Random draws come from the seeded streams of inputs/he_random.h, so that a
+// given (seed, ciphertext id) always yields the same ciphertext.
+//
+// Galois keys are stored pre-permuted: for phi_k the key holds
+// phi_{k^-1}(evk) in the NTT domain, so the inner product reads the ModUp
+// digits in place and the single permutation is applied to its result
+// (sum_j phi_k(d_j) evk_j = phi_k(sum_j d_j phi_{k^-1}(evk_j))).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "../../inputs/he_random.h"
+#include "he_internal.h"
+
+namespace he {
+
+typedef unsigned __int128 u128;
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) throw Error(5, std::string("out of device memory: ") + what);
+  throw Error(7, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), st(s) {
+  if (w == 0) return;
+  void* ptr = nullptr;
+  cudaError_t e = cudaMallocAsync(&ptr, w * 8, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(5, "device allocation of " + std::to_string(w * 8) + " bytes failed");
+  }
+  p = (u64*)ptr;
+}
+DevBuf::~DevBuf() { reset(); }
+void DevBuf::reset() {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+  words = 0;
+}
+DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
+  if (this != &o) {
+    reset();
+    p = o.p; words = o.words; st = o.st;
+    o.p = nullptr; o.words = 0;
+  }
+  return *this;
+}
+
+// ---------------------------------------------------------------------------
+// host number theory
+// ---------------------------------------------------------------------------
+static u64 mul_h(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+static u64 pow_h(u64 b, u64 e, u64 m) {
+  u64 r = 1;
+  b %= m;
+  for (; e; e >>= 1, b = mul_h(b, b, m))
+    if (e & 1) r = mul_h(r, b, m);
+  return r;
+}
+static u64 inv_h(u64 a, u64 m) { return pow_h(a % m, m - 2, m); }
+
+// Miller-Rabin with the 12 smallest prime bases (exact below 3.3e24).
+static bool prime_h(u64 n) {
+  const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (u64 p : small) {
+    if (n == p) return true;
+    if (n % p == 0) return false;
+  }
+  int s = __builtin_ctzll(n - 1);
+  const u64 d = (n - 1) >> s;
+  for (u64 a : small) {
+    u64 x = pow_h(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    int r = 1;
+    for (; r < s; r++) {
+      x = mul_h(x, x, n);
+      if (x == n - 1) break;
+    }
+    if (r == s) return false;
+  }
+  return true;
+}
+
+static u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+static Mod make_mod(u64 q) {
+  const u128 mu = (~(u128)0) / q;  // floor(2^128 / q) since q is odd
+  return Mod{q, (u64)(mu >> 64), (u64)mu};
+}
+
+static u32 brv_h(u32 x, int bits) {
+  u32 r = 0;
+  for (int i = 0; i < bits; i++, x >>= 1) r = (r << 1) | (x & 1);
+  return r;
+}
+
+u64 Ctx::galois_elt(long step) const {
+  const long slots = (long)N / 2;
+  const long r = ((step % slots) + slots) % slots;
+  return pow_h(5, (u64)r, 2 * (u64)N);
+}
+
+const DevBuf& Ctx::key(u64 k) const {
+  auto it = ksk.find(k);
+  if (it == ksk.end())
+    throw Error(3, k == 1 ? "no relinearisation key (call he_keygen)" : "no rotation key for Galois element " + std::to_string(k));
+  return it->second;
+}
+
+static void upload(const Ctx& C, u64* dst, const void* src, size_t bytes) {
+  HE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, C.stream));
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, int special_bits, int alpha,
+              double log_scale, double sigma, u64 seed, cudaStream_t st) {
+  if (log_n < 4 || log_n > 16) throw Error(1, "log_n must be in [4, 16]");
+  if (q_bits.empty() || q_bits.size() > 32) throw Error(1, "n_q must be in [1, 32]");
+  if (n_special < 1 || n_special > 4) throw Error(1, "n_special must be in [1, 4]");
+  if (alpha < 1 || alpha > 8) throw Error(1, "alpha must be in [1, 8]");
+  if (special_bits < 20 || special_bits > 61) throw Error(1, "special_bits must be in [20, 61]");
+  for (int b : q_bits)
+    if (b < 20 || b > 61) throw Error(1, "prime bit sizes must be in [20, 61]");
+  if (!(sigma > 0) || !(log_scale > 0)) throw Error(1, "sigma and log_scale must be positive");
+  HE_CUDA(cudaGetDevice(&C.device));
+  C.stream = st;
+  C.log_n = log_n;
+  C.N = (size_t)1 << log_n;
+  C.L1 = (int)q_bits.size();
+  C.K = n_special;
+  C.alpha = alpha;
+  C.scale0 = std::ldexp(1.0, 0) * std::pow(2.0, log_scale);
+  C.sigma = sigma;
+  C.seed = seed;
+  C.cdt_bound = he_rand_cdt_init(sigma, C.cdt);
+  // keep freed pool memory cached instead of returning it to the driver
+  cudaMemPool_t pool;
+  HE_CUDA(cudaDeviceGetDefaultMemPool(&pool, C.device));
+  uint64_t thr = ~0ull;
+  HE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+
+  // prime chain: specials first, then q_0 .. q_L, each the largest unused
+  // candidate 2^b - t 2N + 1 of its size
+  const u64 two_n = 2 * (u64)C.N;
+  std::map<int, u64> cursor;
+  auto next_prime = [&](int bits) -> u64 {
+    u64& t = cursor[bits];
+    for (;;) {
+      ++t;
+      const u64 top = 1ull << bits;
+      if (t * two_n >= top / 2) throw Error(1, "no NTT-friendly prime of " + std::to_string(bits) + " bits left");
+      const u64 c = top - t * two_n + 1;
+      if (prime_h(c)) return c;
+    }
+  };
+  std::vector<u64> P(n_special);
+  for (auto& p : P) p = next_prime(special_bits);
+  C.q.clear();
+  for (int b : q_bits) C.q.push_back(next_prime(b));
+  for (u64 p : P) C.q.push_back(p);
+  const int np = C.np();
+
+  // per-prime constants and NTT twiddles
+  C.ptab.assign(np, PrimeTab{});
+  std::vector<u64> psi_tab((size_t)np * 2 * C.N), ipsi_tab((size_t)np * 2 * C.N);
+  std::vector<u64> pw(C.N);
+  for (int g = 0; g < np; g++) {
+    const u64 q = C.q[g];
+    PrimeTab& T = C.ptab[g];
+    T.mod = make_mod(q);
+    T.ninv = inv_h(C.N % q, q);
+    T.ninv_sh = shoup_of(T.ninv, q);
+    u64 pm = 1;
+    for (u64 p : P) pm = mul_h(pm, p % q, q);
+    T.pmod = pm;
+    // psi = x^((q-1)/2N), x the smallest quadratic non-residue
+    u64 x = 2;
+    while (pow_h(x, (q - 1) / 2, q) != q - 1) x++;
+    const u64 psi = pow_h(x, (q - 1) / two_n, q), ipsi = inv_h(psi, q);
+    for (int dir = 0; dir < 2; dir++) {
+      const u64 r = dir ? ipsi : psi;
+      pw[0] = 1;
+      for (size_t e = 1; e < C.N; e++) pw[e] = mul_h(pw[e - 1], r, q);
+      u64* tab = (dir ? ipsi_tab.data() : psi_tab.data()) + (size_t)g * 2 * C.N;
+      for (size_t k = 0; k < C.N; k++) {
+        const u64 w = pw[brv_h((u32)k, log_n)];
+        tab[k] = w;
+        tab[C.N + k] = shoup_of(w, q);
+      }
+    }
+  }
+  C.d_ptab = DevBuf((size_t)np * sizeof(PrimeTab) / 8, st);
+  upload(C, C.d_ptab.p, C.ptab.data(), (size_t)np * sizeof(PrimeTab));
+  C.d_psi = DevBuf(psi_tab.size(), st);
+  upload(C, C.d_psi.p, psi_tab.data(), psi_tab.size() * 8);
+  C.d_ipsi = DevBuf(ipsi_tab.size(), st);
+  upload(C, C.d_ipsi.p, ipsi_tab.data(), ipsi_tab.size() * 8);
+
+  // ModUp tables per level: digit j covers primes [j alpha, min((j+1) alpha, limbs))
+  const int L1 = C.L1, K = C.K;
+  std::vector<u64> up((size_t)(L1 + 1) * L1 * 2 + (size_t)(L1 + 1) * L1 * (L1 + K), 0);
+  u64* up_inv = up.data();
+  u64* up_hat = up.data() + (size_t)(L1 + 1) * L1 * 2;
+  for (int limbs = 1; limbs <= L1; limbs++) {
+    for (int i = 0; i < limbs; i++) {
+      const int lo = (i / alpha) * alpha, hi = std::min(lo + alpha, limbs);
+      u64 h = 1;
+      for (int i2 = lo; i2 < hi; i2++)
+        if (i2 != i) h = mul_h(h, C.q[i2] % C.q[i], C.q[i]);
+      const u64 hinv = inv_h(h, C.q[i]);
+      up_inv[((size_t)limbs * L1 + i) * 2] = hinv;
+      up_inv[((size_t)limbs * L1 + i) * 2 + 1] = shoup_of(hinv, C.q[i]);
+      for (int pos = 0; pos < limbs + K; pos++) {
+        const u64 t = C.q[pos < limbs ? pos : L1 + (pos - limbs)];
+        u64 ht = 1;
+        for (int i2 = lo; i2 < hi; i2++)
+          if (i2 != i) ht = mul_h(ht, C.q[i2] % t, t);
+        up_hat[((size_t)limbs * L1 + i) * (L1 + K) + pos] = ht;
+      }
+    }
+  }
+  C.d_up = DevBuf(up.size(), st);
+  upload(C, C.d_up.p, up.data(), up.size() * 8);
+
+  // ModDown tables: (P/p_k)^{-1} mod p_k, (P/p_k) mod q_i, P^{-1} mod q_i
+  std::vector<u64> down((size_t)2 * K + (size_t)K * L1 + (size_t)2 * L1);
+  for (int k = 0; k < K; k++) {
+    const u64 pk = P[k];
+    u64 h = 1;
+    for (int k2 = 0; k2 < K; k2++)
+      if (k2 != k) h = mul_h(h, P[k2] % pk, pk);
+    const u64 hi = inv_h(h, pk);
+    down[2 * k] = hi;
+    down[2 * k + 1] = shoup_of(hi, pk);
+    for (int i = 0; i < L1; i++) {
+      u64 hq = 1;
+      for (int k2 = 0; k2 < K; k2++)
+        if (k2 != k) hq = mul_h(hq, P[k2] % C.q[i], C.q[i]);
+      down[2 * K + (size_t)k * L1 + i] = hq;
+    }
+  }
+  for (int i = 0; i < L1; i++) {
+    const u64 pinv = inv_h(C.ptab[i].pmod, C.q[i]);
+    down[2 * K + (size_t)K * L1 + 2 * i] = pinv;
+    down[2 * K + (size_t)K * L1 + 2 * i + 1] = shoup_of(pinv, C.q[i]);
+  }
+  C.d_down = DevBuf(down.size(), st);
+  upload(C, C.d_down.p, down.data(), down.size() * 8);
+
+  // rescale tables: for `limbs` (before), q_l = q[limbs-1], row i < limbs-1:
+  // floor(q_l/2) mod q_i, q_l^{-1} mod q_i, Shoup companion
+  std::vector<u64> rs((size_t)(L1 + 1) * L1 * 3, 0);
+  for (int limbs = 2; limbs <= L1; limbs++) {
+    const u64 ql = C.q[limbs - 1];
+    for (int i = 0; i < limbs - 1; i++) {
+      const u64 qi = C.q[i];
+      const u64 inv = inv_h(ql % qi, qi);
+      u64* t = rs.data() + ((size_t)limbs * L1 + i) * 3;
+      t[0] = (ql / 2) % qi;
+      t[1] = inv;
+      t[2] = shoup_of(inv, qi);
+    }
+  }
+  C.d_rs = DevBuf(rs.size(), st);
+  upload(C, C.d_rs.p, rs.data(), rs.size() * 8);
+
+  // host FFT tables for encode / decode (M = N/2 point complex DFT)
+  const size_t M = C.N / 2;
+  C.fft_root.resize(2 * M);
+  C.fft_twist.resize(2 * M);
+  C.slot_index.resize(M);
+  for (size_t k = 0; k < M; k++) {
+    const double a = 2.0 * M_PI * (double)k / (double)M;
+    C.fft_root[2 * k] = std::cos(a);
+    C.fft_root[2 * k + 1] = std::sin(a);
+    const double b = M_PI * (double)k / (double)C.N;
+    C.fft_twist[2 * k] = std::cos(b);
+    C.fft_twist[2 * k + 1] = std::sin(b);
+  }
+  u64 e = 1;
+  for (size_t j = 0; j < M; j++) {
+    C.slot_index[j] = (uint32_t)((e - 1) / 4);
+    e = (e * 5) % two_n;
+  }
+  HE_CUDA(cudaStreamSynchronize(st));
+}
+
+std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale) {
+  auto s = std::make_unique<CtSet>();
+  s->ctx = &C;
+  s->n = n;
+  s->polys = polys;
+  s->limbs = limbs;
+  s->scale = scale;
+  s->buf = DevBuf((size_t)n * polys * limbs * C.N, C.stream);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// key generation
+// ---------------------------------------------------------------------------
+namespace {
+
+// run f(i) for i < n over a few host threads
+template <class F>
+void parallel_for(size_t n, F f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 16) nt = 16;
+  if (n < 2 || nt == 1) {
+    for (size_t i = 0; i < n; i++) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; t++)
+    th.emplace_back([&, t] {
+      for (size_t i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+void sample_small(const Ctx& C, int tag, u64 obj, u64 sub, int8_t* out) {
+  const u64 st = he_rand_stream(C.seed, (u64)tag, obj, sub);
+  if (tag == HE_TAG_SECRET || tag == HE_TAG_ENC_V)
+    for (size_t i = 0; i < C.N; i++) out[i] = (int8_t)he_rand_ternary(st, i);
+  else
+    for (size_t i = 0; i < C.N; i++) out[i] = (int8_t)he_rand_gauss(st, i, C.cdt, C.cdt_bound);
+}
+
+// uniform residues for primes g0 .. g0+count-1 with stream sub ids sub0 + g
+void sample_uniform(const Ctx& C, int tag, u64 obj, u64 sub0, int count, u64* out) {
+  parallel_for((size_t)count, [&](size_t g) {
+    const u64 st = he_rand_stream(C.seed, (u64)tag, obj, sub0 + g);
+    const u64 q = C.q[g];
+    u64* o = out + g * C.N;
+    for (size_t i = 0; i < C.N; i++) o[i] = he_rand_uniform_mod(st, i, q);
+  });
+}
+
+LimbMap all_primes(const Ctx& C) {
+  LimbMap m;
+  m.lpp = C.np(); m.split = C.np(); m.base0 = 0; m.base1 = 0; m.poly_stride = (size_t)C.np() * C.N;
+  return m;
+}
+
+// One switching key from s' (NTT domain, np limbs; only Q limbs are used) to s.
+DevBuf make_ksk(Ctx& C, u64 key_id, const u64* d_sprime) {
+  const int np = C.np(), beta = C.beta_at(C.L1);
+  const size_t NPN = (size_t)np * C.N;
+  DevBuf key((size_t)beta * 2 * NPN, C.stream);
+  std::vector<u64> a_host(NPN);
+  std::vector<int8_t> e_host(C.N);
+  DevBuf e8(C.N / 8 + 1, C.stream), e_res(NPN, C.stream);
+  const LimbMap lm = all_primes(C);
+  for (int j = 0; j < beta; j++) {
+    sample_uniform(C, HE_TAG_KSK_A, key_id, (u64)j * 256, np, a_host.data());
+    sample_small(C, HE_TAG_KSK_E, key_id, (u64)j, e_host.data());
+    u64* b = key.p + (size_t)j * 2 * NPN;
+    u64* a = b + NPN;
+    upload(C, a, a_host.data(), NPN * 8);
+    upload(C, e8.p, e_host.data(), C.N);
+    HE_CUDA(cudaStreamSynchronize(C.stream));  // host staging buffers are reused
+    ntt_forward(C, a, 1, lm);
+    k_reduce_small(C, (const int8_t*)e8.p, e_res.p, 1, lm);
+    ntt_forward(C, e_res.p, 1, lm);
+    k_ksk_combine(C, a, e_res.p, d_sprime, b, j);
+  }
+  return key;
+}
+
+}  // namespace
+
+void keygen(Ctx& C, const std::vector<long>& steps) {
+  const int np = C.np();
+  const size_t NPN = (size_t)np * C.N;
+  const LimbMap lm = all_primes(C);
+  if (!C.has_keys) {
+    std::vector<int8_t> s8(C.N);
+    sample_small(C, HE_TAG_SECRET, 0, 0, s8.data());
+    DevBuf tmp8(C.N / 8 + 1, C.stream);
+    upload(C, tmp8.p, s8.data(), C.N);
+    C.d_s = DevBuf(NPN, C.stream);
+    k_reduce_small(C, (const int8_t*)tmp8.p, C.d_s.p, 1, lm);
+    ntt_forward(C, C.d_s.p, 1, lm);
+    // public key over Q (computed over all primes, Q limbs kept)
+    std::vector<u64> a_host(NPN);
+    sample_uniform(C, HE_TAG_PK_A, 0, 0, np, a_host.data());
+    std::vector<int8_t> e8(C.N);
+    sample_small(C, HE_TAG_PK_E, 0, 0, e8.data());
+    DevBuf a(NPN, C.stream), e(NPN, C.stream), b(NPN, C.stream);
+    upload(C, a.p, a_host.data(), NPN * 8);
+    upload(C, tmp8.p, e8.data(), C.N);
+    k_reduce_small(C, (const int8_t*)tmp8.p, e.p, 1, lm);
+    ntt_forward(C, a.p, 1, lm);
+    ntt_forward(C, e.p, 1, lm);
+    k_ksk_combine(C, a.p, e.p, C.d_s.p, b.p, -1);
+    C.d_pk = DevBuf((size_t)2 * C.L1 * C.N, C.stream);
+    HE_CUDA(cudaMemcpyAsync(C.d_pk.p, b.p, (size_t)C.L1 * C.N * 8, cudaMemcpyDeviceToDevice, C.stream));
+    HE_CUDA(cudaMemcpyAsync(C.d_pk.p + (size_t)C.L1 * C.N, a.p, (size_t)C.L1 * C.N * 8, cudaMemcpyDeviceToDevice,
+                            C.stream));
+    // relinearisation key: s' = s^2
+    DevBuf s2(NPN, C.stream);
+    k_mul(C, C.d_s.p, C.d_s.p, s2.p, 1, lm);
+    C.ksk[1] = make_ksk(C, 0, s2.p);
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+    C.has_keys = true;
+  }
+  for (long st : steps) {
+    const u64 k = C.galois_elt(st);
+    if (k == 1 || C.ksk.count(k)) continue;
+    DevBuf sk(NPN, C.stream);
+    k_permute(C, C.d_s.p, sk.p, (size_t)np, k);  // phi_k(s)
+    DevBuf key = make_ksk(C, k, sk.p);
+    // store phi_{k^-1}(key): k^-1 = 5^{-r} mod 2N is the Galois element of step -st
+    const u64 kinv = C.galois_elt(-st);
+    DevBuf perm(key.words, C.stream);
+    k_permute(C, key.p, perm.p, key.words / C.N, kinv);
+    C.ksk[k] = std::move(perm);
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// encryption / decryption
+// ---------------------------------------------------------------------------
+std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs, double scale, u64 id_base) {
+  if (!C.has_keys) throw Error(9, "no keys: call he_keygen first");
+  if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
+  auto out = new_set(C, n, 2, limbs, scale);
+  const size_t N = C.N;
+  // chunks of at most 32 ciphertexts bound the staging memory
+  const int chunk = std::min(n, 32);
+  std::vector<int8_t> small((size_t)3 * chunk * N);
+  DevBuf d8((size_t)3 * chunk * N / 8 + 1, C.stream), dm((size_t)chunk * N, C.stream);
+  DevBuf v((size_t)chunk * limbs * N, C.stream), e0((size_t)chunk * limbs * N, C.stream),
+      e1((size_t)chunk * limbs * N, C.stream), mr((size_t)chunk * limbs * N, C.stream);
+  const LimbMap lm = limbs_q(limbs, N);
+  for (int c0 = 0; c0 < n; c0 += chunk) {
+    const int cn = std::min(chunk, n - c0);
+    parallel_for((size_t)cn, [&](size_t c) {
+      const u64 id = id_base + (u64)(c0 + c);
+      sample_small(C, HE_TAG_ENC_V, id, 0, small.data() + c * N);
+      sample_small(C, HE_TAG_ENC_E0, id, 0, small.data() + ((size_t)chunk + c) * N);
+      sample_small(C, HE_TAG_ENC_E1, id, 0, small.data() + ((size_t)2 * chunk + c) * N);
+    });
+    upload(C, d8.p, small.data(), (size_t)3 * chunk * N);
+    upload(C, dm.p, m + (size_t)c0 * N, (size_t)cn * N * 8);
+    const int8_t* p8 = (const int8_t*)d8.p;
+    k_reduce_small(C, p8, v.p, cn, lm);
+    k_reduce_small(C, p8 + (size_t)chunk * N, e0.p, cn, lm);
+    k_reduce_small(C, p8 + (size_t)2 * chunk * N, e1.p, cn, lm);
+    k_reduce_signed(C, (const int64_t*)dm.p, mr.p, cn, lm);
+    ntt_forward(C, v.p, cn, lm);
+    ntt_forward(C, e0.p, cn, lm);
+    ntt_forward(C, e1.p, cn, lm);
+    ntt_forward(C, mr.p, cn, lm);
+    k_encrypt_combine(C, v.p, e0.p, e1.p, mr.p, out->ct(c0), cn, limbs);
+    HE_CUDA(cudaStreamSynchronize(C.stream));  // host staging reused by the next chunk
+  }
+  return out;
+}
+
+void decrypt_slots(Ctx& C, const CtSet& s, double* out) {
+  if (!C.has_keys) throw Error(9, "no secret key in this context");
+  if (s.polys != 2) throw Error(1, "decrypt expects two-component ciphertexts");
+  const size_t N = C.N, M = N / 2;
+  DevBuf m0((size_t)s.n * N, C.stream);
+  k_decrypt_limb0(C, s.buf.p, s.limbs, s.n, m0.p);
+  LimbMap lm = limbs_q(1, N);
+  ntt_inverse(C, m0.p, s.n, lm);
+  std::vector<u64> h((size_t)s.n * N);
+  HE_CUDA(cudaMemcpyAsync(h.data(), m0.p, h.size() * 8, cudaMemcpyDeviceToHost, C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  const u64 q0 = C.q[0];
+  parallel_for((size_t)s.n, [&](size_t c) {
+    std::vector<double> m(N);
+    for (size_t j = 0; j < N; j++) {
+      const u64 v = h[c * N + j];
+      m[j] = v > q0 / 2 ? -(double)(q0 - v) : (double)v;
+    }
+    decode_real(C, m.data(), s.scale, out + c * M);
+  });
+}
+
+void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
+  DevBuf t(s.buf.words, C.stream);
+  HE_CUDA(cudaMemcpyAsync(t.p, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+  ntt_inverse(C, t.p, s.n * s.polys, limbs_q(s.limbs, C.N));
+  HE_CUDA(cudaMemcpyAsync(host, t.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+}
+
+std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale) {
+  if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
+  for (size_t idx = 0; idx < (size_t)n * 2 * limbs * C.N; idx++) {
+    const int i = (int)((idx / C.N) % limbs);
+    if (host[idx] >= C.q[i]) throw Error(1, "residue out of range");
+  }
+  auto s = new_set(C, n, 2, limbs, scale);
+  upload(C, s->buf.p, host, s->buf.words * 8);
+  ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  return s;
+}
+
+}  // namespace he

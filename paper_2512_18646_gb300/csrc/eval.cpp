@@ -1,0 +1,280 @@
+// eval.cpp - homomorphic operations and the paper's multi-ciphertext layers,
+// as sequences of the kernels in kernels.cu / ntt.cu on the context stream.
+//
+// Canonical schedules (both this library and any checker must follow them for
+// bit-identical ciphertexts):
+//  - Rot(ct, l) (Sec. II-A): ModUp of c1 once per ciphertext; per step, the
+//    automorphism on every extended digit, inner product with the Galois key,
+//    ModDown; result (phi_k(c0) + v0, v1).
+//  - Mul (Sec. II-A): tensor product, relinearisation (key switch of d2), then
+//    rescale by the last prime.
+//  - matmul (Alg. 3 over n ciphertexts per operand, Sec. IV-A): hoisted
+//    rotations of every B~_k by idx = 0..p-1 (RowShifter applied idx times
+//    equals Rot(., idx) under whole-ring period-p tiling, Sec. III-B); per idx
+//    the n tensor products summed as three components (the SumColVec of
+//    Alg. 3 becomes ciphertext additions), one relinearisation, one rescale.
+//  - conv (Alg. 4 over the column layout, Sec. IV-B): hoisted rotations of
+//    every input column by gap*a, a < k; output (o, j') =
+//    sum_{c,b,a} round(K[o][c][a][b] q_l) Rot(X_{c, s j' + b}, gap a);
+//    rescale; + round(bias_o * scale).
+//  - FC: sum_{c,j} pt_{o,c,j} X_{c,j}; rescale; rotate-and-add over
+//    gap, 2 gap, ..., block/2; + round(bias_o * scale).
+#include <cmath>
+#include <cstring>
+
+#include "he_internal.h"
+
+namespace he {
+
+static LimbMap ext_map(const Ctx& C, int limbs) {
+  LimbMap m;
+  m.lpp = limbs + C.K; m.split = limbs; m.base0 = 0; m.base1 = C.L1;
+  m.poly_stride = (size_t)(limbs + C.K) * C.N;
+  return m;
+}
+static LimbMap p_map(const Ctx& C) {
+  LimbMap m;
+  m.lpp = C.K; m.split = 0; m.base0 = 0; m.base1 = C.L1; m.poly_stride = (size_t)C.K * C.N;
+  return m;
+}
+
+static u64 residue_of(int64_t v, u64 q) {
+  const int64_t r = v % (int64_t)q;
+  return r < 0 ? (u64)(r + (int64_t)q) : (u64)r;
+}
+
+// ModUp of polynomial `poly` of every ciphertext of a set (coefficient copy,
+// inverse NTT, base conversion per digit, forward NTT of the extended limbs).
+static DevBuf modup_poly(Ctx& C, const CtSet& in, int poly) {
+  const int n = in.n, lp = in.limbs, beta = C.beta_at(lp), nb = lp + C.K;
+  const size_t N = C.N;
+  DevBuf x((size_t)n * lp * N, C.stream);
+  k_copy_limbs(C, in.buf.p + (size_t)poly * lp * N, in.ct_words(), x.p, (size_t)lp * N, (size_t)n, lp);
+  ntt_inverse(C, x.p, n, limbs_q(lp, N));
+  DevBuf ext((size_t)n * beta * nb * N, C.stream);
+  k_modup(C, x.p, ext.p, n, lp);
+  ntt_forward(C, ext.p, n * beta, ext_map(C, lp));
+  return ext;
+}
+
+DevBuf modup_c1(Ctx& C, const CtSet& in) { return modup_poly(C, in, 1); }
+
+// Inner product with the key of Galois element k and ModDown. mode 0: add the
+// set's first two components (relinearisation of d2); mode 1: add phi_k(c0).
+static void ks_finish(Ctx& C, const CtSet& in, const DevBuf& ext, u64 k, int mode, u64* out, size_t out_stride) {
+  const int n = in.n, lp = in.limbs, nb = lp + C.K;
+  const size_t N = C.N;
+  const DevBuf& key = C.key(k);
+  DevBuf u((size_t)n * 2 * nb * N, C.stream);
+  k_ks_inner(C, ext.p, key.p, u.p, n, lp);
+  DevBuf pl((size_t)n * 2 * C.K * N, C.stream);
+  k_gather_p(C, u.p, pl.p, n, lp, k);
+  ntt_inverse(C, pl.p, n * 2, p_map(C));
+  DevBuf z((size_t)n * 2 * lp * N, C.stream);
+  k_moddown_bconv(C, pl.p, z.p, n, lp);
+  ntt_forward(C, z.p, n * 2, limbs_q(lp, N));
+  k_moddown_combine(C, u.p, z.p, in.buf.p, in.ct_words(), out, out_stride, n, lp, k, mode);
+}
+
+void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<long>& steps, u64* out,
+                     int out_cts_per_ct) {
+  const size_t cw = in.ct_words();
+  for (size_t s = 0; s < steps.size(); s++) {
+    const u64 k = C.galois_elt(steps[s]);
+    u64* o = out + s * cw;
+    if (k == 1) {
+      k_copy_limbs(C, in.buf.p, cw, o, cw * out_cts_per_ct, (size_t)in.n, 2 * in.limbs);
+      continue;
+    }
+    ks_finish(C, in, ext, k, 1, o, cw * out_cts_per_ct);
+  }
+}
+
+std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps) {
+  if (in.polys != 2) throw Error(1, "rotation expects two-component ciphertexts");
+  for (long s : steps)
+    if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
+  const int S = (int)steps.size();
+  auto out = new_set(C, in.n * S, 2, in.limbs, in.scale);
+  bool any = false;
+  for (long s : steps) any |= C.galois_elt(s) != 1;
+  DevBuf ext;
+  if (any) ext = modup_c1(C, in);
+  rotate_from_ext(C, in, ext, steps, out->buf.p, S);
+  return out;
+}
+
+void rescale_inplace(Ctx& C, CtSet& s) {
+  const int lp = s.limbs;
+  if (lp < 2) throw Error(2, "no level left to rescale");
+  const int rows = s.n * s.polys;
+  const size_t N = C.N;
+  DevBuf last((size_t)rows * N, C.stream);
+  k_copy_limbs(C, s.buf.p + (size_t)(lp - 1) * N, (size_t)lp * N, last.p, N, (size_t)rows, 1);
+  LimbMap lm1;
+  lm1.lpp = 1; lm1.split = 1; lm1.base0 = lp - 1; lm1.base1 = 0; lm1.poly_stride = N;
+  ntt_inverse(C, last.p, rows, lm1);
+  DevBuf r((size_t)rows * (lp - 1) * N, C.stream);
+  k_rescale_expand(C, last.p, r.p, rows, lp);
+  ntt_forward(C, r.p, rows, limbs_q(lp - 1, N));
+  DevBuf out((size_t)rows * (lp - 1) * N, C.stream);
+  k_rescale_combine(C, s.buf.p, r.p, out.p, rows, lp);
+  s.buf = std::move(out);
+  s.limbs = lp - 1;
+  s.scale = s.scale / (double)C.q[lp - 1];
+}
+
+std::unique_ptr<CtSet> relin_rescale(Ctx& C, const CtSet& d3) {
+  if (d3.polys != 3) throw Error(1, "relinearisation expects three-component ciphertexts");
+  auto out = new_set(C, d3.n, 2, d3.limbs, d3.scale);
+  DevBuf ext = modup_poly(C, d3, 2);
+  ks_finish(C, d3, ext, 1, 0, out->buf.p, out->ct_words());
+  rescale_inplace(C, *out);
+  return out;
+}
+
+static void check_pair(const CtSet& a, const CtSet& b) {
+  if (a.limbs != b.limbs) throw Error(4, "operands at different levels");
+  if (a.scale != b.scale) throw Error(4, "operands at different scales");
+}
+
+std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b) {
+  if (a.n != b.n) throw Error(1, "sets of different sizes");
+  if (a.limbs != b.limbs) throw Error(4, "operands at different levels");
+  if (a.limbs < 2) throw Error(2, "no level left for a product");
+  auto d = new_set(C, a.n, 3, a.limbs, a.scale * b.scale);
+  k_tensor(C, a.buf.p, b.buf.p, d->buf.p, a.n, a.limbs);
+  return relin_rescale(C, *d);
+}
+
+std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in) { return mul(C, in, in); }
+
+std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b) {
+  if (a.n != b.n) throw Error(1, "sets of different sizes");
+  check_pair(a, b);
+  auto out = new_set(C, a.n, 2, a.limbs, a.scale);
+  k_add(C, a.buf.p, b.buf.p, out->buf.p, a.n * 2, a.limbs);
+  return out;
+}
+
+// per-group constants round(v * scale) mod q_i, uploaded as [groups][limbs]
+static DevBuf const_table(Ctx& C, const double* v, int groups, int limbs, double scale) {
+  std::vector<u64> t((size_t)groups * limbs);
+  for (int g = 0; g < groups; g++) {
+    const int64_t iv = std::llround(v[g] * scale);
+    for (int i = 0; i < limbs; i++) t[(size_t)g * limbs + i] = residue_of(iv, C.q[i]);
+  }
+  DevBuf d(t.size(), C.stream);
+  HE_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  return d;
+}
+
+std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
+                              int c_out, int k, int stride) {
+  if (c_in < 1 || c_out < 1 || k < 1 || stride < 1 || gap < 1) throw Error(1, "bad convolution shape");
+  if (in.n % c_in) throw Error(1, "input set size is not a multiple of c_in");
+  const int w_in = in.n / c_in;
+  if (w_in < k) throw Error(1, "image narrower than the kernel");
+  const int w_out = (w_in - k) / stride + 1;
+  const int lp = in.limbs;
+  if (lp < 2) throw Error(2, "no level left for the convolution");
+  std::vector<long> steps(k);
+  for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
+  for (long s : steps)
+    if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
+  auto rot = rotate(C, in, steps);  // [c][j][a]
+  // integer weights round(K q_l) mod q_i with Shoup companions, [o][c][a][b][limb][2]
+  const u64 ql = C.q[lp - 1];
+  const size_t nw = (size_t)c_out * c_in * k * k;
+  std::vector<u64> wt(nw * lp * 2);
+  for (size_t t = 0; t < nw; t++) {
+    const int64_t iv = std::llround(W[t] * (double)ql);
+    for (int i = 0; i < lp; i++) {
+      const u64 r = residue_of(iv, C.q[i]);
+      wt[(t * lp + i) * 2] = r;
+      wt[(t * lp + i) * 2 + 1] = (u64)(((unsigned __int128)r << 64) / C.q[i]);
+    }
+  }
+  DevBuf dw(wt.size(), C.stream);
+  HE_CUDA(cudaMemcpyAsync(dw.p, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  auto out = new_set(C, c_out * w_out, 2, lp, in.scale);
+  k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp);
+  rot.reset();
+  rescale_inplace(C, *out);
+  out->scale = in.scale;  // scalars were encoded at scale q_l, which the rescale removes
+  if (bias) {
+    DevBuf cb = const_table(C, bias, c_out, lp - 1, out->scale);
+    k_add_const(C, out->buf.p, out->n, lp - 1, cb.p, w_out);
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+  }
+  HE_CUDA(cudaStreamSynchronize(C.stream));  // host weight table is freed on return
+  return out;
+}
+
+std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p) {
+  if (A.n != B.n || A.n < 1) throw Error(1, "A and B must have the same number n of ciphertexts");
+  if (p < 1 || (C.N / 2) % (size_t)p) throw Error(1, "p must divide the slot count");
+  if (A.limbs != B.limbs) throw Error(4, "operands at different levels");
+  if (A.limbs < 2) throw Error(2, "no level left for the product");
+  for (int s = 1; s < p; s++) C.key(C.galois_elt(s));
+  const int n = A.n, lp = A.limbs;
+  const size_t cw = (size_t)2 * lp * C.N;
+  DevBuf ext;
+  if (p > 1) ext = modup_c1(C, B);
+  // rotations by idx in chunks that bound the memory of the rotated operands
+  const size_t budget_words = (size_t)1 << 30;  // 8 GiB
+  int chunk = (int)std::max<size_t>(1, budget_words / ((size_t)n * cw));
+  if (chunk > p) chunk = p;
+  auto d = new_set(C, p, 3, lp, A.scale * B.scale);
+  DevBuf R((size_t)n * chunk * cw, C.stream);
+  for (int i0 = 0; i0 < p; i0 += chunk) {
+    const int ci = std::min(chunk, p - i0);
+    std::vector<long> steps(ci);
+    for (int t = 0; t < ci; t++) steps[t] = i0 + t;
+    rotate_from_ext(C, B, ext, steps, R.p, ci);
+    k_matmul_acc(C, A.buf.p, R.p, d->ct(i0), n, ci, lp);
+  }
+  R.reset();
+  ext.reset();
+  return relin_rescale(C, *d);
+}
+
+DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs) {
+  const size_t N = C.N, per = (size_t)limbs * N;
+  DevBuf pts((size_t)out_dim * n_in * per, C.stream);
+  const int chunk = 64;
+  DevBuf dm((size_t)chunk * N, C.stream);
+  const size_t total = (size_t)out_dim * n_in;
+  for (size_t c0 = 0; c0 < total; c0 += chunk) {
+    const int cn = (int)std::min<size_t>(chunk, total - c0);
+    HE_CUDA(cudaMemcpyAsync(dm.p, pts_host + c0 * N, (size_t)cn * N * 8, cudaMemcpyHostToDevice, C.stream));
+    k_reduce_signed(C, (const int64_t*)dm.p, pts.p + c0 * per, cn, limbs_q(limbs, N));
+    ntt_forward(C, pts.p + c0 * per, cn, limbs_q(limbs, N));
+  }
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  return pts;
+}
+
+std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
+                                const double* bias) {
+  const int lp = in.limbs;
+  if (lp < 2) throw Error(2, "no level left for the dense layer");
+  for (int t = gap; t < block_stride; t *= 2) C.key(C.galois_elt(t));
+  auto z = new_set(C, out_dim, 2, lp, in.scale);
+  k_fc_mac(C, in.buf.p, pts, z->buf.p, in.n, out_dim, lp);
+  rescale_inplace(C, *z);
+  z->scale = in.scale;  // plaintexts were encoded at scale q_l
+  for (int t = gap; t < block_stride; t *= 2) {
+    auto r = rotate(C, *z, {(long)t});
+    k_add(C, z->buf.p, r->buf.p, z->buf.p, z->n * 2, z->limbs);
+  }
+  if (bias) {
+    DevBuf cb = const_table(C, bias, out_dim, z->limbs, z->scale);
+    k_add_const(C, z->buf.p, z->n, z->limbs, cb.p, 1);
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+  }
+  return z;
+}
+
+}  // namespace he

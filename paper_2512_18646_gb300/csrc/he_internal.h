@@ -1,0 +1,221 @@
+// he_internal.h - internal types of the GB300 RNS-CKKS engine.
+//
+// Data layout in device memory (all residues uint64 in [0, q), NTT domain
+// unless stated):
+//   ciphertext set      [n][2][limbs][N]
+//   public key          [2][L1][N]
+//   switching key       [beta][2][L1 + K][N]   (Q limbs then P limbs)
+//   secret              [L1 + K][N]
+//   extended digits     [n][beta][limbs + K][N]   (ModUp output)
+// A "limb" is the N residues of one polynomial modulo one prime. Limb i of a
+// polynomial at level `limbs` uses prime i; extended polynomials append the K
+// special primes (global prime indices L1 .. L1+K-1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "he_arith.cuh"
+
+namespace he {
+
+// Error carried to the C ABI as a status code.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char* what);
+#define HE_CUDA(x) ::he::cuda_check((x), #x)
+
+struct Ctx;
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on the
+// context stream; the pool keeps freed memory for reuse).
+struct DevBuf {
+  u64* p = nullptr;
+  size_t words = 0;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t w, cudaStream_t s);
+  ~DevBuf();
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept;
+  void reset();
+};
+
+// Per-prime constants, one entry per global prime index.
+struct PrimeTab {
+  Mod mod;
+  u64 ninv, ninv_sh;  // N^{-1} mod q and its Shoup companion
+  u64 pmod;           // P = p_0 ... p_{K-1} mod q
+  u64 pad;
+};
+
+// Constants of one launch of the NTT over a batch of limbs. Limb i of each
+// polynomial (i < lpp) uses prime base0 + i if i < split, else base1 + i - split.
+struct LimbMap {
+  int lpp = 1, split = 1, base0 = 0, base1 = 0;
+  size_t poly_stride = 0;  // words between consecutive polynomials
+  __host__ __device__ int prime(int i) const { return i < split ? base0 + i : base1 + (i - split); }
+};
+
+struct Ctx {
+  int device = 0;
+  int log_n = 0;
+  size_t N = 0;
+  int L1 = 0, K = 0, alpha = 1;
+  double scale0 = 1.0, sigma = 3.2;
+  u64 seed = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<u64> q;         // host copy, Q then P
+  std::vector<PrimeTab> ptab; // host copy
+  uint64_t cdt[64];
+  int cdt_bound = 0;
+  // host FFT tables for encode/decode: e^{2 pi i k / M}, zeta^k (zeta = e^{i pi / N}),
+  // and the DFT index t_j = (5^j mod 2N - 1) / 4 of slot j (M = N/2)
+  std::vector<double> fft_root, fft_twist;  // interleaved re, im
+  std::vector<uint32_t> slot_index;
+
+  // device tables
+  DevBuf d_ptab;              // PrimeTab[np] (as words)
+  DevBuf d_psi;               // [np][2][N]: psi^{brv(k)} and Shoup companions
+  DevBuf d_ipsi;              // [np][2][N]: psi^{-brv(k)} and companions
+  DevBuf d_up;                // ModUp constants, see modup_table()
+  DevBuf d_down;              // ModDown constants
+  DevBuf d_rs;                // rescale constants [L1][L1][3]
+
+  // keys
+  bool has_keys = false;
+  DevBuf d_s;                 // secret [L1+K][N], NTT domain
+  DevBuf d_pk;                // [2][L1][N]
+  std::map<u64, DevBuf> ksk;  // Galois element (1 = relinearisation) -> key
+
+  int np() const { return L1 + K; }
+  int beta_at(int limbs) const { return (limbs + alpha - 1) / alpha; }
+  const PrimeTab* dev_ptab() const { return reinterpret_cast<const PrimeTab*>(d_ptab.p); }
+  u64 galois_elt(long step) const;
+  const DevBuf& key(u64 k) const;
+};
+
+// A set of n ciphertexts (or three-component products) at one level.
+struct CtSet {
+  Ctx* ctx = nullptr;
+  int n = 0, polys = 2, limbs = 0;
+  double scale = 1.0;
+  DevBuf buf;
+  size_t ct_words() const { return (size_t)polys * limbs * ctx->N; }
+  u64* ct(int i) const { return buf.p + (size_t)i * ct_words(); }
+};
+
+// ---- kernel launchers (kernels.cu / ntt.cu) ----
+void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
+void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
+inline LimbMap limbs_q(int limbs, size_t N) {  // plain polynomials, primes 0..limbs-1
+  LimbMap m;
+  m.lpp = limbs; m.split = limbs; m.base0 = 0; m.base1 = 0; m.poly_stride = (size_t)limbs * N;
+  return m;
+}
+
+// int64 coefficients [n][N] (device) -> residues [n][limbs][N] for primes of lm
+void k_reduce_signed(const Ctx& C, const int64_t* in, u64* out, int n, const LimbMap& lm);
+// small signed coefficients given as int8 [n][N] -> residues
+void k_reduce_small(const Ctx& C, const int8_t* in, u64* out, int n, const LimbMap& lm);
+
+// out = (v * pk + e + m) per limb, NTT domain; ct [n][2][limbs][N]
+void k_encrypt_combine(const Ctx& C, const u64* v, const u64* e0, const u64* e1, const u64* m, u64* ct, int n,
+                       int limbs);
+// key digit combine: b = -a s + e + (i in digit ? pmod_i s' : 0) over the QP basis
+void k_ksk_combine(const Ctx& C, const u64* a, const u64* e, const u64* sprime, u64* b, int digit);
+// out = a * b pointwise (all over QP or Q basis rows with prime map)
+void k_mul(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, const LimbMap& lm);
+// NTT-domain Galois permutation: out[j] = in[pi_k(j)] per limb (rows of N)
+void k_permute(const Ctx& C, const u64* in, u64* out, size_t rows, u64 k);
+// decrypt q_0 limb: m0 = c0 + c1 s (limb 0), n ciphertexts -> [n][N] (NTT domain)
+void k_decrypt_limb0(const Ctx& C, const u64* ct, int limbs, int n, u64* out);
+void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int limbs);
+// d[n][3][limbs] = tensor(a[n][2], b[n][2])
+void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs);
+// ModUp fast base conversion: x coeff [n][limbs][N] -> ext coeff [n][beta][limbs+K][N]
+void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs);
+// u[n][2][limbs+K] = sum_j ext[n][j] * key[j]  (NTT domain)
+void k_ks_inner(const Ctx& C, const u64* ext, const u64* key, u64* u, int n, int limbs);
+// gather P limbs of u (permuted by pi_k) into p [n][2][K][N]
+void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k);
+// ModDown base conversion: p coeff [n][2][K][N] -> z coeff [n][2][limbs][N]
+void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs);
+// out[n][2][limbs] = (u_Q[pi_k] - z) P^{-1} + add[pi_k or id]; add0/add1 may be null
+//   mode 0 (relin): out_c = d_c + ((u_c - z_c) P^{-1});  mode 1 (rotate): out_0 = phi_k(c0) + ..., out_1 = ...
+void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
+                       size_t out_stride, int n, int limbs, u64 k, int mode);
+// rescale helpers
+void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs);
+void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int rows, int limbs);
+// add integer constants to polynomial 0 of each ciphertext (NTT domain);
+// c_dev [n / per_group][limbs]: ciphertext c gets row c / per_group
+void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int per_group);
+// conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
+void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                int c_out, int w_out, int limbs);
+// matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx])
+void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
+// fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj]
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs);
+// copy groups x rows_per_group limbs: row r of group g at src + g src_gs + r N
+void k_copy_limbs(const Ctx& C, const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups,
+                  int rows_per_group);
+
+// ---- host-side building blocks (context.cpp / eval.cpp) ----
+void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, int special_bits, int alpha,
+              double log_scale, double sigma, u64 seed, cudaStream_t st);
+void keygen(Ctx& C, const std::vector<long>& steps);
+std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale);
+std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs, double scale, u64 id_base);
+void decrypt_slots(Ctx& C, const CtSet& s, double* out);
+void export_coeffs(Ctx& C, const CtSet& s, u64* host);
+std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale);
+
+// ModUp of polynomial 1 of every ciphertext: ext [n][beta][limbs+K][N], NTT domain
+DevBuf modup_c1(Ctx& C, const CtSet& in);
+// Rot by each step from a ModUp made by modup_c1; out ciphertext (c, s) at
+// out + (c * out_cts_per_ct + s) * ct_words
+void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<long>& steps, u64* out,
+                     int out_cts_per_ct);
+std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps);
+std::unique_ptr<CtSet> relin_rescale(Ctx& C, const CtSet& d3);
+void rescale_inplace(Ctx& C, CtSet& s);
+std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
+                              int c_out, int k, int stride);
+std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in);
+std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b);
+std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b);
+std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
+                                const double* bias);
+DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs);
+
+// host encode/decode (encode.cpp): real slot vector -> integer coefficients
+void encode_real(const Ctx& C, const double* z, size_t nz, double scale, int64_t* m);
+void decode_real(const Ctx& C, const double* m, double scale, double* z);
+
+}  // namespace he
+
+struct he_ctx {
+  he::Ctx c;
+};
+struct he_ctset {
+  std::unique_ptr<he::CtSet> s;
+};
+struct he_ptset {
+  he::Ctx* ctx = nullptr;
+  int out_dim = 0, n_in = 0, limbs = 0, gap = 1, block_stride = 1;
+  he::DevBuf buf;  // [out_dim][n_in][limbs][N]
+};

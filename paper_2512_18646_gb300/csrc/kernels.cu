@@ -1,0 +1,564 @@
+// kernels.cu - element-wise, base-conversion, key-switching and layer kernels
+// of the RNS-CKKS engine. Every kernel works on residues in [0, q) and writes
+// residues in [0, q); one thread handles one coefficient position, so global
+// reads and writes are coalesced along the N axis of each limb.
+//
+// Key switching is the hybrid scheme (digits of alpha primes): ModUp by fast
+// base conversion without correction, inner product with the key over the
+// Q*P basis, ModDown by (u_Q - BConv_P->Q(u_P)) P^{-1}. A Galois automorphism
+// phi_k acts on an NTT-domain limb as the permutation
+//   pi_k(j) = brv(((2 brv(j) + 1) k mod 2N - 1) / 2)
+// (evaluation point psi^(2 brv(j) + 1) goes to psi^((2 brv(j) + 1) k)), which
+// the kernels apply as gathers.
+#include "he_internal.h"
+
+namespace he {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned grid_for(size_t total) {
+  size_t b = (total + kBlock - 1) / kBlock;
+  const size_t cap = 152 * 32;
+  if (b > cap) b = cap;
+  if (b == 0) b = 1;
+  return (unsigned)b;
+}
+
+#define HE_GRID_LOOP(idx, total) \
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (total); idx += (size_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ u32 brv_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+
+// Index j' with NTT(phi_k(a))[j] = NTT(a)[j'].
+__device__ __forceinline__ u32 galois_index(u32 j, u64 k, int log_n) {
+  const u64 two_n_mask = (2ull << log_n) - 1;
+  const u64 e = 2 * (u64)brv_bits(j, log_n) + 1;
+  const u64 e2 = (e * k) & two_n_mask;
+  return brv_bits((u32)((e2 - 1) >> 1), log_n);
+}
+
+__device__ __forceinline__ u64 reduce_i64(int64_t v, const Mod& m) {
+  if (v >= 0) return reduce128(0, (u64)v, m);
+  const u64 r = reduce128(0, (u64)(-(v + 1)) + 1, m);  // |v| without overflow at INT64_MIN
+  return r ? m.q - r : 0;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_signed_kernel(const int64_t* in, u64* out, int n, LimbMap lm, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * lm.lpp * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1);
+    const size_t row = idx >> log_n;
+    const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
+    out[(size_t)p * lm.poly_stride + (size_t)i * N + j] = reduce_i64(in[(size_t)p * N + j], pt[lm.prime(i)].mod);
+  }
+}
+
+__global__ void k_reduce_small_kernel(const int8_t* in, u64* out, int n, LimbMap lm, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * lm.lpp * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1);
+    const size_t row = idx >> log_n;
+    const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
+    const int v = in[(size_t)p * N + j];
+    const u64 q = pt[lm.prime(i)].mod.q;
+    out[(size_t)p * lm.poly_stride + (size_t)i * N + j] = v >= 0 ? (u64)v : q - (u64)(-v);
+  }
+}
+
+// ct0 = v pk0 + e0 + m, ct1 = v pk1 + e1 (inputs [n][limbs][N], pk [2][L1][N])
+__global__ void k_encrypt_kernel(const u64* v, const u64* e0, const u64* e1, const u64* m, const u64* pk, u64* ct,
+                                 int n, int limbs, int L1, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * limbs * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1);
+    const size_t row = idx >> log_n;
+    const int i = (int)(row % limbs), c = (int)(row / limbs);
+    const Mod md = pt[i].mod;
+    const u64 vv = v[idx];
+    const u64 p0 = pk[(size_t)i * N + j], p1 = pk[((size_t)L1 + i) * N + j];
+    const size_t o = ((size_t)c * 2 * limbs + i) * N + j;
+    ct[o] = addmod(addmod(mulmod(vv, p0, md), e0[idx], md.q), m[idx], md.q);
+    ct[o + (size_t)limbs * N] = addmod(mulmod(vv, p1, md), e1[idx], md.q);
+  }
+}
+
+// b = -a s + e + [g in digit] (P mod q_g) s'  over all L1+K primes
+__global__ void k_ksk_kernel(const u64* a, const u64* e, const u64* s, const u64* sp, u64* b, int digit, int alpha,
+                             int L1, int np, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)np * N;
+  HE_GRID_LOOP(idx, total) {
+    const int g = (int)(idx >> log_n);
+    const PrimeTab P = pt[g];
+    const u64 q = P.mod.q;
+    u64 r = submod(e[idx], mulmod(a[idx], s[idx], P.mod), q);
+    if (g < L1 && g / alpha == digit) r = addmod(r, mulmod(P.pmod, sp[idx], P.mod), q);
+    b[idx] = r;
+  }
+}
+
+__global__ void k_mul_kernel(const u64* a, const u64* b, u64* out, int n, LimbMap lm, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * lm.lpp * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1);
+    const size_t row = idx >> log_n;
+    const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
+    const size_t o = (size_t)p * lm.poly_stride + (size_t)i * N + j;
+    out[o] = mulmod(a[o], b[o], pt[lm.prime(i)].mod);
+  }
+}
+
+__global__ void k_permute_kernel(const u64* in, u64* out, size_t rows, u64 k, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = rows * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1), r = idx >> log_n;
+    out[idx] = in[r * N + galois_index((u32)j, k, log_n)];
+  }
+}
+
+__global__ void k_decrypt0_kernel(const u64* ct, const u64* s, int limbs, int n, u64* out, const PrimeTab* pt,
+                                  int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * N;
+  const Mod md = pt[0].mod;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1), c = idx >> log_n;
+    const u64* x = ct + c * 2 * limbs * N;
+    out[idx] = addmod(x[j], mulmod(x[(size_t)limbs * N + j], s[j], md), md.q);
+  }
+}
+
+__global__ void k_add_kernel(const u64* a, const u64* b, u64* out, int n_polys, int limbs, const PrimeTab* pt,
+                             int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n_polys * limbs * N;
+  HE_GRID_LOOP(idx, total) {
+    const int i = (int)((idx >> log_n) % limbs);
+    out[idx] = addmod(a[idx], b[idx], pt[i].mod.q);
+  }
+}
+
+__global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int limbs, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)n * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t c = idx / LN, w = idx - c * LN;
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    const u64* A = a + c * 2 * LN;
+    const u64* B = b + c * 2 * LN;
+    const u64 a0 = A[w], a1 = A[LN + w], b0 = B[w], b1 = B[LN + w];
+    u64* D = d + c * 3 * LN;
+    D[w] = mulmod(a0, b0, md);
+    Acc128 acc{0, 0};
+    mac128(acc, a0, b1);
+    mac128(acc, a1, b0);
+    D[LN + w] = reduce128(acc.hi, acc.lo, md);
+    D[2 * LN + w] = mulmod(a1, b1, md);
+  }
+}
+
+// ModUp. Constant tables (words of d_up, indexed by the level `limbs`):
+//   inv [L1+1][L1][2]      (D_j/q_i)^{-1} mod q_i and its Shoup companion
+//   hat [L1+1][L1][L1+K]   (D_j/q_i) mod t_pos, pos over {q_0..q_{limbs-1}, p_0..}
+__global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alpha, int beta, int L1, int K,
+                               const u64* up_inv, const u64* up_hat, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int nb = limbs + K;
+  const size_t total = (size_t)n * beta * N;
+  const u64* inv = up_inv + (size_t)limbs * L1 * 2;
+  const u64* hat = up_hat + (size_t)limbs * L1 * (L1 + K);
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t r = idx >> log_n;
+    const int dg = (int)(r % beta), c = (int)(r / beta);
+    const int lo = dg * alpha, hi = min(lo + alpha, limbs);
+    const u64* X = x + (size_t)c * limbs * N;
+    u64* E = ext + ((size_t)c * beta + dg) * nb * N;
+    u64 y[8];
+    for (int i = lo; i < hi; i++) {
+      const u64 xi = X[(size_t)i * N + jn];
+      y[i - lo] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
+    }
+    for (int pos = 0; pos < nb; pos++) {
+      u64 out;
+      if (pos >= lo && pos < hi) {
+        out = X[(size_t)pos * N + jn];
+      } else {
+        const int g = pos < limbs ? pos : L1 + (pos - limbs);
+        Acc128 acc{0, 0};
+        for (int i = lo; i < hi; i++) mac128(acc, y[i - lo], hat[(size_t)i * (L1 + K) + pos]);
+        out = reduce128(acc.hi, acc.lo, pt[g].mod);
+      }
+      E[(size_t)pos * N + jn] = out;
+    }
+  }
+}
+
+// u[c][comp][pos] = sum_j ext[c][j][pos] key[j][comp][g(pos)]
+__global__ void k_ks_inner_kernel(const u64* ext, const u64* key, u64* u, int n, int limbs, int beta, int L1, int K,
+                                  const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int nb = limbs + K, npk = L1 + K;
+  const size_t total = (size_t)n * nb * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t r = idx >> log_n;
+    const int pos = (int)(r % nb), c = (int)(r / nb);
+    const int g = pos < limbs ? pos : L1 + (pos - limbs);
+    const u64* E = ext + (size_t)c * beta * nb * N + (size_t)pos * N + jn;
+    const u64* Kp = key + (size_t)g * N + jn;
+    Acc128 a0{0, 0}, a1{0, 0};
+    for (int dg = 0; dg < beta; dg++) {
+      const u64 e = E[(size_t)dg * nb * N];
+      mac128(a0, e, Kp[((size_t)dg * 2) * npk * N]);
+      mac128(a1, e, Kp[((size_t)dg * 2 + 1) * npk * N]);
+    }
+    const Mod md = pt[g].mod;
+    u64* U = u + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
+    U[0] = reduce128(a0.hi, a0.lo, md);
+    U[(size_t)nb * N] = reduce128(a1.hi, a1.lo, md);
+  }
+}
+
+__global__ void k_gather_p_kernel(const u64* u, u64* p, int n, int limbs, int K, u64 k, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int nb = limbs + K;
+  const size_t total = (size_t)n * 2 * K * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t r = idx >> log_n;
+    const int kk = (int)(r % K);
+    const size_t cc = r / K;  // ciphertext * 2 + component
+    const u32 src = k == 1 ? (u32)jn : galois_index((u32)jn, k, log_n);
+    p[idx] = u[(cc * nb + limbs + kk) * N + src];
+  }
+}
+
+// ModDown constants (words of d_down):
+//   pinv [K][2]   (P/p_k)^{-1} mod p_k, Shoup companion
+//   phat [K][L1]  (P/p_k) mod q_i
+//   Pinv [L1][2]  P^{-1} mod q_i, Shoup companion
+__global__ void k_moddown_bconv_kernel(const u64* p, u64* z, int n, int limbs, int L1, int K, const u64* down,
+                                       const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * 2 * N;
+  const u64* pinv = down;
+  const u64* phat = down + 2 * K;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1), cc = idx >> log_n;
+    u64 y[4];
+    for (int kk = 0; kk < K; kk++)
+      y[kk] = shoup(p[(cc * K + kk) * N + jn], pinv[2 * kk], pinv[2 * kk + 1], pt[L1 + kk].mod.q);
+    for (int i = 0; i < limbs; i++) {
+      Acc128 acc{0, 0};
+      for (int kk = 0; kk < K; kk++) mac128(acc, y[kk], phat[(size_t)kk * L1 + i]);
+      z[(cc * limbs + i) * N + jn] = reduce128(acc.hi, acc.lo, pt[i].mod);
+    }
+  }
+}
+
+// out[c][comp][i][j] = (u[c][comp][i][pi(j)] - z[c][comp][i][j]) P^{-1}  plus
+//   mode 0: base[c][comp][i][j]                (relinearisation: d0, d1)
+//   mode 1: comp 0 only, base[c][0][i][pi(j)]   (rotation: phi_k(c0))
+__global__ void k_moddown_combine_kernel(const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
+                                         size_t out_stride, int n, int limbs, int K, u64 k, int mode, const u64* Pinv,
+                                         const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int nb = limbs + K;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)n * 2 * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t r = idx >> log_n;
+    const int i = (int)(r % limbs);
+    const size_t cc = r / limbs;
+    const int comp = (int)(cc & 1);
+    const size_t c = cc >> 1;
+    const u32 src = k == 1 ? (u32)jn : galois_index((u32)jn, k, log_n);
+    const u64 q = pt[i].mod.q;
+    const u64 uu = u[(cc * nb + i) * N + src];
+    const u64 v = shoup(submod(uu, z[idx], q), Pinv[2 * i], Pinv[2 * i + 1], q);
+    u64 add = 0;
+    if (mode == 0) add = base[c * base_stride + (size_t)comp * LN + (size_t)i * N + jn];
+    else if (comp == 0) add = base[c * base_stride + (size_t)i * N + src];
+    out[c * out_stride + (size_t)comp * LN + (size_t)i * N + jn] = addmod(v, add, q);
+  }
+}
+
+// Rescale constants (words of d_rs): [L1+1][L1][3] = floor(q_l/2) mod q_i, q_l^{-1} mod q_i, Shoup
+__global__ void k_rescale_expand_kernel(const u64* last, u64* r, int rows, int limbs, const u64* rs,
+                                        const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int lo = limbs - 1;
+  const size_t total = (size_t)rows * N;
+  const Mod ml = pt[lo].mod;
+  const u64 half = ml.q >> 1;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1), row = idx >> log_n;
+    const u64 v = addmod(last[idx], half, ml.q);
+    for (int i = 0; i < lo; i++) r[(row * lo + i) * N + jn] = reduce128(0, v, pt[i].mod);
+  }
+}
+
+__global__ void k_rescale_combine_kernel(const u64* x, const u64* r, u64* out, int rows, int limbs, const u64* rs,
+                                         const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const int lo = limbs - 1;
+  const size_t total = (size_t)rows * lo * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t rr = idx >> log_n;
+    const int i = (int)(rr % lo);
+    const size_t row = rr / lo;
+    const u64 q = pt[i].mod.q;
+    const u64* t = rs + (size_t)i * 3;
+    const u64 xi = x[(row * limbs + i) * N + jn];
+    const u64 v = submod(addmod(xi, t[0], q), r[idx], q);
+    out[idx] = shoup(v, t[1], t[2], q);
+  }
+}
+
+__global__ void k_add_const_kernel(u64* ct, int n, int limbs, const u64* cdev, int per_group, const PrimeTab* pt,
+                                   int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)n * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t c = idx / LN, w = idx - c * LN;
+    const int i = (int)(w >> log_n);
+    u64* p = ct + c * 2 * LN + w;
+    *p = addmod(*p, cdev[(c / per_group) * limbs + i], pt[i].mod.q);
+  }
+}
+
+// Convolution multiply-accumulate. rot [c_in][w_in][k][2][limbs][N] holds
+// Rot(X_{c,j}, gap a) at [c][j][a]; w [c_out][c_in][k][k][limbs][2] holds the
+// integer weights mod q_i and Shoup companions ([o][c][a][b]). One thread per
+// (output column j', component, limb, coefficient) computes up to OB output
+// channels.
+template <int OB>
+__global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                                  int c_out, int w_out, int limbs, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)w_out * 2 * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1);
+    const size_t r = idx >> log_n;
+    const int i = (int)(r % limbs);
+    const int comp = (int)((r / limbs) & 1);
+    const int jp = (int)(r / limbs / 2);
+    const u64 q = pt[i].mod.q, q2 = 2 * q;
+    for (int o0 = 0; o0 < c_out; o0 += OB) {
+      const int ob = min(OB, c_out - o0);
+      u64 acc[OB];
+#pragma unroll
+      for (int t = 0; t < OB; t++) acc[t] = 0;
+      for (int c = 0; c < c_in; c++)
+        for (int b = 0; b < k; b++)
+          for (int a = 0; a < k; a++) {
+            const u64 x = rot[((((size_t)c * w_in + (size_t)stride * jp + b) * k + a) * 2 + comp) * LN + (size_t)i * N + jn];
+#pragma unroll
+            for (int t = 0; t < OB; t++) {
+              if (t < ob) {
+                const u64* ww = w + (((((size_t)(o0 + t) * c_in + c) * k + a) * k + b) * limbs + i) * 2;
+                u64 s = acc[t] + shoup_lazy(x, ww[0], ww[1], q);
+                if (s >= q2) s -= q2;
+                acc[t] = s;
+              }
+            }
+          }
+#pragma unroll
+      for (int t = 0; t < OB; t++)
+        if (t < ob) {
+          u64 v = acc[t];
+          if (v >= q) v -= q;
+          out[(((size_t)(o0 + t) * w_out + jp) * 2 + comp) * LN + (size_t)i * N + jn] = v;
+        }
+    }
+  }
+}
+
+// d[idx] (3 components) = sum_k tensor(A_k, R[k][idx]); R [n][p][2][limbs][N]
+__global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, int p, int limbs, const PrimeTab* pt,
+                                    int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)p * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t w = idx % LN;
+    const int id = (int)(idx / LN);
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
+    for (int kk = 0; kk < n; kk++) {
+      const u64* a = A + (size_t)kk * 2 * LN + w;
+      const u64* rr = R + ((size_t)kk * p + id) * 2 * LN + w;
+      const u64 a0 = a[0], a1 = a[LN], r0 = rr[0], r1 = rr[LN];
+      mac128(s0, a0, r0);
+      mac128(s1, a0, r1);
+      mac128(s1, a1, r0);
+      mac128(s2, a1, r1);
+      if ((kk & 7) == 7) {
+        s0 = Acc128{0, reduce128(s0.hi, s0.lo, md)};
+        s1 = Acc128{0, reduce128(s1.hi, s1.lo, md)};
+        s2 = Acc128{0, reduce128(s2.hi, s2.lo, md)};
+      }
+    }
+    u64* D = d + (size_t)id * 3 * LN + w;
+    D[0] = reduce128(s0.hi, s0.lo, md);
+    D[LN] = reduce128(s1.hi, s1.lo, md);
+    D[2 * LN] = reduce128(s2.hi, s2.lo, md);
+  }
+}
+
+// out[o] = sum_cj pt[o][cj] X[cj]; X [n_in][2][limbs][N], pt [out_dim][n_in][limbs][N]
+template <int OB>
+__global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
+                                const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)2 * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t w = idx % LN;
+    const int comp = (int)(idx / LN);
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    for (int o0 = 0; o0 < out_dim; o0 += OB) {
+      const int ob = min(OB, out_dim - o0);
+      Acc128 acc[OB];
+#pragma unroll
+      for (int t = 0; t < OB; t++) acc[t] = Acc128{0, 0};
+      for (int cj = 0; cj < n_in; cj++) {
+        const u64 x = X[((size_t)cj * 2 + comp) * LN + w];
+#pragma unroll
+        for (int t = 0; t < OB; t++)
+          if (t < ob) mac128(acc[t], x, ptx[((size_t)(o0 + t) * n_in + cj) * LN + w]);
+        if ((cj & 7) == 7) {
+#pragma unroll
+          for (int t = 0; t < OB; t++)
+            if (t < ob) acc[t] = Acc128{0, reduce128(acc[t].hi, acc[t].lo, md)};
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < OB; t++)
+        if (t < ob) out[((size_t)(o0 + t) * 2 + comp) * LN + w] = reduce128(acc[t].hi, acc[t].lo, md);
+    }
+  }
+}
+
+__global__ void k_copy_rows_kernel(const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups, int rpg,
+                                   int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = groups * rpg * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t jn = idx & (N - 1), r = idx >> log_n;
+    const size_t g = r / rpg, rr = r - g * rpg;
+    dst[g * dst_gs + rr * N + jn] = src[g * src_gs + rr * N + jn];
+  }
+}
+
+}  // namespace
+
+#define HE_LAUNCH(kern, total, ...)                                            \
+  do {                                                                         \
+    const size_t tot_ = (total);                                               \
+    if (tot_) kern<<<grid_for(tot_), kBlock, 0, C.stream>>>(__VA_ARGS__);     \
+    HE_CUDA(cudaGetLastError());                                               \
+  } while (0)
+
+void k_reduce_signed(const Ctx& C, const int64_t* in, u64* out, int n, const LimbMap& lm) {
+  HE_LAUNCH(k_reduce_signed_kernel, (size_t)n * lm.lpp * C.N, in, out, n, lm, C.dev_ptab(), C.log_n);
+}
+void k_reduce_small(const Ctx& C, const int8_t* in, u64* out, int n, const LimbMap& lm) {
+  HE_LAUNCH(k_reduce_small_kernel, (size_t)n * lm.lpp * C.N, in, out, n, lm, C.dev_ptab(), C.log_n);
+}
+void k_encrypt_combine(const Ctx& C, const u64* v, const u64* e0, const u64* e1, const u64* m, u64* ct, int n,
+                       int limbs) {
+  HE_LAUNCH(k_encrypt_kernel, (size_t)n * limbs * C.N, v, e0, e1, m, C.d_pk.p, ct, n, limbs, C.L1, C.dev_ptab(),
+            C.log_n);
+}
+void k_ksk_combine(const Ctx& C, const u64* a, const u64* e, const u64* sprime, u64* b, int digit) {
+  HE_LAUNCH(k_ksk_kernel, (size_t)C.np() * C.N, a, e, C.d_s.p, sprime, b, digit, C.alpha, C.L1, C.np(),
+            C.dev_ptab(), C.log_n);
+}
+void k_mul(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, const LimbMap& lm) {
+  HE_LAUNCH(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
+}
+void k_permute(const Ctx& C, const u64* in, u64* out, size_t rows, u64 k) {
+  HE_LAUNCH(k_permute_kernel, rows * C.N, in, out, rows, k, C.log_n);
+}
+void k_decrypt_limb0(const Ctx& C, const u64* ct, int limbs, int n, u64* out) {
+  HE_LAUNCH(k_decrypt0_kernel, (size_t)n * C.N, ct, C.d_s.p, limbs, n, out, C.dev_ptab(), C.log_n);
+}
+void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int limbs) {
+  HE_LAUNCH(k_add_kernel, (size_t)n_polys * limbs * C.N, a, b, out, n_polys, limbs, C.dev_ptab(), C.log_n);
+}
+void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs) {
+  HE_LAUNCH(k_tensor_kernel, (size_t)n * limbs * C.N, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
+}
+void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs) {
+  if (C.alpha > 8) throw Error(8, "digits of more than 8 primes are not supported");
+  const u64* up_inv = C.d_up.p;
+  const u64* up_hat = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2;
+  HE_LAUNCH(k_modup_kernel, (size_t)n * C.beta_at(limbs) * C.N, x, ext, n, limbs, C.alpha, C.beta_at(limbs), C.L1,
+            C.K, up_inv, up_hat, C.dev_ptab(), C.log_n);
+}
+void k_ks_inner(const Ctx& C, const u64* ext, const u64* key, u64* u, int n, int limbs) {
+  HE_LAUNCH(k_ks_inner_kernel, (size_t)n * (limbs + C.K) * C.N, ext, key, u, n, limbs, C.beta_at(limbs), C.L1, C.K,
+            C.dev_ptab(), C.log_n);
+}
+void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k) {
+  HE_LAUNCH(k_gather_p_kernel, (size_t)n * 2 * C.K * C.N, u, p, n, limbs, C.K, k, C.log_n);
+}
+void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs) {
+  if (C.K > 4) throw Error(8, "more than 4 special primes are not supported");
+  HE_LAUNCH(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
+            C.log_n);
+}
+void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
+                       size_t out_stride, int n, int limbs, u64 k, int mode) {
+  const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)C.K * C.L1;
+  HE_LAUNCH(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, u, z, base, base_stride, out, out_stride, n,
+            limbs, C.K, k, mode, Pinv, C.dev_ptab(), C.log_n);
+}
+void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs) {
+  HE_LAUNCH(k_rescale_expand_kernel, (size_t)rows * C.N, last_coeff, r, rows, limbs, C.d_rs.p, C.dev_ptab(),
+            C.log_n);
+}
+void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int rows, int limbs) {
+  const u64* tab = C.d_rs.p + (size_t)limbs * C.L1 * 3;
+  HE_LAUNCH(k_rescale_combine_kernel, (size_t)rows * (limbs - 1) * C.N, x, r, out, rows, limbs, tab, C.dev_ptab(),
+            C.log_n);
+}
+void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int per_group) {
+  HE_LAUNCH(k_add_const_kernel, (size_t)n * limbs * C.N, ct, n, limbs, c_dev, per_group, C.dev_ptab(), C.log_n);
+}
+void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                int c_out, int w_out, int limbs) {
+  HE_LAUNCH(k_conv_mac_kernel<8>, (size_t)w_out * 2 * limbs * C.N, rot, out, w, c_in, w_in, k, stride, c_out, w_out,
+            limbs, C.dev_ptab(), C.log_n);
+}
+void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
+  HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
+}
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs) {
+  HE_LAUNCH(k_fc_mac_kernel<10>, (size_t)2 * limbs * C.N, X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+}
+void k_copy_limbs(const Ctx& C, const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups,
+                  int rows_per_group) {
+  HE_LAUNCH(k_copy_rows_kernel, groups * rows_per_group * C.N, src, src_gs, dst, dst_gs, groups, rows_per_group,
+            C.log_n);
+}
+
+}  // namespace he

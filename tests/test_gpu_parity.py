@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Ciphertexts are compared limb by limb, bit for bit, in the coefficient domain:
+both sides start from the same integer plaintexts and the same seeded
+randomness (inputs/he_random.h) and follow the same canonical schedules.
+Decrypted results are also checked against FP64 closed forms. Sizes span
+several NTT tiles and ragged counts (sets not a multiple of any chunk).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from inputs import synthetic
+from oracle import fp64_ref, layouts
+from tests.gpu_pairs import encode_columns, encrypt_both, image_columns_both, make_pair, pair_from_preset
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_18646_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+# ---------------------------------------------------------------------------
+# transform and encryption
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("log_n", [4, 5, 10, 13, 16])
+def test_ntt_matches_oracle(lib, log_n):
+    o, g = make_pair(log_n, (60, 40, 45), 2, 60, 1, 40.0, steps=None)
+    rng = np.random.default_rng(log_n)
+    a = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.primes])[None]  # [1][np][N]
+    fwd = g.ntt(a, 0)
+    for pi in range(len(o.primes)):
+        assert np.array_equal(fwd[0, pi], o.ntt(a[0, pi], pi)), pi
+    assert np.array_equal(g.ntt(fwd, 0, inverse=True), a)
+    # several polynomials per launch, a prime offset
+    b = np.stack([np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.primes[1:3]]) for _ in range(3)])
+    fb = g.ntt(b, 1)
+    for t in range(3):
+        for i in range(2):
+            assert np.array_equal(fb[t, i], o.ntt(b[t, i], 1 + i))
+
+
+def test_encrypt_matches_oracle(lib):
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=3, steps=[])
+    z = np.random.default_rng(1).uniform(-1, 1, (5, o.slots))
+    m = encode_columns(o, z)
+    for limbs in (4, 2, 1):
+        oc, gc = encrypt_both(o, g, m, limbs, ct_id_base=100 + limbs)
+        assert np.array_equal(gc.export(), oc)
+    # decryption on the device reads the same message
+    d = g.decrypt_slots(gc)
+    assert np.abs(d - z).max() < 1e-6
+
+
+def test_encoder_matches_oracle_encoder(lib):
+    o, g = make_pair(12, (60, 40), 1, 60, 1, 40.0, steps=[])
+    A = np.random.default_rng(2).uniform(-1, 1, (6, 9))
+    gc = g.encrypt_matrix_a(A, 7)
+    z = layouts.matrix_a_columns(A, o.slots)
+    m = encode_columns(o, z)
+    oc = np.stack([o.encrypt(m[i], o.L1, 7 + i) for i in range(9)])
+    ge = gc.export()
+    # independent encoders may round a coefficient differently by one unit;
+    # the difference of the two ciphertexts is then that small plaintext
+    diff = o.decrypt_coeffs(ge[0]) - o.decrypt_coeffs(oc[0])
+    assert np.abs(diff).max() <= 1
+    assert np.abs(g.decrypt_slots(gc)[:, :6] - A.T).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# primitives
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("params", [
+    (10, (60, 40, 40, 40), 1, 60, 1, 40.0),          # one special prime, digits of one prime
+    (11, (60, 45, 45, 45, 45, 45), 2, 60, 2, 45.0),   # CNN shape: two specials, digits of two
+])
+def test_rotation_matches_oracle(lib, params):
+    steps = [0, 1, 3, 5, -2, 17]
+    o, g = make_pair(*params, seed=5, steps=[s for s in steps if s])
+    z = np.random.default_rng(3).uniform(-1, 1, (3, o.slots))
+    m = encode_columns(o, z)
+    for limbs in (o.L1, 2):
+        oc, gc = encrypt_both(o, g, m, limbs, ct_id_base=30)
+        r = g.rotate(gc, steps).export().reshape(3, len(steps), 2, limbs, o.N)
+        for c in range(3):
+            ref = o.rotate(oc[c], steps)
+            for t in range(len(steps)):
+                assert np.array_equal(r[c, t], ref[t]), (limbs, c, steps[t])
+    dz = g.decrypt_slots(g.rotate(gc, [1]))
+    assert np.abs(dz - np.roll(z, -1, axis=1)).max() < 1e-5
+
+
+def test_mul_relin_rescale_matches_oracle(lib):
+    o, g = make_pair(11, (60, 45, 45, 45, 45), 2, 60, 2, 45.0, seed=6, steps=[])
+    rng = np.random.default_rng(4)
+    x, y = rng.uniform(-1, 1, (4, o.slots)), rng.uniform(-1, 1, (4, o.slots))
+    ox, gx = encrypt_both(o, g, encode_columns(o, x), ct_id_base=0)
+    oy, gy = encrypt_both(o, g, encode_columns(o, y), ct_id_base=10)
+    gm = g.mul(gx, gy).export()
+    for c in range(4):
+        ref = o.rescale(o.relin(o.tensor(ox[c], oy[c])))
+        assert np.array_equal(gm[c], ref)
+    sq = g.square(gx).export()
+    for c in range(4):
+        assert np.array_equal(sq[c], o.square(ox[c:c + 1])[0])
+
+
+def test_rescale_matches_oracle_on_random_residues(lib):
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, steps=None)
+    rng = np.random.default_rng(5)
+    ct = np.stack([np.stack([np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.q])
+                             for _ in range(2)]) for _ in range(7)])
+    gs = g.import_coeffs(ct, 2.0 ** 40)
+    assert np.array_equal(gs.export(), ct)
+    g.rescale(gs)
+    out = gs.export()
+    for c in range(7):
+        assert np.array_equal(out[c], o.rescale(ct[c]))
+
+
+# ---------------------------------------------------------------------------
+# layers at small sizes: bit-exact and FP64
+# ---------------------------------------------------------------------------
+def test_matmul_small_config_matches_oracle_and_fp64(lib):
+    """The 4x8 . 8x4 matmul at N = 2^13, Q = 60 + 40 + 40 bits, P = 60 bits."""
+    pre = synthetic.MATMUL_SMALL
+    o, g = pair_from_preset(pre, seed=101, steps=list(range(1, 4)))
+    A, Bm = synthetic.matmul_operands(4, 8, 4, seed=101)
+    oa, ga = encrypt_both(o, g, encode_columns(o, layouts.matrix_a_columns(A, o.slots)), ct_id_base=0)
+    ob, gb = encrypt_both(o, g, encode_columns(o, layouts.matrix_b_rows(Bm, o.slots)), ct_id_base=100)
+    gd = g.matmul(ga, gb, 4, 4)
+    od = o.matmul(oa, ob, 4)
+    assert np.array_equal(gd.export(), od)
+    C = g.decrypt_matrix(gd, 4, 4)
+    assert np.abs(C - A @ Bm).max() < 1e-4
+    # the library's own encoders (he_encrypt_matrix_a/b) give the same product within tolerance
+    C2 = g.decrypt_matrix(g.matmul(g.encrypt_matrix_a(A, 0), g.encrypt_matrix_b(Bm, 100), 4, 4), 4, 4)
+    assert np.abs(C2 - A @ Bm).max() < 1e-4
+
+
+@pytest.mark.parametrize("m,n,p", [(5, 3, 8), (16, 7, 1), (3, 1, 2)])
+def test_matmul_ragged_shapes(lib, m, n, p):
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=9, steps=list(range(1, max(p, 2))))
+    rng = np.random.default_rng(m * 100 + n * 10 + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    oa, ga = encrypt_both(o, g, encode_columns(o, layouts.matrix_a_columns(A, o.slots)), ct_id_base=0)
+    ob, gb = encrypt_both(o, g, encode_columns(o, layouts.matrix_b_rows(Bm, o.slots)), ct_id_base=50)
+    gd = g.matmul(ga, gb, m, p)
+    assert np.array_equal(gd.export(), o.matmul(oa, ob, p))
+    assert np.abs(g.decrypt_matrix(gd, m, p) - A @ Bm).max() < 1e-5
+
+
+@pytest.mark.parametrize("stride,c_in,k,side", [(1, 1, 3, 9), (2, 3, 3, 11), (2, 1, 5, 13), (1, 2, 1, 6)])
+def test_conv2d_matches_oracle_and_fp64(lib, stride, c_in, k, side):
+    H = 16
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=7, steps=list(range(1, k)))
+    rng = np.random.default_rng(stride * 10 + c_in)
+    imgs = rng.uniform(0, 1, (3, c_in, side, side - 1))
+    K = rng.normal(0, 0.3, (4, c_in, k, k))
+    bias = rng.normal(0, 0.3, 4)
+    ox, gx = image_columns_both(o, g, imgs, H, ct_id_base=1000)
+    gy = g.conv2d(gx, c_in, 1, K, bias, stride)
+    oy = o.conv2d(ox, 1, K, bias, stride, o.scale)
+    assert np.array_equal(gy.export(), oy)
+    ref = fp64_ref.conv2d(imgs, K, bias, stride)
+    got = g.decrypt_image(gy, 3, H, stride, ref.shape[2])  # [B][o*w'][h']
+    got = got.reshape(3, 4, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
+    assert np.abs(got - ref).max() < 1e-5
+
+
+def test_fc_matches_oracle(lib):
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=8, steps=[2, 4, 8])
+    rng = np.random.default_rng(8)
+    c_in, hv, w_in, gap, H, Bn, out_dim = 3, 5, 4, 2, 16, 4, 6
+    x = rng.uniform(-1, 1, (Bn, c_in, hv, w_in))
+    W = rng.normal(0, 0.3, (out_dim, c_in * hv * w_in))
+    b = rng.normal(0, 0.3, out_dim)
+    z = np.concatenate([layouts.image_columns(x[:, c], o.slots, H, gap) for c in range(c_in)])
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=0)
+    ox = ox.reshape(c_in, w_in, *ox.shape[1:])
+    lp = o.L1
+    pts = o.fc_plaintexts(lp, c_in, hv, w_in, gap, H, Bn, W, list(range(out_dim)))
+    oz = o.fc(ox, gap, H, pts, b, o.scale, list(range(out_dim)))
+    gp = g.fc_prepare_coeffs(pts, gap, H, lp)
+    gz = g.fc_apply(gx, gp, b)
+    assert np.array_equal(gz.export(), oz)
+    logits = layouts.logits_from_fc(g.decrypt_slots(gz), Bn, H)
+    assert np.abs(logits - fp64_ref.dense(x, W, b)).max() < 1e-5
+    # the library's own weight encoder agrees within tolerance
+    gp2 = g.fc_prepare(W, c_in, hv, w_in, gap, H, Bn, lp)
+    logits2 = layouts.logits_from_fc(g.decrypt_slots(g.fc_apply(gx, gp2, b)), Bn, H)
+    assert np.abs(logits2 - fp64_ref.dense(x, W, b)).max() < 1e-5
+
+
+def test_cnn_small_matches_oracle(lib):
+    """conv 5x5 s2 -> x^2 -> conv 3x3 s2 -> x^2 -> FC, CNN prime shape, reduced ring and image."""
+    o, g = make_pair(10, (60,) + (45,) * 6, 2, 60, 2, 45.0, seed=31, steps=[1, 2, 3, 4, 8, 16])
+    side, H, Bn = 17, 32, 3
+    h1 = (side - 5) // 2 + 1
+    h2 = (h1 - 3) // 2 + 1
+    rng = np.random.default_rng(31)
+    imgs = rng.uniform(0, 1, (Bn, 1, side, side))
+    c1w, c1b = rng.normal(0, 0.2, (2, 1, 5, 5)), rng.normal(0, 0.2, 2)
+    c2w, c2b = rng.normal(0, 0.2, (3, 2, 3, 3)), rng.normal(0, 0.2, 3)
+    fw, fb = rng.normal(0, 0.2, (4, 3 * h2 * h2)), rng.normal(0, 0.2, 4)
+    ox, gx = image_columns_both(o, g, imgs, H)
+    sc = o.scale
+    gy = g.conv2d(gx, 1, 1, c1w, c1b, 2)
+    oy = o.conv2d(ox, 1, c1w, c1b, 2, sc)
+    assert np.array_equal(gy.export(), oy)
+    g.square(gy)
+    oy = o.square(oy)
+    assert np.array_equal(gy.export(), oy)
+    sc = sc * sc / o.q[o.L1 - 2]
+    assert gy.scale == sc
+    oy = oy.reshape(2, h1, *oy.shape[1:])
+    gy2 = g.conv2d(gy, 2, 2, c2w, c2b, 2)
+    oy2 = o.conv2d(oy, 2, c2w, c2b, 2, sc)
+    assert np.array_equal(gy2.export(), oy2)
+    g.square(gy2)
+    oy2 = o.square(oy2)
+    lp = oy2.shape[2]
+    sc = sc * sc / o.q[lp]
+    oy2 = oy2.reshape(3, h2, *oy2.shape[1:])
+    pts = o.fc_plaintexts(lp, 3, h2, h2, 4, H, Bn, fw, list(range(4)))
+    oz = o.fc(oy2, 4, H, pts, fb, sc, list(range(4)))
+    gz = g.fc_apply(gy2, g.fc_prepare_coeffs(pts, 4, H, lp), fb)
+    assert np.array_equal(gz.export(), oz)
+    logits = layouts.logits_from_fc(g.decrypt_slots(gz), Bn, H)
+    x = fp64_ref.conv2d(imgs, c1w, c1b, 2) ** 2
+    x = fp64_ref.conv2d(x, c2w, c2b, 2) ** 2
+    assert np.abs(logits - fp64_ref.dense(x, fw, fb)).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# errors and degenerate cases
+# ---------------------------------------------------------------------------
+def test_errors(lib):
+    from paper_2512_18646_gb300 import HeError, api
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_LEVEL, HE_E_NOKEY, HE_E_STATE
+    g = api.Context(8, (60, 40), 1, 60, 1, 40.0)
+    with pytest.raises(HeError) as e:
+        g.encrypt_matrix_a(np.ones((2, 2)))
+    assert e.value.code == HE_E_STATE
+    g.keygen([1])
+    x = g.encrypt_matrix_a(np.ones((2, 3)))
+    with pytest.raises(HeError) as e:
+        g.rotate(x, [2])
+    assert e.value.code == HE_E_NOKEY
+    y = g.mul(x, x)
+    with pytest.raises(HeError) as e:
+        g.mul(y, y)
+    assert e.value.code == HE_E_LEVEL
+    with pytest.raises(HeError) as e:
+        g.encrypt_matrix_b(np.ones((2, 3)))  # 3 does not divide the slot count
+    assert e.value.code == HE_E_ARG
+    with pytest.raises(HeError) as e:
+        g.encrypt_image(np.ones((1, 5, 5)), 4)  # block smaller than the image
+    assert e.value.code == HE_E_ARG
+    with pytest.raises(HeError) as e:
+        api.Context(20, (60,), 1, 60, 1, 40.0)
+    assert e.value.code == HE_E_ARG
