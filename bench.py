@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted-CNN images/s at N = 2^16 (RNS-CKKS on one GB300).
+
+One step is one encrypted inference of the three-layer CNN
+conv 8x5x5 stride 2 -> x^2 -> conv 16x3x3 stride 2 -> x^2 -> FC 10
+over one batch of 128x128 images packed into the column layout (w = 128
+ciphertexts of h = 128 pixels; `--batch` images side by side in blocks of
+128 slots, 256 fills the 32768 slots). Ring degree N = 2^16, Q = 60 + 12 x 45
+bits, P = 2 x 60 bits, key-switching digits of two primes, scale 2^45.
+
+The step covers every row of the path: hoisted rotations with hybrid key
+switching, the ciphertext-scalar multiply-accumulate of the convolutions,
+ciphertext-ciphertext products with relinearisation, rescales, ciphertext-
+plaintext products and rotate-and-add of the dense layer, all on the NTT
+engine. Inputs are synthetic (seeded), already encrypted and resident in
+device memory when the timed region starts; they are larger than L2.
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the
+same workload on the host cores and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from inputs import synthetic  # noqa: E402
+
+METRIC = "encrypted-CNN images/s (N=2^16, 128x128, conv5x5s2x8-x2-conv3x3s2x16-x2-fc10)"
+UNIT = "images/s"
+SIDE = 128
+H = 128  # block stride (rows per image block)
+ROT_STEPS = [1, 2, 3, 4, 8, 16, 32, 64]
+WORKLOAD = ("encrypted CNN conv5x5s2(8)->x^2->conv3x3s2(16)->x^2->fc10 on 128x128 grayscale images in the "
+            "column layout (128 ciphertexts of 128 pixels); RNS-CKKS N=2^16, Q=60+12x45, P=2x60, alpha=2 (7 digits), "
+            "scale 2^45")
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def profile_read(lib):
+    import ctypes
+    n = ctypes.c_int()
+    names = ctypes.create_string_buffer(1 << 16)
+    ms = (ctypes.c_double * 256)()
+    cnt = (ctypes.c_uint64 * 256)()
+    by = (ctypes.c_double * 256)()
+    rc = lib.he_profile_read(names, len(names), ms, cnt, by, 256, ctypes.byref(n))
+    assert rc == 0
+    nm = names.value.decode().split("\n")[: n.value]
+    return {nm[i]: {"ms": ms[i], "launches": int(cnt[i]), "bytes": by[i]} for i in range(n.value)}
+
+
+def cnn_step(g, x, w, pts):
+    y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
+    g.square(y)
+    y = g.conv2d(y, 8, 2, w.conv2_w, w.conv2_b, 2)
+    g.square(y)
+    return g.fc_apply(y, pts, w.fc_b)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import fp64_ref  # FP64 closed form, used only for the accuracy check outside timing
+    from paper_2512_18646_gb300 import api, load
+
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    pre = synthetic.CNN_N16
+    g = api.Context.from_preset(pre, seed=1000 + rank, stream=stream.cuda_stream)
+    g.keygen(ROT_STEPS)
+    B = args.batch
+    h1, h2 = synthetic.cnn_shapes(SIDE)
+    w = synthetic.cnn_weights(SIDE, seed=302)
+    imgs = synthetic.images(B, SIDE, SIDE, seed=301 + rank)
+    x = g.encrypt_image(imgs, H, ct_id_base=0)
+    fc_limbs = pre_limbs = len(pre.q_bits) - 4
+    pts = g.fc_prepare(w.fc_w, 16, h2, h2, 4, H, B, fc_limbs)
+    g.synchronize()
+
+    def step():
+        return cnn_step(g, x, w, pts)
+
+    for _ in range(args.warmup):
+        z = step()
+    g.synchronize()
+    launches0 = lib.he_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        g.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            z = step()
+        e1.record(stream)
+        e1.synchronize()
+        g.synchronize()
+        torch.cuda.synchronize()
+    launches = lib.he_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = B * args.steps * world / (t_max / 1e3)
+
+    # accuracy of the last step's logits against the FP64 CNN (outside timing)
+    logits = g.decrypt_slots(z)[:, ::H][:, :B].T
+    ref = fp64_ref.cnn(imgs, w)
+    max_err = float(np.abs(logits - ref).max())
+
+    # per-kernel device time with CUDA events on the launching stream
+    lib.he_profile_enable(1)
+    for _ in range(args.steps):
+        step()
+    g.synchronize()
+    prof = profile_read(lib)
+    lib.he_profile_enable(0)
+    prof_total = sum(v["ms"] for v in prof.values())
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    pk = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    t = prof[top]
+    achieved = t["bytes"] / (t["ms"] / 1e3) / 1e9 / 1.0 if t["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_source": "measured" if "fallback" not in pk else "fallback",
+                "share_of_device_time": round(t["ms"] / prof_total, 4),
+                "launches": t["launches"], "avg_launch_us": round(1e3 * t["ms"] / max(1, t["launches"]), 2)}
+    breakdown = {k: {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
+                     "launches_per_step": v["launches"] // args.steps,
+                     "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the C ABI: host ciphertexts in (pinned), encrypted logits out
+    e2e = None
+    if not args.no_e2e:
+        host_in = x.export()
+        pin_in = torch.from_numpy(host_in).pin_memory()
+        pin_arr = pin_in.numpy()
+        out_words = 10 * 2 * (fc_limbs - 1) * g.N
+        pin_out = torch.empty(out_words, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        import ctypes
+        from paper_2512_18646_gb300._lib import P_U64, check
+        g.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xin = g.import_coeffs(pin_arr, g.scale)
+            zz = cnn_step(g, xin, w, pts)
+            check(lib.he_ctset_export(zz.h, pin_out.ctypes.data_as(P_U64), pin_out.size))
+        g.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([t_e2e], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": round(B * args.steps * world / t_e2e, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(pin_arr.nbytes), "d2h_bytes_per_step": int(out_words * 8),
+               "ms_per_step": round(1e3 * t_e2e / args.steps, 3)}
+
+    clocks = clk.summary()
+    return {
+        "value": value, "ms_per_step": t_max / args.steps, "launches": launches // args.steps * args.steps,
+        "roofline": roofline, "breakdown": breakdown, "e2e": e2e, "clocks": clocks, "max_abs_err": max_err,
+        "images_per_step": B,
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+KS_PER_INFERENCE = 128 * 4 + 496 + 496 * 2 + 480 + 10 * 5  # rotations + relinearisations of one step
+
+
+def oracle_sample(batch: int):
+    """Conv-1 output column 0 (all 8 channels) on the oracle at the full parameters.
+
+    The sample runs 20 hoisted rotations (5 ModUps) at the top level, 200
+    ciphertext-scalar products and 8 rescales; its time is scaled to one
+    inference by the number of key switches (KS_PER_INFERENCE / 20)."""
+    from oracle import Oracle, layouts
+    pre = synthetic.CNN_N16
+    o = Oracle.from_preset(pre, seed=7)
+    o.keygen([1, 2, 3, 4])
+    imgs = synthetic.images(batch, SIDE, 5, seed=301)
+    z = layouts.image_columns(imgs, o.slots, H)
+    X = np.stack([o.encrypt(o.encode(z[j]), o.L1, j) for j in range(5)])[None]
+    w = synthetic.cnn_weights(SIDE, seed=302)
+    t0 = time.perf_counter()
+    o.conv2d(X, 1, w.conv1_w, w.conv1_b, 2, o.scale, sel=[(c, 0) for c in range(8)])
+    dt = time.perf_counter() - t0
+    per_inference = dt * KS_PER_INFERENCE / 20.0
+    return dt, per_inference
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    cfg = {"workload": WORKLOAD, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
+           "parallelism": f"replicas x{world} (independent inferences, no collective)",
+           "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.warmup):
+            oracle_sample(args.batch)
+        for _ in range(args.steps):
+            steps.append(oracle_sample(args.batch))
+        per_inf = float(np.mean([s[1] for s in steps]))
+        val = args.batch / per_inf
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_inf,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": "conv-1 output column 0 (8 channels, 20 top-level key switches) per step, "
+                                           "scaled to one inference by key-switch count"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    res = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        dt, per_inf = oracle_sample(args.batch)
+        cpu = {"value": args.batch / per_inf, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"conv-1 output column 0 (8 channels, 20 top-level key switches) took {dt:.2f} s; "
+                         f"scaled to one inference by key-switch count ({KS_PER_INFERENCE}/20)"}
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": res["launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+            "plain_images_per_s": res["value"] / args.batch, "kernel_breakdown": res["breakdown"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -15,7 +15,7 @@
  *  - Return value: HE_OK (0) or one of the HE_E_* codes below. On error the
  *    outputs are left unset (no partially built handle is returned) and
  *    he_last_error() gives a message for the calling thread.
- *  - Handles (he_ctx, he_ctset, he_ptset, he_server) are created and owned by
+ *  - Handles (he_ctx, he_ctset, he_ptset) are created and owned by
  *    the library; release them with the matching *_free / *_destroy call.
  *    Destroying a context invalidates every handle made from it.
  *  - Pointer arguments without further note are HOST pointers, borrowed for
@@ -83,6 +83,9 @@ typedef struct {
  */
 int he_ctx_create(const he_params_desc* desc, uint64_t seed, void* cuda_stream, he_ctx** out);
 void he_ctx_destroy(he_ctx* ctx);
+
+/* Block until all work enqueued on the context's stream has finished. */
+int he_ctx_synchronize(he_ctx* ctx);
 
 /* The n_q + n_special primes, Q then P, into out[n] (n >= their count). */
 int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n);
@@ -266,6 +269,24 @@ void he_ctset_free(he_ctset* set);
  * smallest quadratic non-residue x of q; inverse undoes it.
  */
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse);
+
+/* ---- instrumentation ---- */
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t he_kernel_launches(void);
+
+/* Per-kernel timing: when on, every launch is bracketed by CUDA events on its
+ * stream. Off by default. */
+int he_profile_enable(int on);
+
+/* Synchronise the recorded events and report, per kernel name, the summed
+ * device time (ms), launch count and algorithmic bytes (each operand of a
+ * launch read or written once) since the last read; clears the record.
+ * names receives the kernel names separated by '\n' (truncated to names_len);
+ * ms, counts and bytes (each may be NULL) receive the first max_kernels
+ * entries; *n_kernels the number of distinct kernels. */
+int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts, double* bytes, int max_kernels,
+                    int* n_kernels);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* he_last_error(void);

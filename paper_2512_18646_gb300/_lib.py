@@ -44,6 +44,7 @@ P_D = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "he_ctx_create": (I, [ctypes.POINTER(ParamsDesc), U64, V, PV]),
     "he_ctx_destroy": (None, [V]),
+    "he_ctx_synchronize": (I, [V]),
     "he_ctx_primes": (I, [V, P_U64, I]),
     "he_ctx_info": (I, [V, P_I, P_I, P_I, P_I, P_D]),
     "he_keygen": (I, [V, P_I32, I]),
@@ -75,6 +76,9 @@ SIGNATURES = {
     "he_ctset_concat": (I, [V, PV, I, PV]),
     "he_ctset_free": (None, [V]),
     "he_ntt": (I, [V, P_U64, I, I, I, I]),
+    "he_kernel_launches": (U64, []),
+    "he_profile_enable": (I, [I]),
+    "he_profile_read": (I, [ctypes.c_char_p, SZ, P_D, P_U64, P_D, I, P_I]),
     "he_last_error": (ctypes.c_char_p, []),
 }
 

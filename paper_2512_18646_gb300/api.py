@@ -114,6 +114,9 @@ class Context:
         return cls(preset.log_n, preset.q_bits, preset.n_special, preset.special_bits, preset.alpha,
                    preset.log_scale, preset.sigma, seed, stream)
 
+    def synchronize(self):
+        check(load().he_ctx_synchronize(self.h))
+
     def close(self):
         if getattr(self, "h", None):
             load().he_ctx_destroy(self.h)

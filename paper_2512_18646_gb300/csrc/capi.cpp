@@ -98,6 +98,13 @@ void he_ctx_destroy(he_ctx* ctx) {
   delete ctx;
 }
 
+int he_ctx_synchronize(he_ctx* ctx) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    HE_CUDA(cudaStreamSynchronize(ctx->c.stream));
+  });
+}
+
 int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n) {
   return guard([&] {
     REQUIRE(ctx && out, HE_E_ARG, "null argument");

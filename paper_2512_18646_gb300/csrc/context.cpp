@@ -508,14 +508,17 @@ void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
 
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale) {
   if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
-  for (size_t idx = 0; idx < (size_t)n * 2 * limbs * C.N; idx++) {
-    const int i = (int)((idx / C.N) % limbs);
-    if (host[idx] >= C.q[i]) throw Error(1, "residue out of range");
-  }
   auto s = new_set(C, n, 2, limbs, scale);
   upload(C, s->buf.p, host, s->buf.words * 8);
-  ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
+  // residues are checked on the device before the transform
+  DevBuf bad(1, C.stream);
+  HE_CUDA(cudaMemsetAsync(bad.p, 0, 8, C.stream));
+  k_check_range(C, s->buf.p, (size_t)n * 2 * limbs, limbs, (unsigned long long*)bad.p);
+  unsigned long long nbad = 0;
+  HE_CUDA(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
+  if (nbad) throw Error(1, std::to_string(nbad) + " residues out of range");
+  ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
   return s;
 }
 

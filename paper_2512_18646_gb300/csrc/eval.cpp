@@ -165,8 +165,8 @@ static DevBuf const_table(Ctx& C, const double* v, int groups, int limbs, double
     for (int i = 0; i < limbs; i++) t[(size_t)g * limbs + i] = residue_of(iv, C.q[i]);
   }
   DevBuf d(t.size(), C.stream);
+  // pageable source: the call returns once the data is staged, so t may go
   HE_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
-  HE_CUDA(cudaStreamSynchronize(C.stream));
   return d;
 }
 
@@ -206,9 +206,7 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
   if (bias) {
     DevBuf cb = const_table(C, bias, c_out, lp - 1, out->scale);
     k_add_const(C, out->buf.p, out->n, lp - 1, cb.p, w_out);
-    HE_CUDA(cudaStreamSynchronize(C.stream));
   }
-  HE_CUDA(cudaStreamSynchronize(C.stream));  // host weight table is freed on return
   return out;
 }
 
@@ -272,7 +270,6 @@ std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out
   if (bias) {
     DevBuf cb = const_table(C, bias, out_dim, z->limbs, z->scale);
     k_add_const(C, z->buf.p, z->n, z->limbs, cb.p, 1);
-    HE_CUDA(cudaStreamSynchronize(C.stream));
   }
   return z;
 }

@@ -116,6 +116,11 @@ struct CtSet {
   u64* ct(int i) const { return buf.p + (size_t)i * ct_words(); }
 };
 
+// ---- launch accounting (profile.cpp): every kernel launch is bracketed ----
+// bytes: the launch's algorithmic traffic (each operand read or written once)
+void* prof_begin(const char* name, cudaStream_t st, double bytes);
+void prof_end(void* tok, cudaStream_t st);
+
 // ---- kernel launchers (kernels.cu / ntt.cu) ----
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
@@ -169,6 +174,8 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj]
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs);
+// number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad
+void k_check_range(const Ctx& C, const u64* x, size_t rows, int limbs, unsigned long long* bad);
 // copy groups x rows_per_group limbs: row r of group g at src + g src_gs + r N
 void k_copy_limbs(const Ctx& C, const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups,
                   int rows_per_group);

@@ -295,6 +295,10 @@ __global__ void k_moddown_combine_kernel(const u64* u, const u64* z, const u64* 
   }
 }
 
+// Rescale by q_l: out_i = (x_i + h - r) q_l^{-1} with h = floor(q_l/2) added to
+// EVERY coefficient and r = (x_l + h) mod q_l. The expansion below forms
+// r - h mod q_i per coefficient (coefficient domain) so that, after its
+// forward NTT, the combine is out_i = (x_i - NTT(r - h)) q_l^{-1}.
 // Rescale constants (words of d_rs): [L1+1][L1][3] = floor(q_l/2) mod q_i, q_l^{-1} mod q_i, Shoup
 __global__ void k_rescale_expand_kernel(const u64* last, u64* r, int rows, int limbs, const u64* rs,
                                         const PrimeTab* pt, int log_n) {
@@ -306,7 +310,8 @@ __global__ void k_rescale_expand_kernel(const u64* last, u64* r, int rows, int l
   HE_GRID_LOOP(idx, total) {
     const size_t jn = idx & (N - 1), row = idx >> log_n;
     const u64 v = addmod(last[idx], half, ml.q);
-    for (int i = 0; i < lo; i++) r[(row * lo + i) * N + jn] = reduce128(0, v, pt[i].mod);
+    for (int i = 0; i < lo; i++)
+      r[(row * lo + i) * N + jn] = submod(reduce128(0, v, pt[i].mod), rs[(size_t)i * 3], pt[i].mod.q);
   }
 }
 
@@ -323,8 +328,7 @@ __global__ void k_rescale_combine_kernel(const u64* x, const u64* r, u64* out, i
     const u64 q = pt[i].mod.q;
     const u64* t = rs + (size_t)i * 3;
     const u64 xi = x[(row * limbs + i) * N + jn];
-    const u64 v = submod(addmod(xi, t[0], q), r[idx], q);
-    out[idx] = shoup(v, t[1], t[2], q);
+    out[idx] = shoup(submod(xi, r[idx], q), t[1], t[2], q);
   }
 }
 
@@ -457,6 +461,19 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
   }
 }
 
+// counts residues >= q_i in [n][limbs][N] rows (limb i of each polynomial)
+__global__ void k_check_range_kernel(const u64* x, size_t rows, int limbs, const PrimeTab* pt, int log_n,
+                                     unsigned long long* bad) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = rows * N;
+  unsigned long long local = 0;
+  HE_GRID_LOOP(idx, total) {
+    const int i = (int)((idx >> log_n) % limbs);
+    local += x[idx] >= pt[i].mod.q;
+  }
+  if (local) atomicAdd(bad, local);
+}
+
 __global__ void k_copy_rows_kernel(const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups, int rpg,
                                    int log_n) {
   const size_t N = (size_t)1 << log_n;
@@ -470,94 +487,101 @@ __global__ void k_copy_rows_kernel(const u64* src, size_t src_gs, u64* dst, size
 
 }  // namespace
 
-#define HE_LAUNCH(kern, total, ...)                                            \
+#define HE_LAUNCH(kern, total, bytes, ...)                                     \
   do {                                                                         \
     const size_t tot_ = (total);                                               \
-    if (tot_) kern<<<grid_for(tot_), kBlock, 0, C.stream>>>(__VA_ARGS__);     \
+    if (tot_) {                                                                \
+      void* tok_ = prof_begin(#kern, C.stream, (double)(bytes));               \
+      kern<<<grid_for(tot_), kBlock, 0, C.stream>>>(__VA_ARGS__);             \
+      prof_end(tok_, C.stream);                                                \
+    }                                                                          \
     HE_CUDA(cudaGetLastError());                                               \
   } while (0)
 
 void k_reduce_signed(const Ctx& C, const int64_t* in, u64* out, int n, const LimbMap& lm) {
-  HE_LAUNCH(k_reduce_signed_kernel, (size_t)n * lm.lpp * C.N, in, out, n, lm, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_reduce_signed_kernel, (size_t)n * lm.lpp * C.N, 8.0 * (double)C.N * n * (1 + lm.lpp), in, out, n, lm, C.dev_ptab(), C.log_n);
 }
 void k_reduce_small(const Ctx& C, const int8_t* in, u64* out, int n, const LimbMap& lm) {
-  HE_LAUNCH(k_reduce_small_kernel, (size_t)n * lm.lpp * C.N, in, out, n, lm, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_reduce_small_kernel, (size_t)n * lm.lpp * C.N, 8.0 * (double)C.N * n * (0.125 + lm.lpp), in, out, n, lm, C.dev_ptab(), C.log_n);
 }
 void k_encrypt_combine(const Ctx& C, const u64* v, const u64* e0, const u64* e1, const u64* m, u64* ct, int n,
                        int limbs) {
-  HE_LAUNCH(k_encrypt_kernel, (size_t)n * limbs * C.N, v, e0, e1, m, C.d_pk.p, ct, n, limbs, C.L1, C.dev_ptab(),
+  HE_LAUNCH(k_encrypt_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * limbs * (6.0 * n + 2), v, e0, e1, m, C.d_pk.p, ct, n, limbs, C.L1, C.dev_ptab(),
             C.log_n);
 }
 void k_ksk_combine(const Ctx& C, const u64* a, const u64* e, const u64* sprime, u64* b, int digit) {
-  HE_LAUNCH(k_ksk_kernel, (size_t)C.np() * C.N, a, e, C.d_s.p, sprime, b, digit, C.alpha, C.L1, C.np(),
+  HE_LAUNCH(k_ksk_kernel, (size_t)C.np() * C.N, 8.0 * (double)C.N * 5 * C.np(), a, e, C.d_s.p, sprime, b, digit, C.alpha, C.L1, C.np(),
             C.dev_ptab(), C.log_n);
 }
 void k_mul(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, const LimbMap& lm) {
-  HE_LAUNCH(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, 8.0 * (double)C.N * 3 * n_polys * lm.lpp, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
 }
 void k_permute(const Ctx& C, const u64* in, u64* out, size_t rows, u64 k) {
-  HE_LAUNCH(k_permute_kernel, rows * C.N, in, out, rows, k, C.log_n);
+  HE_LAUNCH(k_permute_kernel, rows * C.N, 8.0 * (double)C.N * 2 * rows, in, out, rows, k, C.log_n);
 }
 void k_decrypt_limb0(const Ctx& C, const u64* ct, int limbs, int n, u64* out) {
-  HE_LAUNCH(k_decrypt0_kernel, (size_t)n * C.N, ct, C.d_s.p, limbs, n, out, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_decrypt0_kernel, (size_t)n * C.N, 8.0 * (double)C.N * (3.0 * n + 1), ct, C.d_s.p, limbs, n, out, C.dev_ptab(), C.log_n);
 }
 void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int limbs) {
-  HE_LAUNCH(k_add_kernel, (size_t)n_polys * limbs * C.N, a, b, out, n_polys, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_add_kernel, (size_t)n_polys * limbs * C.N, 8.0 * (double)C.N * 3 * n_polys * limbs, a, b, out, n_polys, limbs, C.dev_ptab(), C.log_n);
 }
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs) {
-  HE_LAUNCH(k_tensor_kernel, (size_t)n * limbs * C.N, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_tensor_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 7 * n * limbs, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
 }
 void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs) {
   if (C.alpha > 8) throw Error(8, "digits of more than 8 primes are not supported");
   const u64* up_inv = C.d_up.p;
   const u64* up_hat = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2;
-  HE_LAUNCH(k_modup_kernel, (size_t)n * C.beta_at(limbs) * C.N, x, ext, n, limbs, C.alpha, C.beta_at(limbs), C.L1,
+  HE_LAUNCH(k_modup_kernel, (size_t)n * C.beta_at(limbs) * C.N, 8.0 * (double)C.N * n * (limbs + (double)C.beta_at(limbs) * (limbs + C.K)), x, ext, n, limbs, C.alpha, C.beta_at(limbs), C.L1,
             C.K, up_inv, up_hat, C.dev_ptab(), C.log_n);
 }
 void k_ks_inner(const Ctx& C, const u64* ext, const u64* key, u64* u, int n, int limbs) {
-  HE_LAUNCH(k_ks_inner_kernel, (size_t)n * (limbs + C.K) * C.N, ext, key, u, n, limbs, C.beta_at(limbs), C.L1, C.K,
+  HE_LAUNCH(k_ks_inner_kernel, (size_t)n * (limbs + C.K) * C.N, 8.0 * (double)C.N * (limbs + C.K) * ((double)C.beta_at(limbs) * (n + 2) + 2.0 * n), ext, key, u, n, limbs, C.beta_at(limbs), C.L1, C.K,
             C.dev_ptab(), C.log_n);
 }
 void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k) {
-  HE_LAUNCH(k_gather_p_kernel, (size_t)n * 2 * C.K * C.N, u, p, n, limbs, C.K, k, C.log_n);
+  HE_LAUNCH(k_gather_p_kernel, (size_t)n * 2 * C.K * C.N, 8.0 * (double)C.N * 4 * n * C.K, u, p, n, limbs, C.K, k, C.log_n);
 }
 void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs) {
   if (C.K > 4) throw Error(8, "more than 4 special primes are not supported");
-  HE_LAUNCH(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
+  HE_LAUNCH(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, 8.0 * (double)C.N * 2 * n * (C.K + limbs), p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
             C.log_n);
 }
 void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
                        size_t out_stride, int n, int limbs, u64 k, int mode) {
   const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)C.K * C.L1;
-  HE_LAUNCH(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, u, z, base, base_stride, out, out_stride, n,
+  HE_LAUNCH(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * n * limbs * (mode == 0 ? 8.0 : 7.0), u, z, base, base_stride, out, out_stride, n,
             limbs, C.K, k, mode, Pinv, C.dev_ptab(), C.log_n);
 }
 void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs) {
-  HE_LAUNCH(k_rescale_expand_kernel, (size_t)rows * C.N, last_coeff, r, rows, limbs, C.d_rs.p, C.dev_ptab(),
-            C.log_n);
+  const u64* tab = C.d_rs.p + (size_t)limbs * C.L1 * 3;
+  HE_LAUNCH(k_rescale_expand_kernel, (size_t)rows * C.N, 8.0 * (double)C.N * rows * (double)limbs, last_coeff, r, rows, limbs, tab, C.dev_ptab(), C.log_n);
 }
 void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int rows, int limbs) {
   const u64* tab = C.d_rs.p + (size_t)limbs * C.L1 * 3;
-  HE_LAUNCH(k_rescale_combine_kernel, (size_t)rows * (limbs - 1) * C.N, x, r, out, rows, limbs, tab, C.dev_ptab(),
+  HE_LAUNCH(k_rescale_combine_kernel, (size_t)rows * (limbs - 1) * C.N, 8.0 * (double)C.N * 3.0 * rows * (limbs - 1), x, r, out, rows, limbs, tab, C.dev_ptab(),
             C.log_n);
 }
 void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int per_group) {
-  HE_LAUNCH(k_add_const_kernel, (size_t)n * limbs * C.N, ct, n, limbs, c_dev, per_group, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_add_const_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 2.0 * n * limbs, ct, n, limbs, c_dev, per_group, C.dev_ptab(), C.log_n);
 }
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs) {
-  HE_LAUNCH(k_conv_mac_kernel<8>, (size_t)w_out * 2 * limbs * C.N, rot, out, w, c_in, w_in, k, stride, c_out, w_out,
+  HE_LAUNCH(k_conv_mac_kernel<8>, (size_t)w_out * 2 * limbs * C.N, 8.0 * (double)C.N * 2.0 * limbs * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out), rot, out, w, c_in, w_in, k, stride, c_out, w_out,
             limbs, C.dev_ptab(), C.log_n);
 }
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
-  HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p), A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs) {
-  HE_LAUNCH(k_fc_mac_kernel<10>, (size_t)2 * limbs * C.N, X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH(k_fc_mac_kernel<10>, (size_t)2 * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n_in + (double)out_dim * n_in + 2.0 * out_dim), X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+}
+void k_check_range(const Ctx& C, const u64* x, size_t rows, int limbs, unsigned long long* bad) {
+  HE_LAUNCH(k_check_range_kernel, rows * C.N, 8.0 * (double)C.N * rows, x, rows, limbs, C.dev_ptab(), C.log_n, bad);
 }
 void k_copy_limbs(const Ctx& C, const u64* src, size_t src_gs, u64* dst, size_t dst_gs, size_t groups,
                   int rows_per_group) {
-  HE_LAUNCH(k_copy_rows_kernel, groups * rows_per_group * C.N, src, src_gs, dst, dst_gs, groups, rows_per_group,
+  HE_LAUNCH(k_copy_rows_kernel, groups * rows_per_group * C.N, 8.0 * (double)C.N * 2.0 * groups * rows_per_group, src, src_gs, dst, dst_gs, groups, rows_per_group,
             C.log_n);
 }
 

@@ -209,10 +209,14 @@ void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
+    void* t = prof_begin("k_ntt_fwd_cols", C.stream, 16.0 * rr * (double)C.N);
     k_ntt_fwd_cols<<<dim3(S2 / g.C, rr), kThreads, (size_t)R1 * g.C * 8, C.stream>>>(
         base, lm, C.dev_ptab(), C.d_psi.p, g.n, g.n1, g.C);
+    prof_end(t, C.stream);
+    t = prof_begin("k_ntt_fwd_rows", C.stream, 16.0 * rr * (double)C.N);
     k_ntt_fwd_rows<<<dim3(R1 / g.R, rr), kThreads, (size_t)g.R * S2 * 8, C.stream>>>(
         base, lm, C.dev_ptab(), C.d_psi.p, g.n, g.n1, g.R);
+    prof_end(t, C.stream);
   }
   HE_CUDA(cudaGetLastError());
 }
@@ -226,10 +230,14 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
+    void* t = prof_begin("k_ntt_inv_rows", C.stream, 16.0 * rr * (double)C.N);
     k_ntt_inv_rows<<<dim3(R1 / g.R, rr), kThreads, (size_t)g.R * S2 * 8, C.stream>>>(
         base, lm, C.dev_ptab(), C.d_ipsi.p, g.n, g.n1, g.R);
+    prof_end(t, C.stream);
+    t = prof_begin("k_ntt_inv_cols", C.stream, 16.0 * rr * (double)C.N);
     k_ntt_inv_cols<<<dim3(S2 / g.C, rr), kThreads, (size_t)R1 * g.C * 8, C.stream>>>(
         base, lm, C.dev_ptab(), C.d_ipsi.p, g.n, g.n1, g.C);
+    prof_end(t, C.stream);
   }
   HE_CUDA(cudaGetLastError());
 }
