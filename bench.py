@@ -171,10 +171,12 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
         g.synchronize()
+        torch.cuda.nvtx.range_push("timed_steps")
         e0.record(stream)
         for _ in range(args.steps):
             z = step()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         e1.synchronize()
         g.synchronize()
         torch.cuda.synchronize()

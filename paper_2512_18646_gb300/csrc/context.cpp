@@ -198,10 +198,10 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
       pw[0] = 1;
       for (size_t e = 1; e < C.N; e++) pw[e] = mul_h(pw[e - 1], r, q);
       u64* tab = (dir ? ipsi_tab.data() : psi_tab.data()) + (size_t)g * 2 * C.N;
-      for (size_t k = 0; k < C.N; k++) {
+      for (size_t k = 0; k < C.N; k++) {  // interleaved (w, w') pairs for 16-byte loads
         const u64 w = pw[brv_h((u32)k, log_n)];
-        tab[k] = w;
-        tab[C.N + k] = shoup_of(w, q);
+        tab[2 * k] = w;
+        tab[2 * k + 1] = shoup_of(w, q);
       }
     }
   }

@@ -87,8 +87,8 @@ struct Ctx {
 
   // device tables
   DevBuf d_ptab;              // PrimeTab[np] (as words)
-  DevBuf d_psi;               // [np][2][N]: psi^{brv(k)} and Shoup companions
-  DevBuf d_ipsi;              // [np][2][N]: psi^{-brv(k)} and companions
+  DevBuf d_psi;               // [np][N][2]: psi^{brv(k)} and its Shoup companion
+  DevBuf d_ipsi;              // [np][N][2]: psi^{-brv(k)} and its companion
   DevBuf d_up;                // ModUp constants, see modup_table()
   DevBuf d_down;              // ModDown constants
   DevBuf d_rs;                // rescale constants [L1][L1][3]

@@ -4,196 +4,403 @@
 // primitive 2N-th root; the evaluations of a(X) at the odd powers of psi in
 // bit-reversed order, so that a negacyclic product is a pointwise product.
 // Forward: Cooley-Tukey butterflies with psi merged into the twiddles
-// (psi^{brv(m + i)} at stage m, group i); inverse: Gentleman-Sande with
-// psi^{-brv(m + i)} and a final multiply by N^{-1}. Arithmetic: Shoup twiddle
+// (stage with m groups, group i: psi^{brv(m + i)}); inverse: Gentleman-Sande
+// with psi^{-brv(m + i)}, then a multiply by N^{-1}. Arithmetic: Shoup twiddle
 // products and Harvey's lazy ranges ([0, 4q) forward, [0, 2q) inverse).
 //
-// GPU decomposition, N = 2^n = 2^{n1} x 2^{n2}: write j = hi 2^{n2} + lo.
-// The first n1 forward stages pair indices that differ only in `hi`, so for a
-// fixed `lo` they form an independent 2^{n1}-point problem: kernel A loads a
-// tile of C adjacent `lo` columns (2^{n1} x C words, coalesced rows of C words)
-// into shared memory and runs those stages there. The last n2 stages pair
-// indices inside one run of 2^{n2} consecutive words: kernel B loads whole
-// runs. The inverse runs the same kernels in the opposite order. Each launch
-// covers every limb of a batch (grid.y = limb rows), so one launch transforms
-// all limbs of many polynomials.
+// Decomposition, N = 2^n = 2^{n1} x 2^{n2}, index j = hi 2^{n2} + lo: the first
+// n1 forward stages change only `hi` (independent 2^{n1}-point transforms per
+// column `lo`), the last n2 only `lo` (2^{n2}-point transforms per run of
+// consecutive words). Kernel "cols" takes a tile of C adjacent columns, kernel
+// "rows" whole runs; the inverse runs them in the opposite order. grid.y is
+// the limb (row of N words), so one launch covers every limb of a batch.
+//
+// Inside a sub-transform of M = 2^m points each thread holds 8 elements in
+// registers and runs up to three butterfly stages per round before
+// exchanging through shared memory. In round r (stages 3r .. 3r+2, from the
+// largest distance down) element k of thread u is the index with k's bits at
+// the round's distance bit positions (plus, in a short last round, the top
+// positions not in the round) and u's bits in the remaining positions in
+// order. All index arithmetic is compile-time shifts and masks. The row
+// kernel keeps each sub-transform inside one warp; its shared memory is
+// swizzled, word x at x ^ g(x >> 4) for a GF(2)-linear g, which makes every
+// round's 64-bit accesses conflict-free for all M <= 256.
 #include "he_internal.h"
 
 namespace he {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTileWords = 4096;  // 32 KiB of shared memory per block
-
-struct NttGeom {
-  int n, n1, n2, C, R;  // C columns per kernel-A tile, R runs per kernel-B tile
+// ---------------------------------------------------------------------------
+// compile-time round maps
+// ---------------------------------------------------------------------------
+template <int LOGM, int RND>
+struct RMap {
+  static constexpr int KB = LOGM < 3 ? LOGM : 3;  // k bits (elements per thread = 2^KB)
+  static constexpr int E = 1 << KB;
+  static constexpr int S0 = 3 * RND;
+  static constexpr int NS = (LOGM - S0) < 3 ? (LOGM - S0) : 3;  // stages in this round
+  static constexpr int LO = LOGM - S0 - NS;                     // lowest distance bit of the round
+  // bit position of k bit i
+  __host__ __device__ static constexpr int kpos(int i) {
+    if (i < NS) return LO + i;
+    int c = i - NS;
+    for (int p = LOGM - 1; p >= 0; p--) {
+      if (p >= LO && p < LO + NS) continue;
+      if (c == 0) return p;
+      c--;
+    }
+    return 0;
+  }
+  // i-th smallest k position
+  __host__ __device__ static constexpr int sorted_kpos(int i) {
+    int v[3] = {kpos(0), KB > 1 ? kpos(1) : 99, KB > 2 ? kpos(2) : 99};
+    for (int a = 0; a < 3; a++)
+      for (int b = a + 1; b < 3; b++)
+        if (v[b] < v[a]) { const int t = v[a]; v[a] = v[b]; v[b] = t; }
+    return v[i];
+  }
+  // u with zero bits inserted at the k positions
+  __device__ static __forceinline__ int upart(int u) {
+    int x = u;
+#pragma unroll
+    for (int i = 0; i < KB; i++) {
+      const int p = sorted_kpos(i);
+      x = ((x >> p) << (p + 1)) | (x & ((1 << p) - 1));
+    }
+    return x;
+  }
+  __host__ __device__ static constexpr int kbits(int k) {
+    int x = 0;
+    for (int i = 0; i < KB; i++) x |= ((k >> i) & 1) << kpos(i);
+    return x;
+  }
 };
 
-NttGeom geom(int log_n) {
-  NttGeom g;
-  g.n = log_n;
-  g.n1 = log_n / 2;
-  g.n2 = log_n - g.n1;
-  const int S2 = 1 << g.n2, R1 = 1 << g.n1;
-  g.C = S2 < 16 ? S2 : 16;
-  int r = kTileWords / S2;
-  if (r < 1) r = 1;
-  if (r > R1) r = R1;
-  g.R = r;
-  return g;
+template <int LOGM>
+struct Plan {
+  static constexpr int KB = LOGM < 3 ? LOGM : 3;
+  static constexpr int E = 1 << KB;
+  static constexpr int T = (1 << LOGM) / E;  // threads per sub-transform
+  static constexpr int R = (LOGM + 2) / 3;   // rounds
+};
+
+__device__ __forceinline__ ulonglong2 tw_load(const u64* tw, u64 idx) {
+  return __ldg(reinterpret_cast<const ulonglong2*>(tw) + idx);
+}
+
+// One forward round: stages S0 .. S0+NS-1 of an M-point sub-transform.
+// Twiddle of the butterfly whose lower element is e at local stage s:
+//   table[(1 << (soff + s)) + (run << s) + (e >> (LOGM - s))].
+template <int LOGM, int RND>
+__device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
+                                          u64 q) {
+  using M = RMap<LOGM, RND>;
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int st = 0; st < M::NS; st++) {
+    const int s = M::S0 + st;
+    const int ib = M::NS - 1 - st;  // k bit of this stage's distance
+    const u64 base = ((u64)1 << (soff + s)) + (run << s);
+#pragma unroll
+    for (int hi = 0; hi < (M::E >> (ib + 1)); hi++) {
+      const int kb = hi << (ib + 1);
+      const int e = xu | M::kbits(kb);
+      const ulonglong2 w = tw_load(tw, base + (u64)(e >> (LOGM - s)));
+#pragma unroll
+      for (int lo = 0; lo < (1 << ib); lo++) {
+        const int k = kb | lo, k2 = k | (1 << ib);
+        u64 X = a[k];
+        if (X >= q2) X -= q2;
+        const u64 T = shoup_lazy(a[k2], w.x, w.y, q);
+        a[k] = X + T;
+        a[k2] = X - T + q2;
+      }
+    }
+  }
+}
+
+// One inverse round (Gentleman-Sande), stages in the opposite order.
+template <int LOGM, int RND>
+__device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
+                                          u64 q) {
+  using M = RMap<LOGM, RND>;
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int st = M::NS - 1; st >= 0; st--) {
+    const int s = M::S0 + st;
+    const int ib = M::NS - 1 - st;
+    const u64 base = ((u64)1 << (soff + s)) + (run << s);
+#pragma unroll
+    for (int hi = 0; hi < (M::E >> (ib + 1)); hi++) {
+      const int kb = hi << (ib + 1);
+      const int e = xu | M::kbits(kb);
+      const ulonglong2 w = tw_load(tw, base + (u64)(e >> (LOGM - s)));
+#pragma unroll
+      for (int lo = 0; lo < (1 << ib); lo++) {
+        const int k = kb | lo, k2 = k | (1 << ib);
+        const u64 X = a[k], Y = a[k2];
+        u64 S = X + Y;
+        if (S >= q2) S -= q2;
+        a[k] = S;
+        a[k2] = shoup_lazy(X - Y + q2, w.x, w.y, q);
+      }
+    }
+  }
+}
+
+// Rounds RND .. R-1 (forward) with exchanges through shared memory; `addr`
+// maps an element index to its shared-memory word.
+template <int LOGM, int RND, class Sync, class Addr>
+__device__ __forceinline__ void rounds_fwd_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
+                                                const u64* tw, int soff, u64 run, u64 q) {
+  if constexpr (RND < Plan<LOGM>::R) {
+    using Mp = RMap<LOGM, RND - 1>;
+    using Mc = RMap<LOGM, RND>;
+    const int xp = Mp::upart(u);
+#pragma unroll
+    for (int k = 0; k < Plan<LOGM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
+    sync();
+    const int xc = Mc::upart(u);
+#pragma unroll
+    for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
+    sync();
+    round_fwd<LOGM, RND>(a, xc, tw, soff, run, q);
+    rounds_fwd_rest<LOGM, RND + 1>(a, u, sm, addr, sync, tw, soff, run, q);
+  }
+}
+
+template <int LOGM, int RND, class Sync, class Addr>
+__device__ __forceinline__ void rounds_inv_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
+                                                const u64* tw, int soff, u64 run, u64 q) {
+  if constexpr (RND >= 0) {
+    using Mp = RMap<LOGM, RND + 1>;
+    using Mc = RMap<LOGM, RND>;
+    const int xp = Mp::upart(u);
+#pragma unroll
+    for (int k = 0; k < Plan<LOGM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
+    sync();
+    const int xc = Mc::upart(u);
+#pragma unroll
+    for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
+    sync();
+    round_inv<LOGM, RND>(a, xc, tw, soff, run, q);
+    rounds_inv_rest<LOGM, RND - 1>(a, u, sm, addr, sync, tw, soff, run, q);
+  }
+}
+
+__device__ __forceinline__ int swz(int x) {
+  // x ^ g(x >> 4), g GF(2)-linear with columns (3, 5, 10, 0) on bits 4..7
+  const int y = x >> 4;
+  const int g = ((y & 1) ? 3 : 0) ^ ((y & 2) ? 5 : 0) ^ ((y & 4) ? 10 : 0);
+  return x ^ g;
 }
 
 __device__ __forceinline__ u64* row_ptr(u64* base, const LimbMap& lm, int row, size_t N, int& prime) {
-  const int p = row / lm.lpp, i = row % lm.lpp;
+  const int p = row / lm.lpp, i = row - p * lm.lpp;
   prime = lm.prime(i);
   return base + (size_t)p * lm.poly_stride + (size_t)i * N;
 }
 
-// Forward, first n1 stages (large butterfly distances), columns lo0 .. lo0+C-1.
-__global__ void __launch_bounds__(kThreads) k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                           const u64* psi_all, int n, int n1, int C) {
-  extern __shared__ u64 sm[];
+constexpr int kRowThreads = 256;
+
+// ---------------------------------------------------------------------------
+// rows: last n2 forward stages (sub-size M = 2^LOGM = 2^{n2}), warp-contained
+// ---------------------------------------------------------------------------
+template <int LOGM>
+__global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
+                                                              const u64* tw_all, int n, int n1) {
+  using P = Plan<LOGM>;
+  constexpr int M = 1 << LOGM;
+  constexpr int RUNS = kRowThreads / P::T;
+  __shared__ u64 sm[kRowThreads * P::E];
   const size_t N = (size_t)1 << n;
-  const int n2 = n - n1, R1 = 1 << n1;
-  const size_t stride = (size_t)1 << n2;
   int prime;
   u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q, q2 = 2 * q;
-  const u64* W = psi_all + (size_t)prime * 2 * N;
-  const u64* Wp = W + N;
-  const int lo0 = blockIdx.x * C;
-  for (int e = threadIdx.x; e < R1 * C; e += blockDim.x) {
-    const int hi = e / C, c = e - hi * C;
-    sm[e] = x[hi * stride + lo0 + c];
+  const u64 q = pt[prime].mod.q;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
+  const u64 run = (u64)blockIdx.x * RUNS + r_cta;
+  if (run >= ((u64)1 << n1)) return;  // whole runs only, so a warp's active lanes hold whole runs
+  u64* xr = x + run * M;
+  // shared memory of this thread's warp, runs of the warp side by side
+  const int warp = threadIdx.x >> 5;
+  const int rw = (threadIdx.x & 31) / P::T;  // run index inside the warp
+  u64* smw = sm + warp * 32 * P::E;
+  auto addr = [rw](int e) { return swz(rw * M + e); };
+  auto sync = [] { __syncwarp(__activemask()); };
+  u64 a[P::E];
+  {
+    using M0 = RMap<LOGM, 0>;
+    const int x0 = M0::upart(u);
+#pragma unroll
+    for (int k = 0; k < P::E; k++) a[k] = xr[x0 | M0::kbits(k)];
+    round_fwd<LOGM, 0>(a, x0, tw, n1, run, q);
   }
-  __syncthreads();
-  for (int s = 0; s < n1; s++) {
-    const int m = 1 << s, th = R1 >> (s + 1);
-    for (int bf = threadIdx.x; bf < (R1 / 2) * C; bf += blockDim.x) {
-      const int k = bf / C, c = bf - k * C;
-      const int grp = k / th, pos = k - grp * th;
-      const int hi = grp * 2 * th + pos;
-      const u64 w = W[m + grp], wp = Wp[m + grp];
-      u64 X = sm[hi * C + c];
-      const u64 Y = sm[(hi + th) * C + c];
-      if (X >= q2) X -= q2;
-      const u64 T = shoup_lazy(Y, w, wp, q);
-      sm[hi * C + c] = X + T;
-      sm[(hi + th) * C + c] = X - T + q2;
-    }
-    __syncthreads();
+  rounds_fwd_rest<LOGM, 1>(a, u, smw, addr, sync, tw, n1, run, q);
+  using ML = RMap<LOGM, P::R - 1>;
+  const int xl = ML::upart(u);
+#pragma unroll
+  for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = reduce4q(a[k], q);
+}
+
+// inverse, first n2 stages (smallest distances) inside runs; output in [0, 2q)
+template <int LOGM>
+__global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
+                                                              const u64* tw_all, int n, int n1) {
+  using P = Plan<LOGM>;
+  constexpr int M = 1 << LOGM;
+  constexpr int RUNS = kRowThreads / P::T;
+  __shared__ u64 sm[kRowThreads * P::E];
+  const size_t N = (size_t)1 << n;
+  int prime;
+  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
+  const u64 q = pt[prime].mod.q;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
+  const u64 run = (u64)blockIdx.x * RUNS + r_cta;
+  if (run >= ((u64)1 << n1)) return;
+  u64* xr = x + run * M;
+  const int warp = threadIdx.x >> 5;
+  const int rw = (threadIdx.x & 31) / P::T;
+  u64* smw = sm + warp * 32 * P::E;
+  auto addr = [rw](int e) { return swz(rw * M + e); };
+  auto sync = [] { __syncwarp(__activemask()); };
+  u64 a[P::E];
+  {
+    using ML = RMap<LOGM, P::R - 1>;
+    const int xl = ML::upart(u);
+#pragma unroll
+    for (int k = 0; k < P::E; k++) a[k] = xr[xl | ML::kbits(k)];
+    round_inv<LOGM, P::R - 1>(a, xl, tw, n1, run, q);
   }
-  for (int e = threadIdx.x; e < R1 * C; e += blockDim.x) {
-    const int hi = e / C, c = e - hi * C;
-    x[hi * stride + lo0 + c] = sm[e];
+  rounds_inv_rest<LOGM, P::R - 2>(a, u, smw, addr, sync, tw, n1, run, q);
+  using M0 = RMap<LOGM, 0>;
+  const int x0 = M0::upart(u);
+#pragma unroll
+  for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = a[k];
+}
+
+// ---------------------------------------------------------------------------
+// cols: first n1 forward stages (sub-size 2^LOGM = 2^{n1}) on C adjacent columns
+// ---------------------------------------------------------------------------
+template <int LOGM>
+__global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C) {
+  using P = Plan<LOGM>;
+  extern __shared__ u64 smc[];
+  const size_t N = (size_t)1 << n;
+  const size_t stride = N >> LOGM;
+  int prime;
+  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
+  const u64 q = pt[prime].mod.q;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int u = threadIdx.x / C, lo = threadIdx.x - u * C;
+  u64* xc = x + (size_t)blockIdx.x * C + lo;
+  auto addr = [C, lo](int e) { return e * C + lo; };
+  auto sync = [] { __syncthreads(); };
+  u64 a[P::E];
+  {
+    using M0 = RMap<LOGM, 0>;
+    const int x0 = M0::upart(u);
+#pragma unroll
+    for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(x0 | M0::kbits(k)) * stride];
+    round_fwd<LOGM, 0>(a, x0, tw, 0, 0, q);
+  }
+  rounds_fwd_rest<LOGM, 1>(a, u, smc, addr, sync, tw, 0, 0, q);
+  using ML = RMap<LOGM, P::R - 1>;
+  const int xl = ML::upart(u);
+#pragma unroll
+  for (int k = 0; k < P::E; k++) xc[(size_t)(xl | ML::kbits(k)) * stride] = a[k];  // [0, 4q)
+}
+
+// inverse, last n1 stages (largest distances) on columns, then times N^{-1}; output in [0, q)
+template <int LOGM>
+__global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C) {
+  using P = Plan<LOGM>;
+  extern __shared__ u64 smc[];
+  const size_t N = (size_t)1 << n;
+  const size_t stride = N >> LOGM;
+  int prime;
+  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
+  const PrimeTab PT = pt[prime];
+  const u64 q = PT.mod.q;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int u = threadIdx.x / C, lo = threadIdx.x - u * C;
+  u64* xc = x + (size_t)blockIdx.x * C + lo;
+  auto addr = [C, lo](int e) { return e * C + lo; };
+  auto sync = [] { __syncthreads(); };
+  u64 a[P::E];
+  {
+    using ML = RMap<LOGM, P::R - 1>;
+    const int xl = ML::upart(u);
+#pragma unroll
+    for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(xl | ML::kbits(k)) * stride];
+    round_inv<LOGM, P::R - 1>(a, xl, tw, 0, 0, q);
+  }
+  rounds_inv_rest<LOGM, P::R - 2>(a, u, smc, addr, sync, tw, 0, 0, q);
+  using M0 = RMap<LOGM, 0>;
+  const int x0 = M0::upart(u);
+#pragma unroll
+  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], PT.ninv, PT.ninv_sh, q);
+}
+
+struct Geom {
+  int n1, n2, C;
+};
+Geom geom(int log_n) {
+  Geom g;
+  g.n1 = log_n / 2;
+  g.n2 = log_n - g.n1;
+  const int S2 = 1 << g.n2;
+  g.C = S2 < 16 ? S2 : 16;
+  return g;
+}
+
+template <int L>
+void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n1, const u64* tw) {
+  constexpr int RUNS = kRowThreads / Plan<L>::T;
+  const int runs = 1 << n1;
+  const dim3 grid((runs + RUNS - 1) / RUNS, rows);
+  void* t = prof_begin(inv ? "k_ntt_inv_rows" : "k_ntt_fwd_rows", C.stream, 16.0 * rows * (double)C.N);
+  if (inv) k_ntt_inv_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
+  else k_ntt_fwd_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
+  prof_end(t, C.stream);
+}
+
+template <int L>
+void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n2, int Ccols, const u64* tw) {
+  const int threads = Ccols * Plan<L>::T;
+  const size_t smem = (size_t)(1 << L) * Ccols * 8;
+  const dim3 grid((1 << n2) / Ccols, rows);
+  void* t = prof_begin(inv ? "k_ntt_inv_cols" : "k_ntt_fwd_cols", C.stream, 16.0 * rows * (double)C.N);
+  if (inv) k_ntt_inv_cols<L><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols);
+  else k_ntt_fwd_cols<L><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols);
+  prof_end(t, C.stream);
+}
+
+void rows_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw) {
+  switch (g.n2) {
+    case 2: launch_rows<2>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 3: launch_rows<3>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 4: launch_rows<4>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 5: launch_rows<5>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 6: launch_rows<6>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 7: launch_rows<7>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 8: launch_rows<8>(inv, base, lm, rows, C, g.n1, tw); break;
+    default: throw Error(1, "unsupported ring degree");
   }
 }
 
-// Forward, last n2 stages (distances < 2^{n2}), runs seg0 .. seg0+R-1; output in [0, q).
-__global__ void __launch_bounds__(kThreads) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                           const u64* psi_all, int n, int n1, int R) {
-  extern __shared__ u64 sm[];
-  const size_t N = (size_t)1 << n;
-  const int n2 = n - n1, S2 = 1 << n2;
-  int prime;
-  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q, q2 = 2 * q;
-  const u64* W = psi_all + (size_t)prime * 2 * N;
-  const u64* Wp = W + N;
-  const size_t base = (size_t)blockIdx.x * R * S2;
-  for (int e = threadIdx.x; e < R * S2; e += blockDim.x) sm[e] = x[base + e];
-  __syncthreads();
-  for (int s = n1; s < n; s++) {
-    const int m = 1 << s, t = (int)(N >> (s + 1));
-    for (int bf = threadIdx.x; bf < R * (S2 / 2); bf += blockDim.x) {
-      const int seg = bf / (S2 / 2), k = bf - seg * (S2 / 2);
-      const int g = k / t, pos = k - g * t;
-      const int l = seg * S2 + g * 2 * t + pos;
-      const size_t i = (base + (size_t)l) / (2 * (size_t)t);
-      const u64 w = W[m + i], wp = Wp[m + i];
-      u64 X = sm[l];
-      const u64 Y = sm[l + t];
-      if (X >= q2) X -= q2;
-      const u64 T = shoup_lazy(Y, w, wp, q);
-      sm[l] = X + T;
-      sm[l + t] = X - T + q2;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < R * S2; e += blockDim.x) x[base + e] = reduce4q(sm[e], q);
-}
-
-// Inverse, first n2 stages (distances 1 .. 2^{n2-1}) inside runs; output in [0, 2q).
-__global__ void __launch_bounds__(kThreads) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                           const u64* ipsi_all, int n, int n1, int R) {
-  extern __shared__ u64 sm[];
-  const size_t N = (size_t)1 << n;
-  const int n2 = n - n1, S2 = 1 << n2;
-  int prime;
-  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q, q2 = 2 * q;
-  const u64* W = ipsi_all + (size_t)prime * 2 * N;
-  const u64* Wp = W + N;
-  const size_t base = (size_t)blockIdx.x * R * S2;
-  for (int e = threadIdx.x; e < R * S2; e += blockDim.x) sm[e] = x[base + e];
-  __syncthreads();
-  for (int t = 1; t < S2; t <<= 1) {
-    const size_t m = N / (2 * (size_t)t);
-    for (int bf = threadIdx.x; bf < R * (S2 / 2); bf += blockDim.x) {
-      const int seg = bf / (S2 / 2), k = bf - seg * (S2 / 2);
-      const int g = k / t, pos = k - g * t;
-      const int l = seg * S2 + g * 2 * t + pos;
-      const size_t i = (base + (size_t)l) / (2 * (size_t)t);
-      const u64 w = W[m + i], wp = Wp[m + i];
-      const u64 X = sm[l], Y = sm[l + t];
-      u64 S = X + Y;
-      if (S >= q2) S -= q2;
-      sm[l] = S;
-      sm[l + t] = shoup_lazy(X - Y + q2, w, wp, q);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < R * S2; e += blockDim.x) x[base + e] = sm[e];
-}
-
-// Inverse, last n1 stages (distances >= 2^{n2}) on columns, then times N^{-1}; output in [0, q).
-__global__ void __launch_bounds__(kThreads) k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                           const u64* ipsi_all, int n, int n1, int C) {
-  extern __shared__ u64 sm[];
-  const size_t N = (size_t)1 << n;
-  const int n2 = n - n1, R1 = 1 << n1;
-  const size_t stride = (size_t)1 << n2;
-  int prime;
-  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const PrimeTab P = pt[prime];
-  const u64 q = P.mod.q, q2 = 2 * q;
-  const u64* W = ipsi_all + (size_t)prime * 2 * N;
-  const u64* Wp = W + N;
-  const int lo0 = blockIdx.x * C;
-  for (int e = threadIdx.x; e < R1 * C; e += blockDim.x) {
-    const int hi = e / C, c = e - hi * C;
-    sm[e] = x[hi * stride + lo0 + c];
-  }
-  __syncthreads();
-  for (int th = 1; th < R1; th <<= 1) {
-    const int m = R1 / (2 * th);
-    for (int bf = threadIdx.x; bf < (R1 / 2) * C; bf += blockDim.x) {
-      const int k = bf / C, c = bf - k * C;
-      const int grp = k / th, pos = k - grp * th;
-      const int hi = grp * 2 * th + pos;
-      const u64 w = W[m + grp], wp = Wp[m + grp];
-      const u64 X = sm[hi * C + c], Y = sm[(hi + th) * C + c];
-      u64 S = X + Y;
-      if (S >= q2) S -= q2;
-      sm[hi * C + c] = S;
-      sm[(hi + th) * C + c] = shoup_lazy(X - Y + q2, w, wp, q);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < R1 * C; e += blockDim.x) {
-    const int hi = e / C, c = e - hi * C;
-    x[hi * stride + lo0 + c] = shoup(sm[e], P.ninv, P.ninv_sh, q);
+void cols_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw) {
+  switch (g.n1) {
+    case 2: launch_cols<2>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 3: launch_cols<3>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 4: launch_cols<4>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 5: launch_cols<5>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 6: launch_cols<6>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 7: launch_cols<7>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 8: launch_cols<8>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    default: throw Error(1, "unsupported ring degree");
   }
 }
 
@@ -202,21 +409,14 @@ __global__ void __launch_bounds__(kThreads) k_ntt_inv_cols(u64* data, LimbMap lm
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   const int rows = n_polys * lm.lpp;
   if (rows == 0) return;
-  const NttGeom g = geom(C.log_n);
-  const int S2 = 1 << g.n2, R1 = 1 << g.n1;
+  const Geom g = geom(C.log_n);
   // grid.y holds at most 65535 rows; chunks end on polynomial boundaries
   const int step = (65535 / lm.lpp) * lm.lpp;
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
-    void* t = prof_begin("k_ntt_fwd_cols", C.stream, 16.0 * rr * (double)C.N);
-    k_ntt_fwd_cols<<<dim3(S2 / g.C, rr), kThreads, (size_t)R1 * g.C * 8, C.stream>>>(
-        base, lm, C.dev_ptab(), C.d_psi.p, g.n, g.n1, g.C);
-    prof_end(t, C.stream);
-    t = prof_begin("k_ntt_fwd_rows", C.stream, 16.0 * rr * (double)C.N);
-    k_ntt_fwd_rows<<<dim3(R1 / g.R, rr), kThreads, (size_t)g.R * S2 * 8, C.stream>>>(
-        base, lm, C.dev_ptab(), C.d_psi.p, g.n, g.n1, g.R);
-    prof_end(t, C.stream);
+    cols_dispatch(false, base, lm, rr, C, g, C.d_psi.p);
+    rows_dispatch(false, base, lm, rr, C, g, C.d_psi.p);
   }
   HE_CUDA(cudaGetLastError());
 }
@@ -224,20 +424,13 @@ void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   const int rows = n_polys * lm.lpp;
   if (rows == 0) return;
-  const NttGeom g = geom(C.log_n);
-  const int S2 = 1 << g.n2, R1 = 1 << g.n1;
+  const Geom g = geom(C.log_n);
   const int step = (65535 / lm.lpp) * lm.lpp;
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
-    void* t = prof_begin("k_ntt_inv_rows", C.stream, 16.0 * rr * (double)C.N);
-    k_ntt_inv_rows<<<dim3(R1 / g.R, rr), kThreads, (size_t)g.R * S2 * 8, C.stream>>>(
-        base, lm, C.dev_ptab(), C.d_ipsi.p, g.n, g.n1, g.R);
-    prof_end(t, C.stream);
-    t = prof_begin("k_ntt_inv_cols", C.stream, 16.0 * rr * (double)C.N);
-    k_ntt_inv_cols<<<dim3(S2 / g.C, rr), kThreads, (size_t)R1 * g.C * 8, C.stream>>>(
-        base, lm, C.dev_ptab(), C.d_ipsi.p, g.n, g.n1, g.C);
-    prof_end(t, C.stream);
+    rows_dispatch(true, base, lm, rr, C, g, C.d_ipsi.p);
+    cols_dispatch(true, base, lm, rr, C, g, C.d_ipsi.p);
   }
   HE_CUDA(cudaGetLastError());
 }

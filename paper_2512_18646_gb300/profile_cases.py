@@ -1,0 +1,62 @@
+"""Small cases of the hot kernels, sized for profiler captures.
+
+`python -m paper_2512_18646_gb300.profile_cases <case>` runs one case on
+cuda:0 through the library. The cases use the CNN parameter set (N = 2^16,
+Q = 60 + 12 x 45, P = 2 x 60, digits of two primes) on a narrow image slab, so
+every launch has the shape of the full workload's launches per limb while the
+device holds a few GB at most and each launch's data exceeds L2:
+
+  conv1   16 image columns (16 ciphertexts of 128 pixels, 256 images):
+          hoisted rotations by 1..4 (ModUp NTTs over 16 x 7 x 15 limbs,
+          key inner products, ModDown) then the 8-channel 5x5 stride-2 MAC
+          and rescale.
+  square  the x^2 activation (tensor, relinearisation, rescale) of 64
+          ciphertexts at the top level (13 limbs).
+
+The case body (after key generation and encryption) runs inside the NVTX
+range "case", so a capture can be limited to it (ncu --nvtx --nvtx-include
+"case/").
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["conv1", "square"])
+    ap.add_argument("--repeat", type=int, default=2)
+    args = ap.parse_args()
+    from inputs import synthetic
+    from paper_2512_18646_gb300 import api, load
+    from paper_2512_18646_gb300._build import build
+    build()
+    load()
+    pre = synthetic.CNN_N16
+    g = api.Context.from_preset(pre, seed=5)
+    g.keygen([1, 2, 3, 4])
+    w = synthetic.cnn_weights(128, seed=302)
+    import torch
+    imgs = synthetic.images(256, 128, 16 if args.case == "conv1" else 64, seed=301)
+    x = g.encrypt_image(imgs, 128)
+    g.synchronize()
+    torch.cuda.nvtx.range_push("case")
+    for _ in range(args.repeat):
+        if args.case == "conv1":
+            y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
+        else:
+            y = g.mul(x, x)
+        del y
+    g.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(f"profile case {args.case} done")
+
+
+if __name__ == "__main__":
+    main()
