@@ -214,7 +214,7 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
 
   // ModUp tables per level: digit j covers primes [j alpha, min((j+1) alpha, limbs))
   const int L1 = C.L1, K = C.K;
-  std::vector<u64> up((size_t)(L1 + 1) * L1 * 2 + (size_t)(L1 + 1) * L1 * (L1 + K), 0);
+  std::vector<u64> up((size_t)(L1 + 1) * L1 * 2 + (size_t)(L1 + 1) * L1 * (L1 + K) * 2, 0);
   u64* up_inv = up.data();
   u64* up_hat = up.data() + (size_t)(L1 + 1) * L1 * 2;
   for (int limbs = 1; limbs <= L1; limbs++) {
@@ -231,15 +231,18 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
         u64 ht = 1;
         for (int i2 = lo; i2 < hi; i2++)
           if (i2 != i) ht = mul_h(ht, C.q[i2] % t, t);
-        up_hat[((size_t)limbs * L1 + i) * (L1 + K) + pos] = ht;
+        u64* h = up_hat + (((size_t)limbs * L1 + i) * (L1 + K) + pos) * 2;
+        h[0] = ht;
+        h[1] = shoup_of(ht, t);
       }
     }
   }
   C.d_up = DevBuf(up.size(), st);
   upload(C, C.d_up.p, up.data(), up.size() * 8);
 
-  // ModDown tables: (P/p_k)^{-1} mod p_k, (P/p_k) mod q_i, P^{-1} mod q_i
-  std::vector<u64> down((size_t)2 * K + (size_t)K * L1 + (size_t)2 * L1);
+  // ModDown tables: (P/p_k)^{-1} mod p_k, (P/p_k) mod q_i, P^{-1} mod q_i, each with its
+  // Shoup companion
+  std::vector<u64> down((size_t)2 * K + (size_t)2 * K * L1 + (size_t)2 * L1);
   for (int k = 0; k < K; k++) {
     const u64 pk = P[k];
     u64 h = 1;
@@ -252,13 +255,14 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
       u64 hq = 1;
       for (int k2 = 0; k2 < K; k2++)
         if (k2 != k) hq = mul_h(hq, P[k2] % C.q[i], C.q[i]);
-      down[2 * K + (size_t)k * L1 + i] = hq;
+      down[2 * K + ((size_t)k * L1 + i) * 2] = hq;
+      down[2 * K + ((size_t)k * L1 + i) * 2 + 1] = shoup_of(hq, C.q[i]);
     }
   }
   for (int i = 0; i < L1; i++) {
     const u64 pinv = inv_h(C.ptab[i].pmod, C.q[i]);
-    down[2 * K + (size_t)K * L1 + 2 * i] = pinv;
-    down[2 * K + (size_t)K * L1 + 2 * i + 1] = shoup_of(pinv, C.q[i]);
+    down[2 * K + (size_t)2 * K * L1 + 2 * i] = pinv;
+    down[2 * K + (size_t)2 * K * L1 + 2 * i + 1] = shoup_of(pinv, C.q[i]);
   }
   C.d_down = DevBuf(down.size(), st);
   upload(C, C.d_down.p, down.data(), down.size() * 8);

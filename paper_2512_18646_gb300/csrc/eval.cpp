@@ -59,26 +59,43 @@ static DevBuf modup_poly(Ctx& C, const CtSet& in, int poly) {
 
 DevBuf modup_c1(Ctx& C, const CtSet& in) { return modup_poly(C, in, 1); }
 
-// Inner product with the key of Galois element k and ModDown. mode 0: add the
-// set's first two components (relinearisation of d2); mode 1: add phi_k(c0).
-static void ks_finish(Ctx& C, const CtSet& in, const DevBuf& ext, u64 k, int mode, u64* out, size_t out_stride) {
-  const int n = in.n, lp = in.limbs, nb = lp + C.K;
+// Inner products of the ModUp digits `ext` (of set `in`) with the keys of the
+// Galois elements ks[s] (1 = relinearisation key), then ModDown, for all steps
+// together: the digits are read once per group of up to 8 keys, and the P-limb
+// transforms, base conversions and Q-limb transforms of every step share one
+// launch each. mode 0: add the set's first two components (relinearisation of
+// d2); mode 1: add phi_k(c0). Output ciphertext c of step s goes to
+// outs[s] + c * out_stride.
+static void ks_finish(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<u64>& ks, int mode,
+                      const std::vector<u64*>& outs, size_t out_stride) {
+  const int n = in.n, lp = in.limbs, nb = lp + C.K, S = (int)ks.size();
+  if (S == 0) return;
   const size_t N = C.N;
-  const DevBuf& key = C.key(k);
-  DevBuf u((size_t)n * 2 * nb * N, C.stream);
-  k_ks_inner(C, ext.p, key.p, u.p, n, lp);
-  DevBuf pl((size_t)n * 2 * C.K * N, C.stream);
-  k_gather_p(C, u.p, pl.p, n, lp, k);
-  ntt_inverse(C, pl.p, n * 2, p_map(C));
-  DevBuf z((size_t)n * 2 * lp * N, C.stream);
-  k_moddown_bconv(C, pl.p, z.p, n, lp);
-  ntt_forward(C, z.p, n * 2, limbs_q(lp, N));
-  k_moddown_combine(C, u.p, z.p, in.buf.p, in.ct_words(), out, out_stride, n, lp, k, mode);
+  const size_t ustep = (size_t)n * 2 * nb * N, pstep = (size_t)n * 2 * C.K * N, zstep = (size_t)n * 2 * lp * N;
+  DevBuf u((size_t)S * ustep, C.stream);
+  for (int s0 = 0; s0 < S; s0 += 8) {
+    const int cs = std::min(8, S - s0);
+    KeyPtrs kp{};
+    for (int t = 0; t < cs; t++) kp.k[t] = C.key(ks[s0 + t]).p;
+    k_ks_inner(C, ext.p, kp, cs, u.p + s0 * ustep, n, lp);
+  }
+  DevBuf pl((size_t)S * pstep, C.stream);
+  for (int s = 0; s < S; s++) k_gather_p(C, u.p + s * ustep, pl.p + s * pstep, n, lp, ks[s]);
+  ntt_inverse(C, pl.p, S * n * 2, p_map(C));
+  DevBuf z((size_t)S * zstep, C.stream);
+  k_moddown_bconv(C, pl.p, z.p, S * n, lp);
+  pl.reset();
+  ntt_forward(C, z.p, S * n * 2, limbs_q(lp, N));
+  for (int s = 0; s < S; s++)
+    k_moddown_combine(C, u.p + s * ustep, z.p + s * zstep, in.buf.p, in.ct_words(), outs[s], out_stride, n, lp,
+                      ks[s], mode);
 }
 
 void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<long>& steps, u64* out,
                      int out_cts_per_ct) {
   const size_t cw = in.ct_words();
+  std::vector<u64> ks;
+  std::vector<u64*> outs;
   for (size_t s = 0; s < steps.size(); s++) {
     const u64 k = C.galois_elt(steps[s]);
     u64* o = out + s * cw;
@@ -86,8 +103,10 @@ void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vect
       k_copy_limbs(C, in.buf.p, cw, o, cw * out_cts_per_ct, (size_t)in.n, 2 * in.limbs);
       continue;
     }
-    ks_finish(C, in, ext, k, 1, o, cw * out_cts_per_ct);
+    ks.push_back(k);
+    outs.push_back(o);
   }
+  ks_finish(C, in, ext, ks, 1, outs, cw * out_cts_per_ct);
 }
 
 std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps) {
@@ -128,7 +147,7 @@ std::unique_ptr<CtSet> relin_rescale(Ctx& C, const CtSet& d3) {
   if (d3.polys != 3) throw Error(1, "relinearisation expects three-component ciphertexts");
   auto out = new_set(C, d3.n, 2, d3.limbs, d3.scale);
   DevBuf ext = modup_poly(C, d3, 2);
-  ks_finish(C, d3, ext, 1, 0, out->buf.p, out->ct_words());
+  ks_finish(C, d3, ext, {1}, 0, {out->buf.p}, out->ct_words());
   rescale_inplace(C, *out);
   return out;
 }

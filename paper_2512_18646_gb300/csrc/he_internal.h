@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -151,8 +152,12 @@ void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int 
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs);
 // ModUp fast base conversion: x coeff [n][limbs][N] -> ext coeff [n][beta][limbs+K][N]
 void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs);
-// u[n][2][limbs+K] = sum_j ext[n][j] * key[j]  (NTT domain)
-void k_ks_inner(const Ctx& C, const u64* ext, const u64* key, u64* u, int n, int limbs);
+// key pointers of up to 8 steps for one inner-product launch
+struct KeyPtrs {
+  const u64* k[8];
+};
+// u[s][n][2][limbs+K] = sum_j ext[n][j] * key_s[j]  (NTT domain), s < S
+void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u, int n, int limbs);
 // gather P limbs of u (permuted by pi_k) into p [n][2][K][N]
 void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k);
 // ModDown base conversion: p coeff [n][2][K][N] -> z coeff [n][2][limbs][N]

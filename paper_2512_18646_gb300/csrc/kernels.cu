@@ -168,15 +168,18 @@ __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int l
 }
 
 // ModUp. Constant tables (words of d_up, indexed by the level `limbs`):
-//   inv [L1+1][L1][2]      (D_j/q_i)^{-1} mod q_i and its Shoup companion
-//   hat [L1+1][L1][L1+K]   (D_j/q_i) mod t_pos, pos over {q_0..q_{limbs-1}, p_0..}
+//   inv [L1+1][L1][2]         (D_j/q_i)^{-1} mod q_i and its Shoup companion
+//   hat [L1+1][L1][L1+K][2]   (D_j/q_i) mod t_pos and its Shoup companion,
+//                             pos over {q_0..q_{limbs-1}, p_0..}
+// Each term [x_i (D_j/q_i)^{-1}]_{q_i} (D_j/q_i) is a Shoup product in [0, 2t)
+// (valid for any multiplicand below 2^64); partial sums stay below 2t.
 __global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alpha, int beta, int L1, int K,
                                const u64* up_inv, const u64* up_hat, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int nb = limbs + K;
   const size_t total = (size_t)n * beta * N;
   const u64* inv = up_inv + (size_t)limbs * L1 * 2;
-  const u64* hat = up_hat + (size_t)limbs * L1 * (L1 + K);
+  const ulonglong2* hat = reinterpret_cast<const ulonglong2*>(up_hat) + (size_t)limbs * L1 * (L1 + K);
   HE_GRID_LOOP(idx, total) {
     const size_t jn = idx & (N - 1);
     const size_t r = idx >> log_n;
@@ -188,45 +191,68 @@ __global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alp
     for (int i = lo; i < hi; i++) {
       const u64 xi = X[(size_t)i * N + jn];
       y[i - lo] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
+      E[(size_t)i * N + jn] = xi;
     }
     for (int pos = 0; pos < nb; pos++) {
-      u64 out;
-      if (pos >= lo && pos < hi) {
-        out = X[(size_t)pos * N + jn];
-      } else {
-        const int g = pos < limbs ? pos : L1 + (pos - limbs);
-        Acc128 acc{0, 0};
-        for (int i = lo; i < hi; i++) mac128(acc, y[i - lo], hat[(size_t)i * (L1 + K) + pos]);
-        out = reduce128(acc.hi, acc.lo, pt[g].mod);
+      if (pos >= lo && pos < hi) continue;
+      const int g = pos < limbs ? pos : L1 + (pos - limbs);
+      const u64 t = pt[g].mod.q, t2 = 2 * t;
+      u64 s = 0;
+      for (int i = lo; i < hi; i++) {
+        const ulonglong2 h = __ldg(hat + (size_t)i * (L1 + K) + pos);
+        s += shoup_lazy(y[i - lo], h.x, h.y, t);
+        if (s >= t2) s -= t2;
       }
-      E[(size_t)pos * N + jn] = out;
+      E[(size_t)pos * N + jn] = s >= t ? s - t : s;
     }
   }
 }
 
-// u[c][comp][pos] = sum_j ext[c][j][pos] key[j][comp][g(pos)]
-__global__ void k_ks_inner_kernel(const u64* ext, const u64* key, u64* u, int n, int limbs, int beta, int L1, int K,
-                                  const PrimeTab* pt, int log_n) {
+// u[s][c][comp][pos] = sum_j ext[c][j][pos] key_s[j][comp][g(pos)] for the
+// steps s of one launch. A block owns one limb position `pos` and a tile of
+// KS_TILE coefficients: it reads that tile of every key once into shared
+// memory (each thread only touches its own column, so no barrier is needed)
+// and then walks all n ciphertexts, so key traffic is one read per launch
+// instead of one per ciphertext.
+constexpr int KS_TILE = 128;
+template <int MAXB>
+__global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* ext, KeyPtrs keys, int S, u64* u, int n,
+                                                             int limbs, int beta, int L1, int K, const PrimeTab* pt,
+                                                             int log_n) {
+  extern __shared__ u64 skey[];  // [S][beta][2][KS_TILE]
   const size_t N = (size_t)1 << log_n;
   const int nb = limbs + K, npk = L1 + K;
-  const size_t total = (size_t)n * nb * N;
-  HE_GRID_LOOP(idx, total) {
-    const size_t jn = idx & (N - 1);
-    const size_t r = idx >> log_n;
-    const int pos = (int)(r % nb), c = (int)(r / nb);
-    const int g = pos < limbs ? pos : L1 + (pos - limbs);
-    const u64* E = ext + (size_t)c * beta * nb * N + (size_t)pos * N + jn;
-    const u64* Kp = key + (size_t)g * N + jn;
-    Acc128 a0{0, 0}, a1{0, 0};
-    for (int dg = 0; dg < beta; dg++) {
-      const u64 e = E[(size_t)dg * nb * N];
-      mac128(a0, e, Kp[((size_t)dg * 2) * npk * N]);
-      mac128(a1, e, Kp[((size_t)dg * 2 + 1) * npk * N]);
+  const int pos = blockIdx.y;
+  const int g = pos < limbs ? pos : L1 + (pos - limbs);
+  const size_t jn = (size_t)blockIdx.x * KS_TILE + threadIdx.x;
+  if (jn >= N) return;
+  for (int st = 0; st < S; st++)
+    for (int dg = 0; dg < beta; dg++)
+      for (int cp = 0; cp < 2; cp++)
+        skey[((st * beta + dg) * 2 + cp) * KS_TILE + threadIdx.x] =
+            keys.k[st][(((size_t)dg * 2 + cp) * npk + g) * N + jn];
+  const Mod md = pt[g].mod;
+  const size_t ustep = (size_t)n * 2 * nb * N;
+  for (int c = 0; c < n; c++) {
+    const u64* Ep = ext + (size_t)c * beta * nb * N + (size_t)pos * N + jn;
+    u64 e[MAXB];
+#pragma unroll
+    for (int dg = 0; dg < MAXB; dg++)
+      if (dg < beta) e[dg] = Ep[(size_t)dg * nb * N];
+    for (int st = 0; st < S; st++) {
+      const u64* kk = skey + (size_t)st * beta * 2 * KS_TILE + threadIdx.x;
+      Acc128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+      for (int dg = 0; dg < MAXB; dg++) {
+        if (dg < beta) {
+          mac128(a0, e[dg], kk[(dg * 2) * KS_TILE]);
+          mac128(a1, e[dg], kk[(dg * 2 + 1) * KS_TILE]);
+        }
+      }
+      u64* U = u + st * ustep + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
+      U[0] = reduce128(a0.hi, a0.lo, md);
+      U[(size_t)nb * N] = reduce128(a1.hi, a1.lo, md);
     }
-    const Mod md = pt[g].mod;
-    u64* U = u + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
-    U[0] = reduce128(a0.hi, a0.lo, md);
-    U[(size_t)nb * N] = reduce128(a1.hi, a1.lo, md);
   }
 }
 
@@ -245,24 +271,29 @@ __global__ void k_gather_p_kernel(const u64* u, u64* p, int n, int limbs, int K,
 }
 
 // ModDown constants (words of d_down):
-//   pinv [K][2]   (P/p_k)^{-1} mod p_k, Shoup companion
-//   phat [K][L1]  (P/p_k) mod q_i
-//   Pinv [L1][2]  P^{-1} mod q_i, Shoup companion
+//   pinv [K][2]       (P/p_k)^{-1} mod p_k, Shoup companion
+//   phat [K][L1][2]   (P/p_k) mod q_i, Shoup companion
+//   Pinv [L1][2]      P^{-1} mod q_i, Shoup companion
 __global__ void k_moddown_bconv_kernel(const u64* p, u64* z, int n, int limbs, int L1, int K, const u64* down,
                                        const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t total = (size_t)n * 2 * N;
   const u64* pinv = down;
-  const u64* phat = down + 2 * K;
+  const ulonglong2* phat = reinterpret_cast<const ulonglong2*>(down + 2 * K);
   HE_GRID_LOOP(idx, total) {
     const size_t jn = idx & (N - 1), cc = idx >> log_n;
     u64 y[4];
     for (int kk = 0; kk < K; kk++)
       y[kk] = shoup(p[(cc * K + kk) * N + jn], pinv[2 * kk], pinv[2 * kk + 1], pt[L1 + kk].mod.q);
     for (int i = 0; i < limbs; i++) {
-      Acc128 acc{0, 0};
-      for (int kk = 0; kk < K; kk++) mac128(acc, y[kk], phat[(size_t)kk * L1 + i]);
-      z[(cc * limbs + i) * N + jn] = reduce128(acc.hi, acc.lo, pt[i].mod);
+      const u64 q = pt[i].mod.q, q2 = 2 * q;
+      u64 s = 0;
+      for (int kk = 0; kk < K; kk++) {
+        const ulonglong2 h = __ldg(phat + (size_t)kk * L1 + i);
+        s += shoup_lazy(y[kk], h.x, h.y, q);
+        if (s >= q2) s -= q2;
+      }
+      z[(cc * limbs + i) * N + jn] = s >= q ? s - q : s;
     }
   }
 }
@@ -347,48 +378,69 @@ __global__ void k_add_const_kernel(u64* ct, int n, int limbs, const u64* cdev, i
 
 // Convolution multiply-accumulate. rot [c_in][w_in][k][2][limbs][N] holds
 // Rot(X_{c,j}, gap a) at [c][j][a]; w [c_out][c_in][k][k][limbs][2] holds the
-// integer weights mod q_i and Shoup companions ([o][c][a][b]). One thread per
-// (output column j', component, limb, coefficient) computes up to OB output
-// channels.
-template <int OB>
+// integer weights mod q_i and Shoup companions ([o][c][a][b]). A block works
+// on one (component, limb) and 2 * blockDim.x coefficients; its weights for
+// that limb are staged in shared memory (every thread reads the same weight,
+// a broadcast). Each thread computes TN adjacent coefficients of OB output
+// channels for the output columns jp = blockIdx.z, blockIdx.z + gridDim.z, ...
+template <int OB, int TN>
 __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                                   int c_out, int w_out, int limbs, const PrimeTab* pt, int log_n) {
+  extern __shared__ ulonglong2 sw[];  // [c_out][c_in k k]
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
-  const size_t total = (size_t)w_out * 2 * LN;
-  HE_GRID_LOOP(idx, total) {
-    const size_t jn = idx & (N - 1);
-    const size_t r = idx >> log_n;
-    const int i = (int)(r % limbs);
-    const int comp = (int)((r / limbs) & 1);
-    const int jp = (int)(r / limbs / 2);
-    const u64 q = pt[i].mod.q, q2 = 2 * q;
+  const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+  const int T = c_in * k * k;
+  for (int id = threadIdx.x; id < c_out * T; id += blockDim.x)
+    sw[id] = *reinterpret_cast<const ulonglong2*>(w + ((size_t)id * limbs + i) * 2);
+  __syncthreads();
+  const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
+  if (n0 >= N) return;
+  const u64 q = pt[i].mod.q, q2 = 2 * q;
+  const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
+  for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
     for (int o0 = 0; o0 < c_out; o0 += OB) {
-      const int ob = min(OB, c_out - o0);
-      u64 acc[OB];
+      u64 acc[OB][TN];
 #pragma unroll
-      for (int t = 0; t < OB; t++) acc[t] = 0;
+      for (int t = 0; t < OB; t++)
+#pragma unroll
+        for (int v = 0; v < TN; v++) acc[t][v] = 0;
       for (int c = 0; c < c_in; c++)
-        for (int b = 0; b < k; b++)
+        for (int b = 0; b < k; b++) {
+          const u64* src = rot + ((size_t)(c * w_in + stride * jp + b) * k) * 2 * LN + off;
           for (int a = 0; a < k; a++) {
-            const u64 x = rot[((((size_t)c * w_in + (size_t)stride * jp + b) * k + a) * 2 + comp) * LN + (size_t)i * N + jn];
+            u64 x[TN];
+            if constexpr (TN == 2) {
+              const ulonglong2 xx = *reinterpret_cast<const ulonglong2*>(src + (size_t)a * 2 * LN);
+              x[0] = xx.x;
+              x[1] = xx.y;
+            } else {
+#pragma unroll
+              for (int v = 0; v < TN; v++) x[v] = src[(size_t)a * 2 * LN + v];
+            }
+            const ulonglong2* wr = sw + (size_t)o0 * T + (c * k + a) * k + b;
 #pragma unroll
             for (int t = 0; t < OB; t++) {
-              if (t < ob) {
-                const u64* ww = w + (((((size_t)(o0 + t) * c_in + c) * k + a) * k + b) * limbs + i) * 2;
-                u64 s = acc[t] + shoup_lazy(x, ww[0], ww[1], q);
-                if (s >= q2) s -= q2;
-                acc[t] = s;
+              if (o0 + t < c_out) {
+                const ulonglong2 ww = wr[(size_t)t * T];
+#pragma unroll
+                for (int v = 0; v < TN; v++) {
+                  u64 sacc = acc[t][v] + shoup_lazy(x[v], ww.x, ww.y, q);
+                  if (sacc >= q2) sacc -= q2;
+                  acc[t][v] = sacc;
+                }
               }
             }
           }
-#pragma unroll
-      for (int t = 0; t < OB; t++)
-        if (t < ob) {
-          u64 v = acc[t];
-          if (v >= q) v -= q;
-          out[(((size_t)(o0 + t) * w_out + jp) * 2 + comp) * LN + (size_t)i * N + jn] = v;
         }
+#pragma unroll
+      for (int t = 0; t < OB; t++) {
+        if (o0 + t < c_out) {
+          u64* dst = out + ((size_t)(o0 + t) * w_out + jp) * 2 * LN + off;
+#pragma unroll
+          for (int v = 0; v < TN; v++) dst[v] = acc[t][v] >= q ? acc[t][v] - q : acc[t][v];
+        }
+      }
     }
   }
 }
@@ -426,37 +478,58 @@ __global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, i
   }
 }
 
-// out[o] = sum_cj pt[o][cj] X[cj]; X [n_in][2][limbs][N], pt [out_dim][n_in][limbs][N]
-template <int OB>
+// out[o] = sum_cj pt[o][cj] X[cj]; X [n_in][2][limbs][N], pt [out_dim][n_in][limbs][N].
+// One thread per (limb, coefficient) handles both components, so every
+// plaintext word is read once. The loads of UN input columns are issued
+// before their products so that enough reads are in flight to stream the
+// plaintexts at memory speed; sums are reduced every 8 columns.
+template <int OB, int UN>
 __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
                                 const PrimeTab* pt, int log_n) {
+  static_assert(8 % UN == 0, "reduction every 8 columns");
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
-  const size_t total = (size_t)2 * LN;
-  HE_GRID_LOOP(idx, total) {
-    const size_t w = idx % LN;
-    const int comp = (int)(idx / LN);
+  HE_GRID_LOOP(w, LN) {
     const int i = (int)(w >> log_n);
     const Mod md = pt[i].mod;
     for (int o0 = 0; o0 < out_dim; o0 += OB) {
-      const int ob = min(OB, out_dim - o0);
-      Acc128 acc[OB];
+      Acc128 a0[OB], a1[OB];
 #pragma unroll
-      for (int t = 0; t < OB; t++) acc[t] = Acc128{0, 0};
-      for (int cj = 0; cj < n_in; cj++) {
-        const u64 x = X[((size_t)cj * 2 + comp) * LN + w];
+      for (int t = 0; t < OB; t++) a0[t] = a1[t] = Acc128{0, 0};
+      for (int cj0 = 0; cj0 < n_in; cj0 += UN) {
+        u64 x0[UN], x1[UN], pv[UN][OB];
 #pragma unroll
-        for (int t = 0; t < OB; t++)
-          if (t < ob) mac128(acc[t], x, ptx[((size_t)(o0 + t) * n_in + cj) * LN + w]);
-        if ((cj & 7) == 7) {
+        for (int v = 0; v < UN; v++) {
+          const int cj = cj0 + v;
+          const bool ok = cj < n_in;
+          x0[v] = ok ? X[(size_t)cj * 2 * LN + w] : 0;
+          x1[v] = ok ? X[((size_t)cj * 2 + 1) * LN + w] : 0;
 #pragma unroll
           for (int t = 0; t < OB; t++)
-            if (t < ob) acc[t] = Acc128{0, reduce128(acc[t].hi, acc[t].lo, md)};
+            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * n_in + cj) * LN + w] : 0;
+        }
+#pragma unroll
+        for (int v = 0; v < UN; v++)
+#pragma unroll
+          for (int t = 0; t < OB; t++) {
+            mac128(a0[t], x0[v], pv[v][t]);
+            mac128(a1[t], x1[v], pv[v][t]);
+          }
+        if (((cj0 + UN) & 7) == 0) {
+#pragma unroll
+          for (int t = 0; t < OB; t++) {
+            a0[t] = Acc128{0, reduce128(a0[t].hi, a0[t].lo, md)};
+            a1[t] = Acc128{0, reduce128(a1[t].hi, a1[t].lo, md)};
+          }
         }
       }
 #pragma unroll
-      for (int t = 0; t < OB; t++)
-        if (t < ob) out[((size_t)(o0 + t) * 2 + comp) * LN + w] = reduce128(acc[t].hi, acc[t].lo, md);
+      for (int t = 0; t < OB; t++) {
+        if (o0 + t < out_dim) {
+          out[((size_t)(o0 + t) * 2) * LN + w] = reduce128(a0[t].hi, a0[t].lo, md);
+          out[((size_t)(o0 + t) * 2 + 1) * LN + w] = reduce128(a1[t].hi, a1[t].lo, md);
+        }
+      }
     }
   }
 }
@@ -535,9 +608,38 @@ void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs) {
   HE_LAUNCH(k_modup_kernel, (size_t)n * C.beta_at(limbs) * C.N, 8.0 * (double)C.N * n * (limbs + (double)C.beta_at(limbs) * (limbs + C.K)), x, ext, n, limbs, C.alpha, C.beta_at(limbs), C.L1,
             C.K, up_inv, up_hat, C.dev_ptab(), C.log_n);
 }
-void k_ks_inner(const Ctx& C, const u64* ext, const u64* key, u64* u, int n, int limbs) {
-  HE_LAUNCH(k_ks_inner_kernel, (size_t)n * (limbs + C.K) * C.N, 8.0 * (double)C.N * (limbs + C.K) * ((double)C.beta_at(limbs) * (n + 2) + 2.0 * n), ext, key, u, n, limbs, C.beta_at(limbs), C.L1, C.K,
-            C.dev_ptab(), C.log_n);
+void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u, int n, int limbs) {
+  const int beta = C.beta_at(limbs);
+  if (beta > 16) throw Error(8, "more than 16 key-switching digits are not supported");
+  if (S < 1 || S > 8) throw Error(1, "1..8 keys per inner-product launch");
+  const size_t per_step = (size_t)beta * 2 * KS_TILE * 8;
+  // steps per launch so that the staged key tiles fit in 96 KiB of shared memory
+  const int sc = (int)std::max<size_t>(1, std::min<size_t>((size_t)S, (96 * 1024) / per_step));
+  static bool attr = false;
+  if (!attr) {
+    HE_CUDA(cudaFuncSetAttribute(k_ks_inner_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    HE_CUDA(cudaFuncSetAttribute(k_ks_inner_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    attr = true;
+  }
+  const int nb = limbs + C.K;
+  const size_t ustep = (size_t)n * 2 * nb * C.N;
+  for (int s0 = 0; s0 < S; s0 += sc) {
+    const int cs = std::min(sc, S - s0);
+    KeyPtrs kp{};
+    for (int t = 0; t < cs; t++) kp.k[t] = keys.k[s0 + t];
+    const dim3 grid((unsigned)((C.N + KS_TILE - 1) / KS_TILE), (unsigned)nb);
+    const size_t smem = (size_t)cs * per_step;
+    const double bytes = 8.0 * (double)C.N * nb * ((double)beta * (n + 2.0 * cs) + 2.0 * n * cs);
+    void* tok = prof_begin(beta <= 8 ? "k_ks_inner_kernel<8>" : "k_ks_inner_kernel<16>", C.stream, bytes);
+    if (beta <= 8)
+      k_ks_inner_kernel<8><<<grid, KS_TILE, smem, C.stream>>>(ext, kp, cs, u + s0 * ustep, n, limbs, beta, C.L1, C.K,
+                                                               C.dev_ptab(), C.log_n);
+    else
+      k_ks_inner_kernel<16><<<grid, KS_TILE, smem, C.stream>>>(ext, kp, cs, u + s0 * ustep, n, limbs, beta, C.L1,
+                                                                C.K, C.dev_ptab(), C.log_n);
+    prof_end(tok, C.stream);
+    HE_CUDA(cudaGetLastError());
+  }
 }
 void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k) {
   HE_LAUNCH(k_gather_p_kernel, (size_t)n * 2 * C.K * C.N, 8.0 * (double)C.N * 4 * n * C.K, u, p, n, limbs, C.K, k, C.log_n);
@@ -549,7 +651,7 @@ void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs) {
 }
 void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
                        size_t out_stride, int n, int limbs, u64 k, int mode) {
-  const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)C.K * C.L1;
+  const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)2 * C.K * C.L1;
   HE_LAUNCH(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * n * limbs * (mode == 0 ? 8.0 : 7.0), u, z, base, base_stride, out, out_stride, n,
             limbs, C.K, k, mode, Pinv, C.dev_ptab(), C.log_n);
 }
@@ -567,14 +669,46 @@ void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int 
 }
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs) {
-  HE_LAUNCH(k_conv_mac_kernel<8>, (size_t)w_out * 2 * limbs * C.N, 8.0 * (double)C.N * 2.0 * limbs * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out), rot, out, w, c_in, w_in, k, stride, c_out, w_out,
-            limbs, C.dev_ptab(), C.log_n);
+  constexpr int TN = 2, TH = 128;
+  const size_t smem = (size_t)c_out * c_in * k * k * 16;
+  if (smem > 200 * 1024) throw Error(8, "convolution weights exceed shared memory");
+  const unsigned gx = (unsigned)((C.N / TN + TH - 1) / TH), gy = (unsigned)(2 * limbs);
+  unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * gy));
+  if (gz > (unsigned)w_out) gz = (unsigned)w_out;
+  const double bytes = 8.0 * (double)C.N * 2.0 * limbs * ((double)c_in * (stride * (w_out - 1) + k) * k +
+                                                         (double)c_out * w_out);
+  void* tok = prof_begin(c_out <= 8 ? "k_conv_mac_kernel<8>" : "k_conv_mac_kernel<16>", C.stream, bytes);
+  if (c_out <= 8) {
+    static bool attr8 = false;
+    if (!attr8) {
+      HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<8, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr8 = true;
+    }
+    k_conv_mac_kernel<8, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
+                                                                        w_out, limbs, C.dev_ptab(), C.log_n);
+  } else {
+    static bool attr16 = false;
+    if (!attr16) {
+      HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<16, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr16 = true;
+    }
+    k_conv_mac_kernel<16, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
+                                                                         w_out, limbs, C.dev_ptab(), C.log_n);
+  }
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
 }
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
   HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p), A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs) {
-  HE_LAUNCH(k_fc_mac_kernel<10>, (size_t)2 * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n_in + (double)out_dim * n_in + 2.0 * out_dim), X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+  const size_t total = (size_t)limbs * C.N;
+  const double bytes = 8.0 * (double)C.N * limbs * (2.0 * n_in + (double)out_dim * n_in + 2.0 * out_dim);
+  void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes);
+  k_fc_mac_kernel<5, 4><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
+                                                                  C.log_n);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
 }
 void k_check_range(const Ctx& C, const u64* x, size_t rows, int limbs, unsigned long long* bad) {
   HE_LAUNCH(k_check_range_kernel, rows * C.N, 8.0 * (double)C.N * rows, x, rows, limbs, C.dev_ptab(), C.log_n, bad);

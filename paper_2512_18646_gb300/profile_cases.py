@@ -12,6 +12,8 @@ device holds a few GB at most and each launch's data exceeds L2:
           and rescale.
   square  the x^2 activation (tensor, relinearisation, rescale) of 64
           ciphertexts at the top level (13 limbs).
+  fc      the dense layer's plaintext multiply-accumulate, rescale and
+          rotate-and-add on 16 x 4 input ciphertexts at 9 limbs, 10 outputs.
 
 The case body (after key generation and encryption) runs inside the NVTX
 range "case", so a capture can be limited to it (ncu --nvtx --nvtx-include
@@ -30,7 +32,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["conv1", "square"])
+    ap.add_argument("case", choices=["conv1", "square", "fc"])
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
     from inputs import synthetic
@@ -42,14 +44,25 @@ def main():
     g = api.Context.from_preset(pre, seed=5)
     g.keygen([1, 2, 3, 4])
     w = synthetic.cnn_weights(128, seed=302)
+    import numpy as np
     import torch
-    imgs = synthetic.images(256, 128, 16 if args.case == "conv1" else 64, seed=301)
-    x = g.encrypt_image(imgs, 128)
+    if args.case == "fc":
+        g.keygen([4, 8, 16, 32, 64])
+        rng = np.random.default_rng(3)
+        m = rng.integers(-(1 << 40), 1 << 40, size=(64, g.N), dtype=np.int64)
+        x = g.encrypt_coeffs(m, 9, g.scale)
+        W = rng.normal(0, 0.05, (10, 16 * 30 * 4))
+        pts = g.fc_prepare(W, 16, 30, 4, 4, 128, 256, 9)
+    else:
+        imgs = synthetic.images(256, 128, 16 if args.case == "conv1" else 64, seed=301)
+        x = g.encrypt_image(imgs, 128)
     g.synchronize()
     torch.cuda.nvtx.range_push("case")
     for _ in range(args.repeat):
         if args.case == "conv1":
             y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
+        elif args.case == "fc":
+            y = g.fc_apply(x, pts, None)
         else:
             y = g.mul(x, x)
         del y
