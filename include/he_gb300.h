@@ -260,6 +260,34 @@ int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_cts
 
 void he_ctset_free(he_ctset* set);
 
+/*
+ * he_rescale_noalloc: he_rescale for callers that cannot allocate device
+ * memory during the call -- a serving loop that must keep a fixed memory
+ * footprint once started, a framework that hands out every device
+ * allocation from its own pool, or a process whose device-memory quota is
+ * used up. The paper has no counterpart; this is an interface for such
+ * callers. It makes no cudaMalloc, cudaFree or other allocating call.
+ *
+ * in:  DEVICE pointer, n_ct ciphertexts [n_ct][2][limbs][N] in the NTT domain
+ *      (the layout of he_ctset_device_ptr), at the given scale.
+ * out: DEVICE pointer, caller-owned, [n_ct][2][limbs-1][N]; must not overlap in.
+ * out_scale (host, may be NULL) receives scale / q_{limbs-1}.
+ * The result equals he_rescale's. Work is enqueued on the context's stream.
+ *
+ * Scratch: one array of 2^21 64-bit words (16 MiB) that the library keeps in
+ * every GPU that loads it, until the process exits. Sizes with
+ * n_ct * 2 * limbs * N > 2^21 are rejected with HE_E_ARG (e.g. at N = 2^16 one
+ * ciphertext of up to 16 limbs per call). The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. The context's
+ * device must be current. Every call shares the array and it keeps the last
+ * call's contents (no step reads scratch it has not written in the same
+ * call), so calls whose GPU work overlaps -- on different streams or from
+ * different threads -- race on it.
+ */
+int he_rescale_noalloc(he_ctx* ctx, const uint64_t* in, int n_ct, int limbs, double scale, uint64_t* out,
+                       double* out_scale);
+
 /* ---- transforms (testing) ---- */
 
 /*

@@ -75,6 +75,7 @@ SIGNATURES = {
     "he_ctset_slice": (I, [V, V, I, I, PV]),
     "he_ctset_concat": (I, [V, PV, I, PV]),
     "he_ctset_free": (None, [V]),
+    "he_rescale_noalloc": (I, [V, V, I, I, D, V, P_D]),
     "he_ntt": (I, [V, P_U64, I, I, I, I]),
     "he_kernel_launches": (U64, []),
     "he_profile_enable": (I, [I]),

@@ -15,6 +15,10 @@ using namespace he;
 
 static thread_local std::string g_err;
 
+namespace he {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace he
+
 template <class F>
 static int guard(F f) {
   try {

@@ -33,6 +33,8 @@ struct Error : std::runtime_error {
 };
 
 void cuda_check(cudaError_t e, const char* what);
+// message returned by he_last_error() on this thread (capi.cpp)
+void set_last_error(const std::string& msg);
 #define HE_CUDA(x) ::he::cuda_check((x), #x)
 
 struct Ctx;
