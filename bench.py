@@ -50,6 +50,27 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_seeds(rank: int) -> dict:
+    """Each rank encrypts its own batch: distinct keys and images, same weights."""
+    return {"ctx_seed": 1000 + rank, "image_seed": 301 + rank, "weight_seed": 302}
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The slowest rank's time (gloo all-reduce on CPU; no data-path collective)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(images_per_step: int, steps: int, world: int, t_max_s: float) -> float:
+    """Whole-job images/s: every rank processed images_per_step * steps images."""
+    return images_per_step * steps * world / t_max_s
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -127,6 +148,55 @@ def profile_read(lib):
     return {nm[i]: {"ms": ms[i], "launches": int(cnt[i]), "bytes": by[i]} for i in range(n.value)}
 
 
+def ntt_butterflies(kernel: str, alg_bytes: float, log_n: int) -> float:
+    """Butterflies done by NTT launches whose algorithmic bytes (16 N per limb) sum to alg_bytes."""
+    n = 1 << log_n
+    limbs = alg_bytes / (16.0 * n)
+    n1 = log_n // 2
+    stages = n1 if kernel.endswith("cols") else log_n - n1
+    return limbs * (n // 2) * stages
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu capture of this kernel, scaled
+    from the captured launch to this launch by algorithmic bytes (None if absent)."""
+    try:
+        t = json.load(open(TRAFFIC_FILE)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not t:
+        return None
+    return t["dram_bytes"] / t["alg_bytes"] * alg_bytes_per_launch
+
+
+def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n):
+    avg_s = t["ms"] / 1e3 / max(1, t["launches"])
+    alg_per_launch = t["bytes"] / max(1, t["launches"])
+    gbs = alg_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+    base = {"kernel": name, "share_of_device_time": round(t["ms"] / total_ms, 4), "launches": t["launches"],
+            "avg_launch_us": round(avg_s * 1e6, 2),
+            "alg_bytes_per_launch": alg_per_launch,
+            "hbm_view": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                         "peak_source": "measured" if measured else "fallback"}}
+    traffic = ncu_traffic(name, alg_per_launch)
+    if name.startswith("k_ntt_"):
+        # one Shoup modular product per butterfly; peak = measured Shoup products/s
+        bfly = ntt_butterflies(name, t["bytes"], log_n) / max(1, t["launches"])
+        ach = bfly / avg_s / 1e9
+        peak = modmul_peak / 1e9
+        base.update({"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "Gmodmul/s",
+                     "frac": round(ach / peak, 4), "traffic": traffic,
+                     "peak_source": "measured (he_calibrate_modmul, Shoup products in registers)"})
+    else:
+        base.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbs / hbm, 4), "traffic": traffic,
+                     "peak_source": "measured" if measured else "fallback"})
+    return base
+
+
 def cnn_step(g, x, w, pts):
     y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
     g.square(y)
@@ -146,12 +216,13 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     pre = synthetic.CNN_N16
-    g = api.Context.from_preset(pre, seed=1000 + rank, stream=stream.cuda_stream)
+    seeds = rank_seeds(rank)
+    g = api.Context.from_preset(pre, seed=seeds["ctx_seed"], stream=stream.cuda_stream)
     g.keygen(ROT_STEPS)
     B = args.batch
     h1, h2 = synthetic.cnn_shapes(SIDE)
-    w = synthetic.cnn_weights(SIDE, seed=302)
-    imgs = synthetic.images(B, SIDE, SIDE, seed=301 + rank)
+    w = synthetic.cnn_weights(SIDE, seed=seeds["weight_seed"])
+    imgs = synthetic.images(B, SIDE, SIDE, seed=seeds["image_seed"])
     x = g.encrypt_image(imgs, H, ct_id_base=0)
     fc_limbs = pre_limbs = len(pre.q_bits) - 4
     pts = g.fc_prepare(w.fc_w, 16, h2, h2, 4, H, B, fc_limbs)
@@ -182,13 +253,8 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
     launches = lib.he_kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = B * args.steps * world / (t_max / 1e3)
+    t_max = max_over_ranks(ms, world)
+    value = job_throughput(B, args.steps, world, t_max / 1e3)
 
     # accuracy of the last step's logits against the FP64 CNN (outside timing)
     logits = g.decrypt_slots(z)[:, ::H][:, :B].T
@@ -206,13 +272,10 @@ def run_gpu(args, rank, world, local_rank):
     top = max(prof, key=lambda k: prof[k]["ms"])
     pk = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    t = prof[top]
-    achieved = t["bytes"] / (t["ms"] / 1e3) / 1e9 / 1.0 if t["ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
-                "peak_source": "measured" if "fallback" not in pk else "fallback",
-                "share_of_device_time": round(t["ms"] / prof_total, 4),
-                "launches": t["launches"], "avg_launch_us": round(1e3 * t["ms"] / max(1, t["launches"]), 2)}
+    import ctypes
+    modmul_peak = ctypes.c_double()
+    lib.he_calibrate_modmul(g.h, ctypes.byref(modmul_peak))
+    roofline = roofline_for(top, prof[top], prof_total, hbm, "fallback" not in pk, modmul_peak.value, pre.log_n)
     breakdown = {k: {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
                      "launches_per_step": v["launches"] // args.steps,
                      "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0}
@@ -235,13 +298,8 @@ def run_gpu(args, rank, world, local_rank):
             zz = cnn_step(g, xin, w, pts)
             check(lib.he_ctset_export(zz.h, pin_out.ctypes.data_as(P_U64), pin_out.size))
         g.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([t_e2e], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-        e2e = {"value": round(B * args.steps * world / t_e2e, 3), "unit": UNIT,
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": round(job_throughput(B, args.steps, world, t_e2e), 3), "unit": UNIT,
                "h2d_bytes_per_step": int(pin_arr.nbytes), "d2h_bytes_per_step": int(out_words * 8),
                "ms_per_step": round(1e3 * t_e2e / args.steps, 3)}
 
@@ -249,7 +307,7 @@ def run_gpu(args, rank, world, local_rank):
     return {
         "value": value, "ms_per_step": t_max / args.steps, "launches": launches // args.steps * args.steps,
         "roofline": roofline, "breakdown": breakdown, "e2e": e2e, "clocks": clocks, "max_abs_err": max_err,
-        "images_per_step": B,
+        "images_per_step": B, "modmul_peak": modmul_peak.value,
     }
 
 
@@ -340,6 +398,7 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": res["launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+            "alu_peak_modmul_per_s": res["modmul_peak"],
             "plain_images_per_s": res["value"] / args.batch, "kernel_breakdown": res["breakdown"]}
     print(json.dumps(line))
 

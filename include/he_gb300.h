@@ -300,6 +300,12 @@ int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime,
 
 /* ---- instrumentation ---- */
 
+/* Measured peak of 64-bit Shoup modular products (x w mod q with a
+ * precomputed companion of w, the NTT butterfly's product) per second on the
+ * context's GPU: independent chains in registers on every SM, timed with
+ * CUDA events. Used as the integer-arithmetic roofline. */
+int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t he_kernel_launches(void);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "he_ctset_free": (None, [V]),
     "he_rescale_noalloc": (I, [V, V, I, I, D, V, P_D]),
     "he_ntt": (I, [V, P_U64, I, I, I, I]),
+    "he_calibrate_modmul": (I, [V, P_D]),
     "he_kernel_launches": (U64, []),
     "he_profile_enable": (I, [I]),
     "he_profile_read": (I, [ctypes.c_char_p, SZ, P_D, P_U64, P_D, I, P_I]),

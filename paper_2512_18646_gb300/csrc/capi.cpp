@@ -441,6 +441,30 @@ int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_cts
 
 void he_ctset_free(he_ctset* set) { delete set; }
 
+int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s) {
+  return guard([&] {
+    REQUIRE(ctx && modmul_per_s, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    int sms = 0;
+    HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
+    const int threads = 256, blocks = sms * 8, iters = 4096;
+    DevBuf sink((size_t)blocks * threads, C.stream);
+    k_calib_shoup(C, sink.p, blocks, threads, 64);  // warm-up
+    cudaEvent_t a, b;
+    HE_CUDA(cudaEventCreate(&a));
+    HE_CUDA(cudaEventCreate(&b));
+    HE_CUDA(cudaEventRecord(a, C.stream));
+    k_calib_shoup(C, sink.p, blocks, threads, iters);
+    HE_CUDA(cudaEventRecord(b, C.stream));
+    HE_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    HE_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *modmul_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+  });
+}
+
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse) {
   return guard([&] {
     REQUIRE(ctx && host && n_polys >= 1 && limbs >= 1, HE_E_ARG, "bad arguments");

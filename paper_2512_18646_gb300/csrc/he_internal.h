@@ -181,6 +181,8 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj]
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs);
+// calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
+void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters);
 // number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad
 void k_check_range(const Ctx& C, const u64* x, size_t rows, int limbs, unsigned long long* bad);
 // copy groups x rows_per_group limbs: row r of group g at src + g src_gs + r N

@@ -534,6 +534,24 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
   }
 }
 
+// Integer-arithmetic calibration: 8 independent chains of Shoup products per
+// thread (enough instruction-level parallelism to keep the integer pipes
+// busy), `iters` products per chain. The xor of the chains is written so the
+// work cannot be removed.
+__global__ void k_calib_shoup_kernel(u64* sink, u64 q, u64 w, u64 wp, int iters) {
+  u64 a[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) a[c] = (blockIdx.x * 131ull + threadIdx.x * 7ull + c) % q;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) a[c] = shoup_lazy(a[c], w, wp, q);
+  }
+  u64 x = 0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) x ^= a[c];
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
 // counts residues >= q_i in [n][limbs][N] rows (limb i of each polynomial)
 __global__ void k_check_range_kernel(const u64* x, size_t rows, int limbs, const PrimeTab* pt, int log_n,
                                      unsigned long long* bad) {
@@ -707,6 +725,13 @@ void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int
   void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes);
   k_fc_mac_kernel<5, 4><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
                                                                   C.log_n);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
+}
+void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters) {
+  const u64 q = C.q[0], w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);
+  void* tok = prof_begin("k_calib_shoup_kernel", C.stream, 0.0);
+  k_calib_shoup_kernel<<<blocks, threads, 0, C.stream>>>(sink, q, w, wp, iters);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }

@@ -12,6 +12,8 @@ device holds a few GB at most and each launch's data exceeds L2:
           and rescale.
   square  the x^2 activation (tensor, relinearisation, rescale) of 64
           ciphertexts at the top level (13 limbs).
+  conv2   the second convolution (16 x 3 x 3 stride 2 over 8 channels of 16
+          columns, row gap 2) on 128 ciphertexts at 11 limbs.
   fc      the dense layer's plaintext multiply-accumulate, rescale and
           rotate-and-add on 16 x 4 input ciphertexts at 9 limbs, 10 outputs.
 
@@ -32,7 +34,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["conv1", "square", "fc"])
+    ap.add_argument("case", choices=["conv1", "conv2", "square", "fc"])
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
     from inputs import synthetic
@@ -46,7 +48,11 @@ def main():
     w = synthetic.cnn_weights(128, seed=302)
     import numpy as np
     import torch
-    if args.case == "fc":
+    if args.case == "conv2":
+        rng = np.random.default_rng(4)
+        m = rng.integers(-(1 << 40), 1 << 40, size=(8 * 16, g.N), dtype=np.int64)
+        x = g.encrypt_coeffs(m, 11, g.scale)
+    elif args.case == "fc":
         g.keygen([4, 8, 16, 32, 64])
         rng = np.random.default_rng(3)
         m = rng.integers(-(1 << 40), 1 << 40, size=(64, g.N), dtype=np.int64)
@@ -61,6 +67,8 @@ def main():
     for _ in range(args.repeat):
         if args.case == "conv1":
             y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
+        elif args.case == "conv2":
+            y = g.conv2d(x, 8, 2, w.conv2_w, w.conv2_b, 2)
         elif args.case == "fc":
             y = g.fc_apply(x, pts, None)
         else:
