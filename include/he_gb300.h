@@ -168,8 +168,11 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
 
 /*
  * he_poly_act: polynomial activation in place. Supported: degree 2 with
- * coeffs {0, 0, 1} (x -> x^2: tensor, relinearise, rescale). Other
- * polynomials return HE_E_UNIMPL.
+ * coeffs {0, 0, 1} (x -> x^2: tensor product, rescale). The result keeps
+ * three components (d0, d1, d2) and is relinearised by the next operation
+ * that needs two (rotation, convolution, matmul, the end of a dense layer,
+ * decryption) or by he_relinearize; a dense layer consumes it directly.
+ * Other polynomials return HE_E_UNIMPL.
  */
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree);
 
@@ -194,11 +197,13 @@ void he_ptset_free(he_ptset* pts);
  * inside each block by rotate-and-add over gap, 2 gap, ..., block_stride / 2,
  * then add bias[o] (NULL for none). Logit o of image b is at slot
  * b * block_stride of output o (he_decrypt_slots). Needs rotation keys for
- * those steps.
+ * those steps. Three-component inputs are summed component by component and
+ * the out_dim results relinearised.
  */
 int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const double* bias, he_ctset** out);
 
-/* he_fc: he_fc_prepare + he_fc_apply + he_ptset_free. */
+/* he_fc: he_fc_prepare + he_fc_apply + he_ptset_free. Inputs may have two or
+ * three components; the outputs are relinearised before the rotations. */
 int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int out_dim, int c_in, int h_valid,
           int w_in, int gap, int block_stride, int batch, he_ctset** out);
 
@@ -209,8 +214,13 @@ int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int
  * ciphertexts, [ct][step]. */
 int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps, he_ctset** out);
 
-/* Mul(a_i, b_i) pairwise: tensor product, relinearisation, rescale. */
+/* Mul(a_i, b_i) pairwise: tensor product and rescale; the result keeps three
+ * components until relinearised (see he_poly_act). */
 int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out);
+
+/* Three components -> two: key switch of d2 with the relinearisation key
+ * (no-op for two-component sets). */
+int he_relinearize(he_ctx* ctx, he_ctset* inout);
 
 /* Drop the last prime: round(x / q_l) in every limb; scale /= q_l. */
 int he_rescale(he_ctx* ctx, he_ctset* inout);
@@ -238,15 +248,17 @@ int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_strid
 
 /* ---- ciphertext sets ---- */
 
-/* Copy out as coefficient-domain limbs [n][2][limbs][N] (inverse NTT on the
- * device). n_words must be at least n * 2 * limbs * N. Synchronises. */
+/* Copy out as coefficient-domain limbs [n][polys][limbs][N] (inverse NTT on
+ * the device; polys from he_ctset_info). n_words must be at least
+ * n * polys * limbs * N. Synchronises. */
 int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words);
 
 /* Build a set from coefficient-domain limbs [n][2][limbs][N] (residues < q_i). */
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
 
-/* Number of ciphertexts, limbs (level + 1), scale. Any pointer may be NULL. */
-int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale);
+/* Number of ciphertexts, limbs (level + 1), scale, components per ciphertext
+ * (2, or 3 for an unrelinearised product). Any pointer may be NULL. */
+int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int* polys);
 
 /* Device address of the residues, [n][2][limbs][N] uint64 in the NTT domain. */
 int he_ctset_device_ptr(const he_ctset* set, uint64_t** dptr);

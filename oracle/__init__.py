@@ -68,13 +68,13 @@ def _lib():
             "oc_counters": (None, [V, _lp]),
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
-            "oc_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+            "oc_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip,
                                          ctypes.c_int, _u64p]),
             "oc_square": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, _u64p]),
             "oc_fc_plaintexts": (ctypes.c_int, [V, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _ip, _i64p]),
-            "oc_fc": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            "oc_fc": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      _i64p, _dp, ctypes.c_double, ctypes.c_int, _ip, _u64p]),
         }
         for name, (res, args) in sig.items():
@@ -293,9 +293,11 @@ class Oracle:
         return out
 
     def conv2d(self, X, gap: int, K, bias, stride: int, scale: float, sel=None, schedule: int = 0) -> np.ndarray:
-        """X [c_in][w_in][2][lp][N]; K [c_out][c_in][k][k] -> [n_sel][2][lp-1][N]."""
+        """X [c_in][w_in][2 or 3][lp][N]; K [c_out][c_in][k][k] -> [n_sel][2][lp-1][N].
+
+        Three-component inputs (unrelinearised products) are relinearised first."""
         X = _u64(X)
-        c_in, w_in, _, lp, _ = X.shape
+        c_in, w_in, polys, lp, _ = X.shape
         K = np.ascontiguousarray(K, dtype=np.float64)
         c_out, _, k, _ = K.shape
         w_out = (w_in - k) // stride + 1
@@ -304,15 +306,16 @@ class Oracle:
         sel_a = np.ascontiguousarray(np.array(sel, dtype=np.int32).reshape(-1, 2))
         b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
         out = np.zeros((len(sel), 2, lp - 1, self.N), np.uint64)
-        _check(self.lib.oc_conv2d(self.h, _p(X, _u64p), lp, c_in, w_in, gap, _p(K, _dp),
+        _check(self.lib.oc_conv2d(self.h, _p(X, _u64p), polys, lp, c_in, w_in, gap, _p(K, _dp),
                                   None if b is None else _p(b, _dp), c_out, k, stride, scale, len(sel),
                                   _p(sel_a, _ip), schedule, _p(out, _u64p)))
         return out
 
     def square(self, X) -> np.ndarray:
+        """Tensor product and rescale: [n][2][lp][N] -> [n][3][lp-1][N] (relinearised later)."""
         X = _u64(X)
         n, _, lp, _ = X.shape
-        out = np.zeros((n, 2, lp - 1, self.N), np.uint64)
+        out = np.zeros((n, 3, lp - 1, self.N), np.uint64)
         _check(self.lib.oc_square(self.h, _p(X, _u64p), n, lp, _p(out, _u64p)))
         return out
 
@@ -325,12 +328,13 @@ class Oracle:
         return out
 
     def fc(self, X, gap: int, H: int, pts, bias, scale: float, sel_o) -> np.ndarray:
+        """X [c_in][w_in][2 or 3][lp][N] -> [n_sel][2][lp-1][N]."""
         X = _u64(X)
-        c_in, w_in, _, lp, _ = X.shape
+        c_in, w_in, polys, lp, _ = X.shape
         pts = np.ascontiguousarray(pts, dtype=np.int64)
         sel = np.ascontiguousarray(sel_o, dtype=np.int32)
         b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
         out = np.zeros((len(sel), 2, lp - 1, self.N), np.uint64)
-        _check(self.lib.oc_fc(self.h, _p(X, _u64p), lp, c_in, w_in, gap, H, _p(pts, _i64p),
+        _check(self.lib.oc_fc(self.h, _p(X, _u64p), polys, lp, c_in, w_in, gap, H, _p(pts, _i64p),
                               None if b is None else _p(b, _dp), scale, len(sel), _p(sel, _ip), _p(out, _u64p)))
         return out

@@ -18,8 +18,8 @@
 //   idx computes D_idx = sum_k A_k (x) Rot(B~_k, idx): the SumColVec of Alg. 3
 //   over the n columns becomes n - 1 ciphertext additions, and slot i of
 //   D_idx is C[i][(i + idx) mod p]. The rotations of each B~_k share one
-//   ModUp; the n products of a round are summed as three-component tensors and
-//   relinearised once, then rescaled.
+//   ModUp; the n products of a round are summed as three-component tensors,
+//   rescaled, then relinearised once.
 //
 // Convolution (Alg. 4 over the column layout, channels summed as in Sec. IV-B):
 //   X_{c,j} holds column j of channel c, row r at slot g*r (row gap g) within
@@ -36,6 +36,12 @@
 //   holding W[o][c][i][j] at slots b*H + g*i; rescale; sum inside each block by
 //   rotate-and-add over g, 2g, ..., H/2 (SumRowVec-style, Sec. II-B); add the
 //   bias. The logit o of image b is at slot b*H of Z_o.
+//
+// Products and relinearisation: Mul (Sec. II-A) is the tensor product
+// followed by the rescale; the three-component result is relinearised only
+// when an operation needs two components (a rotation, the next product). The
+// dense layer is linear in each component, so a squared input enters its sum
+// with three components and only the out_dim results are relinearised.
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -50,6 +56,9 @@ namespace oracle {
 Ct ct_from(const Ctx& C, const u64* p, int n_polys, int limbs);
 void ct_to(const Ctx& C, const Ct& ct, u64* p);
 
+// Two components: relinearise a three-component ciphertext, pass others on.
+static Ct two_comp(Ctx& C, const Ct& x) { return x.c.size() == 3 ? ct_relin(C, x) : x; }
+
 // D_idx, idx < p, from A_k, B~_k (k < n), all at the same level.
 static std::vector<Ct> matmul(Ctx& C, const std::vector<Ct>& A, const std::vector<Ct>& B, int p) {
   const int n = (int)A.size();
@@ -63,7 +72,7 @@ static std::vector<Ct> matmul(Ctx& C, const std::vector<Ct>& A, const std::vecto
   for (int idx = 0; idx < p; idx++) {
     Ct T = ct_tensor(C, A[0], R[0][idx]);
     for (int k = 1; k < n; k++) T = ct_add(C, T, ct_tensor(C, A[k], R[k][idx]));
-    D[idx] = ct_rescale(C, ct_relin(C, T));
+    D[idx] = ct_relin(C, ct_rescale(C, T));
   }
   return D;
 }
@@ -92,7 +101,8 @@ static std::vector<Ct> conv2d(Ctx& C, const std::vector<std::vector<Ct>>& X, int
     for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
     std::vector<std::vector<Ct>> rot(needv.size());
 #pragma omp parallel for schedule(dynamic)
-    for (size_t t = 0; t < needv.size(); t++) rot[t] = ct_rotate_hoisted(C, X[needv[t].first][needv[t].second], steps);
+    for (size_t t = 0; t < needv.size(); t++)
+      rot[t] = ct_rotate_hoisted(C, two_comp(C, X[needv[t].first][needv[t].second]), steps);
     std::map<std::pair<int, int>, size_t> where;
     for (size_t t = 0; t < needv.size(); t++) where[needv[t]] = t;
 #pragma omp parallel for schedule(dynamic)
@@ -121,7 +131,7 @@ static std::vector<Ct> conv2d(Ctx& C, const std::vector<std::vector<Ct>>& X, int
         bool first = true;
         for (int c = 0; c < c_in; c++)
           for (int b = 0; b < k; b++) {
-            Ct term = ct_mul_scalar(C, X[c][stride * jp + b], quantise(kw(o, c, a, b), ql));
+            Ct term = ct_mul_scalar(C, two_comp(C, X[c][stride * jp + b]), quantise(kw(o, c, a, b), ql));
             part = first ? term : ct_add(C, part, term);
             first = false;
           }
@@ -136,8 +146,8 @@ static std::vector<Ct> conv2d(Ctx& C, const std::vector<std::vector<Ct>>& X, int
   return out;
 }
 
-// Square activation: tensor, relinearise, rescale.
-static Ct square(Ctx& C, const Ct& x) { return ct_rescale(C, ct_relin(C, ct_tensor(C, x, x))); }
+// Square activation: tensor, rescale; the result keeps three components.
+static Ct square(Ctx& C, const Ct& x) { return ct_rescale(C, ct_tensor(C, x, x)); }
 
 // Plaintext of FC weights for output o, input column (c, j): W[o][c][i][j] at
 // slot b*H + g*i for every block b < B and valid row i < hv, zero elsewhere,
@@ -155,13 +165,14 @@ static Ct fc_output(Ctx& C, const std::vector<std::vector<Ct>>& X, const std::ve
                     int gap, int H, double bias_o, bool has_bias, double scale) {
   const int c_in = (int)X.size(), w_in = (int)X[0].size();
   const int lp = X[0][0].limbs();
-  // sum_{c,j} pt (x) X, each product a negacyclic product per limb
+  const int P = (int)X[0][0].c.size();
+  // sum_{c,j} pt (x) X per component, each product a negacyclic product per limb
   Ct acc;
-  acc.c.assign(2, RnsPoly(lp, Poly(C.N, 0)));
+  acc.c.assign(P, RnsPoly(lp, Poly(C.N, 0)));
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < lp; i++) {
     const u64 q = C.q[i];
-    for (int t = 0; t < 2; t++) {
+    for (int t = 0; t < P; t++) {
       Poly sum(C.N, 0), x(C.N), y(C.N);
       for (int c = 0; c < c_in; c++)
         for (int j = 0; j < w_in; j++) {
@@ -177,7 +188,7 @@ static Ct fc_output(Ctx& C, const std::vector<std::vector<Ct>>& X, const std::ve
     }
   }
   C.cnt.ct_plain += (long)c_in * w_in;
-  Ct z = ct_rescale(C, acc);
+  Ct z = two_comp(C, ct_rescale(C, acc));
   for (int t = gap; t < H; t *= 2) z = ct_add(C, z, ct_rotate_hoisted(C, z, {(long)t})[0]);
   if (has_bias) z = ct_add_const(C, z, std::llround(bias_o * scale));
   return z;
@@ -197,13 +208,17 @@ static thread_local std::string g_lerr;
     return -1;                         \
   }
 
-static std::vector<Ct> cts_from(const Ctx& C, const uint64_t* p, int n, int limbs) {
+static std::vector<Ct> cts_from(const Ctx& C, const uint64_t* p, int n, int limbs, int polys = 2) {
   std::vector<Ct> v(n);
-  for (int t = 0; t < n; t++) v[t] = ct_from(C, p + (size_t)t * 2 * limbs * C.N, 2, limbs);
+  for (int t = 0; t < n; t++) v[t] = ct_from(C, p + (size_t)t * polys * limbs * C.N, polys, limbs);
   return v;
 }
 static void cts_to(const Ctx& C, const std::vector<Ct>& v, uint64_t* p) {
-  for (size_t t = 0; t < v.size(); t++) ct_to(C, v[t], p + t * 2 * v[t].limbs() * C.N);
+  size_t off = 0;
+  for (size_t t = 0; t < v.size(); t++) {
+    ct_to(C, v[t], p + off);
+    off += v[t].c.size() * v[t].limbs() * C.N;
+  }
 }
 
 extern "C" {
@@ -216,12 +231,14 @@ int oc_matmul(void* h, const uint64_t* A, const uint64_t* B, int n, int p, int l
          cts_to(*C, d, D));
 }
 
-// X [c_in][w_in][2][lp][N]; K [c_out][c_in][k][k]; bias [c_out] or NULL;
+// X [c_in][w_in][polys][lp][N] (polys 2, or 3 for unrelinearised products);
+// K [c_out][c_in][k][k]; bias [c_out] or NULL;
 // sel [n_sel][2] = (o, j'); out [n_sel][2][lp-1][N].
-int oc_conv2d(void* h, const uint64_t* X, int lp, int c_in, int w_in, int gap, const double* K, const double* bias,
-              int c_out, int k, int stride, double scale, int n_sel, const int* sel, int schedule, uint64_t* out) {
+int oc_conv2d(void* h, const uint64_t* X, int polys, int lp, int c_in, int w_in, int gap, const double* K,
+              const double* bias, int c_out, int k, int stride, double scale, int n_sel, const int* sel, int schedule,
+              uint64_t* out) {
   OL_TRY(Ctx* C = (Ctx*)h; std::vector<std::vector<Ct>> x(c_in);
-         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * 2 * lp * C->N, w_in, lp);
+         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * polys * lp * C->N, w_in, lp, polys);
          std::vector<std::pair<int, int>> s(n_sel);
          for (int t = 0; t < n_sel; t++) {
            s[t] = {sel[2 * t], sel[2 * t + 1]};
@@ -231,7 +248,7 @@ int oc_conv2d(void* h, const uint64_t* X, int lp, int c_in, int w_in, int gap, c
          cts_to(*C, r, out));
 }
 
-// x [n][2][lp][N] -> [n][2][lp-1][N]
+// x [n][2][lp][N] -> [n][3][lp-1][N]
 int oc_square(void* h, const uint64_t* X, int n, int lp, uint64_t* out) {
   try {
     Ctx* C = (Ctx*)h;
@@ -261,12 +278,12 @@ int oc_fc_plaintexts(void* h, int lp, int c_in, int hv, int w_in, int gap, int H
   return 0;
 }
 
-// X [c_in][w_in][2][lp][N]; pts [n_sel][c_in][w_in][N] from oc_fc_plaintexts;
+// X [c_in][w_in][polys][lp][N]; pts [n_sel][c_in][w_in][N] from oc_fc_plaintexts;
 // bias [out] or NULL; out [n_sel][2][lp-1][N].
-int oc_fc(void* h, const uint64_t* X, int lp, int c_in, int w_in, int gap, int H, const int64_t* pts,
+int oc_fc(void* h, const uint64_t* X, int polys, int lp, int c_in, int w_in, int gap, int H, const int64_t* pts,
           const double* bias, double scale, int n_sel, const int* sel_o, uint64_t* out) {
   OL_TRY(Ctx* C = (Ctx*)h; std::vector<std::vector<Ct>> x(c_in);
-         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * 2 * lp * C->N, w_in, lp);
+         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * polys * lp * C->N, w_in, lp, polys);
          for (int s = 0; s < n_sel; s++) {
            std::vector<std::vector<i64>> p((size_t)c_in * w_in);
            for (size_t t = 0; t < p.size(); t++) {

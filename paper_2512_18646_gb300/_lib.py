@@ -63,6 +63,7 @@ SIGNATURES = {
     "he_fc": (I, [V, V, P_D, P_D, I, I, I, I, I, I, I, PV]),
     "he_rotate": (I, [V, V, P_I32, I, PV]),
     "he_mul": (I, [V, V, V, PV]),
+    "he_relinearize": (I, [V, V]),
     "he_rescale": (I, [V, V]),
     "he_add": (I, [V, V, V, PV]),
     "he_decrypt_slots": (I, [V, V, P_D, SZ]),
@@ -70,7 +71,7 @@ SIGNATURES = {
     "he_decrypt_image": (I, [V, V, I, I, I, I, P_D, SZ]),
     "he_ctset_export": (I, [V, P_U64, SZ]),
     "he_ctset_import": (I, [V, P_U64, I, I, D, PV]),
-    "he_ctset_info": (I, [V, P_I, P_I, P_D]),
+    "he_ctset_info": (I, [V, P_I, P_I, P_D, P_I]),
     "he_ctset_device_ptr": (I, [V, ctypes.POINTER(P_U64)]),
     "he_ctset_slice": (I, [V, V, I, I, PV]),
     "he_ctset_concat": (I, [V, PV, I, PV]),

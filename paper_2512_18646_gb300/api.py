@@ -37,9 +37,18 @@ class CtSet:
             pass
 
     def info(self):
-        n, limbs, sc = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        check(load().he_ctset_info(self.h, ctypes.byref(n), ctypes.byref(limbs), ctypes.byref(sc)))
-        return n.value, limbs.value, sc.value
+        """(n, limbs, scale)."""
+        return self.info4()[:3]
+
+    def info4(self):
+        """(n, limbs, scale, polys)."""
+        n, limbs, sc, pol = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        check(load().he_ctset_info(self.h, ctypes.byref(n), ctypes.byref(limbs), ctypes.byref(sc), ctypes.byref(pol)))
+        return n.value, limbs.value, sc.value, pol.value
+
+    @property
+    def polys(self):
+        return self.info4()[3]
 
     @property
     def n(self):
@@ -54,9 +63,9 @@ class CtSet:
         return self.info()[2]
 
     def export(self) -> np.ndarray:
-        """Coefficient-domain limbs [n][2][limbs][N] (uint64)."""
-        n, limbs, _ = self.info()
-        out = np.zeros((n, 2, limbs, self.ctx.N), np.uint64)
+        """Coefficient-domain limbs [n][polys][limbs][N] (uint64)."""
+        n, limbs, _, polys = self.info4()
+        out = np.zeros((n, polys, limbs, self.ctx.N), np.uint64)
         check(load().he_ctset_export(self.h, _ptr(out, P_U64), out.size))
         return out
 
@@ -220,6 +229,10 @@ class Context:
 
     def add(self, a: CtSet, b: CtSet) -> CtSet:
         return self._set(load().he_add, self.h, a.h, b.h)
+
+    def relinearize(self, x: CtSet) -> CtSet:
+        check(load().he_relinearize(self.h, x.h))
+        return x
 
     def rescale(self, x: CtSet) -> CtSet:
         check(load().he_rescale(self.h, x.h))

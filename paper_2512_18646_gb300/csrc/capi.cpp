@@ -224,7 +224,7 @@ int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) 
     REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");
     REQUIRE(degree == 2 && coeffs[0] == 0.0 && coeffs[1] == 0.0 && coeffs[2] == 1.0, HE_E_UNIMPL,
             "only x -> x^2 is supported");
-    inout->s = square(ctx->c, *inout->s);
+    inout->s = square(ctx->c, *inout->s);  // three components until an operation needs two
   });
 }
 
@@ -388,12 +388,20 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
   });
 }
 
-int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale) {
+int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int* polys) {
   return guard([&] {
     REQUIRE(set, HE_E_ARG, "null set");
     if (n_ct) *n_ct = set->s->n;
     if (limbs) *limbs = set->s->limbs;
     if (scale) *scale = set->s->scale;
+    if (polys) *polys = set->s->polys;
+  });
+}
+
+int he_relinearize(he_ctx* ctx, he_ctset* inout) {
+  return guard([&] {
+    REQUIRE(ctx && inout, HE_E_ARG, "null argument");
+    relinearize(ctx->c, *inout->s);
   });
 }
 
@@ -411,7 +419,7 @@ int he_ctset_slice(he_ctx* ctx, const he_ctset* set, int first, int n, he_ctset*
     REQUIRE(first >= 0 && n >= 1 && first + n <= s.n, HE_E_ARG, "slice out of range");
     auto r = new_set(ctx->c, n, s.polys, s.limbs, s.scale);
     HE_CUDA(cudaMemcpyAsync(r->buf.p, s.ct(first), (size_t)n * s.ct_words() * 8, cudaMemcpyDeviceToDevice,
-                            ctx->c.stream));
+                            ctx->c.stream));  // any component count
     *out = wrap(std::move(r));
   });
 }

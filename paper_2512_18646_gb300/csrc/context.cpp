@@ -480,9 +480,16 @@ std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs
   return out;
 }
 
-void decrypt_slots(Ctx& C, const CtSet& s, double* out) {
+void decrypt_slots(Ctx& C, const CtSet& s_any, double* out) {
   if (!C.has_keys) throw Error(9, "no secret key in this context");
-  if (s.polys != 2) throw Error(1, "decrypt expects two-component ciphertexts");
+  std::unique_ptr<CtSet> hold;
+  if (s_any.polys == 3) {  // relinearise a copy first
+    hold = new_set(C, s_any.n, 3, s_any.limbs, s_any.scale);
+    HE_CUDA(cudaMemcpyAsync(hold->buf.p, s_any.buf.p, s_any.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+    relinearize(C, *hold);
+  }
+  const CtSet& s = hold ? *hold : s_any;
+  if (s.polys != 2) throw Error(1, "decrypt expects two- or three-component ciphertexts");
   const size_t N = C.N, M = N / 2;
   DevBuf m0((size_t)s.n * N, C.stream);
   k_decrypt_limb0(C, s.buf.p, s.limbs, s.n, m0.p);

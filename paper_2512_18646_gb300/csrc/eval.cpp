@@ -6,19 +6,22 @@
 //  - Rot(ct, l) (Sec. II-A): ModUp of c1 once per ciphertext; per step, the
 //    automorphism on every extended digit, inner product with the Galois key,
 //    ModDown; result (phi_k(c0) + v0, v1).
-//  - Mul (Sec. II-A): tensor product, relinearisation (key switch of d2), then
-//    rescale by the last prime.
+//  - Mul (Sec. II-A): tensor product, then rescale by the last prime; the
+//    three-component result is relinearised (key switch of d2) only when an
+//    operation needs two components: a rotation, a convolution input, a
+//    matmul operand, the end of a dense layer, decryption.
 //  - matmul (Alg. 3 over n ciphertexts per operand, Sec. IV-A): hoisted
 //    rotations of every B~_k by idx = 0..p-1 (RowShifter applied idx times
 //    equals Rot(., idx) under whole-ring period-p tiling, Sec. III-B); per idx
 //    the n tensor products summed as three components (the SumColVec of
-//    Alg. 3 becomes ciphertext additions), one relinearisation, one rescale.
+//    Alg. 3 becomes ciphertext additions), one rescale, one relinearisation.
 //  - conv (Alg. 4 over the column layout, Sec. IV-B): hoisted rotations of
 //    every input column by gap*a, a < k; output (o, j') =
 //    sum_{c,b,a} round(K[o][c][a][b] q_l) Rot(X_{c, s j' + b}, gap a);
 //    rescale; + round(bias_o * scale).
-//  - FC: sum_{c,j} pt_{o,c,j} X_{c,j}; rescale; rotate-and-add over
-//    gap, 2 gap, ..., block/2; + round(bias_o * scale).
+//  - FC: sum_{c,j} pt_{o,c,j} X_{c,j} component by component (two or three
+//    components); rescale; relinearise; rotate-and-add over gap, 2 gap, ...,
+//    block/2; + round(bias_o * scale).
 #include <cmath>
 #include <cstring>
 
@@ -109,8 +112,29 @@ void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vect
   ks_finish(C, in, ext, ks, 1, outs, cw * out_cts_per_ct);
 }
 
-std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps) {
-  if (in.polys != 2) throw Error(1, "rotation expects two-component ciphertexts");
+void relinearize(Ctx& C, CtSet& s) {
+  if (s.polys == 2) return;
+  if (s.polys != 3) throw Error(1, "relinearisation expects three-component ciphertexts");
+  auto out = new_set(C, s.n, 2, s.limbs, s.scale);
+  DevBuf ext = modup_poly(C, s, 2);
+  ks_finish(C, s, ext, {1}, 0, {out->buf.p}, out->ct_words());
+  ext.reset();
+  s.buf = std::move(out->buf);
+  s.polys = 2;
+}
+
+// A two-component view of `in`: the set itself, or a relinearised copy.
+static const CtSet& two_comp(Ctx& C, const CtSet& in, std::unique_ptr<CtSet>& hold) {
+  if (in.polys == 2) return in;
+  hold = new_set(C, in.n, in.polys, in.limbs, in.scale);
+  HE_CUDA(cudaMemcpyAsync(hold->buf.p, in.buf.p, in.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+  relinearize(C, *hold);
+  return *hold;
+}
+
+std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in_any, const std::vector<long>& steps) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& in = two_comp(C, in_any, hold);
   for (long s : steps)
     if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
   const int S = (int)steps.size();
@@ -143,36 +167,32 @@ void rescale_inplace(Ctx& C, CtSet& s) {
   s.scale = s.scale / (double)C.q[lp - 1];
 }
 
-std::unique_ptr<CtSet> relin_rescale(Ctx& C, const CtSet& d3) {
-  if (d3.polys != 3) throw Error(1, "relinearisation expects three-component ciphertexts");
-  auto out = new_set(C, d3.n, 2, d3.limbs, d3.scale);
-  DevBuf ext = modup_poly(C, d3, 2);
-  ks_finish(C, d3, ext, {1}, 0, {out->buf.p}, out->ct_words());
-  rescale_inplace(C, *out);
-  return out;
-}
 
 static void check_pair(const CtSet& a, const CtSet& b) {
   if (a.limbs != b.limbs) throw Error(4, "operands at different levels");
   if (a.scale != b.scale) throw Error(4, "operands at different scales");
 }
 
-std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b) {
-  if (a.n != b.n) throw Error(1, "sets of different sizes");
-  if (a.limbs != b.limbs) throw Error(4, "operands at different levels");
-  if (a.limbs < 2) throw Error(2, "no level left for a product");
+std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a_any, const CtSet& b_any) {
+  if (a_any.n != b_any.n) throw Error(1, "sets of different sizes");
+  if (a_any.limbs != b_any.limbs) throw Error(4, "operands at different levels");
+  if (a_any.limbs < 2) throw Error(2, "no level left for a product");
+  std::unique_ptr<CtSet> ha, hb;
+  const CtSet& a = two_comp(C, a_any, ha);
+  const CtSet& b = &b_any == &a_any ? a : two_comp(C, b_any, hb);
   auto d = new_set(C, a.n, 3, a.limbs, a.scale * b.scale);
   k_tensor(C, a.buf.p, b.buf.p, d->buf.p, a.n, a.limbs);
-  return relin_rescale(C, *d);
+  rescale_inplace(C, *d);
+  return d;
 }
 
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in) { return mul(C, in, in); }
 
 std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b) {
-  if (a.n != b.n) throw Error(1, "sets of different sizes");
+  if (a.n != b.n || a.polys != b.polys) throw Error(1, "sets of different sizes or component counts");
   check_pair(a, b);
-  auto out = new_set(C, a.n, 2, a.limbs, a.scale);
-  k_add(C, a.buf.p, b.buf.p, out->buf.p, a.n * 2, a.limbs);
+  auto out = new_set(C, a.n, a.polys, a.limbs, a.scale);
+  k_add(C, a.buf.p, b.buf.p, out->buf.p, a.n * a.polys, a.limbs);
   return out;
 }
 
@@ -189,8 +209,10 @@ static DevBuf const_table(Ctx& C, const double* v, int groups, int limbs, double
   return d;
 }
 
-std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
+std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& in = two_comp(C, in_any, hold);
   if (c_in < 1 || c_out < 1 || k < 1 || stride < 1 || gap < 1) throw Error(1, "bad convolution shape");
   if (in.n % c_in) throw Error(1, "input set size is not a multiple of c_in");
   const int w_in = in.n / c_in;
@@ -202,7 +224,7 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
   for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
   for (long s : steps)
     if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
-  auto rot = rotate(C, in, steps);  // [c][j][a]
+  auto rot = rotate(C, in, steps);  // [c][j][a]; `in` (maybe `hold`) is used below
   // integer weights round(K q_l) mod q_i with Shoup companions, [o][c][a][b][limb][2]
   const u64 ql = C.q[lp - 1];
   const size_t nw = (size_t)c_out * c_in * k * k;
@@ -229,7 +251,10 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
   return out;
 }
 
-std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p) {
+std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, int p) {
+  std::unique_ptr<CtSet> ha, hb;
+  const CtSet& A = two_comp(C, A_any, ha);
+  const CtSet& B = two_comp(C, B_any, hb);
   if (A.n != B.n || A.n < 1) throw Error(1, "A and B must have the same number n of ciphertexts");
   if (p < 1 || (C.N / 2) % (size_t)p) throw Error(1, "p must divide the slot count");
   if (A.limbs != B.limbs) throw Error(4, "operands at different levels");
@@ -254,7 +279,9 @@ std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p) {
   }
   R.reset();
   ext.reset();
-  return relin_rescale(C, *d);
+  rescale_inplace(C, *d);
+  relinearize(C, *d);
+  return d;
 }
 
 DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs) {
@@ -278,10 +305,11 @@ std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out
   const int lp = in.limbs;
   if (lp < 2) throw Error(2, "no level left for the dense layer");
   for (int t = gap; t < block_stride; t *= 2) C.key(C.galois_elt(t));
-  auto z = new_set(C, out_dim, 2, lp, in.scale);
-  k_fc_mac(C, in.buf.p, pts, z->buf.p, in.n, out_dim, lp);
+  auto z = new_set(C, out_dim, in.polys, lp, in.scale);
+  k_fc_mac(C, in.buf.p, pts, z->buf.p, in.n, out_dim, lp, in.polys);
   rescale_inplace(C, *z);
   z->scale = in.scale;  // plaintexts were encoded at scale q_l
+  relinearize(C, *z);
   for (int t = gap; t < block_stride; t *= 2) {
     auto r = rotate(C, *z, {(long)t});
     k_add(C, z->buf.p, r->buf.p, z->buf.p, z->n * 2, z->limbs);

@@ -32,6 +32,18 @@ HE_HD u64 mulhi64(u64 a, u64 b) {
 #endif
 }
 
+// Full 64 x 64 -> 128-bit product from four 32 x 32 -> 64-bit products (one
+// wide integer multiply-add each) and carry-free 64-bit additions:
+// a b = p11 2^64 + (p01 + p10) 2^32 + p00.
+HE_HD void mul128(u64 a, u64 b, u64& hi, u64& lo) {
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+  const u64 p00 = (u64)a0 * b0, p01 = (u64)a0 * b1, p10 = (u64)a1 * b0, p11 = (u64)a1 * b1;
+  const u64 mid = p01 + (p00 >> 32);            // < 2^64 - 2^32
+  const u64 mid2 = p10 + (mid & 0xffffffffull);  // < 2^64 - 2^32
+  lo = (mid2 << 32) | (p00 & 0xffffffffull);
+  hi = p11 + (mid >> 32) + (mid2 >> 32);
+}
+
 // A prime with its Barrett constant mu = floor(2^128 / q) = mu_hi 2^64 + mu_lo.
 struct Mod {
   u64 q, mu_hi, mu_lo;
@@ -42,8 +54,9 @@ struct Mod {
 // floor(x/q) - 3 <= qhat <= floor(x/q) and x - qhat q lies in [0, 4q).
 HE_HD u64 reduce128(u64 xh, u64 xl, const Mod& m) {
   const u64 t1 = mulhi64(xl, m.mu_lo);
-  const u64 p1l = xl * m.mu_hi, p1h = mulhi64(xl, m.mu_hi);
-  const u64 p2l = xh * m.mu_lo, p2h = mulhi64(xh, m.mu_lo);
+  u64 p1l, p1h, p2l, p2h;
+  mul128(xl, m.mu_hi, p1h, p1l);
+  mul128(xh, m.mu_lo, p2h, p2l);
   const u64 s = p1l + p2l;
   u64 c = s < p1l;
   const u64 s2 = s + t1;
@@ -57,14 +70,19 @@ HE_HD u64 reduce128(u64 xh, u64 xl, const Mod& m) {
 }
 
 // a b mod q for a b < q 2^64 (e.g. a < 2^64, b < q).
-HE_HD u64 mulmod(u64 a, u64 b, const Mod& m) { return reduce128(mulhi64(a, b), a * b, m); }
+HE_HD u64 mulmod(u64 a, u64 b, const Mod& m) {
+  u64 hi, lo;
+  mul128(a, b, hi, lo);
+  return reduce128(hi, lo, m);
+}
 
 // 128-bit accumulator for sums of products, reduced once.
 struct Acc128 {
   u64 hi, lo;
 };
 HE_HD void mac128(Acc128& acc, u64 a, u64 b) {
-  const u64 lo = a * b, hi = mulhi64(a, b);
+  u64 hi, lo;
+  mul128(a, b, hi, lo);
   acc.lo += lo;
   acc.hi += hi + (acc.lo < lo);
 }

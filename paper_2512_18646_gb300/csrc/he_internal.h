@@ -179,8 +179,8 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
                 int c_out, int w_out, int limbs);
 // matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx])
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
-// fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj]
-void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs);
+// fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
 // calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters);
 // number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad
@@ -206,7 +206,8 @@ DevBuf modup_c1(Ctx& C, const CtSet& in);
 void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<long>& steps, u64* out,
                      int out_cts_per_ct);
 std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps);
-std::unique_ptr<CtSet> relin_rescale(Ctx& C, const CtSet& d3);
+// three components -> two (key switch of d2 with the relinearisation key); no rescale
+void relinearize(Ctx& C, CtSet& s);
 void rescale_inplace(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);

@@ -173,10 +173,12 @@ __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int l
 //                             pos over {q_0..q_{limbs-1}, p_0..}
 // Each term [x_i (D_j/q_i)^{-1}]_{q_i} (D_j/q_i) is a Shoup product in [0, 2t)
 // (valid for any multiplicand below 2^64); partial sums stay below 2t.
-__global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alpha, int beta, int L1, int K,
+template <int ALPHA>
+__global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alpha_rt, int beta, int L1, int K,
                                const u64* up_inv, const u64* up_hat, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int nb = limbs + K;
+  const int alpha = ALPHA > 0 ? ALPHA : alpha_rt;
   const size_t total = (size_t)n * beta * N;
   const u64* inv = up_inv + (size_t)limbs * L1 * 2;
   const ulonglong2* hat = reinterpret_cast<const ulonglong2*>(up_hat) + (size_t)limbs * L1 * (L1 + K);
@@ -184,24 +186,32 @@ __global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alp
     const size_t jn = idx & (N - 1);
     const size_t r = idx >> log_n;
     const int dg = (int)(r % beta), c = (int)(r / beta);
-    const int lo = dg * alpha, hi = min(lo + alpha, limbs);
+    const int lo = dg * alpha, cnt = min(alpha, limbs - lo), hi = lo + cnt;
     const u64* X = x + (size_t)c * limbs * N;
     u64* E = ext + ((size_t)c * beta + dg) * nb * N;
-    u64 y[8];
-    for (int i = lo; i < hi; i++) {
-      const u64 xi = X[(size_t)i * N + jn];
-      y[i - lo] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
-      E[(size_t)i * N + jn] = xi;
+    u64 y[ALPHA > 0 ? ALPHA : 8];
+#pragma unroll
+    for (int ii = 0; ii < (ALPHA > 0 ? ALPHA : 8); ii++) {
+      if (ii < cnt) {
+        const int i = lo + ii;
+        const u64 xi = X[(size_t)i * N + jn];
+        y[ii] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
+        E[(size_t)i * N + jn] = xi;
+      }
     }
     for (int pos = 0; pos < nb; pos++) {
       if (pos >= lo && pos < hi) continue;
       const int g = pos < limbs ? pos : L1 + (pos - limbs);
       const u64 t = pt[g].mod.q, t2 = 2 * t;
+      const ulonglong2* hp = hat + (size_t)lo * (L1 + K) + pos;
       u64 s = 0;
-      for (int i = lo; i < hi; i++) {
-        const ulonglong2 h = __ldg(hat + (size_t)i * (L1 + K) + pos);
-        s += shoup_lazy(y[i - lo], h.x, h.y, t);
-        if (s >= t2) s -= t2;
+#pragma unroll
+      for (int ii = 0; ii < (ALPHA > 0 ? ALPHA : 8); ii++) {
+        if (ii < cnt) {
+          const ulonglong2 h = __ldg(hp + (size_t)ii * (L1 + K));
+          s += shoup_lazy(y[ii], h.x, h.y, t);
+          if (s >= t2) s -= t2;
+        }
       }
       E[(size_t)pos * N + jn] = s >= t ? s - t : s;
     }
@@ -478,12 +488,14 @@ __global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, i
   }
 }
 
-// out[o] = sum_cj pt[o][cj] X[cj]; X [n_in][2][limbs][N], pt [out_dim][n_in][limbs][N].
-// One thread per (limb, coefficient) handles both components, so every
-// plaintext word is read once. The loads of UN input columns are issued
-// before their products so that enough reads are in flight to stream the
-// plaintexts at memory speed; sums are reduced every 8 columns.
-template <int OB, int UN>
+// out[o] = sum_cj pt[o][cj] X[cj]; X [n_in][P][limbs][N], pt [out_dim][n_in][limbs][N],
+// out [out_dim][P][limbs][N], P = 2 or 3 components (products need not be
+// relinearised: the sum is linear in each component). One thread per (limb,
+// coefficient) handles every component, so each plaintext word is read once.
+// The loads of UN input columns are issued before their products so that
+// enough reads are in flight to stream the plaintexts at memory speed; sums
+// are reduced every 8 columns.
+template <int OB, int UN, int P>
 __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
                                 const PrimeTab* pt, int log_n) {
   static_assert(8 % UN == 0, "reduction every 8 columns");
@@ -493,17 +505,19 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
     const int i = (int)(w >> log_n);
     const Mod md = pt[i].mod;
     for (int o0 = 0; o0 < out_dim; o0 += OB) {
-      Acc128 a0[OB], a1[OB];
+      Acc128 acc[P][OB];
 #pragma unroll
-      for (int t = 0; t < OB; t++) a0[t] = a1[t] = Acc128{0, 0};
+      for (int c = 0; c < P; c++)
+#pragma unroll
+        for (int t = 0; t < OB; t++) acc[c][t] = Acc128{0, 0};
       for (int cj0 = 0; cj0 < n_in; cj0 += UN) {
-        u64 x0[UN], x1[UN], pv[UN][OB];
+        u64 xv[UN][P], pv[UN][OB];
 #pragma unroll
         for (int v = 0; v < UN; v++) {
           const int cj = cj0 + v;
           const bool ok = cj < n_in;
-          x0[v] = ok ? X[(size_t)cj * 2 * LN + w] : 0;
-          x1[v] = ok ? X[((size_t)cj * 2 + 1) * LN + w] : 0;
+#pragma unroll
+          for (int c = 0; c < P; c++) xv[v][c] = ok ? X[((size_t)cj * P + c) * LN + w] : 0;
 #pragma unroll
           for (int t = 0; t < OB; t++)
             pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * n_in + cj) * LN + w] : 0;
@@ -511,25 +525,22 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
 #pragma unroll
         for (int v = 0; v < UN; v++)
 #pragma unroll
-          for (int t = 0; t < OB; t++) {
-            mac128(a0[t], x0[v], pv[v][t]);
-            mac128(a1[t], x1[v], pv[v][t]);
-          }
+          for (int t = 0; t < OB; t++)
+#pragma unroll
+            for (int c = 0; c < P; c++) mac128(acc[c][t], xv[v][c], pv[v][t]);
         if (((cj0 + UN) & 7) == 0) {
 #pragma unroll
-          for (int t = 0; t < OB; t++) {
-            a0[t] = Acc128{0, reduce128(a0[t].hi, a0[t].lo, md)};
-            a1[t] = Acc128{0, reduce128(a1[t].hi, a1[t].lo, md)};
-          }
+          for (int c = 0; c < P; c++)
+#pragma unroll
+            for (int t = 0; t < OB; t++) acc[c][t] = Acc128{0, reduce128(acc[c][t].hi, acc[c][t].lo, md)};
         }
       }
 #pragma unroll
-      for (int t = 0; t < OB; t++) {
-        if (o0 + t < out_dim) {
-          out[((size_t)(o0 + t) * 2) * LN + w] = reduce128(a0[t].hi, a0[t].lo, md);
-          out[((size_t)(o0 + t) * 2 + 1) * LN + w] = reduce128(a1[t].hi, a1[t].lo, md);
-        }
-      }
+      for (int t = 0; t < OB; t++)
+        if (o0 + t < out_dim)
+#pragma unroll
+          for (int c = 0; c < P; c++)
+            out[((size_t)(o0 + t) * P + c) * LN + w] = reduce128(acc[c][t].hi, acc[c][t].lo, md);
     }
   }
 }
@@ -623,8 +634,23 @@ void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs) {
   if (C.alpha > 8) throw Error(8, "digits of more than 8 primes are not supported");
   const u64* up_inv = C.d_up.p;
   const u64* up_hat = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2;
-  HE_LAUNCH(k_modup_kernel, (size_t)n * C.beta_at(limbs) * C.N, 8.0 * (double)C.N * n * (limbs + (double)C.beta_at(limbs) * (limbs + C.K)), x, ext, n, limbs, C.alpha, C.beta_at(limbs), C.L1,
-            C.K, up_inv, up_hat, C.dev_ptab(), C.log_n);
+  const int beta = C.beta_at(limbs);
+  const size_t total = (size_t)n * beta * C.N;
+  const double bytes = 8.0 * (double)C.N * n * (limbs + (double)beta * (limbs + C.K));
+  switch (C.alpha) {
+    case 1:
+      HE_LAUNCH(k_modup_kernel<1>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+                C.dev_ptab(), C.log_n);
+      break;
+    case 2:
+      HE_LAUNCH(k_modup_kernel<2>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+                C.dev_ptab(), C.log_n);
+      break;
+    default:
+      HE_LAUNCH(k_modup_kernel<0>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+                C.dev_ptab(), C.log_n);
+      break;
+  }
 }
 void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u, int n, int limbs) {
   const int beta = C.beta_at(limbs);
@@ -719,12 +745,18 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
   HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p), A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
 }
-void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs) {
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
   const size_t total = (size_t)limbs * C.N;
-  const double bytes = 8.0 * (double)C.N * limbs * (2.0 * n_in + (double)out_dim * n_in + 2.0 * out_dim);
+  const double bytes = 8.0 * (double)C.N * limbs * ((double)polys * n_in + (double)out_dim * n_in + (double)polys * out_dim);
   void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes);
-  k_fc_mac_kernel<5, 4><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
-                                                                  C.log_n);
+  if (polys == 2)
+    k_fc_mac_kernel<5, 4, 2><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
+                                                                       C.log_n);
+  else if (polys == 3)
+    k_fc_mac_kernel<5, 4, 3><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
+                                                                       C.log_n);
+  else
+    throw Error(1, "dense layer inputs have two or three components");
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }

@@ -97,16 +97,22 @@ def test_rotation_matches_oracle(lib, params):
     assert np.abs(dz - np.roll(z, -1, axis=1)).max() < 1e-5
 
 
-def test_mul_relin_rescale_matches_oracle(lib):
+def test_mul_rescale_relin_matches_oracle(lib):
     o, g = make_pair(11, (60, 45, 45, 45, 45), 2, 60, 2, 45.0, seed=6, steps=[])
     rng = np.random.default_rng(4)
     x, y = rng.uniform(-1, 1, (4, o.slots)), rng.uniform(-1, 1, (4, o.slots))
     ox, gx = encrypt_both(o, g, encode_columns(o, x), ct_id_base=0)
     oy, gy = encrypt_both(o, g, encode_columns(o, y), ct_id_base=10)
-    gm = g.mul(gx, gy).export()
+    gm = g.mul(gx, gy)
+    assert gm.polys == 3  # Mul = tensor + rescale; relinearisation is deferred
+    m3 = gm.export()
     for c in range(4):
-        ref = o.rescale(o.relin(o.tensor(ox[c], oy[c])))
-        assert np.array_equal(gm[c], ref)
+        assert np.array_equal(m3[c], o.rescale(o.tensor(ox[c], oy[c])))
+    g.relinearize(gm)
+    m2 = gm.export()
+    for c in range(4):
+        assert np.array_equal(m2[c], o.relin(o.rescale(o.tensor(ox[c], oy[c]))))
+    assert np.abs(g.decrypt_slots(gm) - x * y).max() < 1e-5
     sq = g.square(gx).export()
     for c in range(4):
         assert np.array_equal(sq[c], o.square(ox[c:c + 1])[0])

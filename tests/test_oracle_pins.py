@@ -473,11 +473,11 @@ def test_cnn_small_matches_fp64():
     X = encrypt_images(o, imgs[:, None], H)
     sc = o.scale
     Y = o.conv2d(X, 1, c1w, c1b, 2, sc).reshape(2, h1, 2, -1, o.N)
-    Y = o.square(Y.reshape(-1, 2, Y.shape[-2], o.N)).reshape(2, h1, 2, -1, o.N)
+    Y = o.square(Y.reshape(-1, 2, Y.shape[-2], o.N)).reshape(2, h1, 3, -1, o.N)  # three components
     sc = sc * sc / o.q[X.shape[3] - 2]
     Y = o.conv2d(Y, 2, c2w, c2b, 2, sc).reshape(3, h2, 2, -1, o.N)
     lp = Y.shape[3]
-    Y = o.square(Y.reshape(-1, 2, lp, o.N)).reshape(3, h2, 2, lp - 1, o.N)
+    Y = o.square(Y.reshape(-1, 2, lp, o.N)).reshape(3, h2, 3, lp - 1, o.N)
     sc = sc * sc / o.q[lp - 1]
     pts = o.fc_plaintexts(lp - 1, 3, h2, h2, 4, H, Bn, fw, list(range(4)))
     Z = o.fc(Y, 4, H, pts, fb, sc, list(range(4)))
