@@ -148,8 +148,11 @@ int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, h
 
 /*
  * he_matmul_batched: `count` independent products A[i] B[i] (each as in
- * he_matmul, shapes m[i], p[i]) evaluated together; C[i] receives each
- * result.
+ * he_matmul, shapes m[i], p[i]; two-component operands) evaluated together;
+ * C[i] receives each result, identical to he_matmul's. Products with the same
+ * p and level share their ModUp and rotation launches (the B operands of a
+ * group are concatenated within a 48 GiB working-memory budget), so each key
+ * is read once per launch for all of them.
  */
 int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
                       const int* p, he_ctset** C);

@@ -201,12 +201,16 @@ int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he
                       const int* p, he_ctset** C_out) {
   return guard([&] {
     REQUIRE(ctx && A && B && m && p && C_out && count >= 0, HE_E_ARG, "null argument");
-    std::vector<std::unique_ptr<CtSet>> res(count);
+    std::vector<const CtSet*> As(count), Bs(count);
+    std::vector<int> ps(p, p + count);
     for (int i = 0; i < count; i++) {
       REQUIRE(A[i] && B[i], HE_E_ARG, "null operand");
       REQUIRE(A[i]->s->scale == B[i]->s->scale, HE_E_SCALE, "operands at different scales");
-      res[i] = matmul(ctx->c, *A[i]->s, *B[i]->s, p[i]);
+      REQUIRE(m[i] >= 1 && (size_t)m[i] <= ctx->c.N / 2, HE_E_ARG, "bad m");
+      As[i] = A[i]->s.get();
+      Bs[i] = B[i]->s.get();
     }
+    std::vector<std::unique_ptr<CtSet>> res = matmul_batched(ctx->c, As, Bs, ps);
     for (int i = 0; i < count; i++) C_out[i] = wrap(std::move(res[i]));
   });
 }

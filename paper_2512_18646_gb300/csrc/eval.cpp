@@ -24,6 +24,7 @@
 //    block/2; + round(bias_o * scale).
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "he_internal.h"
 
@@ -282,6 +283,89 @@ std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, in
   rescale_inplace(C, *d);
   relinearize(C, *d);
   return d;
+}
+
+// Independent products A_i B_i evaluated together. Matmuls with the same p
+// and level form a group; inside a group, sub-batches of matmuls whose B
+// operands fit the working-memory budget are concatenated into one set, so
+// one ModUp launch and one launch per chunk of rotation steps serve all of
+// them (each key tile is read once per launch for every ciphertext of the
+// sub-batch). Each matmul accumulates into its own three-component set; the
+// results are identical to separate matmul() calls.
+std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<const CtSet*>& As,
+                                                   const std::vector<const CtSet*>& Bs, const std::vector<int>& ps) {
+  const int cnt = (int)As.size();
+  std::vector<std::unique_ptr<CtSet>> out(cnt);
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int i = 0; i < cnt; i++) {
+    const CtSet& A = *As[i];
+    const CtSet& B = *Bs[i];
+    if (A.polys != 2 || B.polys != 2) throw Error(1, "batched matmul operands must have two components");
+    if (A.n != B.n || A.n < 1) throw Error(1, "A and B must have the same number n of ciphertexts");
+    if (ps[i] < 1 || (C.N / 2) % (size_t)ps[i]) throw Error(1, "p must divide the slot count");
+    if (A.limbs != B.limbs || A.scale != B.scale) throw Error(4, "operands at different levels or scales");
+    if (A.limbs < 2) throw Error(2, "no level left for the product");
+    for (int s = 1; s < ps[i]; s++) C.key(C.galois_elt(s));
+    groups[{ps[i], A.limbs}].push_back(i);
+  }
+  const size_t N = C.N;
+  const size_t budget = (size_t)6 << 30;  // words (48 GiB) of digits, rotated operands and key-switch scratch
+  for (auto& kv : groups) {
+    const int p = kv.first.first, lp = kv.first.second;
+    const std::vector<int>& members = kv.second;
+    const size_t cw = (size_t)2 * lp * N;
+    const size_t ext_ct = (size_t)C.beta_at(lp) * (lp + C.K) * N;
+    // words per ciphertext per rotation step: rotated operand, inner products, ModDown terms
+    const size_t step_ct = cw + (size_t)2 * (lp + C.K) * N + cw;
+    size_t m0 = 0;
+    while (m0 < members.size()) {
+      // sub-batch: as many matmuls as fit with at least 4 steps per chunk
+      std::vector<int> sb;
+      int ntot = 0;
+      for (size_t t = m0; t < members.size(); t++) {
+        const int nn = As[members[t]]->n;
+        if (!sb.empty() && (size_t)(ntot + nn) * (ext_ct + 4 * step_ct) > budget) break;
+        sb.push_back(members[t]);
+        ntot += nn;
+      }
+      m0 += sb.size();
+      auto Bcat = new_set(C, ntot, 2, lp, Bs[sb[0]]->scale);
+      std::vector<size_t> off(sb.size());
+      size_t o = 0;
+      for (size_t t = 0; t < sb.size(); t++) {
+        off[t] = o;
+        const CtSet& B = *Bs[sb[t]];
+        HE_CUDA(cudaMemcpyAsync(Bcat->ct((int)o), B.buf.p, B.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+        o += B.n;
+      }
+      DevBuf ext;
+      if (p > 1) ext = modup_c1(C, *Bcat);
+      std::vector<std::unique_ptr<CtSet>> d(sb.size());
+      for (size_t t = 0; t < sb.size(); t++)
+        d[t] = new_set(C, p, 3, lp, As[sb[t]]->scale * Bs[sb[t]]->scale);
+      const size_t room = budget > (size_t)ntot * ext_ct ? budget - (size_t)ntot * ext_ct : 0;
+      int chunk = (int)std::max<size_t>(1, room / ((size_t)ntot * step_ct));
+      if (chunk > p) chunk = p;
+      DevBuf R((size_t)ntot * chunk * cw, C.stream);
+      for (int i0 = 0; i0 < p; i0 += chunk) {
+        const int ci = std::min(chunk, p - i0);
+        std::vector<long> steps(ci);
+        for (int t = 0; t < ci; t++) steps[t] = i0 + t;
+        rotate_from_ext(C, *Bcat, ext, steps, R.p, ci);
+        for (size_t t = 0; t < sb.size(); t++)
+          k_matmul_acc(C, As[sb[t]]->buf.p, R.p + off[t] * ci * cw, d[t]->ct(i0), As[sb[t]]->n, ci, lp);
+      }
+      R.reset();
+      ext.reset();
+      Bcat.reset();
+      for (size_t t = 0; t < sb.size(); t++) {
+        rescale_inplace(C, *d[t]);
+        relinearize(C, *d[t]);
+        out[sb[t]] = std::move(d[t]);
+      }
+    }
+  }
+  return out;
 }
 
 DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs) {

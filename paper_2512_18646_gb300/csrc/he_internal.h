@@ -212,6 +212,8 @@ void rescale_inplace(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<const CtSet*>& As,
+                                                   const std::vector<const CtSet*>& Bs, const std::vector<int>& ps);
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in);
 std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b);

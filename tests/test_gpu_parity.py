@@ -273,3 +273,21 @@ def test_errors(lib):
     with pytest.raises(HeError) as e:
         api.Context(20, (60,), 1, 60, 1, 40.0)
     assert e.value.code == HE_E_ARG
+
+
+def test_matmul_batched_equals_single_matmuls(lib):
+    """Mixed shapes (some sharing p): batched results equal he_matmul's bit for bit, and GEMM."""
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=12, steps=list(range(1, 8)))
+    rng = np.random.default_rng(12)
+    shapes = [(4, 3, 8), (8, 5, 4), (2, 2, 8), (16, 1, 1), (5, 7, 4)]
+    As, Bs, ref = [], [], []
+    for t, (m, n, p) in enumerate(shapes):
+        A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+        As.append(g.encrypt_matrix_a(A, 1000 * t))
+        Bs.append(g.encrypt_matrix_b(Bm, 1000 * t + 500))
+        ref.append(A @ Bm)
+    outs = g.matmul_batched(As, Bs, [s[0] for s in shapes], [s[2] for s in shapes])
+    for t, (m, n, p) in enumerate(shapes):
+        single = g.matmul(As[t], Bs[t], m, p)
+        assert np.array_equal(outs[t].export(), single.export()), t
+        assert np.abs(g.decrypt_matrix(outs[t], m, p) - ref[t]).max() < 1e-5
