@@ -408,6 +408,148 @@ def run_matmul(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# the serving workload (--workload serve)
+# ---------------------------------------------------------------------------
+SERVE_METRIC = ("served encrypted-CNN images/s and p50/p99 latency (Poisson arrivals, image sides {64,128,256}, "
+                "N=2^16), continuous batching vs one request at a time")
+SERVE_SIDES = (64, 128, 256)
+
+
+def _replay(srv, pool, arrival_s, sides, out_buf):
+    """Submit request i at arrival_s[i] (seconds after the start) from a client thread; claim each
+    result as soon as it is done (he_server_take_host into page-locked host memory).
+
+    Returns per request: (scheduled arrival, submit, admit, start, done, claimed), ms of CLOCK_MONOTONIC."""
+    import queue
+    n = len(arrival_s)
+    ids = queue.Queue()
+    t0 = time.monotonic() + 0.05
+
+    def client():
+        for i in range(n):
+            dt = t0 + arrival_s[i] - time.monotonic()
+            if dt > 0:
+                time.sleep(dt)
+            ptr, words = pool[int(sides[i])][i % len(pool[int(sides[i])])]
+            try:
+                ids.put((i, srv.submit_ptr(ptr, words, int(sides[i]))))
+            except Exception as e:  # refused (e.g. budget): reported by the claiming loop
+                ids.put((i, e))
+                return
+
+    th = threading.Thread(target=client)
+    th.start()
+    rec = np.zeros((n, 6))
+    pending = {}
+    claimed = 0
+    deadline = time.monotonic() + 600 + float(arrival_s[-1])
+    while claimed < n:
+        while True:
+            try:
+                i, rid = ids.get_nowait()
+            except queue.Empty:
+                break
+            if isinstance(rid, Exception):
+                th.join()
+                raise rid
+            pending[rid] = i
+        done = [rid for rid in pending if srv.poll(rid) >= 3]
+        for rid in done:
+            i = pending.pop(rid)
+            blk, t = srv.take_host(rid, out_buf)
+            rec[i, 0] = 1e3 * (t0 + arrival_s[i])
+            rec[i, 1:5] = t
+            rec[i, 5] = 1e3 * time.monotonic()
+            claimed += 1
+        if not done:
+            if time.monotonic() > deadline:
+                raise RuntimeError("requests not served within the deadline")
+            time.sleep(0.001)
+    th.join()
+    return rec
+
+
+def run_serve(args, rank, world, local_rank):
+    """A Poisson stream of encrypted CNN requests against the continuous-batching server and against
+    the same server limited to one request per batch (plain FIFO, one request at a time)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api, load
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    pre = synthetic.CNN_N16
+    g = api.Context.from_preset(pre, seed=5000 + rank)
+    g.keygen([])
+    w = {s: synthetic.cnn_weights(s, seed=302) for s in SERVE_SIDES}
+    n_warm, n_meas = args.serve_warmup, args.requests
+    arrival, side = synthetic.poisson_trace(n_warm + n_meas, rate=args.rate)
+    # a pool of encrypted requests per side, each image repeated in every slot block, in page-locked memory
+    pool, keep = {}, []
+    t_enc = time.perf_counter()
+    for s in SERVE_SIDES:
+        pool[s] = []
+        for k in range(args.pool):
+            img = synthetic.images(1, s, s, seed=600 + 7 * k + s)[0]
+            x = g.encrypt_image(np.repeat(img[None], g.slots // s, axis=0), s, ct_id_base=10 ** 6 * (k + 1) + s)
+            buf = torch.empty(s * 2 * g.L1 * g.N, dtype=torch.int64).pin_memory()
+            arr = buf.numpy().view(np.uint64)
+            x.export_raw(arr)
+            del x
+            keep.append(buf)
+            pool[s].append((arr.ctypes.data, arr.size))
+    g.synchronize()
+    t_enc = time.perf_counter() - t_enc
+    out_words = 10 * 2 * (g.L1 - 6) * g.N
+    out_buf = torch.empty(out_words, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    res = {"encrypt_pool_s": t_enc}
+    for mode, max_blocks, n_req in (("batched", args.max_blocks, n_meas), ("plain", 1, args.plain_requests)):
+        t_c = time.perf_counter()
+        srv = api.Server(g, w, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_blocks=max_blocks)
+        create_s = time.perf_counter() - t_c
+        # warm-up: the first n_warm requests of the trace (untimed)
+        _replay(srv, pool, arrival[:n_warm] - arrival[0], side[:n_warm], out_buf)
+        l0 = lib.he_kernel_launches()
+        arr = arrival[n_warm:n_warm + n_req]
+        rec = _replay(srv, pool, arr - arr[0], side[n_warm:n_warm + n_req], out_buf)
+        launches = lib.he_kernel_launches() - l0
+        st = srv.stats()
+        srv.close()
+        lat = rec[:, 4] - rec[:, 0]
+        e2e_lat = rec[:, 5] - rec[:, 0]
+        span = (rec[:, 4].max() - rec[:, 0].min()) / 1e3
+        span_e2e = (rec[:, 5].max() - rec[:, 0].min()) / 1e3
+        res[mode] = {
+            "requests": n_req, "images_per_s": n_req / span, "e2e_images_per_s": n_req / span_e2e,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "e2e_p99_ms": float(np.percentile(e2e_lat, 99)),
+            "queue_p50_ms": float(np.percentile(rec[:, 3] - rec[:, 0], 50)),
+            "submit_jitter_p99_ms": float(np.percentile(rec[:, 1] - rec[:, 0], 99)),
+            "batches": st["batches"], "reserve_gb": st["reserve_bytes"] / 2 ** 30,
+            "max_held_gb": st["max_held_bytes"] / 2 ** 30, "pool_high_gb": st["pool_high_bytes"] / 2 ** 30,
+            "create_s": create_s, "launches": launches,
+            "h2d_bytes": int(sum(int(s) * 2 * g.L1 * g.N * 8 for s in side[n_warm:n_warm + n_req])),
+            "d2h_bytes": int(n_req * out_words * 8),
+        }
+    # accuracy: one request per side through the batched server, against the FP64 CNN (untimed)
+    srv = api.Server(g, w, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_blocks=args.max_blocks,
+                     start_paused=True)
+    from oracle import fp64_ref  # FP64 closed form, used only for the accuracy check outside timing
+    rids = {s: srv.submit_ptr(*pool[s][0], s) for s in SERVE_SIDES}
+    srv.pause(False)
+    err = 0.0
+    for s, rid in rids.items():
+        srv.wait(rid, 600_000)
+        z, blk, _ = srv.take(rid)
+        logit = g.decrypt_slots(z)[:, blk * s]
+        img = synthetic.images(1, s, s, seed=600 + s)[0]
+        err = max(err, float(np.abs(logit - fp64_ref.cnn(img[None], w[s])[0]).max()))
+    srv.close()
+    res["max_abs_err"] = err
+    return res
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle: a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 KS_PER_INFERENCE = 128 * 4 + 496 + 496 * 2 + 480 + 10 * 5  # rotations + relinearisations of one step
@@ -450,8 +592,16 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cnn", "matmul"], default="cnn")
+    ap.add_argument("--workload", choices=["cnn", "matmul", "serve"], default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
+    ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
+    ap.add_argument("--serve-warmup", type=int, default=20, help="serve workload: warm-up requests")
+    ap.add_argument("--plain-requests", type=int, default=40,
+                    help="serve workload: requests replayed on the one-at-a-time path (a prefix of the trace)")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve workload: Poisson arrival rate (req/s)")
+    ap.add_argument("--max-blocks", type=int, default=128, help="serve workload: requests per batch")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve workload: device-memory budget")
+    ap.add_argument("--pool", type=int, default=2, help="serve workload: distinct encrypted images per side")
     args = ap.parse_args()
     rank, world, local_rank = rank_info()
     if world > 1:
@@ -473,6 +623,28 @@ def main():
                     "plain_value": res["plain_value"], "plain_ms": res["plain_ms"], "gpu_launches": res["launches"],
                     "max_abs_err_vs_fp64": res["max_abs_err"], "keygen_s": res["keygen_s"], "waves": res["waves"],
                     "rotations": res["rotations"], "tensor_products": res["tensors"]}
+            print(json.dumps(line))
+        return
+
+    if args.workload == "serve" and args.impl == "gpu":
+        res = run_serve(args, rank, world, local_rank)
+        if rank == 0:
+            b, p = res["batched"], res["plain"]
+            line = {"metric": SERVE_METRIC, "value": b["images_per_s"], "unit": "images/s", "n_gpus": world,
+                    "steps": b["requests"], "warmup": args.serve_warmup, "ms_per_step": 1e3 / b["images_per_s"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                    "data": "synthetic",
+                    "config": {"workload": f"Poisson stream ({args.rate} req/s, seeds 501/502) of encrypted CNN "
+                                           "requests (conv5x5s2(8)-x^2-conv3x3s2(16)-x^2-fc10), square image side "
+                                           "uniform over {64,128,256}; N=2^16, Q=60+12x45, P=2x60, alpha=2",
+                               "max_blocks": args.max_blocks, "budget_gb": args.budget_gb,
+                               "parallelism": f"replicas x{world}"},
+                    "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
+                    "plain": p, "batched": b, "gpu_launches": b["launches"],
+                    "e2e": {"value": b["e2e_images_per_s"], "unit": "images/s",
+                            "h2d_bytes_per_step": b["h2d_bytes"] // b["requests"],
+                            "d2h_bytes_per_step": b["d2h_bytes"] // b["requests"]},
+                    "max_abs_err_vs_fp64": res["max_abs_err"], "encrypt_pool_s": res["encrypt_pool_s"]}
             print(json.dumps(line))
         return
 

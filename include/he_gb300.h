@@ -93,6 +93,13 @@ int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n);
 /* Ring degree exponent, prime counts, digit size, scale. Any pointer may be NULL. */
 int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* alpha, double* scale);
 
+/* Bound, in bytes, on the device temporaries of one convolution,
+ * relinearisation, ciphertext product or rescale: larger sets are processed
+ * in chunks of ciphertexts (convolutions: of output columns, with the input
+ * columns each chunk needs) with the same per-ciphertext arithmetic, so the
+ * results do not change. 0 (the default) means no bound. */
+int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes);
+
 /*
  * he_keygen: draw the ternary secret s, the public key (-a s + e, a) over Q,
  * the relinearisation key (s^2 -> s) and one Galois key per rotation step
@@ -259,6 +266,16 @@ int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words);
 /* Build a set from coefficient-domain limbs [n][2][limbs][N] (residues < q_i). */
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
 
+/* Copy out the device words as held, [n][polys][limbs][N] in the NTT domain
+ * (no transform). n_words must be at least n * polys * limbs * N.
+ * Synchronises. */
+int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words);
+
+/* Build a set of two-component ciphertexts from NTT-domain words
+ * [n][2][limbs][N] as he_ctset_export_raw writes them; every residue is
+ * checked to be below its prime (HE_E_ARG otherwise). */
+int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
+
 /* Number of ciphertexts, limbs (level + 1), scale, components per ciphertext
  * (2, or 3 for an unrelinearised product). Any pointer may be NULL. */
 int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int* polys);
@@ -302,6 +319,165 @@ void he_ctset_free(he_ctset* set);
  */
 int he_rescale_noalloc(he_ctx* ctx, const uint64_t* in, int n_ct, int limbs, double scale, uint64_t* out,
                        double* out_scale);
+
+/*
+ * he_pack_blocks: several images per ciphertext set (Sec. III-D): out =
+ * rescale(sum_t masks_t * sets_t), ciphertext by ciphertext. Each set holds n
+ * two-component ciphertexts at the same level and scale; masks is a plaintext
+ * set prepared by he_fc_prepare_coeffs with out_dim >= n_sets, c_in = w_in = 1
+ * and limbs = the sets' level, mask t encoded at scale q_{limbs-1} (1 on the
+ * slots set t keeps, 0 elsewhere). The result is at one level lower and the
+ * sets' scale. Errors: HE_E_ARG (shapes), HE_E_SCALE, HE_E_LEVEL.
+ */
+int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const he_ptset* masks, he_ctset** out);
+
+/* ---- serving: continuous batching of encrypted CNN requests ---- */
+
+/*
+ * A server answers encrypted inference requests for the three-layer CNN of
+ * the evaluation (conv 8x5x5 stride 2 -> x^2 -> conv 16x3x3 stride 2 -> x^2
+ * -> dense 10; Sec. IV-C uses the same conv / square / dense structure) on
+ * square images of the sides it was created for, all on one context (one
+ * GPU, one key set kept in device memory).
+ *
+ * Request layout: a side x side image as `side` ciphertexts (column j holds
+ * the column's pixels, Sec. I-C), fresh at the top level and the context's
+ * scale, with the image repeated in every slot block of stride `side`
+ * (he_encrypt_image with batch = (N/2)/side copies of the image and
+ * block_stride = side), exported as the device words [side][2][n_q][N]
+ * (he_ctset_export_raw). Requests are batched by slot blocks, the paper's
+ * several images per ciphertext (Sec. III-D): request t of a batch is kept in
+ * block t by a 0/1 plaintext mask, the masked requests are summed into one
+ * set, rescaled once (one level: a request uses 6 of the n_q - 1 levels), and
+ * the network runs once for the whole batch.
+ *
+ * Scheduling (one worker thread per server): requests are admitted to device
+ * memory in submission order while the bytes of admitted requests and
+ * unclaimed results plus a reserve for one running batch stay within
+ * hbm_budget_bytes; the oldest waiting request blocks later ones. When the
+ * GPU is free the next batch takes the image side of the oldest admitted
+ * request and up to max_blocks admitted requests of that side, oldest first.
+ * Requests that arrive while a batch runs are admitted (memory permitting)
+ * and copied to the device on the server's own stream, overlapping the
+ * batch, and join the next batch. The reserve is measured at creation by
+ * running one batch per side on an all-zero request (the stream-ordered
+ * allocator's high-water mark), plus 1/16.
+ *
+ * Results: logit o of a request is slot block*side of ciphertext o of its
+ * result set (10 ciphertexts; decrypt with he_decrypt_slots). Decrypted
+ * results are the same alone and in any mix, up to CKKS noise.
+ */
+typedef struct he_server he_server;
+
+#define HE_REQ_WAITING 0   /* in host memory, not admitted yet  */
+#define HE_REQ_ADMITTED 1  /* copied (or being copied) to the device */
+#define HE_REQ_RUNNING 2   /* in the batch on the GPU           */
+#define HE_REQ_DONE 3      /* result ready for he_server_take   */
+#define HE_REQ_FAILED 4    /* he_server_take reports the error  */
+
+typedef struct {
+  const double* conv1_w;         /* [8][1][5][5]                               */
+  const double* conv1_b;         /* [8]                                        */
+  const double* conv2_w;         /* [16][8][3][3]                              */
+  const double* conv2_b;         /* [16]                                       */
+  int n_sides;                   /* number of image sides served               */
+  const int* sides;              /* [n_sides], powers of two in [16, N/2]      */
+  const double* const* fc_w;     /* per side: [10][16 h2 h2], h2 the spatial
+                                    size after both convs, (c, i, j) order     */
+  const double* const* fc_b;     /* per side: [10]                             */
+  size_t hbm_budget_bytes;       /* device bytes for requests, results and the
+                                    running batch (keys and tables excluded)  */
+  int max_blocks;                /* requests per batch (1 = one at a time)     */
+  int start_paused;              /* nonzero: no batch starts before
+                                    he_server_pause(srv, 0)                    */
+} he_server_desc;
+
+/*
+ * he_server_create: build the masks and dense-layer plaintexts of every side,
+ * add the rotation keys the network needs (he_keygen semantics), measure the
+ * batch reserve, and start the worker. The weights are copied. Needs n_q >= 7.
+ * Lowers the context's work budget (he_ctx_set_work_budget) to at most
+ * 16 GiB, so that batches leave room for requests.
+ * Errors: HE_E_ARG (sides, null weights), HE_E_LEVEL, HE_E_OOM, HE_E_CUDA.
+ * While a server runs, do not call he_keygen on its context or destroy the
+ * context; other calls on the context may come from any thread, and their
+ * GPU work queues on the context stream with the server's batches.
+ */
+int he_server_create(he_ctx* ctx, const he_server_desc* desc, he_server** out);
+
+/* Words of one request of this side: side * 2 * n_q * N. */
+int he_server_request_words(const he_server* srv, int side, size_t* n_words);
+
+/*
+ * he_server_submit: queue a request (layout above). host_words is borrowed
+ * until the request is DONE or FAILED and should be page-locked so its upload
+ * overlaps the running batch. Host work only (the server's uploader thread
+ * copies admitted requests); returns at once with the request id.
+ * Errors: HE_E_ARG (side not served, wrong size), HE_E_OOM (the request alone
+ * exceeds the budget).
+ */
+int he_server_submit(he_server* srv, const uint64_t* host_words, size_t n_words, int side, uint64_t* req_id);
+
+/* Current HE_REQ_* state of a request not yet taken. */
+int he_server_poll(he_server* srv, uint64_t req_id, int* state);
+
+/* Wait up to timeout_ms for a request to be DONE or FAILED (*state gets its
+ * state). HE_E_TIMEOUT if it is not. */
+int he_server_wait(he_server* srv, uint64_t req_id, int timeout_ms, int* state);
+
+/*
+ * he_server_take: claim a DONE request's result, a copy of its batch's 10
+ * logit ciphertexts (free with he_ctset_free), and forget the request. The
+ * copy runs on the server's result stream.
+ * block: its slot block. times_ms (may be NULL): [submit, admit, start of its
+ * batch, end of its batch] in milliseconds of the host's monotonic clock
+ * (CLOCK_MONOTONIC). HE_E_STATE if not done; HE_E_CUDA (with the message)
+ * for a failed request, which is forgotten too.
+ */
+int he_server_take(he_server* srv, uint64_t req_id, he_ctset** logits, int* block, double* times_ms);
+
+/* Words of one result: the 10 logit ciphertexts, 10 * 2 * (n_q - 6) * N. */
+int he_server_result_words(const he_server* srv, size_t* n_words);
+
+/*
+ * he_server_take_host: he_server_take into host memory: the result's device
+ * words as held ([10][2][n_q - 6][N], NTT domain; he_ctset_import_raw at
+ * n_q - 6 limbs and the context's scale rebuilds the set). The copy runs on
+ * the server's result stream, so it does not wait for the running batch;
+ * page-locked memory makes it a direct transfer. n_words >= the result words.
+ */
+int he_server_take_host(he_server* srv, uint64_t req_id, uint64_t* host, size_t n_words, int* block,
+                        double* times_ms);
+
+/* Hold (paused != 0) or resume starting batches; a running batch finishes. */
+int he_server_pause(he_server* srv, int paused);
+
+/*
+ * counts[6]: submitted, waiting (host), admitted (on the device, not
+ * running), done, failed, batches started. bytes[4]: budgeted bytes held now,
+ * the most ever held, the batch reserve, the allocator's high-water mark
+ * (including keys and tables). Either may be NULL.
+ */
+int he_server_stats(he_server* srv, uint64_t* counts, size_t* bytes);
+
+/* Stop the worker after its running batch and free everything the server
+ * holds; result sets already taken stay valid. */
+void he_server_destroy(he_server* srv);
+
+/*
+ * he_sched_simulate: the server's scheduler on a simulated GPU (no device
+ * work), for checking the policy. Request i arrives at arrival_ms[i]
+ * (ascending) with image side[i] and bytes[i]; a batch of T requests of
+ * side sides[s] takes base_ms[s] + per_request_ms[s] * T; a batch's result
+ * (out_bytes) is claimed when the batch ends. Outputs per request: batch
+ * number (-1 if it can never fit the budget), slot block, and the admit /
+ * start / done times (-1 if rejected); *max_held the most budgeted bytes ever
+ * held (may be NULL).
+ */
+int he_sched_simulate(int n, const double* arrival_ms, const int* side, const size_t* bytes, int n_sides,
+                      const int* sides, const double* base_ms, const double* per_request_ms, size_t budget,
+                      size_t reserve, int max_blocks, size_t out_bytes, int64_t* batch, int* block,
+                      double* admit_ms, double* start_ms, double* done_ms, size_t* max_held);
 
 /* ---- transforms (testing) ---- */
 

@@ -28,6 +28,17 @@ class ParamsDesc(ctypes.Structure):
                 ("log_scale", ctypes.c_double), ("sigma", ctypes.c_double)]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("conv1_w", ctypes.POINTER(ctypes.c_double)), ("conv1_b", ctypes.POINTER(ctypes.c_double)),
+                ("conv2_w", ctypes.POINTER(ctypes.c_double)), ("conv2_b", ctypes.POINTER(ctypes.c_double)),
+                ("n_sides", ctypes.c_int), ("sides", ctypes.POINTER(ctypes.c_int)),
+                ("fc_w", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("fc_b", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("max_blocks", ctypes.c_int), ("start_paused", ctypes.c_int)]
+
+
+HE_REQ_WAITING, HE_REQ_ADMITTED, HE_REQ_RUNNING, HE_REQ_DONE, HE_REQ_FAILED = range(5)
+
 V = ctypes.c_void_p
 PV = ctypes.POINTER(ctypes.c_void_p)
 I = ctypes.c_int
@@ -47,6 +58,7 @@ SIGNATURES = {
     "he_ctx_synchronize": (I, [V]),
     "he_ctx_primes": (I, [V, P_U64, I]),
     "he_ctx_info": (I, [V, P_I, P_I, P_I, P_I, P_D]),
+    "he_ctx_set_work_budget": (I, [V, SZ]),
     "he_keygen": (I, [V, P_I32, I]),
     "he_encrypt_image": (I, [V, P_D, I, I, I, I, U64, PV]),
     "he_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
@@ -61,6 +73,7 @@ SIGNATURES = {
     "he_ptset_free": (None, [V]),
     "he_fc_apply": (I, [V, V, V, P_D, PV]),
     "he_fc": (I, [V, V, P_D, P_D, I, I, I, I, I, I, I, PV]),
+    "he_pack_blocks": (I, [V, PV, I, V, PV]),
     "he_rotate": (I, [V, V, P_I32, I, PV]),
     "he_mul": (I, [V, V, V, PV]),
     "he_relinearize": (I, [V, V]),
@@ -71,12 +84,27 @@ SIGNATURES = {
     "he_decrypt_image": (I, [V, V, I, I, I, I, P_D, SZ]),
     "he_ctset_export": (I, [V, P_U64, SZ]),
     "he_ctset_import": (I, [V, P_U64, I, I, D, PV]),
+    "he_ctset_export_raw": (I, [V, P_U64, SZ]),
+    "he_ctset_import_raw": (I, [V, P_U64, I, I, D, PV]),
     "he_ctset_info": (I, [V, P_I, P_I, P_D, P_I]),
     "he_ctset_device_ptr": (I, [V, ctypes.POINTER(P_U64)]),
     "he_ctset_slice": (I, [V, V, I, I, PV]),
     "he_ctset_concat": (I, [V, PV, I, PV]),
     "he_ctset_free": (None, [V]),
     "he_rescale_noalloc": (I, [V, V, I, I, D, V, P_D]),
+    "he_server_create": (I, [V, ctypes.POINTER(ServerDesc), PV]),
+    "he_server_request_words": (I, [V, I, ctypes.POINTER(SZ)]),
+    "he_server_submit": (I, [V, V, SZ, I, P_U64]),
+    "he_server_poll": (I, [V, U64, P_I]),
+    "he_server_wait": (I, [V, U64, I, P_I]),
+    "he_server_take": (I, [V, U64, PV, P_I, P_D]),
+    "he_server_result_words": (I, [V, ctypes.POINTER(SZ)]),
+    "he_server_take_host": (I, [V, U64, V, SZ, P_I, P_D]),
+    "he_server_pause": (I, [V, I]),
+    "he_server_stats": (I, [V, P_U64, ctypes.POINTER(SZ)]),
+    "he_server_destroy": (None, [V]),
+    "he_sched_simulate": (I, [I, P_D, P_I, ctypes.POINTER(SZ), I, P_I, P_D, P_D, SZ, SZ, I, SZ, P_I64, P_I, P_D,
+                              P_D, P_D, ctypes.POINTER(SZ)]),
     "he_ntt": (I, [V, P_U64, I, I, I, I]),
     "he_calibrate_modmul": (I, [V, P_D]),
     "he_kernel_launches": (U64, []),

@@ -7,7 +7,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from ._lib import P_D, P_I, P_I32, P_I64, P_U64, ParamsDesc, check, load
+from ._lib import HE_E_TIMEOUT, P_D, P_I, P_I32, P_I64, P_U64, ParamsDesc, ServerDesc, check, load
 
 
 def _ptr(a: np.ndarray, t):
@@ -69,6 +69,15 @@ class CtSet:
         check(load().he_ctset_export(self.h, _ptr(out, P_U64), out.size))
         return out
 
+    def export_raw(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """The device words as held, [n][polys][limbs][N] uint64 in the NTT domain."""
+        n, limbs, _, polys = self.info4()
+        if out is None:
+            out = np.zeros((n, polys, limbs, self.ctx.N), np.uint64)
+        assert out.dtype == np.uint64 and out.flags.c_contiguous and out.size >= n * polys * limbs * self.ctx.N
+        check(load().he_ctset_export_raw(self.h, _ptr(out, P_U64), out.size))
+        return out
+
     def device_ptr(self) -> int:
         p = P_U64()
         check(load().he_ctset_device_ptr(self.h, ctypes.byref(p)))
@@ -122,6 +131,10 @@ class Context:
     def from_preset(cls, preset, seed: int = 1, stream: Optional[int] = None):
         return cls(preset.log_n, preset.q_bits, preset.n_special, preset.special_bits, preset.alpha,
                    preset.log_scale, preset.sigma, seed, stream)
+
+    def set_work_budget(self, nbytes: int):
+        """Bound the device temporaries of one operation (0 = none); results do not change."""
+        check(load().he_ctx_set_work_budget(self.h, int(nbytes)))
 
     def synchronize(self):
         check(load().he_ctx_synchronize(self.h))
@@ -220,6 +233,11 @@ class Context:
         b = None if bias is None else _f64(bias)
         return self._set(load().he_fc_apply, self.h, x.h, pts.h, None if b is None else _ptr(b, P_D))
 
+    def pack_blocks(self, sets: Sequence[CtSet], masks: PtSet) -> CtSet:
+        """rescale(sum_t masks_t * sets_t) (he_pack_blocks)."""
+        arr = (ctypes.c_void_p * len(sets))(*[s.h.value for s in sets])
+        return self._set(load().he_pack_blocks, self.h, arr, len(sets), masks.h)
+
     def rotate(self, x: CtSet, steps: Sequence[int]) -> CtSet:
         st = (ctypes.c_int32 * len(steps))(*steps)
         return self._set(load().he_rotate, self.h, x.h, st, len(steps))
@@ -245,6 +263,12 @@ class Context:
         check(load().he_decrypt_slots(self.h, x.h, _ptr(out, P_D), out.size))
         return out
 
+    def import_raw(self, words, limbs: int, scale: float) -> CtSet:
+        """A set from NTT-domain words [n][2][limbs][N] (as CtSet.export_raw writes them)."""
+        a = np.ascontiguousarray(words, dtype=np.uint64)
+        n = a.size // (2 * limbs * self.N)
+        return self._set(load().he_ctset_import_raw, self.h, _ptr(a, P_U64), n, limbs, float(scale))
+
     def decrypt_matrix(self, C: CtSet, m: int, p: int) -> np.ndarray:
         out = np.zeros((m, p), np.float64)
         check(load().he_decrypt_matrix(self.h, C.h, m, p, _ptr(out, P_D)))
@@ -262,3 +286,140 @@ class Context:
         a3 = a.reshape(-1, shp[-2] if a.ndim >= 2 else 1, self.N)
         check(load().he_ntt(self.h, _ptr(a3, P_U64), a3.shape[0], a3.shape[1], first_prime, int(inverse)))
         return a3.reshape(shp)
+
+
+class Server:
+    """he_server: continuous batching of encrypted CNN requests (include/he_gb300.h).
+
+    Requests are host arrays of uint64 words (page-locked ones let the upload
+    overlap the running batch); each must stay alive until its request is
+    done, which this class guarantees by holding a reference until take()."""
+
+    def __init__(self, ctx: Context, weights_by_side, hbm_budget_bytes: int, max_blocks: int,
+                 start_paused: bool = False):
+        """weights_by_side: {side: CnnWeights}; the conv layers of the first entry serve every side."""
+        sides = sorted(weights_by_side)
+        w0 = weights_by_side[sides[0]]
+        self._keep = [_f64(w0.conv1_w), _f64(w0.conv1_b), _f64(w0.conv2_w), _f64(w0.conv2_b)]
+        fcw = [_f64(weights_by_side[s].fc_w) for s in sides]
+        fcb = [_f64(weights_by_side[s].fc_b) for s in sides]
+        self._keep += fcw + fcb
+        PD = ctypes.POINTER(ctypes.c_double)
+        self._fcw = (PD * len(sides))(*[_ptr(a, PD) for a in fcw])
+        self._fcb = (PD * len(sides))(*[_ptr(a, PD) for a in fcb])
+        self._sides = (ctypes.c_int * len(sides))(*sides)
+        d = ServerDesc(_ptr(self._keep[0], PD), _ptr(self._keep[1], PD), _ptr(self._keep[2], PD),
+                       _ptr(self._keep[3], PD), len(sides), self._sides, self._fcw, self._fcb,
+                       int(hbm_budget_bytes), int(max_blocks), int(start_paused))
+        h = ctypes.c_void_p()
+        check(load().he_server_create(ctx.h, ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self.sides = sides
+        self._held = {}
+
+    def request_words(self, side: int) -> int:
+        n = ctypes.c_size_t()
+        check(load().he_server_request_words(self.h, side, ctypes.byref(n)))
+        return n.value
+
+    def submit(self, words: np.ndarray, side: int) -> int:
+        assert words.dtype == np.uint64 and words.flags.c_contiguous
+        rid = ctypes.c_uint64()
+        check(load().he_server_submit(self.h, ctypes.c_void_p(words.ctypes.data), words.size, side,
+                                      ctypes.byref(rid)))
+        self._held[rid.value] = words
+        return rid.value
+
+    def submit_ptr(self, ptr: int, n_words: int, side: int) -> int:
+        """Submit from a raw host address (e.g. page-locked memory); the caller keeps it alive."""
+        rid = ctypes.c_uint64()
+        check(load().he_server_submit(self.h, ctypes.c_void_p(ptr), n_words, side, ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = ctypes.c_int()
+        check(load().he_server_poll(self.h, rid, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, rid: int, timeout_ms: int) -> bool:
+        """True once the request is done or failed, False if timeout_ms passed first."""
+        st = ctypes.c_int()
+        rc = load().he_server_wait(self.h, rid, int(timeout_ms), ctypes.byref(st))
+        if rc == HE_E_TIMEOUT:
+            return False
+        check(rc)
+        return True
+
+    def take(self, rid: int):
+        """(logits CtSet, slot block, times_ms [submit, admit, start, done])."""
+        out = ctypes.c_void_p()
+        blk = ctypes.c_int()
+        t = np.zeros(4, np.float64)
+        try:
+            check(load().he_server_take(self.h, rid, ctypes.byref(out), ctypes.byref(blk), _ptr(t, P_D)))
+        finally:
+            self._held.pop(rid, None)
+        return CtSet(self.ctx, out.value), blk.value, t
+
+    def result_words(self) -> int:
+        n = ctypes.c_size_t()
+        check(load().he_server_result_words(self.h, ctypes.byref(n)))
+        return n.value
+
+    def take_host(self, rid: int, out: np.ndarray):
+        """Result words into `out` (uint64, page-locked for a direct copy): (slot block, times_ms)."""
+        assert out.dtype == np.uint64 and out.flags.c_contiguous
+        blk = ctypes.c_int()
+        t = np.zeros(4, np.float64)
+        try:
+            check(load().he_server_take_host(self.h, rid, ctypes.c_void_p(out.ctypes.data), out.size,
+                                             ctypes.byref(blk), _ptr(t, P_D)))
+        finally:
+            self._held.pop(rid, None)
+        return blk.value, t
+
+    def pause(self, on: bool):
+        check(load().he_server_pause(self.h, int(on)))
+
+    def stats(self):
+        c = np.zeros(6, np.uint64)
+        b = (ctypes.c_size_t * 4)()
+        check(load().he_server_stats(self.h, _ptr(c, P_U64), b))
+        keys = ("submitted", "waiting", "admitted", "done", "failed", "batches")
+        out = {k: int(v) for k, v in zip(keys, c)}
+        out.update(held_bytes=b[0], max_held_bytes=b[1], reserve_bytes=b[2], pool_high_bytes=b[3])
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().he_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sched_simulate(arrival_ms, side, nbytes, sides, base_ms, per_request_ms, budget: int, reserve: int,
+                   max_blocks: int, out_bytes: int = 0):
+    """he_sched_simulate: the server's scheduler on a simulated GPU. Returns a dict of per-request arrays."""
+    n = len(arrival_ms)
+    arr = _f64(arrival_ms)
+    sd = np.ascontiguousarray(side, dtype=np.int32)
+    nb = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    ss = np.ascontiguousarray(sides, dtype=np.int32)
+    bm, pm = _f64(base_ms), _f64(per_request_ms)
+    batch = np.zeros(n, np.int64)
+    block = np.zeros(n, np.int32)
+    adm, st, dn = np.zeros(n), np.zeros(n), np.zeros(n)
+    mh = ctypes.c_size_t()
+    SZP = ctypes.POINTER(ctypes.c_size_t)
+    check(load().he_sched_simulate(n, _ptr(arr, P_D), _ptr(sd, P_I), _ptr(nb, SZP), len(ss), _ptr(ss, P_I),
+                                   _ptr(bm, P_D), _ptr(pm, P_D), int(budget), int(reserve), int(max_blocks),
+                                   int(out_bytes), _ptr(batch, P_I64), _ptr(block, P_I), _ptr(adm, P_D),
+                                   _ptr(st, P_D), _ptr(dn, P_D), ctypes.byref(mh)))
+    return dict(batch=batch, block=block, admit_ms=adm, start_ms=st, done_ms=dn, max_held=mh.value)

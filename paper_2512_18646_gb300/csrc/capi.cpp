@@ -44,22 +44,6 @@ static int guard(F f) {
 
 static bool pow2(long x) { return x > 0 && (x & (x - 1)) == 0; }
 
-template <class F>
-static void host_parallel(size_t n, F f) {
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt == 0) nt = 1;
-  if (nt > 16) nt = 16;
-  if (n < 2 || nt == 1) {
-    for (size_t i = 0; i < n; i++) f(i);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; t++)
-    th.emplace_back([&, t] {
-      for (size_t i = t; i < n; i += nt) f(i);
-    });
-  for (auto& x : th) x.join();
-}
 
 // Encode slot vectors z [n][M] (host) at scale and encrypt at the top level.
 static std::unique_ptr<CtSet> encrypt_slots(Ctx& C, const std::vector<double>& z, int n, u64 id_base) {
@@ -309,6 +293,24 @@ int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int
   return rc;
 }
 
+int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const he_ptset* masks, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && sets && masks && out && n_sets >= 1, HE_E_ARG, "null argument");
+    const CtSet& s0 = *sets[0]->s;
+    std::vector<const u64*> xs;
+    for (int t = 0; t < n_sets; t++) {
+      REQUIRE(sets[t], HE_E_ARG, "null set");
+      const CtSet& s = *sets[t]->s;
+      REQUIRE(s.n == s0.n && s.polys == 2, HE_E_ARG, "sets of different sizes or three-component sets");
+      REQUIRE(s.limbs == s0.limbs && s.scale == s0.scale, HE_E_SCALE, "sets at different levels or scales");
+      xs.push_back(s.buf.p);
+    }
+    REQUIRE(masks->n_in == 1 && masks->out_dim >= n_sets && masks->limbs == s0.limbs, HE_E_ARG,
+            "masks must be prepared as [n_sets][1] plaintexts at the sets' level");
+    *out = wrap(pack_blocks(ctx->c, xs, s0.n, s0.limbs, s0.scale, masks->buf.p));
+  });
+}
+
 int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps, he_ctset** out) {
   return guard([&] {
     REQUIRE(ctx && in && steps && out && n_steps >= 1, HE_E_ARG, "bad arguments");
@@ -389,6 +391,28 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
   return guard([&] {
     REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
     *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale));
+  });
+}
+
+int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    ctx->c.work_budget = bytes;
+  });
+}
+
+int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words) {
+  return guard([&] {
+    REQUIRE(set && host, HE_E_ARG, "null argument");
+    REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
+    export_raw(*set->s->ctx, *set->s, host);
+  });
+}
+
+int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
+    *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale, true));
   });
 }
 

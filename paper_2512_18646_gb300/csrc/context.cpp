@@ -483,11 +483,7 @@ std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs
 void decrypt_slots(Ctx& C, const CtSet& s_any, double* out) {
   if (!C.has_keys) throw Error(9, "no secret key in this context");
   std::unique_ptr<CtSet> hold;
-  if (s_any.polys == 3) {  // relinearise a copy first
-    hold = new_set(C, s_any.n, 3, s_any.limbs, s_any.scale);
-    HE_CUDA(cudaMemcpyAsync(hold->buf.p, s_any.buf.p, s_any.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
-    relinearize(C, *hold);
-  }
+  if (s_any.polys == 3) hold = relinearized(C, s_any);  // a relinearised copy
   const CtSet& s = hold ? *hold : s_any;
   if (s.polys != 2) throw Error(1, "decrypt expects two- or three-component ciphertexts");
   const size_t N = C.N, M = N / 2;
@@ -517,7 +513,12 @@ void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
   HE_CUDA(cudaStreamSynchronize(C.stream));
 }
 
-std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale) {
+void export_raw(Ctx& C, const CtSet& s, u64* host) {
+  HE_CUDA(cudaMemcpyAsync(host, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+}
+
+std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale, bool ntt_domain) {
   if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
   auto s = new_set(C, n, 2, limbs, scale);
   upload(C, s->buf.p, host, s->buf.words * 8);
@@ -529,7 +530,7 @@ std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, 
   HE_CUDA(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
   if (nbad) throw Error(1, std::to_string(nbad) + " residues out of range");
-  ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
+  if (!ntt_domain) ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
   return s;
 }
 

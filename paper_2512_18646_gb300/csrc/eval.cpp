@@ -113,13 +113,53 @@ void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vect
   ks_finish(C, in, ext, ks, 1, outs, cw * out_cts_per_ct);
 }
 
-void relinearize(Ctx& C, CtSet& s) {
-  if (s.polys == 2) return;
+// Ciphertexts [first, first + n) of a set, without owning their memory.
+struct SetView {
+  CtSet s;
+  SetView(const CtSet& src, int first, int n) {
+    s.ctx = src.ctx;
+    s.n = n;
+    s.polys = src.polys;
+    s.limbs = src.limbs;
+    s.scale = src.scale;
+    s.buf.p = src.ct(first);
+    s.buf.words = (size_t)n * src.ct_words();
+    s.buf.st = src.buf.st;
+  }
+  ~SetView() {
+    s.buf.p = nullptr;
+    s.buf.words = 0;
+  }
+  SetView(const SetView&) = delete;
+  SetView& operator=(const SetView&) = delete;
+};
+
+// Items per chunk when each item needs `bytes_per_item` of temporaries.
+static int chunk_items(const Ctx& C, int n_items, double bytes_per_item) {
+  if (C.work_budget == 0 || bytes_per_item <= 0) return std::max(n_items, 1);
+  const double k = std::floor((double)C.work_budget / bytes_per_item);
+  return (int)std::max(1.0, std::min((double)n_items, k));
+}
+
+std::unique_ptr<CtSet> relinearized(Ctx& C, const CtSet& s) {
   if (s.polys != 3) throw Error(1, "relinearisation expects three-component ciphertexts");
   auto out = new_set(C, s.n, 2, s.limbs, s.scale);
-  DevBuf ext = modup_poly(C, s, 2);
-  ks_finish(C, s, ext, {1}, 0, {out->buf.p}, out->ct_words());
-  ext.reset();
+  const int lp = s.limbs, nb = lp + C.K, beta = C.beta_at(lp);
+  // per ciphertext: the d2 copy, its ModUp digits, the key sums, their P part, the ModDown result
+  const double per = 8.0 * C.N * (lp + (double)beta * nb + 2.0 * nb + 2.0 * C.K + 2.0 * lp);
+  const int step = chunk_items(C, s.n, per);
+  for (int c0 = 0; c0 < s.n; c0 += step) {
+    const int cn = std::min(step, s.n - c0);
+    SetView v(s, c0, cn);
+    DevBuf ext = modup_poly(C, v.s, 2);
+    ks_finish(C, v.s, ext, {1}, 0, {out->ct(c0)}, out->ct_words());
+  }
+  return out;
+}
+
+void relinearize(Ctx& C, CtSet& s) {
+  if (s.polys == 2) return;
+  auto out = relinearized(C, s);
   s.buf = std::move(out->buf);
   s.polys = 2;
 }
@@ -127,9 +167,7 @@ void relinearize(Ctx& C, CtSet& s) {
 // A two-component view of `in`: the set itself, or a relinearised copy.
 static const CtSet& two_comp(Ctx& C, const CtSet& in, std::unique_ptr<CtSet>& hold) {
   if (in.polys == 2) return in;
-  hold = new_set(C, in.n, in.polys, in.limbs, in.scale);
-  HE_CUDA(cudaMemcpyAsync(hold->buf.p, in.buf.p, in.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
-  relinearize(C, *hold);
+  hold = relinearized(C, in);
   return *hold;
 }
 
@@ -148,21 +186,29 @@ std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in_any, const std::vector<lon
   return out;
 }
 
-void rescale_inplace(Ctx& C, CtSet& s) {
-  const int lp = s.limbs;
-  if (lp < 2) throw Error(2, "no level left to rescale");
-  const int rows = s.n * s.polys;
+// rows polynomials of lp limbs (x) -> rescaled polynomials of lp - 1 limbs (out)
+static void rescale_rows(Ctx& C, const u64* x, int rows, int lp, u64* out) {
   const size_t N = C.N;
   DevBuf last((size_t)rows * N, C.stream);
-  k_copy_limbs(C, s.buf.p + (size_t)(lp - 1) * N, (size_t)lp * N, last.p, N, (size_t)rows, 1);
+  k_copy_limbs(C, x + (size_t)(lp - 1) * N, (size_t)lp * N, last.p, N, (size_t)rows, 1);
   LimbMap lm1;
   lm1.lpp = 1; lm1.split = 1; lm1.base0 = lp - 1; lm1.base1 = 0; lm1.poly_stride = N;
   ntt_inverse(C, last.p, rows, lm1);
   DevBuf r((size_t)rows * (lp - 1) * N, C.stream);
   k_rescale_expand(C, last.p, r.p, rows, lp);
   ntt_forward(C, r.p, rows, limbs_q(lp - 1, N));
+  k_rescale_combine(C, x, r.p, out, rows, lp);
+}
+
+void rescale_inplace(Ctx& C, CtSet& s) {
+  const int lp = s.limbs;
+  if (lp < 2) throw Error(2, "no level left to rescale");
+  const int rows = s.n * s.polys;
+  const size_t N = C.N;
   DevBuf out((size_t)rows * (lp - 1) * N, C.stream);
-  k_rescale_combine(C, s.buf.p, r.p, out.p, rows, lp);
+  const int step = chunk_items(C, rows, 8.0 * N * lp);
+  for (int r0 = 0; r0 < rows; r0 += step)
+    rescale_rows(C, s.buf.p + (size_t)r0 * lp * N, std::min(step, rows - r0), lp, out.p + (size_t)r0 * (lp - 1) * N);
   s.buf = std::move(out);
   s.limbs = lp - 1;
   s.scale = s.scale / (double)C.q[lp - 1];
@@ -181,10 +227,18 @@ std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a_any, const CtSet& b_any) {
   std::unique_ptr<CtSet> ha, hb;
   const CtSet& a = two_comp(C, a_any, ha);
   const CtSet& b = &b_any == &a_any ? a : two_comp(C, b_any, hb);
-  auto d = new_set(C, a.n, 3, a.limbs, a.scale * b.scale);
-  k_tensor(C, a.buf.p, b.buf.p, d->buf.p, a.n, a.limbs);
-  rescale_inplace(C, *d);
-  return d;
+  const int lp = a.limbs;
+  const size_t N = C.N;
+  auto out = new_set(C, a.n, 3, lp - 1, (a.scale * b.scale) / (double)C.q[lp - 1]);
+  // per ciphertext: the three tensor components and the rescale temporaries
+  const int step = chunk_items(C, a.n, 8.0 * N * (3.0 * lp + 3.0 * lp));
+  for (int c0 = 0; c0 < a.n; c0 += step) {
+    const int cn = std::min(step, a.n - c0);
+    DevBuf d((size_t)cn * 3 * lp * N, C.stream);
+    k_tensor(C, a.ct(c0), b.ct(c0), d.p, cn, lp);
+    rescale_rows(C, d.p, cn * 3, lp, out->ct(c0));
+  }
+  return out;
 }
 
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in) { return mul(C, in, in); }
@@ -225,7 +279,6 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
   for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
   for (long s : steps)
     if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
-  auto rot = rotate(C, in, steps);  // [c][j][a]; `in` (maybe `hold`) is used below
   // integer weights round(K q_l) mod q_i with Shoup companions, [o][c][a][b][limb][2]
   const u64 ql = C.q[lp - 1];
   const size_t nw = (size_t)c_out * c_in * k * k;
@@ -241,8 +294,36 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
   DevBuf dw(wt.size(), C.stream);
   HE_CUDA(cudaMemcpyAsync(dw.p, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice, C.stream));
   auto out = new_set(C, c_out * w_out, 2, lp, in.scale);
-  k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp);
-  rot.reset();
+  // temporaries per input ciphertext: a gathered copy, its k rotations, its ModUp digits and, per
+  // non-trivial step, the key sums, their P part and the ModDown result
+  int S = 0;
+  for (long s : steps) S += C.galois_elt(s) != 1;
+  const int nb = lp + C.K, beta = C.beta_at(lp);
+  const double per_ct = 8.0 * C.N * (2.0 * lp + 2.0 * k * lp + (double)beta * nb + S * (2.0 * nb + 2.0 * C.K + 2.0 * lp));
+  // output columns per chunk: a chunk of wc columns reads (wc - 1) stride + k input columns per channel
+  const int max_span = chunk_items(C, w_in, per_ct * c_in);
+  const int wc = max_span >= w_in ? w_out : std::max(1, (max_span - k) / stride + 1);
+  if (wc >= w_out) {
+    auto rot = rotate(C, in, steps);  // [c][j][a]
+    k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp);
+  } else {
+    const size_t cw = in.ct_words();
+    for (int j0 = 0; j0 < w_out; j0 += wc) {
+      const int jn = std::min(wc, w_out - j0), span = (jn - 1) * stride + k, first = j0 * stride;
+      auto part = new_set(C, c_in * span, 2, lp, in.scale);
+      for (int c = 0; c < c_in; c++)
+        HE_CUDA(cudaMemcpyAsync(part->ct(c * span), in.ct(c * w_in + first), (size_t)span * cw * 8,
+                                cudaMemcpyDeviceToDevice, C.stream));
+      auto rot = rotate(C, *part, steps);
+      part.reset();
+      DevBuf oc((size_t)c_out * jn * cw, C.stream);
+      k_conv_mac(C, rot->buf.p, oc.p, dw.p, c_in, span, k, stride, c_out, jn, lp);
+      rot.reset();
+      for (int o = 0; o < c_out; o++)
+        HE_CUDA(cudaMemcpyAsync(out->ct(o * w_out + j0), oc.p + (size_t)o * jn * cw, (size_t)jn * cw * 8,
+                                cudaMemcpyDeviceToDevice, C.stream));
+    }
+  }
   rescale_inplace(C, *out);
   out->scale = in.scale;  // scalars were encoded at scale q_l, which the rescale removes
   if (bias) {
@@ -403,6 +484,21 @@ std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out
     k_add_const(C, z->buf.p, z->n, z->limbs, cb.p, 1);
   }
   return z;
+}
+
+std::unique_ptr<CtSet> pack_blocks(Ctx& C, const std::vector<const u64*>& xs, int n_ct, int limbs, double scale,
+                                   const u64* masks) {
+  const int T = (int)xs.size();
+  if (T < 1 || n_ct < 1) throw Error(1, "nothing to pack");
+  if (limbs < 2) throw Error(2, "packing needs one level");
+  DevBuf dxs((size_t)T, C.stream);
+  // pageable source: the call returns once the pointers are staged
+  HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)T * 8, cudaMemcpyHostToDevice, C.stream));
+  auto x = new_set(C, n_ct, 2, limbs, scale);
+  k_pack_blocks(C, (const u64* const*)dxs.p, masks, T, n_ct, limbs, x->buf.p);
+  rescale_inplace(C, *x);
+  x->scale = scale;  // the masks were encoded at scale q_l
+  return x;
 }
 
 }  // namespace he

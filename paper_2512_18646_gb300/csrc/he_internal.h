@@ -20,6 +20,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "he_arith.cuh"
@@ -95,6 +96,10 @@ struct Ctx {
   DevBuf d_up;                // ModUp constants, see modup_table()
   DevBuf d_down;              // ModDown constants
   DevBuf d_rs;                // rescale constants [L1][L1][3]
+  // bound on the temporaries of one convolution, relinearisation, product or
+  // rescale (bytes; 0 = none): larger sets are processed in ciphertext chunks
+  // with the same per-ciphertext arithmetic
+  size_t work_budget = 0;
 
   // keys
   bool has_keys = false;
@@ -181,6 +186,8 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
+// slot-block packing: out[j] = sum_t masks[t] * xs[t][j] ([n_ct][2][limbs][N]); xs is a device array of T pointers
+void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out);
 // calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters);
 // number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad
@@ -197,7 +204,11 @@ std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale
 std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs, double scale, u64 id_base);
 void decrypt_slots(Ctx& C, const CtSet& s, double* out);
 void export_coeffs(Ctx& C, const CtSet& s, u64* host);
-std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale);
+// device words as held (NTT domain) to host
+void export_raw(Ctx& C, const CtSet& s, u64* host);
+// [n][2][limbs][N] residues, coefficient domain (or already NTT domain), range-checked
+std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale,
+                                     bool ntt_domain = false);
 
 // ModUp of polynomial 1 of every ciphertext: ext [n][beta][limbs+K][N], NTT domain
 DevBuf modup_c1(Ctx& C, const CtSet& in);
@@ -208,6 +219,7 @@ void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vect
 std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& steps);
 // three components -> two (key switch of d2 with the relinearisation key); no rescale
 void relinearize(Ctx& C, CtSet& s);
+std::unique_ptr<CtSet> relinearized(Ctx& C, const CtSet& s);
 void rescale_inplace(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);
@@ -220,6 +232,28 @@ std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
                                 const double* bias);
 DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs);
+// rescale(sum_t masks[t] * X_t): T sets of n_ct two-component ciphertexts at `limbs` limbs
+// (device pointers xs[t]), masks [T][limbs][N] encoded at scale q_{limbs-1}; result at `scale`
+std::unique_ptr<CtSet> pack_blocks(Ctx& C, const std::vector<const u64*>& xs, int n_ct, int limbs, double scale,
+                                   const u64* masks);
+
+// f(0) .. f(n-1) on up to 16 host threads (independent items)
+template <class F>
+void host_parallel(size_t n, F f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 16) nt = 16;
+  if (n < 2 || nt == 1) {
+    for (size_t i = 0; i < n; i++) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; t++)
+    th.emplace_back([&, t] {
+      for (size_t i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
 
 // host encode/decode (encode.cpp): real slot vector -> integer coefficients
 void encode_real(const Ctx& C, const double* z, size_t nz, double scale, int64_t* m);

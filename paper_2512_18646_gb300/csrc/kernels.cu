@@ -545,6 +545,37 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
   }
 }
 
+// Slot-block packing of T requests: out[j] = sum_t mask_t * X_t[j] for both
+// components of column j, where X_t is request t's ciphertext set ([n][2][LN])
+// and mask_t (limbs x N, NTT domain) is the plaintext that keeps block t.
+// xs is a device array of the T request pointers; every request word and
+// every output word is touched once, the masks stay in L2.
+__global__ void k_pack_blocks_kernel(const u64* const* xs, const u64* masks, int T, int n_ct, int limbs,
+                                     u64* out, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)n_ct * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t w = idx % LN;
+    const size_t j = idx / LN;
+    const Mod md = pt[(int)(w >> log_n)].mod;
+    Acc128 s0{0, 0}, s1{0, 0};
+    for (int t = 0; t < T; t++) {
+      const u64* x = xs[t] + j * 2 * LN + w;
+      const u64 m = masks[(size_t)t * LN + w];
+      mac128(s0, x[0], m);
+      mac128(s1, x[LN], m);
+      if ((t & 7) == 7) {
+        s0 = Acc128{0, reduce128(s0.hi, s0.lo, md)};
+        s1 = Acc128{0, reduce128(s1.hi, s1.lo, md)};
+      }
+    }
+    u64* o = out + j * 2 * LN + w;
+    o[0] = reduce128(s0.hi, s0.lo, md);
+    o[LN] = reduce128(s1.hi, s1.lo, md);
+  }
+}
+
 // Integer-arithmetic calibration: 8 independent chains of Shoup products per
 // thread (enough instruction-level parallelism to keep the integer pipes
 // busy), `iters` products per chain. The xor of the chains is written so the
@@ -759,6 +790,11 @@ void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int
     throw Error(1, "dense layer inputs have two or three components");
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
+}
+void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out) {
+  HE_LAUNCH(k_pack_blocks_kernel, (size_t)n_ct * limbs * C.N,
+            8.0 * (double)C.N * limbs * (2.0 * n_ct * T + (double)T + 2.0 * n_ct), xs, masks, T, n_ct, limbs, out,
+            C.dev_ptab(), C.log_n);
 }
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters) {
   const u64 q = C.q[0], w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from inputs import synthetic
-from oracle import fp64_ref, layouts
+from oracle import Oracle, fp64_ref, layouts
 from tests.gpu_pairs import encode_columns, encrypt_both, image_columns_both, make_pair, pair_from_preset
 
 pytestmark = pytest.mark.gpu
@@ -291,3 +291,39 @@ def test_matmul_batched_equals_single_matmuls(lib):
         single = g.matmul(As[t], Bs[t], m, p)
         assert np.array_equal(outs[t].export(), single.export()), t
         assert np.abs(g.decrypt_matrix(outs[t], m, p) - ref[t]).max() < 1e-5
+
+
+
+def test_work_budget_chunks_are_bit_identical(lib):
+    """Chunked convolutions, relinearisations, products and rescales (a 1-byte work budget: one
+    column or ciphertext per chunk) give the same words as the unchunked path; the chunked conv
+    layer matches the oracle."""
+    from paper_2512_18646_gb300 import api
+    pre = synthetic.small_preset(11, q_bits=(60, 40, 40, 40, 40))
+    o = Oracle.from_preset(pre, seed=17)
+    o.keygen([1, 2])
+    imgs = np.random.default_rng(18).uniform(0, 1, (2, 12, 12))
+    z = layouts.image_columns(imgs, o.slots, 16)
+    m = np.stack([o.encode(v) for v in z])
+    rng = np.random.default_rng(19)
+    K1, b1 = rng.normal(0, 0.3, (3, 1, 3, 3)), rng.normal(0, 0.3, 3)
+    K2, b2 = rng.normal(0, 0.3, (2, 3, 3, 3)), rng.normal(0, 0.3, 2)
+    X = np.stack([o.encrypt(m[j], o.L1, j) for j in range(len(m))])[None]
+    oy1 = o.conv2d(X, 1, K1, b1, 1, o.scale)
+    outs = []
+    for budget in (0, 1):
+        g = api.Context.from_preset(pre, seed=17)
+        g.keygen([1, 2])
+        g.set_work_budget(budget)
+        x = g.encrypt_coeffs(m, o.L1, o.scale, 0)
+        y1 = g.conv2d(x, 1, 1, K1, b1, 1)
+        e1 = y1.export()
+        assert np.array_equal(e1, oy1)
+        g.square(y1)                       # three components, rescaled
+        y2 = g.conv2d(y1, 3, 1, K2, b2, 2)  # relinearises its input first
+        y3 = g.mul(y2, y2)
+        outs.append([e1, y1.export(), y2.export(), y3.export()])
+        del x, y1, y2, y3
+        g.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)

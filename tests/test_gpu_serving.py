@@ -1,0 +1,185 @@
+"""Serving: slot-block packing and the continuous-batching CNN server on the GPU.
+
+- he_pack_blocks (the server's packing step) is bit-exact against the
+  oracle's ct x pt products, sums and rescale on the same integer masks;
+- the server's results are the same alone and in a mix of requests of two
+  image sides (within 1e-4 after decryption, CKKS noise being the only
+  difference), and each matches the FP64 CNN within 1e-4;
+- admission respects the device-memory budget and refuses what cannot fit.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from inputs import synthetic
+from oracle import fp64_ref
+
+from tests.gpu_pairs import encrypt_both, make_pair
+
+pytestmark = pytest.mark.gpu
+
+# N = 2^12 with the six levels the served network needs below the top
+PRE = synthetic.small_preset(12, q_bits=(60,) + (40,) * 6)
+SIDES = (16, 32)
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_18646_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def test_pack_blocks_matches_oracle(lib):
+    o, g = make_pair(PRE.log_n, PRE.q_bits, PRE.n_special, PRE.special_bits, PRE.alpha, PRE.log_scale, seed=61,
+                     steps=())
+    T, n, side = 3, 2, 32
+    L = o.L1
+    rng = np.random.default_rng(62)
+    sets_o, sets_g, z_all = [], [], []
+    for t in range(T):
+        z = rng.uniform(-1, 1, size=(n, o.slots))
+        m = np.stack([o.encode(v) for v in z])
+        oc, gc = encrypt_both(o, g, m, ct_id_base=10 * t)
+        sets_o.append(oc)
+        sets_g.append(gc)
+        z_all.append(z)
+    q_last = float(o.q[L - 1])
+    masks = []
+    for t in range(T):
+        v = np.zeros(o.slots)
+        v[t * side:(t + 1) * side] = 1.0
+        masks.append(o.encode(v, scale=q_last))
+    masks = np.stack(masks)
+    pts = g.fc_prepare_coeffs(masks.reshape(T, 1, 1, o.N), 1, 1, L)
+    got = g.pack_blocks(sets_g, pts)
+    assert got.info4() == (n, L - 1, o.scale, 2)
+    ex = got.export()
+    for j in range(n):
+        acc = o.mul_plain(sets_o[0][j], masks[0])
+        for t in range(1, T):
+            acc = o.add(acc, o.mul_plain(sets_o[t][j], masks[t]))
+        assert np.array_equal(ex[j], o.rescale(acc)), j
+    # decrypted: block t holds set t's values, the other slots are zero
+    dec = g.decrypt_slots(got)
+    exp = np.zeros((n, o.slots))
+    for t in range(T):
+        exp[:, t * side:(t + 1) * side] = z_all[t][:, t * side:(t + 1) * side]
+    assert np.abs(dec - exp).max() < 1e-6
+
+
+def _request(g, img, side, ct_id_base):
+    """The request words of one image: repeated in every block of stride side, top level."""
+    nb = g.slots // side
+    x = g.encrypt_image(np.repeat(img[None], nb, axis=0), side, ct_id_base=ct_id_base)
+    return x.export_raw().reshape(-1)
+
+
+def _logits(g, z, block, side):
+    return g.decrypt_slots(z)[:, block * side]
+
+
+@pytest.fixture(scope="module")
+def served(lib):
+    from paper_2512_18646_gb300 import api
+    g = api.Context.from_preset(PRE, seed=71)
+    g.keygen([])
+    w = {s: synthetic.cnn_weights(s, seed=72) for s in SIDES}
+    return g, w
+
+
+def test_server_results_same_alone_and_in_the_mix(served):
+    from paper_2512_18646_gb300 import api
+    g, w = served
+    imgs = {k: synthetic.images(1, s, s, seed=80 + k)[0] for k, s in enumerate((32, 16, 32, 16, 32))}
+    side_of = {0: 32, 1: 16, 2: 32, 3: 16, 4: 32}
+    reqs = {k: _request(g, imgs[k], side_of[k], 1000 * (k + 1)) for k in imgs}
+    srv = api.Server(g, w, hbm_budget_bytes=16 << 30, max_blocks=8, start_paused=True)
+    try:
+        # request 2 alone
+        rid = srv.submit(reqs[2], 32)
+        srv.pause(False)
+        assert srv.wait(rid, 120_000)
+        z, blk, t = srv.take(rid)
+        assert blk == 0 and t[0] <= t[1] <= t[2] <= t[3]
+        alone = _logits(g, z, blk, 32)
+        # then all five, submitted while paused so they share batches: one per side
+        srv.pause(True)
+        b0 = srv.stats()["batches"]
+        ids = {k: srv.submit(reqs[k], side_of[k]) for k in (0, 1, 2, 3, 4)}
+        st = srv.stats()
+        assert st["admitted"] == 5 and st["waiting"] == 0
+        srv.pause(False)
+        out = {}
+        for k, rid in ids.items():
+            assert srv.wait(rid, 120_000)
+            z, blk, t = srv.take(rid)
+            out[k] = (_logits(g, z, blk, side_of[k]), blk)
+        assert srv.stats()["batches"] == b0 + 2
+        # blocks in submission order within each side
+        assert [out[k][1] for k in (0, 2, 4)] == [0, 1, 2]
+        assert [out[k][1] for k in (1, 3)] == [0, 1]
+        for k in imgs:
+            ref = fp64_ref.cnn(imgs[k][None], w[side_of[k]])[0]
+            assert np.abs(out[k][0] - ref).max() < TOL, k
+        assert np.abs(out[2][0] - alone).max() < TOL
+        assert np.abs(alone - fp64_ref.cnn(imgs[2][None], w[32])[0]).max() < TOL
+    finally:
+        srv.close()
+
+
+def test_server_admission_by_budget(served):
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_OOM, HeError
+    g, w = served
+    req_bytes = 32 * 2 * g.L1 * g.N * 8
+    probe = api.Server(g, {32: w[32]}, hbm_budget_bytes=16 << 30, max_blocks=8)
+    reserve = probe.stats()["reserve_bytes"]
+    probe.close()
+    budget = reserve + int(2.5 * req_bytes)
+    srv = api.Server(g, {32: w[32]}, hbm_budget_bytes=budget, max_blocks=8, start_paused=True)
+    try:
+        st = srv.stats()
+        fit = (budget - st["reserve_bytes"]) // req_bytes
+        assert 1 <= fit <= 3
+        imgs = synthetic.images(4, 32, 32, seed=90)
+        reqs = [_request(g, imgs[k], 32, 5000 + 100 * k) for k in range(4)]
+        ids = [srv.submit(r, 32) for r in reqs]
+        st = srv.stats()
+        assert st["admitted"] == min(fit, 4) and st["waiting"] == 4 - min(fit, 4)
+        assert st["held_bytes"] + st["reserve_bytes"] <= budget
+        srv.pause(False)
+        for k, rid in enumerate(ids):
+            assert srv.wait(rid, 120_000)
+            if k == 0:  # the host copy of the result, rebuilt as a set
+                host = np.zeros(srv.result_words(), np.uint64)
+                blk, _ = srv.take_host(rid, host)
+                z = g.import_raw(host, g.L1 - 6, g.scale)
+            else:
+                z, blk, _ = srv.take(rid)
+            ref = fp64_ref.cnn(imgs[k][None], w[32])[0]
+            assert np.abs(_logits(g, z, blk, 32) - ref).max() < TOL
+        st = srv.stats()
+        assert st["max_held_bytes"] + st["reserve_bytes"] <= budget
+        assert st["done"] == 4 and st["failed"] == 0
+        # errors: a side not served, a wrong size
+        with pytest.raises(HeError) as e:
+            srv.submit(reqs[0], 16)
+        assert e.value.code == HE_E_ARG
+        with pytest.raises(HeError) as e:
+            srv.submit(reqs[0][:-1].copy(), 32)
+        assert e.value.code == HE_E_ARG
+    finally:
+        srv.close()
+    # a budget below reserve + one request refuses every request
+    tiny = api.Server(g, {32: w[32]}, hbm_budget_bytes=reserve // 2, max_blocks=2)
+    try:
+        with pytest.raises(HeError) as e:
+            tiny.submit(reqs[0], 32)
+        assert e.value.code == HE_E_OOM
+    finally:
+        tiny.close()
