@@ -142,19 +142,12 @@ def profile_read(lib):
     ms = (ctypes.c_double * 256)()
     cnt = (ctypes.c_uint64 * 256)()
     by = (ctypes.c_double * 256)()
-    rc = lib.he_profile_read(names, len(names), ms, cnt, by, 256, ctypes.byref(n))
+    pr = (ctypes.c_double * 256)()
+    rc = lib.he_profile_read(names, len(names), ms, cnt, by, pr, 256, ctypes.byref(n))
     assert rc == 0
     nm = names.value.decode().split("\n")[: n.value]
-    return {nm[i]: {"ms": ms[i], "launches": int(cnt[i]), "bytes": by[i]} for i in range(n.value)}
-
-
-def ntt_butterflies(kernel: str, alg_bytes: float, log_n: int) -> float:
-    """Butterflies done by NTT launches whose algorithmic bytes (16 N per limb) sum to alg_bytes."""
-    n = 1 << log_n
-    limbs = alg_bytes / (16.0 * n)
-    n1 = log_n // 2
-    stages = n1 if kernel.endswith("cols") else log_n - n1
-    return limbs * (n // 2) * stages
+    return {nm[i]: {"ms": ms[i], "launches": int(cnt[i]), "bytes": by[i], "products": pr[i]}
+            for i in range(n.value)}
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -173,23 +166,24 @@ def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
 
 
 def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n):
+    """The kernel's bound is whichever takes longer at peak: its algorithmic bytes at the measured HBM
+    bandwidth, or its modular products at the measured Shoup-product rate (he_calibrate_modmul)."""
     avg_s = t["ms"] / 1e3 / max(1, t["launches"])
     alg_per_launch = t["bytes"] / max(1, t["launches"])
+    prod_per_launch = t.get("products", 0.0) / max(1, t["launches"])
     gbs = alg_per_launch / avg_s / 1e9 if avg_s > 0 else 0.0
     base = {"kernel": name, "share_of_device_time": round(t["ms"] / total_ms, 4), "launches": t["launches"],
             "avg_launch_us": round(avg_s * 1e6, 2),
-            "alg_bytes_per_launch": alg_per_launch,
+            "alg_bytes_per_launch": alg_per_launch, "modmul_per_launch": prod_per_launch,
             "hbm_view": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
                          "peak_source": "measured" if measured else "fallback"}}
     traffic = ncu_traffic(name, alg_per_launch)
-    if name.startswith("k_ntt_"):
-        # one Shoup modular product per butterfly; peak = measured Shoup products/s
-        bfly = ntt_butterflies(name, t["bytes"], log_n) / max(1, t["launches"])
-        ach = bfly / avg_s / 1e9
+    if prod_per_launch / modmul_peak > alg_per_launch / (hbm * 1e9):
+        ach = prod_per_launch / avg_s / 1e9
         peak = modmul_peak / 1e9
         base.update({"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "Gmodmul/s",
                      "frac": round(ach / peak, 4), "traffic": traffic,
-                     "peak_source": "measured (he_calibrate_modmul, Shoup products in registers)"})
+                     "peak_source": "measured (he_calibrate_modmul: Shoup products in registers, all SMs)"})
     else:
         base.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": traffic,
@@ -275,10 +269,12 @@ def run_gpu(args, rank, world, local_rank):
     import ctypes
     modmul_peak = ctypes.c_double()
     lib.he_calibrate_modmul(g.h, ctypes.byref(modmul_peak))
+    prof.pop("k_calib_shoup_kernel", None)
     roofline = roofline_for(top, prof[top], prof_total, hbm, "fallback" not in pk, modmul_peak.value, pre.log_n)
     breakdown = {k: {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
                      "launches_per_step": v["launches"] // args.steps,
-                     "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0}
+                     "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
+                     "alu_frac": round(v["products"] / (v["ms"] / 1e3) / modmul_peak.value, 3) if v["ms"] > 0 else 0.0}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     # end to end through the C ABI: host ciphertexts in (pinned), encrypted logits out

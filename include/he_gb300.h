@@ -505,13 +505,15 @@ uint64_t he_kernel_launches(void);
 int he_profile_enable(int on);
 
 /* Synchronise the recorded events and report, per kernel name, the summed
- * device time (ms), launch count and algorithmic bytes (each operand of a
- * launch read or written once) since the last read; clears the record.
+ * device time (ms), launch count, algorithmic bytes (each operand of a
+ * launch read or written once) and modular products (64-bit multiplications
+ * that are reduced or accumulated: NTT butterflies, multiply-accumulate
+ * terms, base-conversion terms) since the last read; clears the record.
  * names receives the kernel names separated by '\n' (truncated to names_len);
- * ms, counts and bytes (each may be NULL) receive the first max_kernels
- * entries; *n_kernels the number of distinct kernels. */
-int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts, double* bytes, int max_kernels,
-                    int* n_kernels);
+ * ms, counts, bytes and products (each may be NULL) receive the first
+ * max_kernels entries; *n_kernels the number of distinct kernels. */
+int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts, double* bytes, double* products,
+                    int max_kernels, int* n_kernels);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* he_last_error(void);

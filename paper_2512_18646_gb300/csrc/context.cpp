@@ -189,6 +189,7 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
     u64 pm = 1;
     for (u64 p : P) pm = mul_h(pm, p % q, q);
     T.pmod = pm;
+    T.one_sh = shoup_of(1, q);
     // psi = x^((q-1)/2N), x the smallest quadratic non-residue
     u64 x = 2;
     while (pow_h(x, (q - 1) / 2, q) != q - 1) x++;

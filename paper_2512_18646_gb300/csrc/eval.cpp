@@ -56,8 +56,17 @@ static DevBuf modup_poly(Ctx& C, const CtSet& in, int poly) {
   k_copy_limbs(C, in.buf.p + (size_t)poly * lp * N, in.ct_words(), x.p, (size_t)lp * N, (size_t)n, lp);
   ntt_inverse(C, x.p, n, limbs_q(lp, N));
   DevBuf ext((size_t)n * beta * nb * N, C.stream);
-  k_modup(C, x.p, ext.p, n, lp);
-  ntt_forward(C, ext.p, n * beta, ext_map(C, lp));
+  k_modup(C, x.p, in.buf.p + (size_t)poly * lp * N, in.ct_words(), ext.p, n, lp);
+  // each digit's own limbs are already in the NTT domain: transform the others
+  for (int j = 0; j < beta; j++) {
+    const int lo = j * C.alpha, cnt = std::min(C.alpha, lp - lo);
+    LimbMap m = ext_map(C, lp);
+    m.lpp = nb - cnt;
+    m.gap_at = lo;
+    m.gap = cnt;
+    m.poly_stride = (size_t)beta * nb * N;
+    ntt_forward(C, ext.p + (size_t)j * nb * N, n, m);
+  }
   return ext;
 }
 
@@ -186,18 +195,14 @@ std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in_any, const std::vector<lon
   return out;
 }
 
-// rows polynomials of lp limbs (x) -> rescaled polynomials of lp - 1 limbs (out)
-static void rescale_rows(Ctx& C, const u64* x, int rows, int lp, u64* out) {
+// rows polynomials of lp limbs (x) -> rescaled polynomials of lp - 1 limbs (out).
+// The last limb of x is transformed in place (x is consumed).
+static void rescale_rows(Ctx& C, u64* x, int rows, int lp, u64* out) {
   const size_t N = C.N;
-  DevBuf last((size_t)rows * N, C.stream);
-  k_copy_limbs(C, x + (size_t)(lp - 1) * N, (size_t)lp * N, last.p, N, (size_t)rows, 1);
   LimbMap lm1;
-  lm1.lpp = 1; lm1.split = 1; lm1.base0 = lp - 1; lm1.base1 = 0; lm1.poly_stride = N;
-  ntt_inverse(C, last.p, rows, lm1);
-  DevBuf r((size_t)rows * (lp - 1) * N, C.stream);
-  k_rescale_expand(C, last.p, r.p, rows, lp);
-  ntt_forward(C, r.p, rows, limbs_q(lp - 1, N));
-  k_rescale_combine(C, x, r.p, out, rows, lp);
+  lm1.lpp = 1; lm1.split = 1; lm1.base0 = lp - 1; lm1.base1 = 0; lm1.poly_stride = (size_t)lp * N;
+  ntt_inverse(C, x + (size_t)(lp - 1) * N, rows, lm1);
+  ntt_forward_rescale(C, out, x, rows, lp);
 }
 
 void rescale_inplace(Ctx& C, CtSet& s) {

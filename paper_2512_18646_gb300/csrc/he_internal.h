@@ -61,15 +61,22 @@ struct PrimeTab {
   Mod mod;
   u64 ninv, ninv_sh;  // N^{-1} mod q and its Shoup companion
   u64 pmod;           // P = p_0 ... p_{K-1} mod q
-  u64 pad;
+  u64 one_sh;         // floor(2^64 / q): Shoup companion of 1 (x mod q in [0, 2q) for any word x)
 };
 
-// Constants of one launch of the NTT over a batch of limbs. Limb i of each
-// polynomial (i < lpp) uses prime base0 + i if i < split, else base1 + i - split.
+// Constants of one launch over a batch of limbs. Limb i of each polynomial
+// (i < lpp) sits at limb position e = i, or i + gap from position gap_at on
+// (a launch that skips limbs gap_at .. gap_at + gap - 1), and uses prime
+// base0 + e if e < split, else base1 + e - split.
 struct LimbMap {
   int lpp = 1, split = 1, base0 = 0, base1 = 0;
+  int gap_at = 1 << 30, gap = 0;
   size_t poly_stride = 0;  // words between consecutive polynomials
-  __host__ __device__ int prime(int i) const { return i < split ? base0 + i : base1 + (i - split); }
+  __host__ __device__ int mem(int i) const { return i >= gap_at ? i + gap : i; }
+  __host__ __device__ int prime(int i) const {
+    const int e = mem(i);
+    return e < split ? base0 + e : base1 + (e - split);
+  }
 };
 
 struct Ctx {
@@ -125,13 +132,18 @@ struct CtSet {
 };
 
 // ---- launch accounting (profile.cpp): every kernel launch is bracketed ----
-// bytes: the launch's algorithmic traffic (each operand read or written once)
-void* prof_begin(const char* name, cudaStream_t st, double bytes);
+// bytes: the launch's algorithmic traffic (each operand read or written once);
+// products: its modular products (64 x 64-bit multiplications followed by a
+// reduction or accumulated for one)
+void* prof_begin(const char* name, cudaStream_t st, double bytes, double products = 0.0);
 void prof_end(void* tok, cudaStream_t st);
 
 // ---- kernel launchers (kernels.cu / ntt.cu) ----
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
+// rescale of `rows` polynomials x [rows][lp][N] whose limb lp - 1 is already in the
+// coefficient domain: out [rows][lp - 1][N] = (x_i - NTT_i(expanded last limb)) q_l^{-1}
+void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp);
 inline LimbMap limbs_q(int limbs, size_t N) {  // plain polynomials, primes 0..limbs-1
   LimbMap m;
   m.lpp = limbs; m.split = limbs; m.base0 = 0; m.base1 = 0; m.poly_stride = (size_t)limbs * N;
@@ -157,8 +169,10 @@ void k_decrypt_limb0(const Ctx& C, const u64* ct, int limbs, int n, u64* out);
 void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int limbs);
 // d[n][3][limbs] = tensor(a[n][2], b[n][2])
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs);
-// ModUp fast base conversion: x coeff [n][limbs][N] -> ext coeff [n][beta][limbs+K][N]
-void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs);
+// ModUp fast base conversion: x coeff [n][limbs][N] -> ext [n][beta][limbs+K][N], coefficient
+// domain except each digit's own limbs, which are copied from the NTT-domain input
+// xntt (ciphertext c at xntt + c * xntt_stride)
+void k_modup(const Ctx& C, const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs);
 // key pointers of up to 8 steps for one inner-product launch
 struct KeyPtrs {
   const u64* k[8];

@@ -53,7 +53,7 @@ __global__ void k_reduce_signed_kernel(const int64_t* in, u64* out, int n, LimbM
     const size_t j = idx & (N - 1);
     const size_t row = idx >> log_n;
     const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
-    out[(size_t)p * lm.poly_stride + (size_t)i * N + j] = reduce_i64(in[(size_t)p * N + j], pt[lm.prime(i)].mod);
+    out[(size_t)p * lm.poly_stride + (size_t)lm.mem(i) * N + j] = reduce_i64(in[(size_t)p * N + j], pt[lm.prime(i)].mod);
   }
 }
 
@@ -66,7 +66,7 @@ __global__ void k_reduce_small_kernel(const int8_t* in, u64* out, int n, LimbMap
     const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
     const int v = in[(size_t)p * N + j];
     const u64 q = pt[lm.prime(i)].mod.q;
-    out[(size_t)p * lm.poly_stride + (size_t)i * N + j] = v >= 0 ? (u64)v : q - (u64)(-v);
+    out[(size_t)p * lm.poly_stride + (size_t)lm.mem(i) * N + j] = v >= 0 ? (u64)v : q - (u64)(-v);
   }
 }
 
@@ -110,7 +110,7 @@ __global__ void k_mul_kernel(const u64* a, const u64* b, u64* out, int n, LimbMa
     const size_t j = idx & (N - 1);
     const size_t row = idx >> log_n;
     const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
-    const size_t o = (size_t)p * lm.poly_stride + (size_t)i * N + j;
+    const size_t o = (size_t)p * lm.poly_stride + (size_t)lm.mem(i) * N + j;
     out[o] = mulmod(a[o], b[o], pt[lm.prime(i)].mod);
   }
 }
@@ -174,8 +174,9 @@ __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int l
 // Each term [x_i (D_j/q_i)^{-1}]_{q_i} (D_j/q_i) is a Shoup product in [0, 2t)
 // (valid for any multiplicand below 2^64); partial sums stay below 2t.
 template <int ALPHA>
-__global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alpha_rt, int beta, int L1, int K,
-                               const u64* up_inv, const u64* up_hat, const PrimeTab* pt, int log_n) {
+__global__ void k_modup_kernel(const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs,
+                               int alpha_rt, int beta, int L1, int K, const u64* up_inv, const u64* up_hat,
+                               const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int nb = limbs + K;
   const int alpha = ALPHA > 0 ? ALPHA : alpha_rt;
@@ -196,7 +197,8 @@ __global__ void k_modup_kernel(const u64* x, u64* ext, int n, int limbs, int alp
         const int i = lo + ii;
         const u64 xi = X[(size_t)i * N + jn];
         y[ii] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
-        E[(size_t)i * N + jn] = xi;
+        // the digit's own limbs: BConv gives x_i itself, already known in the NTT domain
+        E[(size_t)i * N + jn] = xntt[(size_t)c * xntt_stride + (size_t)i * N + jn];
       }
     }
     for (int pos = 0; pos < nb; pos++) {
@@ -620,16 +622,17 @@ __global__ void k_copy_rows_kernel(const u64* src, size_t src_gs, u64* dst, size
 
 }  // namespace
 
-#define HE_LAUNCH(kern, total, bytes, ...)                                     \
+#define HE_LAUNCH_P(kern, total, bytes, products, ...)                         \
   do {                                                                         \
     const size_t tot_ = (total);                                               \
     if (tot_) {                                                                \
-      void* tok_ = prof_begin(#kern, C.stream, (double)(bytes));               \
+      void* tok_ = prof_begin(#kern, C.stream, (double)(bytes), (double)(products)); \
       kern<<<grid_for(tot_), kBlock, 0, C.stream>>>(__VA_ARGS__);             \
       prof_end(tok_, C.stream);                                                \
     }                                                                          \
     HE_CUDA(cudaGetLastError());                                               \
   } while (0)
+#define HE_LAUNCH(kern, total, bytes, ...) HE_LAUNCH_P(kern, total, bytes, 0.0, __VA_ARGS__)
 
 void k_reduce_signed(const Ctx& C, const int64_t* in, u64* out, int n, const LimbMap& lm) {
   HE_LAUNCH(k_reduce_signed_kernel, (size_t)n * lm.lpp * C.N, 8.0 * (double)C.N * n * (1 + lm.lpp), in, out, n, lm, C.dev_ptab(), C.log_n);
@@ -647,7 +650,8 @@ void k_ksk_combine(const Ctx& C, const u64* a, const u64* e, const u64* sprime, 
             C.dev_ptab(), C.log_n);
 }
 void k_mul(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, const LimbMap& lm) {
-  HE_LAUNCH(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, 8.0 * (double)C.N * 3 * n_polys * lm.lpp, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
+  HE_LAUNCH_P(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, 8.0 * (double)C.N * 3 * n_polys * lm.lpp,
+              (double)C.N * n_polys * lm.lpp, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
 }
 void k_permute(const Ctx& C, const u64* in, u64* out, size_t rows, u64 k) {
   HE_LAUNCH(k_permute_kernel, rows * C.N, 8.0 * (double)C.N * 2 * rows, in, out, rows, k, C.log_n);
@@ -659,26 +663,33 @@ void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int 
   HE_LAUNCH(k_add_kernel, (size_t)n_polys * limbs * C.N, 8.0 * (double)C.N * 3 * n_polys * limbs, a, b, out, n_polys, limbs, C.dev_ptab(), C.log_n);
 }
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs) {
-  HE_LAUNCH(k_tensor_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 7 * n * limbs, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH_P(k_tensor_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 7 * n * limbs, 4.0 * C.N * n * limbs, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
 }
-void k_modup(const Ctx& C, const u64* x, u64* ext, int n, int limbs) {
+void k_modup(const Ctx& C, const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs) {
   if (C.alpha > 8) throw Error(8, "digits of more than 8 primes are not supported");
   const u64* up_inv = C.d_up.p;
   const u64* up_hat = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2;
   const int beta = C.beta_at(limbs);
   const size_t total = (size_t)n * beta * C.N;
-  const double bytes = 8.0 * (double)C.N * n * (limbs + (double)beta * (limbs + C.K));
+  // coefficient input, the own limbs again in the NTT domain, the extended digits
+  const double bytes = 8.0 * (double)C.N * n * (2.0 * limbs + (double)beta * (limbs + C.K));
+  double prods = 0.0;  // per coefficient: x_i (D_j/q_i)^{-1}, then cnt terms for every other limb
+  for (int j = 0; j < beta; j++) {
+    const int cnt = std::min(C.alpha, limbs - j * C.alpha);
+    prods += cnt + (double)cnt * (limbs + C.K - cnt);
+  }
+  prods *= (double)C.N * n;
   switch (C.alpha) {
     case 1:
-      HE_LAUNCH(k_modup_kernel<1>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+      HE_LAUNCH_P(k_modup_kernel<1>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
                 C.dev_ptab(), C.log_n);
       break;
     case 2:
-      HE_LAUNCH(k_modup_kernel<2>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+      HE_LAUNCH_P(k_modup_kernel<2>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
                 C.dev_ptab(), C.log_n);
       break;
     default:
-      HE_LAUNCH(k_modup_kernel<0>, total, bytes, x, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
+      HE_LAUNCH_P(k_modup_kernel<0>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
                 C.dev_ptab(), C.log_n);
       break;
   }
@@ -705,7 +716,8 @@ void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u
     const dim3 grid((unsigned)((C.N + KS_TILE - 1) / KS_TILE), (unsigned)nb);
     const size_t smem = (size_t)cs * per_step;
     const double bytes = 8.0 * (double)C.N * nb * ((double)beta * (n + 2.0 * cs) + 2.0 * n * cs);
-    void* tok = prof_begin(beta <= 8 ? "k_ks_inner_kernel<8>" : "k_ks_inner_kernel<16>", C.stream, bytes);
+    void* tok = prof_begin(beta <= 8 ? "k_ks_inner_kernel<8>" : "k_ks_inner_kernel<16>", C.stream, bytes,
+                           2.0 * C.N * nb * beta * (double)n * cs);
     if (beta <= 8)
       k_ks_inner_kernel<8><<<grid, KS_TILE, smem, C.stream>>>(ext, kp, cs, u + s0 * ustep, n, limbs, beta, C.L1, C.K,
                                                                C.dev_ptab(), C.log_n);
@@ -721,13 +733,15 @@ void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k) {
 }
 void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs) {
   if (C.K > 4) throw Error(8, "more than 4 special primes are not supported");
-  HE_LAUNCH(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, 8.0 * (double)C.N * 2 * n * (C.K + limbs), p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
+  HE_LAUNCH_P(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, 8.0 * (double)C.N * 2 * n * (C.K + limbs),
+              2.0 * C.N * n * C.K * (1.0 + limbs), p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
             C.log_n);
 }
 void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
                        size_t out_stride, int n, int limbs, u64 k, int mode) {
   const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)2 * C.K * C.L1;
-  HE_LAUNCH(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * n * limbs * (mode == 0 ? 8.0 : 7.0), u, z, base, base_stride, out, out_stride, n,
+  HE_LAUNCH_P(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * n * limbs * (mode == 0 ? 8.0 : 7.0),
+              2.0 * C.N * n * limbs, u, z, base, base_stride, out, out_stride, n,
             limbs, C.K, k, mode, Pinv, C.dev_ptab(), C.log_n);
 }
 void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs) {
@@ -752,7 +766,8 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   if (gz > (unsigned)w_out) gz = (unsigned)w_out;
   const double bytes = 8.0 * (double)C.N * 2.0 * limbs * ((double)c_in * (stride * (w_out - 1) + k) * k +
                                                          (double)c_out * w_out);
-  void* tok = prof_begin(c_out <= 8 ? "k_conv_mac_kernel<8>" : "k_conv_mac_kernel<16>", C.stream, bytes);
+  const double prods = 2.0 * C.N * limbs * (double)c_out * w_out * c_in * k * k;
+  void* tok = prof_begin(c_out <= 8 ? "k_conv_mac_kernel<8>" : "k_conv_mac_kernel<16>", C.stream, bytes, prods);
   if (c_out <= 8) {
     static bool attr8 = false;
     if (!attr8) {
@@ -774,12 +789,13 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   HE_CUDA(cudaGetLastError());
 }
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
-  HE_LAUNCH(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p), A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
+  HE_LAUNCH_P(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p),
+              4.0 * C.N * limbs * n * p, A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
   const size_t total = (size_t)limbs * C.N;
   const double bytes = 8.0 * (double)C.N * limbs * ((double)polys * n_in + (double)out_dim * n_in + (double)polys * out_dim);
-  void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes);
+  void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes, (double)C.N * limbs * polys * (double)n_in * out_dim);
   if (polys == 2)
     k_fc_mac_kernel<5, 4, 2><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
                                                                        C.log_n);
@@ -792,13 +808,13 @@ void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int
   HE_CUDA(cudaGetLastError());
 }
 void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out) {
-  HE_LAUNCH(k_pack_blocks_kernel, (size_t)n_ct * limbs * C.N,
-            8.0 * (double)C.N * limbs * (2.0 * n_ct * T + (double)T + 2.0 * n_ct), xs, masks, T, n_ct, limbs, out,
-            C.dev_ptab(), C.log_n);
+  HE_LAUNCH_P(k_pack_blocks_kernel, (size_t)n_ct * limbs * C.N,
+              8.0 * (double)C.N * limbs * (2.0 * n_ct * T + (double)T + 2.0 * n_ct), 2.0 * C.N * limbs * n_ct * T,
+              xs, masks, T, n_ct, limbs, out, C.dev_ptab(), C.log_n);
 }
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters) {
   const u64 q = C.q[0], w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);
-  void* tok = prof_begin("k_calib_shoup_kernel", C.stream, 0.0);
+  void* tok = prof_begin("k_calib_shoup_kernel", C.stream, 0.0, 8.0 * blocks * threads * (double)iters);
   k_calib_shoup_kernel<<<blocks, threads, 0, C.stream>>>(sink, q, w, wp, iters);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());

@@ -31,6 +31,16 @@ namespace he {
 
 namespace {
 
+// Operands of a rescale fused into a forward transform: x [rows][lp][N] holds
+// the polynomials being rescaled, with limb lp - 1 already in the coefficient
+// domain; rs [L1][3] holds floor(q_l/2) mod q_i, q_l^{-1} mod q_i and its
+// Shoup companion for this lp.
+struct RescaleFuse {
+  const u64* x = nullptr;
+  const u64* rs = nullptr;
+  int lp = 0;
+};
+
 // ---------------------------------------------------------------------------
 // compile-time round maps
 // ---------------------------------------------------------------------------
@@ -199,7 +209,7 @@ __device__ __forceinline__ int swz(int x) {
 __device__ __forceinline__ u64* row_ptr(u64* base, const LimbMap& lm, int row, size_t N, int& prime) {
   const int p = row / lm.lpp, i = row - p * lm.lpp;
   prime = lm.prime(i);
-  return base + (size_t)p * lm.poly_stride + (size_t)i * N;
+  return base + (size_t)p * lm.poly_stride + (size_t)lm.mem(i) * N;
 }
 
 constexpr int kRowThreads = 256;
@@ -207,9 +217,9 @@ constexpr int kRowThreads = 256;
 // ---------------------------------------------------------------------------
 // rows: last n2 forward stages (sub-size M = 2^LOGM = 2^{n2}), warp-contained
 // ---------------------------------------------------------------------------
-template <int LOGM>
+template <int LOGM, int MODE>
 __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                              const u64* tw_all, int n, int n1) {
+                                                              const u64* tw_all, int n, int n1, RescaleFuse fz) {
   using P = Plan<LOGM>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
@@ -240,8 +250,20 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap
   rounds_fwd_rest<LOGM, 1>(a, u, smw, addr, sync, tw, n1, run, q);
   using ML = RMap<LOGM, P::R - 1>;
   const int xl = ML::upart(u);
+  if constexpr (MODE == 0) {
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = reduce4q(a[k], q);
+    for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = reduce4q(a[k], q);
+  } else {
+    // rescale: out_i = (x_i - R_i) q_l^{-1} mod q_i, R_i this transform of the expanded last limb
+    const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
+    const u64* xi = fz.x + ((size_t)pr * fz.lp + i) * N + run * M;
+    const u64 qi = fz.rs[(size_t)i * 3 + 1], qs = fz.rs[(size_t)i * 3 + 2];
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+      const int e = xl | ML::kbits(k);
+      xr[e] = shoup(submod(xi[e], reduce4q(a[k], q), q), qi, qs, q);
+    }
+  }
 }
 
 // inverse, first n2 stages (smallest distances) inside runs; output in [0, 2q)
@@ -284,8 +306,9 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap
 // ---------------------------------------------------------------------------
 // cols: first n1 forward stages (sub-size 2^LOGM = 2^{n1}) on C adjacent columns
 // ---------------------------------------------------------------------------
-template <int LOGM>
-__global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C) {
+template <int LOGM, int MODE>
+__global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
+                               RescaleFuse fz) {
   using P = Plan<LOGM>;
   extern __shared__ u64 smc[];
   const size_t N = (size_t)1 << n;
@@ -302,8 +325,21 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
   {
     using M0 = RMap<LOGM, 0>;
     const int x0 = M0::upart(u);
+    if constexpr (MODE == 0) {
 #pragma unroll
-    for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(x0 | M0::kbits(k)) * stride];
+      for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(x0 | M0::kbits(k)) * stride];
+    } else {
+      // rescale: the last limb's coefficients r (mod q_l), as (r + floor(q_l/2) mod q_l) - floor(q_l/2) mod q_i
+      const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
+      const u64* src = fz.x + ((size_t)pr * fz.lp + fz.lp - 1) * N + (size_t)blockIdx.x * C + lo;
+      const u64 ql = pt[fz.lp - 1].mod.q, one_sh = pt[i].one_sh;
+      const u64 half = ql >> 1, q_m_half = q - fz.rs[(size_t)i * 3];
+#pragma unroll
+      for (int k = 0; k < P::E; k++) {
+        const u64 v = addmod(src[(size_t)(x0 | M0::kbits(k)) * stride], half, ql);
+        a[k] = shoup_lazy(v, 1, one_sh, q) + q_m_half;  // [0, 3q), within the transform's [0, 4q) inputs
+      }
+    }
     round_fwd<LOGM, 0>(a, x0, tw, 0, 0, q);
   }
   rounds_fwd_rest<LOGM, 1>(a, u, smc, addr, sync, tw, 0, 0, q);
@@ -356,50 +392,63 @@ Geom geom(int log_n) {
   return g;
 }
 
-template <int L>
-void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n1, const u64* tw) {
+template <int L, int MODE>
+void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n1, const u64* tw,
+                 const RescaleFuse& fz) {
   constexpr int RUNS = kRowThreads / Plan<L>::T;
   const int runs = 1 << n1;
   const dim3 grid((runs + RUNS - 1) / RUNS, rows);
-  void* t = prof_begin(inv ? "k_ntt_inv_rows" : "k_ntt_fwd_rows", C.stream, 16.0 * rows * (double)C.N);
+  // a fused rescale also reads the limbs being rescaled and multiplies by q_l^{-1}
+  const double bytes = (MODE ? 24.0 : 16.0) * rows * (double)C.N;
+  const double prods = (double)rows * C.N * ((C.log_n - n1) / 2.0 + (MODE ? 1.0 : 0.0));
+  void* t = prof_begin(inv ? "k_ntt_inv_rows" : MODE ? "k_ntt_fwd_rows<rescale>" : "k_ntt_fwd_rows", C.stream, bytes,
+                       prods);
   if (inv) k_ntt_inv_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
-  else k_ntt_fwd_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
+  else k_ntt_fwd_rows<L, MODE><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1, fz);
   prof_end(t, C.stream);
 }
 
-template <int L>
-void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n2, int Ccols, const u64* tw) {
+template <int L, int MODE>
+void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n2, int Ccols, const u64* tw,
+                 const RescaleFuse& fz) {
   const int threads = Ccols * Plan<L>::T;
   const size_t smem = (size_t)(1 << L) * Ccols * 8;
   const dim3 grid((1 << n2) / Ccols, rows);
-  void* t = prof_begin(inv ? "k_ntt_inv_cols" : "k_ntt_fwd_cols", C.stream, 16.0 * rows * (double)C.N);
+  // butterflies, plus N^{-1} (inverse) or the reduction of the expanded limb (fused rescale)
+  const double prods = (double)rows * C.N * ((C.log_n - n2) / 2.0 + (inv || MODE ? 1.0 : 0.0));
+  void* t = prof_begin(inv ? "k_ntt_inv_cols" : MODE ? "k_ntt_fwd_cols<rescale>" : "k_ntt_fwd_cols", C.stream,
+                       16.0 * rows * (double)C.N, prods);
   if (inv) k_ntt_inv_cols<L><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols);
-  else k_ntt_fwd_cols<L><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols);
+  else k_ntt_fwd_cols<L, MODE><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols, fz);
   prof_end(t, C.stream);
 }
 
-void rows_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw) {
+template <int MODE>
+void rows_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw,
+                   const RescaleFuse& fz = RescaleFuse{}) {
   switch (g.n2) {
-    case 2: launch_rows<2>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 3: launch_rows<3>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 4: launch_rows<4>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 5: launch_rows<5>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 6: launch_rows<6>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 7: launch_rows<7>(inv, base, lm, rows, C, g.n1, tw); break;
-    case 8: launch_rows<8>(inv, base, lm, rows, C, g.n1, tw); break;
+    case 2: launch_rows<2, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 3: launch_rows<3, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 4: launch_rows<4, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 5: launch_rows<5, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 6: launch_rows<6, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 7: launch_rows<7, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
+    case 8: launch_rows<8, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
     default: throw Error(1, "unsupported ring degree");
   }
 }
 
-void cols_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw) {
+template <int MODE>
+void cols_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw,
+                   const RescaleFuse& fz = RescaleFuse{}) {
   switch (g.n1) {
-    case 2: launch_cols<2>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 3: launch_cols<3>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 4: launch_cols<4>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 5: launch_cols<5>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 6: launch_cols<6>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 7: launch_cols<7>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
-    case 8: launch_cols<8>(inv, base, lm, rows, C, g.n2, g.C, tw); break;
+    case 2: launch_cols<2, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 3: launch_cols<3, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 4: launch_cols<4, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 5: launch_cols<5, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 6: launch_cols<6, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 7: launch_cols<7, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
+    case 8: launch_cols<8, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
     default: throw Error(1, "unsupported ring degree");
   }
 }
@@ -415,8 +464,8 @@ void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
-    cols_dispatch(false, base, lm, rr, C, g, C.d_psi.p);
-    rows_dispatch(false, base, lm, rr, C, g, C.d_psi.p);
+    cols_dispatch<0>(false, base, lm, rr, C, g, C.d_psi.p);
+    rows_dispatch<0>(false, base, lm, rr, C, g, C.d_psi.p);
   }
   HE_CUDA(cudaGetLastError());
 }
@@ -429,8 +478,24 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lm.lpp) * lm.poly_stride;
-    rows_dispatch(true, base, lm, rr, C, g, C.d_ipsi.p);
-    cols_dispatch(true, base, lm, rr, C, g, C.d_ipsi.p);
+    rows_dispatch<0>(true, base, lm, rr, C, g, C.d_ipsi.p);
+    cols_dispatch<0>(true, base, lm, rr, C, g, C.d_ipsi.p);
+  }
+  HE_CUDA(cudaGetLastError());
+}
+
+void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
+  if (rows == 0) return;
+  const Geom g = geom(C.log_n);
+  const LimbMap lm = limbs_q(lp - 1, C.N);
+  const u64* tab = C.d_rs.p + (size_t)lp * C.L1 * 3;
+  const int per = 65535 / (lp - 1);  // polynomials per launch (grid.y <= 65535)
+  for (int p0 = 0; p0 < rows; p0 += per) {
+    const int pn = rows - p0 < per ? rows - p0 : per;
+    RescaleFuse fz{x + (size_t)p0 * lp * C.N, tab, lp};
+    u64* base = out + (size_t)p0 * (lp - 1) * C.N;
+    cols_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
+    rows_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
   }
   HE_CUDA(cudaGetLastError());
 }

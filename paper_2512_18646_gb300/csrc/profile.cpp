@@ -20,7 +20,7 @@ static std::mutex g_mu;
 
 struct Rec {
   const char* name;
-  double bytes;
+  double bytes, products;
   cudaEvent_t a, b;
 };
 static std::vector<Rec> g_recs;
@@ -37,11 +37,11 @@ static cudaEvent_t take_event() {
   return e;
 }
 
-void* prof_begin(const char* name, cudaStream_t st, double bytes) {
+void* prof_begin(const char* name, cudaStream_t st, double bytes, double products) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_timing.load(std::memory_order_relaxed)) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
-  Rec r{name, bytes, take_event(), take_event()};
+  Rec r{name, bytes, products, take_event(), take_event()};
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   return (void*)(g_recs.size());
@@ -68,12 +68,12 @@ int he_profile_enable(int on) {
   return HE_OK;
 }
 
-int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts, double* bytes, int max_kernels,
-                    int* n_kernels) {
+int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts, double* bytes, double* products,
+                    int max_kernels, int* n_kernels) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!n_kernels) return HE_E_ARG;
   std::vector<std::string> nm;
-  std::vector<double> t, by;
+  std::vector<double> t, by, pr;
   std::vector<uint64_t> c;
   for (const Rec& r : g_recs) {
     float e = 0.f;
@@ -89,10 +89,12 @@ int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts,
       t.push_back(0);
       c.push_back(0);
       by.push_back(0);
+      pr.push_back(0);
     }
     t[k] += e;
     c[k] += 1;
     by[k] += r.bytes;
+    pr[k] += r.products;
     g_free.push_back(r.a);
     g_free.push_back(r.b);
   }
@@ -104,6 +106,7 @@ int he_profile_read(char* names, size_t names_len, double* ms, uint64_t* counts,
       if (ms) ms[k] = t[k];
       if (counts) counts[k] = c[k];
       if (bytes) bytes[k] = by[k];
+      if (products) products[k] = pr[k];
     }
     joined += nm[k];
     joined += '\n';
