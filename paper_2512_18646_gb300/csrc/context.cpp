@@ -190,6 +190,11 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
     for (u64 p : P) pm = mul_h(pm, p % q, q);
     T.pmod = pm;
     T.one_sh = shoup_of(1, q);
+    T.mont_r = (u64)(((u128)1 << 64) % q);
+    T.mont_r_sh = shoup_of(T.mont_r, q);
+    u64 qi = 1;  // q^{-1} mod 2^64 by Newton iteration (q odd): each step doubles the correct bits
+    for (int it = 0; it < 6; it++) qi *= 2 - q * qi;
+    T.qinv_neg = (u64)0 - qi;
     // psi = x^((q-1)/2N), x the smallest quadratic non-residue
     u64 x = 2;
     while (pow_h(x, (q - 1) / 2, q) != q - 1) x++;
@@ -386,6 +391,8 @@ DevBuf make_ksk(Ctx& C, u64 key_id, const u64* d_sprime) {
     ntt_forward(C, e_res.p, 1, lm);
     k_ksk_combine(C, a, e_res.p, d_sprime, b, j);
   }
+  // the inner product reduces its sums by Montgomery reduction, so keys are kept as k 2^64 mod q
+  k_mont_form(C, key.p, beta * 2, lm);
   return key;
 }
 

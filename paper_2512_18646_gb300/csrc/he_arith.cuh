@@ -32,16 +32,36 @@ HE_HD u64 mulhi64(u64 a, u64 b) {
 #endif
 }
 
-// Full 64 x 64 -> 128-bit product from four 32 x 32 -> 64-bit products (one
-// wide integer multiply-add each) and carry-free 64-bit additions:
-// a b = p11 2^64 + (p01 + p10) 2^32 + p00.
+// Full 64 x 64 -> 128-bit product. Schoolbook on 32-bit words:
+// a b = a1 b1 2^64 + (a0 b1 + a1 b0) 2^32 + a0 b0. On the device the word
+// products are accumulated with PTX carry chains (mad.lo/madc.hi with .cc);
+// on the host, four 32 x 32 -> 64-bit products and carry-free additions.
 HE_HD void mul128(u64 a, u64 b, u64& hi, u64& lo) {
+#if defined(__CUDA_ARCH__)
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+  u32 w0, w1, w2, w3;
+  asm("mul.lo.u32     %0, %4, %6;\n\t"
+      "mul.hi.u32     %1, %4, %6;\n\t"
+      "mul.lo.u32     %2, %5, %7;\n\t"
+      "mul.hi.u32     %3, %5, %7;\n\t"
+      "mad.lo.cc.u32  %1, %4, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32       %3, %3, 0;\n\t"
+      "mad.lo.cc.u32  %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32       %3, %3, 0;"
+      : "=&r"(w0), "=&r"(w1), "=&r"(w2), "=&r"(w3)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  lo = ((u64)w1 << 32) | w0;
+  hi = ((u64)w3 << 32) | w2;
+#else
   const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
   const u64 p00 = (u64)a0 * b0, p01 = (u64)a0 * b1, p10 = (u64)a1 * b0, p11 = (u64)a1 * b1;
   const u64 mid = p01 + (p00 >> 32);            // < 2^64 - 2^32
   const u64 mid2 = p10 + (mid & 0xffffffffull);  // < 2^64 - 2^32
   lo = (mid2 << 32) | (p00 & 0xffffffffull);
   hi = p11 + (mid >> 32) + (mid2 >> 32);
+#endif
 }
 
 // A prime with its Barrett constant mu = floor(2^128 / q) = mu_hi 2^64 + mu_lo.
@@ -80,11 +100,43 @@ HE_HD u64 mulmod(u64 a, u64 b, const Mod& m) {
 struct Acc128 {
   u64 hi, lo;
 };
+// acc += a b; the caller keeps the sum below 2^128.
 HE_HD void mac128(Acc128& acc, u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+  // the even word products straight into the accumulator, then the two cross products one word up
+  u32 w0 = (u32)acc.lo, w1 = (u32)(acc.lo >> 32), w2 = (u32)acc.hi, w3 = (u32)(acc.hi >> 32);
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+  asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.u32    %3, %5, %7, %3;\n\t"
+      "mad.lo.cc.u32  %1, %4, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32       %3, %3, 0;\n\t"
+      "mad.lo.cc.u32  %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32       %3, %3, 0;"
+      : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+  acc.lo = ((u64)w1 << 32) | w0;
+  acc.hi = ((u64)w3 << 32) | w2;
+#else
   u64 hi, lo;
   mul128(a, b, hi, lo);
   acc.lo += lo;
   acc.hi += hi + (acc.lo < lo);
+#endif
+}
+
+// Montgomery reduction (Montgomery, Math. Comp. 1985) of x = hi 2^64 + lo < q 2^64:
+// x 2^{-64} mod q in [0, q), with qneg = -q^{-1} mod 2^64. m = lo qneg makes
+// x + m q divisible by 2^64; its low word sums to 2^64 unless lo = 0.
+HE_HD u64 redc128(u64 hi, u64 lo, u64 q, u64 qneg) {
+  const u64 m = lo * qneg;
+  u64 mh, ml;
+  mul128(m, q, mh, ml);
+  const u64 t = hi + mh + (lo != 0);
+  return t >= q ? t - q : t;
 }
 
 // a w mod q in [0, 2q) for any a < 2^64, w < q, wp = floor(w 2^64 / q).

@@ -62,6 +62,8 @@ struct PrimeTab {
   u64 ninv, ninv_sh;  // N^{-1} mod q and its Shoup companion
   u64 pmod;           // P = p_0 ... p_{K-1} mod q
   u64 one_sh;         // floor(2^64 / q): Shoup companion of 1 (x mod q in [0, 2q) for any word x)
+  u64 mont_r, mont_r_sh;  // R = 2^64 mod q (Montgomery radix) and its Shoup companion
+  u64 qinv_neg;           // -q^{-1} mod 2^64
 };
 
 // Constants of one launch over a batch of limbs. Limb i of each polynomial
@@ -202,6 +204,8 @@ void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
 // slot-block packing: out[j] = sum_t masks[t] * xs[t][j] ([n_ct][2][limbs][N]); xs is a device array of T pointers
 void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out);
+// data[p][i] *= R mod q (Montgomery form) for the primes of lm
+void k_mont_form(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters);
 // number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad

@@ -103,6 +103,18 @@ __global__ void k_ksk_kernel(const u64* a, const u64* e, const u64* s, const u64
   }
 }
 
+__global__ void k_mont_form_kernel(u64* data, int n, LimbMap lm, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = (size_t)n * lm.lpp * N;
+  HE_GRID_LOOP(idx, total) {
+    const size_t j = idx & (N - 1), row = idx >> log_n;
+    const int i = (int)(row % lm.lpp), p = (int)(row / lm.lpp);
+    const PrimeTab& T = pt[lm.prime(i)];
+    u64* x = data + (size_t)p * lm.poly_stride + (size_t)lm.mem(i) * N + j;
+    *x = shoup(*x, T.mont_r, T.mont_r_sh, T.mod.q);
+  }
+}
+
 __global__ void k_mul_kernel(const u64* a, const u64* b, u64* out, int n, LimbMap lm, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t total = (size_t)n * lm.lpp * N;
@@ -223,15 +235,17 @@ __global__ void k_modup_kernel(const u64* x, const u64* xntt, size_t xntt_stride
 // u[s][c][comp][pos] = sum_j ext[c][j][pos] key_s[j][comp][g(pos)] for the
 // steps s of one launch. A block owns one limb position `pos` and a tile of
 // KS_TILE coefficients: it reads that tile of every key once into shared
-// memory (each thread only touches its own column, so no barrier is needed)
-// and then walks all n ciphertexts, so key traffic is one read per launch
-// instead of one per ciphertext.
+// memory, the two components of a key word side by side (one 16-byte load
+// per digit; each thread only touches its own column, so no barrier is
+// needed), and then walks all n ciphertexts, loading the next ciphertext's
+// digits while the current one is accumulated. Key traffic is one read per
+// launch instead of one per ciphertext.
 constexpr int KS_TILE = 128;
 template <int MAXB>
-__global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* ext, KeyPtrs keys, int S, u64* u, int n,
-                                                             int limbs, int beta, int L1, int K, const PrimeTab* pt,
-                                                             int log_n) {
-  extern __shared__ u64 skey[];  // [S][beta][2][KS_TILE]
+__global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* __restrict__ ext, KeyPtrs keys, int S,
+                                                             u64* __restrict__ u, int n, int limbs, int beta, int L1,
+                                                             int K, const PrimeTab* pt, int log_n) {
+  extern __shared__ ulonglong2 skey[];  // [S][beta][KS_TILE] (component 0, component 1)
   const size_t N = (size_t)1 << log_n;
   const int nb = limbs + K, npk = L1 + K;
   const int pos = blockIdx.y;
@@ -239,32 +253,41 @@ __global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* ext, Key
   const size_t jn = (size_t)blockIdx.x * KS_TILE + threadIdx.x;
   if (jn >= N) return;
   for (int st = 0; st < S; st++)
-    for (int dg = 0; dg < beta; dg++)
-      for (int cp = 0; cp < 2; cp++)
-        skey[((st * beta + dg) * 2 + cp) * KS_TILE + threadIdx.x] =
-            keys.k[st][(((size_t)dg * 2 + cp) * npk + g) * N + jn];
+    for (int dg = 0; dg < beta; dg++) {
+      const u64* kp = keys.k[st] + ((size_t)dg * 2 * npk + g) * N + jn;
+      skey[(st * beta + dg) * KS_TILE + threadIdx.x] = make_ulonglong2(__ldg(kp), __ldg(kp + (size_t)npk * N));
+    }
   const Mod md = pt[g].mod;
+  const u64 qneg = pt[g].qinv_neg;
   const size_t ustep = (size_t)n * 2 * nb * N;
-  for (int c = 0; c < n; c++) {
-    const u64* Ep = ext + (size_t)c * beta * nb * N + (size_t)pos * N + jn;
-    u64 e[MAXB];
+  const size_t cstride = (size_t)beta * nb * N;
+  const u64* Ep = ext + (size_t)pos * N + jn;
+  u64 e[MAXB];
 #pragma unroll
-    for (int dg = 0; dg < MAXB; dg++)
-      if (dg < beta) e[dg] = Ep[(size_t)dg * nb * N];
+  for (int dg = 0; dg < MAXB; dg++) e[dg] = dg < beta ? Ep[(size_t)dg * nb * N] : 0;
+  for (int c = 0; c < n; c++) {
+    u64 en[MAXB];
+    const u64* En = Ep + (size_t)(c + 1 < n ? c + 1 : c) * cstride;
+#pragma unroll
+    for (int dg = 0; dg < MAXB; dg++) en[dg] = dg < beta ? En[(size_t)dg * nb * N] : 0;
+    u64* U = u + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
     for (int st = 0; st < S; st++) {
-      const u64* kk = skey + (size_t)st * beta * 2 * KS_TILE + threadIdx.x;
+      const ulonglong2* kk = skey + (size_t)st * beta * KS_TILE + threadIdx.x;
       Acc128 a0{0, 0}, a1{0, 0};
 #pragma unroll
       for (int dg = 0; dg < MAXB; dg++) {
         if (dg < beta) {
-          mac128(a0, e[dg], kk[(dg * 2) * KS_TILE]);
-          mac128(a1, e[dg], kk[(dg * 2 + 1) * KS_TILE]);
+          const ulonglong2 kv = kk[dg * KS_TILE];
+          mac128(a0, e[dg], kv.x);
+          mac128(a1, e[dg], kv.y);
         }
       }
-      u64* U = u + st * ustep + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
-      U[0] = reduce128(a0.hi, a0.lo, md);
-      U[(size_t)nb * N] = reduce128(a1.hi, a1.lo, md);
+      // keys are in Montgomery form: the reduction divides the sum by 2^64 (beta q^2 < q 2^64)
+      U[st * ustep] = redc128(a0.hi, a0.lo, md.q, qneg);
+      U[st * ustep + (size_t)nb * N] = redc128(a1.hi, a1.lo, md.q, qneg);
     }
+#pragma unroll
+    for (int dg = 0; dg < MAXB; dg++) e[dg] = en[dg];
   }
 }
 
@@ -408,7 +431,10 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
   __syncthreads();
   const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
   if (n0 >= N) return;
-  const u64 q = pt[i].mod.q, q2 = 2 * q;
+  const u64 q = pt[i].mod.q, one_sh = pt[i].one_sh;
+  // lazy products are below 2q: a word holds `room` of them on top of a reduced sum
+  const u64 fit = (~0ull) / (2 * q) - 1;
+  const int room = fit > (1u << 20) ? (1 << 20) : (int)fit;
   const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
   for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
     for (int o0 = 0; o0 < c_out; o0 += OB) {
@@ -417,6 +443,7 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
       for (int t = 0; t < OB; t++)
 #pragma unroll
         for (int v = 0; v < TN; v++) acc[t][v] = 0;
+      int pending = 0;
       for (int c = 0; c < c_in; c++)
         for (int b = 0; b < k; b++) {
           const u64* src = rot + ((size_t)(c * w_in + stride * jp + b) * k) * 2 * LN + off;
@@ -431,16 +458,20 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
               for (int v = 0; v < TN; v++) x[v] = src[(size_t)a * 2 * LN + v];
             }
             const ulonglong2* wr = sw + (size_t)o0 * T + (c * k + a) * k + b;
+            if (pending == room) {  // uniform across the block
+#pragma unroll
+              for (int t = 0; t < OB; t++)
+#pragma unroll
+                for (int v = 0; v < TN; v++) acc[t][v] = shoup_lazy(acc[t][v], 1, one_sh, q);
+              pending = 0;
+            }
+            pending++;
 #pragma unroll
             for (int t = 0; t < OB; t++) {
               if (o0 + t < c_out) {
                 const ulonglong2 ww = wr[(size_t)t * T];
 #pragma unroll
-                for (int v = 0; v < TN; v++) {
-                  u64 sacc = acc[t][v] + shoup_lazy(x[v], ww.x, ww.y, q);
-                  if (sacc >= q2) sacc -= q2;
-                  acc[t][v] = sacc;
-                }
+                for (int v = 0; v < TN; v++) acc[t][v] += shoup_lazy(x[v], ww.x, ww.y, q);
               }
             }
           }
@@ -450,7 +481,7 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
         if (o0 + t < c_out) {
           u64* dst = out + ((size_t)(o0 + t) * w_out + jp) * 2 * LN + off;
 #pragma unroll
-          for (int v = 0; v < TN; v++) dst[v] = acc[t][v] >= q ? acc[t][v] - q : acc[t][v];
+          for (int v = 0; v < TN; v++) dst[v] = shoup(acc[t][v], 1, one_sh, q);
         }
       }
     }
@@ -653,6 +684,10 @@ void k_mul(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, cons
   HE_LAUNCH_P(k_mul_kernel, (size_t)n_polys * lm.lpp * C.N, 8.0 * (double)C.N * 3 * n_polys * lm.lpp,
               (double)C.N * n_polys * lm.lpp, a, b, out, n_polys, lm, C.dev_ptab(), C.log_n);
 }
+void k_mont_form(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
+  HE_LAUNCH_P(k_mont_form_kernel, (size_t)n_polys * lm.lpp * C.N, 16.0 * (double)C.N * n_polys * lm.lpp,
+              (double)C.N * n_polys * lm.lpp, data, n_polys, lm, C.dev_ptab(), C.log_n);
+}
 void k_permute(const Ctx& C, const u64* in, u64* out, size_t rows, u64 k) {
   HE_LAUNCH(k_permute_kernel, rows * C.N, 8.0 * (double)C.N * 2 * rows, in, out, rows, k, C.log_n);
 }
@@ -698,7 +733,7 @@ void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u
   const int beta = C.beta_at(limbs);
   if (beta > 16) throw Error(8, "more than 16 key-switching digits are not supported");
   if (S < 1 || S > 8) throw Error(1, "1..8 keys per inner-product launch");
-  const size_t per_step = (size_t)beta * 2 * KS_TILE * 8;
+  const size_t per_step = (size_t)beta * KS_TILE * 16;
   // steps per launch so that the staged key tiles fit in 96 KiB of shared memory
   const int sc = (int)std::max<size_t>(1, std::min<size_t>((size_t)S, (96 * 1024) / per_step));
   static bool attr = false;
