@@ -218,11 +218,17 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
   C.d_ipsi = DevBuf(ipsi_tab.size(), st);
   upload(C, C.d_ipsi.p, ipsi_tab.data(), ipsi_tab.size() * 8);
 
-  // ModUp tables per level: digit j covers primes [j alpha, min((j+1) alpha, limbs))
+  // ModUp tables per level (`limbs`); digit j covers primes [j alpha, min((j+1) alpha, limbs)):
+  //   inv   [L1+1][L1][2]         (D_j/q_i)^{-1} mod q_i, Shoup companion
+  //   hat   [L1+1][L1][L1+K][2]   (D_j/q_i) mod t_pos, pos over {q_0..q_{limbs-1}, p_0..}, companion
+  //   scale [L1+1][L1][2]         N^{-1} (D_j/q_i)^{-1} mod q_i, companion
+  // Each conversion term [x_i (D_j/q_i)^{-1}]_{q_i} (D_j/q_i) is a lazy Shoup product below 2 t.
   const int L1 = C.L1, K = C.K;
-  std::vector<u64> up((size_t)(L1 + 1) * L1 * 2 + (size_t)(L1 + 1) * L1 * (L1 + K) * 2, 0);
+  std::vector<u64> up((size_t)(L1 + 1) * L1 * 2 + (size_t)(L1 + 1) * L1 * (L1 + K) * 2 + (size_t)(L1 + 1) * L1 * 2, 0);
   u64* up_inv = up.data();
   u64* up_hat = up.data() + (size_t)(L1 + 1) * L1 * 2;
+  // N^{-1} (D_j/q_i)^{-1} mod q_i: the inverse transform before ModUp ends with this one factor
+  u64* up_scale = up_hat + (size_t)(L1 + 1) * L1 * (L1 + K) * 2;
   for (int limbs = 1; limbs <= L1; limbs++) {
     for (int i = 0; i < limbs; i++) {
       const int lo = (i / alpha) * alpha, hi = std::min(lo + alpha, limbs);
@@ -232,6 +238,9 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
       const u64 hinv = inv_h(h, C.q[i]);
       up_inv[((size_t)limbs * L1 + i) * 2] = hinv;
       up_inv[((size_t)limbs * L1 + i) * 2 + 1] = shoup_of(hinv, C.q[i]);
+      const u64 sc = mul_h(C.ptab[i].ninv, hinv, C.q[i]);
+      up_scale[((size_t)limbs * L1 + i) * 2] = sc;
+      up_scale[((size_t)limbs * L1 + i) * 2 + 1] = shoup_of(sc, C.q[i]);
       for (int pos = 0; pos < limbs + K; pos++) {
         const u64 t = C.q[pos < limbs ? pos : L1 + (pos - limbs)];
         u64 ht = 1;
@@ -248,7 +257,7 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
 
   // ModDown tables: (P/p_k)^{-1} mod p_k, (P/p_k) mod q_i, P^{-1} mod q_i, each with its
   // Shoup companion
-  std::vector<u64> down((size_t)2 * K + (size_t)2 * K * L1 + (size_t)2 * L1);
+  std::vector<u64> down((size_t)2 * K + (size_t)2 * K * L1 + (size_t)2 * L1 + (size_t)2 * K);
   for (int k = 0; k < K; k++) {
     const u64 pk = P[k];
     u64 h = 1;
@@ -269,6 +278,13 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
     const u64 pinv = inv_h(C.ptab[i].pmod, C.q[i]);
     down[2 * K + (size_t)2 * K * L1 + 2 * i] = pinv;
     down[2 * K + (size_t)2 * K * L1 + 2 * i + 1] = shoup_of(pinv, C.q[i]);
+  }
+  // N^{-1} (P/p_k)^{-1} mod p_k: the inverse transform of the P part ends with this one factor
+  for (int k = 0; k < K; k++) {
+    const u64 pk = P[k];
+    const u64 v = mul_h(C.ptab[L1 + k].ninv, down[2 * k], pk);
+    down[2 * K + (size_t)2 * K * L1 + 2 * L1 + 2 * k] = v;
+    down[2 * K + (size_t)2 * K * L1 + 2 * L1 + 2 * k + 1] = shoup_of(v, pk);
   }
   C.d_down = DevBuf(down.size(), st);
   upload(C, C.d_down.p, down.data(), down.size() * 8);

@@ -36,11 +36,6 @@ static LimbMap ext_map(const Ctx& C, int limbs) {
   m.poly_stride = (size_t)(limbs + C.K) * C.N;
   return m;
 }
-static LimbMap p_map(const Ctx& C) {
-  LimbMap m;
-  m.lpp = C.K; m.split = 0; m.base0 = 0; m.base1 = C.L1; m.poly_stride = (size_t)C.K * C.N;
-  return m;
-}
 
 static u64 residue_of(int64_t v, u64 q) {
   const int64_t r = v % (int64_t)q;
@@ -52,20 +47,24 @@ static u64 residue_of(int64_t v, u64 q) {
 static DevBuf modup_poly(Ctx& C, const CtSet& in, int poly) {
   const int n = in.n, lp = in.limbs, beta = C.beta_at(lp), nb = lp + C.K;
   const size_t N = C.N;
+  // the polynomial to the coefficient domain, each limb times N^{-1} (D_j/q_i)^{-1}
   DevBuf x((size_t)n * lp * N, C.stream);
   k_copy_limbs(C, in.buf.p + (size_t)poly * lp * N, in.ct_words(), x.p, (size_t)lp * N, (size_t)n, lp);
-  ntt_inverse(C, x.p, n, limbs_q(lp, N));
+  ntt_inverse_qscaled(C, x.p, n, lp);
   DevBuf ext((size_t)n * beta * nb * N, C.stream);
-  k_modup(C, x.p, in.buf.p + (size_t)poly * lp * N, in.ct_words(), ext.p, n, lp);
-  // each digit's own limbs are already in the NTT domain: transform the others
+  const ulonglong2* hat_level = reinterpret_cast<const ulonglong2*>(C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2) +
+                                (size_t)lp * C.L1 * (C.L1 + C.K);
   for (int j = 0; j < beta; j++) {
     const int lo = j * C.alpha, cnt = std::min(C.alpha, lp - lo);
+    // the digit's own limbs are the input itself (the inner product reads them there); the
+    // others: base conversion in the load of their forward transform
     LimbMap m = ext_map(C, lp);
     m.lpp = nb - cnt;
     m.gap_at = lo;
     m.gap = cnt;
     m.poly_stride = (size_t)beta * nb * N;
-    ntt_forward(C, ext.p + (size_t)j * nb * N, n, m);
+    ntt_forward_modup(C, ext.p + (size_t)j * nb * N, n, m, x.p + (size_t)lo * N, (size_t)lp * N,
+                      reinterpret_cast<const u64*>(hat_level + (size_t)lo * (C.L1 + C.K)), C.L1 + C.K, cnt);
   }
   return ext;
 }
@@ -79,7 +78,7 @@ DevBuf modup_c1(Ctx& C, const CtSet& in) { return modup_poly(C, in, 1); }
 // launch each. mode 0: add the set's first two components (relinearisation of
 // d2); mode 1: add phi_k(c0). Output ciphertext c of step s goes to
 // outs[s] + c * out_stride.
-static void ks_finish(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<u64>& ks, int mode,
+static void ks_finish(Ctx& C, const CtSet& in, int poly, const DevBuf& ext, const std::vector<u64>& ks, int mode,
                       const std::vector<u64*>& outs, size_t out_stride) {
   const int n = in.n, lp = in.limbs, nb = lp + C.K, S = (int)ks.size();
   if (S == 0) return;
@@ -90,18 +89,17 @@ static void ks_finish(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vec
     const int cs = std::min(8, S - s0);
     KeyPtrs kp{};
     for (int t = 0; t < cs; t++) kp.k[t] = C.key(ks[s0 + t]).p;
-    k_ks_inner(C, ext.p, kp, cs, u.p + s0 * ustep, n, lp);
+    k_ks_inner(C, ext.p, in.buf.p + (size_t)poly * lp * N, in.ct_words(), kp, cs, u.p + s0 * ustep, n, lp);
   }
+  // ModDown: the P part (permuted by the step's automorphism) to the coefficient domain, scaled
+  // for the base conversion; the conversion, forward transform and combine run as one transform
   DevBuf pl((size_t)S * pstep, C.stream);
   for (int s = 0; s < S; s++) k_gather_p(C, u.p + s * ustep, pl.p + s * pstep, n, lp, ks[s]);
-  ntt_inverse(C, pl.p, S * n * 2, p_map(C));
-  DevBuf z((size_t)S * zstep, C.stream);
-  k_moddown_bconv(C, pl.p, z.p, S * n, lp);
-  pl.reset();
-  ntt_forward(C, z.p, S * n * 2, limbs_q(lp, N));
+  ntt_inverse_pscaled(C, pl.p, S * n * 2);
+  DevBuf z(zstep, C.stream);
   for (int s = 0; s < S; s++)
-    k_moddown_combine(C, u.p + s * ustep, z.p + s * zstep, in.buf.p, in.ct_words(), outs[s], out_stride, n, lp,
-                      ks[s], mode);
+    ntt_forward_moddown(C, z.p, pl.p + s * pstep, n, lp, u.p + s * ustep, nb, in.buf.p, in.ct_words(), outs[s],
+                        out_stride, ks[s], mode);
 }
 
 void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vector<long>& steps, u64* out,
@@ -119,7 +117,7 @@ void rotate_from_ext(Ctx& C, const CtSet& in, const DevBuf& ext, const std::vect
     ks.push_back(k);
     outs.push_back(o);
   }
-  ks_finish(C, in, ext, ks, 1, outs, cw * out_cts_per_ct);
+  ks_finish(C, in, 1, ext, ks, 1, outs, cw * out_cts_per_ct);
 }
 
 // Ciphertexts [first, first + n) of a set, without owning their memory.
@@ -161,7 +159,7 @@ std::unique_ptr<CtSet> relinearized(Ctx& C, const CtSet& s) {
     const int cn = std::min(step, s.n - c0);
     SetView v(s, c0, cn);
     DevBuf ext = modup_poly(C, v.s, 2);
-    ks_finish(C, v.s, ext, {1}, 0, {out->ct(c0)}, out->ct_words());
+    ks_finish(C, v.s, 2, ext, {1}, 0, {out->ct(c0)}, out->ct_words());
   }
   return out;
 }

@@ -161,4 +161,18 @@ HE_HD u64 reduce4q(u64 a, u64 q) {
   return a;
 }
 
+#if defined(__CUDACC__)
+__device__ __forceinline__ u32 brv_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+
+// Index j' with NTT(phi_k(a))[j] = NTT(a)[j'] for the bit-reversed evaluation
+// order: slot j holds a(psi^(2 brv(j) + 1)), and phi_k maps that point to
+// psi^((2 brv(j) + 1) k).
+__device__ __forceinline__ u32 galois_index(u32 j, u64 k, int log_n) {
+  const u64 two_n_mask = (2ull << log_n) - 1;
+  const u64 e = 2 * (u64)brv_bits(j, log_n) + 1;
+  const u64 e2 = (e * k) & two_n_mask;
+  return brv_bits((u32)((e2 - 1) >> 1), log_n);
+}
+#endif
+
 }  // namespace he

@@ -146,6 +146,24 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // rescale of `rows` polynomials x [rows][lp][N] whose limb lp - 1 is already in the
 // coefficient domain: out [rows][lp - 1][N] = (x_i - NTT_i(expanded last limb)) q_l^{-1}
 void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp);
+// inverse transform of n_polys polynomials [n_polys][lp][N] over q_0..q_{lp-1}, ending with
+// the factor N^{-1} (D_j/q_i)^{-1} mod q_i (the first step of ModUp's base conversion)
+void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp);
+// ModUp of one digit fused into the forward transform of its extended limbs: polynomial p,
+// launch limb i (position lm.mem(i)) gets sum_{t < cnt} yt[p ystride + t N] hat[t hstride +
+// lm.mem(i)] and is transformed; lm skips the digit's own limbs
+void ntt_forward_modup(const Ctx& C, u64* ext_digit, int n, const LimbMap& lm, const u64* yt, size_t ystride,
+                       const u64* hat, int hstride, int cnt);
+// inverse transform of n_polys P-part polynomials [n_polys][K][N], ending with the
+// factor N^{-1} (P/p_k)^{-1} mod p_k (the first step of ModDown's base conversion)
+void ntt_inverse_pscaled(const Ctx& C, u64* data, int n_polys);
+// ModDown of the n ciphertexts of one key-switch step, fused into the forward
+// transform of z = BConv_{P->Q}(yt): yt [n][2][K][N] from ntt_inverse_pscaled, z
+// scratch [n][2][lp][N], u the inner products [n][2][nb][N]; writes
+// out[c][comp] = (u_Q[pi_gk] - z) P^{-1} + base term (kmode 0: base[c][comp];
+// kmode 1: comp 0 gets base[c][0][pi_gk]), ciphertext c at out + c out_stride
+void ntt_forward_moddown(const Ctx& C, u64* z, const u64* yt, int n, int lp, const u64* u, int nb, const u64* base,
+                         size_t base_stride, u64* out, size_t out_stride, u64 gk, int kmode);
 inline LimbMap limbs_q(int limbs, size_t N) {  // plain polynomials, primes 0..limbs-1
   LimbMap m;
   m.lpp = limbs; m.split = limbs; m.base0 = 0; m.base1 = 0; m.poly_stride = (size_t)limbs * N;
@@ -171,24 +189,16 @@ void k_decrypt_limb0(const Ctx& C, const u64* ct, int limbs, int n, u64* out);
 void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int limbs);
 // d[n][3][limbs] = tensor(a[n][2], b[n][2])
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs);
-// ModUp fast base conversion: x coeff [n][limbs][N] -> ext [n][beta][limbs+K][N], coefficient
-// domain except each digit's own limbs, which are copied from the NTT-domain input
-// xntt (ciphertext c at xntt + c * xntt_stride)
-void k_modup(const Ctx& C, const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs);
 // key pointers of up to 8 steps for one inner-product launch
 struct KeyPtrs {
   const u64* k[8];
 };
-// u[s][n][2][limbs+K] = sum_j ext[n][j] * key_s[j]  (NTT domain), s < S
-void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u, int n, int limbs);
+// u[s][n][2][limbs+K] = sum_j ext[n][j] * key_s[j]  (NTT domain), s < S; digit j's own limbs
+// (positions j alpha ..) are read from the input polynomial own + c own_stride instead of ext
+void k_ks_inner(const Ctx& C, const u64* ext, const u64* own, size_t own_stride, const KeyPtrs& keys, int S, u64* u,
+                int n, int limbs);
 // gather P limbs of u (permuted by pi_k) into p [n][2][K][N]
 void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k);
-// ModDown base conversion: p coeff [n][2][K][N] -> z coeff [n][2][limbs][N]
-void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs);
-// out[n][2][limbs] = (u_Q[pi_k] - z) P^{-1} + add[pi_k or id]; add0/add1 may be null
-//   mode 0 (relin): out_c = d_c + ((u_c - z_c) P^{-1});  mode 1 (rotate): out_0 = phi_k(c0) + ..., out_1 = ...
-void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
-                       size_t out_stride, int n, int limbs, u64 k, int mode);
 // rescale helpers
 void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs);
 void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int rows, int limbs);
@@ -228,7 +238,8 @@ void export_raw(Ctx& C, const CtSet& s, u64* host);
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale,
                                      bool ntt_domain = false);
 
-// ModUp of polynomial 1 of every ciphertext: ext [n][beta][limbs+K][N], NTT domain
+// ModUp of polynomial 1 of every ciphertext: ext [n][beta][limbs+K][N], NTT domain, except
+// each digit's own limbs, which are left unset (they equal the input polynomial's limbs)
 DevBuf modup_c1(Ctx& C, const CtSet& in);
 // Rot by each step from a ModUp made by modup_c1; out ciphertext (c, s) at
 // out + (c * out_cts_per_ct + s) * ct_words

@@ -29,15 +29,6 @@ inline unsigned grid_for(size_t total) {
 #define HE_GRID_LOOP(idx, total) \
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (total); idx += (size_t)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ u32 brv_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
-
-// Index j' with NTT(phi_k(a))[j] = NTT(a)[j'].
-__device__ __forceinline__ u32 galois_index(u32 j, u64 k, int log_n) {
-  const u64 two_n_mask = (2ull << log_n) - 1;
-  const u64 e = 2 * (u64)brv_bits(j, log_n) + 1;
-  const u64 e2 = (e * k) & two_n_mask;
-  return brv_bits((u32)((e2 - 1) >> 1), log_n);
-}
 
 __device__ __forceinline__ u64 reduce_i64(int64_t v, const Mod& m) {
   if (v >= 0) return reduce128(0, (u64)v, m);
@@ -179,58 +170,6 @@ __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int l
   }
 }
 
-// ModUp. Constant tables (words of d_up, indexed by the level `limbs`):
-//   inv [L1+1][L1][2]         (D_j/q_i)^{-1} mod q_i and its Shoup companion
-//   hat [L1+1][L1][L1+K][2]   (D_j/q_i) mod t_pos and its Shoup companion,
-//                             pos over {q_0..q_{limbs-1}, p_0..}
-// Each term [x_i (D_j/q_i)^{-1}]_{q_i} (D_j/q_i) is a Shoup product in [0, 2t)
-// (valid for any multiplicand below 2^64); partial sums stay below 2t.
-template <int ALPHA>
-__global__ void k_modup_kernel(const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs,
-                               int alpha_rt, int beta, int L1, int K, const u64* up_inv, const u64* up_hat,
-                               const PrimeTab* pt, int log_n) {
-  const size_t N = (size_t)1 << log_n;
-  const int nb = limbs + K;
-  const int alpha = ALPHA > 0 ? ALPHA : alpha_rt;
-  const size_t total = (size_t)n * beta * N;
-  const u64* inv = up_inv + (size_t)limbs * L1 * 2;
-  const ulonglong2* hat = reinterpret_cast<const ulonglong2*>(up_hat) + (size_t)limbs * L1 * (L1 + K);
-  HE_GRID_LOOP(idx, total) {
-    const size_t jn = idx & (N - 1);
-    const size_t r = idx >> log_n;
-    const int dg = (int)(r % beta), c = (int)(r / beta);
-    const int lo = dg * alpha, cnt = min(alpha, limbs - lo), hi = lo + cnt;
-    const u64* X = x + (size_t)c * limbs * N;
-    u64* E = ext + ((size_t)c * beta + dg) * nb * N;
-    u64 y[ALPHA > 0 ? ALPHA : 8];
-#pragma unroll
-    for (int ii = 0; ii < (ALPHA > 0 ? ALPHA : 8); ii++) {
-      if (ii < cnt) {
-        const int i = lo + ii;
-        const u64 xi = X[(size_t)i * N + jn];
-        y[ii] = shoup(xi, inv[i * 2], inv[i * 2 + 1], pt[i].mod.q);
-        // the digit's own limbs: BConv gives x_i itself, already known in the NTT domain
-        E[(size_t)i * N + jn] = xntt[(size_t)c * xntt_stride + (size_t)i * N + jn];
-      }
-    }
-    for (int pos = 0; pos < nb; pos++) {
-      if (pos >= lo && pos < hi) continue;
-      const int g = pos < limbs ? pos : L1 + (pos - limbs);
-      const u64 t = pt[g].mod.q, t2 = 2 * t;
-      const ulonglong2* hp = hat + (size_t)lo * (L1 + K) + pos;
-      u64 s = 0;
-#pragma unroll
-      for (int ii = 0; ii < (ALPHA > 0 ? ALPHA : 8); ii++) {
-        if (ii < cnt) {
-          const ulonglong2 h = __ldg(hp + (size_t)ii * (L1 + K));
-          s += shoup_lazy(y[ii], h.x, h.y, t);
-          if (s >= t2) s -= t2;
-        }
-      }
-      E[(size_t)pos * N + jn] = s >= t ? s - t : s;
-    }
-  }
-}
 
 // u[s][c][comp][pos] = sum_j ext[c][j][pos] key_s[j][comp][g(pos)] for the
 // steps s of one launch. A block owns one limb position `pos` and a tile of
@@ -242,7 +181,8 @@ __global__ void k_modup_kernel(const u64* x, const u64* xntt, size_t xntt_stride
 // launch instead of one per ciphertext.
 constexpr int KS_TILE = 128;
 template <int MAXB>
-__global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* __restrict__ ext, KeyPtrs keys, int S,
+__global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* __restrict__ ext, const u64* __restrict__ own,
+                                                             size_t own_stride, int alpha, KeyPtrs keys, int S,
                                                              u64* __restrict__ u, int n, int limbs, int beta, int L1,
                                                              int K, const PrimeTab* pt, int log_n) {
   extern __shared__ ulonglong2 skey[];  // [S][beta][KS_TILE] (component 0, component 1)
@@ -261,15 +201,21 @@ __global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* __restri
   const u64 qneg = pt[g].qinv_neg;
   const size_t ustep = (size_t)n * 2 * nb * N;
   const size_t cstride = (size_t)beta * nb * N;
+  // digit dg at this position: the ModUp output, or for the digit's own primes the input itself
   const u64* Ep = ext + (size_t)pos * N + jn;
+  const u64* Op = own + (size_t)pos * N + jn;
+  const int own_dg = pos < limbs ? pos / alpha : -1;
+  auto digit = [&](int c, int dg) {
+    return dg == own_dg ? Op[(size_t)c * own_stride] : Ep[(size_t)c * cstride + (size_t)dg * nb * N];
+  };
   u64 e[MAXB];
 #pragma unroll
-  for (int dg = 0; dg < MAXB; dg++) e[dg] = dg < beta ? Ep[(size_t)dg * nb * N] : 0;
+  for (int dg = 0; dg < MAXB; dg++) e[dg] = dg < beta ? digit(0, dg) : 0;
   for (int c = 0; c < n; c++) {
     u64 en[MAXB];
-    const u64* En = Ep + (size_t)(c + 1 < n ? c + 1 : c) * cstride;
+    const int cn = c + 1 < n ? c + 1 : c;
 #pragma unroll
-    for (int dg = 0; dg < MAXB; dg++) en[dg] = dg < beta ? En[(size_t)dg * nb * N] : 0;
+    for (int dg = 0; dg < MAXB; dg++) en[dg] = dg < beta ? digit(cn, dg) : 0;
     u64* U = u + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
     for (int st = 0; st < S; st++) {
       const ulonglong2* kk = skey + (size_t)st * beta * KS_TILE + threadIdx.x;
@@ -302,62 +248,6 @@ __global__ void k_gather_p_kernel(const u64* u, u64* p, int n, int limbs, int K,
     const size_t cc = r / K;  // ciphertext * 2 + component
     const u32 src = k == 1 ? (u32)jn : galois_index((u32)jn, k, log_n);
     p[idx] = u[(cc * nb + limbs + kk) * N + src];
-  }
-}
-
-// ModDown constants (words of d_down):
-//   pinv [K][2]       (P/p_k)^{-1} mod p_k, Shoup companion
-//   phat [K][L1][2]   (P/p_k) mod q_i, Shoup companion
-//   Pinv [L1][2]      P^{-1} mod q_i, Shoup companion
-__global__ void k_moddown_bconv_kernel(const u64* p, u64* z, int n, int limbs, int L1, int K, const u64* down,
-                                       const PrimeTab* pt, int log_n) {
-  const size_t N = (size_t)1 << log_n;
-  const size_t total = (size_t)n * 2 * N;
-  const u64* pinv = down;
-  const ulonglong2* phat = reinterpret_cast<const ulonglong2*>(down + 2 * K);
-  HE_GRID_LOOP(idx, total) {
-    const size_t jn = idx & (N - 1), cc = idx >> log_n;
-    u64 y[4];
-    for (int kk = 0; kk < K; kk++)
-      y[kk] = shoup(p[(cc * K + kk) * N + jn], pinv[2 * kk], pinv[2 * kk + 1], pt[L1 + kk].mod.q);
-    for (int i = 0; i < limbs; i++) {
-      const u64 q = pt[i].mod.q, q2 = 2 * q;
-      u64 s = 0;
-      for (int kk = 0; kk < K; kk++) {
-        const ulonglong2 h = __ldg(phat + (size_t)kk * L1 + i);
-        s += shoup_lazy(y[kk], h.x, h.y, q);
-        if (s >= q2) s -= q2;
-      }
-      z[(cc * limbs + i) * N + jn] = s >= q ? s - q : s;
-    }
-  }
-}
-
-// out[c][comp][i][j] = (u[c][comp][i][pi(j)] - z[c][comp][i][j]) P^{-1}  plus
-//   mode 0: base[c][comp][i][j]                (relinearisation: d0, d1)
-//   mode 1: comp 0 only, base[c][0][i][pi(j)]   (rotation: phi_k(c0))
-__global__ void k_moddown_combine_kernel(const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
-                                         size_t out_stride, int n, int limbs, int K, u64 k, int mode, const u64* Pinv,
-                                         const PrimeTab* pt, int log_n) {
-  const size_t N = (size_t)1 << log_n;
-  const int nb = limbs + K;
-  const size_t LN = (size_t)limbs * N;
-  const size_t total = (size_t)n * 2 * LN;
-  HE_GRID_LOOP(idx, total) {
-    const size_t jn = idx & (N - 1);
-    const size_t r = idx >> log_n;
-    const int i = (int)(r % limbs);
-    const size_t cc = r / limbs;
-    const int comp = (int)(cc & 1);
-    const size_t c = cc >> 1;
-    const u32 src = k == 1 ? (u32)jn : galois_index((u32)jn, k, log_n);
-    const u64 q = pt[i].mod.q;
-    const u64 uu = u[(cc * nb + i) * N + src];
-    const u64 v = shoup(submod(uu, z[idx], q), Pinv[2 * i], Pinv[2 * i + 1], q);
-    u64 add = 0;
-    if (mode == 0) add = base[c * base_stride + (size_t)comp * LN + (size_t)i * N + jn];
-    else if (comp == 0) add = base[c * base_stride + (size_t)i * N + src];
-    out[c * out_stride + (size_t)comp * LN + (size_t)i * N + jn] = addmod(v, add, q);
   }
 }
 
@@ -700,36 +590,8 @@ void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int 
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs) {
   HE_LAUNCH_P(k_tensor_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 7 * n * limbs, 4.0 * C.N * n * limbs, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
 }
-void k_modup(const Ctx& C, const u64* x, const u64* xntt, size_t xntt_stride, u64* ext, int n, int limbs) {
-  if (C.alpha > 8) throw Error(8, "digits of more than 8 primes are not supported");
-  const u64* up_inv = C.d_up.p;
-  const u64* up_hat = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2;
-  const int beta = C.beta_at(limbs);
-  const size_t total = (size_t)n * beta * C.N;
-  // coefficient input, the own limbs again in the NTT domain, the extended digits
-  const double bytes = 8.0 * (double)C.N * n * (2.0 * limbs + (double)beta * (limbs + C.K));
-  double prods = 0.0;  // per coefficient: x_i (D_j/q_i)^{-1}, then cnt terms for every other limb
-  for (int j = 0; j < beta; j++) {
-    const int cnt = std::min(C.alpha, limbs - j * C.alpha);
-    prods += cnt + (double)cnt * (limbs + C.K - cnt);
-  }
-  prods *= (double)C.N * n;
-  switch (C.alpha) {
-    case 1:
-      HE_LAUNCH_P(k_modup_kernel<1>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
-                C.dev_ptab(), C.log_n);
-      break;
-    case 2:
-      HE_LAUNCH_P(k_modup_kernel<2>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
-                C.dev_ptab(), C.log_n);
-      break;
-    default:
-      HE_LAUNCH_P(k_modup_kernel<0>, total, bytes, prods, x, xntt, xntt_stride, ext, n, limbs, C.alpha, beta, C.L1, C.K, up_inv, up_hat,
-                C.dev_ptab(), C.log_n);
-      break;
-  }
-}
-void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u, int n, int limbs) {
+void k_ks_inner(const Ctx& C, const u64* ext, const u64* own, size_t own_stride, const KeyPtrs& keys, int S, u64* u,
+                int n, int limbs) {
   const int beta = C.beta_at(limbs);
   if (beta > 16) throw Error(8, "more than 16 key-switching digits are not supported");
   if (S < 1 || S > 8) throw Error(1, "1..8 keys per inner-product launch");
@@ -754,30 +616,17 @@ void k_ks_inner(const Ctx& C, const u64* ext, const KeyPtrs& keys, int S, u64* u
     void* tok = prof_begin(beta <= 8 ? "k_ks_inner_kernel<8>" : "k_ks_inner_kernel<16>", C.stream, bytes,
                            2.0 * C.N * nb * beta * (double)n * cs);
     if (beta <= 8)
-      k_ks_inner_kernel<8><<<grid, KS_TILE, smem, C.stream>>>(ext, kp, cs, u + s0 * ustep, n, limbs, beta, C.L1, C.K,
-                                                               C.dev_ptab(), C.log_n);
+      k_ks_inner_kernel<8><<<grid, KS_TILE, smem, C.stream>>>(ext, own, own_stride, C.alpha, kp, cs, u + s0 * ustep,
+                                                               n, limbs, beta, C.L1, C.K, C.dev_ptab(), C.log_n);
     else
-      k_ks_inner_kernel<16><<<grid, KS_TILE, smem, C.stream>>>(ext, kp, cs, u + s0 * ustep, n, limbs, beta, C.L1,
-                                                                C.K, C.dev_ptab(), C.log_n);
+      k_ks_inner_kernel<16><<<grid, KS_TILE, smem, C.stream>>>(ext, own, own_stride, C.alpha, kp, cs, u + s0 * ustep,
+                                                                n, limbs, beta, C.L1, C.K, C.dev_ptab(), C.log_n);
     prof_end(tok, C.stream);
     HE_CUDA(cudaGetLastError());
   }
 }
 void k_gather_p(const Ctx& C, const u64* u, u64* p, int n, int limbs, u64 k) {
   HE_LAUNCH(k_gather_p_kernel, (size_t)n * 2 * C.K * C.N, 8.0 * (double)C.N * 4 * n * C.K, u, p, n, limbs, C.K, k, C.log_n);
-}
-void k_moddown_bconv(const Ctx& C, const u64* p, u64* z, int n, int limbs) {
-  if (C.K > 4) throw Error(8, "more than 4 special primes are not supported");
-  HE_LAUNCH_P(k_moddown_bconv_kernel, (size_t)n * 2 * C.N, 8.0 * (double)C.N * 2 * n * (C.K + limbs),
-              2.0 * C.N * n * C.K * (1.0 + limbs), p, z, n, limbs, C.L1, C.K, C.d_down.p, C.dev_ptab(),
-            C.log_n);
-}
-void k_moddown_combine(const Ctx& C, const u64* u, const u64* z, const u64* base, size_t base_stride, u64* out,
-                       size_t out_stride, int n, int limbs, u64 k, int mode) {
-  const u64* Pinv = C.d_down.p + 2 * C.K + (size_t)2 * C.K * C.L1;
-  HE_LAUNCH_P(k_moddown_combine_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * n * limbs * (mode == 0 ? 8.0 : 7.0),
-              2.0 * C.N * n * limbs, u, z, base, base_stride, out, out_stride, n,
-            limbs, C.K, k, mode, Pinv, C.dev_ptab(), C.log_n);
 }
 void k_rescale_expand(const Ctx& C, const u64* last_coeff, u64* r, int rows, int limbs) {
   const u64* tab = C.d_rs.p + (size_t)limbs * C.L1 * 3;

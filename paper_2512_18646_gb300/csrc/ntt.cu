@@ -31,14 +31,39 @@ namespace he {
 
 namespace {
 
-// Operands of a rescale fused into a forward transform: x [rows][lp][N] holds
-// the polynomials being rescaled, with limb lp - 1 already in the coefficient
-// domain; rs [L1][3] holds floor(q_l/2) mod q_i, q_l^{-1} mod q_i and its
-// Shoup companion for this lp.
-struct RescaleFuse {
+// Operands of work fused into a transform's load (cols kernel) or store (rows
+// kernel), by MODE:
+//  1 rescale:  x [rows][lp][N] holds the polynomials being rescaled, limb lp - 1
+//              already in the coefficient domain; rs [L1][3] holds floor(q_l/2)
+//              mod q_i, q_l^{-1} mod q_i and its Shoup companion for this lp.
+//  2 ModDown:  load: yt [polys][K][N] the P part times N^{-1} (P/p_k)^{-1}
+//              (coefficient domain), phat [K][L1][2] (P/p_k) mod q_i with Shoup
+//              companions; store: out[c][comp][i][j] = (u[c][comp][i][pi(j)] - z)
+//              P^{-1} + (mode 0: base[c][comp][i][j]; mode 1, comp 0:
+//              base[c][0][i][pi(j)]), pi the Galois index of element gk.
+//  3 scaled inverse: the inverse transform ends with the factor iscale[prime -
+//              scale_base] (w, Shoup companion) instead of N^{-1}.
+//  4 ModUp:    load: the target limb at extended position e = lm.mem(i) of digit
+//              polynomial pr is sum_{t < K} yt[pr ystride + t N] hat[t hstride + e],
+//              yt the digit's source limbs times N^{-1} (D_j/q_i)^{-1} (coefficient
+//              domain), hat (D_j/q_i) mod target prime with Shoup companions.
+struct Fuse {
   const u64* x = nullptr;
   const u64* rs = nullptr;
   int lp = 0;
+  const u64* yt = nullptr;
+  const u64* phat = nullptr;
+  int K = 0, L1 = 0, nb = 0, kmode = 0;
+  const u64* u = nullptr;
+  const u64* base = nullptr;
+  size_t base_stride = 0, out_stride = 0;
+  u64* out = nullptr;
+  u64 gk = 1;
+  const u64* pinv = nullptr;
+  const u64* iscale = nullptr;
+  int scale_base = 0;
+  size_t ystride = 0;
+  int hstride = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -94,6 +119,13 @@ struct Plan {
   static constexpr int T = (1 << LOGM) / E;  // threads per sub-transform
   static constexpr int R = (LOGM + 2) / 3;   // rounds
 };
+
+// bit reversal of the low `bits` bits, for compile-time arguments
+__host__ __device__ constexpr u32 brv_const(u32 x, int bits) {
+  u32 r = 0;
+  for (int b = 0; b < bits; b++) r |= ((x >> b) & 1u) << (bits - 1 - b);
+  return r;
+}
 
 __device__ __forceinline__ ulonglong2 tw_load(const u64* tw, u64 idx) {
   return __ldg(reinterpret_cast<const ulonglong2*>(tw) + idx);
@@ -219,7 +251,7 @@ constexpr int kRowThreads = 256;
 // ---------------------------------------------------------------------------
 template <int LOGM, int MODE>
 __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                              const u64* tw_all, int n, int n1, RescaleFuse fz) {
+                                                              const u64* tw_all, int n, int n1, Fuse fz) {
   using P = Plan<LOGM>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
@@ -253,7 +285,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap
   if constexpr (MODE == 0) {
 #pragma unroll
     for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = reduce4q(a[k], q);
-  } else {
+  } else if constexpr (MODE == 1) {
     // rescale: out_i = (x_i - R_i) q_l^{-1} mod q_i, R_i this transform of the expanded last limb
     const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
     const u64* xi = fz.x + ((size_t)pr * fz.lp + i) * N + run * M;
@@ -262,6 +294,33 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap
     for (int k = 0; k < P::E; k++) {
       const int e = xl | ML::kbits(k);
       xr[e] = shoup(submod(xi[e], reduce4q(a[k], q), q), qi, qs, q);
+    }
+  } else {
+    // ModDown combine: (u_Q[pi(j)] - z) P^{-1} plus the part the key switch does not touch
+    const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
+    const int comp = pr & 1;
+    const size_t c = (size_t)(pr >> 1);
+    const size_t LN = (size_t)lm.lpp * N;
+    const u64* ui = fz.u + ((size_t)pr * fz.nb + i) * N;
+    const u64* bi = fz.base + c * fz.base_stride + (fz.kmode == 0 ? (size_t)comp * LN : 0) + (size_t)i * N;
+    u64* oi = fz.out + c * fz.out_stride + (size_t)comp * LN + (size_t)i * N;
+    const u64 pv = fz.pinv[2 * i], ps = fz.pinv[2 * i + 1];
+    const bool add = fz.kmode == 0 || comp == 0;
+    // Galois index of j = run M + e: brv_n(j) = brv_L(e) 2^(n-L) + brv_(n-L)(run), and brv_L(e) is
+    // brv_L(xl) | brv_L(kbits(k)) (disjoint bits), so only a constant is or-ed per element
+    const u32 hb = (brv_bits((u32)xl, LOGM) << (n - LOGM)) | (n > LOGM ? brv_bits((u32)run, n - LOGM) : 0u);
+    const u32 mask = (2u << n) - 1, gk = (u32)fz.gk;
+#pragma unroll
+    for (int k = 0; k < P::E; k++) {
+      const u32 j = (u32)(run * M) + (u32)(xl | ML::kbits(k));
+      u32 src = j;
+      if (gk != 1) {
+        const u32 bj = hb | (brv_const(ML::kbits(k), LOGM) << (n - LOGM));
+        const u32 e2 = ((2 * bj + 1) * gk) & mask;
+        src = brv_bits((e2 - 1) >> 1, n);
+      }
+      const u64 v = shoup(submod(ui[src], reduce4q(a[k], q), q), pv, ps, q);
+      oi[j] = add ? addmod(v, bi[fz.kmode == 0 ? j : src], q) : v;
     }
   }
 }
@@ -308,7 +367,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap
 // ---------------------------------------------------------------------------
 template <int LOGM, int MODE>
 __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
-                               RescaleFuse fz) {
+                               Fuse fz) {
   using P = Plan<LOGM>;
   extern __shared__ u64 smc[];
   const size_t N = (size_t)1 << n;
@@ -328,6 +387,64 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
     if constexpr (MODE == 0) {
 #pragma unroll
       for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(x0 | M0::kbits(k)) * stride];
+    } else if constexpr (MODE == 4) {
+      // ModUp: fast base conversion of the digit, sum_t yt_t (D_j/q_t) mod the target prime
+      const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
+      const u64* y = fz.yt + (size_t)pr * fz.ystride + (size_t)blockIdx.x * C + lo;
+      const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(fz.phat) + lm.mem(i);
+      if (fz.K == 2) {  // two lazy products: below 4q, the transform's input range
+        const ulonglong2 h0 = __ldg(ph), h1 = __ldg(ph + fz.hstride);
+        u64 y0[P::E], y1[P::E];
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+          y0[k] = y[(size_t)(x0 | M0::kbits(k)) * stride];
+          y1[k] = y[N + (size_t)(x0 | M0::kbits(k)) * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < P::E; k++) a[k] = shoup_lazy(y0[k], h0.x, h0.y, q) + shoup_lazy(y1[k], h1.x, h1.y, q);
+      } else {
+        const u64 q2 = 2 * q;
+#pragma unroll
+        for (int k = 0; k < P::E; k++) a[k] = 0;
+        for (int t = 0; t < fz.K; t++) {
+          const ulonglong2 h = __ldg(ph + (size_t)t * fz.hstride);
+          const u64* yk = y + (size_t)t * N;
+#pragma unroll
+          for (int k = 0; k < P::E; k++) {
+            u64 v = a[k] + shoup_lazy(yk[(size_t)(x0 | M0::kbits(k)) * stride], h.x, h.y, q);
+            a[k] = v >= q2 ? v - q2 : v;
+          }
+        }
+      }
+    } else if constexpr (MODE == 2) {
+      // ModDown: fast base conversion of the P part, sum_k yt_k (P/p_k) mod q_i (lazy, below 2q)
+      const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
+      const u64* y = fz.yt + (size_t)pr * fz.K * N + (size_t)blockIdx.x * C + lo;
+      const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(fz.phat) + i;
+      if (fz.K == 2) {  // two lazy products: below 4q, the transform's input range
+        const ulonglong2 h0 = __ldg(ph), h1 = __ldg(ph + fz.L1);
+        u64 y0[P::E], y1[P::E];
+#pragma unroll
+        for (int k = 0; k < P::E; k++) {
+          y0[k] = y[(size_t)(x0 | M0::kbits(k)) * stride];
+          y1[k] = y[N + (size_t)(x0 | M0::kbits(k)) * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < P::E; k++) a[k] = shoup_lazy(y0[k], h0.x, h0.y, q) + shoup_lazy(y1[k], h1.x, h1.y, q);
+      } else {
+        const u64 q2 = 2 * q;
+#pragma unroll
+        for (int k = 0; k < P::E; k++) a[k] = 0;
+        for (int kk = 0; kk < fz.K; kk++) {
+          const ulonglong2 h = __ldg(ph + (size_t)kk * fz.L1);
+          const u64* yk = y + (size_t)kk * N;
+#pragma unroll
+          for (int k = 0; k < P::E; k++) {
+            u64 t = a[k] + shoup_lazy(yk[(size_t)(x0 | M0::kbits(k)) * stride], h.x, h.y, q);
+            a[k] = t >= q2 ? t - q2 : t;
+          }
+        }
+      }
     } else {
       // rescale: the last limb's coefficients r (mod q_l), as (r + floor(q_l/2) mod q_l) - floor(q_l/2) mod q_i
       const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
@@ -350,8 +467,9 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
 }
 
 // inverse, last n1 stages (largest distances) on columns, then times N^{-1}; output in [0, q)
-template <int LOGM>
-__global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C) {
+template <int LOGM, int MODE>
+__global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
+                               Fuse fz) {
   using P = Plan<LOGM>;
   extern __shared__ u64 smc[];
   const size_t N = (size_t)1 << n;
@@ -376,8 +494,13 @@ __global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
   rounds_inv_rest<LOGM, P::R - 2>(a, u, smc, addr, sync, tw, 0, 0, q);
   using M0 = RMap<LOGM, 0>;
   const int x0 = M0::upart(u);
+  u64 sc = PT.ninv, scs = PT.ninv_sh;
+  if constexpr (MODE == 3) {
+    sc = fz.iscale[2 * (prime - fz.scale_base)];
+    scs = fz.iscale[2 * (prime - fz.scale_base) + 1];
+  }
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], PT.ninv, PT.ninv_sh, q);
+  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], sc, scs, q);
 }
 
 struct Geom {
@@ -394,38 +517,52 @@ Geom geom(int log_n) {
 
 template <int L, int MODE>
 void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n1, const u64* tw,
-                 const RescaleFuse& fz) {
+                 const Fuse& fz) {
   constexpr int RUNS = kRowThreads / Plan<L>::T;
   const int runs = 1 << n1;
   const dim3 grid((runs + RUNS - 1) / RUNS, rows);
   // a fused rescale also reads the limbs being rescaled and multiplies by q_l^{-1}
-  const double bytes = (MODE ? 24.0 : 16.0) * rows * (double)C.N;
-  const double prods = (double)rows * C.N * ((C.log_n - n1) / 2.0 + (MODE ? 1.0 : 0.0));
-  void* t = prof_begin(inv ? "k_ntt_inv_rows" : MODE ? "k_ntt_fwd_rows<rescale>" : "k_ntt_fwd_rows", C.stream, bytes,
-                       prods);
+  const bool fused = !inv && (MODE == 1 || MODE == 2);
+  const double bytes = (fused ? (MODE == 2 ? 32.0 : 24.0) : 16.0) * rows * (double)C.N;
+  const double prods = (double)rows * C.N * ((C.log_n - n1) / 2.0 + (fused ? 1.0 : 0.0));
+  const char* name = inv ? "k_ntt_inv_rows"
+                         : MODE == 1 ? "k_ntt_fwd_rows<rescale>" : MODE == 2 ? "k_ntt_fwd_rows<moddown>" : "k_ntt_fwd_rows";
+  static_assert(MODE >= 0 && MODE <= 4, "transform modes 0..4");
+  void* t = prof_begin(name, C.stream, bytes, prods);
   if (inv) k_ntt_inv_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
-  else k_ntt_fwd_rows<L, MODE><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1, fz);
+  else
+    k_ntt_fwd_rows<L, (MODE == 1 || MODE == 2) ? MODE : 0><<<grid, kRowThreads, 0, C.stream>>>(
+        base, lm, C.dev_ptab(), tw, C.log_n, n1, fz);
   prof_end(t, C.stream);
 }
 
 template <int L, int MODE>
 void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n2, int Ccols, const u64* tw,
-                 const RescaleFuse& fz) {
+                 const Fuse& fz) {
   const int threads = Ccols * Plan<L>::T;
   const size_t smem = (size_t)(1 << L) * Ccols * 8;
   const dim3 grid((1 << n2) / Ccols, rows);
   // butterflies, plus N^{-1} (inverse) or the reduction of the expanded limb (fused rescale)
-  const double prods = (double)rows * C.N * ((C.log_n - n2) / 2.0 + (inv || MODE ? 1.0 : 0.0));
-  void* t = prof_begin(inv ? "k_ntt_inv_cols" : MODE ? "k_ntt_fwd_cols<rescale>" : "k_ntt_fwd_cols", C.stream,
-                       16.0 * rows * (double)C.N, prods);
-  if (inv) k_ntt_inv_cols<L><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols);
-  else k_ntt_fwd_cols<L, MODE><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, Ccols, fz);
+  const double prods = (double)rows * C.N *
+                       ((C.log_n - n2) / 2.0 + (inv || MODE == 1 ? 1.0 : MODE == 2 ? 2.0 : MODE == 4 ? 2.0 : 0.0));
+  const char* name = inv ? "k_ntt_inv_cols"
+                         : MODE == 1   ? "k_ntt_fwd_cols<rescale>"
+                         : MODE == 2   ? "k_ntt_fwd_cols<moddown>"
+                         : MODE == 4   ? "k_ntt_fwd_cols<modup>"
+                                       : "k_ntt_fwd_cols";
+  void* t = prof_begin(name, C.stream, 16.0 * rows * (double)C.N, prods);
+  if (inv)
+    k_ntt_inv_cols<L, MODE == 3 ? 3 : 0><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n,
+                                                                           Ccols, fz);
+  else
+    k_ntt_fwd_cols<L, MODE == 3 ? 0 : MODE><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n,
+                                                                              Ccols, fz);
   prof_end(t, C.stream);
 }
 
 template <int MODE>
 void rows_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw,
-                   const RescaleFuse& fz = RescaleFuse{}) {
+                   const Fuse& fz = Fuse{}) {
   switch (g.n2) {
     case 2: launch_rows<2, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
     case 3: launch_rows<3, MODE>(inv, base, lm, rows, C, g.n1, tw, fz); break;
@@ -440,7 +577,7 @@ void rows_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& 
 
 template <int MODE>
 void cols_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, const Geom& g, const u64* tw,
-                   const RescaleFuse& fz = RescaleFuse{}) {
+                   const Fuse& fz = Fuse{}) {
   switch (g.n1) {
     case 2: launch_cols<2, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
     case 3: launch_cols<3, MODE>(inv, base, lm, rows, C, g.n2, g.C, tw, fz); break;
@@ -484,6 +621,95 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   HE_CUDA(cudaGetLastError());
 }
 
+void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp) {
+  const int rows = n_polys * lp;
+  if (rows == 0) return;
+  const Geom g = geom(C.log_n);
+  const LimbMap lm = limbs_q(lp, C.N);
+  Fuse fz;
+  fz.iscale = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2 + (size_t)(C.L1 + 1) * C.L1 * (C.L1 + C.K) * 2 +
+              (size_t)lp * C.L1 * 2;
+  fz.scale_base = 0;
+  const int step = (65535 / lp) * lp;
+  for (int r0 = 0; r0 < rows; r0 += step) {
+    const int rr = rows - r0 < step ? rows - r0 : step;
+    u64* base = data + (size_t)(r0 / lp) * lm.poly_stride;
+    rows_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
+    cols_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
+  }
+  HE_CUDA(cudaGetLastError());
+}
+
+void ntt_forward_modup(const Ctx& C, u64* ext_digit, int n, const LimbMap& lm, const u64* yt, size_t ystride,
+                       const u64* hat, int hstride, int cnt) {
+  const int rows = n * lm.lpp;
+  if (rows == 0) return;
+  const Geom g = geom(C.log_n);
+  const int per = 65535 / lm.lpp;  // polynomials per launch (grid.y <= 65535)
+  for (int p0 = 0; p0 < n; p0 += per) {
+    const int pn = n - p0 < per ? n - p0 : per;
+    Fuse fz;
+    fz.yt = yt + (size_t)p0 * ystride;
+    fz.ystride = ystride;
+    fz.phat = hat;
+    fz.hstride = hstride;
+    fz.K = cnt;
+    u64* base = ext_digit + (size_t)p0 * lm.poly_stride;
+    cols_dispatch<4>(false, base, lm, pn * lm.lpp, C, g, C.d_psi.p, fz);
+    rows_dispatch<4>(false, base, lm, pn * lm.lpp, C, g, C.d_psi.p, fz);
+  }
+  HE_CUDA(cudaGetLastError());
+}
+
+void ntt_inverse_pscaled(const Ctx& C, u64* data, int n_polys) {
+  const int lpp = C.K;
+  const int rows = n_polys * lpp;
+  if (rows == 0) return;
+  const Geom g = geom(C.log_n);
+  LimbMap lm;
+  lm.lpp = C.K; lm.split = 0; lm.base0 = 0; lm.base1 = C.L1; lm.poly_stride = (size_t)C.K * C.N;
+  Fuse fz;
+  fz.iscale = C.d_down.p + 2 * C.K + (size_t)2 * C.K * C.L1 + (size_t)2 * C.L1;
+  fz.scale_base = C.L1;
+  const int step = (65535 / lpp) * lpp;
+  for (int r0 = 0; r0 < rows; r0 += step) {
+    const int rr = rows - r0 < step ? rows - r0 : step;
+    u64* base = data + (size_t)(r0 / lpp) * lm.poly_stride;
+    rows_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
+    cols_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
+  }
+  HE_CUDA(cudaGetLastError());
+}
+
+void ntt_forward_moddown(const Ctx& C, u64* z, const u64* yt, int n, int lp, const u64* u, int nb, const u64* base,
+                         size_t base_stride, u64* out, size_t out_stride, u64 gk, int kmode) {
+  if (n == 0) return;
+  const Geom g = geom(C.log_n);
+  const LimbMap lm = limbs_q(lp, C.N);
+  const int per = 65535 / (2 * lp) * 2;  // polynomials per launch: whole ciphertexts, grid.y <= 65535
+  for (int p0 = 0; p0 < 2 * n; p0 += per) {
+    const int pn = 2 * n - p0 < per ? 2 * n - p0 : per;
+    Fuse fz;
+    fz.yt = yt + (size_t)p0 * C.K * C.N;
+    fz.phat = C.d_down.p + 2 * C.K;
+    fz.K = C.K;
+    fz.L1 = C.L1;
+    fz.u = u + (size_t)p0 * nb * C.N;
+    fz.nb = nb;
+    fz.base = base + (size_t)(p0 / 2) * base_stride;
+    fz.base_stride = base_stride;
+    fz.out = out + (size_t)(p0 / 2) * out_stride;
+    fz.out_stride = out_stride;
+    fz.gk = gk;
+    fz.kmode = kmode;
+    fz.pinv = C.d_down.p + 2 * C.K + (size_t)2 * C.K * C.L1;
+    u64* zb = z + (size_t)p0 * lp * C.N;
+    cols_dispatch<2>(false, zb, lm, pn * lp, C, g, C.d_psi.p, fz);
+    rows_dispatch<2>(false, zb, lm, pn * lp, C, g, C.d_psi.p, fz);
+  }
+  HE_CUDA(cudaGetLastError());
+}
+
 void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
   if (rows == 0) return;
   const Geom g = geom(C.log_n);
@@ -492,7 +718,7 @@ void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
   const int per = 65535 / (lp - 1);  // polynomials per launch (grid.y <= 65535)
   for (int p0 = 0; p0 < rows; p0 += per) {
     const int pn = rows - p0 < per ? rows - p0 : per;
-    RescaleFuse fz{x + (size_t)p0 * lp * C.N, tab, lp};
+    Fuse fz{x + (size_t)p0 * lp * C.N, tab, lp};
     u64* base = out + (size_t)p0 * (lp - 1) * C.N;
     cols_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
     rows_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
