@@ -146,6 +146,28 @@ HE_HD u64 shoup(u64 a, u64 w, u64 wp, u64 q) {
   return r >= q ? r - q : r;
 }
 
+// a w mod q in [0, 4q) for any a < 2^64, w < q, wp = floor(w 2^64 / q), 4q < 2^64.
+// Shoup's product with a cheaper quotient estimate: of the four 32 x 32-bit word
+// products of a wp only a1 wp1 and the high halves of a1 wp0 and a0 wp1 are kept
+// (dropped: their low halves and a0 wp0, together below 3 2^64). The estimate is
+// therefore at most 2 below floor(a wp / 2^64), which is itself at most 1 below
+// floor(a w / q) and never above it, so the remainder a w - qhat q is in [0, 4q)
+// and exact as a 64-bit word.
+HE_HD u64 shoup_approx(u64 a, u64 w, u64 wp, u64 q) {
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), p0 = (u32)wp, p1 = (u32)(wp >> 32);
+#if defined(__CUDA_ARCH__)
+  const u64 qh = (u64)a1 * p1 + ((u64)__umulhi(a1, p0) + __umulhi(a0, p1));
+#else
+  const u64 qh = (u64)a1 * p1 + ((((u64)a1 * p0) >> 32) + (((u64)a0 * p1) >> 32));
+#endif
+  return a * w - qh * q;
+}
+
+// Primes below this bound take the transforms' growing-range path: values are
+// not reduced between butterfly stages (each forward stage adds at most 4q, each
+// inverse stage at most doubles), which stays below 2^64 through 16 stages.
+constexpr u64 kNarrowPrime = 1ull << 54;
+
 HE_HD u64 addmod(u64 a, u64 b, u64 q) {
   const u64 s = a + b;
   return s >= q ? s - q : s;

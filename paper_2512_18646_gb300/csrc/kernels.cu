@@ -308,24 +308,16 @@ __global__ void k_add_const_kernel(u64* ct, int n, int limbs, const u64* cdev, i
 // that limb are staged in shared memory (every thread reads the same weight,
 // a broadcast). Each thread computes TN adjacent coefficients of OB output
 // channels for the output columns jp = blockIdx.z, blockIdx.z + gridDim.z, ...
-template <int OB, int TN>
-__global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
-                                  int c_out, int w_out, int limbs, const PrimeTab* pt, int log_n) {
-  extern __shared__ ulonglong2 sw[];  // [c_out][c_in k k]
-  const size_t N = (size_t)1 << log_n;
-  const size_t LN = (size_t)limbs * N;
-  const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+// NAR (primes below kNarrowPrime): the products take the cheaper quotient
+// estimate and lie in [0, 4q); otherwise Shoup's lazy products in [0, 2q).
+template <int OB, int TN, bool NAR>
+__device__ __forceinline__ void conv_mac_body(const ulonglong2* sw, const u64* rot, u64* out, int c_in, int w_in,
+                                              int k, int stride, int c_out, int w_out, size_t LN, size_t off, u64 q,
+                                              u64 one_sh) {
   const int T = c_in * k * k;
-  for (int id = threadIdx.x; id < c_out * T; id += blockDim.x)
-    sw[id] = *reinterpret_cast<const ulonglong2*>(w + ((size_t)id * limbs + i) * 2);
-  __syncthreads();
-  const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
-  if (n0 >= N) return;
-  const u64 q = pt[i].mod.q, one_sh = pt[i].one_sh;
-  // lazy products are below 2q: a word holds `room` of them on top of a reduced sum
-  const u64 fit = (~0ull) / (2 * q) - 1;
+  // lazy products are below 2q (4q): a word holds `room` of them on top of a reduced sum
+  const u64 fit = (~0ull) / ((NAR ? 4 : 2) * q) - 1;
   const int room = fit > (1u << 20) ? (1 << 20) : (int)fit;
-  const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
   for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
     for (int o0 = 0; o0 < c_out; o0 += OB) {
       u64 acc[OB][TN];
@@ -361,7 +353,8 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
               if (o0 + t < c_out) {
                 const ulonglong2 ww = wr[(size_t)t * T];
 #pragma unroll
-                for (int v = 0; v < TN; v++) acc[t][v] += shoup_lazy(x[v], ww.x, ww.y, q);
+                for (int v = 0; v < TN; v++)
+                  acc[t][v] += NAR ? shoup_approx(x[v], ww.x, ww.y, q) : shoup_lazy(x[v], ww.x, ww.y, q);
               }
             }
           }
@@ -376,6 +369,27 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
       }
     }
   }
+}
+
+template <int OB, int TN>
+__global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                                  int c_out, int w_out, int limbs, const PrimeTab* pt, int log_n) {
+  extern __shared__ ulonglong2 sw[];  // [c_out][c_in k k]
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+  const int T = c_in * k * k;
+  for (int id = threadIdx.x; id < c_out * T; id += blockDim.x)
+    sw[id] = *reinterpret_cast<const ulonglong2*>(w + ((size_t)id * limbs + i) * 2);
+  __syncthreads();
+  const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
+  if (n0 >= N) return;
+  const u64 q = pt[i].mod.q, one_sh = pt[i].one_sh;
+  const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
+  if (q < kNarrowPrime)
+    conv_mac_body<OB, TN, true>(sw, rot, out, c_in, w_in, k, stride, c_out, w_out, LN, off, q, one_sh);
+  else
+    conv_mac_body<OB, TN, false>(sw, rot, out, c_in, w_in, k, stride, c_out, w_out, LN, off, q, one_sh);
 }
 
 // d[idx] (3 components) = sum_k tensor(A_k, R[k][idx]); R [n][p][2][limbs][N]

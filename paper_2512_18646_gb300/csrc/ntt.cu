@@ -134,11 +134,14 @@ __device__ __forceinline__ ulonglong2 tw_load(const u64* tw, u64 idx) {
 // One forward round: stages S0 .. S0+NS-1 of an M-point sub-transform.
 // Twiddle of the butterfly whose lower element is e at local stage s:
 //   table[(1 << (soff + s)) + (run << s) + (e >> (LOGM - s))].
-template <int LOGM, int RND>
+// NAR (primes below kNarrowPrime): no reduction of the upper input and the
+// cheaper quotient estimate, so each stage raises the bound on the values by
+// at most 4q; otherwise Harvey's butterfly keeps them in [0, 4q).
+template <int LOGM, int RND, bool NAR>
 __device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
                                           u64 q) {
   using M = RMap<LOGM, RND>;
-  const u64 q2 = 2 * q;
+  const u64 q2 = 2 * q, q4 = 4 * q;
 #pragma unroll
   for (int st = 0; st < M::NS; st++) {
     const int s = M::S0 + st;
@@ -153,17 +156,25 @@ __device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM>::E], int xu, const
       for (int lo = 0; lo < (1 << ib); lo++) {
         const int k = kb | lo, k2 = k | (1 << ib);
         u64 X = a[k];
-        if (X >= q2) X -= q2;
-        const u64 T = shoup_lazy(a[k2], w.x, w.y, q);
-        a[k] = X + T;
-        a[k2] = X - T + q2;
+        if constexpr (NAR) {
+          const u64 T = shoup_approx(a[k2], w.x, w.y, q);
+          a[k] = X + T;
+          a[k2] = X - T + q4;
+        } else {
+          if (X >= q2) X -= q2;
+          const u64 T = shoup_lazy(a[k2], w.x, w.y, q);
+          a[k] = X + T;
+          a[k2] = X - T + q2;
+        }
       }
     }
   }
 }
 
-// One inverse round (Gentleman-Sande), stages in the opposite order.
-template <int LOGM, int RND>
+// One inverse round (Gentleman-Sande), stages in the opposite order. NAR: the
+// sums are not reduced; the inputs of the stage executed t-th (t = LOGM - 1 - s)
+// are below 2^(t+1) q, which the difference adds before its product.
+template <int LOGM, int RND, bool NAR>
 __device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
                                           u64 q) {
   using M = RMap<LOGM, RND>;
@@ -173,6 +184,7 @@ __device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const
     const int s = M::S0 + st;
     const int ib = M::NS - 1 - st;
     const u64 base = ((u64)1 << (soff + s)) + (run << s);
+    const u64 bt = q << (LOGM - s);
 #pragma unroll
     for (int hi = 0; hi < (M::E >> (ib + 1)); hi++) {
       const int kb = hi << (ib + 1);
@@ -182,10 +194,15 @@ __device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const
       for (int lo = 0; lo < (1 << ib); lo++) {
         const int k = kb | lo, k2 = k | (1 << ib);
         const u64 X = a[k], Y = a[k2];
-        u64 S = X + Y;
-        if (S >= q2) S -= q2;
-        a[k] = S;
-        a[k2] = shoup_lazy(X - Y + q2, w.x, w.y, q);
+        if constexpr (NAR) {
+          a[k] = X + Y;
+          a[k2] = shoup_approx(X - Y + bt, w.x, w.y, q);
+        } else {
+          u64 S = X + Y;
+          if (S >= q2) S -= q2;
+          a[k] = S;
+          a[k2] = shoup_lazy(X - Y + q2, w.x, w.y, q);
+        }
       }
     }
   }
@@ -193,7 +210,7 @@ __device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const
 
 // Rounds RND .. R-1 (forward) with exchanges through shared memory; `addr`
 // maps an element index to its shared-memory word.
-template <int LOGM, int RND, class Sync, class Addr>
+template <int LOGM, int RND, bool NAR, class Sync, class Addr>
 __device__ __forceinline__ void rounds_fwd_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
                                                 const u64* tw, int soff, u64 run, u64 q) {
   if constexpr (RND < Plan<LOGM>::R) {
@@ -207,12 +224,12 @@ __device__ __forceinline__ void rounds_fwd_rest(u64 (&a)[Plan<LOGM>::E], int u, 
 #pragma unroll
     for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
     sync();
-    round_fwd<LOGM, RND>(a, xc, tw, soff, run, q);
-    rounds_fwd_rest<LOGM, RND + 1>(a, u, sm, addr, sync, tw, soff, run, q);
+    round_fwd<LOGM, RND, NAR>(a, xc, tw, soff, run, q);
+    rounds_fwd_rest<LOGM, RND + 1, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
   }
 }
 
-template <int LOGM, int RND, class Sync, class Addr>
+template <int LOGM, int RND, bool NAR, class Sync, class Addr>
 __device__ __forceinline__ void rounds_inv_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
                                                 const u64* tw, int soff, u64 run, u64 q) {
   if constexpr (RND >= 0) {
@@ -226,8 +243,8 @@ __device__ __forceinline__ void rounds_inv_rest(u64 (&a)[Plan<LOGM>::E], int u, 
 #pragma unroll
     for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
     sync();
-    round_inv<LOGM, RND>(a, xc, tw, soff, run, q);
-    rounds_inv_rest<LOGM, RND - 1>(a, u, sm, addr, sync, tw, soff, run, q);
+    round_inv<LOGM, RND, NAR>(a, xc, tw, soff, run, q);
+    rounds_inv_rest<LOGM, RND - 1, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
   }
 }
 
@@ -249,42 +266,32 @@ constexpr int kRowThreads = 256;
 // ---------------------------------------------------------------------------
 // rows: last n2 forward stages (sub-size M = 2^LOGM = 2^{n2}), warp-contained
 // ---------------------------------------------------------------------------
-template <int LOGM, int MODE>
-__global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                              const u64* tw_all, int n, int n1, Fuse fz) {
+// Inputs below 4q (wide primes) or below 40q (narrow primes: the column
+// kernel's growing range); outputs in [0, q).
+template <int LOGM, int MODE, bool NAR>
+__device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n, int n1, u64 run,
+                                              u64 q, u64 one_sh, const LimbMap& lm, const Fuse& fz) {
   using P = Plan<LOGM>;
   constexpr int M = 1 << LOGM;
-  constexpr int RUNS = kRowThreads / P::T;
-  __shared__ u64 sm[kRowThreads * P::E];
   const size_t N = (size_t)1 << n;
-  int prime;
-  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q;
-  const u64* tw = tw_all + (size_t)prime * 2 * N;
-  const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
-  const u64 run = (u64)blockIdx.x * RUNS + r_cta;
-  if (run >= ((u64)1 << n1)) return;  // whole runs only, so a warp's active lanes hold whole runs
-  u64* xr = x + run * M;
-  // shared memory of this thread's warp, runs of the warp side by side
-  const int warp = threadIdx.x >> 5;
-  const int rw = (threadIdx.x & 31) / P::T;  // run index inside the warp
-  u64* smw = sm + warp * 32 * P::E;
   auto addr = [rw](int e) { return swz(rw * M + e); };
   auto sync = [] { __syncwarp(__activemask()); };
+  // the transform's result reduced to [0, q)
+  auto fin = [q, one_sh](u64 v) { return NAR ? shoup(v, 1, one_sh, q) : reduce4q(v, q); };
   u64 a[P::E];
   {
     using M0 = RMap<LOGM, 0>;
     const int x0 = M0::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xr[x0 | M0::kbits(k)];
-    round_fwd<LOGM, 0>(a, x0, tw, n1, run, q);
+    round_fwd<LOGM, 0, NAR>(a, x0, tw, n1, run, q);
   }
-  rounds_fwd_rest<LOGM, 1>(a, u, smw, addr, sync, tw, n1, run, q);
+  rounds_fwd_rest<LOGM, 1, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
   using ML = RMap<LOGM, P::R - 1>;
   const int xl = ML::upart(u);
   if constexpr (MODE == 0) {
 #pragma unroll
-    for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = reduce4q(a[k], q);
+    for (int k = 0; k < P::E; k++) xr[xl | ML::kbits(k)] = fin(a[k]);
   } else if constexpr (MODE == 1) {
     // rescale: out_i = (x_i - R_i) q_l^{-1} mod q_i, R_i this transform of the expanded last limb
     const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap
 #pragma unroll
     for (int k = 0; k < P::E; k++) {
       const int e = xl | ML::kbits(k);
-      xr[e] = shoup(submod(xi[e], reduce4q(a[k], q), q), qi, qs, q);
+      xr[e] = shoup(submod(xi[e], fin(a[k]), q), qi, qs, q);
     }
   } else {
     // ModDown combine: (u_Q[pi(j)] - z) P^{-1} plus the part the key switch does not touch
@@ -319,16 +326,15 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_fwd_rows(u64* data, LimbMap
         const u32 e2 = ((2 * bj + 1) * gk) & mask;
         src = brv_bits((e2 - 1) >> 1, n);
       }
-      const u64 v = shoup(submod(ui[src], reduce4q(a[k], q), q), pv, ps, q);
+      const u64 v = shoup(submod(ui[src], fin(a[k]), q), pv, ps, q);
       oi[j] = add ? addmod(v, bi[fz.kmode == 0 ? j : src], q) : v;
     }
   }
 }
 
-// inverse, first n2 stages (smallest distances) inside runs; output in [0, 2q)
-template <int LOGM>
-__global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                              const u64* tw_all, int n, int n1) {
+template <int LOGM, int MODE>
+__global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
+                                                              const u64* tw_all, int n, int n1, Fuse fz) {
   using P = Plan<LOGM>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
@@ -336,15 +342,29 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap
   const size_t N = (size_t)1 << n;
   int prime;
   u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q;
+  const u64 q = pt[prime].mod.q, one_sh = pt[prime].one_sh;
   const u64* tw = tw_all + (size_t)prime * 2 * N;
   const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
   const u64 run = (u64)blockIdx.x * RUNS + r_cta;
-  if (run >= ((u64)1 << n1)) return;
+  if (run >= ((u64)1 << n1)) return;  // whole runs only, so a warp's active lanes hold whole runs
   u64* xr = x + run * M;
+  // shared memory of this thread's warp, runs of the warp side by side
   const int warp = threadIdx.x >> 5;
-  const int rw = (threadIdx.x & 31) / P::T;
+  const int rw = (threadIdx.x & 31) / P::T;  // run index inside the warp
   u64* smw = sm + warp * 32 * P::E;
+  if (q < kNarrowPrime)
+    fwd_rows_body<LOGM, MODE, true>(xr, smw, rw, u, tw, n, n1, run, q, one_sh, lm, fz);
+  else
+    fwd_rows_body<LOGM, MODE, false>(xr, smw, rw, u, tw, n, n1, run, q, one_sh, lm, fz);
+}
+
+// inverse, first n2 stages (smallest distances) inside runs; inputs below 2q,
+// outputs in [0, 2q)
+template <int LOGM, bool NAR>
+__device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n1, u64 run, u64 q,
+                                              u64 one_sh) {
+  using P = Plan<LOGM>;
+  constexpr int M = 1 << LOGM;
   auto addr = [rw](int e) { return swz(rw * M + e); };
   auto sync = [] { __syncwarp(__activemask()); };
   u64 a[P::E];
@@ -353,33 +373,56 @@ __global__ void __launch_bounds__(kRowThreads) k_ntt_inv_rows(u64* data, LimbMap
     const int xl = ML::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xr[xl | ML::kbits(k)];
-    round_inv<LOGM, P::R - 1>(a, xl, tw, n1, run, q);
+    round_inv<LOGM, P::R - 1, NAR>(a, xl, tw, n1, run, q);
   }
-  rounds_inv_rest<LOGM, P::R - 2>(a, u, smw, addr, sync, tw, n1, run, q);
+  rounds_inv_rest<LOGM, P::R - 2, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
   using M0 = RMap<LOGM, 0>;
   const int x0 = M0::upart(u);
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = a[k];
+  for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = NAR ? shoup_lazy(a[k], 1, one_sh, q) : a[k];
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
+                                                              const u64* tw_all, int n, int n1) {
+  using P = Plan<LOGM>;
+  constexpr int M = 1 << LOGM;
+  constexpr int RUNS = kRowThreads / P::T;
+  __shared__ u64 sm[kRowThreads * P::E];
+  const size_t N = (size_t)1 << n;
+  int prime;
+  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
+  const u64 q = pt[prime].mod.q, one_sh = pt[prime].one_sh;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
+  const u64 run = (u64)blockIdx.x * RUNS + r_cta;
+  if (run >= ((u64)1 << n1)) return;
+  u64* xr = x + run * M;
+  const int warp = threadIdx.x >> 5;
+  const int rw = (threadIdx.x & 31) / P::T;
+  u64* smw = sm + warp * 32 * P::E;
+  if (q < kNarrowPrime)
+    inv_rows_body<LOGM, true>(xr, smw, rw, u, tw, n1, run, q, one_sh);
+  else
+    inv_rows_body<LOGM, false>(xr, smw, rw, u, tw, n1, run, q, one_sh);
 }
 
 // ---------------------------------------------------------------------------
 // cols: first n1 forward stages (sub-size 2^LOGM = 2^{n1}) on C adjacent columns
 // ---------------------------------------------------------------------------
-template <int LOGM, int MODE>
-__global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
-                               Fuse fz) {
+// Inputs below 4q (8q from a fused two-term base conversion of a narrow prime);
+// outputs below 4q (wide primes) or 40q (narrow primes).
+template <int LOGM, int MODE, bool NAR>
+__device__ __forceinline__ void fwd_cols_body(u64* xc, u64* smc, int u, int C, int lo, const u64* tw, int n, u64 q,
+                                              const LimbMap& lm, const PrimeTab* pt, const Fuse& fz) {
   using P = Plan<LOGM>;
-  extern __shared__ u64 smc[];
   const size_t N = (size_t)1 << n;
   const size_t stride = N >> LOGM;
-  int prime;
-  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q;
-  const u64* tw = tw_all + (size_t)prime * 2 * N;
-  const int u = threadIdx.x / C, lo = threadIdx.x - u * C;
-  u64* xc = x + (size_t)blockIdx.x * C + lo;
   auto addr = [C, lo](int e) { return e * C + lo; };
   auto sync = [] { __syncthreads(); };
+  // fused base conversions: two lazy products per element (below 4q, or 8q with the cheaper
+  // estimate of narrow primes), else a running sum kept below 2q
+  auto prod = [q](u64 y, ulonglong2 h) { return NAR ? shoup_approx(y, h.x, h.y, q) : shoup_lazy(y, h.x, h.y, q); };
   u64 a[P::E];
   {
     using M0 = RMap<LOGM, 0>;
@@ -387,13 +430,16 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
     if constexpr (MODE == 0) {
 #pragma unroll
       for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(x0 | M0::kbits(k)) * stride];
-    } else if constexpr (MODE == 4) {
-      // ModUp: fast base conversion of the digit, sum_t yt_t (D_j/q_t) mod the target prime
+    } else if constexpr (MODE == 4 || MODE == 2) {
+      // ModUp: fast base conversion of the digit, sum_t yt_t (D_j/q_t) mod the target prime;
+      // ModDown: of the P part, sum_k yt_k (P/p_k) mod q_i
       const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
-      const u64* y = fz.yt + (size_t)pr * fz.ystride + (size_t)blockIdx.x * C + lo;
-      const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(fz.phat) + lm.mem(i);
-      if (fz.K == 2) {  // two lazy products: below 4q, the transform's input range
-        const ulonglong2 h0 = __ldg(ph), h1 = __ldg(ph + fz.hstride);
+      const u64* y = MODE == 4 ? fz.yt + (size_t)pr * fz.ystride + (size_t)blockIdx.x * C + lo
+                               : fz.yt + (size_t)pr * fz.K * N + (size_t)blockIdx.x * C + lo;
+      const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(fz.phat) + (MODE == 4 ? lm.mem(i) : i);
+      const size_t hs = MODE == 4 ? (size_t)fz.hstride : (size_t)fz.L1;
+      if (fz.K == 2) {
+        const ulonglong2 h0 = __ldg(ph), h1 = __ldg(ph + hs);
         u64 y0[P::E], y1[P::E];
 #pragma unroll
         for (int k = 0; k < P::E; k++) {
@@ -401,47 +447,18 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
           y1[k] = y[N + (size_t)(x0 | M0::kbits(k)) * stride];
         }
 #pragma unroll
-        for (int k = 0; k < P::E; k++) a[k] = shoup_lazy(y0[k], h0.x, h0.y, q) + shoup_lazy(y1[k], h1.x, h1.y, q);
+        for (int k = 0; k < P::E; k++) a[k] = prod(y0[k], h0) + prod(y1[k], h1);
       } else {
         const u64 q2 = 2 * q;
 #pragma unroll
         for (int k = 0; k < P::E; k++) a[k] = 0;
         for (int t = 0; t < fz.K; t++) {
-          const ulonglong2 h = __ldg(ph + (size_t)t * fz.hstride);
+          const ulonglong2 h = __ldg(ph + (size_t)t * hs);
           const u64* yk = y + (size_t)t * N;
 #pragma unroll
           for (int k = 0; k < P::E; k++) {
             u64 v = a[k] + shoup_lazy(yk[(size_t)(x0 | M0::kbits(k)) * stride], h.x, h.y, q);
             a[k] = v >= q2 ? v - q2 : v;
-          }
-        }
-      }
-    } else if constexpr (MODE == 2) {
-      // ModDown: fast base conversion of the P part, sum_k yt_k (P/p_k) mod q_i (lazy, below 2q)
-      const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
-      const u64* y = fz.yt + (size_t)pr * fz.K * N + (size_t)blockIdx.x * C + lo;
-      const ulonglong2* ph = reinterpret_cast<const ulonglong2*>(fz.phat) + i;
-      if (fz.K == 2) {  // two lazy products: below 4q, the transform's input range
-        const ulonglong2 h0 = __ldg(ph), h1 = __ldg(ph + fz.L1);
-        u64 y0[P::E], y1[P::E];
-#pragma unroll
-        for (int k = 0; k < P::E; k++) {
-          y0[k] = y[(size_t)(x0 | M0::kbits(k)) * stride];
-          y1[k] = y[N + (size_t)(x0 | M0::kbits(k)) * stride];
-        }
-#pragma unroll
-        for (int k = 0; k < P::E; k++) a[k] = shoup_lazy(y0[k], h0.x, h0.y, q) + shoup_lazy(y1[k], h1.x, h1.y, q);
-      } else {
-        const u64 q2 = 2 * q;
-#pragma unroll
-        for (int k = 0; k < P::E; k++) a[k] = 0;
-        for (int kk = 0; kk < fz.K; kk++) {
-          const ulonglong2 h = __ldg(ph + (size_t)kk * fz.L1);
-          const u64* yk = y + (size_t)kk * N;
-#pragma unroll
-          for (int k = 0; k < P::E; k++) {
-            u64 t = a[k] + shoup_lazy(yk[(size_t)(x0 | M0::kbits(k)) * stride], h.x, h.y, q);
-            a[k] = t >= q2 ? t - q2 : t;
           }
         }
       }
@@ -457,30 +474,40 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
         a[k] = shoup_lazy(v, 1, one_sh, q) + q_m_half;  // [0, 3q), within the transform's [0, 4q) inputs
       }
     }
-    round_fwd<LOGM, 0>(a, x0, tw, 0, 0, q);
+    round_fwd<LOGM, 0, NAR>(a, x0, tw, 0, 0, q);
   }
-  rounds_fwd_rest<LOGM, 1>(a, u, smc, addr, sync, tw, 0, 0, q);
+  rounds_fwd_rest<LOGM, 1, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
   using ML = RMap<LOGM, P::R - 1>;
   const int xl = ML::upart(u);
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xc[(size_t)(xl | ML::kbits(k)) * stride] = a[k];  // [0, 4q)
+  for (int k = 0; k < P::E; k++) xc[(size_t)(xl | ML::kbits(k)) * stride] = a[k];
 }
 
-// inverse, last n1 stages (largest distances) on columns, then times N^{-1}; output in [0, q)
 template <int LOGM, int MODE>
-__global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
+__global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
                                Fuse fz) {
-  using P = Plan<LOGM>;
   extern __shared__ u64 smc[];
   const size_t N = (size_t)1 << n;
-  const size_t stride = N >> LOGM;
   int prime;
   u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const PrimeTab PT = pt[prime];
-  const u64 q = PT.mod.q;
+  const u64 q = pt[prime].mod.q;
   const u64* tw = tw_all + (size_t)prime * 2 * N;
   const int u = threadIdx.x / C, lo = threadIdx.x - u * C;
   u64* xc = x + (size_t)blockIdx.x * C + lo;
+  if (q < kNarrowPrime)
+    fwd_cols_body<LOGM, MODE, true>(xc, smc, u, C, lo, tw, n, q, lm, pt, fz);
+  else
+    fwd_cols_body<LOGM, MODE, false>(xc, smc, u, C, lo, tw, n, q, lm, pt, fz);
+}
+
+// inverse, last n1 stages (largest distances) on columns, then times N^{-1};
+// inputs below 2q, output in [0, q)
+template <int LOGM, int MODE, bool NAR>
+__device__ __forceinline__ void inv_cols_body(u64* xc, u64* smc, int u, int C, int lo, const u64* tw, int n, u64 q,
+                                              u64 sc, u64 scs) {
+  using P = Plan<LOGM>;
+  const size_t N = (size_t)1 << n;
+  const size_t stride = N >> LOGM;
   auto addr = [C, lo](int e) { return e * C + lo; };
   auto sync = [] { __syncthreads(); };
   u64 a[P::E];
@@ -489,18 +516,36 @@ __global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
     const int xl = ML::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(xl | ML::kbits(k)) * stride];
-    round_inv<LOGM, P::R - 1>(a, xl, tw, 0, 0, q);
+    round_inv<LOGM, P::R - 1, NAR>(a, xl, tw, 0, 0, q);
   }
-  rounds_inv_rest<LOGM, P::R - 2>(a, u, smc, addr, sync, tw, 0, 0, q);
+  rounds_inv_rest<LOGM, P::R - 2, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
   using M0 = RMap<LOGM, 0>;
   const int x0 = M0::upart(u);
+#pragma unroll
+  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], sc, scs, q);
+}
+
+template <int LOGM, int MODE>
+__global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const u64* tw_all, int n, int C,
+                               Fuse fz) {
+  extern __shared__ u64 smc[];
+  const size_t N = (size_t)1 << n;
+  int prime;
+  u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
+  const PrimeTab PT = pt[prime];
+  const u64 q = PT.mod.q;
+  const u64* tw = tw_all + (size_t)prime * 2 * N;
+  const int u = threadIdx.x / C, lo = threadIdx.x - u * C;
+  u64* xc = x + (size_t)blockIdx.x * C + lo;
   u64 sc = PT.ninv, scs = PT.ninv_sh;
   if constexpr (MODE == 3) {
     sc = fz.iscale[2 * (prime - fz.scale_base)];
     scs = fz.iscale[2 * (prime - fz.scale_base) + 1];
   }
-#pragma unroll
-  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], sc, scs, q);
+  if (q < kNarrowPrime)
+    inv_cols_body<LOGM, MODE, true>(xc, smc, u, C, lo, tw, n, q, sc, scs);
+  else
+    inv_cols_body<LOGM, MODE, false>(xc, smc, u, C, lo, tw, n, q, sc, scs);
 }
 
 struct Geom {
@@ -550,7 +595,12 @@ void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C,
                          : MODE == 2   ? "k_ntt_fwd_cols<moddown>"
                          : MODE == 4   ? "k_ntt_fwd_cols<modup>"
                                        : "k_ntt_fwd_cols";
-  void* t = prof_begin(name, C.stream, 16.0 * rows * (double)C.N, prods);
+  // bytes: every row read and written once; a fused base conversion (ModUp, ModDown) or rescale
+  // instead reads its fz.K (resp. one) source limbs per polynomial and writes the rows
+  const double src_limbs = MODE == 4 || MODE == 2 ? (double)fz.K : MODE == 1 ? 1.0 : 0.0;
+  const double bytes = (!inv && src_limbs > 0) ? 8.0 * (double)C.N * (rows + src_limbs * rows / lm.lpp)
+                                               : 16.0 * rows * (double)C.N;
+  void* t = prof_begin(name, C.stream, bytes, prods);
   if (inv)
     k_ntt_inv_cols<L, MODE == 3 ? 3 : 0><<<grid, threads, smem, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n,
                                                                            Ccols, fz);
