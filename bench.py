@@ -319,7 +319,9 @@ def run_matmul(args, rank, world, local_rank):
     Operands are encrypted (untimed) in waves that fit device memory; each wave
     is evaluated twice, once as 64-way-style batched launches (he_matmul_batched)
     and once as one he_matmul call per product, both timed with CUDA events on
-    the context's stream. value = products / total batched time."""
+    the context's stream, then a third time in the zero-rotation layout (A encrypted with
+    he_encrypt_matrix_a_volley, one he_matmul_volley per product).
+    value = products / total zero-rotation time; the revolver figures are reported beside it."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -340,7 +342,7 @@ def run_matmul(args, rank, world, local_rank):
     budget = 96 << 30
     waves, cur, used = [], [], 0
     for i, (m, n, p) in enumerate(shapes):
-        need = 2 * n * ct_bytes
+        need = (1 + max(2, api.volley_geometry(g.N // 2, m, p)[2])) * n * ct_bytes
         if cur and used + need > budget:
             waves.append(cur)
             cur, used = [], 0
@@ -363,9 +365,10 @@ def run_matmul(args, rank, world, local_rank):
     wb = g.encrypt_matrix_b(np.ones((4, 4)), 100)
     g.matmul(wa, wb, 4, 4)
     g.matmul_batched([wa], [wb], [4], [4])
-    t_batched = t_plain = 0.0
-    launches_b = 0
-    max_err = 0.0
+    g.matmul_volley(g.encrypt_matrix_a_volley(np.ones((4, 4)), 4, 0), wb)
+    t_batched = t_plain = t_volley = 0.0
+    launches_b = launches_v = 0
+    max_err = max_err_v = 0.0
     rng_seed = 402
     for wave in waves:
         As, Bs, mats = [], [], []
@@ -393,14 +396,38 @@ def run_matmul(args, rank, world, local_rank):
             return None
         _, dt = timed(plain)
         t_plain += dt
-        del As, Bs
+        del As
+        # the zero-rotation form: A in the volley layout (G groups of n ciphertexts), same B
+        Vs = []
+        for i in wave:
+            m, n, p = shapes[i]
+            A, _ = synthetic.matmul_operands(m, n, p, seed=rng_seed + i)
+            Vs.append(g.encrypt_matrix_a_volley(A, p, 10 ** 6 * i + 2 * 10 ** 5))
+        l0 = lib.he_kernel_launches()
+
+        def volley():
+            res = []
+            for t in range(len(wave)):
+                res.append(g.matmul_volley(Vs[t], Bs[t]))
+            return res
+        vouts, dt = timed(volley)
+        launches_v += lib.he_kernel_launches() - l0
+        t_volley += dt
+        for t in range(len(wave)):
+            max_err_v = max(max_err_v, float(np.abs(g.decrypt_matrix_volley(vouts[t], ms[t], ps[t]) - mats[t]).max()))
+        del vouts, Vs, Bs
     total = len(shapes)
     t_b = max_over_ranks(t_batched, world)
     t_p = max_over_ranks(t_plain, world)
+    t_v = max_over_ranks(t_volley, world)
     rot = sum(n * (p - 1) for _, n, p in shapes)
-    return {"value": total * world / t_b, "ms_per_step": 1e3 * t_b, "plain_value": total * world / t_p,
-            "plain_ms": 1e3 * t_p, "launches": launches_b, "max_abs_err": max_err, "keygen_s": keygen_s,
-            "waves": len(waves), "rotations": rot, "tensors": sum(n * p for _, n, p in shapes)}
+    groups = [api.volley_geometry(g.N // 2, m, p)[2] for m, _, p in shapes]
+    return {"value": total * world / t_v, "ms_per_step": 1e3 * t_v, "launches": launches_v, "max_abs_err": max_err_v,
+            "revolver_batched_value": total * world / t_b, "revolver_batched_ms": 1e3 * t_b,
+            "revolver_plain_value": total * world / t_p, "revolver_plain_ms": 1e3 * t_p,
+            "revolver_launches": launches_b, "revolver_max_abs_err": max_err, "keygen_s": keygen_s,
+            "waves": len(waves), "revolver_rotations": rot, "revolver_tensors": sum(n * p for _, n, p in shapes),
+            "volley_tensors": sum(G * n for G, (_, n, _) in zip(groups, shapes)), "volley_rotations": 0}
 
 
 # ---------------------------------------------------------------------------
@@ -616,9 +643,18 @@ def main():
                     "config": {"workload": "64 encrypted matmuls A(m x n) B(n x p), m,n,p i.i.d. uniform over "
                                            "{16,...,256} (seed 401), entries U[-1,1]; N=2^16, CNN primes, top level",
                                "parallelism": f"replicas x{world}"},
-                    "plain_value": res["plain_value"], "plain_ms": res["plain_ms"], "gpu_launches": res["launches"],
-                    "max_abs_err_vs_fp64": res["max_abs_err"], "keygen_s": res["keygen_s"], "waves": res["waves"],
-                    "rotations": res["rotations"], "tensor_products": res["tensors"]}
+                    "path": "zero-rotation (volley) layout: A's columns replicated at blocks t*M + o_g, "
+                            "M = 1 mod p; one he_matmul_volley call per product",
+                    "gpu_launches": res["launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+                    "rotations": res["volley_rotations"], "tensor_products": res["volley_tensors"],
+                    "revolver": {"batched_value": res["revolver_batched_value"],
+                                 "batched_ms": res["revolver_batched_ms"],
+                                 "plain_value": res["revolver_plain_value"], "plain_ms": res["revolver_plain_ms"],
+                                 "gpu_launches": res["revolver_launches"],
+                                 "max_abs_err_vs_fp64": res["revolver_max_abs_err"],
+                                 "rotations": res["revolver_rotations"],
+                                 "tensor_products": res["revolver_tensors"]},
+                    "keygen_s": res["keygen_s"], "waves": res["waves"]}
             print(json.dumps(line))
         return
 

@@ -133,6 +133,29 @@ int he_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_
 int he_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out);
 
 /*
+ * he_volley_geometry: the zero-rotation ("volley") layout of an m x n by n x p
+ * product on `slots` slots. B stays as he_encrypt_matrix_b encodes it (row k
+ * tiled with period p, so slot s holds B[k][s mod p]); A's column k is copied to
+ * blocks starting at t * M + o_g, with M >= m and M = 1 (mod p), so slot
+ * t * M + o_g + i pairs A[i][k] with B[k][(i + g * per + t) mod p]: position
+ * idx = g * per + t of the revolver of Alg. 3 (Sec. III-B), without rotating.
+ * Outputs: *M the block stride, *per the positions one ciphertext holds
+ * (t < per), *groups = ceil(p / per) ciphertexts per column of A; group g
+ * starts at block offset o_g = (g * per) mod p. Host-only arithmetic.
+ * Errors: HE_E_ARG if p does not divide `slots` or m + p - 1 > slots.
+ */
+int he_volley_geometry(int slots, int m, int p, int* M, int* per, int* groups);
+
+/*
+ * he_encrypt_matrix_a_volley: A [m][n] -> groups * n ciphertexts, group-major
+ * ([g][k]), in the layout of he_volley_geometry for this p (slots = N/2): group
+ * g, column k holds A[i][k] at slots t * M + o_g + i for t < min(per, p - g *
+ * per), i < m, zero elsewhere. Ids ct_id_base + g * n + k.
+ */
+int he_encrypt_matrix_a_volley(he_ctx* ctx, const double* A, int m, int n, int p, uint64_t ct_id_base,
+                               he_ctset** out);
+
+/*
  * he_encrypt_coeffs: encrypt already-encoded plaintexts. m is [n_ct][N]
  * signed integer coefficients; the result has `limbs` Q limbs and the given
  * scale. Ciphertext i uses randomness id ct_id_base + i. Used to start two
@@ -152,6 +175,17 @@ int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double
  * Errors: HE_E_ARG (shape), HE_E_SCALE, HE_E_LEVEL, HE_E_NOKEY.
  */
 int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C);
+
+/*
+ * he_matmul_volley: encrypted C = A B without rotations. A from
+ * he_encrypt_matrix_a_volley (groups * n ciphertexts), B from
+ * he_encrypt_matrix_b (n ciphertexts), same level and scale. Result: `groups`
+ * ciphertexts at one level lower, D_g = relin(rescale(sum_k Ahat_{g,k} (x)
+ * B~_k)); slot t * M + o_g + i of D_g holds C[i][(i + g * per + t) mod p]
+ * (decode with he_decrypt_matrix_volley). Needs only the relinearisation key.
+ * Errors: HE_E_ARG (counts), HE_E_SCALE, HE_E_LEVEL.
+ */
+int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset** C);
 
 /*
  * he_matmul_batched: `count` independent products A[i] B[i] (each as in
@@ -177,12 +211,23 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
               int c_out, int k, int stride, he_ctset** out);
 
 /*
- * he_poly_act: polynomial activation in place. Supported: degree 2 with
- * coeffs {0, 0, 1} (x -> x^2: tensor product, rescale). The result keeps
- * three components (d0, d1, d2) and is relinearised by the next operation
- * that needs two (rotation, convolution, matmul, the end of a dense layer,
- * decryption) or by he_relinearize; a dense layer consumes it directly.
- * Other polynomials return HE_E_UNIMPL.
+ * he_poly_act: polynomial activation in place, coeffs[0..degree] the
+ * coefficients c0, c1, ... of f(x) = sum_d c_d x^d.
+ *  - degree 2 with coeffs {0, 0, 1} (x -> x^2): tensor product, rescale; one
+ *    level.
+ *  - degree 3 (the ACT layers of Table I, e.g. ACT-1 = -0.00015120704 +
+ *    0.4610149 x + 2.0225089 x^2 - 1.4511951 x^3), and any other degree-2
+ *    polynomial (as c3 = 0): depth two, as x^2 (c3 x + c2) + (c1 x + c0):
+ *    u = relin(rescale(x (x) x)), t = rescale(x round(c3 q1)) + round(c2 D),
+ *    y = rescale(u (x) t), v = rescale(x round(c1 s_y q1 / D)) with its last
+ *    limb dropped, + round(c0 s_y); f(x) = y + v. q1, q2 are the primes the
+ *    two rescales drop, D the input scale, s_y = ((D D / q1) D) / q2 the
+ *    output scale (computed in that order in double precision). Needs the
+ *    relinearisation key and two levels (HE_E_LEVEL otherwise).
+ * The result keeps three components (d0, d1, d2) and is relinearised by the
+ * next operation that needs two (rotation, convolution, matmul, the end of a
+ * dense layer, decryption) or by he_relinearize; a dense layer consumes it
+ * directly. Other degrees return HE_E_UNIMPL.
  */
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree);
 
@@ -250,6 +295,9 @@ int he_decrypt_slots(he_ctx* ctx, const he_ctset* in, double* out, size_t out_le
 
 /* he_decrypt_matrix: C [m][p] from he_matmul's p diagonal ciphertexts. */
 int he_decrypt_matrix(he_ctx* ctx, const he_ctset* C, int m, int p, double* C_out);
+
+/* he_decrypt_matrix_volley: C [m][p] from he_matmul_volley's ciphertexts. */
+int he_decrypt_matrix_volley(he_ctx* ctx, const he_ctset* C, int m, int p, double* C_out);
 
 /* he_decrypt_image: [batch][n_ct][h_valid] column values, row i of image b
  * read at slot b * block_stride + gap * i of each ciphertext. */

@@ -68,6 +68,9 @@ def _lib():
             "oc_counters": (None, [V, _lp]),
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_matmul_volley": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_poly_act3": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                            _u64p, _dp]),
             "oc_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip,
                                          ctypes.c_int, _u64p]),
@@ -292,6 +295,14 @@ class Oracle:
         _check(self.lib.oc_matmul(self.h, _p(A, _u64p), _p(B, _u64p), n, p, lp, _p(out, _u64p)))
         return out
 
+    def matmul_volley(self, Ahat, B) -> np.ndarray:
+        """Ahat [G][n][2][lp][N] (volley encoding of A), B [n][2][lp][N] -> D [G][2][lp-1][N]."""
+        Ahat, B = _u64(Ahat), _u64(B)
+        G, n, _, lp, _ = Ahat.shape
+        out = np.zeros((G, 2, lp - 1, self.N), np.uint64)
+        _check(self.lib.oc_matmul_volley(self.h, _p(Ahat, _u64p), _p(B, _u64p), n, G, lp, _p(out, _u64p)))
+        return out
+
     def conv2d(self, X, gap: int, K, bias, stride: int, scale: float, sel=None, schedule: int = 0) -> np.ndarray:
         """X [c_in][w_in][2 or 3][lp][N]; K [c_out][c_in][k][k] -> [n_sel][2][lp-1][N].
 
@@ -318,6 +329,19 @@ class Oracle:
         out = np.zeros((n, 3, lp - 1, self.N), np.uint64)
         _check(self.lib.oc_square(self.h, _p(X, _u64p), n, lp, _p(out, _u64p)))
         return out
+
+    def poly_act3(self, X, coeffs, scale: float):
+        """Degree-3 activation c0 + c1 x + c2 x^2 + c3 x^3 of X [n][2 or 3][lp][N]
+        -> ([n][3][lp-2][N], output scale)."""
+        X = _u64(X)
+        n, polys, lp, _ = X.shape
+        c = np.ascontiguousarray(np.zeros(4) if coeffs is None else coeffs, dtype=np.float64)
+        assert c.shape == (4,)
+        out = np.zeros((n, 3, lp - 2, self.N), np.uint64)
+        so = ctypes.c_double()
+        _check(self.lib.oc_poly_act3(self.h, _p(X, _u64p), n, polys, lp, _p(c, _dp), scale, _p(out, _u64p),
+                                     ctypes.byref(so)))
+        return out, so.value
 
     def fc_plaintexts(self, lp: int, c_in: int, hv: int, w_in: int, gap: int, H: int, B: int, W, sel_o) -> np.ndarray:
         W = np.ascontiguousarray(W, dtype=np.float64)

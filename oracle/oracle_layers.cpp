@@ -77,6 +77,61 @@ static std::vector<Ct> matmul(Ctx& C, const std::vector<Ct>& A, const std::vecto
   return D;
 }
 
+// Zero-rotation ("volley") form of the same product: group g of A's volley
+// encoding holds column k at blocks t*M + o_g (M = 1 mod p), so the slotwise
+// product with B~_k (period p) already pairs A[i][k] with B[k][(i + idx) mod p]
+// for idx = g*per + t: D_g = sum_k Ahat_{g,k} (x) B~_k, rescaled, then
+// relinearised. Ahat is group-major ([G][n]); no rotation is performed.
+static std::vector<Ct> matmul_volley(Ctx& C, const std::vector<Ct>& Ahat, const std::vector<Ct>& B) {
+  const int n = (int)B.size(), G = (int)Ahat.size() / n;
+  std::vector<Ct> D(G);
+#pragma omp parallel for schedule(dynamic)
+  for (int g = 0; g < G; g++) {
+    Ct T = ct_tensor(C, Ahat[(size_t)g * n], B[0]);
+    for (int k = 1; k < n; k++) T = ct_add(C, T, ct_tensor(C, Ahat[(size_t)g * n + k], B[k]));
+    D[g] = ct_relin(C, ct_rescale(C, T));
+  }
+  return D;
+}
+
+// Degree-3 polynomial activation f(x) = c0 + c1 x + c2 x^2 + c3 x^3 (the ACT
+// layers of Table I), depth two, as x^2 (c3 x + c2) + (c1 x + c0). With q1, q2
+// the primes the two rescales drop and D the input scale:
+//   u = relin(rescale(x (x) x))                      level - 1, scale s_u = D D / q1
+//   t = rescale(x round(c3 q1)) + round(c2 D)        level - 1, scale D
+//   y = rescale(u (x) t)                             level - 2, scale s_y = s_u D / q2
+//   v = rescale(x round(c1 s_y q1 / D)) without its last limb, + round(c0 s_y)
+//                                                    level - 2, scale s_y
+//   f(x) = y + v, three components (relinearised by the next operation).
+// Constants enter component 0 only; a scalar times a ciphertext multiplies every
+// component.
+static Ct drop_last_limb(const Ct& x) {
+  Ct r = x;
+  for (auto& comp : r.c) comp.pop_back();
+  return r;
+}
+
+static Ct poly_act3(Ctx& C, const Ct& x_any, const double* c, double D, double& s_out) {
+  const Ct x = two_comp(C, x_any);
+  const int lp = x.limbs();
+  if (lp < 3) throw std::runtime_error("a degree-3 activation needs two levels");
+  const u64 q1 = C.q[lp - 1], q2 = C.q[lp - 2];
+  const Ct u = ct_relin(C, ct_rescale(C, ct_tensor(C, x, x)));
+  const double s_u = (D * D) / (double)q1;
+  const Ct t = ct_add_const(C, ct_rescale(C, ct_mul_scalar(C, x, std::llround(c[3] * (double)q1))),
+                            std::llround(c[2] * D));
+  Ct y = ct_rescale(C, ct_tensor(C, u, t));
+  const double s_y = (s_u * D) / (double)q2;
+  const Ct v = ct_add_const(
+      C, drop_last_limb(ct_rescale(C, ct_mul_scalar(C, x, std::llround(c[1] * s_y * (double)q1 / D)))),
+      std::llround(c[0] * s_y));
+  for (int comp = 0; comp < 2; comp++)
+    for (int i = 0; i < y.limbs(); i++)
+      for (size_t n = 0; n < C.N; n++) y.c[comp][i][n] = addmod(y.c[comp][i][n], v.c[comp][i][n], C.q[i]);
+  s_out = s_y;
+  return y;
+}
+
 static i64 quantise(double w, u64 q) { return std::llround(w * (double)q); }
 
 // Convolution outputs sel = [(o, j')] from inputs X[c][j].
@@ -229,6 +284,32 @@ const char* ol_last_error() { return g_lerr.c_str(); }
 int oc_matmul(void* h, const uint64_t* A, const uint64_t* B, int n, int p, int lp, uint64_t* D) {
   OL_TRY(Ctx* C = (Ctx*)h; std::vector<Ct> d = matmul(*C, cts_from(*C, A, n, lp), cts_from(*C, B, n, lp), p);
          cts_to(*C, d, D));
+}
+
+// Ahat [G][n][2][lp][N] (volley encoding of A), B [n][2][lp][N] -> D [G][2][lp-1][N]
+int oc_matmul_volley(void* h, const uint64_t* Ahat, const uint64_t* B, int n, int G, int lp, uint64_t* D) {
+  OL_TRY(Ctx* C = (Ctx*)h; std::vector<Ct> d = matmul_volley(*C, cts_from(*C, Ahat, n * G, lp), cts_from(*C, B, n, lp));
+         cts_to(*C, d, D));
+}
+
+// X [n][polys][lp][N] (polys 2 or 3), coeffs c0..c3 -> out [n][3][lp-2][N]; *scale_out
+int oc_poly_act3(void* h, const uint64_t* X, int n, int polys, int lp, const double* coeffs, double scale,
+                 uint64_t* out, double* scale_out) {
+  try {
+    Ctx* C = (Ctx*)h;
+    if (lp < 3) throw std::runtime_error("a degree-3 activation needs two levels");
+    std::vector<Ct> x = cts_from(*C, X, n, lp, polys);
+    std::vector<Ct> r(n);
+    std::vector<double> so(n, scale);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < n; t++) r[t] = poly_act3(*C, x[t], coeffs, scale, so[t]);
+    *scale_out = so[0];
+    cts_to(*C, r, out);
+    return 0;
+  } catch (const std::exception& e) {
+    g_lerr = e.what();
+    return -1;
+  }
 }
 
 // X [c_in][w_in][polys][lp][N] (polys 2, or 3 for unrelinearised products);

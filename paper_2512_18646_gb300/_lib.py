@@ -63,9 +63,12 @@ SIGNATURES = {
     "he_encrypt_image": (I, [V, P_D, I, I, I, I, U64, PV]),
     "he_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
     "he_encrypt_matrix_b": (I, [V, P_D, I, I, U64, PV]),
+    "he_volley_geometry": (I, [I, I, I, P_I, P_I, P_I]),
+    "he_encrypt_matrix_a_volley": (I, [V, P_D, I, I, I, U64, PV]),
     "he_encrypt_coeffs": (I, [V, P_I64, I, I, D, U64, PV]),
     "he_matmul": (I, [V, V, V, I, I, PV]),
     "he_matmul_batched": (I, [V, I, PV, PV, P_I, P_I, PV]),
+    "he_matmul_volley": (I, [V, V, V, PV]),
     "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
     "he_poly_act": (I, [V, V, P_D, I]),
     "he_fc_prepare": (I, [V, P_D, I, I, I, I, I, I, I, I, PV]),
@@ -81,6 +84,7 @@ SIGNATURES = {
     "he_add": (I, [V, V, V, PV]),
     "he_decrypt_slots": (I, [V, V, P_D, SZ]),
     "he_decrypt_matrix": (I, [V, V, I, I, P_D]),
+    "he_decrypt_matrix_volley": (I, [V, V, I, I, P_D]),
     "he_decrypt_image": (I, [V, V, I, I, I, I, P_D, SZ]),
     "he_ctset_export": (I, [V, P_U64, SZ]),
     "he_ctset_import": (I, [V, P_U64, I, I, D, PV]),

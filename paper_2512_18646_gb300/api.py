@@ -18,6 +18,13 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def volley_geometry(slots: int, m: int, p: int):
+    """(M, per, groups) of the zero-rotation matmul layout (he_volley_geometry)."""
+    M, per, G = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(load().he_volley_geometry(slots, m, p, ctypes.byref(M), ctypes.byref(per), ctypes.byref(G)))
+    return M.value, per.value, G.value
+
+
 class CtSet:
     """n ciphertexts at one level and scale, in device memory (NTT domain)."""
 
@@ -169,6 +176,11 @@ class Context:
         A = _f64(A)
         return self._set(load().he_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)
 
+    def encrypt_matrix_a_volley(self, A, p: int, ct_id_base: int = 0) -> CtSet:
+        A = _f64(A)
+        return self._set(load().he_encrypt_matrix_a_volley, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], p,
+                         ct_id_base)
+
     def encrypt_matrix_b(self, B, ct_id_base: int = 0) -> CtSet:
         B = _f64(B)
         return self._set(load().he_encrypt_matrix_b, self.h, _ptr(B, P_D), B.shape[0], B.shape[1], ct_id_base)
@@ -187,6 +199,9 @@ class Context:
     # ---- evaluation ----
     def matmul(self, A: CtSet, B: CtSet, m: int, p: int) -> CtSet:
         return self._set(load().he_matmul, self.h, A.h, B.h, m, p)
+
+    def matmul_volley(self, A: CtSet, B: CtSet) -> CtSet:
+        return self._set(load().he_matmul_volley, self.h, A.h, B.h)
 
     def matmul_batched(self, As, Bs, ms, ps):
         n = len(As)
@@ -272,6 +287,11 @@ class Context:
     def decrypt_matrix(self, C: CtSet, m: int, p: int) -> np.ndarray:
         out = np.zeros((m, p), np.float64)
         check(load().he_decrypt_matrix(self.h, C.h, m, p, _ptr(out, P_D)))
+        return out
+
+    def decrypt_matrix_volley(self, C: CtSet, m: int, p: int) -> np.ndarray:
+        out = np.zeros((m, p), np.float64)
+        check(load().he_decrypt_matrix_volley(self.h, C.h, m, p, _ptr(out, P_D)))
         return out
 
     def decrypt_image(self, x: CtSet, batch: int, block_stride: int, gap: int, h_valid: int) -> np.ndarray:

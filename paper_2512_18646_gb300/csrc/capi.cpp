@@ -163,6 +163,33 @@ int he_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_
   });
 }
 
+int he_volley_geometry(int slots, int m, int p, int* M, int* per, int* groups) {
+  return guard([&] {
+    REQUIRE(M && per && groups && slots >= 1, HE_E_ARG, "null argument");
+    volley_geometry(slots, m, p, *M, *per, *groups);
+  });
+}
+
+int he_encrypt_matrix_a_volley(he_ctx* ctx, const double* A, int m, int n, int p, uint64_t ct_id_base,
+                               he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(n >= 1, HE_E_ARG, "bad matrix shape");
+    int Mb, per, G;
+    volley_geometry(S, m, p, Mb, per, G);
+    std::vector<double> z((size_t)G * n * S, 0.0);
+    for (int g = 0; g < G; g++) {
+      const long o = ((long)g * per) % p;
+      for (int t = 0; t < per && g * per + t < p; t++)
+        for (int k = 0; k < n; k++)
+          for (int i = 0; i < m; i++) z[((size_t)g * n + k) * S + (size_t)t * Mb + o + i] = A[(size_t)i * n + k];
+    }
+    *out = wrap(encrypt_slots(C, z, G * n, ct_id_base));
+  });
+}
+
 int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double scale, uint64_t ct_id_base,
                       he_ctset** out) {
   return guard([&] {
@@ -178,6 +205,14 @@ int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, h
     REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
     REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
     *C_out = wrap(matmul(ctx->c, *A->s, *B->s, p));
+  });
+}
+
+int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset** C_out) {
+  return guard([&] {
+    REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
+    REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
+    *C_out = wrap(matmul_volley(ctx->c, *A->s, *B->s));
   });
 }
 
@@ -210,9 +245,13 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) {
   return guard([&] {
     REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");
-    REQUIRE(degree == 2 && coeffs[0] == 0.0 && coeffs[1] == 0.0 && coeffs[2] == 1.0, HE_E_UNIMPL,
-            "only x -> x^2 is supported");
-    inout->s = square(ctx->c, *inout->s);  // three components until an operation needs two
+    REQUIRE(degree == 2 || degree == 3, HE_E_UNIMPL, "degree 2 or 3 polynomials only");
+    if (degree == 2 && coeffs[0] == 0.0 && coeffs[1] == 0.0 && coeffs[2] == 1.0) {
+      inout->s = square(ctx->c, *inout->s);  // three components until an operation needs two
+      return;
+    }
+    const double c[4] = {coeffs[0], coeffs[1], coeffs[2], degree == 3 ? coeffs[3] : 0.0};
+    inout->s = poly_act3(ctx->c, *inout->s, c);
   });
 }
 
@@ -357,6 +396,25 @@ int he_decrypt_matrix(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_o
     decrypt_slots(ctx->c, *Cs->s, z.data());
     for (int idx = 0; idx < p; idx++)
       for (int i = 0; i < m; i++) C_out[(size_t)i * p + (i + idx) % p] = z[(size_t)idx * M + i];
+  });
+}
+
+int he_decrypt_matrix_volley(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_out) {
+  return guard([&] {
+    REQUIRE(ctx && Cs && C_out, HE_E_ARG, "null argument");
+    const long S = (long)ctx->c.N / 2;
+    int Mb, per, G;
+    volley_geometry(S, m, p, Mb, per, G);
+    REQUIRE(Cs->s->n == G, HE_E_ARG, "shape does not match");
+    std::vector<double> z((size_t)G * S);
+    decrypt_slots(ctx->c, *Cs->s, z.data());
+    for (int g = 0; g < G; g++) {
+      const long o = ((long)g * per) % p;
+      for (int t = 0; t < per && g * per + t < p; t++) {
+        const int idx = g * per + t;
+        for (int i = 0; i < m; i++) C_out[(size_t)i * p + (i + idx) % p] = z[(size_t)g * S + (size_t)t * Mb + o + i];
+      }
+    }
   });
 }
 

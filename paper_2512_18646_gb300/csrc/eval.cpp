@@ -267,6 +267,71 @@ static DevBuf const_table(Ctx& C, const double* v, int groups, int limbs, double
   return d;
 }
 
+// x times the integer v (every component), a new set at x's level and scale
+static std::unique_ptr<CtSet> times_integer(Ctx& C, const CtSet& x, int64_t v) {
+  std::vector<u64> t((size_t)2 * x.limbs);
+  for (int i = 0; i < x.limbs; i++) {
+    const u64 r = residue_of(v, C.q[i]);
+    t[2 * i] = r;
+    t[2 * i + 1] = (u64)(((unsigned __int128)r << 64) / C.q[i]);
+  }
+  DevBuf d(t.size(), C.stream);
+  // pageable source: the call returns once the data is staged, so t may go
+  HE_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  auto out = new_set(C, x.n, x.polys, x.limbs, x.scale);
+  k_mul_const(C, x.buf.p, out->buf.p, (size_t)x.n * x.polys, x.limbs, d.p);
+  return out;
+}
+
+// the same ciphertexts without their last limb (modulus drop; the scale is unchanged)
+static std::unique_ptr<CtSet> drop_last_limb(Ctx& C, const CtSet& x) {
+  auto out = new_set(C, x.n, x.polys, x.limbs - 1, x.scale);
+  k_copy_limbs(C, x.buf.p, (size_t)x.limbs * C.N, out->buf.p, (size_t)(x.limbs - 1) * C.N, (size_t)x.n * x.polys,
+               x.limbs - 1);
+  return out;
+}
+
+// Degree-3 activation (the ACT layers of Table I), depth two, evaluated as
+// x^2 (c3 x + c2) + (c1 x + c0); q1, q2 the primes the two rescales drop, D the
+// input scale:
+//   u = relin(rescale(x (x) x))                  scale s_u = D D / q1
+//   t = rescale(x round(c3 q1)) + round(c2 D)    scale D
+//   y = rescale(u (x) t)                         scale s_y = s_u D / q2, two levels down
+//   v = rescale(x round(c1 s_y q1 / D)) without its last limb, + round(c0 s_y)
+//   result y + v with three components (relinearised by the next operation).
+std::unique_ptr<CtSet> poly_act3(Ctx& C, const CtSet& x_any, const double* c) {
+  std::unique_ptr<CtSet> hx;
+  const CtSet& x = two_comp(C, x_any, hx);
+  const int lp = x.limbs;
+  if (lp < 3) throw Error(2, "a degree-3 activation needs two levels");
+  const double D = x.scale;
+  const u64 q1 = C.q[lp - 1];
+  auto u = mul(C, x, x);
+  relinearize(C, *u);
+  auto t = times_integer(C, x, std::llround(c[3] * (double)q1));
+  rescale_inplace(C, *t);
+  t->scale = D;
+  {
+    DevBuf cb = const_table(C, &c[2], 1, t->limbs, D);
+    k_add_const(C, t->buf.p, t->n, t->limbs, cb.p, t->n);
+  }
+  auto y = mul(C, *u, *t);
+  u.reset();
+  t.reset();
+  const double s_y = y->scale;
+  auto v1 = times_integer(C, x, std::llround(c[1] * s_y * (double)q1 / D));
+  rescale_inplace(C, *v1);
+  auto v = drop_last_limb(C, *v1);
+  v1.reset();
+  v->scale = s_y;
+  {
+    DevBuf cb = const_table(C, &c[0], 1, v->limbs, s_y);
+    k_add_const(C, v->buf.p, v->n, v->limbs, cb.p, v->n);
+  }
+  k_add_comps(C, y->buf.p, v->buf.p, y->n, y->polys, y->limbs);
+  return y;
+}
+
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride) {
   std::unique_ptr<CtSet> hold;
@@ -364,6 +429,41 @@ std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, in
   }
   R.reset();
   ext.reset();
+  rescale_inplace(C, *d);
+  relinearize(C, *d);
+  return d;
+}
+
+// Zero-rotation form of the product. B~_k is tiled with period p, so its slot s
+// holds B[k][s mod p]; with A's column k copied to blocks t M + o_g (M = 1 mod p,
+// o_g = (g per) mod p) the slotwise product pairs A[i][k] with B[k][(i + g per + t)
+// mod p], the revolver's position idx = g per + t, at slot t M + o_g + i. So
+// D_g = sum_k Ahat_{g,k} (x) B~_k needs no rotation: G n tensor products summed as
+// three components, one rescale and one relinearisation per group.
+void volley_geometry(long slots, int m, int p, int& M, int& per, int& G) {
+  if (m < 1 || p < 1 || slots % p) throw Error(1, "p must divide the slot count");
+  M = p > 1 ? m + (int)(((1 - (long)m) % p + p) % p) : m;
+  if ((long)(p - 1) * M + m <= slots) {
+    per = p;
+    G = 1;
+    return;
+  }
+  const long r = slots - m - (p - 1);
+  if (r < 0) throw Error(1, "matrix does not fit the slots");
+  per = (int)(r / M) + 1;
+  G = (p + per - 1) / per;
+}
+
+std::unique_ptr<CtSet> matmul_volley(Ctx& C, const CtSet& Ah_any, const CtSet& B_any) {
+  std::unique_ptr<CtSet> ha, hb;
+  const CtSet& Ah = two_comp(C, Ah_any, ha);
+  const CtSet& B = two_comp(C, B_any, hb);
+  if (B.n < 1 || Ah.n % B.n) throw Error(1, "A's volley encoding must hold G groups of n ciphertexts");
+  if (Ah.limbs != B.limbs) throw Error(4, "operands at different levels");
+  if (Ah.limbs < 2) throw Error(2, "no level left for the product");
+  const int n = B.n, G = Ah.n / B.n, lp = B.limbs;
+  auto d = new_set(C, G, 3, lp, Ah.scale * B.scale);
+  k_volley_acc(C, Ah.buf.p, B.buf.p, d->buf.p, n, G, lp);
   rescale_inplace(C, *d);
   relinearize(C, *d);
   return d;

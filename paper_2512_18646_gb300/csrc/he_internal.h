@@ -205,11 +205,17 @@ void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int r
 // add integer constants to polynomial 0 of each ciphertext (NTT domain);
 // c_dev [n / per_group][limbs]: ciphertext c gets row c / per_group
 void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int per_group);
+// out = in * w mod q_i for rows [rows][limbs][N]; wsh [limbs][2] (residue, Shoup companion)
+void k_mul_const(const Ctx& C, const u64* in, u64* out, size_t rows, int limbs, const u64* wsh);
+// y[c][comp] += v[c][comp], comp < 2 (y with ypolys components, v with two)
+void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limbs);
 // conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs);
 // matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx])
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
+// zero-rotation matmul accumulate: d[g] = sum_k tensor(Ahat[g][k], B[k]), g < G
+void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
 // slot-block packing: out[j] = sum_t masks[t] * xs[t][j] ([n_ct][2][limbs][N]); xs is a device array of T pointers
@@ -253,9 +259,16 @@ void rescale_inplace(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// zero-rotation matmul: Ahat [G][n] (group-major volley encoding of A), B [n] -> D [G]
+std::unique_ptr<CtSet> matmul_volley(Ctx& C, const CtSet& Ahat, const CtSet& B);
+// block stride M, positions per ciphertext and groups of the volley layout (throws on misfit)
+void volley_geometry(long slots, int m, int p, int& M, int& per, int& G);
 std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<const CtSet*>& As,
                                                    const std::vector<const CtSet*>& Bs, const std::vector<int>& ps);
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in);
+// degree-3 activation c0 + c1 x + c2 x^2 + c3 x^3 (coeffs c[0..3]); two levels, three components out
+std::unique_ptr<CtSet> poly_act3(Ctx& C, const CtSet& x, const double* c);
+
 std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,

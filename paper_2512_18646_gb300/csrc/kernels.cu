@@ -301,6 +301,32 @@ __global__ void k_add_const_kernel(u64* ct, int n, int limbs, const u64* cdev, i
   }
 }
 
+// out = in * w_i mod q_i for rows [rows][limbs][N] (every component of every
+// ciphertext); wsh [limbs][2]: the integer's residue mod q_i and its Shoup companion.
+__global__ void k_mul_const_kernel(const u64* in, u64* out, size_t rows, int limbs, const u64* wsh,
+                                   const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t total = rows * limbs * N;
+  HE_GRID_LOOP(idx, total) {
+    const int i = (int)((idx >> log_n) % (size_t)limbs);
+    out[idx] = shoup(in[idx], wsh[2 * i], wsh[2 * i + 1], pt[i].mod.q);
+  }
+}
+
+// y[c][comp] += v[c][comp] for comp < 2: y [n][ypolys][limbs][N], v [n][2][limbs][N]
+__global__ void k_add_comps_kernel(u64* y, const u64* v, int n, int ypolys, int limbs, const PrimeTab* pt,
+                                   int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)n * 2 * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t c = idx / (2 * LN), w = idx - c * 2 * LN;
+    const int i = (int)((w >> log_n) % (size_t)limbs);
+    u64* p = y + c * ypolys * LN + w;
+    *p = addmod(*p, v[idx], pt[i].mod.q);
+  }
+}
+
 // Convolution multiply-accumulate. rot [c_in][w_in][k][2][limbs][N] holds
 // Rot(X_{c,j}, gap a) at [c][j][a]; w [c_out][c_in][k][k][limbs][2] holds the
 // integer weights mod q_i and Shoup companions ([o][c][a][b]). A block works
@@ -419,6 +445,41 @@ __global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, i
       }
     }
     u64* D = d + (size_t)id * 3 * LN + w;
+    D[0] = reduce128(s0.hi, s0.lo, md);
+    D[LN] = reduce128(s1.hi, s1.lo, md);
+    D[2 * LN] = reduce128(s2.hi, s2.lo, md);
+  }
+}
+
+// Zero-rotation matmul accumulate: d[g] (3 components) = sum_k tensor(Ahat[g][k], B[k]);
+// Ahat [G][n][2][limbs][N], B [n][2][limbs][N]. Sums of 128-bit products, reduced
+// every 8 terms.
+__global__ void k_volley_acc_kernel(const u64* Ah, const u64* B, u64* d, int n, int G, int limbs, const PrimeTab* pt,
+                                    int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)G * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t w = idx % LN;
+    const int g = (int)(idx / LN);
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
+    for (int kk = 0; kk < n; kk++) {
+      const u64* a = Ah + ((size_t)g * n + kk) * 2 * LN + w;
+      const u64* b = B + (size_t)kk * 2 * LN + w;
+      const u64 a0 = a[0], a1 = a[LN], b0 = b[0], b1 = b[LN];
+      mac128(s0, a0, b0);
+      mac128(s1, a0, b1);
+      mac128(s1, a1, b0);
+      mac128(s2, a1, b1);
+      if ((kk & 7) == 7) {
+        s0 = Acc128{0, reduce128(s0.hi, s0.lo, md)};
+        s1 = Acc128{0, reduce128(s1.hi, s1.lo, md)};
+        s2 = Acc128{0, reduce128(s2.hi, s2.lo, md)};
+      }
+    }
+    u64* D = d + (size_t)g * 3 * LN + w;
     D[0] = reduce128(s0.hi, s0.lo, md);
     D[LN] = reduce128(s1.hi, s1.lo, md);
     D[2 * LN] = reduce128(s2.hi, s2.lo, md);
@@ -651,6 +712,14 @@ void k_rescale_combine(const Ctx& C, const u64* x, const u64* r, u64* out, int r
   HE_LAUNCH(k_rescale_combine_kernel, (size_t)rows * (limbs - 1) * C.N, 8.0 * (double)C.N * 3.0 * rows * (limbs - 1), x, r, out, rows, limbs, tab, C.dev_ptab(),
             C.log_n);
 }
+void k_mul_const(const Ctx& C, const u64* in, u64* out, size_t rows, int limbs, const u64* wsh) {
+  HE_LAUNCH_P(k_mul_const_kernel, rows * limbs * C.N, 16.0 * (double)C.N * rows * limbs, (double)C.N * rows * limbs,
+              in, out, rows, limbs, wsh, C.dev_ptab(), C.log_n);
+}
+void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limbs) {
+  HE_LAUNCH(k_add_comps_kernel, (size_t)n * 2 * limbs * C.N, 8.0 * (double)C.N * 6.0 * n * limbs, y, v, n, ypolys,
+            limbs, C.dev_ptab(), C.log_n);
+}
 void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int per_group) {
   HE_LAUNCH(k_add_const_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 2.0 * n * limbs, ct, n, limbs, c_dev, per_group, C.dev_ptab(), C.log_n);
 }
@@ -689,6 +758,11 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
   HE_LAUNCH_P(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p),
               4.0 * C.N * limbs * n * p, A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
+}
+void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs) {
+  HE_LAUNCH_P(k_volley_acc_kernel, (size_t)G * limbs * C.N,
+              8.0 * (double)C.N * limbs * (2.0 * n * G + 2.0 * n + 3.0 * G), 4.0 * C.N * limbs * n * G, Ah, B, d, n,
+              G, limbs, C.dev_ptab(), C.log_n);
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
   const size_t total = (size_t)limbs * C.N;

@@ -49,3 +49,21 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_volley_geometry_matches_oracle_layout():
+    """Host-only arithmetic of the library (no CUDA call): the zero-rotation matmul
+    geometry equals the oracle layout's, and misfits are rejected."""
+    import pytest
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import layouts
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HeError
+    for slots, m, p in [(64, 5, 8), (64, 4, 4), (32, 3, 16), (64, 9, 1), (512, 20, 32), (32768, 256, 256),
+                        (32768, 16, 256), (32768, 128, 128), (32768, 255, 2), (32768, 100, 64)]:
+        M, per, G, _ = layouts.volley_geometry(slots, m, p)
+        assert api.volley_geometry(slots, m, p) == (M, per, G)
+    for slots, m, p in [(64, 5, 3), (16, 20, 4), (16, 10, 8)]:  # p does not divide, or no block fits
+        with pytest.raises(HeError):
+            api.volley_geometry(slots, m, p)

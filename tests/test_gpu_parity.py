@@ -163,6 +163,38 @@ def test_matmul_ragged_shapes(lib, m, n, p):
     assert np.abs(g.decrypt_matrix(gd, m, p) - A @ Bm).max() < 1e-5
 
 
+@pytest.mark.parametrize("log_n,m,n,p", [(13, 4, 8, 4), (10, 20, 3, 32), (10, 1, 5, 2), (10, 16, 9, 1)])
+def test_matmul_volley_matches_oracle_and_fp64(lib, log_n, m, n, p):
+    """Zero-rotation matmul: bit-exact with the oracle from the same plaintexts, decrypts to
+    A @ B; the (20, 3, 32) case splits the positions into several groups."""
+    if log_n == 13:
+        o, g = pair_from_preset(synthetic.MATMUL_SMALL, seed=101, steps=[])
+        A, Bm = synthetic.matmul_operands(m, n, p, seed=101)
+    else:
+        o, g = make_pair(log_n, (60, 40, 40), 1, 60, 1, 40.0, seed=12, steps=[])
+        rng = np.random.default_rng(m * 7 + n + p)
+        A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    M, per, G, _ = layouts.volley_geometry(o.slots, m, p)
+    if (m, p) == (20, 32):
+        assert G == 3
+    Ah = layouts.matrix_a_volley(A, o.slots, p).reshape(G * n, o.slots)
+    oa, ga = encrypt_both(o, g, encode_columns(o, Ah), ct_id_base=0)
+    ob, gb = encrypt_both(o, g, encode_columns(o, layouts.matrix_b_rows(Bm, o.slots)), ct_id_base=500)
+    gd = g.matmul_volley(ga, gb)
+    od = o.matmul_volley(oa.reshape(G, n, *oa.shape[1:]), ob)
+    assert np.array_equal(gd.export(), od)
+    assert np.abs(g.decrypt_matrix_volley(gd, m, p) - A @ Bm).max() < 1e-5
+    # the library's own encoder of the volley layout
+    C2 = g.decrypt_matrix_volley(g.matmul_volley(g.encrypt_matrix_a_volley(A, p, 0), g.encrypt_matrix_b(Bm, 500)),
+                                 m, p)
+    assert np.abs(C2 - A @ Bm).max() < 1e-5
+    # the same product through the revolver path (rotations) decrypts to the same matrix
+    if p > 1:
+        g.keygen(list(range(1, p)))
+        C3 = g.decrypt_matrix(g.matmul(g.encrypt_matrix_a(A, 0), g.encrypt_matrix_b(Bm, 500), m, p), m, p)
+        assert np.abs(C3 - C2).max() < 1e-5
+
+
 @pytest.mark.parametrize("stride,c_in,k,side", [(1, 1, 3, 9), (2, 3, 3, 11), (2, 1, 5, 13), (1, 2, 1, 6)])
 def test_conv2d_matches_oracle_and_fp64(lib, stride, c_in, k, side):
     H = 16
@@ -179,6 +211,38 @@ def test_conv2d_matches_oracle_and_fp64(lib, stride, c_in, k, side):
     got = g.decrypt_image(gy, 3, H, stride, ref.shape[2])  # [B][o*w'][h']
     got = got.reshape(3, 4, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
     assert np.abs(got - ref).max() < 1e-5
+
+
+def _act_polynomials():
+    from tests.test_oracle_pins import act_polynomials
+    return act_polynomials()
+
+
+@pytest.mark.parametrize("name", ["ACT-1", "ACT-2", "deg2"])
+def test_poly_act_degree3_matches_oracle_and_fp64(lib, name):
+    """The paper's ACT-1 / ACT-2 (Table I) and a general degree-2 polynomial: bit-exact with the
+    oracle (two- and three-component inputs), decrypting to f(x) in FP64."""
+    c = _act_polynomials()[name] if name != "deg2" else [0.3, -0.7, 1.1, 0.0]
+    o, g = make_pair(10, (60,) + (45,) * 4, 2, 60, 2, 45.0, seed=23, steps=[])
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (3, o.slots))
+    ox, gx = encrypt_both(o, g, encode_columns(o, x), ct_id_base=70)
+    coeffs = c if name != "deg2" else c[:3]
+    gy = g.poly_act(gx, coeffs)
+    oy, sy = o.poly_act3(ox, c, o.scale)
+    assert gy.polys == 3 and gy.limbs == o.L1 - 2 and gy.scale == sy
+    assert np.array_equal(gy.export(), oy)
+    want = c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+    got = g.decrypt_slots(gy)
+    assert np.abs(got - want).max() < 1e-5
+    # three-component input: x^2 (unrelinearised) through the activation
+    gs = g.poly_act(encrypt_both(o, g, encode_columns(o, x), ct_id_base=70)[1], [0.0, 0.0, 1.0])
+    os_ = np.stack([o.rescale(o.tensor(ox[t], ox[t])) for t in range(3)])
+    g2 = g.poly_act(gs, coeffs)
+    o2, s2 = o.poly_act3(os_, c, o.scale * o.scale / o.q[o.L1 - 1])
+    assert np.array_equal(g2.export(), o2) and g2.scale == s2
+    x2 = x ** 2
+    assert np.abs(g.decrypt_slots(g2) - (c[0] + c[1] * x2 + c[2] * x2 ** 2 + c[3] * x2 ** 3)).max() < 1e-5
 
 
 def test_fc_matches_oracle(lib):

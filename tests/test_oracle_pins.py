@@ -418,6 +418,113 @@ def test_matmul_rectangular_detects_transposition():
     assert np.abs(C - A @ Bm).max() < 1e-6
 
 
+@pytest.mark.parametrize("slots,m,n,p", [(64, 5, 3, 8), (64, 4, 2, 4), (32, 3, 5, 16), (64, 9, 2, 1),
+                                          (4096, 17, 4, 64), (32768, 256, 3, 256), (32768, 16, 2, 256)])
+def test_volley_layout_is_gemm_in_slots(slots, m, n, p):
+    """Zero-rotation matmul layout: block geometry, and the slotwise sum of products of A's
+    volley encoding with B's period-p rows decodes to A @ B (plaintext slots, exact up to fp)."""
+    M, per, G, off = layouts.volley_geometry(slots, m, p)
+    assert M >= m and (M - 1) % p == 0 and G == -(-p // per)
+    covered = []
+    for g in range(G):
+        cnt = min(per, p - g * per)
+        assert cnt >= 1 and (cnt - 1) * M + off[g] + m <= slots
+        assert off[g] == (g * per) % p
+        covered += [g * per + t for t in range(cnt)]
+    assert covered == list(range(p))
+    rng = np.random.default_rng(slots + m + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    Ah = layouts.matrix_a_volley(A, slots, p)
+    Bt = layouts.matrix_b_rows(Bm, slots)
+    assert Ah.shape == (G, n, slots)
+    # each group holds m * cnt nonzero slots per column ciphertext, nothing else
+    assert all(np.count_nonzero(Ah[g, 0]) == m * min(per, p - g * per) for g in range(G))
+    d = np.stack([(Ah[g] * Bt).sum(0) for g in range(G)])
+    assert np.abs(layouts.matmul_from_volley(d, m, p) - A @ Bm).max() < 1e-12
+    # a transposed operand is caught
+    if m == n and m > 1:
+        d2 = np.stack([(layouts.matrix_a_volley(A.T, slots, p)[g] * Bt).sum(0) for g in range(G)])
+        assert np.abs(layouts.matmul_from_volley(d2, m, p) - A @ Bm).max() > 1e-3
+
+
+@pytest.mark.parametrize("m,n,p", [(5, 3, 8), (20, 2, 16)])
+def test_matmul_volley_encrypted_matches_fp64_without_rotations(m, n, p):
+    """Encrypted zero-rotation matmul: decrypts to A @ B; G n tensors, G relins, no rotation."""
+    o = Oracle(8, (60, 40, 40), 1, 60, 1, 40.0, seed=5)
+    o.keygen([])
+    rng = np.random.default_rng(m + n + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    M, per, G, off = layouts.volley_geometry(o.slots, m, p)
+    Ah = layouts.matrix_a_volley(A, o.slots, p)
+    Ac = np.stack([[o.encrypt(o.encode(Ah[g, k]), ct_id=g * n + k) for k in range(n)] for g in range(G)])
+    Bc = np.stack([o.encrypt(o.encode(v), ct_id=50 + i) for i, v in enumerate(layouts.matrix_b_rows(Bm, o.slots))])
+    o.reset_counters()
+    D = o.matmul_volley(Ac, Bc)
+    c = o.counters()
+    assert c["rotations"] == 0 and c["tensors"] == G * n and c["relins"] == G and c["rescales"] == G
+    C = layouts.matmul_from_volley(np.stack([o.decrypt(d, o.scale ** 2 / o.q[-1]) for d in D]), m, p)
+    assert np.abs(C - A @ Bm).max() < 1e-6
+    if m == 20:
+        assert G > 1  # the second case splits the positions into groups
+
+
+def act_polynomials():
+    """Table I's ACT-1 / ACT-2 coefficients from the golden fixture: {name: [c0, c1, c2, c3]}."""
+    out = {}
+    for line in open(golden_path("act_polynomials_table1.txt")):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            out[f[0]] = [float(v) for v in f[1:]]
+    return out
+
+
+def test_act_fixture_matches_table1():
+    acts = act_polynomials()
+    assert set(acts) == {"ACT-1", "ACT-2"} and all(len(c) == 4 for c in acts.values())
+    assert acts["ACT-1"][2] == 2.0225089 and acts["ACT-2"][0] == -1.5650465
+
+
+@pytest.mark.parametrize("name,coeffs", [("ACT-1", None), ("ACT-2", None), ("x^2", [0, 0, 1, 0]),
+                                         ("const", [0.75, 0, 0, 0]), ("identity", [0, 1, 0, 0]),
+                                         ("cube", [0, 0, 0, 1])])
+def test_poly_act3_decrypts_to_polynomial(name, coeffs):
+    """Degree-3 activation (Table I's ACT layers): decrypts to c0 + c1 x + c2 x^2 + c3 x^3 at every
+    slot, two levels consumed, three components out; also from a three-component input."""
+    c = act_polynomials()[name] if coeffs is None else coeffs
+    o = Oracle(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=21)
+    o.keygen([])
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, (2, o.slots))
+    X = np.stack([o.encrypt(o.encode(v), ct_id=i) for i, v in enumerate(x)])
+    o.reset_counters()
+    Y, sy = o.poly_act3(X, c, o.scale)
+    cnt = o.counters()
+    assert Y.shape == (2, 3, o.L1 - 2, o.N)
+    assert cnt["tensors"] == 4 and cnt["rescales"] == 8 and cnt["relins"] == 2 and cnt["ct_scalar"] == 4
+    want = c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+    got = np.stack([o.decrypt(o.relin(y), sy) for y in Y])
+    assert np.abs(got - want).max() < 1e-6
+    # a three-component input (an unrelinearised product) is relinearised first
+    sq = o.rescale(o.tensor(X[0], X[0]))
+    s2 = o.scale * o.scale / o.q[o.L1 - 1]
+    Y2, sy2 = o.poly_act3(sq[None], c, s2)
+    x2 = x[0] ** 2
+    got2 = o.decrypt(o.relin(Y2[0]), sy2)
+    assert np.abs(got2 - (c[0] + c[1] * x2 + c[2] * x2 ** 2 + c[3] * x2 ** 3)).max() < 1e-5
+
+
+def test_poly_act3_dropped_term_is_caught():
+    """Planted mistake check: a wrong coefficient order (c3 <-> c2) changes the result."""
+    o = Oracle(9, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=22)
+    o.keygen([])
+    x = np.random.default_rng(4).uniform(-1, 1, o.slots)
+    X = o.encrypt(o.encode(x), ct_id=0)[None]
+    c = act_polynomials()["ACT-1"]
+    Y, sy = o.poly_act3(X, [c[0], c[1], c[3], c[2]], o.scale)
+    got = o.decrypt(o.relin(Y[0]), sy)
+    assert np.abs(got - (c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3)).max() > 1e-2
+
+
 def encrypt_images(o, imgs, H, limbs=None, base_id=0):
     """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
     Bn, C, h, w = imgs.shape
