@@ -15,16 +15,19 @@
 // "rows" whole runs; the inverse runs them in the opposite order. grid.y is
 // the limb (row of N words), so one launch covers every limb of a batch.
 //
-// Inside a sub-transform of M = 2^m points each thread holds 8 elements in
-// registers and runs up to three butterfly stages per round before
-// exchanging through shared memory. In round r (stages 3r .. 3r+2, from the
-// largest distance down) element k of thread u is the index with k's bits at
-// the round's distance bit positions (plus, in a short last round, the top
-// positions not in the round) and u's bits in the remaining positions in
-// order. All index arithmetic is compile-time shifts and masks. The row
-// kernel keeps each sub-transform inside one warp; its shared memory is
-// swizzled, word x at x ^ g(x >> 4) for a GF(2)-linear g, which makes every
-// round's 64-bit accesses conflict-free for all M <= 256.
+// Inside a sub-transform of M = 2^m points each thread holds 2^b elements in
+// registers (b = 4 in the column kernels, 3 in the row kernels) and runs up to
+// b butterfly stages per round before exchanging through shared memory. In
+// round r (stages b r .. b r + b - 1, from the largest distance down) element
+// k of thread u is the index with k's bits at the round's distance bit
+// positions (plus, in a short last round, the top positions not in the round)
+// and u's bits in the remaining positions in order. All index arithmetic is
+// compile-time shifts and masks. The column kernels address shared memory by
+// element index times the column count plus the column, so the threads of a
+// half-warp (adjacent columns) touch adjacent words; the row kernel keeps each
+// sub-transform inside one warp and swizzles its shared memory, word x at
+// x ^ g(x >> 4) for a GF(2)-linear g, which makes every round's 64-bit
+// accesses conflict-free for all M <= 256.
 #include "he_internal.h"
 
 namespace he {
@@ -69,13 +72,16 @@ struct Fuse {
 // ---------------------------------------------------------------------------
 // compile-time round maps
 // ---------------------------------------------------------------------------
-template <int LOGM, int RND>
+// Each thread holds 2^KBM elements of a sub-transform and runs up to KBM
+// butterfly stages per round between exchanges: KBM = 4 in the column kernels,
+// 3 in the row kernels (whose 64-register budget keeps four blocks per SM).
+template <int LOGM, int RND, int KBM>
 struct RMap {
-  static constexpr int KB = LOGM < 3 ? LOGM : 3;  // k bits (elements per thread = 2^KB)
+  static constexpr int KB = LOGM < KBM ? LOGM : KBM;  // k bits (elements per thread = 2^KB)
   static constexpr int E = 1 << KB;
-  static constexpr int S0 = 3 * RND;
-  static constexpr int NS = (LOGM - S0) < 3 ? (LOGM - S0) : 3;  // stages in this round
-  static constexpr int LO = LOGM - S0 - NS;                     // lowest distance bit of the round
+  static constexpr int S0 = KBM * RND;
+  static constexpr int NS = (LOGM - S0) < KBM ? (LOGM - S0) : KBM;  // stages in this round
+  static constexpr int LO = LOGM - S0 - NS;                         // lowest distance bit of the round
   // bit position of k bit i
   __host__ __device__ static constexpr int kpos(int i) {
     if (i < NS) return LO + i;
@@ -89,9 +95,10 @@ struct RMap {
   }
   // i-th smallest k position
   __host__ __device__ static constexpr int sorted_kpos(int i) {
-    int v[3] = {kpos(0), KB > 1 ? kpos(1) : 99, KB > 2 ? kpos(2) : 99};
-    for (int a = 0; a < 3; a++)
-      for (int b = a + 1; b < 3; b++)
+    int v[KBM] = {};
+    for (int a = 0; a < KBM; a++) v[a] = a < KB ? kpos(a) : 99;
+    for (int a = 0; a < KBM; a++)
+      for (int b = a + 1; b < KBM; b++)
         if (v[b] < v[a]) { const int t = v[a]; v[a] = v[b]; v[b] = t; }
     return v[i];
   }
@@ -112,13 +119,14 @@ struct RMap {
   }
 };
 
-template <int LOGM>
+template <int LOGM, int KBM>
 struct Plan {
-  static constexpr int KB = LOGM < 3 ? LOGM : 3;
+  static constexpr int KB = LOGM < KBM ? LOGM : KBM;
   static constexpr int E = 1 << KB;
-  static constexpr int T = (1 << LOGM) / E;  // threads per sub-transform
-  static constexpr int R = (LOGM + 2) / 3;   // rounds
+  static constexpr int T = (1 << LOGM) / E;         // threads per sub-transform
+  static constexpr int R = (LOGM + KBM - 1) / KBM;  // rounds
 };
+constexpr int kColKB = 4, kRowKB = 3;
 
 // bit reversal of the low `bits` bits, for compile-time arguments
 __host__ __device__ constexpr u32 brv_const(u32 x, int bits) {
@@ -137,10 +145,10 @@ __device__ __forceinline__ ulonglong2 tw_load(const u64* tw, u64 idx) {
 // NAR (primes below kNarrowPrime): no reduction of the upper input and the
 // cheaper quotient estimate, so each stage raises the bound on the values by
 // at most 4q; otherwise Harvey's butterfly keeps them in [0, 4q).
-template <int LOGM, int RND, bool NAR>
-__device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
+template <int LOGM, int RND, int KBM, bool NAR>
+__device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM, KBM>::E], int xu, const u64* tw, int soff, u64 run,
                                           u64 q) {
-  using M = RMap<LOGM, RND>;
+  using M = RMap<LOGM, RND, KBM>;
   const u64 q2 = 2 * q, q4 = 4 * q;
 #pragma unroll
   for (int st = 0; st < M::NS; st++) {
@@ -174,10 +182,10 @@ __device__ __forceinline__ void round_fwd(u64 (&a)[Plan<LOGM>::E], int xu, const
 // One inverse round (Gentleman-Sande), stages in the opposite order. NAR: the
 // sums are not reduced; the inputs of the stage executed t-th (t = LOGM - 1 - s)
 // are below 2^(t+1) q, which the difference adds before its product.
-template <int LOGM, int RND, bool NAR>
-__device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const u64* tw, int soff, u64 run,
+template <int LOGM, int RND, int KBM, bool NAR>
+__device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM, KBM>::E], int xu, const u64* tw, int soff, u64 run,
                                           u64 q) {
-  using M = RMap<LOGM, RND>;
+  using M = RMap<LOGM, RND, KBM>;
   const u64 q2 = 2 * q;
 #pragma unroll
   for (int st = M::NS - 1; st >= 0; st--) {
@@ -210,41 +218,41 @@ __device__ __forceinline__ void round_inv(u64 (&a)[Plan<LOGM>::E], int xu, const
 
 // Rounds RND .. R-1 (forward) with exchanges through shared memory; `addr`
 // maps an element index to its shared-memory word.
-template <int LOGM, int RND, bool NAR, class Sync, class Addr>
-__device__ __forceinline__ void rounds_fwd_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
+template <int LOGM, int RND, int KBM, bool NAR, class Sync, class Addr>
+__device__ __forceinline__ void rounds_fwd_rest(u64 (&a)[Plan<LOGM, KBM>::E], int u, u64* sm, Addr addr, Sync sync,
                                                 const u64* tw, int soff, u64 run, u64 q) {
-  if constexpr (RND < Plan<LOGM>::R) {
-    using Mp = RMap<LOGM, RND - 1>;
-    using Mc = RMap<LOGM, RND>;
+  if constexpr (RND < Plan<LOGM, KBM>::R) {
+    using Mp = RMap<LOGM, RND - 1, KBM>;
+    using Mc = RMap<LOGM, RND, KBM>;
     const int xp = Mp::upart(u);
 #pragma unroll
-    for (int k = 0; k < Plan<LOGM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
+    for (int k = 0; k < Plan<LOGM, KBM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
     sync();
     const int xc = Mc::upart(u);
 #pragma unroll
-    for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
+    for (int k = 0; k < Plan<LOGM, KBM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
     sync();
-    round_fwd<LOGM, RND, NAR>(a, xc, tw, soff, run, q);
-    rounds_fwd_rest<LOGM, RND + 1, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
+    round_fwd<LOGM, RND, KBM, NAR>(a, xc, tw, soff, run, q);
+    rounds_fwd_rest<LOGM, RND + 1, KBM, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
   }
 }
 
-template <int LOGM, int RND, bool NAR, class Sync, class Addr>
-__device__ __forceinline__ void rounds_inv_rest(u64 (&a)[Plan<LOGM>::E], int u, u64* sm, Addr addr, Sync sync,
+template <int LOGM, int RND, int KBM, bool NAR, class Sync, class Addr>
+__device__ __forceinline__ void rounds_inv_rest(u64 (&a)[Plan<LOGM, KBM>::E], int u, u64* sm, Addr addr, Sync sync,
                                                 const u64* tw, int soff, u64 run, u64 q) {
   if constexpr (RND >= 0) {
-    using Mp = RMap<LOGM, RND + 1>;
-    using Mc = RMap<LOGM, RND>;
+    using Mp = RMap<LOGM, RND + 1, KBM>;
+    using Mc = RMap<LOGM, RND, KBM>;
     const int xp = Mp::upart(u);
 #pragma unroll
-    for (int k = 0; k < Plan<LOGM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
+    for (int k = 0; k < Plan<LOGM, KBM>::E; k++) sm[addr(xp | Mp::kbits(k))] = a[k];
     sync();
     const int xc = Mc::upart(u);
 #pragma unroll
-    for (int k = 0; k < Plan<LOGM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
+    for (int k = 0; k < Plan<LOGM, KBM>::E; k++) a[k] = sm[addr(xc | Mc::kbits(k))];
     sync();
-    round_inv<LOGM, RND, NAR>(a, xc, tw, soff, run, q);
-    rounds_inv_rest<LOGM, RND - 1, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
+    round_inv<LOGM, RND, KBM, NAR>(a, xc, tw, soff, run, q);
+    rounds_inv_rest<LOGM, RND - 1, KBM, NAR>(a, u, sm, addr, sync, tw, soff, run, q);
   }
 }
 
@@ -271,7 +279,7 @@ constexpr int kRowThreads = 256;
 template <int LOGM, int MODE, bool NAR>
 __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n, int n1, u64 run,
                                               u64 q, u64 one_sh, const LimbMap& lm, const Fuse& fz) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   const size_t N = (size_t)1 << n;
   auto addr = [rw](int e) { return swz(rw * M + e); };
@@ -280,14 +288,14 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
   auto fin = [q, one_sh](u64 v) { return NAR ? shoup(v, 1, one_sh, q) : reduce4q(v, q); };
   u64 a[P::E];
   {
-    using M0 = RMap<LOGM, 0>;
+    using M0 = RMap<LOGM, 0, kRowKB>;
     const int x0 = M0::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xr[x0 | M0::kbits(k)];
-    round_fwd<LOGM, 0, NAR>(a, x0, tw, n1, run, q);
+    round_fwd<LOGM, 0, kRowKB, NAR>(a, x0, tw, n1, run, q);
   }
-  rounds_fwd_rest<LOGM, 1, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
-  using ML = RMap<LOGM, P::R - 1>;
+  rounds_fwd_rest<LOGM, 1, kRowKB, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
+  using ML = RMap<LOGM, P::R - 1, kRowKB>;
   const int xl = ML::upart(u);
   if constexpr (MODE == 0) {
 #pragma unroll
@@ -335,7 +343,7 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
 template <int LOGM, int MODE>
 __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, LimbMap lm, const PrimeTab* pt,
                                                               const u64* tw_all, int n, int n1, Fuse fz) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
   __shared__ u64 sm[kRowThreads * P::E];
@@ -363,20 +371,20 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, Limb
 template <int LOGM, bool NAR>
 __device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n1, u64 run, u64 q,
                                               u64 one_sh) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   auto addr = [rw](int e) { return swz(rw * M + e); };
   auto sync = [] { __syncwarp(__activemask()); };
   u64 a[P::E];
   {
-    using ML = RMap<LOGM, P::R - 1>;
+    using ML = RMap<LOGM, P::R - 1, kRowKB>;
     const int xl = ML::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xr[xl | ML::kbits(k)];
-    round_inv<LOGM, P::R - 1, NAR>(a, xl, tw, n1, run, q);
+    round_inv<LOGM, P::R - 1, kRowKB, NAR>(a, xl, tw, n1, run, q);
   }
-  rounds_inv_rest<LOGM, P::R - 2, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
-  using M0 = RMap<LOGM, 0>;
+  rounds_inv_rest<LOGM, P::R - 2, kRowKB, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
+  using M0 = RMap<LOGM, 0, kRowKB>;
   const int x0 = M0::upart(u);
 #pragma unroll
   for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = NAR ? shoup_lazy(a[k], 1, one_sh, q) : a[k];
@@ -385,7 +393,7 @@ __device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, 
 template <int LOGM>
 __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
                                                               const u64* tw_all, int n, int n1) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
   __shared__ u64 sm[kRowThreads * P::E];
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, Limb
 template <int LOGM, int MODE, bool NAR>
 __device__ __forceinline__ void fwd_cols_body(u64* xc, u64* smc, int u, int C, int lo, const u64* tw, int n, u64 q,
                                               const LimbMap& lm, const PrimeTab* pt, const Fuse& fz) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kColKB>;
   const size_t N = (size_t)1 << n;
   const size_t stride = N >> LOGM;
   auto addr = [C, lo](int e) { return e * C + lo; };
@@ -425,7 +433,7 @@ __device__ __forceinline__ void fwd_cols_body(u64* xc, u64* smc, int u, int C, i
   auto prod = [q](u64 y, ulonglong2 h) { return NAR ? shoup_approx(y, h.x, h.y, q) : shoup_lazy(y, h.x, h.y, q); };
   u64 a[P::E];
   {
-    using M0 = RMap<LOGM, 0>;
+    using M0 = RMap<LOGM, 0, kColKB>;
     const int x0 = M0::upart(u);
     if constexpr (MODE == 0) {
 #pragma unroll
@@ -474,10 +482,10 @@ __device__ __forceinline__ void fwd_cols_body(u64* xc, u64* smc, int u, int C, i
         a[k] = shoup_lazy(v, 1, one_sh, q) + q_m_half;  // [0, 3q), within the transform's [0, 4q) inputs
       }
     }
-    round_fwd<LOGM, 0, NAR>(a, x0, tw, 0, 0, q);
+    round_fwd<LOGM, 0, kColKB, NAR>(a, x0, tw, 0, 0, q);
   }
-  rounds_fwd_rest<LOGM, 1, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
-  using ML = RMap<LOGM, P::R - 1>;
+  rounds_fwd_rest<LOGM, 1, kColKB, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
+  using ML = RMap<LOGM, P::R - 1, kColKB>;
   const int xl = ML::upart(u);
 #pragma unroll
   for (int k = 0; k < P::E; k++) xc[(size_t)(xl | ML::kbits(k)) * stride] = a[k];
@@ -505,21 +513,21 @@ __global__ void k_ntt_fwd_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
 template <int LOGM, int MODE, bool NAR>
 __device__ __forceinline__ void inv_cols_body(u64* xc, u64* smc, int u, int C, int lo, const u64* tw, int n, u64 q,
                                               u64 sc, u64 scs) {
-  using P = Plan<LOGM>;
+  using P = Plan<LOGM, kColKB>;
   const size_t N = (size_t)1 << n;
   const size_t stride = N >> LOGM;
   auto addr = [C, lo](int e) { return e * C + lo; };
   auto sync = [] { __syncthreads(); };
   u64 a[P::E];
   {
-    using ML = RMap<LOGM, P::R - 1>;
+    using ML = RMap<LOGM, P::R - 1, kColKB>;
     const int xl = ML::upart(u);
 #pragma unroll
     for (int k = 0; k < P::E; k++) a[k] = xc[(size_t)(xl | ML::kbits(k)) * stride];
-    round_inv<LOGM, P::R - 1, NAR>(a, xl, tw, 0, 0, q);
+    round_inv<LOGM, P::R - 1, kColKB, NAR>(a, xl, tw, 0, 0, q);
   }
-  rounds_inv_rest<LOGM, P::R - 2, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
-  using M0 = RMap<LOGM, 0>;
+  rounds_inv_rest<LOGM, P::R - 2, kColKB, NAR>(a, u, smc, addr, sync, tw, 0, 0, q);
+  using M0 = RMap<LOGM, 0, kColKB>;
   const int x0 = M0::upart(u);
 #pragma unroll
   for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], sc, scs, q);
@@ -563,7 +571,7 @@ Geom geom(int log_n) {
 template <int L, int MODE>
 void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n1, const u64* tw,
                  const Fuse& fz) {
-  constexpr int RUNS = kRowThreads / Plan<L>::T;
+  constexpr int RUNS = kRowThreads / Plan<L, kRowKB>::T;
   const int runs = 1 << n1;
   const dim3 grid((runs + RUNS - 1) / RUNS, rows);
   // a fused rescale also reads the limbs being rescaled and multiplies by q_l^{-1}
@@ -584,7 +592,7 @@ void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C,
 template <int L, int MODE>
 void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C, int n2, int Ccols, const u64* tw,
                  const Fuse& fz) {
-  const int threads = Ccols * Plan<L>::T;
+  const int threads = Ccols * Plan<L, kColKB>::T;
   const size_t smem = (size_t)(1 << L) * Ccols * 8;
   const dim3 grid((1 << n2) / Ccols, rows);
   // butterflies, plus N^{-1} (inverse) or the reduction of the expanded limb (fused rescale)
