@@ -211,6 +211,28 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
               int c_out, int k, int stride, he_ctset** out);
 
 /*
+ * he_encrypt_conv_weights: the model provider's kernel ciphertexts (Sec. V:
+ * kernels are encrypted before they reach the server; Kernelspanner's role,
+ * Sec. III-C, in the column layout). W [c_out][c_in][k][k] -> c_out * c_in * k
+ * * k ciphertexts in that order, each encrypting the constant polynomial
+ * round(W q_{limbs-1}) (the weight at every slot, at scale q_{limbs-1}) with
+ * `limbs` limbs. Ids ct_id_base + index. Errors: HE_E_ARG, HE_E_LEVEL.
+ */
+int he_encrypt_conv_weights(he_ctx* ctx, const double* W, int c_out, int c_in, int k, int limbs, uint64_t ct_id_base,
+                            he_ctset** out);
+
+/*
+ * he_conv2d_enc: he_conv2d with encrypted kernels (from
+ * he_encrypt_conv_weights at the input's level). Output (o, j') = sum_{c,b,a}
+ * W[o][c][a][b] (x) Rot(X_{c, s j' + b}, gap a), summed as three-component
+ * tensor products, rescaled, relinearised, plus round(bias_o scale); layout,
+ * scale, level and keys as he_conv2d (plus the relinearisation key). All
+ * rotations of the input are held at once (the work budget is not applied).
+ */
+int he_conv2d_enc(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const he_ctset* weights, const double* bias,
+                  int c_out, int k, int stride, he_ctset** out);
+
+/*
  * he_poly_act: polynomial activation in place, coeffs[0..degree] the
  * coefficients c0, c1, ... of f(x) = sum_d c_d x^d.
  *  - degree 2 with coeffs {0, 0, 1} (x -> x^2): tensor product, rescale; one

@@ -12,6 +12,7 @@ in the coefficient domain (residues in [0, q_i)).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Optional, Sequence
 
@@ -69,6 +70,11 @@ def _lib():
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
             "oc_matmul_volley": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_matmul_bsgs": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              _u64p]),
+            "oc_conv2d_enc": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _u64p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int, _ip, _u64p]),
             "oc_poly_act3": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                             _u64p, _dp]),
             "oc_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
@@ -86,6 +92,15 @@ def _lib():
             f.argtypes = args
         _LIB = lib
     return _LIB
+
+
+def round_half_away(x: float) -> int:
+    """Nearest integer to the double x, ties away from zero (C's llround): the
+    fraction |x| - floor(|x|) is exact in double precision."""
+    a = abs(x)
+    f = math.floor(a)
+    r = int(f) + (1 if a - f >= 0.5 else 0)
+    return -r if x < 0 else r
 
 
 def _p(a: np.ndarray, t):
@@ -295,6 +310,14 @@ class Oracle:
         _check(self.lib.oc_matmul(self.h, _p(A, _u64p), _p(B, _u64p), n, p, lp, _p(out, _u64p)))
         return out
 
+    def matmul_bsgs(self, A, B, p: int, g: int) -> np.ndarray:
+        """A, B: [n][2][lp][N] -> D [p][2][lp-1][N] (diagonal layout), baby-step size g."""
+        A, B = _u64(A), _u64(B)
+        n, _, lp, _ = A.shape
+        out = np.zeros((p, 2, lp - 1, self.N), np.uint64)
+        _check(self.lib.oc_matmul_bsgs(self.h, _p(A, _u64p), _p(B, _u64p), n, p, g, lp, _p(out, _u64p)))
+        return out
+
     def matmul_volley(self, Ahat, B) -> np.ndarray:
         """Ahat [G][n][2][lp][N] (volley encoding of A), B [n][2][lp][N] -> D [G][2][lp-1][N]."""
         Ahat, B = _u64(Ahat), _u64(B)
@@ -320,6 +343,32 @@ class Oracle:
         _check(self.lib.oc_conv2d(self.h, _p(X, _u64p), polys, lp, c_in, w_in, gap, _p(K, _dp),
                                   None if b is None else _p(b, _dp), c_out, k, stride, scale, len(sel),
                                   _p(sel_a, _ip), schedule, _p(out, _u64p)))
+        return out
+
+    def conv_weight_plaintexts(self, K, lp: int) -> np.ndarray:
+        """Constant plaintexts of encrypted kernels: K [c_out][c_in][k][k] -> [c_out*c_in*k*k][N]
+        int64, coefficient 0 = round(K q_{lp-1}) (every slot K at scale q_{lp-1}), others 0."""
+        K = np.asarray(K, dtype=np.float64)
+        m = np.zeros((K.size, self.N), np.int64)
+        ql = float(self.q[lp - 1])
+        m[:, 0] = [int(round_half_away(w * ql)) for w in K.reshape(-1)]
+        return m
+
+    def conv2d_enc(self, X, gap: int, Wct, bias, c_out: int, k: int, stride: int, scale: float,
+                   sel=None) -> np.ndarray:
+        """X [c_in][w_in][2 or 3][lp][N]; Wct [c_out*c_in*k*k][2][lp][N] kernel ciphertexts
+        -> [n_sel][2][lp-1][N]."""
+        X, Wct = _u64(X), _u64(Wct)
+        c_in, w_in, polys, lp, _ = X.shape
+        w_out = (w_in - k) // stride + 1
+        if sel is None:
+            sel = [(o, j) for o in range(c_out) for j in range(w_out)]
+        sel_a = np.ascontiguousarray(np.array(sel, dtype=np.int32).reshape(-1, 2))
+        b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+        out = np.zeros((len(sel), 2, lp - 1, self.N), np.uint64)
+        _check(self.lib.oc_conv2d_enc(self.h, _p(X, _u64p), polys, lp, c_in, w_in, gap, _p(Wct, _u64p),
+                                      None if b is None else _p(b, _dp), c_out, k, stride, scale, len(sel),
+                                      _p(sel_a, _ip), _p(out, _u64p)))
         return out
 
     def square(self, X) -> np.ndarray:

@@ -77,6 +77,81 @@ static std::vector<Ct> matmul(Ctx& C, const std::vector<Ct>& A, const std::vecto
   return D;
 }
 
+// Convolution with encrypted kernels (the model provider's kernel ciphertexts,
+// Sec. V; Kernelspanner's role, Sec. III-C, in the column layout): Wct[o][c][a][b]
+// encrypts the constant K[o][c][a][b] (every slot) at scale q_l. Output (o, j') is
+//     sum_c sum_b sum_a Wct[o][c][a][b] (x) Rot(X_{c, s j' + b}, g a)
+// accumulated as three-component tensors (order c, b, a), rescaled,
+// relinearised, plus round(bias_o * scale). The rotations are hoisted per input
+// column as in the plaintext-weight schedule.
+static std::vector<Ct> conv2d_enc(Ctx& C, const std::vector<std::vector<Ct>>& X, int gap, const std::vector<Ct>& Wct,
+                                  const double* bias, int c_out, int k, int stride, double scale,
+                                  const std::vector<std::pair<int, int>>& sel) {
+  const int c_in = (int)X.size();
+  std::set<std::pair<int, int>> need;
+  for (auto& s : sel)
+    for (int c = 0; c < c_in; c++)
+      for (int b = 0; b < k; b++) need.insert({c, stride * s.second + b});
+  std::vector<std::pair<int, int>> needv(need.begin(), need.end());
+  std::vector<long> steps(k);
+  for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
+  std::vector<std::vector<Ct>> rot(needv.size());
+#pragma omp parallel for schedule(dynamic)
+  for (size_t t = 0; t < needv.size(); t++)
+    rot[t] = ct_rotate_hoisted(C, two_comp(C, X[needv[t].first][needv[t].second]), steps);
+  std::map<std::pair<int, int>, size_t> where;
+  for (size_t t = 0; t < needv.size(); t++) where[needv[t]] = t;
+  std::vector<Ct> out(sel.size());
+#pragma omp parallel for schedule(dynamic)
+  for (size_t t = 0; t < sel.size(); t++) {
+    const int o = sel[t].first, jp = sel[t].second;
+    Ct acc;
+    bool first = true;
+    for (int c = 0; c < c_in; c++)
+      for (int b = 0; b < k; b++)
+        for (int a = 0; a < k; a++) {
+          const Ct& w = Wct[(((size_t)o * c_in + c) * k + a) * k + b];
+          Ct term = ct_tensor(C, w, rot[where.at({c, stride * jp + b})][a]);
+          acc = first ? term : ct_add(C, acc, term);
+          first = false;
+        }
+    Ct r = ct_relin(C, ct_rescale(C, acc));
+    if (bias) r = ct_add_const(C, r, std::llround(bias[o] * scale));
+    out[t] = r;
+  }
+  return out;
+}
+
+// Baby-step giant-step form of the revolver: idx = g i + j (j < g). Since
+// rotation commutes with slotwise products and sums,
+//   D_{g i + j} = Rot( sum_k Rot(A_k, -g i) (x) Rot(B~_k, j), g i ):
+// the n(p-1) rotations of B~ become n(g-1) baby steps of B~, n(ceil(p/g)-1)
+// giant steps of A (hoisted per ciphertext) and one rotation by g i of each
+// output with i >= 1, after its rescale and relinearisation.
+static std::vector<Ct> matmul_bsgs(Ctx& C, const std::vector<Ct>& A, const std::vector<Ct>& B, int p, int g) {
+  const int n = (int)A.size(), ng = (p + g - 1) / g;
+  const long S = (long)C.N / 2;
+  std::vector<long> baby(g), giant(ng);
+  for (int j = 0; j < g; j++) baby[j] = j;
+  for (int i = 0; i < ng; i++) giant[i] = i == 0 ? 0 : S - (long)g * i;
+  std::vector<std::vector<Ct>> Rb(n), Ra(n);
+#pragma omp parallel for schedule(dynamic)
+  for (int k = 0; k < n; k++) {
+    Rb[k] = ct_rotate_hoisted(C, B[k], baby);
+    Ra[k] = ct_rotate_hoisted(C, A[k], giant);
+  }
+  std::vector<Ct> D(p);
+#pragma omp parallel for schedule(dynamic)
+  for (int idx = 0; idx < p; idx++) {
+    const int i = idx / g, j = idx % g;
+    Ct T = ct_tensor(C, Ra[0][i], Rb[0][j]);
+    for (int k = 1; k < n; k++) T = ct_add(C, T, ct_tensor(C, Ra[k][i], Rb[k][j]));
+    Ct d = ct_relin(C, ct_rescale(C, T));
+    D[idx] = i == 0 ? d : ct_rotate_hoisted(C, d, {(long)g * i})[0];
+  }
+  return D;
+}
+
 // Zero-rotation ("volley") form of the same product: group g of A's volley
 // encoding holds column k at blocks t*M + o_g (M = 1 mod p), so the slotwise
 // product with B~_k (period p) already pairs A[i][k] with B[k][(i + idx) mod p]
@@ -284,6 +359,29 @@ const char* ol_last_error() { return g_lerr.c_str(); }
 int oc_matmul(void* h, const uint64_t* A, const uint64_t* B, int n, int p, int lp, uint64_t* D) {
   OL_TRY(Ctx* C = (Ctx*)h; std::vector<Ct> d = matmul(*C, cts_from(*C, A, n, lp), cts_from(*C, B, n, lp), p);
          cts_to(*C, d, D));
+}
+
+// X [c_in][w_in][polys][lp][N]; Wct [c_out][c_in][k][k][2][lp][N]; bias [c_out] or NULL;
+// sel [n_sel][2] = (o, j'); out [n_sel][2][lp-1][N].
+int oc_conv2d_enc(void* h, const uint64_t* X, int polys, int lp, int c_in, int w_in, int gap, const uint64_t* Wct,
+                  const double* bias, int c_out, int k, int stride, double scale, int n_sel, const int* sel,
+                  uint64_t* out) {
+  OL_TRY(Ctx* C = (Ctx*)h; std::vector<std::vector<Ct>> x(c_in);
+         for (int c = 0; c < c_in; c++) x[c] = cts_from(*C, X + (size_t)c * w_in * polys * lp * C->N, w_in, lp, polys);
+         std::vector<Ct> w = cts_from(*C, Wct, c_out * c_in * k * k, lp);
+         std::vector<std::pair<int, int>> s(n_sel);
+         for (int t = 0; t < n_sel; t++) {
+           s[t] = {sel[2 * t], sel[2 * t + 1]};
+           if (s[t].first < 0 || s[t].first >= c_out || stride * s[t].second + k > w_in) throw std::runtime_error("bad output index");
+         }
+         std::vector<Ct> r = conv2d_enc(*C, x, gap, w, bias, c_out, k, stride, scale, s);
+         cts_to(*C, r, out));
+}
+
+// A, B [n][2][lp][N] -> D [p][2][lp-1][N], baby-step size g
+int oc_matmul_bsgs(void* h, const uint64_t* A, const uint64_t* B, int n, int p, int g, int lp, uint64_t* D) {
+  OL_TRY(Ctx* C = (Ctx*)h; if (g < 1 || g > p) throw std::runtime_error("baby-step size out of range");
+         std::vector<Ct> d = matmul_bsgs(*C, cts_from(*C, A, n, lp), cts_from(*C, B, n, lp), p, g); cts_to(*C, d, D));
 }
 
 // Ahat [G][n][2][lp][N] (volley encoding of A), B [n][2][lp][N] -> D [G][2][lp-1][N]

@@ -70,6 +70,8 @@ SIGNATURES = {
     "he_matmul_batched": (I, [V, I, PV, PV, P_I, P_I, PV]),
     "he_matmul_volley": (I, [V, V, V, PV]),
     "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
+    "he_encrypt_conv_weights": (I, [V, P_D, I, I, I, I, U64, PV]),
+    "he_conv2d_enc": (I, [V, V, I, I, V, P_D, I, I, I, PV]),
     "he_poly_act": (I, [V, V, P_D, I]),
     "he_fc_prepare": (I, [V, P_D, I, I, I, I, I, I, I, I, PV]),
     "he_fc_prepare_coeffs": (I, [V, P_I64, I, I, I, I, I, I, PV]),

@@ -220,6 +220,17 @@ class Context:
         return self._set(load().he_conv2d, self.h, x.h, c_in, gap, _ptr(W, P_D), None if b is None else _ptr(b, P_D),
                          c_out, k, stride)
 
+    def encrypt_conv_weights(self, K, limbs: Optional[int] = None, ct_id_base: int = 0) -> CtSet:
+        K = _f64(K)
+        c_out, c_in, k, _ = K.shape
+        return self._set(load().he_encrypt_conv_weights, self.h, _ptr(K, P_D), c_out, c_in, k,
+                         self.L1 if limbs is None else limbs, ct_id_base)
+
+    def conv2d_enc(self, x: CtSet, c_in: int, gap: int, Wct: CtSet, bias, c_out: int, k: int, stride: int) -> CtSet:
+        b = None if bias is None else _f64(bias)
+        return self._set(load().he_conv2d_enc, self.h, x.h, c_in, gap, Wct.h, None if b is None else _ptr(b, P_D),
+                         c_out, k, stride)
+
     def poly_act(self, x: CtSet, coeffs: Sequence[float]):
         c = _f64(coeffs)
         check(load().he_poly_act(self.h, x.h, _ptr(c, P_D), len(coeffs) - 1))

@@ -242,6 +242,29 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
   });
 }
 
+int he_encrypt_conv_weights(he_ctx* ctx, const double* W, int c_out, int c_in, int k, int limbs, uint64_t ct_id_base,
+                            he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && W && out, HE_E_ARG, "null argument");
+    REQUIRE(c_out >= 1 && c_in >= 1 && k >= 1, HE_E_ARG, "bad kernel shape");
+    Ctx& C = ctx->c;
+    REQUIRE(limbs >= 2 && limbs <= C.L1, HE_E_LEVEL, "bad level");
+    const size_t nw = (size_t)c_out * c_in * k * k;
+    const double ql = (double)C.q[limbs - 1];
+    std::vector<int64_t> m(nw * C.N, 0);
+    for (size_t t = 0; t < nw; t++) m[t * C.N] = std::llround(W[t] * ql);  // the constant K q_l
+    *out = wrap(encrypt_coeffs(C, m.data(), (int)nw, limbs, ql, ct_id_base));
+  });
+}
+
+int he_conv2d_enc(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const he_ctset* weights, const double* bias,
+                  int c_out, int k, int stride, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && weights && out, HE_E_ARG, "null argument");
+    *out = wrap(conv2d_enc(ctx->c, *in->s, c_in, gap, *weights->s, bias, c_out, k, stride));
+  });
+}
+
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) {
   return guard([&] {
     REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");

@@ -401,6 +401,44 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
   return out;
 }
 
+// Convolution with encrypted kernels (the model provider's kernel ciphertexts,
+// Sec. V; Kernelspanner's role, Sec. III-C, in the column layout): Wct[o][c][a][b]
+// encrypts the constant K[o][c][a][b] at scale q_l, l the input level. Output (o, j')
+// is sum_{c,b,a} Wct[o][c][a][b] (x) Rot(X_{c, s j' + b}, g a) as three components,
+// rescaled (scale q_l D / q_l = D), relinearised, plus round(bias_o D). The rotations
+// are hoisted per input column as in conv2d; the work budget is not applied.
+std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in_any, int c_in, int gap, const CtSet& Wct_any,
+                                  const double* bias, int c_out, int k, int stride) {
+  std::unique_ptr<CtSet> hold, holdw;
+  const CtSet& in = two_comp(C, in_any, hold);
+  const CtSet& Wct = two_comp(C, Wct_any, holdw);
+  if (c_in < 1 || c_out < 1 || k < 1 || stride < 1 || gap < 1) throw Error(1, "bad convolution shape");
+  if (in.n % c_in) throw Error(1, "input set size is not a multiple of c_in");
+  if (Wct.n != c_out * c_in * k * k) throw Error(1, "expected c_out c_in k k kernel ciphertexts");
+  if (Wct.limbs != in.limbs) throw Error(4, "kernels and input at different levels");
+  const int w_in = in.n / c_in;
+  if (w_in < k) throw Error(1, "image narrower than the kernel");
+  const int w_out = (w_in - k) / stride + 1;
+  const int lp = in.limbs;
+  if (lp < 2) throw Error(2, "no level left for the convolution");
+  std::vector<long> steps(k);
+  for (int a = 0; a < k; a++) steps[a] = (long)gap * a;
+  for (long s : steps)
+    if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
+  auto rot = rotate(C, in, steps);  // [c][j][a]
+  auto out = new_set(C, c_out * w_out, 3, lp, in.scale * Wct.scale);
+  k_conv_enc_mac(C, rot->buf.p, Wct.buf.p, out->buf.p, c_in, w_in, k, stride, c_out, w_out, lp);
+  rot.reset();
+  rescale_inplace(C, *out);
+  relinearize(C, *out);
+  out->scale = in.scale;  // the kernels were encrypted at scale q_l, which the rescale removes
+  if (bias) {
+    DevBuf cb = const_table(C, bias, c_out, lp - 1, out->scale);
+    k_add_const(C, out->buf.p, out->n, lp - 1, cb.p, w_out);
+  }
+  return out;
+}
+
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, int p) {
   std::unique_ptr<CtSet> ha, hb;
   const CtSet& A = two_comp(C, A_any, ha);

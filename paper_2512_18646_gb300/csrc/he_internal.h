@@ -212,8 +212,12 @@ void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limb
 // conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs);
-// matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx])
-void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs);
+// conv MAC with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a} tensor(W[o][c][a][b], R[c][s j' + b][a])
+void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_in, int w_in, int k, int stride,
+                    int c_out, int w_out, int limbs);
+// matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx]), idx < p; R holds rstride (default p)
+// ciphertexts per k
+void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs, int rstride = 0);
 // zero-rotation matmul accumulate: d[g] = sum_k tensor(Ahat[g][k], B[k]), g < G
 void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
@@ -258,7 +262,12 @@ std::unique_ptr<CtSet> relinearized(Ctx& C, const CtSet& s);
 void rescale_inplace(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);
+// convolution with encrypted kernels Wct [c_out][c_in][k][k] (constants at scale q_{limbs-1})
+std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in, int c_in, int gap, const CtSet& Wct, const double* bias,
+                                  int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// baby-step giant-step revolver with baby-step size g: D [p] as matmul's
+std::unique_ptr<CtSet> matmul_bsgs(Ctx& C, const CtSet& A, const CtSet& B, int p, int g);
 // zero-rotation matmul: Ahat [G][n] (group-major volley encoding of A), B [n] -> D [G]
 std::unique_ptr<CtSet> matmul_volley(Ctx& C, const CtSet& Ahat, const CtSet& B);
 // block stride M, positions per ciphertext and groups of the volley layout (throws on misfit)

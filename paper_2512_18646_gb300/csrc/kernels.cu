@@ -418,9 +418,84 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
     conv_mac_body<OB, TN, false>(sw, rot, out, c_in, w_in, k, stride, c_out, w_out, LN, off, q, one_sh);
 }
 
-// d[idx] (3 components) = sum_k tensor(A_k, R[k][idx]); R [n][p][2][limbs][N]
-__global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, int p, int limbs, const PrimeTab* pt,
-                                    int log_n) {
+// Convolution with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a}
+// tensor(W[o][c][a][b], R[c][s j' + b][a]); W [c_out][c_in][k][k][2][limbs][N]
+// kernel ciphertexts, R [c_in][w_in][k][2][limbs][N] the hoisted rotations, out
+// [c_out][w_out][3][limbs][N]. A thread owns one word position (limb,
+// coefficient) and a tile of CO output channels x CJ output columns (blockIdx.y
+// enumerates the tiles), so each kernel word is read once per CJ columns and
+// each rotated input word once per CO channels. 128-bit sums, reduced every 8
+// terms.
+template <int CO, int CJ>
+__global__ void __launch_bounds__(128) k_conv_enc_mac_kernel(const u64* R, const u64* W, u64* out, int c_in, int w_in, int k, int stride,
+                                      int c_out, int w_out, int limbs, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const int tj = (w_out + CJ - 1) / CJ;
+  const int o0 = (blockIdx.y / tj) * CO, j0 = (blockIdx.y % tj) * CJ;
+  HE_GRID_LOOP(w, LN) {
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    Acc128 acc[CO][CJ][3];
+#pragma unroll
+    for (int t = 0; t < CO; t++)
+#pragma unroll
+      for (int u = 0; u < CJ; u++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) acc[t][u][d] = Acc128{0, 0};
+    int terms = 0;
+    for (int c = 0; c < c_in; c++)
+      for (int b = 0; b < k; b++)
+        for (int a = 0; a < k; a++) {
+          u64 w0[CO], w1[CO], r0[CJ], r1[CJ];
+#pragma unroll
+          for (int t = 0; t < CO; t++) {
+            const int o = o0 + t < c_out ? o0 + t : c_out - 1;
+            const u64* wp = W + ((((size_t)o * c_in + c) * k + a) * k + b) * 2 * LN + w;
+            w0[t] = wp[0];
+            w1[t] = wp[LN];
+          }
+#pragma unroll
+          for (int u = 0; u < CJ; u++) {
+            const int jp = j0 + u < w_out ? j0 + u : w_out - 1;
+            const u64* rp = R + (((size_t)(c * w_in + stride * jp + b) * k + a) * 2) * LN + w;
+            r0[u] = rp[0];
+            r1[u] = rp[LN];
+          }
+#pragma unroll
+          for (int t = 0; t < CO; t++)
+#pragma unroll
+            for (int u = 0; u < CJ; u++) {
+              mac128(acc[t][u][0], w0[t], r0[u]);
+              mac128(acc[t][u][1], w0[t], r1[u]);
+              mac128(acc[t][u][1], w1[t], r0[u]);
+              mac128(acc[t][u][2], w1[t], r1[u]);
+            }
+          if ((++terms & 7) == 0) {
+#pragma unroll
+            for (int t = 0; t < CO; t++)
+#pragma unroll
+              for (int u = 0; u < CJ; u++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) acc[t][u][d] = Acc128{0, reduce128(acc[t][u][d].hi, acc[t][u][d].lo, md)};
+          }
+        }
+#pragma unroll
+    for (int t = 0; t < CO; t++)
+#pragma unroll
+      for (int u = 0; u < CJ; u++) {
+        if (o0 + t < c_out && j0 + u < w_out) {
+          u64* dst = out + ((size_t)(o0 + t) * w_out + j0 + u) * 3 * LN + w;
+#pragma unroll
+          for (int d = 0; d < 3; d++) dst[(size_t)d * LN] = reduce128(acc[t][u][d].hi, acc[t][u][d].lo, md);
+        }
+      }
+  }
+}
+
+// d[idx] (3 components) = sum_k tensor(A_k, R[k][idx]), idx < p; R [n][rstride][2][limbs][N]
+__global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, int p, int rstride, int limbs,
+                                    const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
   const size_t total = (size_t)p * LN;
@@ -432,7 +507,7 @@ __global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, i
     Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
     for (int kk = 0; kk < n; kk++) {
       const u64* a = A + (size_t)kk * 2 * LN + w;
-      const u64* rr = R + ((size_t)kk * p + id) * 2 * LN + w;
+      const u64* rr = R + ((size_t)kk * rstride + id) * 2 * LN + w;
       const u64 a0 = a[0], a1 = a[LN], r0 = rr[0], r1 = rr[LN];
       mac128(s0, a0, r0);
       mac128(s1, a0, r1);
@@ -755,9 +830,25 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }
-void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs) {
+void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_in, int w_in, int k, int stride,
+                    int c_out, int w_out, int limbs) {
+  constexpr int CO = 2, CJ = 2;
+  const size_t LN = (size_t)limbs * C.N;
+  const unsigned tiles = (unsigned)(((c_out + CO - 1) / CO) * ((w_out + CJ - 1) / CJ));
+  constexpr int TH = 128;  // ~160 registers a thread: small blocks keep three per SM
+  const unsigned gx = (unsigned)((LN + TH - 1) / TH);
+  const double T = (double)c_in * k * k;
+  const double bytes = 8.0 * (double)LN * (2.0 * c_out * T + 2.0 * c_in * (stride * (w_out - 1) + k) * k +
+                                           3.0 * c_out * w_out);
+  void* tok = prof_begin("k_conv_enc_mac_kernel", C.stream, bytes, 4.0 * (double)LN * c_out * w_out * T);
+  k_conv_enc_mac_kernel<CO, CJ><<<dim3(gx, tiles), TH, 0, C.stream>>>(rot, W, out, c_in, w_in, k, stride, c_out,
+                                                                          w_out, limbs, C.dev_ptab(), C.log_n);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
+}
+void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs, int rstride) {
   HE_LAUNCH_P(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p),
-              4.0 * C.N * limbs * n * p, A, R, d, n, p, limbs, C.dev_ptab(), C.log_n);
+              4.0 * C.N * limbs * n * p, A, R, d, n, p, rstride > 0 ? rstride : p, limbs, C.dev_ptab(), C.log_n);
 }
 void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs) {
   HE_LAUNCH_P(k_volley_acc_kernel, (size_t)G * limbs * C.N,

@@ -96,3 +96,68 @@ def test_cnn_n16_128x128(lib):
     logits = layouts.logits_from_fc(g.decrypt_slots(z), B, H)
     ref = fp64_ref.cnn(imgs, w)
     assert np.abs(logits - ref).max() < 1e-4
+
+
+def test_conv_layer_encrypted_kernels_n15_64x64(lib):
+    """The conv layer with the model provider's encrypted kernels at N = 2^15: sampled output columns bit
+    for bit against the oracle (same kernel plaintexts and seeds), the whole layer against FP64."""
+    from paper_2512_18646_gb300 import api
+    pre = synthetic.CONV_LAYER
+    o = Oracle.from_preset(pre, seed=203)
+    g = api.Context.from_preset(pre, seed=203)
+    o.keygen([1, 2])
+    g.keygen([1, 2])
+    img = synthetic.images(1, 64, 64, seed=201)
+    K, bias = synthetic.conv_weights(4, 1, 3, 0.1, seed=202)
+    H = 64
+    m = _columns(o, img, H)
+    gx = g.encrypt_coeffs(m, o.L1, o.scale, 0)
+    gw = g.encrypt_conv_weights(K, o.L1, 9000)
+    gy = g.conv2d_enc(gx, 1, 1, gw, bias, 4, 3, 1)
+    got = gy.export().reshape(4, 62, 2, o.L1 - 1, o.N)
+    cols = [0, 1, 2, 61, 62, 63]
+    X = np.zeros((1, 64, 2, o.L1, o.N), np.uint64)
+    for j in cols:
+        X[0, j] = o.encrypt(m[j], o.L1, j)
+    mw = o.conv_weight_plaintexts(K, o.L1)
+    ow = np.stack([o.encrypt(mw[i], o.L1, 9000 + i) for i in range(len(mw))])
+    sel = [(c, jp) for c in range(4) for jp in (0, 61)]
+    oy = o.conv2d_enc(X, 1, ow, bias, 4, 3, 1, o.scale, sel=sel)
+    for t, (c, jp) in enumerate(sel):
+        assert np.array_equal(got[c, jp], oy[t]), (c, jp)
+    ref = fp64_ref.conv2d(img[:, None], K, bias, 1)
+    dec = g.decrypt_image(gy, 1, H, 1, 62)[0].reshape(4, 62, 62)
+    assert np.abs(dec.transpose(0, 2, 1) - ref[0]).max() < 1e-4
+
+
+def test_matmul_volley_and_act3_n16(lib):
+    """At the CNN parameters (N = 2^16, 13 limbs): a zero-rotation matmul of the batched workload's
+    largest shape class (m = p = 256, three groups) bit for bit against the oracle and within 1e-4 of
+    FP64, then Table I's ACT-1 on its outputs bit for bit."""
+    from paper_2512_18646_gb300 import api
+    from tests.test_oracle_pins import act_polynomials
+    pre = synthetic.CNN_N16
+    o = Oracle.from_preset(pre, seed=411)
+    g = api.Context.from_preset(pre, seed=411)
+    o.keygen([])
+    g.keygen([])
+    m_, n_, p_ = 256, 8, 256
+    A, Bm = synthetic.matmul_operands(m_, n_, p_, seed=412)
+    M, per, G, _ = layouts.volley_geometry(o.slots, m_, p_)
+    assert G == 3
+    ma = np.stack([o.encode(v) for v in layouts.matrix_a_volley(A, o.slots, p_).reshape(G * n_, o.slots)])
+    mb = np.stack([o.encode(v) for v in layouts.matrix_b_rows(Bm, o.slots)])
+    ga = g.encrypt_coeffs(ma, o.L1, o.scale, 0)
+    gb = g.encrypt_coeffs(mb, o.L1, o.scale, 100)
+    oa = np.stack([o.encrypt(ma[i], o.L1, i) for i in range(len(ma))]).reshape(G, n_, 2, o.L1, o.N)
+    ob = np.stack([o.encrypt(mb[i], o.L1, 100 + i) for i in range(n_)])
+    gd = g.matmul_volley(ga, gb)
+    od = o.matmul_volley(oa, ob)
+    assert np.array_equal(gd.export(), od)
+    assert np.abs(g.decrypt_matrix_volley(gd, m_, p_) - A @ Bm).max() < 1e-4
+    sd = o.scale * o.scale / o.q[o.L1 - 1]
+    assert gd.scale == sd
+    c = act_polynomials()["ACT-1"]
+    gy = g.poly_act(gd, c)
+    oy, sy = o.poly_act3(od, c, sd)
+    assert np.array_equal(gy.export(), oy) and gy.scale == sy

@@ -213,6 +213,32 @@ def test_conv2d_matches_oracle_and_fp64(lib, stride, c_in, k, side):
     assert np.abs(got - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("stride,c_in,k", [(1, 1, 3), (2, 3, 3), (2, 2, 5)])
+def test_conv2d_encrypted_kernels_matches_oracle_and_fp64(lib, stride, c_in, k):
+    """Encrypted kernels (the model provider's ciphertexts): bit-exact with the oracle from the same
+    kernel plaintexts and seeds, decrypting to the FP64 convolution; the library's own kernel
+    encryption (he_encrypt_conv_weights) encodes the same integers, so it is bit-exact too."""
+    H, side, c_out = 16, 11, 3
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=17, steps=list(range(1, k)))
+    rng = np.random.default_rng(30 + stride * 10 + c_in)
+    imgs = rng.uniform(0, 1, (3, c_in, side, side - 1))
+    K = rng.normal(0, 0.3, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.3, c_out)
+    ox, gx = image_columns_both(o, g, imgs, H, ct_id_base=1000)
+    lp = o.L1
+    m = o.conv_weight_plaintexts(K, lp)
+    ow, gw = encrypt_both(o, g, m, ct_id_base=7000, scale=float(o.q[lp - 1]))
+    gy = g.conv2d_enc(gx, c_in, 1, gw, bias, c_out, k, stride)
+    oy = o.conv2d_enc(ox, 1, ow, bias, c_out, k, stride, o.scale)
+    assert np.array_equal(gy.export(), oy)
+    gw2 = g.encrypt_conv_weights(K, lp, 7000)
+    assert np.array_equal(gw2.export(), ow)
+    ref = fp64_ref.conv2d(imgs, K, bias, stride)
+    got = g.decrypt_image(gy, 3, H, stride, ref.shape[2])
+    got = got.reshape(3, c_out, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
+    assert np.abs(got - ref).max() < 1e-5
+
+
 def _act_polynomials():
     from tests.test_oracle_pins import act_polynomials
     return act_polynomials()

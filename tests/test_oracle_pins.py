@@ -525,6 +525,28 @@ def test_poly_act3_dropped_term_is_caught():
     assert np.abs(got - (c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3)).max() > 1e-2
 
 
+@pytest.mark.parametrize("m,n,p,g", [(5, 3, 8, 4), (6, 2, 8, 3), (4, 4, 4, 1), (3, 2, 4, 4)])
+def test_matmul_bsgs_matches_fp64_with_fewer_rotations(m, n, p, g):
+    """Baby-step giant-step revolver: decrypts to A @ B and to the revolver's diagonals, with
+    n(g-1) + n(ceil(p/g)-1) + (p - g) rotations (all outputs rotated back but the first g)."""
+    o = Oracle(8, (60, 40, 40), 1, 60, 1, 40.0, seed=6)
+    S = o.slots
+    ng = -(-p // g)
+    o.keygen(sorted(set(list(range(1, p)) + [S - g * i for i in range(1, ng)])))
+    rng = np.random.default_rng(m * 10 + p + g)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    Ac = np.stack([o.encrypt(o.encode(v), ct_id=i) for i, v in enumerate(layouts.matrix_a_columns(A, S))])
+    Bc = np.stack([o.encrypt(o.encode(v), ct_id=50 + i) for i, v in enumerate(layouts.matrix_b_rows(Bm, S))])
+    o.reset_counters()
+    D = o.matmul_bsgs(Ac, Bc, p, g)
+    c = o.counters()
+    assert c["rotations"] == n * (g - 1) + n * (ng - 1) + (p - min(g, p))
+    assert c["tensors"] == n * p and c["relins"] == p
+    sc = o.scale ** 2 / o.q[-1]
+    C = layouts.matmul_from_diagonals(np.stack([o.decrypt(d, sc) for d in D]), m, p)
+    assert np.abs(C - A @ Bm).max() < 1e-6
+
+
 def encrypt_images(o, imgs, H, limbs=None, base_id=0):
     """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
     Bn, C, h, w = imgs.shape
@@ -563,6 +585,40 @@ def test_conv2d_matches_fp64_and_schedules_agree(stride, c_in):
     got2 = np.moveaxis(layouts.image_from_columns(z2, 3, H, stride, ref.shape[2]), 0, 1)
     assert np.abs(got2 - got).max() < 1e-6
     assert not np.array_equal(Y, Y2)  # different key switches, same decryption
+
+
+@pytest.mark.parametrize("stride,c_in", [(1, 1), (2, 2)])
+def test_conv2d_encrypted_kernels_matches_fp64(stride, c_in):
+    """Convolution with encrypted kernels (the model provider's role, Sec. V): kernel ciphertexts
+    encrypt the constant K at scale q_l; decrypts to the FP64 convolution and to the plaintext-weight
+    schedule; c_out w' c_in k^2 tensor products, one relinearisation per output."""
+    o = Oracle(8, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=24)
+    k, c_out, H = 3, 2, 16
+    o.keygen([1, 2])
+    rng = np.random.default_rng(10 + stride)
+    imgs = rng.uniform(0, 1, (3, c_in, 9, 8))
+    K = rng.normal(0, 0.3, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.3, c_out)
+    X = encrypt_images(o, imgs, H)
+    lp = o.L1
+    m = o.conv_weight_plaintexts(K, lp)
+    assert m.shape == (K.size, o.N) and not m[:, 1:].any()
+    Wct = np.stack([o.encrypt(m[i], lp, 5000 + i) for i in range(len(m))])
+    # each kernel ciphertext holds K at every slot
+    assert np.abs(o.decrypt(Wct[1], float(o.q[lp - 1])) - K.reshape(-1)[1]).max() < 1e-6
+    o.reset_counters()
+    Y = o.conv2d_enc(X, 1, Wct, bias, c_out, k, stride, o.scale)
+    c = o.counters()
+    w_out = (8 - k) // stride + 1
+    assert c["tensors"] == c_out * w_out * c_in * k * k and c["relins"] == c_out * w_out
+    assert c["rescales"] == c_out * w_out and c["ct_scalar"] == 0
+    ref = fp64_ref.conv2d(imgs, K, bias, stride)
+    z = np.stack([o.decrypt(y) for y in Y]).reshape(c_out, w_out, o.slots)
+    got = np.moveaxis(layouts.image_from_columns(z, 3, H, stride, ref.shape[2]), 0, 1)
+    assert np.abs(got - ref).max() < 1e-6
+    Yp = o.conv2d(X, 1, K, bias, stride, o.scale)
+    zp = np.stack([o.decrypt(y) for y in Yp]).reshape(c_out, w_out, o.slots)
+    assert np.abs(zp - z).max() < 1e-6
 
 
 def test_cnn_small_matches_fp64():
