@@ -317,10 +317,11 @@ def run_matmul(args, rank, world, local_rank):
     """64 independent encrypted matmuls at the CNN parameters (top level, 13 limbs).
 
     Operands are encrypted (untimed) in waves that fit device memory; each wave
-    is evaluated twice, once as 64-way-style batched launches (he_matmul_batched)
-    and once as one he_matmul call per product, both timed with CUDA events on
-    the context's stream, then a third time in the zero-rotation layout (A encrypted with
-    he_encrypt_matrix_a_volley, one he_matmul_volley per product).
+    is evaluated as 64-way-style batched launches (he_matmul_batched), as one
+    he_matmul call per product, as one baby-step giant-step he_matmul_bsgs call per
+    product, all timed with CUDA events on the context's stream, and in the
+    zero-rotation layout (A encrypted with he_encrypt_matrix_a_volley, one
+    he_matmul_volley per product).
     value = products / total zero-rotation time; the revolver figures are reported beside it."""
     import torch
     import __graft_entry__
@@ -335,7 +336,15 @@ def run_matmul(args, rank, world, local_rank):
     if args.count:
         shapes = shapes[: args.count]
     t0 = time.perf_counter()
-    g.keygen(list(range(1, max(p for _, _, p in shapes))))
+    S = (1 << pre.log_n) // 2
+    bsgs_steps = set()
+    for _, _, p in shapes:
+        gb_ = 1
+        while 4 * gb_ * gb_ <= 2 * p:
+            gb_ *= 2
+        gb_ = min(gb_, p)
+        bsgs_steps |= {S - gb_ * i for i in range(1, -(-p // gb_))}
+    g.keygen(sorted(set(range(1, max(p for _, _, p in shapes))) | bsgs_steps))
     g.synchronize()
     keygen_s = time.perf_counter() - t0
     ct_bytes = 2 * len(pre.q_bits) * g.N * 8
@@ -366,7 +375,7 @@ def run_matmul(args, rank, world, local_rank):
     g.matmul(wa, wb, 4, 4)
     g.matmul_batched([wa], [wb], [4], [4])
     g.matmul_volley(g.encrypt_matrix_a_volley(np.ones((4, 4)), 4, 0), wb)
-    t_batched = t_plain = t_volley = 0.0
+    t_batched = t_plain = t_volley = t_bsgs = 0.0
     launches_b = launches_v = 0
     max_err = max_err_v = 0.0
     rng_seed = 402
@@ -396,6 +405,14 @@ def run_matmul(args, rank, world, local_rank):
             return None
         _, dt = timed(plain)
         t_plain += dt
+
+        def bsgs():
+            for t in range(len(wave)):
+                r = g.matmul_bsgs(As[t], Bs[t], ms[t], ps[t])
+                del r
+            return None
+        _, dt = timed(bsgs)
+        t_bsgs += dt
         del As
         # the zero-rotation form: A in the volley layout (G groups of n ciphertexts), same B
         Vs = []
@@ -425,6 +442,7 @@ def run_matmul(args, rank, world, local_rank):
     return {"value": total * world / t_v, "ms_per_step": 1e3 * t_v, "launches": launches_v, "max_abs_err": max_err_v,
             "revolver_batched_value": total * world / t_b, "revolver_batched_ms": 1e3 * t_b,
             "revolver_plain_value": total * world / t_p, "revolver_plain_ms": 1e3 * t_p,
+            "bsgs_value": total * world / max_over_ranks(t_bsgs, world), "bsgs_ms": 1e3 * max_over_ranks(t_bsgs, world),
             "revolver_launches": launches_b, "revolver_max_abs_err": max_err, "keygen_s": keygen_s,
             "waves": len(waves), "revolver_rotations": rot, "revolver_tensors": sum(n * p for _, n, p in shapes),
             "volley_tensors": sum(G * n for G, (_, n, _) in zip(groups, shapes)), "volley_rotations": 0}
@@ -650,6 +668,7 @@ def main():
                     "revolver": {"batched_value": res["revolver_batched_value"],
                                  "batched_ms": res["revolver_batched_ms"],
                                  "plain_value": res["revolver_plain_value"], "plain_ms": res["revolver_plain_ms"],
+                                 "bsgs_value": res["bsgs_value"], "bsgs_ms": res["bsgs_ms"],
                                  "gpu_launches": res["revolver_launches"],
                                  "max_abs_err_vs_fp64": res["revolver_max_abs_err"],
                                  "rotations": res["revolver_rotations"],

@@ -54,6 +54,7 @@ extern "C" {
 typedef struct he_ctx he_ctx;       /* parameters, NTT tables, keys, stream      */
 typedef struct he_ctset he_ctset;   /* n ciphertexts at one level and scale      */
 typedef struct he_ptset he_ptset;   /* encoded plaintexts prepared on the device */
+typedef struct he_graph he_graph;   /* a captured sequence of library calls       */
 
 /*
  * Scheme parameters. Primes: the n_special primes of P take the largest
@@ -177,6 +178,18 @@ int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double
 int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C);
 
 /*
+ * he_matmul_bsgs: he_matmul's result (same operands, same p diagonal
+ * ciphertexts, decoded by he_decrypt_matrix) with the rotations of Alg. 3 split
+ * into baby and giant steps: idx = g i + j, j < g, and
+ * D_{g i + j} = Rot(sum_k Rot(A_k, -g i) (x) Rot(B~_k, j), g i), which needs
+ * n(g-1) + n(ceil(p/g)-1) + (p - g) rotations instead of n(p-1). g <= 0 picks
+ * the power of two nearest sqrt(p). Needs rotation keys for steps 1..g-1,
+ * N/2 - g i and g i (i = 1..ceil(p/g)-1), and m + p - 1 <= N/2.
+ * Errors: HE_E_ARG, HE_E_SCALE, HE_E_LEVEL, HE_E_NOKEY.
+ */
+int he_matmul_bsgs(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int g, he_ctset** C);
+
+/*
  * he_matmul_volley: encrypted C = A B without rotations. A from
  * he_encrypt_matrix_a_volley (groups * n ciphertexts), B from
  * he_encrypt_matrix_b (n ciphertexts), same level and scale. Result: `groups`
@@ -209,6 +222,23 @@ int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he
  */
 int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* weights, const double* bias,
               int c_out, int k, int stride, he_ctset** out);
+
+/*
+ * he_reform: ReForm (Sec. IV-C) in the column layout. After a strided layer
+ * row i of image block b sits at slot b * block_stride + gap * i; ReForm moves
+ * it to b * block_stride + i (row gap 1), every other slot becoming 0:
+ * out = rescale(sum_{i < h_valid} mask_i (x) Rot(X, (gap - 1) i)), mask_i the
+ * 0/1 plaintext of slots b * block_stride + i encoded at scale q_l. h_valid - 1
+ * rotations per ciphertext (one hoisted ModUp), one level, scale unchanged.
+ * Needs rotation keys for steps (gap - 1) i, i = 1..h_valid-1. Errors:
+ * HE_E_ARG (shape), HE_E_LEVEL, HE_E_NOKEY.
+ */
+int he_reform(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, int block_stride, he_ctset** out);
+
+/* he_reform_coeffs: he_reform with the masks given as encoded integer
+ * plaintexts masks [h_valid][N] (signed coefficients at scale q_l), so two
+ * implementations can start from the same plaintexts. */
+int he_reform_coeffs(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, const int64_t* masks, he_ctset** out);
 
 /*
  * he_encrypt_conv_weights: the model provider's kernel ciphertexts (Sec. V:
@@ -437,6 +467,38 @@ int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const h
  * result set (10 ciphertexts; decrypt with he_decrypt_slots). Decrypted
  * results are the same alone and in any mix, up to CKKS noise.
  */
+/* ---- CUDA graphs of library calls (no counterpart in the paper) ----
+ *
+ * he_graph_begin starts capturing the calls made on ctx's stream (which must
+ * be a non-default stream) into a CUDA graph; he_graph_end stops, instantiates
+ * it and returns the graph; he_graph_launch replays it on ctx's stream. A
+ * replay reads the current contents of the sets made before the capture and
+ * rewrites the sets made during it: their handles stay valid and hold the
+ * results of the latest replay once the stream has reached it (the graph's
+ * memory is re-allocated at the same addresses on each replay). Inside a
+ * capture:
+ *  - calls that only read their input sets and return new sets (products,
+ *    rotations, matmuls, dense layers, ...) are captured;
+ *  - in-place calls (he_rescale, he_relinearize, he_poly_act) and
+ *    he_ctset_assign into sets made before the capture return HE_E_STATE;
+ *  - calls that upload host data (encryption, convolution weights, biases,
+ *    plaintext preparation) cannot be captured: the capture fails and
+ *    he_graph_end returns HE_E_CUDA;
+ *  - he_ctset_free of a set made before the capture is deferred to he_graph_end.
+ * Free the sets made during a capture after the graph's last replay. Kernel
+ * launches of a replay are added to he_kernel_launches.
+ */
+int he_graph_begin(he_ctx* ctx);
+int he_graph_end(he_ctx* ctx, he_graph** out);
+int he_graph_launch(he_graph* g);
+/* number of kernel nodes in the graph */
+int he_graph_info(const he_graph* g, uint64_t* kernel_nodes);
+void he_graph_destroy(he_graph* g);
+
+/* Copy src's ciphertexts into dst (same count, components and level; device to
+ * device on ctx's stream): new inputs for a graph's next replay. */
+int he_ctset_assign(he_ctx* ctx, he_ctset* dst, const he_ctset* src);
+
 typedef struct he_server he_server;
 
 #define HE_REQ_WAITING 0   /* in host memory, not admitted yet  */

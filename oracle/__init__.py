@@ -70,6 +70,8 @@ def _lib():
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
             "oc_matmul_volley": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_reform": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _i64p, _u64p]),
             "oc_matmul_bsgs": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               _u64p]),
             "oc_conv2d_enc": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -316,6 +318,25 @@ class Oracle:
         n, _, lp, _ = A.shape
         out = np.zeros((p, 2, lp - 1, self.N), np.uint64)
         _check(self.lib.oc_matmul_bsgs(self.h, _p(A, _u64p), _p(B, _u64p), n, p, g, lp, _p(out, _u64p)))
+        return out
+
+    def reform_masks(self, h: int, H: int, lp: int) -> np.ndarray:
+        """ReForm's plaintexts: mask_i (1 at slots b H + i of every block, else 0) encoded at
+        scale q_{lp-1} -> [h][N] int64."""
+        out = np.zeros((h, self.N), np.int64)
+        for i in range(h):
+            z = np.zeros(self.slots)
+            z[i::H] = 1.0
+            out[i] = self.encode(z, float(self.q[lp - 1]))
+        return out
+
+    def reform(self, X, gap: int, h: int, masks) -> np.ndarray:
+        """ReForm: X [n][2 or 3][lp][N] with rows at gap `gap` -> [n][2][lp-1][N] with rows at gap 1."""
+        X = _u64(X)
+        n, polys, lp, _ = X.shape
+        masks = np.ascontiguousarray(masks, dtype=np.int64)
+        out = np.zeros((n, 2, lp - 1, self.N), np.uint64)
+        _check(self.lib.oc_reform(self.h, _p(X, _u64p), n, polys, lp, gap, h, _p(masks, _i64p), _p(out, _u64p)))
         return out
 
     def matmul_volley(self, Ahat, B) -> np.ndarray:

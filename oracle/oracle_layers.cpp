@@ -122,6 +122,27 @@ static std::vector<Ct> conv2d_enc(Ctx& C, const std::vector<std::vector<Ct>>& X,
   return out;
 }
 
+// ReForm (Sec. IV-C) in the column layout: after a strided layer row i of every
+// block sits at slot b H + g i; ReForm moves it to b H + i. A left rotation by
+// (g - 1) i brings slot b H + g i to b H + i, so
+//   out = rescale( sum_{i < h} mask_i (x) Rot(X, (g - 1) i) ),
+// mask_i the 0/1 plaintext of slots b H + i encoded at scale q_l (rotations
+// hoisted per ciphertext): O(h) rotations, products and additions, as the paper
+// counts for its own layout.
+static Ct reform(Ctx& C, const Ct& x_any, int gap, int h, const int64_t* masks) {
+  const Ct x = two_comp(C, x_any);
+  std::vector<long> steps(h);
+  for (int i = 0; i < h; i++) steps[i] = (long)(gap - 1) * i;
+  std::vector<Ct> r = ct_rotate_hoisted(C, x, steps);
+  Ct acc;
+  for (int i = 0; i < h; i++) {
+    std::vector<i64> m(masks + (size_t)i * C.N, masks + (size_t)(i + 1) * C.N);
+    Ct t = ct_mul_plain(C, r[i], m);
+    acc = i == 0 ? t : ct_add(C, acc, t);
+  }
+  return ct_rescale(C, acc);
+}
+
 // Baby-step giant-step form of the revolver: idx = g i + j (j < g). Since
 // rotation commutes with slotwise products and sums,
 //   D_{g i + j} = Rot( sum_k Rot(A_k, -g i) (x) Rot(B~_k, j), g i ):
@@ -376,6 +397,24 @@ int oc_conv2d_enc(void* h, const uint64_t* X, int polys, int lp, int c_in, int w
          }
          std::vector<Ct> r = conv2d_enc(*C, x, gap, w, bias, c_out, k, stride, scale, s);
          cts_to(*C, r, out));
+}
+
+// X [n][polys][lp][N] at row gap `gap`, masks [h][N] -> out [n][2][lp-1][N] at gap 1
+int oc_reform(void* h, const uint64_t* X, int n, int polys, int lp, int gap, int rows, const int64_t* masks,
+              uint64_t* out) {
+  try {
+    Ctx* C = (Ctx*)h;
+    if (gap < 2 || rows < 1) throw std::runtime_error("bad ReForm shape");
+    std::vector<Ct> x = cts_from(*C, X, n, lp, polys);
+    std::vector<Ct> r(n);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < n; t++) r[t] = reform(*C, x[t], gap, rows, masks);
+    cts_to(*C, r, out);
+    return 0;
+  } catch (const std::exception& e) {
+    g_lerr = e.what();
+    return -1;
+  }
 }
 
 // A, B [n][2][lp][N] -> D [p][2][lp-1][N], baby-step size g

@@ -69,7 +69,10 @@ SIGNATURES = {
     "he_matmul": (I, [V, V, V, I, I, PV]),
     "he_matmul_batched": (I, [V, I, PV, PV, P_I, P_I, PV]),
     "he_matmul_volley": (I, [V, V, V, PV]),
+    "he_matmul_bsgs": (I, [V, V, V, I, I, I, PV]),
     "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
+    "he_reform": (I, [V, V, I, I, I, PV]),
+    "he_reform_coeffs": (I, [V, V, I, I, P_I64, PV]),
     "he_encrypt_conv_weights": (I, [V, P_D, I, I, I, I, U64, PV]),
     "he_conv2d_enc": (I, [V, V, I, I, V, P_D, I, I, I, PV]),
     "he_poly_act": (I, [V, V, P_D, I]),
@@ -97,6 +100,12 @@ SIGNATURES = {
     "he_ctset_slice": (I, [V, V, I, I, PV]),
     "he_ctset_concat": (I, [V, PV, I, PV]),
     "he_ctset_free": (None, [V]),
+    "he_graph_begin": (I, [V]),
+    "he_graph_end": (I, [V, PV]),
+    "he_graph_launch": (I, [V]),
+    "he_graph_info": (I, [V, P_U64]),
+    "he_graph_destroy": (None, [V]),
+    "he_ctset_assign": (I, [V, V, V]),
     "he_rescale_noalloc": (I, [V, V, I, I, D, V, P_D]),
     "he_server_create": (I, [V, ctypes.POINTER(ServerDesc), PV]),
     "he_server_request_words": (I, [V, I, ctypes.POINTER(SZ)]),

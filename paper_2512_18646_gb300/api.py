@@ -109,6 +109,34 @@ class PtSet:
             pass
 
 
+class Graph:
+    """A captured sequence of library calls (he_graph_*); replay with launch()."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.h = ctypes.c_void_p(handle)
+
+    def launch(self):
+        check(load().he_graph_launch(self.h))
+
+    @property
+    def kernel_nodes(self) -> int:
+        n = ctypes.c_uint64()
+        check(load().he_graph_info(self.h, ctypes.byref(n)))
+        return n.value
+
+    def destroy(self):
+        if self.h:
+            load().he_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 class Context:
     """he_ctx: parameters, NTT tables and keys on the current CUDA device."""
 
@@ -176,6 +204,17 @@ class Context:
         A = _f64(A)
         return self._set(load().he_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)
 
+    def graph_begin(self):
+        check(load().he_graph_begin(self.h))
+
+    def graph_end(self) -> Graph:
+        out = ctypes.c_void_p()
+        check(load().he_graph_end(self.h, ctypes.byref(out)))
+        return Graph(self, out.value)
+
+    def assign(self, dst: CtSet, src: CtSet):
+        check(load().he_ctset_assign(self.h, dst.h, src.h))
+
     def encrypt_matrix_a_volley(self, A, p: int, ct_id_base: int = 0) -> CtSet:
         A = _f64(A)
         return self._set(load().he_encrypt_matrix_a_volley, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], p,
@@ -200,6 +239,9 @@ class Context:
     def matmul(self, A: CtSet, B: CtSet, m: int, p: int) -> CtSet:
         return self._set(load().he_matmul, self.h, A.h, B.h, m, p)
 
+    def matmul_bsgs(self, A: CtSet, B: CtSet, m: int, p: int, g: int = 0) -> CtSet:
+        return self._set(load().he_matmul_bsgs, self.h, A.h, B.h, m, p, g)
+
     def matmul_volley(self, A: CtSet, B: CtSet) -> CtSet:
         return self._set(load().he_matmul_volley, self.h, A.h, B.h)
 
@@ -219,6 +261,13 @@ class Context:
         b = None if bias is None else _f64(bias)
         return self._set(load().he_conv2d, self.h, x.h, c_in, gap, _ptr(W, P_D), None if b is None else _ptr(b, P_D),
                          c_out, k, stride)
+
+    def reform(self, x: CtSet, gap: int, h_valid: int, block_stride: int) -> CtSet:
+        return self._set(load().he_reform, self.h, x.h, gap, h_valid, block_stride)
+
+    def reform_coeffs(self, x: CtSet, gap: int, h_valid: int, masks) -> CtSet:
+        m = np.ascontiguousarray(masks, dtype=np.int64)
+        return self._set(load().he_reform_coeffs, self.h, x.h, gap, h_valid, _ptr(m, P_I64))
 
     def encrypt_conv_weights(self, K, limbs: Optional[int] = None, ct_id_base: int = 0) -> CtSet:
         K = _f64(K)

@@ -208,6 +208,21 @@ int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, h
   });
 }
 
+int he_matmul_bsgs(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int g, he_ctset** C_out) {
+  return guard([&] {
+    REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
+    REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
+    REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
+    REQUIRE(p >= 1 && (long)m + p - 1 <= (long)ctx->c.N / 2, HE_E_ARG, "m + p - 1 exceeds the slot count");
+    if (g <= 0) {  // the power of two nearest sqrt(p)
+      g = 1;
+      while ((long)4 * g * g <= (long)2 * p) g *= 2;
+      if (g > p) g = p;
+    }
+    *C_out = wrap(matmul_bsgs(ctx->c, *A->s, *B->s, p, g));
+  });
+}
+
 int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset** C_out) {
   return guard([&] {
     REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
@@ -268,6 +283,8 @@ int he_conv2d_enc(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const he_c
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) {
   return guard([&] {
     REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");
+    REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
+            "in-place operation on a set made before the capture");
     REQUIRE(degree == 2 || degree == 3, HE_E_UNIMPL, "degree 2 or 3 polynomials only");
     if (degree == 2 && coeffs[0] == 0.0 && coeffs[1] == 0.0 && coeffs[2] == 1.0) {
       inout->s = square(ctx->c, *inout->s);  // three components until an operation needs two
@@ -355,6 +372,40 @@ int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int
   return rc;
 }
 
+int he_reform_coeffs(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, const int64_t* masks, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && masks && out, HE_E_ARG, "null argument");
+    REQUIRE(gap >= 2 && h_valid >= 1, HE_E_ARG, "bad ReForm shape");
+    Ctx& C = ctx->c;
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 2, HE_E_LEVEL, "no level left for ReForm");
+    DevBuf m = fc_prepare(C, masks, 1, h_valid, lp);
+    *out = wrap(reform(C, *in->s, gap, h_valid, m.p));
+  });
+}
+
+int he_reform(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, int block_stride, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(gap >= 2 && h_valid >= 1 && pow2(block_stride) && block_stride <= S &&
+                (long)gap * (h_valid - 1) < block_stride,
+            HE_E_ARG, "rows do not fit the blocks");
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 2, HE_E_LEVEL, "no level left for ReForm");
+    const double ql = (double)C.q[lp - 1];
+    std::vector<int64_t> m((size_t)h_valid * C.N);
+    host_parallel((size_t)h_valid, [&](size_t i) {
+      std::vector<double> z(S, 0.0);
+      for (long b = 0; b < S / block_stride; b++) z[b * block_stride + (long)i] = 1.0;
+      encode_real(C, z.data(), (size_t)S, ql, m.data() + i * C.N);
+    });
+    DevBuf dm = fc_prepare(C, m.data(), 1, h_valid, lp);
+    *out = wrap(reform(C, *in->s, gap, h_valid, dm.p));
+  });
+}
+
 int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const he_ptset* masks, he_ctset** out) {
   return guard([&] {
     REQUIRE(ctx && sets && masks && out && n_sets >= 1, HE_E_ARG, "null argument");
@@ -391,6 +442,8 @@ int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
 int he_rescale(he_ctx* ctx, he_ctset* inout) {
   return guard([&] {
     REQUIRE(ctx && inout, HE_E_ARG, "null argument");
+    REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
+            "in-place operation on a set made before the capture");
     rescale_inplace(ctx->c, *inout->s);
   });
 }
@@ -510,6 +563,8 @@ int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int
 int he_relinearize(he_ctx* ctx, he_ctset* inout) {
   return guard([&] {
     REQUIRE(ctx && inout, HE_E_ARG, "null argument");
+    REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
+            "in-place operation on a set made before the capture");
     relinearize(ctx->c, *inout->s);
   });
 }
@@ -556,7 +611,103 @@ int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_cts
   });
 }
 
-void he_ctset_free(he_ctset* set) { delete set; }
+void he_ctset_free(he_ctset* set) {
+  if (!set) return;
+  Ctx* C = set->s ? set->s->ctx : nullptr;
+  if (C && C->capturing && set->s->gen != C->capture_gen) {
+    // made before the capture: its memory is not the graph's to free; release it after the capture
+    C->deferred.push_back(std::move(set->s));
+  }
+  delete set;
+}
+
+int he_graph_begin(he_ctx* ctx) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    REQUIRE(!C.capturing, HE_E_STATE, "a capture is already open on this context");
+    REQUIRE(C.stream != nullptr, HE_E_STATE, "graphs need a non-default context stream");
+    HE_CUDA(cudaStreamSynchronize(C.stream));
+    HE_CUDA(cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal));
+    C.capturing = true;
+    C.capture_gen++;
+  });
+}
+
+int he_graph_end(he_ctx* ctx, he_graph** out) {
+  return guard([&] {
+    REQUIRE(ctx && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    REQUIRE(C.capturing, HE_E_STATE, "no capture is open on this context");
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(C.stream, &g);
+    C.capturing = false;
+    C.deferred.clear();  // sets made before the capture and freed during it
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      throw Error(HE_E_CUDA, std::string("capture failed (a call inside it is not capturable): ") +
+                                 cudaGetErrorString(e));
+    }
+    auto* h = new he_graph;
+    h->ctx = ctx;
+    h->graph = g;
+    const cudaError_t ei = cudaGraphInstantiateWithFlags(&h->exec, g, cudaGraphInstantiateFlagAutoFreeOnLaunch);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      delete h;
+      throw Error(HE_E_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ei));
+    }
+    size_t nn = 0;
+    HE_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) HE_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      HE_CUDA(cudaGraphNodeGetType(nd, &t));
+      h->kernels += t == cudaGraphNodeTypeKernel;
+    }
+    *out = h;
+  });
+}
+
+int he_graph_launch(he_graph* g) {
+  return guard([&] {
+    REQUIRE(g && g->exec, HE_E_ARG, "null graph");
+    Ctx& C = g->ctx->c;
+    REQUIRE(!C.capturing, HE_E_STATE, "a capture is open on this context");
+    HE_CUDA(cudaGraphLaunch(g->exec, C.stream));
+    prof_add_launches(g->kernels);
+  });
+}
+
+int he_graph_info(const he_graph* g, uint64_t* kernel_nodes) {
+  return guard([&] {
+    REQUIRE(g && kernel_nodes, HE_E_ARG, "null argument");
+    *kernel_nodes = g->kernels;
+  });
+}
+
+void he_graph_destroy(he_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+int he_ctset_assign(he_ctx* ctx, he_ctset* dst, const he_ctset* src) {
+  return guard([&] {
+    REQUIRE(ctx && dst && src, HE_E_ARG, "null argument");
+    const CtSet& a = *src->s;
+    CtSet& b = *dst->s;
+    REQUIRE(a.n == b.n && a.polys == b.polys && a.limbs == b.limbs, HE_E_ARG, "sets of different shapes");
+    REQUIRE(!ctx->c.capturing || b.gen == ctx->c.capture_gen, HE_E_STATE,
+            "a set made before the capture cannot be overwritten inside it");
+    HE_CUDA(cudaMemcpyAsync(b.buf.p, a.buf.p, a.buf.words * 8, cudaMemcpyDeviceToDevice, ctx->c.stream));
+    b.scale = a.scale;
+  });
+}
 
 int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s) {
   return guard([&] {

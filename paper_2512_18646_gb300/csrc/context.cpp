@@ -334,6 +334,7 @@ std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale
   s->polys = polys;
   s->limbs = limbs;
   s->scale = scale;
+  s->gen = C.capturing ? C.capture_gen : 0;
   s->buf = DevBuf((size_t)n * polys * limbs * C.N, C.stream);
   return s;
 }

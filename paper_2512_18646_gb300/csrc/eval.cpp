@@ -472,6 +472,87 @@ std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, in
   return d;
 }
 
+// ReForm (Sec. IV-C) in the column layout: a strided layer leaves row i of every
+// block at slot b H + g i; a left rotation by (g - 1) i brings it to b H + i, so
+// out = rescale(sum_{i < h} mask_i (x) Rot(X, (g - 1) i)) with mask_i the 0/1
+// plaintext of slots b H + i at scale q_l: h - 1 hoisted rotations per
+// ciphertext, one masked multiply-accumulate launch (k_pack_blocks over the
+// rotation steps), one rescale. The scale is unchanged.
+std::unique_ptr<CtSet> reform(Ctx& C, const CtSet& in_any, int gap, int h, const u64* masks) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& in = two_comp(C, in_any, hold);
+  if (gap < 2 || h < 1) throw Error(1, "ReForm needs a row gap of at least 2 and at least one row");
+  if (in.limbs < 2) throw Error(2, "no level left for ReForm");
+  std::vector<long> steps(h);
+  for (int i = 0; i < h; i++) steps[i] = (long)(gap - 1) * i;
+  auto R = rotate(C, in, steps);  // [ct][i]
+  const size_t cw = in.ct_words();
+  std::vector<const u64*> xs(h);
+  for (int i = 0; i < h; i++) xs[i] = R->buf.p + (size_t)i * cw;
+  DevBuf dxs((size_t)h, C.stream);
+  // pageable source: the call returns once the pointers are staged
+  HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)h * 8, cudaMemcpyHostToDevice, C.stream));
+  auto out = new_set(C, in.n, 2, in.limbs, in.scale);
+  k_pack_blocks(C, (const u64* const*)dxs.p, masks, h, in.n, in.limbs, out->buf.p, (size_t)h * cw);
+  R.reset();
+  rescale_inplace(C, *out);
+  out->scale = in.scale;  // the masks were encoded at scale q_l
+  return out;
+}
+
+// Baby-step giant-step form of the revolver: idx = g i + j (j < g). Rotation
+// commutes with slotwise products and sums, so
+//   D_{g i + j} = Rot( sum_k Rot(A_k, -g i) (x) Rot(B~_k, j), g i ):
+// hoisted baby steps j < g of every B~_k, hoisted giant steps -g i of every A_k,
+// per giant step one accumulate launch over its g outputs, one rescale and
+// relinearisation of all p outputs, then a rotation by g i of the outputs of
+// giant step i >= 1: n(g-1) + n(ceil(p/g)-1) + (p - g) rotations instead of n(p-1).
+std::unique_ptr<CtSet> matmul_bsgs(Ctx& C, const CtSet& A_any, const CtSet& B_any, int p, int g) {
+  std::unique_ptr<CtSet> ha, hb;
+  const CtSet& A = two_comp(C, A_any, ha);
+  const CtSet& B = two_comp(C, B_any, hb);
+  if (A.n != B.n || A.n < 1) throw Error(1, "A and B must have the same number n of ciphertexts");
+  const long S = (long)C.N / 2;
+  if (p < 1 || S % p) throw Error(1, "p must divide the slot count");
+  if (g < 1 || g > p) throw Error(1, "baby-step size out of range");
+  if (A.limbs != B.limbs) throw Error(4, "operands at different levels");
+  if (A.limbs < 2) throw Error(2, "no level left for the product");
+  const int n = A.n, lp = A.limbs, ng = (p + g - 1) / g;
+  std::vector<long> baby(g), giant(ng);
+  for (int j = 0; j < g; j++) baby[j] = j;
+  for (int i = 0; i < ng; i++) giant[i] = i == 0 ? 0 : S - (long)g * i;
+  for (long st : baby) C.key(C.galois_elt(st));
+  for (int i = 1; i < ng; i++) {
+    C.key(C.galois_elt(giant[i]));
+    C.key(C.galois_elt((long)g * i));
+  }
+  const size_t cw = (size_t)2 * lp * C.N;
+  auto Rb = rotate(C, B, baby);   // [k][j]
+  auto Ra = rotate(C, A, giant);  // [k][i]
+  auto d = new_set(C, p, 3, lp, A.scale * B.scale);
+  {
+    DevBuf Ai((size_t)n * cw, C.stream);
+    for (int i = 0; i < ng; i++) {
+      const int cnt = std::min(g, p - g * i);
+      // the giant step i of every A_k, gathered into n consecutive ciphertexts
+      k_copy_limbs(C, Ra->buf.p + (size_t)i * cw, (size_t)ng * cw, Ai.p, cw, (size_t)n, 2 * lp);
+      k_matmul_acc(C, Ai.p, Rb->buf.p, d->ct(g * i), n, cnt, lp, g);
+    }
+  }
+  Ra.reset();
+  Rb.reset();
+  rescale_inplace(C, *d);
+  relinearize(C, *d);
+  for (int i = 1; i < ng; i++) {
+    const int cnt = std::min(g, p - g * i);
+    SetView v(*d, g * i, cnt);
+    auto r = rotate(C, v.s, {(long)g * i});
+    HE_CUDA(cudaMemcpyAsync(d->ct(g * i), r->buf.p, (size_t)cnt * d->ct_words() * 8, cudaMemcpyDeviceToDevice,
+                            C.stream));
+  }
+  return d;
+}
+
 // Zero-rotation form of the product. B~_k is tiled with period p, so its slot s
 // holds B[k][s mod p]; with A's column k copied to blocks t M + o_g (M = 1 mod p,
 // o_g = (g per) mod p) the slotwise product pairs A[i][k] with B[k][(i + g per + t)

@@ -39,6 +39,7 @@ void set_last_error(const std::string& msg);
 #define HE_CUDA(x) ::he::cuda_check((x), #x)
 
 struct Ctx;
+struct CtSet;
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on the
 // context stream; the pool keeps freed memory for reuse).
@@ -110,6 +111,13 @@ struct Ctx {
   // with the same per-ciphertext arithmetic
   size_t work_budget = 0;
 
+  // capture of library calls into a CUDA graph (he_graph_begin / he_graph_end): sets made during
+  // a capture carry its generation; sets made before it and freed during it are kept here and
+  // released after the capture ends (their memory is not the graph's to free)
+  bool capturing = false;
+  uint64_t capture_gen = 0;
+  std::vector<std::unique_ptr<CtSet>> deferred;
+
   // keys
   bool has_keys = false;
   DevBuf d_s;                 // secret [L1+K][N], NTT domain
@@ -128,6 +136,7 @@ struct CtSet {
   Ctx* ctx = nullptr;
   int n = 0, polys = 2, limbs = 0;
   double scale = 1.0;
+  uint64_t gen = 0;  // capture generation at creation (0: made outside any capture)
   DevBuf buf;
   size_t ct_words() const { return (size_t)polys * limbs * ctx->N; }
   u64* ct(int i) const { return buf.p + (size_t)i * ct_words(); }
@@ -139,6 +148,8 @@ struct CtSet {
 // reduction or accumulated for one)
 void* prof_begin(const char* name, cudaStream_t st, double bytes, double products = 0.0);
 void prof_end(void* tok, cudaStream_t st);
+// count n kernel launches made by replaying a graph
+void prof_add_launches(uint64_t n);
 
 // ---- kernel launchers (kernels.cu / ntt.cu) ----
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
@@ -223,7 +234,9 @@ void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int 
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
 // slot-block packing: out[j] = sum_t masks[t] * xs[t][j] ([n_ct][2][limbs][N]); xs is a device array of T pointers
-void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out);
+// (ct_stride: words between the ciphertexts of one set, 0 = contiguous)
+void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out,
+                   size_t ct_stride = 0);
 // data[p][i] *= R mod q (Montgomery form) for the primes of lm
 void k_mont_form(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
@@ -266,6 +279,9 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
 std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in, int c_in, int gap, const CtSet& Wct, const double* bias,
                                   int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// ReForm: rows at gap `gap` (slots b H + gap i, i < h) moved to gap 1; masks [h][limbs][N] (NTT domain,
+// 0/1 at slots b H + i, scale q_{limbs-1}); one level
+std::unique_ptr<CtSet> reform(Ctx& C, const CtSet& in, int gap, int h, const u64* masks);
 // baby-step giant-step revolver with baby-step size g: D [p] as matmul's
 std::unique_ptr<CtSet> matmul_bsgs(Ctx& C, const CtSet& A, const CtSet& B, int p, int g);
 // zero-rotation matmul: Ahat [G][n] (group-major volley encoding of A), B [n] -> D [G]
@@ -317,6 +333,12 @@ struct he_ctx {
 };
 struct he_ctset {
   std::unique_ptr<he::CtSet> s;
+};
+struct he_graph {
+  he_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;  // kernel nodes, added to the launch counter per replay
 };
 struct he_ptset {
   he::Ctx* ctx = nullptr;

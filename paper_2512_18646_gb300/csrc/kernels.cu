@@ -624,7 +624,7 @@ __global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in
 // xs is a device array of the T request pointers; every request word and
 // every output word is touched once, the masks stay in L2.
 __global__ void k_pack_blocks_kernel(const u64* const* xs, const u64* masks, int T, int n_ct, int limbs,
-                                     u64* out, const PrimeTab* pt, int log_n) {
+                                     size_t ct_stride, u64* out, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
   const size_t total = (size_t)n_ct * LN;
@@ -634,7 +634,7 @@ __global__ void k_pack_blocks_kernel(const u64* const* xs, const u64* masks, int
     const Mod md = pt[(int)(w >> log_n)].mod;
     Acc128 s0{0, 0}, s1{0, 0};
     for (int t = 0; t < T; t++) {
-      const u64* x = xs[t] + j * 2 * LN + w;
+      const u64* x = xs[t] + j * ct_stride + w;
       const u64 m = masks[(size_t)t * LN + w];
       mac128(s0, x[0], m);
       mac128(s1, x[LN], m);
@@ -870,10 +870,11 @@ void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }
-void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out) {
+void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out,
+                   size_t ct_stride) {
   HE_LAUNCH_P(k_pack_blocks_kernel, (size_t)n_ct * limbs * C.N,
               8.0 * (double)C.N * limbs * (2.0 * n_ct * T + (double)T + 2.0 * n_ct), 2.0 * C.N * limbs * n_ct * T,
-              xs, masks, T, n_ct, limbs, out, C.dev_ptab(), C.log_n);
+              xs, masks, T, n_ct, limbs, ct_stride ? ct_stride : (size_t)2 * limbs * C.N, out, C.dev_ptab(), C.log_n);
 }
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters) {
   const u64 q = C.q[0], w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);

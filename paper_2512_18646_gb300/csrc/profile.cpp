@@ -40,12 +40,16 @@ static cudaEvent_t take_event() {
 void* prof_begin(const char* name, cudaStream_t st, double bytes, double products) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_timing.load(std::memory_order_relaxed)) return nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r{name, bytes, products, take_event(), take_event()};
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   return (void*)(g_recs.size());
 }
+
+void prof_add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void prof_end(void* tok, cudaStream_t st) {
   if (!tok) return;

@@ -163,6 +163,33 @@ def test_matmul_ragged_shapes(lib, m, n, p):
     assert np.abs(g.decrypt_matrix(gd, m, p) - A @ Bm).max() < 1e-5
 
 
+@pytest.mark.parametrize("m,n,p,g", [(5, 3, 8, 4), (6, 2, 8, 3), (16, 5, 32, 0), (3, 2, 4, 4), (4, 3, 1, 0)])
+def test_matmul_bsgs_matches_oracle_and_revolver(lib, m, n, p, g):
+    """Baby-step giant-step revolver: bit-exact with the oracle's schedule, decrypting to A @ B and
+    to the plain revolver's diagonals (g = 0 picks the power of two nearest sqrt(p))."""
+    gg = g
+    if g == 0:
+        gg = 1
+        while 4 * gg * gg <= 2 * p:
+            gg *= 2
+        gg = min(gg, p)
+    o, gl = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=13, steps=None)
+    S = o.slots
+    ng = -(-p // gg)
+    steps = sorted(set(list(range(1, max(p, 2))) + [S - gg * i for i in range(1, ng)]))
+    o.keygen(steps)
+    gl.keygen(steps)
+    rng = np.random.default_rng(m * 11 + n + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    oa, ga = encrypt_both(o, gl, encode_columns(o, layouts.matrix_a_columns(A, S)), ct_id_base=0)
+    ob, gb = encrypt_both(o, gl, encode_columns(o, layouts.matrix_b_rows(Bm, S)), ct_id_base=60)
+    gd = gl.matmul_bsgs(ga, gb, m, p, g)
+    assert np.array_equal(gd.export(), o.matmul_bsgs(oa, ob, p, gg))
+    C = gl.decrypt_matrix(gd, m, p)
+    assert np.abs(C - A @ Bm).max() < 1e-5
+    assert np.abs(C - gl.decrypt_matrix(gl.matmul(ga, gb, m, p), m, p)).max() < 1e-5
+
+
 @pytest.mark.parametrize("log_n,m,n,p", [(13, 4, 8, 4), (10, 20, 3, 32), (10, 1, 5, 2), (10, 16, 9, 1)])
 def test_matmul_volley_matches_oracle_and_fp64(lib, log_n, m, n, p):
     """Zero-rotation matmul: bit-exact with the oracle from the same plaintexts, decrypts to
@@ -237,6 +264,32 @@ def test_conv2d_encrypted_kernels_matches_oracle_and_fp64(lib, stride, c_in, k):
     got = g.decrypt_image(gy, 3, H, stride, ref.shape[2])
     got = got.reshape(3, c_out, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
     assert np.abs(got - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("gap,h,H", [(2, 5, 16), (4, 3, 16), (2, 31, 64)])
+def test_reform_matches_oracle(lib, gap, h, H):
+    """ReForm: bit-exact with the oracle from the same mask plaintexts; the library's own mask
+    encoder decrypts to the same compacted rows."""
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=27, steps=None)
+    steps = [(gap - 1) * i for i in range(1, h)]
+    o.keygen(steps)
+    g.keygen(steps)
+    rng = np.random.default_rng(gap + h)
+    B = o.slots // H
+    rows = rng.uniform(-1, 1, (2, B, h))
+    z = np.zeros((2, o.slots))
+    for c in range(2):
+        for b in range(B):
+            z[c, b * H + gap * np.arange(h)] = rows[c, b]
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=40)
+    masks = o.reform_masks(h, H, o.L1)
+    gy = g.reform_coeffs(gx, gap, h, masks)
+    assert np.array_equal(gy.export(), o.reform(ox, gap, h, masks))
+    want = np.zeros((2, o.slots))
+    for c in range(2):
+        for b in range(B):
+            want[c, b * H: b * H + h] = rows[c, b]
+    assert np.abs(g.decrypt_slots(g.reform(gx, gap, h, H)) - want).max() < 1e-5
 
 
 def _act_polynomials():

@@ -547,6 +547,33 @@ def test_matmul_bsgs_matches_fp64_with_fewer_rotations(m, n, p, g):
     assert np.abs(C - A @ Bm).max() < 1e-6
 
 
+@pytest.mark.parametrize("gap,h,H", [(2, 5, 16), (4, 3, 16), (2, 8, 16)])
+def test_reform_compacts_rows(gap, h, H):
+    """ReForm (Sec. IV-C) in the column layout: rows at slots b H + gap i move to b H + i, every other
+    slot becomes 0; h - 1 rotations (one hoisted ModUp), h plaintext products, one rescale."""
+    o = Oracle(8, (60, 40, 40), 1, 60, 1, 40.0, seed=26)
+    steps = [(gap - 1) * i for i in range(1, h)]
+    o.keygen(steps)
+    rng = np.random.default_rng(gap * 10 + h)
+    B = o.slots // H
+    rows = rng.uniform(-1, 1, (B, h))
+    z = np.zeros(o.slots)
+    for b in range(B):
+        z[b * H + gap * np.arange(h)] = rows[b]
+        z[b * H + gap * h - 1] = 5.0  # an invalid slot (between rows) must not leak
+    X = o.encrypt(o.encode(z), ct_id=0)[None]
+    masks = o.reform_masks(h, H, o.L1)
+    o.reset_counters()
+    Y = o.reform(X, gap, h, masks)
+    c = o.counters()
+    assert c["rotations"] == h - 1 and c["modups"] == 1 and c["ct_plain"] == h and c["rescales"] == 1
+    got = o.decrypt(Y[0])
+    want = np.zeros(o.slots)
+    for b in range(B):
+        want[b * H: b * H + h] = rows[b]
+    assert np.abs(got - want).max() < 1e-6
+
+
 def encrypt_images(o, imgs, H, limbs=None, base_id=0):
     """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
     Bn, C, h, w = imgs.shape
