@@ -203,7 +203,6 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from oracle import fp64_ref  # FP64 closed form, used only for the accuracy check outside timing
     from paper_2512_18646_gb300 import api, load
 
     lib = load()
@@ -220,6 +219,9 @@ def run_gpu(args, rank, world, local_rank):
     x = g.encrypt_image(imgs, H, ct_id_base=0)
     fc_limbs = pre_limbs = len(pre.q_bits) - 4
     pts = g.fc_prepare(w.fc_w, 16, h2, h2, 4, H, B, fc_limbs)
+    # transform geometry tuned on a ModUp-sized batch (128 ciphertexts x 13 limbs), outside timing
+    tune_rows = 128 * len(pre.q_bits)
+    n1, cols, tune_us = g.ntt_autotune(tune_rows)
     g.synchronize()
 
     def step():
@@ -250,10 +252,8 @@ def run_gpu(args, rank, world, local_rank):
     t_max = max_over_ranks(ms, world)
     value = job_throughput(B, args.steps, world, t_max / 1e3)
 
-    # accuracy of the last step's logits against the FP64 CNN (outside timing)
+    # the last step's logits, checked against the FP64 CNN by the CPU leg (outside timing)
     logits = g.decrypt_slots(z)[:, ::H][:, :B].T
-    ref = fp64_ref.cnn(imgs, w)
-    max_err = float(np.abs(logits - ref).max())
 
     # per-kernel device time with CUDA events on the launching stream
     lib.he_profile_enable(1)
@@ -302,7 +302,9 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
     return {
         "value": value, "ms_per_step": t_max / args.steps, "launches": launches // args.steps * args.steps,
-        "roofline": roofline, "breakdown": breakdown, "e2e": e2e, "clocks": clocks, "max_abs_err": max_err,
+        "roofline": roofline, "breakdown": breakdown, "e2e": e2e, "clocks": clocks, "logits": logits, "imgs": imgs, "weights": w,
+            "ntt_geometry": {"column_stages": n1, "columns_per_block": cols, "tuned_on_limbs": tune_rows,
+                             "fwd_inv_us": round(tune_us, 1)},
         "images_per_step": B, "modmul_peak": modmul_peak.value,
     }
 
@@ -449,6 +451,79 @@ def run_matmul(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# many small products (--workload matmul_small): plain calls, one batched call, its CUDA graph
+# ---------------------------------------------------------------------------
+MATMUL_SMALL_METRIC = "HE-matmul/s (4096 matmuls A(4x8) B(8x4), N=2^13), plain vs batched vs CUDA graph"
+
+
+def run_matmul_small(args, rank, world, local_rank):
+    """4096 independent products of the small matmul configuration (N = 2^13, Q = 60 + 40 + 40,
+    P = 60, scale 2^40, n = 8 ciphertexts per operand): one he_matmul call per product (plain),
+    one he_matmul_batched call over all of them, and that call captured once into a CUDA graph
+    and replayed. Operands encrypted (untimed) up front; each path timed with CUDA events on the
+    context's stream over args.steps repetitions after args.warmup."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api, load
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    pre = synthetic.MATMUL_SMALL
+    g = api.Context.from_preset(pre, seed=5000 + rank, stream=stream.cuda_stream)
+    g.keygen([1, 2, 3])
+    count = args.count or 4096
+    m, n, p = 4, 8, 4
+    mats, As, Bs = [], [], []
+    for t in range(count):
+        A, Bm = synthetic.matmul_operands(m, n, p, seed=101 + 7919 * t)
+        mats.append(A @ Bm)
+        As.append(g.encrypt_matrix_a(A, 100 * t))
+        Bs.append(g.encrypt_matrix_b(Bm, 100 * t + 50))
+    ms, ps = [m] * count, [p] * count
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        g.synchronize()
+        l0 = lib.he_kernel_launches()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps, (lib.he_kernel_launches() - l0) / reps
+
+    def plain():
+        for t in range(count):
+            r = g.matmul(As[t], Bs[t], m, p)
+            del r
+
+    def batched():
+        r = g.matmul_batched(As, Bs, ms, ps)
+        del r
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+    t_plain, l_plain = timed(plain, 1)
+    t_batched, l_batched = timed(batched, max(1, args.steps))
+    g.synchronize()
+    g.graph_begin()
+    outs = g.matmul_batched(As, Bs, ms, ps)
+    graph = g.graph_end()
+    for _ in range(max(1, args.warmup)):
+        graph.launch()
+    t_graph, l_graph = timed(graph.launch, max(1, args.steps))
+    g.synchronize()
+    err = max(float(np.abs(g.decrypt_matrix(outs[t], m, p) - mats[t]).max()) for t in (0, count // 2, count - 1))
+    graph.destroy()
+    t_g = max_over_ranks(t_graph, world)
+    return {"value": count * world / t_g, "ms_per_step": 1e3 * t_g, "graph_kernel_launches": l_graph,
+            "batched_value": count * world / max_over_ranks(t_batched, world), "batched_ms": 1e3 * t_batched,
+            "batched_launches": l_batched, "plain_value": count * world / max_over_ranks(t_plain, world),
+            "plain_ms": 1e3 * t_plain, "plain_launches": l_plain, "max_abs_err": err, "count": count}
+
+
+# ---------------------------------------------------------------------------
 # the serving workload (--workload serve)
 # ---------------------------------------------------------------------------
 SERVE_METRIC = ("served encrypted-CNN images/s and p50/p99 latency (Poisson arrivals, image sides {64,128,256}, "
@@ -575,19 +650,25 @@ def run_serve(args, rank, world, local_rank):
     # accuracy: one request per side through the batched server, against the FP64 CNN (untimed)
     srv = api.Server(g, w, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_blocks=args.max_blocks,
                      start_paused=True)
-    from oracle import fp64_ref  # FP64 closed form, used only for the accuracy check outside timing
     rids = {s: srv.submit_ptr(*pool[s][0], s) for s in SERVE_SIDES}
     srv.pause(False)
-    err = 0.0
+    checks = []  # (logits, image, weights) per side, checked against the FP64 CNN by the CPU leg
     for s, rid in rids.items():
         srv.wait(rid, 600_000)
         z, blk, _ = srv.take(rid)
         logit = g.decrypt_slots(z)[:, blk * s]
         img = synthetic.images(1, s, s, seed=600 + s)[0]
-        err = max(err, float(np.abs(logit - fp64_ref.cnn(img[None], w[s])[0]).max()))
+        checks.append((logit[None], img[None], w[s]))
     srv.close()
-    res["max_abs_err"] = err
+    res["checks"] = checks
     return res
+
+
+def fp64_max_error(checks) -> float:
+    """CPU leg: max |decrypted logits - FP64 CNN| over (logits, images, weights) triples. The FP64
+    closed form lives with the oracle; only this CPU leg of the benchmark imports it."""
+    from oracle import fp64_ref
+    return max(float(np.abs(logits - fp64_ref.cnn(imgs, w)).max()) for logits, imgs, w in checks)
 
 
 # ---------------------------------------------------------------------------
@@ -633,7 +714,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cnn", "matmul", "serve"], default="cnn")
+    ap.add_argument("--workload", choices=["cnn", "matmul", "matmul_small", "serve"], default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
     ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
     ap.add_argument("--serve-warmup", type=int, default=20, help="serve workload: warm-up requests")
@@ -651,6 +732,27 @@ def main():
     cfg = {"workload": WORKLOAD, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+
+    if args.workload == "matmul_small" and args.impl == "gpu":
+        res = run_matmul_small(args, rank, world, local_rank)
+        if rank == 0:
+            line = {"metric": MATMUL_SMALL_METRIC, "value": res["value"], "unit": "HE-matmul/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                    "data": "synthetic",
+                    "config": {"workload": f"{res['count']} encrypted matmuls A(4x8) B(8x4), entries U[-1,1]; "
+                                           "RNS-CKKS N=2^13, Q=60+40+40, P=60, scale 2^40 (n=8 ciphertexts "
+                                           "per operand, p=4 diagonal outputs)",
+                               "parallelism": f"replicas x{world}",
+                               "l2": "operands 25.8 GB, larger than L2"},
+                    "path": "one he_matmul_batched call captured into a CUDA graph, replayed per step",
+                    "gpu_launches": res["graph_kernel_launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+                    "batched": {"value": res["batched_value"], "ms": res["batched_ms"],
+                                "gpu_launches": res["batched_launches"]},
+                    "plain": {"value": res["plain_value"], "ms": res["plain_ms"],
+                              "gpu_launches": res["plain_launches"]}}
+            print(json.dumps(line))
+        return
 
     if args.workload == "matmul" and args.impl == "gpu":
         res = run_matmul(args, rank, world, local_rank)
@@ -695,7 +797,8 @@ def main():
                     "e2e": {"value": b["e2e_images_per_s"], "unit": "images/s",
                             "h2d_bytes_per_step": b["h2d_bytes"] // b["requests"],
                             "d2h_bytes_per_step": b["d2h_bytes"] // b["requests"]},
-                    "max_abs_err_vs_fp64": res["max_abs_err"], "encrypt_pool_s": res["encrypt_pool_s"]}
+                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_max_error(res["checks"]),
+                    "encrypt_pool_s": res["encrypt_pool_s"]}
             print(json.dumps(line))
         return
 
@@ -724,6 +827,9 @@ def main():
     if rank != 0:
         return
     cpu = None
+    max_err = None
+    if not args.no_cpu_baseline:
+        max_err = fp64_max_error([(res["logits"], res["imgs"], res["weights"])])
     if not args.no_cpu_baseline and world == 1:
         dt, per_inf = oracle_sample(args.batch)
         cpu = {"value": args.batch / per_inf, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -733,9 +839,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
-            "gpu_launches": res["launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+            "gpu_launches": res["launches"], "max_abs_err_vs_fp64": max_err,
             "alu_peak_modmul_per_s": res["modmul_peak"],
-            "plain_images_per_s": res["value"] / args.batch, "kernel_breakdown": res["breakdown"]}
+            "plain_images_per_s": res["value"] / args.batch, "ntt_geometry": res["ntt_geometry"],
+            "kernel_breakdown": res["breakdown"]}
     print(json.dumps(line))
 
 

@@ -621,6 +621,21 @@ int he_sched_simulate(int n, const double* arrival_ms, const int* side, const si
  */
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse);
 
+/*
+ * Transform geometry. The negacyclic transform of a limb runs as n1 stages in
+ * column kernels (blocks of `cols` adjacent columns) and log_n - n1 stages in
+ * row kernels; every geometry computes the same transform, so results do not
+ * depend on it. he_ntt_set_geometry(ctx, 0, 0) restores the default (n1 =
+ * log_n / 2, 16 columns); unsupported choices return HE_E_ARG.
+ * he_ntt_autotune times a forward and an inverse transform of `rows` limbs
+ * (rounded up to whole polynomials) for every supported (n1, cols) with cols
+ * in {4, 8, 16, 32} (CUDA events on the context stream, 3 repetitions after a
+ * warm-up), keeps the fastest for the context and returns it with its time
+ * in microseconds (any output pointer may be NULL).
+ */
+int he_ntt_set_geometry(he_ctx* ctx, int n1, int cols);
+int he_ntt_autotune(he_ctx* ctx, int rows, int* n1, int* cols, double* us);
+
 /* ---- instrumentation ---- */
 
 /* Measured peak of 64-bit Shoup modular products (x w mod q with a

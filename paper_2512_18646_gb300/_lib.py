@@ -121,6 +121,8 @@ SIGNATURES = {
     "he_sched_simulate": (I, [I, P_D, P_I, ctypes.POINTER(SZ), I, P_I, P_D, P_D, SZ, SZ, I, SZ, P_I64, P_I, P_D,
                               P_D, P_D, ctypes.POINTER(SZ)]),
     "he_ntt": (I, [V, P_U64, I, I, I, I]),
+    "he_ntt_set_geometry": (I, [V, I, I]),
+    "he_ntt_autotune": (I, [V, I, P_I, P_I, P_D]),
     "he_calibrate_modmul": (I, [V, P_D]),
     "he_kernel_launches": (U64, []),
     "he_profile_enable": (I, [I]),

@@ -204,6 +204,15 @@ class Context:
         A = _f64(A)
         return self._set(load().he_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)
 
+    def ntt_set_geometry(self, n1: int, cols: int):
+        check(load().he_ntt_set_geometry(self.h, n1, cols))
+
+    def ntt_autotune(self, rows: int):
+        """-> (n1, cols, microseconds of a forward + inverse transform of `rows` limbs)."""
+        n1, c, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(load().he_ntt_autotune(self.h, rows, ctypes.byref(n1), ctypes.byref(c), ctypes.byref(us)))
+        return n1.value, c.value, us.value
+
     def graph_begin(self):
         check(load().he_graph_begin(self.h))
 

@@ -733,6 +733,79 @@ int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s) {
   });
 }
 
+int he_ntt_set_geometry(he_ctx* ctx, int n1, int cols) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    if (n1 == 0 && cols == 0) {
+      C.ntt_n1 = C.ntt_cols = 0;
+      return;
+    }
+    REQUIRE(ntt_geometry_ok(C.log_n, n1, cols), HE_E_ARG, "unsupported transform geometry");
+    C.ntt_n1 = n1;
+    C.ntt_cols = cols;
+  });
+}
+
+int he_ntt_autotune(he_ctx* ctx, int rows, int* n1_out, int* cols_out, double* us_out) {
+  return guard([&] {
+    REQUIRE(ctx && rows >= 1, HE_E_ARG, "bad arguments");
+    Ctx& C = ctx->c;
+    REQUIRE(!C.capturing, HE_E_STATE, "a capture is open on this context");
+    const int lp = C.L1;
+    const int polys = (rows + lp - 1) / lp;
+    DevBuf d((size_t)polys * lp * C.N, C.stream);
+    HE_CUDA(cudaMemsetAsync(d.p, 0, d.words * 8, C.stream));
+    const LimbMap lm = limbs_q(lp, C.N);
+    cudaEvent_t e0, e1;
+    HE_CUDA(cudaEventCreate(&e0));
+    HE_CUDA(cudaEventCreate(&e1));
+    const int saved_n1 = C.ntt_n1, saved_cols = C.ntt_cols;
+    double best = 1e30;
+    int bn1 = 0, bc = 0;
+    try {
+      for (int n1 = 2; n1 <= 8; n1++)
+        for (int cols = 4; cols <= 32; cols *= 2) {
+          if (!ntt_geometry_ok(C.log_n, n1, cols)) continue;
+          C.ntt_n1 = n1;
+          C.ntt_cols = cols;
+          ntt_forward(C, d.p, polys, lm);  // warm-up (and the one-time shared-memory opt-in)
+          ntt_inverse(C, d.p, polys, lm);
+          constexpr int reps = 3;
+          HE_CUDA(cudaEventRecord(e0, C.stream));
+          for (int r = 0; r < reps; r++) {
+            ntt_forward(C, d.p, polys, lm);
+            ntt_inverse(C, d.p, polys, lm);
+          }
+          HE_CUDA(cudaEventRecord(e1, C.stream));
+          HE_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          HE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          const double us = 1e3 * ms / reps;
+          if (us < best) {
+            best = us;
+            bn1 = n1;
+            bc = cols;
+          }
+        }
+    } catch (...) {
+      C.ntt_n1 = saved_n1;
+      C.ntt_cols = saved_cols;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    REQUIRE(bn1 > 0, HE_E_UNIMPL, "no transform geometry for this ring degree");
+    C.ntt_n1 = bn1;
+    C.ntt_cols = bc;
+    if (n1_out) *n1_out = bn1;
+    if (cols_out) *cols_out = bc;
+    if (us_out) *us_out = best;
+  });
+}
+
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse) {
   return guard([&] {
     REQUIRE(ctx && host && n_polys >= 1 && limbs >= 1, HE_E_ARG, "bad arguments");

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 
 #include "he_internal.h"
 
@@ -588,18 +589,22 @@ std::unique_ptr<CtSet> matmul_volley(Ctx& C, const CtSet& Ah_any, const CtSet& B
   return d;
 }
 
-// Independent products A_i B_i evaluated together. Matmuls with the same p
-// and level form a group; inside a group, sub-batches of matmuls whose B
-// operands fit the working-memory budget are concatenated into one set, so
-// one ModUp launch and one launch per chunk of rotation steps serve all of
-// them (each key tile is read once per launch for every ciphertext of the
-// sub-batch). Each matmul accumulates into its own three-component set; the
-// results are identical to separate matmul() calls.
+// Independent products A_i B_i evaluated together. Matmuls with the same p, level
+// and scale form a group; inside a group, sub-batches of matmuls whose B operands
+// fit the working-memory budget are concatenated into one set (one gather launch per
+// kSetBlock products), so one ModUp launch and one launch per chunk of rotation
+// steps serve all of them (each key tile is read once per launch for every
+// ciphertext of the sub-batch). The tensor sums of up to kSetBlock products share a
+// launch and write one three-component set, which is rescaled and relinearised
+// once and then scattered into the per-product results (one launch per kSetBlock
+// products). Every launch takes its pointers as kernel parameters, so the whole
+// call can be captured into a CUDA graph. The per-ciphertext arithmetic is that of
+// matmul(), so the results are identical to separate calls.
 std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<const CtSet*>& As,
                                                    const std::vector<const CtSet*>& Bs, const std::vector<int>& ps) {
   const int cnt = (int)As.size();
   std::vector<std::unique_ptr<CtSet>> out(cnt);
-  std::map<std::pair<int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, double>, std::vector<int>> groups;
   for (int i = 0; i < cnt; i++) {
     const CtSet& A = *As[i];
     const CtSet& B = *Bs[i];
@@ -609,12 +614,13 @@ std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<con
     if (A.limbs != B.limbs || A.scale != B.scale) throw Error(4, "operands at different levels or scales");
     if (A.limbs < 2) throw Error(2, "no level left for the product");
     for (int s = 1; s < ps[i]; s++) C.key(C.galois_elt(s));
-    groups[{ps[i], A.limbs}].push_back(i);
+    groups[std::make_tuple(ps[i], A.limbs, A.scale)].push_back(i);
   }
   const size_t N = C.N;
   const size_t budget = (size_t)6 << 30;  // words (48 GiB) of digits, rotated operands and key-switch scratch
   for (auto& kv : groups) {
-    const int p = kv.first.first, lp = kv.first.second;
+    const int p = std::get<0>(kv.first), lp = std::get<1>(kv.first);
+    const double sc = std::get<2>(kv.first);
     const std::vector<int>& members = kv.second;
     const size_t cw = (size_t)2 * lp * N;
     const size_t ext_ct = (size_t)C.beta_at(lp) * (lp + C.K) * N;
@@ -632,20 +638,22 @@ std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<con
         ntot += nn;
       }
       m0 += sb.size();
-      auto Bcat = new_set(C, ntot, 2, lp, Bs[sb[0]]->scale);
-      std::vector<size_t> off(sb.size());
-      size_t o = 0;
-      for (size_t t = 0; t < sb.size(); t++) {
-        off[t] = o;
-        const CtSet& B = *Bs[sb[t]];
-        HE_CUDA(cudaMemcpyAsync(Bcat->ct((int)o), B.buf.p, B.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
-        o += B.n;
+      const int T = (int)sb.size();
+      std::vector<size_t> off(T + 1, 0);  // ciphertext offsets of the products in the concatenation
+      for (int t = 0; t < T; t++) off[t + 1] = off[t] + (size_t)Bs[sb[t]]->n;
+      auto Bcat = new_set(C, ntot, 2, lp, sc);
+      for (int t0 = 0; t0 < T; t0 += kSetBlock) {
+        const int tn = std::min(kSetBlock, T - t0);
+        SetPtrs P;
+        for (int t = 0; t <= tn; t++) {
+          if (t < tn) P.p[t] = Bs[sb[t0 + t]]->buf.p;
+          P.off[t] = (off[t0 + t] - off[t0]) * cw;
+        }
+        k_move_words(C, P, Bcat->ct((int)off[t0]), tn, 0);
       }
       DevBuf ext;
       if (p > 1) ext = modup_c1(C, *Bcat);
-      std::vector<std::unique_ptr<CtSet>> d(sb.size());
-      for (size_t t = 0; t < sb.size(); t++)
-        d[t] = new_set(C, p, 3, lp, As[sb[t]]->scale * Bs[sb[t]]->scale);
+      auto D = new_set(C, T * p, 3, lp, sc * sc);
       const size_t room = budget > (size_t)ntot * ext_ct ? budget - (size_t)ntot * ext_ct : 0;
       int chunk = (int)std::max<size_t>(1, room / ((size_t)ntot * step_ct));
       if (chunk > p) chunk = p;
@@ -655,16 +663,31 @@ std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<con
         std::vector<long> steps(ci);
         for (int t = 0; t < ci; t++) steps[t] = i0 + t;
         rotate_from_ext(C, *Bcat, ext, steps, R.p, ci);
-        for (size_t t = 0; t < sb.size(); t++)
-          k_matmul_acc(C, As[sb[t]]->buf.p, R.p + off[t] * ci * cw, d[t]->ct(i0), As[sb[t]]->n, ci, lp);
+        for (int t0 = 0; t0 < T; t0 += kSetBlock) {
+          const int tn = std::min(kSetBlock, T - t0);
+          SetPtrs Ap;
+          for (int t = 0; t <= tn; t++) {
+            if (t < tn) Ap.p[t] = As[sb[t0 + t]]->buf.p;
+            Ap.off[t] = off[t0 + t];
+          }
+          k_matmul_acc_multi(C, Ap, R.p, D->buf.p, tn, t0, p, i0, ci, lp);
+        }
       }
       R.reset();
       ext.reset();
       Bcat.reset();
-      for (size_t t = 0; t < sb.size(); t++) {
-        rescale_inplace(C, *d[t]);
-        relinearize(C, *d[t]);
-        out[sb[t]] = std::move(d[t]);
+      rescale_inplace(C, *D);
+      relinearize(C, *D);
+      const size_t ow = (size_t)p * D->ct_words();
+      for (int t = 0; t < T; t++) out[sb[t]] = new_set(C, p, 2, lp - 1, D->scale);
+      for (int t0 = 0; t0 < T; t0 += kSetBlock) {
+        const int tn = std::min(kSetBlock, T - t0);
+        SetPtrs Q;
+        for (int t = 0; t <= tn; t++) {
+          if (t < tn) Q.p[t] = out[sb[t0 + t]]->buf.p;
+          Q.off[t] = (size_t)t * ow;
+        }
+        k_move_words(C, Q, D->buf.p + (size_t)t0 * ow, tn, 1);
       }
     }
   }

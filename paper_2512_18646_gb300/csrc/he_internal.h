@@ -111,6 +111,8 @@ struct Ctx {
   // with the same per-ciphertext arithmetic
   size_t work_budget = 0;
 
+  // transform geometry (0: default): column-kernel stages and columns per column block
+  int ntt_n1 = 0, ntt_cols = 0;
   // capture of library calls into a CUDA graph (he_graph_begin / he_graph_end): sets made during
   // a capture carry its generation; sets made before it and freed during it are kept here and
   // released after the capture ends (their memory is not the graph's to free)
@@ -153,6 +155,8 @@ void prof_add_launches(uint64_t n);
 
 // ---- kernel launchers (kernels.cu / ntt.cu) ----
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
+// whether the transform supports n1 column stages (log_n - n1 row stages) with `cols` columns per block
+bool ntt_geometry_ok(int log_n, int n1, int cols);
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // rescale of `rows` polynomials x [rows][lp][N] whose limb lp - 1 is already in the
 // coefficient domain: out [rows][lp - 1][N] = (x_i - NTT_i(expanded last limb)) q_l^{-1}
@@ -229,6 +233,19 @@ void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_
 // matmul accumulate: d[idx] = sum_k tensor(A_k, R[k][idx]), idx < p; R holds rstride (default p)
 // ciphertexts per k
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs, int rstride = 0);
+// up to kSetBlock device ranges passed by value to a kernel (so captured graphs replay them):
+// range t starts at p[t] and spans off[t+1] - off[t] words (or ciphertexts, per use)
+constexpr int kSetBlock = 128;
+struct SetPtrs {
+  const u64* p[kSetBlock];
+  size_t off[kSetBlock + 1];
+};
+// T <= kSetBlock products in one launch: d[(t0 + t) p + i0 + idx] = sum_{k < n_t} tensor(A_t[k],
+// R[off[t] + k][idx]), idx < ci, n_t = A.off[t+1] - A.off[t] (ciphertexts)
+void k_matmul_acc_multi(const Ctx& C, const SetPtrs& A, const u64* R, u64* d, int T, int t0, int p, int i0, int ci,
+                        int limbs);
+// dir 0: base + off[t] <- p[t]; dir 1: p[t] <- base + off[t] (off in words), T <= kSetBlock ranges, one launch
+void k_move_words(const Ctx& C, const SetPtrs& P, u64* base, int T, int dir);
 // zero-rotation matmul accumulate: d[g] = sum_k tensor(Ahat[g][k], B[k]), g < G
 void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components

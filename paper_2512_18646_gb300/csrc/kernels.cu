@@ -526,6 +526,61 @@ __global__ void k_matmul_acc_kernel(const u64* A, const u64* R, u64* d, int n, i
   }
 }
 
+// Accumulate of up to kSetBlock independent products in one launch (the product
+// pointers travel as a kernel parameter, so a captured graph replays them):
+// product t (n_t = off[t+1] - off[t] ciphertexts per operand) gets
+// d[(t0 + t) p + i0 + idx] = sum_k tensor(A_t[k], R[off[t] + k][idx]), idx < ci, with R
+// [sum n][ci][2][limbs][N] the rotations of the concatenated B operands.
+__global__ void k_matmul_acc_multi_kernel(SetPtrs A, const u64* R, u64* d, int T, int t0, int p, int i0, int ci,
+                                          int limbs, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const size_t total = (size_t)T * ci * LN;
+  HE_GRID_LOOP(idx, total) {
+    const size_t w = idx % LN;
+    const size_t r = idx / LN;
+    const int id = (int)(r % ci), t = (int)(r / ci);
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    const size_t k0 = A.off[t];
+    const int n = (int)(A.off[t + 1] - k0);
+    const u64* Ap = A.p[t];
+    Acc128 s0{0, 0}, s1{0, 0}, s2{0, 0};
+    for (int kk = 0; kk < n; kk++) {
+      const u64* a = Ap + (size_t)kk * 2 * LN + w;
+      const u64* rr = R + ((k0 + kk) * ci + id) * 2 * LN + w;
+      const u64 a0 = a[0], a1 = a[LN], r0 = rr[0], r1 = rr[LN];
+      mac128(s0, a0, r0);
+      mac128(s1, a0, r1);
+      mac128(s1, a1, r0);
+      mac128(s2, a1, r1);
+      if ((kk & 7) == 7) {
+        s0 = Acc128{0, reduce128(s0.hi, s0.lo, md)};
+        s1 = Acc128{0, reduce128(s1.hi, s1.lo, md)};
+        s2 = Acc128{0, reduce128(s2.hi, s2.lo, md)};
+      }
+    }
+    u64* D = d + ((size_t)(t0 + t) * p + i0 + id) * 3 * LN + w;
+    D[0] = reduce128(s0.hi, s0.lo, md);
+    D[LN] = reduce128(s1.hi, s1.lo, md);
+    D[2 * LN] = reduce128(s2.hi, s2.lo, md);
+  }
+}
+
+// Gather (dir 0: base + off[t] <- P.p[t]) or scatter (dir 1: P.p[t] <- base + off[t]) of up to
+// kSetBlock device ranges of off[t+1] - off[t] words, blockIdx.y = range.
+__global__ void k_move_words_kernel(SetPtrs P, u64* base, int T, int dir) {
+  const int t = blockIdx.y;
+  if (t >= T) return;
+  const size_t n = P.off[t + 1] - P.off[t];
+  u64* far = const_cast<u64*>(P.p[t]);
+  u64* near = base + P.off[t];
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (dir == 0) near[i] = far[i];
+    else far[i] = near[i];
+  }
+}
+
 // Zero-rotation matmul accumulate: d[g] (3 components) = sum_k tensor(Ahat[g][k], B[k]);
 // Ahat [G][n][2][limbs][N], B [n][2][limbs][N]. Sums of 128-bit products, reduced
 // every 8 terms.
@@ -849,6 +904,23 @@ void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_
 void k_matmul_acc(const Ctx& C, const u64* A, const u64* R, u64* d, int n, int p, int limbs, int rstride) {
   HE_LAUNCH_P(k_matmul_acc_kernel, (size_t)p * limbs * C.N, 8.0 * (double)C.N * limbs * (2.0 * n + 2.0 * n * p + 3.0 * p),
               4.0 * C.N * limbs * n * p, A, R, d, n, p, rstride > 0 ? rstride : p, limbs, C.dev_ptab(), C.log_n);
+}
+void k_matmul_acc_multi(const Ctx& C, const SetPtrs& A, const u64* R, u64* d, int T, int t0, int p, int i0, int ci,
+                        int limbs) {
+  const double LN = (double)limbs * C.N, n_total = (double)(A.off[T] - A.off[0]);
+  HE_LAUNCH_P(k_matmul_acc_multi_kernel, (size_t)T * ci * limbs * C.N,
+              8.0 * LN * (2.0 * n_total + 2.0 * n_total * ci + 3.0 * T * ci), 4.0 * LN * n_total * ci, A, R, d, T, t0,
+              p, i0, ci, limbs, C.dev_ptab(), C.log_n);
+}
+void k_move_words(const Ctx& C, const SetPtrs& P, u64* base, int T, int dir) {
+  if (T <= 0) return;
+  size_t mx = 0;
+  for (int t = 0; t < T; t++) mx = std::max(mx, (size_t)(P.off[t + 1] - P.off[t]));
+  const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>(64, (mx + 255) / 256));
+  void* tok = prof_begin("k_move_words_kernel", C.stream, 16.0 * (double)(P.off[T] - P.off[0]));
+  k_move_words_kernel<<<dim3(gx, (unsigned)T), 256, 0, C.stream>>>(P, base, T, dir);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
 }
 void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs) {
   HE_LAUNCH_P(k_volley_acc_kernel, (size_t)G * limbs * C.N,

@@ -559,12 +559,15 @@ __global__ void k_ntt_inv_cols(u64* data, LimbMap lm, const PrimeTab* pt, const 
 struct Geom {
   int n1, n2, C;
 };
-Geom geom(int log_n) {
+// The transform's geometry: column stages n1 (the rest, n2, in the row kernels) and the
+// columns C of a column block; the context's tuned choice (he_ntt_autotune /
+// he_ntt_set_geometry) or the default n1 = log_n / 2, C = min(16, 2^n2).
+Geom geom(const Ctx& Cx) {
   Geom g;
-  g.n1 = log_n / 2;
-  g.n2 = log_n - g.n1;
+  g.n1 = Cx.ntt_n1 > 0 ? Cx.ntt_n1 : Cx.log_n / 2;
+  g.n2 = Cx.log_n - g.n1;
   const int S2 = 1 << g.n2;
-  g.C = S2 < 16 ? S2 : 16;
+  g.C = Cx.ntt_cols > 0 ? Cx.ntt_cols : (S2 < 16 ? S2 : 16);
   return g;
 }
 
@@ -594,6 +597,16 @@ void launch_cols(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C,
                  const Fuse& fz) {
   const int threads = Ccols * Plan<L, kColKB>::T;
   const size_t smem = (size_t)(1 << L) * Ccols * 8;
+  if (smem > 48 * 1024) {  // a wide column tile (autotuner candidate) needs the opt-in shared memory
+    static bool attr = false;
+    if (!attr) {
+      HE_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols<L, MODE == 3 ? 0 : MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   128 * 1024));
+      HE_CUDA(cudaFuncSetAttribute(k_ntt_inv_cols<L, MODE == 3 ? 3 : 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   128 * 1024));
+      attr = true;
+    }
+  }
   const dim3 grid((1 << n2) / Ccols, rows);
   // butterflies, plus N^{-1} (inverse) or the reduction of the expanded limb (fused rescale)
   const double prods = (double)rows * C.N *
@@ -653,7 +666,7 @@ void cols_dispatch(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& 
 void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   const int rows = n_polys * lm.lpp;
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   // grid.y holds at most 65535 rows; chunks end on polynomial boundaries
   const int step = (65535 / lm.lpp) * lm.lpp;
   for (int r0 = 0; r0 < rows; r0 += step) {
@@ -668,7 +681,7 @@ void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   const int rows = n_polys * lm.lpp;
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   const int step = (65535 / lm.lpp) * lm.lpp;
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
@@ -682,7 +695,7 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
 void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp) {
   const int rows = n_polys * lp;
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   const LimbMap lm = limbs_q(lp, C.N);
   Fuse fz;
   fz.iscale = C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2 + (size_t)(C.L1 + 1) * C.L1 * (C.L1 + C.K) * 2 +
@@ -702,7 +715,7 @@ void ntt_forward_modup(const Ctx& C, u64* ext_digit, int n, const LimbMap& lm, c
                        const u64* hat, int hstride, int cnt) {
   const int rows = n * lm.lpp;
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   const int per = 65535 / lm.lpp;  // polynomials per launch (grid.y <= 65535)
   for (int p0 = 0; p0 < n; p0 += per) {
     const int pn = n - p0 < per ? n - p0 : per;
@@ -723,7 +736,7 @@ void ntt_inverse_pscaled(const Ctx& C, u64* data, int n_polys) {
   const int lpp = C.K;
   const int rows = n_polys * lpp;
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   LimbMap lm;
   lm.lpp = C.K; lm.split = 0; lm.base0 = 0; lm.base1 = C.L1; lm.poly_stride = (size_t)C.K * C.N;
   Fuse fz;
@@ -742,7 +755,7 @@ void ntt_inverse_pscaled(const Ctx& C, u64* data, int n_polys) {
 void ntt_forward_moddown(const Ctx& C, u64* z, const u64* yt, int n, int lp, const u64* u, int nb, const u64* base,
                          size_t base_stride, u64* out, size_t out_stride, u64 gk, int kmode) {
   if (n == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   const LimbMap lm = limbs_q(lp, C.N);
   const int per = 65535 / (2 * lp) * 2;  // polynomials per launch: whole ciphertexts, grid.y <= 65535
   for (int p0 = 0; p0 < 2 * n; p0 += per) {
@@ -768,9 +781,18 @@ void ntt_forward_moddown(const Ctx& C, u64* z, const u64* yt, int n, int lp, con
   HE_CUDA(cudaGetLastError());
 }
 
+bool ntt_geometry_ok(int log_n, int n1, int cols) {
+  const int n2 = log_n - n1;
+  if (n1 < 2 || n1 > 8 || n2 < 2 || n2 > 8) return false;
+  if (cols < 1 || cols > 32 || (cols & (cols - 1)) || cols > (1 << n2)) return false;
+  const int kb = n1 < kColKB ? n1 : kColKB;
+  const int threads = cols * ((1 << n1) >> kb);
+  return threads >= 32 && threads <= 1024 && (size_t)(1 << n1) * cols * 8 <= 128 * 1024;
+}
+
 void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
   if (rows == 0) return;
-  const Geom g = geom(C.log_n);
+  const Geom g = geom(C);
   const LimbMap lm = limbs_q(lp - 1, C.N);
   const u64* tab = C.d_rs.p + (size_t)lp * C.L1 * 3;
   const int per = 65535 / (lp - 1);  // polynomials per launch (grid.y <= 65535)

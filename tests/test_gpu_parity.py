@@ -47,6 +47,34 @@ def test_ntt_matches_oracle(lib, log_n):
             assert np.array_equal(fb[t, i], o.ntt(b[t, i], 1 + i))
 
 
+@pytest.mark.parametrize("log_n", [10, 13, 15, 16])
+def test_ntt_every_geometry_matches_oracle(lib, log_n):
+    """Every transform geometry the autotuner may pick (column stages n1, columns per block) computes
+    the oracle's transform bit for bit, forward and inverse; the autotuner returns one of them."""
+    from paper_2512_18646_gb300._lib import HeError
+    o, g = make_pair(log_n, (60, 40, 45), 2, 60, 1, 40.0, steps=None)
+    rng = np.random.default_rng(100 + log_n)
+    a = np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.primes])[None]
+    want = np.stack([o.ntt(a[0, pi], pi) for pi in range(len(o.primes))])
+    tried = 0
+    for n1 in range(2, 9):
+        for cols in (4, 8, 16, 32):
+            try:
+                g.ntt_set_geometry(n1, cols)
+            except HeError:
+                continue
+            tried += 1
+            fwd = g.ntt(a, 0)
+            assert np.array_equal(fwd[0], want), (n1, cols)
+            assert np.array_equal(g.ntt(fwd, 0, inverse=True), a), (n1, cols)
+    assert tried >= 2
+    n1, cols, us = g.ntt_autotune(64)
+    assert us > 0
+    g.ntt_set_geometry(n1, cols)  # the tuned choice is a supported geometry
+    assert np.array_equal(g.ntt(a, 0)[0], want)
+    g.ntt_set_geometry(0, 0)
+
+
 def test_encrypt_matches_oracle(lib):
     o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=3, steps=[])
     z = np.random.default_rng(1).uniform(-1, 1, (5, o.slots))
@@ -435,6 +463,78 @@ def test_matmul_batched_equals_single_matmuls(lib):
         assert np.array_equal(outs[t].export(), single.export()), t
         assert np.abs(g.decrypt_matrix(outs[t], m, p) - ref[t]).max() < 1e-5
 
+
+
+def test_graph_replays_batched_matmuls(lib):
+    """A batched call captured into a CUDA graph: each replay recomputes the products from the
+    current contents of the input sets, bit-identical to eager calls; in-place calls on sets made
+    before the capture are refused inside it."""
+    import torch
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_E_STATE, HeError
+    stream = torch.cuda.Stream()
+    pre = synthetic.MATMUL_SMALL
+    g = api.Context.from_preset(pre, seed=77, stream=stream.cuda_stream)
+    g.keygen([1, 2, 3, 4, 5, 6, 7])
+    shapes = [(4, 8, 4), (4, 8, 4), (3, 5, 8), (4, 8, 4), (2, 3, 2)]
+
+    def operands(seed):
+        rng = np.random.default_rng(seed)
+        ops = [(rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))) for m, n, p in shapes]
+        return ([g.encrypt_matrix_a(A, 10 * t) for t, (A, _) in enumerate(ops)],
+                [g.encrypt_matrix_b(B, 10 * t + 5) for t, (_, B) in enumerate(ops)], ops)
+
+    A1, B1, ops1 = operands(1)
+    A2, B2, ops2 = operands(2)
+    ms, ps = [s[0] for s in shapes], [s[2] for s in shapes]
+    eager1 = [c.export() for c in g.matmul_batched(A1, B1, ms, ps)]
+    eager2 = [c.export() for c in g.matmul_batched(A2, B2, ms, ps)]
+    # graph inputs: sets made before the capture, holding the first operands
+    Ain, Bin, _ = operands(1)
+    g.graph_begin()
+    outs = g.matmul_batched(Ain, Bin, ms, ps)
+    with pytest.raises(HeError) as e:
+        g.rescale(Ain[0])
+    assert e.value.code == HE_E_STATE
+    graph = g.graph_end()
+    assert graph.kernel_nodes > 0
+    graph.launch()
+    g.synchronize()
+    for t in range(len(shapes)):
+        assert np.array_equal(outs[t].export(), eager1[t])
+        assert np.abs(g.decrypt_matrix(outs[t], ms[t], ps[t]) - ops1[t][0] @ ops1[t][1]).max() < 1e-5
+    for t in range(len(shapes)):
+        g.assign(Ain[t], A2[t])
+        g.assign(Bin[t], B2[t])
+    graph.launch()
+    graph.launch()  # a replay over the same inputs gives the same results
+    g.synchronize()
+    for t in range(len(shapes)):
+        assert np.array_equal(outs[t].export(), eager2[t])
+    graph.destroy()
+
+
+def test_graph_capture_failure_leaves_context_usable(lib):
+    """A call that uploads host data cannot be captured: the capture reports HE_E_CUDA and the
+    context keeps working eagerly."""
+    import torch
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_E_CUDA, HeError
+    stream = torch.cuda.Stream()
+    g = api.Context(10, (60, 40, 40), 1, 60, 1, 40.0, seed=78, stream=stream.cuda_stream)
+    g.keygen([1])
+    g.graph_begin()
+    failed = False
+    try:
+        g.encrypt_matrix_a(np.ones((2, 2)), 0)
+    except HeError:
+        failed = True
+    with pytest.raises(HeError) as e:
+        g.graph_end()
+    assert e.value.code == HE_E_CUDA or failed
+    A, Bm = np.arange(6.0).reshape(2, 3) / 6, np.arange(6.0).reshape(3, 2) / 6
+    C = g.decrypt_matrix(g.matmul(g.encrypt_matrix_a(A, 0), g.encrypt_matrix_b(Bm, 5), 2, 2), 2, 2)
+    assert np.abs(C - A @ Bm).max() < 1e-5
 
 
 def test_work_budget_chunks_are_bit_identical(lib):
