@@ -524,6 +524,98 @@ def run_matmul_small(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# Table I's first layer on 28x28 images (--workload layer28): the paper's single-ciphertext method
+# (Alg. 4 over virtual ciphertexts) against the column layout, same layer
+# ---------------------------------------------------------------------------
+LAYER28_METRIC = ("encrypted-layer images/s (Table I CONV 4x3x3 stride 1 + ACT-1 on 28x28 images, N=2^16), "
+                  "column layout vs single-ciphertext Alg. 4")
+ACT1 = (-0.00015120704, 0.4610149, 2.0225089, -1.4511951)  # Table I, ACT-1
+
+
+def run_layer28(args, rank, world, local_rank):
+    """CONV (4 kernels 3x3, stride 1) + ACT-1 of Table I on synthetic 28x28 images at the CNN
+    parameters (N = 2^16, Q = 60 + 12 x 45, P = 2 x 60). Single-ciphertext path (the paper's
+    original method): 32 images per ciphertext in 32x32 blocks (Sec. V: 32 images per ciphertext),
+    Alg. 4 per kernel with encrypted Kernelspanner ciphertexts and bias. Column path: 1024 images per
+    ciphertext set (blocks of 32 rows), 28 column ciphertexts, he_conv2d with the 4 kernels. Both
+    followed by ACT-1 (degree 3). Timed with CUDA events on the context's stream."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api, load
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    pre = synthetic.CNN_N16
+    g = api.Context.from_preset(pre, seed=6000 + rank, stream=stream.cuda_stream)
+    side, k, Hb = 28, 3, 32
+    g.keygen([1, 2, Hb, 2 * Hb])
+    K, bias = synthetic.conv_weights(4, 1, k, 0.1, seed=202)
+    S = g.N // 2
+    n_vr = S // (Hb * Hb)  # 32 images per ciphertext
+    n_col = S // Hb        # 1024 images per column set
+    imgs_vr = synthetic.images(n_vr, side, side, seed=701)
+    imgs_col = synthetic.images(n_col, side, side, seed=702)
+    x_vr = g.vr_encrypt_images(imgs_vr, Hb, Hb, 0)
+    kern = [g.vr_encrypt_kernels(K[o, 0], float(bias[o]), side, side, Hb, Hb, g.L1, 100 * (o + 1))
+            for o in range(4)]
+    x_col = g.encrypt_image(imgs_col, Hb, ct_id_base=1000)
+    g.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        g.synchronize()
+        l0 = lib.he_kernel_launches()
+        ev0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps, (lib.he_kernel_launches() - l0) / reps, r
+
+    def single():
+        outs = []
+        for o in range(4):
+            y = g.vr_conv2d(x_vr, kern[o][0], kern[o][1], side, side, k, Hb, Hb)
+            outs.append(g.poly_act(y, ACT1))
+        return outs
+
+    def column():
+        y = g.conv2d(x_col, 1, 1, K, bias, 1)
+        return g.poly_act(y, ACT1)
+
+    t_vr, l_vr, out_vr = timed(single, max(1, args.steps))
+    t_col, l_col, out_col = timed(column, max(1, args.steps))
+    # decrypted outputs for the CPU leg's FP64 check (first 4 images of each path)
+    ho = side - k + 1
+    dec_vr = np.stack([g.decrypt_slots(y)[0] for y in out_vr])  # [o][slots]
+    vr_img = np.zeros((4, 4, ho, ho))
+    for o in range(4):
+        for b in range(4):
+            for r in range(ho):
+                vr_img[b, o, r] = dec_vr[o, b * Hb * Hb + r * Hb: b * Hb * Hb + r * Hb + ho]
+    dec_col = g.decrypt_image(out_col, 4, Hb, 1, ho).reshape(4, 4, ho, ho).transpose(0, 1, 3, 2)
+    t_c = max_over_ranks(t_col, world)
+    return {"value": n_col * world / t_c, "ms_per_step": 1e3 * t_c, "launches": l_col,
+            "single_value": n_vr * world / max_over_ranks(t_vr, world), "single_ms": 1e3 * t_vr,
+            "single_launches": l_vr,
+            "checks": [(vr_img, imgs_vr[:4], K, bias), (dec_col, imgs_col[:4], K, bias)]}
+
+
+def fp64_layer_error(checks) -> float:
+    """CPU leg: max |decrypted - FP64 (conv + ACT-1)| (the closed forms live with the oracle)."""
+    from oracle import fp64_ref
+    err = 0.0
+    for got, imgs, K, bias in checks:
+        x = fp64_ref.conv2d(imgs[:, None], K, bias, 1)
+        ref = ACT1[0] + ACT1[1] * x + ACT1[2] * x ** 2 + ACT1[3] * x ** 3
+        err = max(err, float(np.abs(got - ref).max()))
+    return err
+
+
+# ---------------------------------------------------------------------------
 # the serving workload (--workload serve)
 # ---------------------------------------------------------------------------
 SERVE_METRIC = ("served encrypted-CNN images/s and p50/p99 latency (Poisson arrivals, image sides {64,128,256}, "
@@ -714,7 +806,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cnn", "matmul", "matmul_small", "serve"], default="cnn")
+    ap.add_argument("--workload", choices=["cnn", "matmul", "matmul_small", "layer28", "serve"], default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
     ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
     ap.add_argument("--serve-warmup", type=int, default=20, help="serve workload: warm-up requests")
@@ -732,6 +824,25 @@ def main():
     cfg = {"workload": WORKLOAD, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+
+    if args.workload == "layer28" and args.impl == "gpu":
+        res = run_layer28(args, rank, world, local_rank)
+        if rank == 0:
+            line = {"metric": LAYER28_METRIC, "value": res["value"], "unit": "images/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                    "data": "synthetic",
+                    "config": {"workload": "Table I CONV (4 kernels 3x3, stride 1, weights N(0,0.1)) + ACT-1 on "
+                                           "28x28 images U[0,1]; RNS-CKKS N=2^16, Q=60+12x45, P=2x60, alpha=2",
+                               "parallelism": f"replicas x{world}"},
+                    "path": "column layout (1024 images per set of 28 column ciphertexts, he_conv2d + he_poly_act)",
+                    "gpu_launches": res["launches"],
+                    "single_ciphertext": {"value": res["single_value"], "ms": res["single_ms"],
+                                          "images_per_ciphertext": 32, "gpu_launches": res["single_launches"],
+                                          "path": "Alg. 4 per kernel (he_vr_conv2d) + he_poly_act"},
+                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_layer_error(res["checks"])}
+            print(json.dumps(line))
+        return
 
     if args.workload == "matmul_small" and args.impl == "gpu":
         res = run_matmul_small(args, rank, world, local_rank)

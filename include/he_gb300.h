@@ -223,6 +223,64 @@ int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he
 int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* weights, const double* bias,
               int c_out, int k, int stride, he_ctset** out);
 
+/* ---- the paper's single-ciphertext method (Sec. III-C/D): images in one ciphertext ----
+ *
+ * Layout (virtual ciphertexts, Sec. III-D): image b of a batch is row-major
+ * inside a block of block_h x block_w slots starting at slot (b mod per)
+ * block_h block_w of ciphertext b / per, per = (N/2) / (block_h block_w);
+ * row r at + r block_w. Rot by pos and by pos block_w move one column / row in
+ * every block at once.
+ *
+ * he_vr_encrypt_images: px [batch][h][w] -> ceil(batch / per) ciphertexts.
+ *
+ * he_vr_encrypt_kernels: the model provider's Kernelspanner (Sec. III-C) for a
+ * k x k kernel K (row-major) and bias k0 on h x w images: k^2 ciphertexts at
+ * `limbs` limbs, offset (r, c) at index r k + c, holding K tiled from (r, c) at
+ * every position where a whole copy fits (scale q_{limbs-1}); and one bias
+ * ciphertext at limbs - 2 limbs holding k0 at every valid output position
+ * (scale of the context). Ids ct_id_base + t, bias ct_id_base + k^2.
+ *
+ * he_vr_conv2d: Alg. 4 over every input ciphertext: for each offset t,
+ * T = relin(rescale(X (x) S_t)), U = sum_{pos < k} Rot(T, pos), V = U + sum_{1
+ * <= pos < k} Rot(U, pos block_w) (SumForConv, Alg. 1, its row pass on the
+ * column sums), acc += rescale(V (x) F_t) with F_t Alg. 4's offset mask
+ * ((hth - r) mod k = 0, (wth - c) mod k = 0, hth + k <= h, wth + k <= w, at
+ * scale q_{l-1}), acc starting from the bias ciphertext. Output: valid
+ * convolution (no kernel flip) at positions hth <= h - k, wth <= w - k of each
+ * block, two levels down, the input's scale. Needs rotation keys for steps
+ * 1..k-1 and block_w .. (k-1) block_w. he_vr_conv2d_coeffs takes the k^2 masks
+ * as encoded integer plaintexts [k^2][N] at scale q_{l-1} instead.
+ */
+/*
+ * Alg. 3 with one ciphertext per operand (the paper's single-ciphertext matmul).
+ * he_vr_encrypt_matrix_a: tau_a, A [m][n] row-major at slots i n + j (m n <= N/2).
+ * he_vr_encrypt_matrix_b: tau_b tiled over the whole ring, slot i n + j holds
+ * B[j][i mod p] for every row i < N/(2n) (n | N/2, p | N/(2n)); then
+ * RowShifter applied idx times is Rot(., idx n) (the m mod p = 0 case, Sec. III-B).
+ * he_vr_matmul: for idx < p, T = relin(rescale(A (x) Rot(Bbar, idx n))),
+ * SumColVec (T += Rot(T, t), t = 1, 2, .., n/2; rescale(T (x) E) with E the
+ * column-0 mask at scale q_{l-2}; T += Rot(T, -t)), acc += rescale(T (x) F_idx)
+ * with F_idx keeping slot i n + ((i + idx) mod p), i < m, at scale q_{l-3}.
+ * C[i][c] ends at slot i n + c (c < p <= n), three levels down, scale
+ * D D / q_{l-1}. n must be a power of two. Keys: steps idx n (idx < p) and
+ * +-1, +-2, .., +-n/2. he_vr_matmul_coeffs takes the plaintexts as encoded
+ * integers [1 + p][N] (E, then F_idx).
+ */
+int he_vr_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out);
+int he_vr_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out);
+int he_vr_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, he_ctset** out);
+int he_vr_matmul_coeffs(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, const int64_t* masks,
+                        he_ctset** out);
+
+int he_vr_encrypt_images(he_ctx* ctx, const double* px, int batch, int h, int w, int block_h, int block_w,
+                         uint64_t ct_id_base, he_ctset** out);
+int he_vr_encrypt_kernels(he_ctx* ctx, const double* K, int k, double k0, int h, int w, int block_h, int block_w,
+                          int limbs, uint64_t ct_id_base, he_ctset** kernels, he_ctset** bias);
+int he_vr_conv2d(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int h, int w, int k,
+                 int block_h, int block_w, he_ctset** out);
+int he_vr_conv2d_coeffs(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int k,
+                        int block_w, const int64_t* masks, he_ctset** out);
+
 /*
  * he_reform: ReForm (Sec. IV-C) in the column layout. After a strided layer
  * row i of image block b sits at slot b * block_stride + gap * i; ReForm moves

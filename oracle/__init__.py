@@ -70,6 +70,10 @@ def _lib():
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
             "oc_matmul_volley": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_vr_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p,
+                                            _u64p]),
+            "oc_vr_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p, _u64p,
+                                            ctypes.c_int, ctypes.c_int, _i64p, _u64p]),
             "oc_reform": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          _i64p, _u64p]),
             "oc_matmul_bsgs": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -318,6 +322,30 @@ class Oracle:
         n, _, lp, _ = A.shape
         out = np.zeros((p, 2, lp - 1, self.N), np.uint64)
         _check(self.lib.oc_matmul_bsgs(self.h, _p(A, _u64p), _p(B, _u64p), n, p, g, lp, _p(out, _u64p)))
+        return out
+
+    def vr_matmul(self, A, Bbar, n: int, p: int, masks) -> np.ndarray:
+        """Alg. 3 on one ciphertext per operand: A, Bbar [2][lp][N] -> [2][lp-3][N]. masks [1 + p][N]:
+        the column-0 mask of SumColVec encoded at scale q_{lp-2}, then the masks F_idx at scale
+        q_{lp-3} (layouts.vr_matmul_masks)."""
+        A, Bbar = _u64(A), _u64(Bbar)
+        lp = A.shape[1]
+        masks = np.ascontiguousarray(masks, dtype=np.int64)
+        out = np.zeros((2, lp - 3, self.N), np.uint64)
+        _check(self.lib.oc_vr_matmul(self.h, _p(A, _u64p), _p(Bbar, _u64p), lp, n, p, _p(masks, _i64p),
+                                     _p(out, _u64p)))
+        return out
+
+    def vr_conv2d(self, X, S, bias, k: int, Wb: int, masks) -> np.ndarray:
+        """Alg. 4 over one-ciphertext image blocks: X [n][2 or 3][lp][N], kernel ciphertexts
+        S [k*k][2][lp][N] (scale q_{lp-1}), bias ciphertext [2][lp-2][N], mask plaintexts
+        [k*k][N] (scale q_{lp-2}) -> [n][2][lp-2][N]."""
+        X, S, bias = _u64(X), _u64(S), _u64(bias)
+        n, polys, lp, _ = X.shape
+        masks = np.ascontiguousarray(masks, dtype=np.int64)
+        out = np.zeros((n, 2, lp - 2, self.N), np.uint64)
+        _check(self.lib.oc_vr_conv2d(self.h, _p(X, _u64p), n, polys, lp, _p(S, _u64p), _p(bias, _u64p), k, Wb,
+                                     _p(masks, _i64p), _p(out, _u64p)))
         return out
 
     def reform_masks(self, h: int, H: int, lp: int) -> np.ndarray:

@@ -118,3 +118,102 @@ def matmul_from_volley(d: np.ndarray, m: int, p: int) -> np.ndarray:
             for i in range(m):
                 C[i, (i + idx) % p] = d[g, t * M + off[g] + i]
     return C
+
+
+# ---------------------------------------------------------------------------
+# single-ciphertext layout of the paper's original method (virtual ciphertexts)
+# ---------------------------------------------------------------------------
+# Sec. III-D packs several images into one ciphertext as virtual ciphertexts; in
+# this reading image b is row-major inside a block of Hb x Wb slots starting at
+# slot b Hb Wb (row r at b Hb Wb + r Wb), zeros elsewhere, so Rot by pos and by
+# pos Wb move one column / one row inside every block at once (Alg. 1, Alg. 4).
+
+def vr_images(images: np.ndarray, slots: int, Hb: int, Wb: int) -> np.ndarray:
+    """images [B][h][w] -> slot vectors [n_ct][slots] (slots // (Hb Wb) images per ciphertext)."""
+    B, h, w = images.shape
+    per = slots // (Hb * Wb)
+    if per < 1 or h > Hb or w > Wb:
+        raise ValueError("images do not fit the blocks")
+    n_ct = -(-B // per)
+    z = np.zeros((n_ct, slots))
+    for b in range(B):
+        base = (b % per) * Hb * Wb
+        for r in range(h):
+            z[b // per, base + r * Wb: base + r * Wb + w] = images[b, r]
+    return z
+
+
+def vr_images_from(z: np.ndarray, B: int, h: int, w: int, Hb: int, Wb: int) -> np.ndarray:
+    """slot vectors [n_ct][slots] -> [B][h][w] (the top-left h x w of every block)."""
+    per = z.shape[-1] // (Hb * Wb)
+    out = np.zeros((B, h, w))
+    for b in range(B):
+        base = (b % per) * Hb * Wb
+        for r in range(h):
+            out[b, r] = z[b // per, base + r * Wb: base + r * Wb + w]
+    return out
+
+
+def _blocks(mat: np.ndarray, slots: int, Hb: int, Wb: int) -> np.ndarray:
+    """an h x w matrix replicated into every block -> slot vector"""
+    h, w = mat.shape
+    v = np.zeros(slots)
+    for b in range(slots // (Hb * Wb)):
+        for r in range(h):
+            v[b * Hb * Wb + r * Wb: b * Hb * Wb + r * Wb + w] = mat[r]
+    return v
+
+
+def vr_kernelspanner(K: np.ndarray, h: int, w: int, slots: int, Hb: int, Wb: int) -> np.ndarray:
+    """Kernelspanner (Sec. III-C) in every block: [k*k][slots], offset (r, c) at index r k + c."""
+    from .slot_sim import kernelspanner
+    P = kernelspanner(K, h, w)
+    k = K.shape[0]
+    return np.stack([_blocks(P[(r, c)], slots, Hb, Wb) for r in range(k) for c in range(k)])
+
+
+def vr_masks(k: int, h: int, w: int, slots: int, Hb: int, Wb: int) -> np.ndarray:
+    """Alg. 4's offset masks in every block: [k*k][slots], offset (r, c) at index r k + c."""
+    from .slot_sim import offset_mask
+    return np.stack([_blocks(offset_mask(h, w, k, r, c).reshape(h, w), slots, Hb, Wb)
+                     for r in range(k) for c in range(k)])
+
+
+def vr_bias(k0: float, k: int, h: int, w: int, slots: int, Hb: int, Wb: int) -> np.ndarray:
+    """Alg. 4's initial accumulator: k0 at every valid output position of every block."""
+    from .slot_sim import bias_block
+    return _blocks(bias_block(k0, h, w, k), slots, Hb, Wb)
+
+
+def vr_matrix_a(A: np.ndarray, slots: int) -> np.ndarray:
+    """tau_a (Sec. III-A): A [m][n] row-major, slot i n + j = A[i][j]."""
+    m, n = A.shape
+    z = np.zeros(slots)
+    z[: m * n] = A.reshape(-1)
+    return z
+
+
+def vr_matrix_b(Bm: np.ndarray, slots: int) -> np.ndarray:
+    """tau_b (Sec. III-A) over the whole ring: B transposed and tiled by rows with period p,
+    slot i n + j = B[j][i mod p] for every row i < slots / n (whole-ring tiling, so that Rot by
+    idx n is RowShifter applied idx times)."""
+    n, p = Bm.shape
+    rows = slots // n
+    if slots % n or rows % p:
+        raise ValueError("n must divide the slots and p the row count")
+    return np.stack([Bm[:, i % p] for i in range(rows)]).reshape(-1)
+
+
+def vr_matmul_masks(m: int, n: int, p: int, slots: int) -> np.ndarray:
+    """Alg. 3's plaintexts: [0] the column-0 mask of SumColVec (1 at slots i n, i < m), then for
+    idx < p the mask F_idx keeping slot i n + ((i + idx) mod p), i < m -> [1 + p][slots]."""
+    out = np.zeros((1 + p, slots))
+    out[0, np.arange(m) * n] = 1.0
+    for idx in range(p):
+        out[1 + idx, np.arange(m) * n + (np.arange(m) + idx) % p] = 1.0
+    return out
+
+
+def vr_matmul_from(z: np.ndarray, m: int, n: int, p: int) -> np.ndarray:
+    """Alg. 3's result slot vector -> C [m][p] (C[i][c] at slot i n + c)."""
+    return np.stack([z[i * n: i * n + p] for i in range(m)])

@@ -122,6 +122,62 @@ static std::vector<Ct> conv2d_enc(Ctx& C, const std::vector<std::vector<Ct>>& X,
   return out;
 }
 
+// Alg. 4 on one ciphertext holding images in row-major blocks of width Wb (the
+// paper's single-ciphertext convolution over virtual ciphertexts, Sec. III-C/D).
+// For each kernel offset t = r k + c (order t = 0 .. k^2-1):
+//   T = relin(rescale(X (x) S_t))                     (S_t the Kernelspanner ciphertext)
+//   U = sum_{pos < k} Rot(T, pos)                     (column pass of SumForConv, Alg. 1)
+//   V = U + sum_{1 <= pos < k} Rot(U, pos Wb)         (row pass on the column sums)
+//   acc += rescale(V (x) F_t)                         (F_t the offset mask)
+// starting from acc = the encrypted bias block. Rotations of T and of U are hoisted.
+static Ct vr_conv2d(Ctx& C, const Ct& x_any, const std::vector<Ct>& S, const Ct& bias, int k, int Wb,
+                    const int64_t* masks) {
+  const Ct x = two_comp(C, x_any);
+  std::vector<long> col(k), row(k);
+  for (int pos = 0; pos < k; pos++) {
+    col[pos] = pos;
+    row[pos] = (long)pos * Wb;
+  }
+  Ct acc = bias;
+  for (int t = 0; t < k * k; t++) {
+    const Ct T = ct_relin(C, ct_rescale(C, ct_tensor(C, x, S[t])));
+    std::vector<Ct> rc = ct_rotate_hoisted(C, T, col);
+    Ct U = rc[0];
+    for (int pos = 1; pos < k; pos++) U = ct_add(C, U, rc[pos]);
+    std::vector<Ct> rr = ct_rotate_hoisted(C, U, row);
+    Ct V = rr[0];
+    for (int pos = 1; pos < k; pos++) V = ct_add(C, V, rr[pos]);
+    std::vector<i64> m(masks + (size_t)t * C.N, masks + (size_t)(t + 1) * C.N);
+    acc = ct_add(C, acc, ct_rescale(C, ct_mul_plain(C, V, m)));
+  }
+  return acc;
+}
+
+// Alg. 3 on one ciphertext per operand (the paper's single-ciphertext matmul):
+// A row-major (tau_a), Bbar = tau_b(B) tiled over the whole ring. For idx < p:
+//   T = relin(rescale(A (x) Rot(Bbar, idx n)))     (RowShifter applied idx times)
+//   T = SumColVec(T): T += Rot(T, t) for t = 1, 2, .., n/2 (row sums in column 0);
+//       T = rescale(T (x) E) with E the column-0 mask; T += Rot(T, -t) for t = 1, .., n/2
+//   acc += rescale(T (x) F_idx), F_idx keeping slot i n + ((i + idx) mod p)
+// so C[i][c] ends at slot i n + c. masks [1 + p][N]: E (scale q_{l-2}), then F_idx (q_{l-3}).
+static Ct vr_matmul(Ctx& C, const Ct& A_any, const Ct& Bbar, int n, int p, const int64_t* masks) {
+  const Ct A = two_comp(C, A_any);
+  std::vector<long> shifts(p);
+  for (int idx = 0; idx < p; idx++) shifts[idx] = (long)idx * n;
+  const std::vector<Ct> R = ct_rotate_hoisted(C, Bbar, shifts);
+  auto mask = [&](int t) { return std::vector<i64>(masks + (size_t)t * C.N, masks + (size_t)(t + 1) * C.N); };
+  Ct acc;
+  for (int idx = 0; idx < p; idx++) {
+    Ct T = ct_relin(C, ct_rescale(C, ct_tensor(C, A, R[idx])));
+    for (int t = 1; t < n; t *= 2) T = ct_add(C, T, ct_rotate_hoisted(C, T, {(long)t})[0]);
+    T = ct_rescale(C, ct_mul_plain(C, T, mask(0)));
+    for (int t = 1; t < n; t *= 2) T = ct_add(C, T, ct_rotate_hoisted(C, T, {-(long)t})[0]);
+    const Ct D = ct_rescale(C, ct_mul_plain(C, T, mask(1 + idx)));
+    acc = idx == 0 ? D : ct_add(C, acc, D);
+  }
+  return acc;
+}
+
 // ReForm (Sec. IV-C) in the column layout: after a strided layer row i of every
 // block sits at slot b H + g i; ReForm moves it to b H + i. A left rotation by
 // (g - 1) i brings slot b H + g i to b H + i, so
@@ -397,6 +453,34 @@ int oc_conv2d_enc(void* h, const uint64_t* X, int polys, int lp, int c_in, int w
          }
          std::vector<Ct> r = conv2d_enc(*C, x, gap, w, bias, c_out, k, stride, scale, s);
          cts_to(*C, r, out));
+}
+
+// A, Bbar [2][lp][N] (one ciphertext each); masks [1 + p][N] -> out [2][lp-3][N]
+int oc_vr_matmul(void* h, const uint64_t* A, const uint64_t* Bbar, int lp, int n, int p, const int64_t* masks,
+                 uint64_t* out) {
+  OL_TRY(Ctx* C = (Ctx*)h; if (lp < 4 || n < 1 || p < 1) throw std::runtime_error("bad single-ciphertext matmul shape");
+         const Ct r = vr_matmul(*C, cts_from(*C, A, 1, lp)[0], cts_from(*C, Bbar, 1, lp)[0], n, p, masks);
+         cts_to(*C, std::vector<Ct>{r}, out));
+}
+
+// X [n][polys][lp][N]; S [k*k][2][lp][N]; bias [2][lp-2][N]; masks [k*k][N] -> out [n][2][lp-2][N]
+int oc_vr_conv2d(void* h, const uint64_t* X, int n, int polys, int lp, const uint64_t* S, const uint64_t* bias, int k,
+                 int Wb, const int64_t* masks, uint64_t* out) {
+  try {
+    Ctx* C = (Ctx*)h;
+    if (k < 1 || lp < 3) throw std::runtime_error("bad single-ciphertext convolution shape");
+    std::vector<Ct> x = cts_from(*C, X, n, lp, polys);
+    std::vector<Ct> s = cts_from(*C, S, k * k, lp);
+    const Ct b = cts_from(*C, bias, 1, lp - 2)[0];
+    std::vector<Ct> r(n);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < n; t++) r[t] = vr_conv2d(*C, x[t], s, b, k, Wb, masks);
+    cts_to(*C, r, out);
+    return 0;
+  } catch (const std::exception& e) {
+    g_lerr = e.what();
+    return -1;
+  }
 }
 
 // X [n][polys][lp][N] at row gap `gap`, masks [h][N] -> out [n][2][lp-1][N] at gap 1

@@ -71,6 +71,14 @@ SIGNATURES = {
     "he_matmul_volley": (I, [V, V, V, PV]),
     "he_matmul_bsgs": (I, [V, V, V, I, I, I, PV]),
     "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
+    "he_vr_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
+    "he_vr_encrypt_matrix_b": (I, [V, P_D, I, I, U64, PV]),
+    "he_vr_matmul": (I, [V, V, V, I, I, I, PV]),
+    "he_vr_matmul_coeffs": (I, [V, V, V, I, I, I, P_I64, PV]),
+    "he_vr_encrypt_images": (I, [V, P_D, I, I, I, I, I, U64, PV]),
+    "he_vr_encrypt_kernels": (I, [V, P_D, I, D, I, I, I, I, I, U64, PV, PV]),
+    "he_vr_conv2d": (I, [V, V, V, V, I, I, I, I, I, PV]),
+    "he_vr_conv2d_coeffs": (I, [V, V, V, V, I, I, P_I64, PV]),
     "he_reform": (I, [V, V, I, I, I, PV]),
     "he_reform_coeffs": (I, [V, V, I, I, P_I64, PV]),
     "he_encrypt_conv_weights": (I, [V, P_D, I, I, I, I, U64, PV]),

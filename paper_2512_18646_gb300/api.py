@@ -271,6 +271,43 @@ class Context:
         return self._set(load().he_conv2d, self.h, x.h, c_in, gap, _ptr(W, P_D), None if b is None else _ptr(b, P_D),
                          c_out, k, stride)
 
+    def vr_encrypt_matrix_a(self, A, ct_id_base: int = 0) -> CtSet:
+        A = _f64(A)
+        return self._set(load().he_vr_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)
+
+    def vr_encrypt_matrix_b(self, B, ct_id_base: int = 0) -> CtSet:
+        B = _f64(B)
+        return self._set(load().he_vr_encrypt_matrix_b, self.h, _ptr(B, P_D), B.shape[0], B.shape[1], ct_id_base)
+
+    def vr_matmul(self, A: CtSet, Bbar: CtSet, m: int, n: int, p: int) -> CtSet:
+        return self._set(load().he_vr_matmul, self.h, A.h, Bbar.h, m, n, p)
+
+    def vr_matmul_coeffs(self, A: CtSet, Bbar: CtSet, m: int, n: int, p: int, masks) -> CtSet:
+        mm = np.ascontiguousarray(masks, dtype=np.int64)
+        return self._set(load().he_vr_matmul_coeffs, self.h, A.h, Bbar.h, m, n, p, _ptr(mm, P_I64))
+
+    def vr_encrypt_images(self, px, block_h: int, block_w: int, ct_id_base: int = 0) -> CtSet:
+        px = _f64(px)
+        b, h, w = px.shape
+        return self._set(load().he_vr_encrypt_images, self.h, _ptr(px, P_D), b, h, w, block_h, block_w, ct_id_base)
+
+    def vr_encrypt_kernels(self, K, k0: float, h: int, w: int, block_h: int, block_w: int,
+                           limbs: Optional[int] = None, ct_id_base: int = 0):
+        K = _f64(K)
+        ks, bs = ctypes.c_void_p(), ctypes.c_void_p()
+        check(load().he_vr_encrypt_kernels(self.h, _ptr(K, P_D), K.shape[0], float(k0), h, w, block_h, block_w,
+                                           self.L1 if limbs is None else limbs, ct_id_base, ctypes.byref(ks),
+                                           ctypes.byref(bs)))
+        return CtSet(self, ks.value), CtSet(self, bs.value)
+
+    def vr_conv2d(self, x: CtSet, kernels: CtSet, bias: CtSet, h: int, w: int, k: int, block_h: int,
+                  block_w: int) -> CtSet:
+        return self._set(load().he_vr_conv2d, self.h, x.h, kernels.h, bias.h, h, w, k, block_h, block_w)
+
+    def vr_conv2d_coeffs(self, x: CtSet, kernels: CtSet, bias: CtSet, k: int, block_w: int, masks) -> CtSet:
+        m = np.ascontiguousarray(masks, dtype=np.int64)
+        return self._set(load().he_vr_conv2d_coeffs, self.h, x.h, kernels.h, bias.h, k, block_w, _ptr(m, P_I64))
+
     def reform(self, x: CtSet, gap: int, h_valid: int, block_stride: int) -> CtSet:
         return self._set(load().he_reform, self.h, x.h, gap, h_valid, block_stride)
 

@@ -372,6 +372,177 @@ int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int
   return rc;
 }
 
+// ---- the paper's single-ciphertext layout (virtual ciphertexts, Sec. III-C/D) ----
+// an h x w matrix (row-major, doubles) replicated into every Hb x Wb block of a slot vector
+static void vr_blocks(const std::vector<double>& mat, int h, int w, int Hb, int Wb, long S, double* z) {
+  for (long b = 0; b < S / ((long)Hb * Wb); b++)
+    for (int r = 0; r < h; r++)
+      for (int c = 0; c < w; c++) z[b * Hb * Wb + (long)r * Wb + c] = mat[(size_t)r * w + c];
+}
+
+static void vr_check(const Ctx& C, int h, int w, int k, int Hb, int Wb) {
+  const long S = (long)C.N / 2;
+  if (h < 1 || w < 1 || k < 1 || k > h || k > w || Hb < h || Wb < w || (long)Hb * Wb > S)
+    throw Error(HE_E_ARG, "image, kernel or block sizes do not fit");
+}
+
+int he_vr_encrypt_images(he_ctx* ctx, const double* px, int batch, int h, int w, int block_h, int block_w,
+                         uint64_t ct_id_base, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && px && out && batch >= 1, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    vr_check(C, h, w, 1, block_h, block_w);
+    const long S = (long)C.N / 2, per = S / ((long)block_h * block_w);
+    const int n_ct = (int)((batch + per - 1) / per);
+    std::vector<double> z((size_t)n_ct * S, 0.0);
+    for (int b = 0; b < batch; b++) {
+      const long base = (b / per) * S + (b % per) * block_h * block_w;
+      for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) z[base + (long)r * block_w + c] = px[((size_t)b * h + r) * w + c];
+    }
+    *out = wrap(encrypt_slots(C, z, n_ct, ct_id_base));
+  });
+}
+
+int he_vr_encrypt_kernels(he_ctx* ctx, const double* K, int k, double k0, int h, int w, int block_h, int block_w,
+                          int limbs, uint64_t ct_id_base, he_ctset** kernels, he_ctset** bias) {
+  return guard([&] {
+    REQUIRE(ctx && K && kernels && bias, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    vr_check(C, h, w, k, block_h, block_w);
+    REQUIRE(limbs >= 3 && limbs <= C.L1, HE_E_LEVEL, "bad level");
+    const long S = (long)C.N / 2;
+    const int T = k * k;
+    // Kernelspanner (Sec. III-C): for offset (r, c) the kernel tiled from (r, c) wherever a copy fits
+    std::vector<double> z((size_t)T * S, 0.0);
+    for (int r = 0; r < k; r++)
+      for (int c = 0; c < k; c++) {
+        std::vector<double> P((size_t)h * w, 0.0);
+        for (int top = r; top + k <= h; top += k)
+          for (int left = c; left + k <= w; left += k)
+            for (int a = 0; a < k; a++)
+              for (int b = 0; b < k; b++) P[(size_t)(top + a) * w + left + b] = K[a * k + b];
+        vr_blocks(P, h, w, block_h, block_w, S, z.data() + (size_t)(r * k + c) * S);
+      }
+    const double ql = (double)C.q[limbs - 1];
+    std::vector<int64_t> m((size_t)T * C.N);
+    host_parallel((size_t)T, [&](size_t t) { encode_real(C, z.data() + t * S, (size_t)S, ql, m.data() + t * C.N); });
+    auto ks = encrypt_coeffs(C, m.data(), T, limbs, ql, ct_id_base);
+    // the initial accumulator of Alg. 4: k0 at every valid output position
+    std::vector<double> B((size_t)h * w, 0.0), zb(S, 0.0);
+    for (int r = 0; r + k <= h; r++)
+      for (int c = 0; c + k <= w; c++) B[(size_t)r * w + c] = k0;
+    vr_blocks(B, h, w, block_h, block_w, S, zb.data());
+    std::vector<int64_t> mb(C.N);
+    encode_real(C, zb.data(), (size_t)S, C.scale0, mb.data());
+    auto bs = encrypt_coeffs(C, mb.data(), 1, limbs - 2, C.scale0, ct_id_base + (uint64_t)T);
+    *kernels = wrap(std::move(ks));
+    *bias = wrap(std::move(bs));
+  });
+}
+
+int he_vr_conv2d_coeffs(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int k,
+                        int block_w, const int64_t* masks, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && kernels && bias && masks && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 3, HE_E_LEVEL, "the single-ciphertext convolution needs two levels");
+    DevBuf m = fc_prepare(C, masks, 1, k * k, lp - 1);
+    *out = wrap(vr_conv2d(C, *in->s, *kernels->s, *bias->s, k, block_w, m.p));
+  });
+}
+
+int he_vr_conv2d(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int h, int w, int k,
+                 int block_h, int block_w, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && kernels && bias && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    vr_check(C, h, w, k, block_h, block_w);
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 3, HE_E_LEVEL, "the single-ciphertext convolution needs two levels");
+    const long S = (long)C.N / 2;
+    const int T = k * k;
+    // Alg. 4's offset masks: (hth - r) mod k = 0, (wth - c) mod k = 0, hth + k <= h, wth + k <= w
+    std::vector<double> z((size_t)T * S, 0.0);
+    for (int r = 0; r < k; r++)
+      for (int c = 0; c < k; c++) {
+        std::vector<double> F((size_t)h * w, 0.0);
+        for (int hth = r; hth + k <= h; hth += k)
+          for (int wth = c; wth + k <= w; wth += k) F[(size_t)hth * w + wth] = 1.0;
+        vr_blocks(F, h, w, block_h, block_w, S, z.data() + (size_t)(r * k + c) * S);
+      }
+    const double ql = (double)C.q[lp - 2];
+    std::vector<int64_t> m((size_t)T * C.N);
+    host_parallel((size_t)T, [&](size_t t) { encode_real(C, z.data() + t * S, (size_t)S, ql, m.data() + t * C.N); });
+    DevBuf dm = fc_prepare(C, m.data(), 1, T, lp - 1);
+    *out = wrap(vr_conv2d(C, *in->s, *kernels->s, *bias->s, k, block_w, dm.p));
+  });
+}
+
+int he_vr_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(m >= 1 && n >= 1 && (long)m * n <= S, HE_E_ARG, "A does not fit one ciphertext");
+    std::vector<double> z(S, 0.0);
+    for (long t = 0; t < (long)m * n; t++) z[t] = A[t];  // tau_a: row-major
+    *out = wrap(encrypt_slots(C, z, 1, ct_id_base));
+  });
+}
+
+int he_vr_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && B && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(n >= 1 && p >= 1 && S % n == 0 && (S / n) % p == 0, HE_E_ARG,
+            "n must divide the slot count and p the number of rows");
+    std::vector<double> z(S);
+    for (long s = 0; s < S; s++) z[s] = B[(size_t)(s % n) * p + (s / n) % p];  // tau_b tiled over the ring
+    *out = wrap(encrypt_slots(C, z, 1, ct_id_base));
+  });
+}
+
+static std::unique_ptr<CtSet> vr_matmul_from_host(Ctx& C, const CtSet& A, const CtSet& Bb, int n, int p,
+                                                  const int64_t* masks) {
+  const int lp = A.limbs;
+  if (lp < 4) throw Error(HE_E_LEVEL, "the single-ciphertext matmul needs three levels");
+  DevBuf E = fc_prepare(C, masks, 1, 1, lp - 1);
+  DevBuf F = fc_prepare(C, masks + C.N, 1, p, lp - 2);
+  return vr_matmul(C, A, Bb, n, p, E.p, F.p);
+}
+
+int he_vr_matmul_coeffs(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, const int64_t* masks,
+                        he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && A && Bbar && masks && out, HE_E_ARG, "null argument");
+    REQUIRE(m >= 1 && (long)m * n <= (long)ctx->c.N / 2, HE_E_ARG, "bad shape");
+    *out = wrap(vr_matmul_from_host(ctx->c, *A->s, *Bbar->s, n, p, masks));
+  });
+}
+
+int he_vr_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && A && Bbar && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(m >= 1 && (long)m * n <= S && p >= 1 && p <= n, HE_E_ARG, "bad shape");
+    const int lp = A->s->limbs;
+    REQUIRE(lp >= 4, HE_E_LEVEL, "the single-ciphertext matmul needs three levels");
+    std::vector<double> z((size_t)(1 + p) * S, 0.0);
+    for (int i = 0; i < m; i++) z[(size_t)i * n] = 1.0;  // SumColVec's column-0 mask
+    for (int idx = 0; idx < p; idx++)
+      for (int i = 0; i < m; i++) z[(size_t)(1 + idx) * S + (size_t)i * n + (i + idx) % p] = 1.0;  // Alg. 3's F
+    std::vector<int64_t> m_((size_t)(1 + p) * C.N);
+    host_parallel((size_t)(1 + p), [&](size_t t) {
+      encode_real(C, z.data() + t * S, (size_t)S, (double)C.q[t == 0 ? lp - 2 : lp - 3], m_.data() + t * C.N);
+    });
+    *out = wrap(vr_matmul_from_host(C, *A->s, *Bbar->s, n, p, m_.data()));
+  });
+}
+
 int he_reform_coeffs(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, const int64_t* masks, he_ctset** out) {
   return guard([&] {
     REQUIRE(ctx && in && masks && out, HE_E_ARG, "null argument");

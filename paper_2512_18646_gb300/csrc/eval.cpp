@@ -473,6 +473,118 @@ std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, in
   return d;
 }
 
+// Alg. 4 on one-ciphertext image blocks (the paper's single-ciphertext convolution
+// over virtual ciphertexts, Sec. III-C/D): images row-major in blocks of width Wb;
+// S [k^2] the Kernelspanner ciphertexts (scale q_l), bias the encrypted bias block
+// (level l - 2, scale D), masks [k^2][l - 1][N] the offset masks (NTT domain, scale
+// q_{l-1}). For each offset t = r k + c and each input ciphertext:
+//   T = relin(rescale(X (x) S_t)); U = sum_{pos < k} Rot(T, pos);
+//   V = U + sum_{1 <= pos < k} Rot(U, pos Wb); acc += rescale(V (x) F_t)
+// with hoisted rotations of T and of U (SumForConv, Alg. 1, with its row pass on
+// the column sums). Output: n ciphertexts at level l - 2, scale D.
+std::unique_ptr<CtSet> vr_conv2d(Ctx& C, const CtSet& in_any, const CtSet& S, const CtSet& bias, int k, int Wb,
+                                 const u64* masks) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& in = two_comp(C, in_any, hold);
+  const int lp = in.limbs;
+  if (k < 1 || Wb < 1) throw Error(1, "bad kernel or block width");
+  if (lp < 3) throw Error(2, "the single-ciphertext convolution needs two levels");
+  if (S.n != k * k || S.limbs != lp || S.polys != 2) throw Error(1, "expected k^2 kernel ciphertexts at the input level");
+  if (bias.n != 1 || bias.limbs != lp - 2 || bias.polys != 2) throw Error(1, "expected one bias ciphertext two levels down");
+  const double D = in.scale;
+  std::vector<long> col(k), row(k);
+  for (int pos = 0; pos < k; pos++) {
+    col[pos] = pos;
+    row[pos] = (long)pos * Wb;
+  }
+  auto out = new_set(C, in.n, 2, lp - 2, D);
+  const size_t mw = (size_t)(lp - 1) * C.N;
+  for (int c = 0; c < in.n; c++) {
+    SetView xc(in, c, 1);
+    HE_CUDA(cudaMemcpyAsync(out->ct(c), bias.buf.p, bias.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+    for (int t = 0; t < k * k; t++) {
+      SetView st(S, t, 1);
+      auto T = mul(C, xc.s, st.s);
+      relinearize(C, *T);
+      auto R = rotate(C, *T, col);  // [1][k]
+      T.reset();
+      for (int pos = 1; pos < k; pos++) k_add(C, R->ct(0), R->ct(pos), R->ct(0), 2, lp - 1);
+      SetView U(*R, 0, 1);
+      auto R2 = rotate(C, U.s, row);
+      R.reset();
+      for (int pos = 1; pos < k; pos++) k_add(C, R2->ct(0), R2->ct(pos), R2->ct(0), 2, lp - 1);
+      // V (x) F_t, rescaled: the masked-sum kernel with one term
+      auto W = new_set(C, 1, 2, lp - 1, D);
+      const u64* xs0 = R2->ct(0);
+      DevBuf dxs(1, C.stream);
+      HE_CUDA(cudaMemcpyAsync(dxs.p, &xs0, 8, cudaMemcpyHostToDevice, C.stream));
+      k_pack_blocks(C, (const u64* const*)dxs.p, masks + (size_t)t * mw, 1, 1, lp - 1, W->buf.p);
+      R2.reset();
+      rescale_inplace(C, *W);
+      k_add(C, out->ct(c), W->ct(0), out->ct(c), 2, lp - 2);
+    }
+  }
+  out->scale = D;  // kernels at scale q_l and masks at q_{l-1}, which the two rescales remove
+  return out;
+}
+
+// Alg. 3 with one ciphertext per operand (the paper's single-ciphertext matmul): A
+// row-major (tau_a), Bbar = tau_b(B) tiled over the whole ring, so RowShifter applied
+// idx times is Rot(Bbar, idx n). For idx < p:
+//   T = relin(rescale(A (x) Rot(Bbar, idx n)))
+//   SumColVec: T += Rot(T, t) (t = 1, 2, .., n/2: row sums in column 0);
+//              T = rescale(T (x) E); T += Rot(T, -t) (t = 1, .., n/2: replicated over the row)
+//   acc += rescale(T (x) F_idx), F_idx keeping slot i n + ((i + idx) mod p), i < m
+// E [lp-1][N] and F [p][lp-2][N] are NTT-domain plaintexts at scales q_{lp-2}, q_{lp-3}.
+// C[i][c] ends at slot i n + c; three levels; scale D D / q_{lp-1}.
+std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A_any, const CtSet& Bbar, int n, int p, const u64* E,
+                                 const u64* F) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& A = two_comp(C, A_any, hold);
+  const int lp = A.limbs;
+  if (A.n != 1 || Bbar.n != 1 || Bbar.polys != 2 || Bbar.limbs != lp) throw Error(1, "one ciphertext per operand");
+  if (lp < 4) throw Error(2, "the single-ciphertext matmul needs three levels");
+  if (n < 1 || (n & (n - 1)) || p < 1) throw Error(1, "n must be a power of two and p positive");
+  std::vector<long> shifts(p);
+  for (int idx = 0; idx < p; idx++) shifts[idx] = (long)idx * n;
+  auto R = rotate(C, Bbar, shifts);  // [1][p]
+  const double sc = (A.scale * Bbar.scale) / (double)C.q[lp - 1];
+  auto acc = new_set(C, 1, 2, lp - 3, sc);
+  const size_t fw = (size_t)(lp - 2) * C.N;
+  auto masked = [&](const CtSet& x, const u64* m) {  // rescale(x (x) m)
+    auto W = new_set(C, 1, 2, x.limbs, x.scale);
+    const u64* xs0 = x.buf.p;
+    DevBuf dxs(1, C.stream);
+    // pageable source: the call returns once the pointer is staged
+    HE_CUDA(cudaMemcpyAsync(dxs.p, &xs0, 8, cudaMemcpyHostToDevice, C.stream));
+    k_pack_blocks(C, (const u64* const*)dxs.p, m, 1, 1, x.limbs, W->buf.p);
+    rescale_inplace(C, *W);
+    W->scale = x.scale;
+    return W;
+  };
+  for (int idx = 0; idx < p; idx++) {
+    SetView ri(*R, idx, 1);
+    auto T = mul(C, A, ri.s);
+    relinearize(C, *T);
+    for (int t = 1; t < n; t *= 2) {
+      auto r = rotate(C, *T, {(long)t});
+      k_add(C, T->buf.p, r->buf.p, T->buf.p, 2, T->limbs);
+    }
+    auto U = masked(*T, E);
+    T.reset();
+    for (int t = 1; t < n; t *= 2) {
+      auto r = rotate(C, *U, {-(long)t});
+      k_add(C, U->buf.p, r->buf.p, U->buf.p, 2, U->limbs);
+    }
+    auto Dd = masked(*U, F + (size_t)idx * fw);
+    if (idx == 0)
+      HE_CUDA(cudaMemcpyAsync(acc->buf.p, Dd->buf.p, Dd->buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+    else
+      k_add(C, acc->buf.p, Dd->buf.p, acc->buf.p, 2, lp - 3);
+  }
+  return acc;
+}
+
 // ReForm (Sec. IV-C) in the column layout: a strided layer leaves row i of every
 // block at slot b H + g i; a left rotation by (g - 1) i brings it to b H + i, so
 // out = rescale(sum_{i < h} mask_i (x) Rot(X, (g - 1) i)) with mask_i the 0/1

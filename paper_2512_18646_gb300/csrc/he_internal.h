@@ -296,6 +296,12 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
 std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in, int c_in, int gap, const CtSet& Wct, const double* bias,
                                   int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// Alg. 3 with one ciphertext per operand: E [lp-1][N] column-0 mask, F [p][lp-2][N] (NTT domain); three levels
+std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A, const CtSet& Bbar, int n, int p, const u64* E, const u64* F);
+// Alg. 4 over one-ciphertext image blocks of width Wb: S [k^2] kernel ciphertexts (scale q_{l-1}), bias one
+// ciphertext two levels down, masks [k^2][l-1][N] offset masks (NTT domain); two levels
+std::unique_ptr<CtSet> vr_conv2d(Ctx& C, const CtSet& in, const CtSet& S, const CtSet& bias, int k, int Wb,
+                                 const u64* masks);
 // ReForm: rows at gap `gap` (slots b H + gap i, i < h) moved to gap 1; masks [h][limbs][N] (NTT domain,
 // 0/1 at slots b H + i, scale q_{limbs-1}); one level
 std::unique_ptr<CtSet> reform(Ctx& C, const CtSet& in, int gap, int h, const u64* masks);

@@ -320,6 +320,68 @@ def test_reform_matches_oracle(lib, gap, h, H):
     assert np.abs(g.decrypt_slots(g.reform(gx, gap, h, H)) - want).max() < 1e-5
 
 
+@pytest.mark.parametrize("h,w,k,Hb,Wb", [(6, 6, 3, 8, 8), (7, 5, 2, 8, 8), (12, 10, 3, 16, 16)])
+def test_vr_conv2d_matches_oracle_and_fp64(lib, h, w, k, Hb, Wb):
+    """The paper's single-ciphertext convolution (Alg. 4 with Kernelspanner and SumForConv) over
+    virtual image blocks: bit-exact with the oracle from the same plaintexts and seeds, decrypting to
+    FP64; the library's own encoders agree within tolerance."""
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=29,
+                     steps=list(range(1, k)) + [Wb * p for p in range(1, k)])
+    S = o.slots
+    rng = np.random.default_rng(h * 100 + k)
+    B = 2 * (S // (Hb * Wb))  # two ciphertexts of images
+    imgs = rng.uniform(0, 1, (B, h, w))
+    K = rng.normal(0, 0.4, (k, k))
+    k0 = 0.15
+    lp = o.L1
+    mx = encode_columns(o, layouts.vr_images(imgs, S, Hb, Wb))
+    ox, gx = encrypt_both(o, g, mx, ct_id_base=0)
+    ql = float(o.q[lp - 1])
+    ms = np.stack([o.encode(v, ql) for v in layouts.vr_kernelspanner(K, h, w, S, Hb, Wb)])
+    os_, gs = encrypt_both(o, g, ms, ct_id_base=20, scale=ql)
+    mb = o.encode(layouts.vr_bias(k0, k, h, w, S, Hb, Wb))[None]
+    ob, gb = encrypt_both(o, g, mb, limbs=lp - 2, ct_id_base=90)
+    masks = np.stack([o.encode(v, float(o.q[lp - 2])) for v in layouts.vr_masks(k, h, w, S, Hb, Wb)])
+    gy = g.vr_conv2d_coeffs(gx, gs, gb, k, Wb, masks)
+    oy = o.vr_conv2d(ox, os_, ob[0], k, Wb, masks)
+    assert np.array_equal(gy.export(), oy)
+    ref = fp64_ref.conv2d(imgs[:, None], K[None, None], np.array([k0]), 1)[:, 0]
+    ho, wo = h - k + 1, w - k + 1
+    got = layouts.vr_images_from(g.decrypt_slots(gy), B, h, w, Hb, Wb)
+    assert np.abs(got[:, :ho, :wo] - ref).max() < 1e-5
+    # the library's own encoders (images, Kernelspanner, bias, masks)
+    gx2 = g.vr_encrypt_images(imgs, Hb, Wb, 0)
+    gk2, gb2 = g.vr_encrypt_kernels(K, k0, h, w, Hb, Wb, lp, 20)
+    got2 = layouts.vr_images_from(g.decrypt_slots(g.vr_conv2d(gx2, gk2, gb2, h, w, k, Hb, Wb)), B, h, w, Hb, Wb)
+    assert np.abs(got2[:, :ho, :wo] - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("m,n,p", [(4, 8, 4), (8, 4, 2), (16, 16, 8)])
+def test_vr_matmul_matches_oracle_and_fp64(lib, m, n, p):
+    """The paper's single-ciphertext matmul (Alg. 3: tau_a, tau_b, RowShifter, SumColVec, mask F):
+    bit-exact with the oracle from the same plaintexts and seeds, decrypting to A @ B; the library's
+    own encoders agree within tolerance."""
+    steps = [idx * n for idx in range(1, p)] + [t for t in (1, 2, 4, 8, 16) if t < n] + \
+            [-t for t in (1, 2, 4, 8, 16) if t < n]
+    o, g = make_pair(10, (60, 40, 40, 40, 40), 1, 60, 1, 40.0, seed=31, steps=steps)
+    S = o.slots
+    rng = np.random.default_rng(m + n * 10 + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    lp = o.L1
+    oa, ga = encrypt_both(o, g, encode_columns(o, layouts.vr_matrix_a(A, S)[None]), ct_id_base=3)
+    ob, gb = encrypt_both(o, g, encode_columns(o, layouts.vr_matrix_b(Bm, S)[None]), ct_id_base=4)
+    mv = layouts.vr_matmul_masks(m, n, p, S)
+    masks = np.stack([o.encode(mv[0], float(o.q[lp - 2]))] + [o.encode(v, float(o.q[lp - 3])) for v in mv[1:]])
+    gd = g.vr_matmul_coeffs(ga, gb, m, n, p, masks)
+    od = o.vr_matmul(oa[0], ob[0], n, p, masks)
+    assert np.array_equal(gd.export()[0], od)
+    sc = o.scale ** 2 / o.q[lp - 1]
+    assert np.abs(layouts.vr_matmul_from(g.decrypt_slots(gd)[0], m, n, p) - A @ Bm).max() < 1e-5
+    gd2 = g.vr_matmul(g.vr_encrypt_matrix_a(A, 3), g.vr_encrypt_matrix_b(Bm, 4), m, n, p)
+    assert np.abs(layouts.vr_matmul_from(g.decrypt_slots(gd2)[0], m, n, p) - A @ Bm).max() < 1e-5
+    assert gd.scale == sc
+
+
 def _act_polynomials():
     from tests.test_oracle_pins import act_polynomials
     return act_polynomials()

@@ -574,6 +574,93 @@ def test_reform_compacts_rows(gap, h, H):
     assert np.abs(got - want).max() < 1e-6
 
 
+def _vr_conv_slots(x, P, F, bias_v, k, Wb):
+    """Alg. 4 on slot vectors (the slot simulator's steps, several image blocks at once)."""
+    acc = bias_v.copy()
+    for t in range(k * k):
+        acc = acc + slot_sim.sum_for_conv(x * P[t], 0, Wb, k) * F[t]
+    return acc
+
+
+@pytest.mark.parametrize("h,w,k,Hb,Wb", [(6, 5, 3, 8, 8), (7, 7, 2, 8, 8), (5, 6, 3, 8, 16)])
+def test_vr_layout_alg4_over_virtual_images(h, w, k, Hb, Wb):
+    """Alg. 4 over several images in one slot vector (row-major blocks of Hb x Wb, Sec. III-D):
+    every image's valid output equals its FP64 convolution plus the bias; invalid positions hold 0."""
+    slots = 256
+    rng = np.random.default_rng(h * 10 + k)
+    B = slots // (Hb * Wb)
+    imgs = rng.uniform(0, 1, (B, h, w))
+    K = rng.normal(0, 0.5, (k, k))
+    k0 = 0.3
+    x = layouts.vr_images(imgs, slots, Hb, Wb)[0]
+    P = layouts.vr_kernelspanner(K, h, w, slots, Hb, Wb)
+    F = layouts.vr_masks(k, h, w, slots, Hb, Wb)
+    bias_v = layouts.vr_bias(k0, k, h, w, slots, Hb, Wb)
+    out = _vr_conv_slots(x, P, F, bias_v, k, Wb)
+    got = layouts.vr_images_from(out[None], B, h, w, Hb, Wb)
+    ref = fp64_ref.conv2d(imgs[:, None], K[None, None], np.array([k0]), 1)[:, 0]
+    ho, wo = h - k + 1, w - k + 1
+    assert np.abs(got[:, :ho, :wo] - ref).max() < 1e-12
+    assert np.abs(got[:, ho:, :]).max() < 1e-12 and np.abs(got[:, :, wo:]).max() < 1e-12
+
+
+def test_vr_conv2d_encrypted_matches_fp64():
+    """Alg. 4 encrypted over virtual images (the paper's single-ciphertext convolution): kernel
+    ciphertexts at scale q_l, masks at scale q_{l-1}, encrypted bias; decrypts to FP64; k^2 tensor
+    products and relinearisations, 2 k^2 (k-1) rotations from 2 k^2 hoisted ModUps."""
+    o = Oracle(9, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=28)
+    h, w, k, Hb, Wb = 6, 6, 3, 8, 8
+    o.keygen(list(range(1, k)) + [Wb * p for p in range(1, k)])
+    S = o.slots
+    rng = np.random.default_rng(5)
+    B = S // (Hb * Wb)
+    imgs = rng.uniform(0, 1, (B, h, w))
+    K = rng.normal(0, 0.5, (k, k))
+    k0 = -0.2
+    lp = o.L1
+    X = o.encrypt(o.encode(layouts.vr_images(imgs, S, Hb, Wb)[0]), lp, 0)[None]
+    Sct = np.stack([o.encrypt(o.encode(v, float(o.q[lp - 1])), lp, 10 + t)
+                    for t, v in enumerate(layouts.vr_kernelspanner(K, h, w, S, Hb, Wb))])
+    bias = o.encrypt(o.encode(layouts.vr_bias(k0, k, h, w, S, Hb, Wb)), lp - 2, 99)
+    masks = np.stack([o.encode(v, float(o.q[lp - 2])) for v in layouts.vr_masks(k, h, w, S, Hb, Wb)])
+    o.reset_counters()
+    Y = o.vr_conv2d(X, Sct, bias, k, Wb, masks)
+    c = o.counters()
+    assert c["tensors"] == k * k and c["relins"] == k * k and c["ct_plain"] == k * k
+    assert c["rotations"] == 2 * k * k * (k - 1) and c["modups"] == 2 * k * k + k * k
+    got = layouts.vr_images_from(o.decrypt(Y[0])[None], B, h, w, Hb, Wb)
+    ref = fp64_ref.conv2d(imgs[:, None], K[None, None], np.array([k0]), 1)[:, 0]
+    assert np.abs(got[:, : h - k + 1, : w - k + 1] - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("m,n,p", [(4, 8, 4), (8, 4, 2), (3, 8, 8), (16, 4, 4)])
+def test_vr_matmul_single_ciphertext_matches_fp64(m, n, p):
+    """Alg. 3 with one ciphertext per operand (tau_a, tau_b, RowShifter as Rot(., idx n), SumColVec by
+    log-rotations with a column-0 mask, Alg. 3's mask F): decrypts to A @ B with C[i][c] at slot
+    i n + c; p products, 2 p log2(n) + (p - 1) rotations, 2 p plaintext products (tab2's counts
+    with log2 n for SumColVec)."""
+    o = Oracle(9, (60, 40, 40, 40, 40), 1, 60, 1, 40.0, seed=30)
+    S = o.slots
+    steps = [idx * n for idx in range(1, p)] + [t for t in (1, 2, 4, 8, 16) if t < n] + \
+            [-t for t in (1, 2, 4, 8, 16) if t < n]
+    o.keygen(steps)
+    rng = np.random.default_rng(m * 100 + n + p)
+    A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+    lp = o.L1
+    Ac = o.encrypt(o.encode(layouts.vr_matrix_a(A, S)), lp, 0)
+    Bc = o.encrypt(o.encode(layouts.vr_matrix_b(Bm, S)), lp, 1)
+    mv = layouts.vr_matmul_masks(m, n, p, S)
+    masks = np.stack([o.encode(mv[0], float(o.q[lp - 2]))] + [o.encode(v, float(o.q[lp - 3])) for v in mv[1:]])
+    o.reset_counters()
+    D = o.vr_matmul(Ac, Bc, n, p, masks)
+    c = o.counters()
+    lg = int(math.log2(n))
+    assert c["tensors"] == p and c["relins"] == p and c["ct_plain"] == 2 * p
+    assert c["rotations"] == (p - 1) + 2 * p * lg
+    C = layouts.vr_matmul_from(o.decrypt(D, o.scale ** 2 / o.q[lp - 1]), m, n, p)
+    assert np.abs(C - A @ Bm).max() < 1e-5
+
+
 def encrypt_images(o, imgs, H, limbs=None, base_id=0):
     """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
     Bn, C, h, w = imgs.shape
