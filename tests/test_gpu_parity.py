@@ -508,6 +508,56 @@ def test_errors(lib):
     assert e.value.code == HE_E_ARG
 
 
+def test_errors_of_the_layer_variants(lib):
+    """Argument, level and state errors of the matmul variants, activations, ReForm, the
+    single-ciphertext layers, graphs and the transform geometry (no GPU fault on any path)."""
+    import torch
+    from paper_2512_18646_gb300 import HeError, api
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_LEVEL, HE_E_STATE, HE_E_UNIMPL
+
+    def code(fn):
+        with pytest.raises(HeError) as e:
+            fn()
+        return e.value.code
+
+    g = api.Context(8, (60, 40, 40), 1, 60, 1, 40.0, stream=torch.cuda.Stream().cuda_stream)
+    g.keygen([1, 2, 3])
+    assert code(lambda: api.volley_geometry(128, 5, 3)) == HE_E_ARG  # p does not divide the slots
+    assert code(lambda: api.volley_geometry(16, 20, 4)) == HE_E_ARG  # no block fits
+    A = g.encrypt_matrix_a(np.ones((2, 4)), 0)
+    B = g.encrypt_matrix_b(np.ones((4, 4)), 10)
+    assert code(lambda: g.matmul_bsgs(A, B, 2, 4, 5)) == HE_E_ARG  # baby step larger than p
+    Ahat = g.encrypt_matrix_a_volley(np.ones((2, 4)), 4, 0)
+    B3 = g.encrypt_matrix_b(np.ones((3, 4)), 20)
+    assert code(lambda: g.matmul_volley(Ahat, B3)) == HE_E_ARG  # 4 ciphertexts of A, 3 of B
+    x = g.encrypt_matrix_a(np.ones((2, 2)), 30)
+    assert code(lambda: g.poly_act(x, [0, 1, 0, 0, 1])) == HE_E_UNIMPL  # degree 4
+    low = g.mul(x, x)  # one level left
+    assert code(lambda: g.poly_act(low, [0.1, 0.2, 0.3, 0.4])) == HE_E_LEVEL  # two levels needed
+    assert code(lambda: g.reform(x, 1, 2, 8)) == HE_E_ARG  # gap 1
+    assert code(lambda: g.reform(x, 2, 5, 8)) == HE_E_ARG  # rows do not fit the block
+    xi = g.vr_encrypt_images(np.ones((2, 4, 4)), 4, 4, 0)
+    assert code(lambda: g.vr_encrypt_kernels(np.ones((5, 5)), 0.0, 4, 4, 4, 4)) == HE_E_ARG  # kernel > image
+    kk, bb = g.vr_encrypt_kernels(np.ones((2, 2)), 0.0, 4, 4, 4, 4)
+    assert code(lambda: g.vr_conv2d(xi, bb, bb, 4, 4, 2, 4, 4)) == HE_E_ARG  # one kernel ciphertext, k^2 = 4 needed
+    assert code(lambda: g.vr_conv2d(low, kk, bb, 4, 4, 2, 4, 4)) == HE_E_LEVEL  # input one level from the bottom
+    assert code(lambda: g.vr_encrypt_matrix_b(np.ones((4, 3)), 0)) == HE_E_ARG  # p does not divide the rows
+    assert code(lambda: g.ntt_set_geometry(9, 16)) == HE_E_ARG
+    assert code(lambda: g.ntt_autotune(0)) == HE_E_ARG
+    assert code(lambda: g.graph_end()) == HE_E_STATE  # no capture open
+    g.graph_begin()
+    assert code(lambda: g.graph_begin()) == HE_E_STATE  # already capturing
+    A2 = g.add(A, A)  # made during the capture
+    assert code(lambda: g.assign(A, A2)) == HE_E_STATE  # into a set made before the capture
+    y = g.add(x, x)
+    graph = g.graph_end()
+    graph.launch()
+    g.synchronize()
+    assert np.array_equal(y.export(), g.add(x, x).export())
+    graph.destroy()
+    del xi
+
+
 def test_matmul_batched_equals_single_matmuls(lib):
     """Mixed shapes (some sharing p): batched results equal he_matmul's bit for bit, and GEMM."""
     o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=12, steps=list(range(1, 8)))
