@@ -624,7 +624,7 @@ __global__ void k_volley_acc_kernel(const u64* Ah, const u64* B, u64* d, int n, 
 // enough reads are in flight to stream the plaintexts at memory speed; sums
 // are reduced every 8 columns.
 template <int OB, int UN, int P>
-__global__ void k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
+__global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
                                 const PrimeTab* pt, int log_n) {
   static_assert(8 % UN == 0, "reduction every 8 columns");
   const size_t N = (size_t)1 << log_n;
@@ -929,13 +929,15 @@ void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int 
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
   const size_t total = (size_t)limbs * C.N;
+  // 128-thread blocks: at 126-156 registers a thread, three or four blocks fit an SM
+  const unsigned grid_fc = (unsigned)std::min<size_t>((total + 127) / 128, (size_t)152 * 64);
   const double bytes = 8.0 * (double)C.N * limbs * ((double)polys * n_in + (double)out_dim * n_in + (double)polys * out_dim);
   void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes, (double)C.N * limbs * polys * (double)n_in * out_dim);
   if (polys == 2)
-    k_fc_mac_kernel<5, 4, 2><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
+    k_fc_mac_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
                                                                        C.log_n);
   else if (polys == 3)
-    k_fc_mac_kernel<5, 4, 3><<<grid_for(total), kBlock, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
+    k_fc_mac_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
                                                                        C.log_n);
   else
     throw Error(1, "dense layer inputs have two or three components");

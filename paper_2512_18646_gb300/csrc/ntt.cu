@@ -286,6 +286,10 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
   auto sync = [] { __syncwarp(__activemask()); };
   // the transform's result reduced to [0, q)
   auto fin = [q, one_sh](u64 v) { return NAR ? shoup(v, 1, one_sh, q) : reduce4q(v, q); };
+  // a multiple of q above every transform output (72q growing range, 4q Harvey), so that
+  // x + zq - a is a nonnegative representative of x - a for the fused epilogues, whose exact
+  // Shoup product then reduces it
+  const u64 zq = (NAR ? 72 : 4) * q;
   u64 a[P::E];
   {
     using M0 = RMap<LOGM, 0, kRowKB>;
@@ -308,7 +312,7 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
 #pragma unroll
     for (int k = 0; k < P::E; k++) {
       const int e = xl | ML::kbits(k);
-      xr[e] = shoup(submod(xi[e], fin(a[k]), q), qi, qs, q);
+      xr[e] = shoup(xi[e] + zq - a[k], qi, qs, q);
     }
   } else {
     // ModDown combine: (u_Q[pi(j)] - z) P^{-1} plus the part the key switch does not touch
@@ -334,7 +338,7 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
         const u32 e2 = ((2 * bj + 1) * gk) & mask;
         src = brv_bits((e2 - 1) >> 1, n);
       }
-      const u64 v = shoup(submod(ui[src], fin(a[k]), q), pv, ps, q);
+      const u64 v = shoup(ui[src] + zq - a[k], pv, ps, q);
       oi[j] = add ? addmod(v, bi[fz.kmode == 0 ? j : src], q) : v;
     }
   }
