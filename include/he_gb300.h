@@ -204,9 +204,12 @@ int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset
  * he_matmul_batched: `count` independent products A[i] B[i] (each as in
  * he_matmul, shapes m[i], p[i]; two-component operands) evaluated together;
  * C[i] receives each result, identical to he_matmul's. Products with the same
- * p and level share their ModUp and rotation launches (the B operands of a
- * group are concatenated within a 48 GiB working-memory budget), so each key
- * is read once per launch for all of them.
+ * p, level and scale share their ModUp and rotation launches (the B operands of
+ * a group are concatenated within a 48 GiB working-memory budget), so each key
+ * is read once per launch for all of them; their tensor sums share launches
+ * (128 products each), one rescale and one relinearisation. Every launch takes
+ * its pointers as kernel parameters, so the call can be captured into a CUDA
+ * graph (he_graph_begin) and replayed on new operand contents.
  */
 int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
                       const int* p, he_ctset** C);
@@ -251,6 +254,20 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
  * 1..k-1 and block_w .. (k-1) block_w. he_vr_conv2d_coeffs takes the k^2 masks
  * as encoded integer plaintexts [k^2][N] at scale q_{l-1} instead.
  */
+/*
+ * he_vrot: vRot (Alg. 5). Virtual ciphertexts are rows of row_len slots (row_len
+ * divides N/2) whose first img_len slots hold an image; every row's image is
+ * rotated left by r (0 <= r < img_len): R = rescale(Rot(X, r) (x) F1 +
+ * Rot(X, N/2 - img_len + r) (x) F2), F1 keeping row positions j < img_len - r and
+ * F2 positions img_len - r <= j < img_len of every row (Alg. 5 applies F2 to the
+ * last row only, a misprint: every row needs its wrapped part), masks at scale
+ * q_l; slots past img_len become 0. One level, the scale unchanged. Needs
+ * rotation keys for steps r and N/2 - img_len + r. he_vrot_coeffs takes F1, F2
+ * as encoded integer plaintexts [2][N].
+ */
+int he_vrot(he_ctx* ctx, const he_ctset* in, int r, int row_len, int img_len, he_ctset** out);
+int he_vrot_coeffs(he_ctx* ctx, const he_ctset* in, int r, int img_len, const int64_t* masks, he_ctset** out);
+
 /*
  * Alg. 3 with one ciphertext per operand (the paper's single-ciphertext matmul).
  * he_vr_encrypt_matrix_a: tau_a, A [m][n] row-major at slots i n + j (m n <= N/2).
@@ -680,7 +697,8 @@ int he_sched_simulate(int n, const double* arrival_ms, const int* side, const si
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse);
 
 /*
- * Transform geometry. The negacyclic transform of a limb runs as n1 stages in
+ * Transform geometry (no counterpart in the paper, which describes no number-
+ * theoretic transform). The negacyclic transform of a limb runs as n1 stages in
  * column kernels (blocks of `cols` adjacent columns) and log_n - n1 stages in
  * row kernels; every geometry computes the same transform, so results do not
  * depend on it. he_ntt_set_geometry(ctx, 0, 0) restores the default (n1 =

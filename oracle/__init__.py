@@ -70,6 +70,8 @@ def _lib():
             "oc_reset_counters": (None, [V]),
             "oc_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
             "oc_matmul_volley": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]),
+            "oc_vrot": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long, ctypes.c_int,
+                                       _i64p, _u64p]),
             "oc_vr_matmul": (ctypes.c_int, [V, _u64p, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p,
                                             _u64p]),
             "oc_vr_conv2d": (ctypes.c_int, [V, _u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p, _u64p,
@@ -322,6 +324,16 @@ class Oracle:
         n, _, lp, _ = A.shape
         out = np.zeros((p, 2, lp - 1, self.N), np.uint64)
         _check(self.lib.oc_matmul_bsgs(self.h, _p(A, _u64p), _p(B, _u64p), n, p, g, lp, _p(out, _u64p)))
+        return out
+
+    def vrot(self, X, r: int, hw: int, masks) -> np.ndarray:
+        """vRot (Alg. 5) of X [n_ct][2 or 3][lp][N] by r inside rows of images of hw slots; masks
+        [2][N] (F1, F2 encoded at scale q_{lp-1}) -> [n_ct][2][lp-1][N]."""
+        X = _u64(X)
+        n_ct, polys, lp, _ = X.shape
+        masks = np.ascontiguousarray(masks, dtype=np.int64)
+        out = np.zeros((n_ct, 2, lp - 1, self.N), np.uint64)
+        _check(self.lib.oc_vrot(self.h, _p(X, _u64p), n_ct, polys, lp, r, hw, _p(masks, _i64p), _p(out, _u64p)))
         return out
 
     def vr_matmul(self, A, Bbar, n: int, p: int, masks) -> np.ndarray:

@@ -217,3 +217,22 @@ def vr_matmul_masks(m: int, n: int, p: int, slots: int) -> np.ndarray:
 def vr_matmul_from(z: np.ndarray, m: int, n: int, p: int) -> np.ndarray:
     """Alg. 3's result slot vector -> C [m][p] (C[i][c] at slot i n + c)."""
     return np.stack([z[i * n: i * n + p] for i in range(m)])
+
+
+def vrot_masks(n: int, hw: int, r: int, slots: int) -> np.ndarray:
+    """Alg. 5's masks for virtual ciphertexts held as rows of n slots (image of hw <= n values at
+    the start of each row): F1 keeps row positions j < hw - r, F2 keeps hw - r <= j < hw -> [2][slots]."""
+    F = np.zeros((2, slots))
+    for row in range(slots // n):
+        F[0, row * n: row * n + hw - r] = 1.0
+        F[1, row * n + hw - r: row * n + hw] = 1.0
+    return F
+
+
+def vrot_slots(v: np.ndarray, n: int, hw: int, r: int) -> np.ndarray:
+    """What vRot computes: every row's first hw entries rotated left by r, the rest 0."""
+    out = np.zeros_like(v)
+    for row in range(v.shape[-1] // n):
+        seg = v[..., row * n: row * n + hw]
+        out[..., row * n: row * n + hw] = np.roll(seg, -r, axis=-1)
+    return out

@@ -153,6 +153,19 @@ static Ct vr_conv2d(Ctx& C, const Ct& x_any, const std::vector<Ct>& S, const Ct&
   return acc;
 }
 
+// vRot (Alg. 5): virtual ciphertexts are rows of n slots whose first hw slots hold
+// an image; vRot(ct, r) rotates every row's image left by r:
+//   R = rescale(Rot(X, r) (x) F1 + Rot(X, S - hw + r) (x) F2)
+// with F1 keeping row positions j < hw - r and F2 positions hw - r <= j < hw (the
+// rotations hoisted, the two masked terms summed before one rescale). masks [2][N].
+static Ct vrot(Ctx& C, const Ct& x_any, long r, int hw, const int64_t* masks) {
+  const Ct x = two_comp(C, x_any);
+  const long S = (long)C.N / 2;
+  std::vector<Ct> R = ct_rotate_hoisted(C, x, {r, S - hw + r});
+  std::vector<i64> f1(masks, masks + C.N), f2(masks + C.N, masks + 2 * C.N);
+  return ct_rescale(C, ct_add(C, ct_mul_plain(C, R[0], f1), ct_mul_plain(C, R[1], f2)));
+}
+
 // Alg. 3 on one ciphertext per operand (the paper's single-ciphertext matmul):
 // A row-major (tau_a), Bbar = tau_b(B) tiled over the whole ring. For idx < p:
 //   T = relin(rescale(A (x) Rot(Bbar, idx n)))     (RowShifter applied idx times)
@@ -453,6 +466,14 @@ int oc_conv2d_enc(void* h, const uint64_t* X, int polys, int lp, int c_in, int w
          }
          std::vector<Ct> r = conv2d_enc(*C, x, gap, w, bias, c_out, k, stride, scale, s);
          cts_to(*C, r, out));
+}
+
+// X [n_ct][polys][lp][N]; masks [2][N] (F1, F2 at scale q_{lp-1}) -> out [n_ct][2][lp-1][N]
+int oc_vrot(void* h, const uint64_t* X, int n_ct, int polys, int lp, long r, int hw, const int64_t* masks,
+            uint64_t* out) {
+  OL_TRY(Ctx* C = (Ctx*)h; if (lp < 2 || r < 0 || r >= hw) throw std::runtime_error("bad vRot arguments");
+         std::vector<Ct> x = cts_from(*C, X, n_ct, lp, polys); std::vector<Ct> res(n_ct);
+         for (int t = 0; t < n_ct; t++) res[t] = vrot(*C, x[t], r, hw, masks); cts_to(*C, res, out));
 }
 
 // A, Bbar [2][lp][N] (one ciphertext each); masks [1 + p][N] -> out [2][lp-3][N]

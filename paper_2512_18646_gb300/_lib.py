@@ -71,6 +71,8 @@ SIGNATURES = {
     "he_matmul_volley": (I, [V, V, V, PV]),
     "he_matmul_bsgs": (I, [V, V, V, I, I, I, PV]),
     "he_conv2d": (I, [V, V, I, I, P_D, P_D, I, I, I, PV]),
+    "he_vrot": (I, [V, V, I, I, I, PV]),
+    "he_vrot_coeffs": (I, [V, V, I, I, P_I64, PV]),
     "he_vr_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
     "he_vr_encrypt_matrix_b": (I, [V, P_D, I, I, U64, PV]),
     "he_vr_matmul": (I, [V, V, V, I, I, I, PV]),

@@ -271,6 +271,13 @@ class Context:
         return self._set(load().he_conv2d, self.h, x.h, c_in, gap, _ptr(W, P_D), None if b is None else _ptr(b, P_D),
                          c_out, k, stride)
 
+    def vrot(self, x: CtSet, r: int, row_len: int, img_len: int) -> CtSet:
+        return self._set(load().he_vrot, self.h, x.h, r, row_len, img_len)
+
+    def vrot_coeffs(self, x: CtSet, r: int, img_len: int, masks) -> CtSet:
+        m = np.ascontiguousarray(masks, dtype=np.int64)
+        return self._set(load().he_vrot_coeffs, self.h, x.h, r, img_len, _ptr(m, P_I64))
+
     def vr_encrypt_matrix_a(self, A, ct_id_base: int = 0) -> CtSet:
         A = _f64(A)
         return self._set(load().he_vr_encrypt_matrix_a, self.h, _ptr(A, P_D), A.shape[0], A.shape[1], ct_id_base)

@@ -480,6 +480,35 @@ int he_vr_conv2d(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const
   });
 }
 
+int he_vrot_coeffs(he_ctx* ctx, const he_ctset* in, int r, int img_len, const int64_t* masks, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && masks && out, HE_E_ARG, "null argument");
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 2, HE_E_LEVEL, "no level left for vRot");
+    DevBuf m = fc_prepare(ctx->c, masks, 1, 2, lp);
+    *out = wrap(vrot(ctx->c, *in->s, r, img_len, m.p));
+  });
+}
+
+int he_vrot(he_ctx* ctx, const he_ctset* in, int r, int row_len, int img_len, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    const long S = (long)C.N / 2;
+    REQUIRE(row_len >= 1 && S % row_len == 0 && img_len >= 1 && img_len <= row_len && r >= 0 && r < img_len,
+            HE_E_ARG, "rows must tile the slots, images fit the rows and 0 <= r < img_len");
+    const int lp = in->s->limbs;
+    REQUIRE(lp >= 2, HE_E_LEVEL, "no level left for vRot");
+    std::vector<double> z((size_t)2 * S, 0.0);
+    for (long row = 0; row < S / row_len; row++)
+      for (int j = 0; j < img_len; j++) z[(size_t)(j < img_len - r ? 0 : 1) * S + row * row_len + j] = 1.0;
+    std::vector<int64_t> m((size_t)2 * C.N);
+    for (int t = 0; t < 2; t++) encode_real(C, z.data() + (size_t)t * S, (size_t)S, (double)C.q[lp - 1], m.data() + t * C.N);
+    DevBuf dm = fc_prepare(C, m.data(), 1, 2, lp);
+    *out = wrap(vrot(C, *in->s, r, img_len, dm.p));
+  });
+}
+
 int he_vr_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
     REQUIRE(ctx && A && out, HE_E_ARG, "null argument");

@@ -528,6 +528,32 @@ std::unique_ptr<CtSet> vr_conv2d(Ctx& C, const CtSet& in_any, const CtSet& S, co
   return out;
 }
 
+// vRot (Alg. 5): virtual ciphertexts are rows of n slots whose first hw slots hold
+// an image; every row's image rotates left by r:
+//   R = rescale(Rot(X, r) (x) F1 + Rot(X, S - hw + r) (x) F2)
+// F1 keeping row positions j < hw - r, F2 positions hw - r <= j < hw (masks [2][lp][N],
+// NTT domain, scale q_{lp-1}); the two rotations share one ModUp, the masked terms one
+// multiply-accumulate launch and one rescale. One level; the scale is unchanged.
+std::unique_ptr<CtSet> vrot(Ctx& C, const CtSet& in_any, long r, int hw, const u64* masks) {
+  std::unique_ptr<CtSet> hold;
+  const CtSet& in = two_comp(C, in_any, hold);
+  if (hw < 1 || r < 0 || r >= hw) throw Error(1, "vRot needs 0 <= r < the image length");
+  if (in.limbs < 2) throw Error(2, "no level left for vRot");
+  const long S = (long)C.N / 2;
+  auto R = rotate(C, in, {r, S - hw + r});  // [ct][2]
+  const size_t cw = in.ct_words();
+  const u64* xs[2] = {R->buf.p, R->buf.p + cw};
+  DevBuf dxs(2, C.stream);
+  // pageable source: the call returns once the pointers are staged
+  HE_CUDA(cudaMemcpyAsync(dxs.p, xs, 16, cudaMemcpyHostToDevice, C.stream));
+  auto out = new_set(C, in.n, 2, in.limbs, in.scale);
+  k_pack_blocks(C, (const u64* const*)dxs.p, masks, 2, in.n, in.limbs, out->buf.p, 2 * cw);
+  R.reset();
+  rescale_inplace(C, *out);
+  out->scale = in.scale;  // the masks were encoded at scale q_l
+  return out;
+}
+
 // Alg. 3 with one ciphertext per operand (the paper's single-ciphertext matmul): A
 // row-major (tau_a), Bbar = tau_b(B) tiled over the whole ring, so RowShifter applied
 // idx times is Rot(Bbar, idx n). For idx < p:

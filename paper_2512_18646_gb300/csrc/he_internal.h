@@ -296,6 +296,8 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
 std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in, int c_in, int gap, const CtSet& Wct, const double* bias,
                                   int c_out, int k, int stride);
 std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// vRot (Alg. 5) by r inside rows of images of hw slots; masks [2][lp][N] (F1, F2; NTT domain); one level
+std::unique_ptr<CtSet> vrot(Ctx& C, const CtSet& in, long r, int hw, const u64* masks);
 // Alg. 3 with one ciphertext per operand: E [lp-1][N] column-0 mask, F [p][lp-2][N] (NTT domain); three levels
 std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A, const CtSet& Bbar, int n, int p, const u64* E, const u64* F);
 // Alg. 4 over one-ciphertext image blocks of width Wb: S [k^2] kernel ciphertexts (scale q_{l-1}), bias one

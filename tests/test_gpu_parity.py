@@ -382,6 +382,22 @@ def test_vr_matmul_matches_oracle_and_fp64(lib, m, n, p):
     assert gd.scale == sc
 
 
+@pytest.mark.parametrize("n,hw,r", [(16, 12, 5), (32, 20, 19), (64, 64, 3)])
+def test_vrot_matches_oracle(lib, n, hw, r):
+    """vRot (Alg. 5): bit-exact with the oracle from the same mask plaintexts; the library's own
+    masks decrypt to every virtual ciphertext rotated left by r."""
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=33, steps=None)
+    S = o.slots
+    o.keygen([r, S - hw + r])
+    g.keygen([r, S - hw + r])
+    v = np.random.default_rng(n + r).uniform(-1, 1, (2, S))
+    ox, gx = encrypt_both(o, g, encode_columns(o, v), ct_id_base=11)
+    masks = np.stack([o.encode(f, float(o.q[o.L1 - 1])) for f in layouts.vrot_masks(n, hw, r, S)])
+    assert np.array_equal(g.vrot_coeffs(gx, r, hw, masks).export(), o.vrot(ox, r, hw, masks))
+    want = np.stack([layouts.vrot_slots(v[t], n, hw, r) for t in range(2)])
+    assert np.abs(g.decrypt_slots(g.vrot(gx, r, n, hw)) - want).max() < 1e-5
+
+
 def _act_polynomials():
     from tests.test_oracle_pins import act_polynomials
     return act_polynomials()

@@ -661,6 +661,28 @@ def test_vr_matmul_single_ciphertext_matches_fp64(m, n, p):
     assert np.abs(C - A @ Bm).max() < 1e-5
 
 
+@pytest.mark.parametrize("n,hw,r", [(16, 12, 5), (16, 16, 1), (32, 20, 19), (8, 8, 7)])
+def test_vrot_rotates_every_virtual_ciphertext(n, hw, r):
+    """vRot (Alg. 5, with F2 applied to every row): every row's image of hw slots rotates left by r,
+    the rest of the row becomes 0; two rotations from one ModUp, two masks, one rescale."""
+    o = Oracle(8, (60, 40, 40), 1, 60, 1, 40.0, seed=32)
+    S = o.slots
+    o.keygen([r, S - hw + r])
+    v = np.random.default_rng(n + hw + r).uniform(-1, 1, S)
+    X = o.encrypt(o.encode(v), ct_id=0)[None]
+    masks = np.stack([o.encode(f, float(o.q[o.L1 - 1])) for f in layouts.vrot_masks(n, hw, r, S)])
+    o.reset_counters()
+    Y = o.vrot(X, r, hw, masks)
+    c = o.counters()
+    assert c["rotations"] == 2 and c["modups"] == 1 and c["ct_plain"] == 2 and c["rescales"] == 1
+    assert np.abs(o.decrypt(Y[0]) - layouts.vrot_slots(v, n, hw, r)).max() < 1e-6
+    # the literal F2[m][j] (last row only) would leave the wrapped part of the other rows empty
+    if S // n > 1:
+        wrong = layouts.vrot_slots(v, n, hw, r).copy()
+        wrong[: n * (S // n - 1)] *= layouts.vrot_masks(n, hw, r, S)[0][: n * (S // n - 1)]
+        assert np.abs(o.decrypt(Y[0]) - wrong).max() > 1e-3
+
+
 def encrypt_images(o, imgs, H, limbs=None, base_id=0):
     """imgs [B][C][h][w] -> X [C][w][2][limbs][N]."""
     Bn, C, h, w = imgs.shape
