@@ -234,7 +234,7 @@ int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset
 int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
                       const int* p, he_ctset** C_out) {
   return guard([&] {
-    REQUIRE(ctx && A && B && m && p && C_out && count >= 0, HE_E_ARG, "null argument");
+    REQUIRE(ctx && count >= 0 && (count == 0 || (A && B && m && p && C_out)), HE_E_ARG, "null argument");
     std::vector<const CtSet*> As(count), Bs(count);
     std::vector<int> ps(p, p + count);
     for (int i = 0; i < count; i++) {

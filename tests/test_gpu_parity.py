@@ -574,6 +574,29 @@ def test_errors_of_the_layer_variants(lib):
     del xi
 
 
+def test_degenerate_cases(lib):
+    """Empty and one-element inputs of the layer variants: an empty batch, ReForm of one row, vRot by 0
+    (the image part of every row kept, the rest cleared), the identity polynomial."""
+    from paper_2512_18646_gb300 import api
+    o, g = make_pair(8, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=34, steps=[128 - 12])  # vRot by 0 wraps by -12
+    assert g.matmul_batched([], [], [], []) == []
+    S = o.slots
+    v = np.random.default_rng(1).uniform(-1, 1, (1, S))
+    ox, gx = encrypt_both(o, g, encode_columns(o, v), ct_id_base=0)
+    # ReForm of a single row is the row mask itself
+    masks = o.reform_masks(1, 16, o.L1)
+    assert np.array_equal(g.reform_coeffs(gx, 2, 1, masks).export(), o.reform(ox, 2, 1, masks))
+    want = np.zeros(S)
+    want[::16] = v[0, ::16]
+    assert np.abs(g.decrypt_slots(g.reform(gx, 2, 1, 16))[0] - want).max() < 1e-5
+    # vRot by 0: F2 is empty, every row keeps its image part
+    got = g.decrypt_slots(g.vrot(gx, 0, 16, 12))[0]
+    assert np.abs(got - layouts.vrot_slots(v[0], 16, 12, 0)).max() < 1e-5
+    # f(x) = x through the degree-3 schedule
+    y = g.poly_act(g.encrypt_coeffs(encode_columns(o, v), o.L1, o.scale, 5), [0.0, 1.0, 0.0, 0.0])
+    assert np.abs(g.decrypt_slots(y)[0] - v[0]).max() < 1e-5
+
+
 def test_matmul_batched_equals_single_matmuls(lib):
     """Mixed shapes (some sharing p): batched results equal he_matmul's bit for bit, and GEMM."""
     o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=12, steps=list(range(1, 8)))
