@@ -255,6 +255,18 @@ def run_gpu(args, rank, world, local_rank):
     # the last step's logits, checked against the FP64 CNN by the CPU leg (outside timing)
     logits = g.decrypt_slots(z)[:, ::H][:, :B].T
 
+    # the same step on one image per ciphertext set (same ciphertext count, same kernels)
+    x1 = g.encrypt_image(imgs[:1], H, ct_id_base=0)
+    cnn_step(g, x1, w, pts)
+    g.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        cnn_step(g, x1, w, pts)
+    e1.record(stream)
+    e1.synchronize()
+    plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    x1.free()
+
     # per-kernel device time with CUDA events on the launching stream
     lib.he_profile_enable(1)
     for _ in range(args.steps):
@@ -306,6 +318,8 @@ def run_gpu(args, rank, world, local_rank):
             "ntt_geometry": {"column_stages": n1, "columns_per_block": cols, "tuned_on_limbs": tune_rows,
                              "fwd_inv_us": round(tune_us, 1)},
         "images_per_step": B, "modmul_peak": modmul_peak.value,
+        "plain_value": job_throughput(1, args.steps, world, plain_ms / 1e3),
+        "plain_ms": plain_ms / args.steps,
     }
 
 
@@ -616,6 +630,88 @@ def fp64_layer_error(checks) -> float:
 
 
 # ---------------------------------------------------------------------------
+# one conv + x^2 layer at N = 2^15 (--workload layer): latency and GB/s
+# ---------------------------------------------------------------------------
+LAYER_METRIC = ("encrypted conv+x^2 layer images/s and latency (N=2^15, 64x64, conv 4x3x3 stride 1 + x^2, "
+                "relinearised)")
+
+
+def run_layer(args, rank, world, local_rank):
+    """conv (4 kernels 3x3, stride 1, weights and biases N(0, 0.1)) -> x^2 -> relinearisation on 64x64
+    images U[0, 1] at N = 2^15, Q = 60 + 8 x 40, P = 60, alpha = 1, scale 2^40. Two inputs through
+    the same call sequence: one image per set of 64 column ciphertexts (the layer's latency) and
+    256 images slot-packed per set (block stride 64, S / 64 blocks). GB/s = the library's algorithmic
+    bytes of one layer call (every operand read and written once, per kernel) / its device time.
+    Timed with CUDA events on the context's stream."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api, load
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    pre = synthetic.CONV_LAYER
+    g = api.Context.from_preset(pre, seed=201 + 1000 * rank, stream=stream.cuda_stream)
+    g.keygen([1, 2])
+    side, Hs = 64, 64
+    K, bias = synthetic.conv_weights(4, 1, 3, 0.1, seed=202)
+    n_batch = (g.N // 2) // Hs
+    imgs = synthetic.images(n_batch, side, side, seed=201)
+    x1 = g.encrypt_image(imgs[:1], Hs, ct_id_base=0)
+    xb = g.encrypt_image(imgs, Hs, ct_id_base=100)
+    g.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def layer(x):
+        y = g.conv2d(x, 1, 1, K, bias, 1)
+        g.square(y)
+        return g.relinearize(y)
+
+    def timed(x, reps):
+        for _ in range(max(1, args.warmup)):
+            y = layer(x)
+            y.free()
+        g.synchronize()
+        l0 = lib.he_kernel_launches()
+        ys = []
+        ev0.record(stream)
+        for _ in range(reps):
+            ys.append(layer(x))
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps, (lib.he_kernel_launches() - l0) // reps, ys[-1]
+
+    reps = max(1, args.steps)
+    t1, l1, y1 = timed(x1, reps)
+    tb, lb, yb = timed(xb, reps)
+    # algorithmic bytes of one layer call from the library's per-kernel counts
+    lib.he_profile_enable(1)
+    layer(xb).free()
+    g.synchronize()
+    prof = profile_read(lib)
+    lib.he_profile_enable(0)
+    alg_bytes = sum(v["bytes"] for v in prof.values())
+    ho = side - 2
+    dec1 = g.decrypt_image(y1, 1, Hs, 1, ho).reshape(1, 4, ho, ho).transpose(0, 1, 3, 2)
+    decb = g.decrypt_image(yb, 4, Hs, 1, ho).reshape(4, 4, ho, ho).transpose(0, 1, 3, 2)
+    t1m, tbm = max_over_ranks(t1, world), max_over_ranks(tb, world)
+    return {"value": n_batch * world / tbm, "ms_per_step": 1e3 * tbm, "launches": lb,
+            "latency_ms": 1e3 * t1m, "plain_value": world / t1m, "plain_launches": l1,
+            "alg_bytes": alg_bytes, "GBps": alg_bytes / tbm / 1e9, "images_per_set": n_batch,
+            "checks": [(dec1, imgs[:1], K, bias), (decb, imgs[:4], K, bias)]}
+
+
+def fp64_square_layer_error(checks) -> float:
+    """CPU leg: max |decrypted - FP64 (conv, then x^2)|."""
+    from oracle import fp64_ref
+    err = 0.0
+    for got, imgs, K, bias in checks:
+        ref = fp64_ref.conv2d(imgs[:, None], K, bias, 1) ** 2
+        err = max(err, float(np.abs(got - ref).max()))
+    return err
+
+
+# ---------------------------------------------------------------------------
 # the serving workload (--workload serve)
 # ---------------------------------------------------------------------------
 SERVE_METRIC = ("served encrypted-CNN images/s and p50/p99 latency (Poisson arrivals, image sides {64,128,256}, "
@@ -806,7 +902,8 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cnn", "matmul", "matmul_small", "layer28", "serve"], default="cnn")
+    ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "serve"],
+                    default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
     ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
     ap.add_argument("--serve-warmup", type=int, default=20, help="serve workload: warm-up requests")
@@ -824,6 +921,29 @@ def main():
     cfg = {"workload": WORKLOAD, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+
+    if args.workload == "layer" and args.impl == "gpu":
+        res = run_layer(args, rank, world, local_rank)
+        if rank == 0:
+            line = {"metric": LAYER_METRIC, "value": res["value"], "unit": "images/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                    "data": "synthetic",
+                    "config": {"workload": "conv (4 kernels 3x3, stride 1, weights and biases N(0,0.1), seed 202) "
+                                           "-> x^2 -> relinearisation on 64x64 images U[0,1] (seed 201); RNS-CKKS "
+                                           "N=2^15, Q=60+8x40, P=60, alpha=1, scale 2^40",
+                               "images_per_set": res["images_per_set"], "parallelism": f"replicas x{world}",
+                               "l2": "input set (64 ciphertexts of 9 limbs, 0.3 GB) and its rotations exceed L2"},
+                    "path": "he_conv2d (hoisted rotations by 1 and 2, scalar multiply-accumulate, rescale) + "
+                            "he_poly_act x^2 + he_relinearize; 256 images slot-packed per set",
+                    "gpu_launches": res["launches"],
+                    "latency_ms": res["latency_ms"],
+                    "plain": {"value": res["plain_value"], "ms": res["latency_ms"], "images_per_set": 1,
+                              "gpu_launches": res["plain_launches"]},
+                    "algorithmic_bytes_per_layer": res["alg_bytes"], "GBps": res["GBps"],
+                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_square_layer_error(res["checks"])}
+            print(json.dumps(line))
+        return
 
     if args.workload == "layer28" and args.impl == "gpu":
         res = run_layer28(args, rank, world, local_rank)
@@ -952,7 +1072,8 @@ def main():
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": res["launches"], "max_abs_err_vs_fp64": max_err,
             "alu_peak_modmul_per_s": res["modmul_peak"],
-            "plain_images_per_s": res["value"] / args.batch, "ntt_geometry": res["ntt_geometry"],
+            "plain": {"value": res["plain_value"], "ms_per_step": res["plain_ms"], "images_per_set": 1},
+            "ntt_geometry": res["ntt_geometry"],
             "kernel_breakdown": res["breakdown"]}
     print(json.dumps(line))
 
