@@ -893,6 +893,20 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return f"{ln.split(':', 1)[1].strip()} ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1047,7 +1061,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_inf,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic", "config": cfg,
-                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
                                  "sample": "conv-1 output column 0 (8 channels, 20 top-level key switches) per step, "
                                            "scaled to one inference by key-switch count"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -1063,7 +1077,7 @@ def main():
         max_err = fp64_max_error([(res["logits"], res["imgs"], res["weights"])])
     if not args.no_cpu_baseline and world == 1:
         dt, per_inf = oracle_sample(args.batch)
-        cpu = {"value": args.batch / per_inf, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": args.batch / per_inf, "unit": UNIT, "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"conv-1 output column 0 (8 channels, 20 top-level key switches) took {dt:.2f} s; "
                          f"scaled to one inference by key-switch count ({KS_PER_INFERENCE}/20)"}
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -284,8 +284,11 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
   const size_t N = (size_t)1 << n;
   auto addr = [rw](int e) { return swz(rw * M + e); };
   auto sync = [] { __syncwarp(__activemask()); };
-  // the transform's result reduced to [0, q)
-  auto fin = [q, one_sh](u64 v) { return NAR ? shoup(v, 1, one_sh, q) : reduce4q(v, q); };
+  // the transform's result reduced to [0, q) (growing range: the cheaper quotient estimate
+  // leaves [0, 4q), as the lazy butterflies do)
+  auto fin = [q, one_sh](u64 v) { return reduce4q(NAR ? shoup_approx(v, 1, one_sh, q) : v, q); };
+  // exact products of the fused epilogues, by way of [0, 4q)
+  auto mulq = [q](u64 v, u64 w, u64 wp) { return reduce4q(shoup_approx(v, w, wp, q), q); };
   // a multiple of q above every transform output (72q growing range, 4q Harvey), so that
   // x + zq - a is a nonnegative representative of x - a for the fused epilogues, whose exact
   // Shoup product then reduces it
@@ -312,7 +315,7 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
 #pragma unroll
     for (int k = 0; k < P::E; k++) {
       const int e = xl | ML::kbits(k);
-      xr[e] = shoup(xi[e] + zq - a[k], qi, qs, q);
+      xr[e] = mulq(xi[e] + zq - a[k], qi, qs);
     }
   } else {
     // ModDown combine: (u_Q[pi(j)] - z) P^{-1} plus the part the key switch does not touch
@@ -338,7 +341,7 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
         const u32 e2 = ((2 * bj + 1) * gk) & mask;
         src = brv_bits((e2 - 1) >> 1, n);
       }
-      const u64 v = shoup(ui[src] + zq - a[k], pv, ps, q);
+      const u64 v = mulq(ui[src] + zq - a[k], pv, ps);
       oi[j] = add ? addmod(v, bi[fz.kmode == 0 ? j : src], q) : v;
     }
   }
@@ -534,7 +537,7 @@ __device__ __forceinline__ void inv_cols_body(u64* xc, u64* smc, int u, int C, i
   using M0 = RMap<LOGM, 0, kColKB>;
   const int x0 = M0::upart(u);
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = shoup(a[k], sc, scs, q);
+  for (int k = 0; k < P::E; k++) xc[(size_t)(x0 | M0::kbits(k)) * stride] = reduce4q(shoup_approx(a[k], sc, scs, q), q);
 }
 
 template <int LOGM, int MODE>
