@@ -43,15 +43,15 @@ static u64 residue_of(int64_t v, u64 q) {
   return r < 0 ? (u64)(r + (int64_t)q) : (u64)r;
 }
 
-// ModUp of polynomial `poly` of every ciphertext of a set (coefficient copy,
-// inverse NTT, base conversion per digit, forward NTT of the extended limbs).
+// ModUp of polynomial `poly` of every ciphertext of a set (inverse NTT into a
+// scratch buffer, base conversion per digit, forward NTT of the extended limbs).
 static DevBuf modup_poly(Ctx& C, const CtSet& in, int poly) {
   const int n = in.n, lp = in.limbs, beta = C.beta_at(lp), nb = lp + C.K;
   const size_t N = C.N;
-  // the polynomial to the coefficient domain, each limb times N^{-1} (D_j/q_i)^{-1}
+  // the polynomial to the coefficient domain, each limb times N^{-1} (D_j/q_i)^{-1} (the first
+  // pass reads the set, the result goes to x)
   DevBuf x((size_t)n * lp * N, C.stream);
-  k_copy_limbs(C, in.buf.p + (size_t)poly * lp * N, in.ct_words(), x.p, (size_t)lp * N, (size_t)n, lp);
-  ntt_inverse_qscaled(C, x.p, n, lp);
+  ntt_inverse_qscaled(C, x.p, n, lp, in.buf.p + (size_t)poly * lp * N, in.ct_words());
   DevBuf ext((size_t)n * beta * nb * N, C.stream);
   const ulonglong2* hat_level = reinterpret_cast<const ulonglong2*>(C.d_up.p + (size_t)(C.L1 + 1) * C.L1 * 2) +
                                 (size_t)lp * C.L1 * (C.L1 + C.K);
@@ -196,15 +196,15 @@ std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in_any, const std::vector<lon
 
 // rows polynomials of lp limbs (x) -> rescaled polynomials of lp - 1 limbs (out).
 // The last limb of x is transformed in place (x is consumed).
-static void rescale_rows(Ctx& C, u64* x, int rows, int lp, u64* out) {
+static void rescale_rows(Ctx& C, u64* x, int rows, int lp, u64* out, const u64* addc = nullptr, int row0 = 0) {
   const size_t N = C.N;
   LimbMap lm1;
   lm1.lpp = 1; lm1.split = 1; lm1.base0 = lp - 1; lm1.base1 = 0; lm1.poly_stride = (size_t)lp * N;
   ntt_inverse(C, x + (size_t)(lp - 1) * N, rows, lm1);
-  ntt_forward_rescale(C, out, x, rows, lp);
+  ntt_forward_rescale(C, out, x, rows, lp, addc, row0);
 }
 
-void rescale_inplace(Ctx& C, CtSet& s) {
+void rescale_inplace(Ctx& C, CtSet& s, const u64* addc) {
   const int lp = s.limbs;
   if (lp < 2) throw Error(2, "no level left to rescale");
   const int rows = s.n * s.polys;
@@ -212,7 +212,8 @@ void rescale_inplace(Ctx& C, CtSet& s) {
   DevBuf out((size_t)rows * (lp - 1) * N, C.stream);
   const int step = chunk_items(C, rows, 8.0 * N * lp);
   for (int r0 = 0; r0 < rows; r0 += step)
-    rescale_rows(C, s.buf.p + (size_t)r0 * lp * N, std::min(step, rows - r0), lp, out.p + (size_t)r0 * (lp - 1) * N);
+    rescale_rows(C, s.buf.p + (size_t)r0 * lp * N, std::min(step, rows - r0), lp, out.p + (size_t)r0 * (lp - 1) * N,
+                 addc, r0);
   s.buf = std::move(out);
   s.limbs = lp - 1;
   s.scale = s.scale / (double)C.q[lp - 1];
@@ -393,12 +394,21 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
                                 cudaMemcpyDeviceToDevice, C.stream));
     }
   }
-  rescale_inplace(C, *out);
-  out->scale = in.scale;  // scalars were encoded at scale q_l, which the rescale removes
+  // scalars were encoded at scale q_l, which the rescale removes; the bias round(bias_o D) joins
+  // component 0 of every output ciphertext of channel o in the rescale's last pass
+  DevBuf cb;
   if (bias) {
-    DevBuf cb = const_table(C, bias, c_out, lp - 1, out->scale);
-    k_add_const(C, out->buf.p, out->n, lp - 1, cb.p, w_out);
+    std::vector<u64> t((size_t)out->n * 2 * (lp - 1), 0);
+    for (int o = 0; o < c_out; o++) {
+      const int64_t iv = std::llround(bias[o] * in.scale);
+      for (int j = 0; j < w_out; j++)
+        for (int i = 0; i < lp - 1; i++) t[((size_t)(o * w_out + j) * 2) * (lp - 1) + i] = residue_of(iv, C.q[i]);
+    }
+    cb = DevBuf(t.size(), C.stream);
+    HE_CUDA(cudaMemcpyAsync(cb.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
   }
+  rescale_inplace(C, *out, bias ? cb.p : nullptr);
+  out->scale = in.scale;
   return out;
 }
 

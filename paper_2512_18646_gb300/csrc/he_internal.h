@@ -159,11 +159,17 @@ void ntt_forward(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 bool ntt_geometry_ok(int log_n, int n1, int cols);
 void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // rescale of `rows` polynomials x [rows][lp][N] whose limb lp - 1 is already in the
-// coefficient domain: out [rows][lp - 1][N] = (x_i - NTT_i(expanded last limb)) q_l^{-1}
-void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp);
+// coefficient domain: out [rows][lp - 1][N] = (x_i - NTT_i(expanded last limb)) q_l^{-1};
+// with addc [all rows][lp - 1], output row r (row0 + r of the whole set) also gains the
+// constant addc[(row0 + r) (lp - 1) + i] in limb i
+void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp, const u64* addc = nullptr,
+                         int row0 = 0);
 // inverse transform of n_polys polynomials [n_polys][lp][N] over q_0..q_{lp-1}, ending with
-// the factor N^{-1} (D_j/q_i)^{-1} mod q_i (the first step of ModUp's base conversion)
-void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp);
+// the factor N^{-1} (D_j/q_i)^{-1} mod q_i (the first step of ModUp's base conversion); with
+// `src`, polynomial p is read from src + p src_stride (not modified) and the result written to
+// data
+void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp, const u64* src = nullptr,
+                         size_t src_stride = 0);
 // ModUp of one digit fused into the forward transform of its extended limbs: polynomial p,
 // launch limb i (position lm.mem(i)) gets sum_{t < cnt} yt[p ystride + t N] hat[t hstride +
 // lm.mem(i)] and is transformed; lm skips the digit's own limbs
@@ -289,7 +295,9 @@ std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in, const std::vector<long>& 
 // three components -> two (key switch of d2 with the relinearisation key); no rescale
 void relinearize(Ctx& C, CtSet& s);
 std::unique_ptr<CtSet> relinearized(Ctx& C, const CtSet& s);
-void rescale_inplace(Ctx& C, CtSet& s);
+// rescale in place; addc [n polys][limbs - 1] (optional): after the rescale, polynomial r of
+// the set gains the constant addc[r (limbs - 1) + i] in limb i (e.g. a bias on component 0)
+void rescale_inplace(Ctx& C, CtSet& s, const u64* addc = nullptr);
 std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const double* W, const double* bias,
                               int c_out, int k, int stride);
 // convolution with encrypted kernels Wct [c_out][c_in][k][k] (constants at scale q_{limbs-1})

@@ -39,6 +39,8 @@ namespace {
 //  1 rescale:  x [rows][lp][N] holds the polynomials being rescaled, limb lp - 1
 //              already in the coefficient domain; rs [L1][3] holds floor(q_l/2)
 //              mod q_i, q_l^{-1} mod q_i and its Shoup companion for this lp.
+//              addc (optional): a constant added after the rescale to polynomial
+//              add_row0 + p (of the whole set), limb i: addc[(add_row0 + p) (lp - 1) + i].
 //  2 ModDown:  load: yt [polys][K][N] the P part times N^{-1} (P/p_k)^{-1}
 //              (coefficient domain), phat [K][L1][2] (P/p_k) mod q_i with Shoup
 //              companions; store: out[c][comp][i][j] = (u[c][comp][i][pi(j)] - z)
@@ -46,6 +48,9 @@ namespace {
 //              base[c][0][i][pi(j)]), pi the Galois index of element gk.
 //  3 scaled inverse: the inverse transform ends with the factor iscale[prime -
 //              scale_base] (w, Shoup companion) instead of N^{-1}.
+//  (inverse rows, any mode) src: when set, polynomial p's limb i is read from
+//              src + p src_stride + lm.mem(i) N and the result written to the
+//              rows of `data` (an out-of-place first pass).
 //  4 ModUp:    load: the target limb at extended position e = lm.mem(i) of digit
 //              polynomial pr is sum_{t < K} yt[pr ystride + t N] hat[t hstride + e],
 //              yt the digit's source limbs times N^{-1} (D_j/q_i)^{-1} (coefficient
@@ -67,6 +72,10 @@ struct Fuse {
   int scale_base = 0;
   size_t ystride = 0;
   int hstride = 0;
+  const u64* src = nullptr;
+  size_t src_stride = 0;
+  const u64* addc = nullptr;
+  int add_row0 = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -312,10 +321,19 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
     const int pr = blockIdx.y / lm.lpp, i = blockIdx.y - pr * lm.lpp;
     const u64* xi = fz.x + ((size_t)pr * fz.lp + i) * N + run * M;
     const u64 qi = fz.rs[(size_t)i * 3 + 1], qs = fz.rs[(size_t)i * 3 + 2];
+    const u64 cadd = fz.addc ? fz.addc[(size_t)(fz.add_row0 + pr) * lm.lpp + i] : 0;
+    if (cadd == 0) {
 #pragma unroll
-    for (int k = 0; k < P::E; k++) {
-      const int e = xl | ML::kbits(k);
-      xr[e] = mulq(xi[e] + zq - a[k], qi, qs);
+      for (int k = 0; k < P::E; k++) {
+        const int e = xl | ML::kbits(k);
+        xr[e] = mulq(xi[e] + zq - a[k], qi, qs);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < P::E; k++) {
+        const int e = xl | ML::kbits(k);
+        xr[e] = addmod(mulq(xi[e] + zq - a[k], qi, qs), cadd, q);
+      }
     }
   } else {
     // ModDown combine: (u_Q[pi(j)] - z) P^{-1} plus the part the key switch does not touch
@@ -376,8 +394,8 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, Limb
 // inverse, first n2 stages (smallest distances) inside runs; inputs below 2q,
 // outputs in [0, 2q)
 template <int LOGM, bool NAR>
-__device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n1, u64 run, u64 q,
-                                              u64 one_sh) {
+__device__ __forceinline__ void inv_rows_body(const u64* xs, u64* xr, u64* smw, int rw, int u, const u64* tw, int n1,
+                                              u64 run, u64 q, u64 one_sh) {
   using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   auto addr = [rw](int e) { return swz(rw * M + e); };
@@ -387,7 +405,7 @@ __device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, 
     using ML = RMap<LOGM, P::R - 1, kRowKB>;
     const int xl = ML::upart(u);
 #pragma unroll
-    for (int k = 0; k < P::E; k++) a[k] = xr[xl | ML::kbits(k)];
+    for (int k = 0; k < P::E; k++) a[k] = xs[xl | ML::kbits(k)];
     round_inv<LOGM, P::R - 1, kRowKB, NAR>(a, xl, tw, n1, run, q);
   }
   rounds_inv_rest<LOGM, P::R - 2, kRowKB, NAR>(a, u, smw, addr, sync, tw, n1, run, q);
@@ -399,7 +417,7 @@ __device__ __forceinline__ void inv_rows_body(u64* xr, u64* smw, int rw, int u, 
 
 template <int LOGM>
 __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, LimbMap lm, const PrimeTab* pt,
-                                                              const u64* tw_all, int n, int n1) {
+                                                              const u64* tw_all, int n, int n1, Fuse fz) {
   using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   constexpr int RUNS = kRowThreads / P::T;
@@ -413,13 +431,18 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, Limb
   const u64 run = (u64)blockIdx.x * RUNS + r_cta;
   if (run >= ((u64)1 << n1)) return;
   u64* xr = x + run * M;
+  const u64* xs = xr;
+  if (fz.src) {
+    const int p = blockIdx.y / lm.lpp, i = blockIdx.y - p * lm.lpp;
+    xs = fz.src + (size_t)p * fz.src_stride + (size_t)lm.mem(i) * N + run * M;
+  }
   const int warp = threadIdx.x >> 5;
   const int rw = (threadIdx.x & 31) / P::T;
   u64* smw = sm + warp * 32 * P::E;
   if (q < kNarrowPrime)
-    inv_rows_body<LOGM, true>(xr, smw, rw, u, tw, n1, run, q, one_sh);
+    inv_rows_body<LOGM, true>(xs, xr, smw, rw, u, tw, n1, run, q, one_sh);
   else
-    inv_rows_body<LOGM, false>(xr, smw, rw, u, tw, n1, run, q, one_sh);
+    inv_rows_body<LOGM, false>(xs, xr, smw, rw, u, tw, n1, run, q, one_sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,7 +615,7 @@ void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C,
                          : MODE == 1 ? "k_ntt_fwd_rows<rescale>" : MODE == 2 ? "k_ntt_fwd_rows<moddown>" : "k_ntt_fwd_rows";
   static_assert(MODE >= 0 && MODE <= 4, "transform modes 0..4");
   void* t = prof_begin(name, C.stream, bytes, prods);
-  if (inv) k_ntt_inv_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1);
+  if (inv) k_ntt_inv_rows<L><<<grid, kRowThreads, 0, C.stream>>>(base, lm, C.dev_ptab(), tw, C.log_n, n1, fz);
   else
     k_ntt_fwd_rows<L, (MODE == 1 || MODE == 2) ? MODE : 0><<<grid, kRowThreads, 0, C.stream>>>(
         base, lm, C.dev_ptab(), tw, C.log_n, n1, fz);
@@ -699,7 +722,7 @@ void ntt_inverse(const Ctx& C, u64* data, int n_polys, const LimbMap& lm) {
   HE_CUDA(cudaGetLastError());
 }
 
-void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp) {
+void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp, const u64* src, size_t src_stride) {
   const int rows = n_polys * lp;
   if (rows == 0) return;
   const Geom g = geom(C);
@@ -712,7 +735,12 @@ void ntt_inverse_qscaled(const Ctx& C, u64* data, int n_polys, int lp) {
   for (int r0 = 0; r0 < rows; r0 += step) {
     const int rr = rows - r0 < step ? rows - r0 : step;
     u64* base = data + (size_t)(r0 / lp) * lm.poly_stride;
-    rows_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
+    Fuse fr = fz;
+    if (src) {
+      fr.src = src + (size_t)(r0 / lp) * src_stride;
+      fr.src_stride = src_stride;
+    }
+    rows_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fr);
     cols_dispatch<3>(true, base, lm, rr, C, g, C.d_ipsi.p, fz);
   }
   HE_CUDA(cudaGetLastError());
@@ -797,7 +825,7 @@ bool ntt_geometry_ok(int log_n, int n1, int cols) {
   return threads >= 32 && threads <= 1024 && (size_t)(1 << n1) * cols * 8 <= 128 * 1024;
 }
 
-void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
+void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp, const u64* addc, int row0) {
   if (rows == 0) return;
   const Geom g = geom(C);
   const LimbMap lm = limbs_q(lp - 1, C.N);
@@ -806,6 +834,8 @@ void ntt_forward_rescale(const Ctx& C, u64* out, u64* x, int rows, int lp) {
   for (int p0 = 0; p0 < rows; p0 += per) {
     const int pn = rows - p0 < per ? rows - p0 : per;
     Fuse fz{x + (size_t)p0 * lp * C.N, tab, lp};
+    fz.addc = addc;
+    fz.add_row0 = row0 + p0;
     u64* base = out + (size_t)p0 * (lp - 1) * C.N;
     cols_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
     rows_dispatch<1>(false, base, lm, pn * (lp - 1), C, g, C.d_psi.p, fz);
