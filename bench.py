@@ -165,9 +165,22 @@ def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
     return t["dram_bytes"] / t["alg_bytes"] * alg_bytes_per_launch
 
 
-def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n):
+MAC96_KERNELS = ("k_conv_mac96_kernel",)
+
+
+def alu_peak_for(name, modmul_peak, mac96_peak):
+    """(products/s, unit, source) of the kernel's own product: the 96-bit multiply-accumulate for the
+    kernels built on it, else the Shoup product."""
+    if name.startswith(MAC96_KERNELS):
+        return mac96_peak, "Gmac96/s", "measured (he_calibrate_mac96: 96-bit multiply-accumulates in registers, all SMs)"
+    return modmul_peak, "Gmodmul/s", "measured (he_calibrate_modmul: Shoup products in registers, all SMs)"
+
+
+def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n, mac96_peak=None):
     """The kernel's bound is whichever takes longer at peak: its algorithmic bytes at the measured HBM
-    bandwidth, or its modular products at the measured Shoup-product rate (he_calibrate_modmul)."""
+    bandwidth, or its products at the measured rate of that product (he_calibrate_modmul for Shoup
+    products, he_calibrate_mac96 for 96-bit multiply-accumulates)."""
+    alu_peak, alu_unit, alu_src = alu_peak_for(name, modmul_peak, mac96_peak or modmul_peak)
     avg_s = t["ms"] / 1e3 / max(1, t["launches"])
     alg_per_launch = t["bytes"] / max(1, t["launches"])
     prod_per_launch = t.get("products", 0.0) / max(1, t["launches"])
@@ -178,12 +191,11 @@ def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n):
             "hbm_view": {"achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
                          "peak_source": "measured" if measured else "fallback"}}
     traffic = ncu_traffic(name, alg_per_launch)
-    if prod_per_launch / modmul_peak > alg_per_launch / (hbm * 1e9):
+    if prod_per_launch / alu_peak > alg_per_launch / (hbm * 1e9):
         ach = prod_per_launch / avg_s / 1e9
-        peak = modmul_peak / 1e9
-        base.update({"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "Gmodmul/s",
-                     "frac": round(ach / peak, 4), "traffic": traffic,
-                     "peak_source": "measured (he_calibrate_modmul: Shoup products in registers, all SMs)"})
+        peak = alu_peak / 1e9
+        base.update({"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": alu_unit,
+                     "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": alu_src})
     else:
         base.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": traffic,
@@ -279,14 +291,17 @@ def run_gpu(args, rank, world, local_rank):
     pk = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
     import ctypes
-    modmul_peak = ctypes.c_double()
+    modmul_peak, mac96_peak = ctypes.c_double(), ctypes.c_double()
     lib.he_calibrate_modmul(g.h, ctypes.byref(modmul_peak))
-    prof.pop("k_calib_shoup_kernel", None)
-    roofline = roofline_for(top, prof[top], prof_total, hbm, "fallback" not in pk, modmul_peak.value, pre.log_n)
+    lib.he_calibrate_mac96(g.h, ctypes.byref(mac96_peak))
+    roofline = roofline_for(top, prof[top], prof_total, hbm, "fallback" not in pk, modmul_peak.value, pre.log_n,
+                            mac96_peak.value)
     breakdown = {k: {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
                      "launches_per_step": v["launches"] // args.steps,
                      "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
-                     "alu_frac": round(v["products"] / (v["ms"] / 1e3) / modmul_peak.value, 3) if v["ms"] > 0 else 0.0}
+                     "alu_frac": round(v["products"] / (v["ms"] / 1e3) /
+                                       alu_peak_for(k, modmul_peak.value, mac96_peak.value)[0], 3)
+                     if v["ms"] > 0 else 0.0}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     # end to end through the C ABI: host ciphertexts in (pinned), encrypted logits out
@@ -317,7 +332,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roofline, "breakdown": breakdown, "e2e": e2e, "clocks": clocks, "logits": logits, "imgs": imgs, "weights": w,
             "ntt_geometry": {"column_stages": n1, "columns_per_block": cols, "tuned_on_limbs": tune_rows,
                              "fwd_inv_us": round(tune_us, 1)},
-        "images_per_step": B, "modmul_peak": modmul_peak.value,
+        "images_per_step": B, "modmul_peak": modmul_peak.value, "mac96_peak": mac96_peak.value,
         "plain_value": job_throughput(1, args.steps, world, plain_ms / 1e3),
         "plain_ms": plain_ms / args.steps,
     }
@@ -1085,7 +1100,7 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": res["launches"], "max_abs_err_vs_fp64": max_err,
-            "alu_peak_modmul_per_s": res["modmul_peak"],
+            "alu_peak_modmul_per_s": res["modmul_peak"], "alu_peak_mac96_per_s": res["mac96_peak"],
             "plain": {"value": res["plain_value"], "ms_per_step": res["plain_ms"], "images_per_set": 1},
             "ntt_geometry": res["ntt_geometry"],
             "kernel_breakdown": res["breakdown"]}

@@ -720,6 +720,12 @@ int he_ntt_autotune(he_ctx* ctx, int rows, int* n1, int* cols, double* us);
  * CUDA events. Used as the integer-arithmetic roofline. */
 int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s);
 
+/* Measured peak of 96-bit multiply-accumulates (acc += a b for residues a, b
+ * below 2^46, seven 32-bit multiplies by PTX carry chains, the product of the
+ * convolution kernels for such primes) per second on the context's GPU,
+ * measured like he_calibrate_modmul. */
+int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t he_kernel_launches(void);
 

@@ -128,6 +128,49 @@ HE_HD void mac128(Acc128& acc, u64 a, u64 b) {
 #endif
 }
 
+// 96-bit accumulator (three 32-bit words) for sums of products of residues below
+// kMac96Prime: a product is below 2^92 and its high words' product a1 b1 below 2^28,
+// so a b = a0 b0 + (a0 b1 + a1 b0) 2^32 + a1 b1 2^64 needs seven 32-bit multiplies
+// (three of them high halves) and no fourth word while the sum stays below 2^96.
+struct Acc96 {
+  u32 w0, w1, w2;
+};
+constexpr u64 kMac96Prime = 1ull << 46;
+// acc += a b for a, b < kMac96Prime; the caller keeps the sum below 2^96 (every partial
+// sum is then below 2^96 too, so the dropped carries out of the top word are zero).
+HE_HD void mac96(Acc96& acc, u64 a, u64 b) {
+#if defined(__CUDA_ARCH__)
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+  asm("mad.lo.cc.u32  %0, %3, %5, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
+      "madc.lo.u32    %2, %4, %6, %2;\n\t"
+      "mad.lo.cc.u32  %1, %3, %6, %1;\n\t"
+      "madc.hi.u32    %2, %3, %6, %2;\n\t"
+      "mad.lo.cc.u32  %1, %4, %5, %1;\n\t"
+      "madc.hi.u32    %2, %4, %5, %2;"
+      : "+r"(acc.w0), "+r"(acc.w1), "+r"(acc.w2)
+      : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+#else
+  u64 hi, lo;
+  mul128(a, b, hi, lo);
+  const u64 l = (((u64)acc.w1 << 32) | acc.w0) + lo;
+  const u64 h = (u64)acc.w2 + hi + (l < lo);
+  acc.w0 = (u32)l;
+  acc.w1 = (u32)(l >> 32);
+  acc.w2 = (u32)h;
+#endif
+}
+// the accumulated value mod q in [0, q) (Barrett on the 96-bit value, below q 2^64)
+HE_HD u64 reduce96(const Acc96& acc, const Mod& m) {
+  return reduce128((u64)acc.w2, ((u64)acc.w1 << 32) | acc.w0, m);
+}
+// products of residues mod q that fit on top of a reduced sum: floor(2^96 / (q - 1)^2) - 1
+// (so that v + room (q - 1)^2 < 2^96 for v < q), computed in double precision with a margin
+HE_HD int mac96_room(u64 q) {
+  const double r = 79228162514264337593543950336.0 / ((double)(q - 1) * (double)(q - 1)) * (1.0 - 1e-12);
+  return r >= (double)(1 << 20) ? (1 << 20) : (int)r - 1;
+}
+
 // Montgomery reduction (Montgomery, Math. Comp. 1985) of x = hi 2^64 + lo < q 2^64:
 // x 2^{-64} mod q in [0, q), with qneg = -q^{-1} mod 2^64. m = lo qneg makes
 // x + m q divisible by 2^64; its low word sums to 2^64 unless lo = 0.

@@ -217,20 +217,37 @@ __global__ void __launch_bounds__(KS_TILE) k_ks_inner_kernel(const u64* __restri
 #pragma unroll
     for (int dg = 0; dg < MAXB; dg++) en[dg] = dg < beta ? digit(cn, dg) : 0;
     u64* U = u + (size_t)c * 2 * nb * N + (size_t)pos * N + jn;
-    for (int st = 0; st < S; st++) {
-      const ulonglong2* kk = skey + (size_t)st * beta * KS_TILE + threadIdx.x;
-      Acc128 a0{0, 0}, a1{0, 0};
+    if (md.q < kMac96Prime) {  // uniform across the block: beta products of residues fit 96 bits
+      for (int st = 0; st < S; st++) {
+        const ulonglong2* kk = skey + (size_t)st * beta * KS_TILE + threadIdx.x;
+        Acc96 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
-      for (int dg = 0; dg < MAXB; dg++) {
-        if (dg < beta) {
-          const ulonglong2 kv = kk[dg * KS_TILE];
-          mac128(a0, e[dg], kv.x);
-          mac128(a1, e[dg], kv.y);
+        for (int dg = 0; dg < MAXB; dg++) {
+          if (dg < beta) {
+            const ulonglong2 kv = kk[dg * KS_TILE];
+            mac96(a0, e[dg], kv.x);
+            mac96(a1, e[dg], kv.y);
+          }
         }
+        U[st * ustep] = redc128(a0.w2, ((u64)a0.w1 << 32) | a0.w0, md.q, qneg);
+        U[st * ustep + (size_t)nb * N] = redc128(a1.w2, ((u64)a1.w1 << 32) | a1.w0, md.q, qneg);
       }
-      // keys are in Montgomery form: the reduction divides the sum by 2^64 (beta q^2 < q 2^64)
-      U[st * ustep] = redc128(a0.hi, a0.lo, md.q, qneg);
-      U[st * ustep + (size_t)nb * N] = redc128(a1.hi, a1.lo, md.q, qneg);
+    } else {
+      for (int st = 0; st < S; st++) {
+        const ulonglong2* kk = skey + (size_t)st * beta * KS_TILE + threadIdx.x;
+        Acc128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+        for (int dg = 0; dg < MAXB; dg++) {
+          if (dg < beta) {
+            const ulonglong2 kv = kk[dg * KS_TILE];
+            mac128(a0, e[dg], kv.x);
+            mac128(a1, e[dg], kv.y);
+          }
+        }
+        // keys are in Montgomery form: the reduction divides the sum by 2^64 (beta q^2 < q 2^64)
+        U[st * ustep] = redc128(a0.hi, a0.lo, md.q, qneg);
+        U[st * ustep + (size_t)nb * N] = redc128(a1.hi, a1.lo, md.q, qneg);
+      }
     }
 #pragma unroll
     for (int dg = 0; dg < MAXB; dg++) e[dg] = en[dg];
@@ -404,6 +421,7 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
   const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+  if (pt[i].mod.q < kMac96Prime) return;  // uniform across the block
   const int T = c_in * k * k;
   for (int id = threadIdx.x; id < c_out * T; id += blockDim.x)
     sw[id] = *reinterpret_cast<const ulonglong2*>(w + ((size_t)id * limbs + i) * 2);
@@ -411,11 +429,86 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
   const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
   if (n0 >= N) return;
   const u64 q = pt[i].mod.q, one_sh = pt[i].one_sh;
+  if (q < kMac96Prime) return;  // k_conv_mac96_kernel's limbs (uniform across the block)
   const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
   if (q < kNarrowPrime)
     conv_mac_body<OB, TN, true>(sw, rot, out, c_in, w_in, k, stride, c_out, w_out, LN, off, q, one_sh);
   else
     conv_mac_body<OB, TN, false>(sw, rot, out, c_in, w_in, k, stride, c_out, w_out, LN, off, q, one_sh);
+}
+
+// The same multiply-accumulate for limbs whose prime is below kMac96Prime: each
+// product goes into a 96-bit sum (seven 32-bit multiplies, no per-term reduction;
+// Barrett once every `room` terms and at the end). Each thread computes TN
+// adjacent coefficients of OB output channels (one shared-memory weight serves TN
+// products); the weights (residues only) are staged in shared memory. Blocks of
+// other limbs return at once (the Shoup kernel takes them).
+template <int OB, int TN>
+__global__ void __launch_bounds__(128) k_conv_mac96_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in,
+                                                           int k, int stride, int c_out, int w_out, int limbs,
+                                                           const PrimeTab* pt, int log_n) {
+  static_assert(TN == 1 || TN == 2, "one or two adjacent coefficients a thread");
+  extern __shared__ u64 sw64[];  // [c_out][c_in k k]
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+  const Mod md = pt[i].mod;
+  if (md.q >= kMac96Prime) return;  // uniform across the block
+  const int T = c_in * k * k;
+  for (int id = threadIdx.x; id < c_out * T; id += blockDim.x) sw64[id] = w[((size_t)id * limbs + i) * 2];
+  __syncthreads();
+  const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
+  if (n0 >= N) return;
+  const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
+  const int room = mac96_room(md.q);
+  for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
+    for (int o0 = 0; o0 < c_out; o0 += OB) {
+      Acc96 acc[OB][TN];
+#pragma unroll
+      for (int t = 0; t < OB; t++)
+#pragma unroll
+        for (int v = 0; v < TN; v++) acc[t][v] = Acc96{0, 0, 0};
+      int pending = 0;
+      for (int c = 0; c < c_in; c++)
+        for (int b = 0; b < k; b++) {
+          const u64* src = rot + ((size_t)(c * w_in + stride * jp + b) * k) * 2 * LN + off;
+          for (int a = 0; a < k; a++) {
+            u64 x[TN];
+            if constexpr (TN == 2) {
+              const ulonglong2 xx = *reinterpret_cast<const ulonglong2*>(src + (size_t)a * 2 * LN);
+              x[0] = xx.x;
+              x[1] = xx.y;
+            } else {
+              x[0] = src[(size_t)a * 2 * LN];
+            }
+            const u64* wr = sw64 + (size_t)o0 * T + (c * k + a) * k + b;
+            if (pending == room) {  // uniform across the block
+#pragma unroll
+              for (int t = 0; t < OB; t++)
+#pragma unroll
+                for (int v = 0; v < TN; v++) {
+                  const u64 r = reduce96(acc[t][v], md);
+                  acc[t][v] = Acc96{(u32)r, (u32)(r >> 32), 0};
+                }
+              pending = 0;
+            }
+            pending++;
+#pragma unroll
+            for (int t = 0; t < OB; t++)
+              if (o0 + t < c_out) {
+                const u64 wt = wr[(size_t)t * T];
+#pragma unroll
+                for (int v = 0; v < TN; v++) mac96(acc[t][v], x[v], wt);
+              }
+          }
+        }
+#pragma unroll
+      for (int t = 0; t < OB; t++)
+        if (o0 + t < c_out)
+#pragma unroll
+          for (int v = 0; v < TN; v++) out[((size_t)(o0 + t) * w_out + jp) * 2 * LN + off + v] = reduce96(acc[t][v], md);
+    }
+  }
 }
 
 // Convolution with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a}
@@ -722,6 +815,28 @@ __global__ void k_calib_shoup_kernel(u64* sink, u64 q, u64 w, u64 wp, int iters)
   sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
+// Calibration of the 96-bit multiply-accumulate: eight independent sums per
+// thread, each gaining a product of two residues below kMac96Prime per iteration
+// (the sums wrap; only the time is used).
+__global__ void k_calib_mac96_kernel(u64* sink, u64 q, int iters) {
+  Acc96 acc[8];
+  u64 a[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    a[c] = (blockIdx.x * 131ull + threadIdx.x * 7ull + c) % q;
+    acc[c] = Acc96{0, 0, 0};
+  }
+  const u64 b = q - 3;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) mac96(acc[c], a[c], b);
+  }
+  u64 x = 0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) x ^= ((u64)acc[c].w2 << 32) ^ acc[c].w1 ^ acc[c].w0;
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
 // counts residues >= q_i in [n][limbs][N] rows (limb i of each polynomial)
 __global__ void k_check_range_kernel(const u64* x, size_t rows, int limbs, const PrimeTab* pt, int log_n,
                                      unsigned long long* bad) {
@@ -858,32 +973,63 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   constexpr int TN = 2, TH = 128;
   const size_t smem = (size_t)c_out * c_in * k * k * 16;
   if (smem > 200 * 1024) throw Error(8, "convolution weights exceed shared memory");
-  const unsigned gx = (unsigned)((C.N / TN + TH - 1) / TH), gy = (unsigned)(2 * limbs);
-  unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * gy));
-  if (gz > (unsigned)w_out) gz = (unsigned)w_out;
-  const double bytes = 8.0 * (double)C.N * 2.0 * limbs * ((double)c_in * (stride * (w_out - 1) + k) * k +
-                                                         (double)c_out * w_out);
-  const double prods = 2.0 * C.N * limbs * (double)c_out * w_out * c_in * k * k;
-  void* tok = prof_begin(c_out <= 8 ? "k_conv_mac_kernel<8>" : "k_conv_mac_kernel<16>", C.stream, bytes, prods);
-  if (c_out <= 8) {
-    static bool attr8 = false;
-    if (!attr8) {
-      HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<8, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr8 = true;
+  // limbs by kernel: 96-bit sums below kMac96Prime, Shoup products above
+  int wide = 0;
+  for (int i = 0; i < limbs; i++) wide += C.q[i] >= kMac96Prime;
+  const int narrow = limbs - wide;
+  const double T = (double)c_in * k * k;
+  auto per_limb_bytes = [&] {
+    return 8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
+  };
+  const double prods_limb = 2.0 * C.N * (double)c_out * w_out * T;
+  const unsigned gy = (unsigned)(2 * limbs);
+  if (wide > 0) {
+    const unsigned gx = (unsigned)((C.N / TN + TH - 1) / TH);
+    unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * 2 * wide));
+    if (gz > (unsigned)w_out) gz = (unsigned)w_out;
+    void* tok = prof_begin(c_out <= 8 ? "k_conv_mac_kernel<8>" : "k_conv_mac_kernel<16>", C.stream,
+                           per_limb_bytes() * wide, prods_limb * wide);
+    if (c_out <= 8) {
+      static bool attr8 = false;
+      if (!attr8) {
+        HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<8, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr8 = true;
+      }
+      k_conv_mac_kernel<8, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
+                                                                          w_out, limbs, C.dev_ptab(), C.log_n);
+    } else {
+      static bool attr16 = false;
+      if (!attr16) {
+        HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<16, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr16 = true;
+      }
+      k_conv_mac_kernel<16, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
+                                                                           w_out, limbs, C.dev_ptab(), C.log_n);
     }
-    k_conv_mac_kernel<8, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
-                                                                        w_out, limbs, C.dev_ptab(), C.log_n);
-  } else {
-    static bool attr16 = false;
-    if (!attr16) {
-      HE_CUDA(cudaFuncSetAttribute(k_conv_mac_kernel<16, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr16 = true;
-    }
-    k_conv_mac_kernel<16, TN><<<dim3(gx, gy, gz), TH, smem, C.stream>>>(rot, out, w, c_in, w_in, k, stride, c_out,
-                                                                         w_out, limbs, C.dev_ptab(), C.log_n);
+    prof_end(tok, C.stream);
+    HE_CUDA(cudaGetLastError());
   }
-  prof_end(tok, C.stream);
-  HE_CUDA(cudaGetLastError());
+  if (narrow > 0) {
+    // 8 output channels x 2 coefficients a thread (48 words of sums); 16 channels take two passes
+    // over the rotated inputs, which the idle memory bandwidth absorbs
+    constexpr int OB96 = 8, TN96 = 2;
+    const size_t smem64 = (size_t)c_out * c_in * k * k * 8;
+    const unsigned gx = (unsigned)((C.N / TN96 + TH - 1) / TH);
+    unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * 2 * narrow));
+    if (gz > (unsigned)w_out) gz = (unsigned)w_out;
+    // algorithmic bytes: every rotated input and output word once (the second pass re-reads inputs)
+    void* tok = prof_begin("k_conv_mac96_kernel<8, 2>", C.stream, per_limb_bytes() * narrow, prods_limb * narrow);
+    static bool attr96 = false;
+    if (!attr96) {
+      HE_CUDA(cudaFuncSetAttribute(k_conv_mac96_kernel<OB96, TN96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+      attr96 = true;
+    }
+    k_conv_mac96_kernel<OB96, TN96><<<dim3(gx, gy, gz), TH, smem64, C.stream>>>(
+        rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, C.dev_ptab(), C.log_n);
+    prof_end(tok, C.stream);
+    HE_CUDA(cudaGetLastError());
+  }
 }
 void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_in, int w_in, int k, int stride,
                     int c_out, int w_out, int limbs) {
@@ -954,6 +1100,18 @@ void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters) 
   const u64 q = C.q[0], w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);
   void* tok = prof_begin("k_calib_shoup_kernel", C.stream, 0.0, 8.0 * blocks * threads * (double)iters);
   k_calib_shoup_kernel<<<blocks, threads, 0, C.stream>>>(sink, q, w, wp, iters);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
+}
+void k_calib_mac96(const Ctx& C, u64* sink, int blocks, int threads, int iters) {
+  u64 q = (1ull << 45) - 55;
+  for (int i = 0; i < C.L1; i++)
+    if (C.q[i] < kMac96Prime) {
+      q = C.q[i];
+      break;
+    }
+  void* tok = prof_begin("k_calib_mac96_kernel", C.stream, 0.0, 8.0 * blocks * threads * (double)iters);
+  k_calib_mac96_kernel<<<blocks, threads, 0, C.stream>>>(sink, q, iters);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }
