@@ -165,7 +165,7 @@ def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
     return t["dram_bytes"] / t["alg_bytes"] * alg_bytes_per_launch
 
 
-MAC96_KERNELS = ("k_conv_mac96_kernel",)
+MAC96_KERNELS = ("k_conv_mac96_kernel", "k_fc_mac96_kernel")
 
 
 def alu_peak_for(name, modmul_peak, mac96_peak):

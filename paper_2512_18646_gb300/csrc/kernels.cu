@@ -444,7 +444,7 @@ __global__ void k_conv_mac_kernel(const u64* rot, u64* out, const u64* w, int c_
 // products); the weights (residues only) are staged in shared memory. Blocks of
 // other limbs return at once (the Shoup kernel takes them).
 template <int OB, int TN>
-__global__ void __launch_bounds__(128) k_conv_mac96_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in,
+__global__ void __launch_bounds__(128, 6) k_conv_mac96_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in,
                                                            int k, int stride, int c_out, int w_out, int limbs,
                                                            const PrimeTab* pt, int log_n) {
   static_assert(TN == 1 || TN == 2, "one or two adjacent coefficients a thread");
@@ -469,39 +469,45 @@ __global__ void __launch_bounds__(128) k_conv_mac96_kernel(const u64* rot, u64* 
 #pragma unroll
         for (int v = 0; v < TN; v++) acc[t][v] = Acc96{0, 0, 0};
       int pending = 0;
-      for (int c = 0; c < c_in; c++)
-        for (int b = 0; b < k; b++) {
-          const u64* src = rot + ((size_t)(c * w_in + stride * jp + b) * k) * 2 * LN + off;
-          for (int a = 0; a < k; a++) {
-            u64 x[TN];
-            if constexpr (TN == 2) {
-              const ulonglong2 xx = *reinterpret_cast<const ulonglong2*>(src + (size_t)a * 2 * LN);
-              x[0] = xx.x;
-              x[1] = xx.y;
-            } else {
-              x[0] = src[(size_t)a * 2 * LN];
-            }
-            const u64* wr = sw64 + (size_t)o0 * T + (c * k + a) * k + b;
-            if (pending == room) {  // uniform across the block
-#pragma unroll
-              for (int t = 0; t < OB; t++)
-#pragma unroll
-                for (int v = 0; v < TN; v++) {
-                  const u64 r = reduce96(acc[t][v], md);
-                  acc[t][v] = Acc96{(u32)r, (u32)(r >> 32), 0};
-                }
-              pending = 0;
-            }
-            pending++;
-#pragma unroll
-            for (int t = 0; t < OB; t++)
-              if (o0 + t < c_out) {
-                const u64 wt = wr[(size_t)t * T];
-#pragma unroll
-                for (int v = 0; v < TN; v++) mac96(acc[t][v], x[v], wt);
-              }
+      // terms in the order (c, b, a); the words of the next term are loaded before the products
+      // of the current one, so the load overlaps them
+      auto load = [&](int c, int b, int a) {
+        const u64* p = rot + ((size_t)(c * w_in + stride * jp + b) * k + a) * 2 * LN + off;
+        if constexpr (TN == 2) return *reinterpret_cast<const ulonglong2*>(p);
+        else return make_ulonglong2(*p, 0);
+      };
+      ulonglong2 nx = load(0, 0, 0);
+      int c = 0, b = 0, a = 0;
+      for (int term = 0; term < T; term++) {
+        const u64 x[2] = {nx.x, nx.y};
+        const u64* wr = sw64 + (size_t)o0 * T + (c * k + a) * k + b;
+        if (++a == k) {
+          a = 0;
+          if (++b == k) {
+            b = 0;
+            ++c;
           }
         }
+        if (term + 1 < T) nx = load(c, b, a);
+        if (pending == room) {  // uniform across the block
+#pragma unroll
+          for (int t = 0; t < OB; t++)
+#pragma unroll
+            for (int v = 0; v < TN; v++) {
+              const u64 r = reduce96(acc[t][v], md);
+              acc[t][v] = Acc96{(u32)r, (u32)(r >> 32), 0};
+            }
+          pending = 0;
+        }
+        pending++;
+#pragma unroll
+        for (int t = 0; t < OB; t++)
+          if (o0 + t < c_out) {
+            const u64 wt = wr[(size_t)t * T];
+#pragma unroll
+            for (int v = 0; v < TN; v++) mac96(acc[t][v], x[v], wt);
+          }
+      }
 #pragma unroll
       for (int t = 0; t < OB; t++)
         if (o0 + t < c_out)
@@ -725,6 +731,7 @@ __global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* 
   HE_GRID_LOOP(w, LN) {
     const int i = (int)(w >> log_n);
     const Mod md = pt[i].mod;
+    if (md.q < kMac96Prime) continue;  // k_fc_mac96_kernel's limbs (uniform across the block)
     for (int o0 = 0; o0 < out_dim; o0 += OB) {
       Acc128 acc[P][OB];
 #pragma unroll
@@ -762,6 +769,65 @@ __global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* 
 #pragma unroll
           for (int c = 0; c < P; c++)
             out[((size_t)(o0 + t) * P + c) * LN + w] = reduce128(acc[c][t].hi, acc[c][t].lo, md);
+    }
+  }
+}
+
+// The dense-layer multiply-accumulate for limbs whose prime is below kMac96Prime:
+// 96-bit sums (seven 32-bit multiplies a product), reduced once every `room`
+// columns and at the end. Same layout and tiling as k_fc_mac_kernel.
+template <int OB, int UN, int P>
+__global__ void __launch_bounds__(128) k_fc_mac96_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim,
+                                                         int limbs, const PrimeTab* pt, int log_n) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  HE_GRID_LOOP(w, LN) {
+    const int i = (int)(w >> log_n);
+    const Mod md = pt[i].mod;
+    if (md.q >= kMac96Prime) continue;  // k_fc_mac_kernel's limbs (uniform across the block)
+    const int room = mac96_room(md.q);
+    for (int o0 = 0; o0 < out_dim; o0 += OB) {
+      Acc96 acc[P][OB];
+#pragma unroll
+      for (int c = 0; c < P; c++)
+#pragma unroll
+        for (int t = 0; t < OB; t++) acc[c][t] = Acc96{0, 0, 0};
+      int pending = 0;
+      for (int cj0 = 0; cj0 < n_in; cj0 += UN) {
+        u64 xv[UN][P], pv[UN][OB];
+#pragma unroll
+        for (int v = 0; v < UN; v++) {
+          const int cj = cj0 + v;
+          const bool ok = cj < n_in;
+#pragma unroll
+          for (int c = 0; c < P; c++) xv[v][c] = ok ? X[((size_t)cj * P + c) * LN + w] : 0;
+#pragma unroll
+          for (int t = 0; t < OB; t++)
+            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * n_in + cj) * LN + w] : 0;
+        }
+        if (pending + UN > room) {  // uniform across the block
+#pragma unroll
+          for (int c = 0; c < P; c++)
+#pragma unroll
+            for (int t = 0; t < OB; t++) {
+              const u64 r = reduce96(acc[c][t], md);
+              acc[c][t] = Acc96{(u32)r, (u32)(r >> 32), 0};
+            }
+          pending = 0;
+        }
+        pending += UN;
+#pragma unroll
+        for (int v = 0; v < UN; v++)
+#pragma unroll
+          for (int t = 0; t < OB; t++)
+#pragma unroll
+            for (int c = 0; c < P; c++) mac96(acc[c][t], xv[v][c], pv[v][t]);
+      }
+#pragma unroll
+      for (int t = 0; t < OB; t++)
+        if (o0 + t < out_dim)
+#pragma unroll
+          for (int c = 0; c < P; c++) out[((size_t)(o0 + t) * P + c) * LN + w] = reduce96(acc[c][t], md);
     }
   }
 }
@@ -1074,21 +1140,34 @@ void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int 
               G, limbs, C.dev_ptab(), C.log_n);
 }
 void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
+  if (polys != 2 && polys != 3) throw Error(1, "dense layer inputs have two or three components");
   const size_t total = (size_t)limbs * C.N;
   // 128-thread blocks: at 126-156 registers a thread, three or four blocks fit an SM
   const unsigned grid_fc = (unsigned)std::min<size_t>((total + 127) / 128, (size_t)152 * 64);
-  const double bytes = 8.0 * (double)C.N * limbs * ((double)polys * n_in + (double)out_dim * n_in + (double)polys * out_dim);
-  void* tok = prof_begin("k_fc_mac_kernel", C.stream, bytes, (double)C.N * limbs * polys * (double)n_in * out_dim);
-  if (polys == 2)
-    k_fc_mac_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
-                                                                       C.log_n);
-  else if (polys == 3)
-    k_fc_mac_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(),
-                                                                       C.log_n);
-  else
-    throw Error(1, "dense layer inputs have two or three components");
-  prof_end(tok, C.stream);
-  HE_CUDA(cudaGetLastError());
+  // limbs by kernel: 96-bit sums below kMac96Prime, 128-bit sums above
+  int wide = 0;
+  for (int i = 0; i < limbs; i++) wide += C.q[i] >= kMac96Prime;
+  const int narrow = limbs - wide;
+  const double limb_bytes = 8.0 * (double)C.N * ((double)polys * n_in + (double)out_dim * n_in + (double)polys * out_dim);
+  const double limb_prods = (double)C.N * polys * (double)n_in * out_dim;
+  if (wide > 0) {
+    void* tok = prof_begin("k_fc_mac_kernel", C.stream, limb_bytes * wide, limb_prods * wide);
+    if (polys == 2)
+      k_fc_mac_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+    else
+      k_fc_mac_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+    prof_end(tok, C.stream);
+    HE_CUDA(cudaGetLastError());
+  }
+  if (narrow > 0) {
+    void* tok = prof_begin("k_fc_mac96_kernel", C.stream, limb_bytes * narrow, limb_prods * narrow);
+    if (polys == 2)
+      k_fc_mac96_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+    else
+      k_fc_mac96_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+    prof_end(tok, C.stream);
+    HE_CUDA(cudaGetLastError());
+  }
 }
 void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out,
                    size_t ct_stride) {
