@@ -149,24 +149,33 @@ __global__ void k_add_kernel(const u64* a, const u64* b, u64* out, int n_polys, 
   }
 }
 
+// d[c] = (a0 b0, a0 b1 + a1 b0, a1 b1) for ciphertext c = blockIdx.y; a square (a = b)
+// takes one cross product, doubled, and reads one operand.
 __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int limbs, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
-  const size_t total = (size_t)n * LN;
-  HE_GRID_LOOP(idx, total) {
-    const size_t c = idx / LN, w = idx - c * LN;
-    const int i = (int)(w >> log_n);
-    const Mod md = pt[i].mod;
-    const u64* A = a + c * 2 * LN;
-    const u64* B = b + c * 2 * LN;
-    const u64 a0 = A[w], a1 = A[LN + w], b0 = B[w], b1 = B[LN + w];
-    u64* D = d + c * 3 * LN;
-    D[w] = mulmod(a0, b0, md);
-    Acc128 acc{0, 0};
-    mac128(acc, a0, b1);
-    mac128(acc, a1, b0);
-    D[LN + w] = reduce128(acc.hi, acc.lo, md);
-    D[2 * LN + w] = mulmod(a1, b1, md);
+  const size_t c = blockIdx.y;
+  const u64* A = a + c * 2 * LN;
+  const u64* B = b + c * 2 * LN;
+  u64* D = d + c * 3 * LN;
+  const bool square = a == b;
+  for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < LN; w += (size_t)gridDim.x * blockDim.x) {
+    const Mod md = pt[(int)(w >> log_n)].mod;
+    const u64 a0 = A[w], a1 = A[LN + w];
+    if (square) {
+      D[w] = mulmod(a0, a0, md);
+      const u64 t = mulmod(a0, a1, md);
+      D[LN + w] = addmod(t, t, md.q);
+      D[2 * LN + w] = mulmod(a1, a1, md);
+    } else {
+      const u64 b0 = B[w], b1 = B[LN + w];
+      D[w] = mulmod(a0, b0, md);
+      Acc128 acc{0, 0};
+      mac128(acc, a0, b1);
+      mac128(acc, a1, b0);
+      D[LN + w] = reduce128(acc.hi, acc.lo, md);
+      D[2 * LN + w] = mulmod(a1, b1, md);
+    }
   }
 }
 
@@ -447,20 +456,31 @@ template <int OB, int TN>
 __global__ void __launch_bounds__(128, 6) k_conv_mac96_kernel(const u64* rot, u64* out, const u64* w, int c_in, int w_in,
                                                            int k, int stride, int c_out, int w_out, int limbs,
                                                            const PrimeTab* pt, int log_n) {
-  static_assert(TN == 1 || TN == 2, "one or two adjacent coefficients a thread");
-  extern __shared__ u64 sw64[];  // [c_out][c_in k k]
+  static_assert(TN == 2 && OB % 2 == 0, "two adjacent coefficients a thread, channels in pairs");
+  // weights of this limb in term order (c, b, a), the channels of a term side by side:
+  // [T][cp], cp = c_out rounded up to even, so a pair of channels is one 16-byte load
+  extern __shared__ ulonglong2 sw128[];
+  u64* sw64 = reinterpret_cast<u64*>(sw128);
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
   const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
   const Mod md = pt[i].mod;
   if (md.q >= kMac96Prime) return;  // uniform across the block
-  const int T = c_in * k * k;
-  for (int id = threadIdx.x; id < c_out * T; id += blockDim.x) sw64[id] = w[((size_t)id * limbs + i) * 2];
+  const int kk = k * k, T = c_in * kk, cp = (c_out + 1) & ~1;
+  for (int id = threadIdx.x; id < T * cp; id += blockDim.x) {
+    const int term = id / cp, o = id - term * cp;
+    const int c = term / kk, r = term - c * kk, b = r / k, a = r - b * k;  // term = (c k + b) k + a
+    sw64[id] = o < c_out ? w[(((size_t)o * T + (c * k + a) * k + b) * limbs + i) * 2] : 0;
+  }
   __syncthreads();
   const size_t n0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * TN;
   if (n0 >= N) return;
   const size_t off = (size_t)comp * LN + (size_t)i * N + n0;
   const int room = mac96_room(md.q);
+  // rot [c][j][a][2][LN]: for one channel c the terms (b, a) of output column jp are consecutive
+  // blocks of 2 LN words (column j = stride jp + b, rotation a); the next channel starts w_in k
+  // blocks further
+  const size_t step = 2 * LN, chan = (size_t)w_in * k * 2 * LN;
   for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
     for (int o0 = 0; o0 < c_out; o0 += OB) {
       Acc96 acc[OB][TN];
@@ -469,44 +489,45 @@ __global__ void __launch_bounds__(128, 6) k_conv_mac96_kernel(const u64* rot, u6
 #pragma unroll
         for (int v = 0; v < TN; v++) acc[t][v] = Acc96{0, 0, 0};
       int pending = 0;
-      // terms in the order (c, b, a); the words of the next term are loaded before the products
-      // of the current one, so the load overlaps them
-      auto load = [&](int c, int b, int a) {
-        const u64* p = rot + ((size_t)(c * w_in + stride * jp + b) * k + a) * 2 * LN + off;
-        if constexpr (TN == 2) return *reinterpret_cast<const ulonglong2*>(p);
-        else return make_ulonglong2(*p, 0);
-      };
-      ulonglong2 nx = load(0, 0, 0);
-      int c = 0, b = 0, a = 0;
+      const u64* cbase = rot + (size_t)stride * jp * k * 2 * LN + off;  // channel 0, b = 0, a = 0
+      const u64* p = cbase;
+      const u64* wr = sw64 + o0;
+      ulonglong2 nx = *reinterpret_cast<const ulonglong2*>(p);  // loaded a term ahead
+      int r = 0;                                                // (b, a) index inside the channel
       for (int term = 0; term < T; term++) {
-        const u64 x[2] = {nx.x, nx.y};
-        const u64* wr = sw64 + (size_t)o0 * T + (c * k + a) * k + b;
-        if (++a == k) {
-          a = 0;
-          if (++b == k) {
-            b = 0;
-            ++c;
-          }
+        const u64 x0 = nx.x, x1 = nx.y;
+        if (++r == kk) {
+          r = 0;
+          cbase += chan;
+          p = cbase;
+        } else {
+          p += step;
         }
-        if (term + 1 < T) nx = load(c, b, a);
+        if (term + 1 < T) nx = *reinterpret_cast<const ulonglong2*>(p);
         if (pending == room) {  // uniform across the block
 #pragma unroll
           for (int t = 0; t < OB; t++)
 #pragma unroll
             for (int v = 0; v < TN; v++) {
-              const u64 r = reduce96(acc[t][v], md);
-              acc[t][v] = Acc96{(u32)r, (u32)(r >> 32), 0};
+              const u64 rr = reduce96(acc[t][v], md);
+              acc[t][v] = Acc96{(u32)rr, (u32)(rr >> 32), 0};
             }
           pending = 0;
         }
         pending++;
 #pragma unroll
-        for (int t = 0; t < OB; t++)
-          if (o0 + t < c_out) {
-            const u64 wt = wr[(size_t)t * T];
-#pragma unroll
-            for (int v = 0; v < TN; v++) mac96(acc[t][v], x[v], wt);
+        for (int t2 = 0; t2 < OB / 2; t2++) {
+          const ulonglong2 ww = reinterpret_cast<const ulonglong2*>(wr)[t2];
+          if (o0 + 2 * t2 < c_out) {
+            mac96(acc[2 * t2][0], x0, ww.x);
+            mac96(acc[2 * t2][1], x1, ww.x);
           }
+          if (o0 + 2 * t2 + 1 < c_out) {
+            mac96(acc[2 * t2 + 1][0], x0, ww.y);
+            mac96(acc[2 * t2 + 1][1], x1, ww.y);
+          }
+        }
+        wr += cp;
       }
 #pragma unroll
       for (int t = 0; t < OB; t++)
@@ -974,7 +995,17 @@ void k_add(const Ctx& C, const u64* a, const u64* b, u64* out, int n_polys, int 
   HE_LAUNCH(k_add_kernel, (size_t)n_polys * limbs * C.N, 8.0 * (double)C.N * 3 * n_polys * limbs, a, b, out, n_polys, limbs, C.dev_ptab(), C.log_n);
 }
 void k_tensor(const Ctx& C, const u64* a, const u64* b, u64* d, int n, int limbs) {
-  HE_LAUNCH_P(k_tensor_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 7 * n * limbs, 4.0 * C.N * n * limbs, a, b, d, n, limbs, C.dev_ptab(), C.log_n);
+  if (n <= 0) return;
+  if (n > 65535) throw Error(1, "more than 65535 ciphertexts in one product launch");
+  const size_t LN = (size_t)limbs * C.N;
+  // a few words a thread, one grid row per ciphertext
+  const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>((LN + kBlock - 1) / kBlock,
+                                                                     (152 * 32 + (size_t)n - 1) / (size_t)n * 4));
+  const double bytes = 8.0 * (double)C.N * limbs * n * (a == b ? 5.0 : 7.0);
+  void* tok = prof_begin("k_tensor_kernel", C.stream, bytes, (a == b ? 3.0 : 4.0) * C.N * n * limbs);
+  k_tensor_kernel<<<dim3(gx, (unsigned)n), kBlock, 0, C.stream>>>(a, b, d, n, limbs, C.dev_ptab(), C.log_n);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
 }
 void k_ks_inner(const Ctx& C, const u64* ext, const u64* own, size_t own_stride, const KeyPtrs& keys, int S, u64* u,
                 int n, int limbs) {
@@ -1079,7 +1110,7 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
     // 8 output channels x 2 coefficients a thread (48 words of sums); 16 channels take two passes
     // over the rotated inputs, which the idle memory bandwidth absorbs
     constexpr int OB96 = 8, TN96 = 2;
-    const size_t smem64 = (size_t)c_out * c_in * k * k * 8;
+    const size_t smem64 = (size_t)((c_out + 1) & ~1) * c_in * k * k * 8;
     const unsigned gx = (unsigned)((C.N / TN96 + TH - 1) / TH);
     unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * 2 * narrow));
     if (gz > (unsigned)w_out) gz = (unsigned)w_out;
