@@ -727,6 +727,63 @@ def fp64_square_layer_error(checks) -> float:
 
 
 # ---------------------------------------------------------------------------
+# Table I's whole CNN in the single-ciphertext layout (--workload table1)
+# ---------------------------------------------------------------------------
+TABLE1_METRIC = ("encrypted Table I CNN images/s (CONV 4x3x3, ACT-1, FC-1 2704->64, ACT-2, FC-2 64->10 on 28x28 "
+                 "images, N=2^16), the paper's single-ciphertext layout")
+
+
+def run_table1(args, rank, world, local_rank):
+    """Table I's CNN through the paper's own method: 32 images of 28 x 28 per ciphertext in 32 x 32
+    blocks, CONV by Alg. 4, ACT-1, FC-1 and FC-2 by Alg. 3 (table1.forward), at the CNN parameters
+    (N = 2^16, Q = 60 + 12 x 45, P = 2 x 60), all twelve levels. One step = one inference of one
+    ciphertext of 32 images; timed with CUDA events on the context's stream."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api, load, table1
+    lib = load()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    g = api.Context.from_preset(synthetic.CNN_N16, seed=7000 + rank, stream=stream.cuda_stream)
+    geo = table1.Geometry(h=28, w=28, k=3, Hb=32, Wb=32, channels=4, fc1_out=64, fc2_out=10, slots=g.N // 2)
+    t0 = time.perf_counter()
+    g.keygen(table1.rotation_steps(geo))
+    keygen_s = time.perf_counter() - t0
+    wts = synthetic.table1_weights(seed=202)
+    imgs = synthetic.images(geo.images, 28, 28, seed=703)
+    model = table1.encrypt_model(g, geo, wts)
+    x = g.vr_encrypt_images(imgs, 32, 32, 0)
+    g.synchronize()
+    for _ in range(max(1, args.warmup)):
+        table1.forward(g, geo, x, model)
+    g.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = lib.he_kernel_launches()
+    reps = max(1, args.steps)
+    ev0.record(stream)
+    for _ in range(reps):
+        out = table1.forward(g, geo, x, model)
+    ev1.record(stream)
+    ev1.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3 / reps
+    launches = (lib.he_kernel_launches() - l0) // reps
+    got = table1.logits(g, geo, out)
+    tm = max_over_ranks(t, world)
+    return {"value": geo.images * world / tm, "ms_per_step": 1e3 * tm, "launches": launches,
+            "keygen_s": keygen_s, "rotation_keys": len(table1.rotation_steps(geo)), "images": geo.images,
+            "check": (got, imgs, wts)}
+
+
+def fp64_table1_error(check) -> float:
+    """CPU leg: max |decrypted logits - FP64 Table I CNN|."""
+    from oracle import fp64_ref
+    from paper_2512_18646_gb300 import table1
+    got, imgs, wts = check
+    return float(np.abs(got - fp64_ref.table1_cnn(imgs, wts, table1.ACT1, table1.ACT2)).max())
+
+
+# ---------------------------------------------------------------------------
 # the serving workload (--workload serve)
 # ---------------------------------------------------------------------------
 SERVE_METRIC = ("served encrypted-CNN images/s and p50/p99 latency (Poisson arrivals, image sides {64,128,256}, "
@@ -931,7 +988,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "serve"],
+    ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "table1", "serve"],
                     default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
     ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
@@ -971,6 +1028,26 @@ def main():
                               "gpu_launches": res["plain_launches"]},
                     "algorithmic_bytes_per_layer": res["alg_bytes"], "GBps": res["GBps"],
                     "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_square_layer_error(res["checks"])}
+            print(json.dumps(line))
+        return
+
+    if args.workload == "table1" and args.impl == "gpu":
+        res = run_table1(args, rank, world, local_rank)
+        if rank == 0:
+            line = {"metric": TABLE1_METRIC, "value": res["value"], "unit": "images/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                    "data": "synthetic",
+                    "config": {"workload": "Table I CNN on 32 synthetic 28x28 images U[0,1] per ciphertext (32x32 "
+                                           "blocks): CONV 4 kernels 3x3 stride 1 (Alg. 4), ACT-1, FC-1 2704->64 and "
+                                           "FC-2 64->10 (Alg. 3, tau_b-encoded weights), ACT-2; synthetic weights "
+                                           "(seed 202); RNS-CKKS N=2^16, Q=60+12x45, P=2x60, alpha=2, 12 levels",
+                               "parallelism": f"replicas x{world}"},
+                    "path": "paper_2512_18646_gb300.table1.forward: he_vr_conv2d, he_poly_act, he_vr_matmul, "
+                            "he_rotate, he_add, he_add_slots, he_ctset_drop_levels",
+                    "gpu_launches": res["launches"], "images_per_ciphertext": res["images"],
+                    "rotation_keys": res["rotation_keys"], "keygen_s": res["keygen_s"],
+                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_table1_error(res["check"])}
             print(json.dumps(line))
         return
 

@@ -410,6 +410,24 @@ int he_rescale(he_ctx* ctx, he_ctset* inout);
 /* Add(a_i, b_i) pairwise (same level and scale). */
 int he_add(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out);
 
+/* Add with a plaintext operand (Sec. II-A's Add; Alg. 3 starts its accumulator
+ * from such a constant, e.g. a dense layer's bias), in place on component 0:
+ * he_add_slots encodes the real slot vectors v (n_vec = 1: one vector of N/2
+ * values for every ciphertext; n_vec = the set size: one per ciphertext) at the
+ * set's own scale, reduces them modulo the set's primes and adds them;
+ * he_add_plain_coeffs takes the encoded integer plaintexts m [n_vec][N]
+ * instead. HE_E_ARG for another n_vec; refused (HE_E_STATE) on a set made
+ * before an open capture. */
+int he_add_slots(he_ctx* ctx, he_ctset* inout, const double* v, int n_vec);
+int he_add_plain_coeffs(he_ctx* ctx, he_ctset* inout, const int64_t* m, int n_vec);
+
+/* Modulus dropping: a new set holding every polynomial's residues modulo
+ * q_0 .. q_{limbs-1} only (the same ciphertexts modulo a smaller Q, no
+ * division, the scale unchanged), e.g. to bring an operand encrypted at the
+ * top level down to its partner's level before a product. HE_E_LEVEL unless
+ * 1 <= limbs <= the set's limbs. The caller frees *out. */
+int he_ctset_drop_levels(he_ctx* ctx, const he_ctset* in, int limbs, he_ctset** out);
+
 /* ---- decryption (Dec_sk, Sec. II-A) ---- */
 
 /*

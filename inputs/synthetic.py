@@ -118,6 +118,36 @@ def cnn_weights(side: int = 128, std: float = 0.05, seed: int = 302) -> CnnWeigh
     return CnnWeights(c1w, c1b, c2w, c2b, fcw, fcb)
 
 
+@dataclasses.dataclass
+class Table1Weights:
+    """Table I's CNN: CONV (c kernels k x k, stride 1) -> ACT-1 -> FC-1 -> ACT-2 -> FC-2."""
+    conv_w: np.ndarray  # [c][k][k]
+    conv_b: np.ndarray  # [c]
+    fc1_w: np.ndarray   # [c][ho][wo][fc1_out], inputs in (channel, row, column) order
+    fc1_b: np.ndarray   # [fc1_out]
+    fc2_w: np.ndarray   # [fc1_out][fc2_out]
+    fc2_b: np.ndarray   # [fc2_out]
+
+
+def table1_weights(h: int = 28, w: int = 28, c: int = 4, k: int = 3, fc1_out: int = 64, fc2_out: int = 10,
+                   seed: int = 202) -> Table1Weights:
+    """Synthetic weights of Table I's shapes (the trained MNIST weights are not available):
+    kernels and biases N(0, 0.1^2); dense weights N(0, 1 / fan_in) scaled by 0.5 so that the
+    activations stay in the range the degree-3 fits of Table I were made for; dense biases
+    N(0, 0.05^2)."""
+    g = _rng(seed)
+    ho, wo = h - k + 1, w - k + 1
+    n1 = c * ho * wo
+    return Table1Weights(
+        conv_w=g.normal(0.0, 0.1, size=(c, k, k)),
+        conv_b=g.normal(0.0, 0.1, size=(c,)),
+        fc1_w=g.normal(0.0, 0.5 / np.sqrt(n1), size=(c, ho, wo, fc1_out)),
+        fc1_b=g.normal(0.0, 0.05, size=(fc1_out,)),
+        fc2_w=g.normal(0.0, 0.5 / np.sqrt(fc1_out), size=(fc1_out, fc2_out)),
+        fc2_b=g.normal(0.0, 0.05, size=(fc2_out,)),
+    )
+
+
 def batched_matmul_shapes(count: int = 64, seed: int = 401,
                           choices=(16, 32, 64, 128, 256)) -> List[Tuple[int, int, int]]:
     """(m, n, p) triples drawn i.i.d. uniformly from `choices`."""

@@ -256,6 +256,17 @@ class Oracle:
         _check(self.lib.oc_add(self.h, _p(a, _u64p), _p(b, _u64p), a.shape[0], a.shape[1], _p(out, _u64p)))
         return out
 
+    def add_plain(self, ct, m) -> np.ndarray:
+        """Add with a plaintext operand (Sec. II-A's Add): ct [polys][lp][N] (coefficient domain)
+        plus the encoded integer plaintext m [N] on component 0, limb i taken modulo q_i."""
+        ct = _u64(ct).copy()
+        m = np.asarray(m, dtype=np.int64)
+        for i in range(ct.shape[1]):
+            q = int(self.q[i])
+            r = np.mod(m, np.int64(q)).astype(np.uint64)
+            ct[0, i] = (ct[0, i] + r) % np.uint64(q)
+        return ct
+
     def tensor(self, a, b) -> np.ndarray:
         a, b = _u64(a), _u64(b)
         out = np.zeros((3,) + a.shape[1:], np.uint64)

@@ -49,3 +49,15 @@ def cnn(images: np.ndarray, wts) -> np.ndarray:
     x = conv2d(x, wts.conv1_w, wts.conv1_b, 2) ** 2
     x = conv2d(x, wts.conv2_w, wts.conv2_b, 2) ** 2
     return dense(x, wts.fc_w, wts.fc_b)
+
+
+def table1_cnn(images: np.ndarray, wts, act1, act2) -> np.ndarray:
+    """Table I's CNN in FP64 on images [B][h][w]: CONV (wts.conv_w [c][k][k] + bias, stride 1,
+    valid), ACT-1, FC-1 over the (channel, row, column)-ordered features, ACT-2, FC-2 -> logits
+    [B][fc2_out]; act1, act2 the coefficients of x^0 .. x^3."""
+    c, k = wts.conv_w.shape[0], wts.conv_w.shape[1]
+    y = conv2d(images[:, None], wts.conv_w[:, None], wts.conv_b, 1)  # [B][c][ho][wo]
+    act = lambda v, a: a[0] + a[1] * v + a[2] * v ** 2 + a[3] * v ** 3  # noqa: E731
+    y = act(y, act1)
+    z = act(y.reshape(y.shape[0], -1) @ wts.fc1_w.reshape(-1, wts.fc1_w.shape[-1]) + wts.fc1_b, act2)
+    return z @ wts.fc2_w + wts.fc2_b

@@ -97,6 +97,9 @@ SIGNATURES = {
     "he_relinearize": (I, [V, V]),
     "he_rescale": (I, [V, V]),
     "he_add": (I, [V, V, V, PV]),
+    "he_add_slots": (I, [V, V, P_D, I]),
+    "he_add_plain_coeffs": (I, [V, V, P_I64, I]),
+    "he_ctset_drop_levels": (I, [V, V, I, PV]),
     "he_decrypt_slots": (I, [V, V, P_D, SZ]),
     "he_decrypt_matrix": (I, [V, V, I, I, P_D]),
     "he_decrypt_matrix_volley": (I, [V, V, I, I, P_D]),

@@ -376,6 +376,27 @@ class Context:
     def add(self, a: CtSet, b: CtSet) -> CtSet:
         return self._set(load().he_add, self.h, a.h, b.h)
 
+    def add_slots(self, x: CtSet, v) -> CtSet:
+        """In place: component 0 of every ciphertext gains the slot vector(s) v ([N/2] for all,
+        or [n][N/2] one per ciphertext), encoded at x's scale."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        n_vec = 1 if v.ndim == 1 else v.shape[0]
+        full = np.zeros((n_vec, self.N // 2))
+        full[:, : v.shape[-1]] = v.reshape(n_vec, -1)
+        check(load().he_add_slots(self.h, x.h, _ptr(full, P_D), n_vec))
+        return x
+
+    def add_plain_coeffs(self, x: CtSet, m) -> CtSet:
+        """In place: component 0 of every ciphertext gains the encoded plaintext(s) m ([N] or [n][N])."""
+        mm = np.ascontiguousarray(m, dtype=np.int64)
+        n_vec = 1 if mm.ndim == 1 else mm.shape[0]
+        check(load().he_add_plain_coeffs(self.h, x.h, _ptr(mm, P_I64), n_vec))
+        return x
+
+    def drop_levels(self, x: CtSet, limbs: int) -> CtSet:
+        """A new set: x modulo its first `limbs` primes (scale unchanged)."""
+        return self._set(load().he_ctset_drop_levels, self.h, x.h, limbs)
+
     def relinearize(self, x: CtSet) -> CtSet:
         check(load().he_relinearize(self.h, x.h))
         return x

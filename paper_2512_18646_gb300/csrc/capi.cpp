@@ -760,6 +760,38 @@ int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int
   });
 }
 
+int he_ctset_drop_levels(he_ctx* ctx, const he_ctset* in, int limbs, he_ctset** out) {
+  return guard([&] {
+    REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
+    REQUIRE(limbs >= 1 && limbs <= in->s->limbs, HE_E_LEVEL, "the target level must keep 1 .. limbs primes");
+    *out = wrap(drop_limbs(ctx->c, *in->s, limbs));
+  });
+}
+
+int he_add_plain_coeffs(he_ctx* ctx, he_ctset* inout, const int64_t* m, int n_vec) {
+  return guard([&] {
+    REQUIRE(ctx && inout && m, HE_E_ARG, "null argument");
+    REQUIRE(n_vec == 1 || n_vec == inout->s->n, HE_E_ARG, "one plaintext, or one per ciphertext");
+    REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
+            "in-place operation on a set made before the capture");
+    add_plain(ctx->c, *inout->s, m, n_vec);
+  });
+}
+
+int he_add_slots(he_ctx* ctx, he_ctset* inout, const double* v, int n_vec) {
+  return guard([&] {
+    REQUIRE(ctx && inout && v, HE_E_ARG, "null argument");
+    REQUIRE(n_vec == 1 || n_vec == inout->s->n, HE_E_ARG, "one slot vector, or one per ciphertext");
+    REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
+            "in-place operation on a set made before the capture");
+    Ctx& C = ctx->c;
+    const size_t M = C.N / 2;
+    std::vector<int64_t> m((size_t)n_vec * C.N);
+    for (int k = 0; k < n_vec; k++) encode_real(C, v + (size_t)k * M, M, inout->s->scale, m.data() + (size_t)k * C.N);
+    add_plain(C, *inout->s, m.data(), n_vec);
+  });
+}
+
 int he_relinearize(he_ctx* ctx, he_ctset* inout) {
   return guard([&] {
     REQUIRE(ctx && inout, HE_E_ARG, "null argument");

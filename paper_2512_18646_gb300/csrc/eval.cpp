@@ -286,11 +286,34 @@ static std::unique_ptr<CtSet> times_integer(Ctx& C, const CtSet& x, int64_t v) {
 }
 
 // the same ciphertexts without their last limb (modulus drop; the scale is unchanged)
-static std::unique_ptr<CtSet> drop_last_limb(Ctx& C, const CtSet& x) {
-  auto out = new_set(C, x.n, x.polys, x.limbs - 1, x.scale);
-  k_copy_limbs(C, x.buf.p, (size_t)x.limbs * C.N, out->buf.p, (size_t)(x.limbs - 1) * C.N, (size_t)x.n * x.polys,
-               x.limbs - 1);
+// The set modulo q_0 .. q_{limbs-1} only: the residues of the remaining primes, unchanged
+// (modulus dropping without division; the scale stays).
+std::unique_ptr<CtSet> drop_limbs(Ctx& C, const CtSet& x, int limbs) {
+  if (limbs < 1 || limbs > x.limbs) throw Error(1, "the target level must keep 1 .. limbs primes");
+  auto out = new_set(C, x.n, x.polys, limbs, x.scale);
+  k_copy_limbs(C, x.buf.p, (size_t)x.limbs * C.N, out->buf.p, (size_t)limbs * C.N, (size_t)x.n * x.polys, limbs);
   return out;
+}
+static std::unique_ptr<CtSet> drop_last_limb(Ctx& C, const CtSet& x) { return drop_limbs(C, x, x.limbs - 1); }
+
+// Plaintext addition: component 0 of ciphertext c gains the encoded integer plaintext m[c]
+// (n_vec = set size) or m[0] (n_vec = 1), reduced modulo the set's primes and transformed
+// (the plaintext carries the set's scale, so the slots add).
+void add_plain(Ctx& C, CtSet& x, const int64_t* m, int n_vec) {
+  if (n_vec != 1 && n_vec != x.n) throw Error(1, "one plaintext, or one per ciphertext");
+  const int lp = x.limbs;
+  const size_t N = C.N;
+  DevBuf mi((size_t)n_vec * N, C.stream);
+  // pageable source: the call returns once the data is staged
+  HE_CUDA(cudaMemcpyAsync(mi.p, m, (size_t)n_vec * N * 8, cudaMemcpyHostToDevice, C.stream));
+  DevBuf pt((size_t)n_vec * lp * N, C.stream);
+  const LimbMap lm = limbs_q(lp, N);
+  k_reduce_signed(C, reinterpret_cast<const int64_t*>(mi.p), pt.p, n_vec, lm);
+  ntt_forward(C, pt.p, n_vec, lm);
+  for (int c = 0; c < x.n; c++) {
+    u64* c0 = x.ct(c);
+    k_add(C, c0, pt.p + (size_t)(n_vec == 1 ? 0 : c) * lp * N, c0, 1, lp);
+  }
 }
 
 // Degree-3 activation (the ACT layers of Table I), depth two, evaluated as

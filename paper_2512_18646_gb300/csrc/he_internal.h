@@ -326,6 +326,8 @@ std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<con
                                                    const std::vector<const CtSet*>& Bs, const std::vector<int>& ps);
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in);
 // degree-3 activation c0 + c1 x + c2 x^2 + c3 x^3 (coeffs c[0..3]); two levels, three components out
+std::unique_ptr<CtSet> drop_limbs(Ctx& C, const CtSet& x, int limbs);
+void add_plain(Ctx& C, CtSet& x, const int64_t* m, int n_vec);
 std::unique_ptr<CtSet> poly_act3(Ctx& C, const CtSet& x, const double* c);
 
 std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b);

@@ -721,3 +721,93 @@ def test_work_budget_chunks_are_bit_identical(lib):
         g.close()
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
+
+
+def test_table1_network_single_ciphertext(lib):
+    """Table I's CNN (CONV, ACT-1, FC-1, ACT-2, FC-2) in the paper's single-ciphertext layout at a
+    reduced size (N = 2^11: 16 images of 6 x 6 in 8 x 8 blocks, 2 kernels 3 x 3, FC-1 from 2 x 4 x 4
+    inputs to 32 outputs in two groups of 16, FC-2 to 4 outputs), twelve levels: every stage
+    bit-exact with the oracle from the same plaintexts and seeds (CONV per kernel after ACT-1, each
+    FC-1 group, FC-1 with its bias, ACT-2, FC-2 with its bias), the logits within 1e-3 of FP64;
+    then the network from the library's own encoders (table1.encrypt_model / forward) against
+    FP64."""
+    from paper_2512_18646_gb300 import table1
+    geo = table1.Geometry(h=6, w=6, k=3, Hb=8, Wb=8, channels=2, fc1_out=32, fc2_out=4, slots=1024)
+    o, g = make_pair(11, (60,) + (40,) * 12, 1, 60, 1, 40.0, seed=43, steps=table1.rotation_steps(geo))
+    S, n, m, p1, p2 = o.slots, geo.n, geo.images, geo.p1, geo.p2
+    assert (n, m, p1, p2) == (64, 16, 16, 4)
+    wts = synthetic.table1_weights(h=6, w=6, c=2, k=3, fc1_out=32, fc2_out=4, seed=44)
+    imgs = synthetic.images(m, 6, 6, seed=45)
+    lp = o.L1
+
+    def mm_masks(limbs, p):
+        mv = layouts.vr_matmul_masks(m, n, p, S)
+        return np.stack([o.encode(mv[0], float(o.q[limbs - 2]))] +
+                        [o.encode(v, float(o.q[limbs - 3])) for v in mv[1:]])
+
+    ox, gx = encrypt_both(o, g, encode_columns(o, layouts.vr_images(imgs, S, 8, 8)), ct_id_base=0)
+    cmasks = np.stack([o.encode(v, float(o.q[lp - 2])) for v in layouts.vr_masks(3, 6, 6, S, 8, 8)])
+    ys_o, ys_g = [], []
+    s1 = None
+    for c in range(2):
+        ks = layouts.vr_kernelspanner(wts.conv_w[c], 6, 6, S, 8, 8)
+        ms = np.stack([o.encode(v, float(o.q[lp - 1])) for v in ks])
+        os_, gs = encrypt_both(o, g, ms, ct_id_base=20 + 10 * c, scale=float(o.q[lp - 1]))
+        mb = o.encode(layouts.vr_bias(float(wts.conv_b[c]), 3, 6, 6, S, 8, 8))[None]
+        ob, gb = encrypt_both(o, g, mb, limbs=lp - 2, ct_id_base=90 + c)
+        gy = g.vr_conv2d_coeffs(gx, gs, gb, 3, 8, cmasks)
+        g.relinearize(g.poly_act(gy, table1.ACT1))
+        oy3, s1 = o.poly_act3(o.vr_conv2d(ox, os_, ob[0], 3, 8, cmasks), table1.ACT1, o.scale)
+        oy = o.relin(oy3[0])
+        assert np.array_equal(gy.export()[0], oy), c
+        ys_o.append(oy)
+        ys_g.append(gy)
+    l1 = lp - 4
+    B1 = table1.fc1_blocks(geo, wts.fc1_w)
+    masks1 = mm_masks(l1, p1)
+    oz, gz = None, None
+    for t in range(B1.shape[1]):
+        ozt, gzt = None, None
+        for c in range(2):
+            obb, gbb = encrypt_both(o, g, encode_columns(o, layouts.vr_matrix_b(B1[c, t], S)[None]),
+                                    ct_id_base=200 + 10 * c + t)
+            gbd = g.drop_levels(gbb, l1)
+            assert gbd.limbs == l1 and gbd.scale == gbb.scale
+            op = o.vr_matmul(ys_o[c], obb[0][:, :l1], n, p1, masks1)
+            gp = g.vr_matmul_coeffs(ys_g[c], gbd, m, n, p1, masks1)
+            ozt = op if ozt is None else o.add(ozt, op)
+            gzt = gp if gzt is None else g.add(gzt, gp)
+        if t > 0:
+            ozt = o.rotate(ozt, [-t * p1])[0]
+            gzt = g.rotate(gzt, [-t * p1])
+        assert np.array_equal(gzt.export()[0], ozt), t
+        oz = ozt if oz is None else o.add(oz, ozt)
+        gz = gzt if gz is None else g.add(gz, gzt)
+    sz = (s1 * o.scale) / float(o.q[l1 - 1])
+    assert gz.scale == sz
+    mb1 = o.encode(table1.row_vector(geo, wts.fc1_b), sz)
+    oz = o.add_plain(oz, mb1)
+    g.add_plain_coeffs(gz, mb1)
+    assert np.array_equal(gz.export()[0], oz)
+    oa3, s2 = o.poly_act3(oz[None], table1.ACT2, sz)
+    oa = o.relin(oa3[0])
+    g.relinearize(g.poly_act(gz, table1.ACT2))
+    assert np.array_equal(gz.export()[0], oa)
+    l2 = l1 - 5
+    ob2, gb2 = encrypt_both(o, g, encode_columns(o, layouts.vr_matrix_b(table1.fc2_block(geo, wts.fc2_w), S)[None]),
+                            ct_id_base=300)
+    masks2 = mm_masks(l2, p2)
+    oo = o.vr_matmul(oa, ob2[0][:, :l2], n, p2, masks2)
+    go = g.vr_matmul_coeffs(gz, g.drop_levels(gb2, l2), m, n, p2, masks2)
+    so = (s2 * o.scale) / float(o.q[l2 - 1])
+    mb2 = o.encode(table1.row_vector(geo, wts.fc2_b), so)
+    oo = o.add_plain(oo, mb2)
+    g.add_plain_coeffs(go, mb2)
+    assert go.limbs == 1
+    assert np.array_equal(go.export()[0], oo)
+    ref = fp64_ref.table1_cnn(imgs, wts, table1.ACT1, table1.ACT2)
+    assert np.abs(table1.logits(g, geo, go) - ref).max() < 1e-3
+    # the library's own encoders end to end
+    model = table1.encrypt_model(g, geo, wts)
+    out = table1.forward(g, geo, g.vr_encrypt_images(imgs, 8, 8, 0), model)
+    assert np.abs(table1.logits(g, geo, out) - ref).max() < 1e-3

@@ -309,6 +309,21 @@ def test_cmul_scalar_and_plain(small):
     assert np.abs(small.decrypt(r) - w * x).max() < 1e-6
 
 
+def test_add_plain_adds_slots(small):
+    """Add with a plaintext operand decrypts to the slotwise sum; a plaintext that is not reduced
+    modulo the primes (a negative constant) is taken modulo each prime."""
+    rng = np.random.default_rng(13)
+    x, v = rng.uniform(-1, 1, small.slots), rng.uniform(-1, 1, small.slots)
+    a = small.encrypt(small.encode(x), ct_id=21)
+    assert np.abs(small.decrypt(small.add_plain(a, small.encode(v))) - (x + v)).max() < 1e-6
+    c = np.full(small.slots, -0.75)
+    assert np.abs(small.decrypt(small.add_plain(a, small.encode(c))) - (x - 0.75)).max() < 1e-6
+    # adding to component 1 instead would not decrypt to the sum: the pin sees the component
+    wrong = a.copy()
+    wrong[1] = small.add_plain(a[1:2], small.encode(v))[0]
+    assert np.abs(small.decrypt(wrong) - (x + v)).max() > 1e-2
+
+
 # ---------------------------------------------------------------------------
 # Paper's worked examples in the plaintext slot simulator (P8, P9)
 # ---------------------------------------------------------------------------
