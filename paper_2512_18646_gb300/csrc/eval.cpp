@@ -606,41 +606,55 @@ std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A_any, const CtSet& Bbar, 
   if (n < 1 || (n & (n - 1)) || p < 1) throw Error(1, "n must be a power of two and p positive");
   std::vector<long> shifts(p);
   for (int idx = 0; idx < p; idx++) shifts[idx] = (long)idx * n;
-  auto R = rotate(C, Bbar, shifts);  // [1][p]
-  const double sc = (A.scale * Bbar.scale) / (double)C.q[lp - 1];
-  auto acc = new_set(C, 1, 2, lp - 3, sc);
-  const size_t fw = (size_t)(lp - 2) * C.N;
-  auto masked = [&](const CtSet& x, const u64* m) {  // rescale(x (x) m)
-    auto W = new_set(C, 1, 2, x.limbs, x.scale);
-    const u64* xs0 = x.buf.p;
-    DevBuf dxs(1, C.stream);
-    // pageable source: the call returns once the pointer is staged
-    HE_CUDA(cudaMemcpyAsync(dxs.p, &xs0, 8, cudaMemcpyHostToDevice, C.stream));
-    k_pack_blocks(C, (const u64* const*)dxs.p, m, 1, 1, x.limbs, W->buf.p);
-    rescale_inplace(C, *W);
-    W->scale = x.scale;
-    return W;
-  };
-  for (int idx = 0; idx < p; idx++) {
-    SetView ri(*R, idx, 1);
-    auto T = mul(C, A, ri.s);
-    relinearize(C, *T);
-    for (int t = 1; t < n; t *= 2) {
-      auto r = rotate(C, *T, {(long)t});
-      k_add(C, T->buf.p, r->buf.p, T->buf.p, 2, T->limbs);
-    }
-    auto U = masked(*T, E);
-    T.reset();
-    for (int t = 1; t < n; t *= 2) {
-      auto r = rotate(C, *U, {-(long)t});
-      k_add(C, U->buf.p, r->buf.p, U->buf.p, 2, U->limbs);
-    }
-    auto Dd = masked(*U, F + (size_t)idx * fw);
-    if (idx == 0)
-      HE_CUDA(cudaMemcpyAsync(acc->buf.p, Dd->buf.p, Dd->buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
-    else
-      k_add(C, acc->buf.p, Dd->buf.p, acc->buf.p, 2, lp - 3);
+  auto R = rotate(C, Bbar, shifts);  // [p]: RowShifter applied idx times
+  // the p revolver positions run side by side as one set of p ciphertexts (each position's
+  // arithmetic is unchanged): T_idx = relin(rescale(A (x) R_idx))
+  auto Ap = new_set(C, p, 2, lp, A.scale);
+  k_copy_limbs(C, A.buf.p, 0, Ap->buf.p, A.ct_words(), (size_t)p, 2 * lp);
+  auto T = mul(C, *Ap, *R);
+  Ap.reset();
+  R.reset();
+  relinearize(C, *T);
+  const double sc = T->scale;  // (A.scale Bbar.scale) / q_{lp-1}
+  // SumColVec, left half: T += Rot(T, t)
+  for (int t = 1; t < n; t *= 2) {
+    auto r = rotate(C, *T, {(long)t});
+    k_add(C, T->buf.p, r->buf.p, T->buf.p, 2 * p, T->limbs);
   }
+  // U = rescale(T (x) E) for every position (E at scale q_{lp-2}, so the scale stays)
+  auto U = new_set(C, p, 2, T->limbs, sc);
+  {
+    const u64* x0 = T->buf.p;
+    DevBuf dx(1, C.stream);
+    // pageable source: the call returns once the pointer is staged
+    HE_CUDA(cudaMemcpyAsync(dx.p, &x0, 8, cudaMemcpyHostToDevice, C.stream));
+    k_pack_blocks(C, (const u64* const*)dx.p, E, 1, p, T->limbs, U->buf.p);
+  }
+  T.reset();
+  rescale_inplace(C, *U);
+  U->scale = sc;
+  // SumColVec, right half: U += Rot(U, -t)
+  for (int t = 1; t < n; t *= 2) {
+    auto r = rotate(C, *U, {-(long)t});
+    k_add(C, U->buf.p, r->buf.p, U->buf.p, 2 * p, U->limbs);
+  }
+  // D_idx = rescale(U_idx (x) F_idx), then acc = sum over idx
+  const size_t fw = (size_t)U->limbs * C.N;
+  auto D = new_set(C, p, 2, U->limbs, sc);
+  {
+    std::vector<const u64*> xs(p);
+    for (int idx = 0; idx < p; idx++) xs[idx] = U->ct(idx);
+    DevBuf dxs((size_t)p, C.stream);
+    // pageable source: the call returns once the pointers are staged
+    HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)p * 8, cudaMemcpyHostToDevice, C.stream));
+    for (int idx = 0; idx < p; idx++)
+      k_pack_blocks(C, (const u64* const*)dxs.p + idx, F + (size_t)idx * fw, 1, 1, U->limbs, D->ct(idx));
+  }
+  U.reset();
+  rescale_inplace(C, *D);
+  auto acc = new_set(C, 1, 2, lp - 3, sc);
+  HE_CUDA(cudaMemcpyAsync(acc->buf.p, D->ct(0), acc->buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+  for (int idx = 1; idx < p; idx++) k_add(C, acc->buf.p, D->ct(idx), acc->buf.p, 2, lp - 3);
   return acc;
 }
 
