@@ -532,30 +532,54 @@ std::unique_ptr<CtSet> vr_conv2d(Ctx& C, const CtSet& in_any, const CtSet& S, co
   }
   auto out = new_set(C, in.n, 2, lp - 2, D);
   const size_t mw = (size_t)(lp - 1) * C.N;
-  for (int c = 0; c < in.n; c++) {
-    SetView xc(in, c, 1);
-    HE_CUDA(cudaMemcpyAsync(out->ct(c), bias.buf.p, bias.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
-    for (int t = 0; t < k * k; t++) {
-      SetView st(S, t, 1);
-      auto T = mul(C, xc.s, st.s);
-      relinearize(C, *T);
-      auto R = rotate(C, *T, col);  // [1][k]
-      T.reset();
-      for (int pos = 1; pos < k; pos++) k_add(C, R->ct(0), R->ct(pos), R->ct(0), 2, lp - 1);
-      SetView U(*R, 0, 1);
-      auto R2 = rotate(C, U.s, row);
-      R.reset();
-      for (int pos = 1; pos < k; pos++) k_add(C, R2->ct(0), R2->ct(pos), R2->ct(0), 2, lp - 1);
-      // V (x) F_t, rescaled: the masked-sum kernel with one term
-      auto W = new_set(C, 1, 2, lp - 1, D);
-      const u64* xs0 = R2->ct(0);
-      DevBuf dxs(1, C.stream);
-      HE_CUDA(cudaMemcpyAsync(dxs.p, &xs0, 8, cudaMemcpyHostToDevice, C.stream));
-      k_pack_blocks(C, (const u64* const*)dxs.p, masks + (size_t)t * mw, 1, 1, lp - 1, W->buf.p);
-      R2.reset();
-      rescale_inplace(C, *W);
-      k_add(C, out->ct(c), W->ct(0), out->ct(c), 2, lp - 2);
+  const int kk = k * k;
+  // the k^2 offsets of one input ciphertext run side by side as one set (each offset's
+  // arithmetic is unchanged); sum_pos R[t][pos] for every offset t: gather R[.][pos] (one
+  // launch) and add it to the running sums (one launch)
+  auto sum_steps = [&](const CtSet& R, int limbs) {
+    const size_t cw = R.ct_words();
+    auto U = new_set(C, kk, 2, limbs, R.scale);
+    k_copy_limbs(C, R.buf.p, (size_t)k * cw, U->buf.p, cw, (size_t)kk, 2 * limbs);
+    if (k > 1) {
+      DevBuf g((size_t)kk * cw, C.stream);
+      for (int pos = 1; pos < k; pos++) {
+        k_copy_limbs(C, R.ct(pos), (size_t)k * cw, g.p, cw, (size_t)kk, 2 * limbs);
+        k_add(C, U->buf.p, g.p, U->buf.p, 2 * kk, limbs);
+      }
     }
+    return U;
+  };
+  for (int c = 0; c < in.n; c++) {
+    // T_t = relin(rescale(X_c (x) S_t)) for every offset t
+    auto Xr = new_set(C, kk, 2, lp, in.scale);
+    k_copy_limbs(C, in.ct(c), 0, Xr->buf.p, in.ct_words(), (size_t)kk, 2 * lp);
+    auto T = mul(C, *Xr, S);
+    Xr.reset();
+    relinearize(C, *T);
+    // SumForConv: the column pass (Rot by pos) then the row pass (Rot by pos Wb)
+    auto R = rotate(C, *T, col);  // [t][pos]
+    T.reset();
+    auto U = sum_steps(*R, lp - 1);
+    R.reset();
+    auto R2 = rotate(C, *U, row);  // [t][pos]
+    U.reset();
+    auto V = sum_steps(*R2, lp - 1);
+    R2.reset();
+    // W_t = rescale(V_t (x) F_t): the masked-sum kernel with one term per offset
+    auto W = new_set(C, kk, 2, lp - 1, D);
+    {
+      std::vector<const u64*> xs(kk);
+      for (int t = 0; t < kk; t++) xs[t] = V->ct(t);
+      DevBuf dxs((size_t)kk, C.stream);
+      // pageable source: the call returns once the pointers are staged
+      HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)kk * 8, cudaMemcpyHostToDevice, C.stream));
+      for (int t = 0; t < kk; t++)
+        k_pack_blocks(C, (const u64* const*)dxs.p + t, masks + (size_t)t * mw, 1, 1, lp - 1, W->ct(t));
+    }
+    V.reset();
+    rescale_inplace(C, *W);
+    HE_CUDA(cudaMemcpyAsync(out->ct(c), bias.buf.p, bias.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+    for (int t = 0; t < kk; t++) k_add(C, out->ct(c), W->ct(t), out->ct(c), 2, lp - 2);
   }
   out->scale = D;  // kernels at scale q_l and masks at q_{l-1}, which the two rescales remove
   return out;
