@@ -861,6 +861,7 @@ int oc_export_key(void* h, uint64_t key_id, uint64_t* out) {
 
 int oc_encrypt(void* h, const int64_t* m, int limbs, uint64_t ct_id, uint64_t* ct) {
   OC_TRY(Ctx* C = (Ctx*)h; if (limbs < 1 || limbs > C->L1) throw std::runtime_error("bad level");
+         if (C->pk0.size() != (size_t)C->L1) throw std::runtime_error("no public key (call keygen first)");
          Ct r = encrypt(*C, m, limbs, ct_id); ct_to(*C, r, ct));
 }
 // m' = sum_t c_t s^t, CRT-centred, as doubles [N]

@@ -811,3 +811,46 @@ def test_table1_network_single_ciphertext(lib):
     model = table1.encrypt_model(g, geo, wts)
     out = table1.forward(g, geo, g.vr_encrypt_images(imgs, 8, 8, 0), model)
     assert np.abs(table1.logits(g, geo, out) - ref).max() < 1e-3
+
+
+def test_plaintext_add_and_drop_levels(lib):
+    """Add with a plaintext operand and modulus dropping: bit-exact with the oracle from the same
+    plaintexts and seeds (two and three components, one plaintext for the set or one per
+    ciphertext), the slots decrypting to the sums; dropped sets keep their scale and decrypt to the
+    same values; argument and level errors."""
+    from paper_2512_18646_gb300 import HeError
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_LEVEL
+    o, g = make_pair(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=47, steps=())
+    S = o.slots
+    rng = np.random.default_rng(48)
+    x, v = rng.uniform(-1, 1, (3, S)), rng.uniform(-1, 1, (3, S))
+    ox, gx = encrypt_both(o, g, encode_columns(o, x), ct_id_base=5)
+    mv = encode_columns(o, v)
+    # one plaintext per ciphertext
+    g.add_plain_coeffs(gx, mv)
+    want = np.stack([o.add_plain(ox[i], mv[i]) for i in range(3)])
+    assert np.array_equal(gx.export(), want)
+    assert np.abs(g.decrypt_slots(gx) - (x + v)).max() < 1e-6
+    # one plaintext for the set, on a three-component product
+    d = g.mul(gx, gx)
+    od = np.stack([o.rescale(o.tensor(want[i], want[i])) for i in range(3)])
+    assert np.array_equal(d.export(), od)
+    g.add_plain_coeffs(d, mv[0])
+    assert np.array_equal(d.export(), np.stack([o.add_plain(od[i], mv[0]) for i in range(3)]))
+    # the library's own encoding at the set's scale
+    y = g.encrypt_coeffs(encode_columns(o, x), o.L1, o.scale, 40)
+    g.add_slots(y, v[1])
+    assert np.abs(g.decrypt_slots(y) - (x + v[1])).max() < 1e-6
+    # dropping primes: the same residues, the same scale, the same values
+    low = g.drop_levels(y, 2)
+    assert low.limbs == 2 and low.scale == y.scale
+    full = y.export().reshape(3, 2, o.L1, o.N)
+    assert np.array_equal(low.export().reshape(3, 2, 2, o.N), full[:, :, :2])
+    assert np.abs(g.decrypt_slots(low) - (x + v[1])).max() < 1e-6
+    for bad in (0, o.L1 + 1):
+        with pytest.raises(HeError) as e:
+            g.drop_levels(y, bad)
+        assert e.value.code == HE_E_LEVEL
+    with pytest.raises(HeError) as e:
+        g.add_plain_coeffs(y, mv[:2])  # two plaintexts for three ciphertexts
+    assert e.value.code == HE_E_ARG
