@@ -990,10 +990,16 @@ def oracle_sample(batch: int):
 
 
 def cpu_cores():
+    """Threads the oracle runs on: its OpenMP thread count (OMP_NUM_THREADS when set, else one per
+    core this process may use)."""
     try:
-        return len(os.sched_getaffinity(0))
+        n = len(os.sched_getaffinity(0))
     except AttributeError:
-        return os.cpu_count()
+        n = os.cpu_count() or 1
+    omp = os.environ.get("OMP_NUM_THREADS", "")
+    if omp.isdigit() and int(omp) > 0:
+        n = min(n, int(omp))
+    return n
 
 
 def cpu_model() -> str:
