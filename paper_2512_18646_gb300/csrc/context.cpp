@@ -121,6 +121,36 @@ const DevBuf& Ctx::key(u64 k) const {
   return it->second;
 }
 
+Staging::~Staging() {
+  for (int i = 0; i < kSlots; i++) {
+    if (ev[i]) cudaEventSynchronize(ev[i]), cudaEventDestroy(ev[i]);
+    if (buf[i]) cudaFreeHost(buf[i]);
+  }
+}
+
+void upload_async(Ctx& C, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  if (C.capturing || bytes > Staging::kSlotBytes) {
+    // pageable source: the call returns once the data is staged (a capture refuses it)
+    HE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, C.stream));
+    return;
+  }
+  Staging& S = C.staging;
+  std::lock_guard<std::mutex> lk(S.mu);
+  const int i = S.next;
+  S.next = (i + 1) % Staging::kSlots;
+  if (!S.buf[i]) {
+    HE_CUDA(cudaHostAlloc(&S.buf[i], Staging::kSlotBytes, cudaHostAllocDefault));
+    HE_CUDA(cudaEventCreateWithFlags(&S.ev[i], cudaEventDisableTiming));
+  } else if (S.used[i]) {
+    HE_CUDA(cudaEventSynchronize(S.ev[i]));  // the slot's previous copy has run
+  }
+  std::memcpy(S.buf[i], src, bytes);
+  HE_CUDA(cudaMemcpyAsync(dst, S.buf[i], bytes, cudaMemcpyHostToDevice, C.stream));
+  HE_CUDA(cudaEventRecord(S.ev[i], C.stream));
+  S.used[i] = true;
+}
+
 static void upload(const Ctx& C, u64* dst, const void* src, size_t bytes) {
   HE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, C.stream));
 }

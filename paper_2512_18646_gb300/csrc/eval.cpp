@@ -264,8 +264,7 @@ static DevBuf const_table(Ctx& C, const double* v, int groups, int limbs, double
     for (int i = 0; i < limbs; i++) t[(size_t)g * limbs + i] = residue_of(iv, C.q[i]);
   }
   DevBuf d(t.size(), C.stream);
-  // pageable source: the call returns once the data is staged, so t may go
-  HE_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, d.p, t.data(), t.size() * 8);
   return d;
 }
 
@@ -278,8 +277,7 @@ static std::unique_ptr<CtSet> times_integer(Ctx& C, const CtSet& x, int64_t v) {
     t[2 * i + 1] = (u64)(((unsigned __int128)r << 64) / C.q[i]);
   }
   DevBuf d(t.size(), C.stream);
-  // pageable source: the call returns once the data is staged, so t may go
-  HE_CUDA(cudaMemcpyAsync(d.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, d.p, t.data(), t.size() * 8);
   auto out = new_set(C, x.n, x.polys, x.limbs, x.scale);
   k_mul_const(C, x.buf.p, out->buf.p, (size_t)x.n * x.polys, x.limbs, d.p);
   return out;
@@ -304,8 +302,7 @@ void add_plain(Ctx& C, CtSet& x, const int64_t* m, int n_vec) {
   const int lp = x.limbs;
   const size_t N = C.N;
   DevBuf mi((size_t)n_vec * N, C.stream);
-  // pageable source: the call returns once the data is staged
-  HE_CUDA(cudaMemcpyAsync(mi.p, m, (size_t)n_vec * N * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, mi.p, m, (size_t)n_vec * N * 8);
   DevBuf pt((size_t)n_vec * lp * N, C.stream);
   const LimbMap lm = limbs_q(lp, N);
   k_reduce_signed(C, reinterpret_cast<const int64_t*>(mi.p), pt.p, n_vec, lm);
@@ -385,7 +382,7 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
     }
   }
   DevBuf dw(wt.size(), C.stream);
-  HE_CUDA(cudaMemcpyAsync(dw.p, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, dw.p, wt.data(), wt.size() * 8);
   auto out = new_set(C, c_out * w_out, 2, lp, in.scale);
   // temporaries per input ciphertext: a gathered copy, its k rotations, its ModUp digits and, per
   // non-trivial step, the key sums, their P part and the ModDown result
@@ -428,7 +425,7 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
         for (int i = 0; i < lp - 1; i++) t[((size_t)(o * w_out + j) * 2) * (lp - 1) + i] = residue_of(iv, C.q[i]);
     }
     cb = DevBuf(t.size(), C.stream);
-    HE_CUDA(cudaMemcpyAsync(cb.p, t.data(), t.size() * 8, cudaMemcpyHostToDevice, C.stream));
+    upload_async(C, cb.p, t.data(), t.size() * 8);
   }
   rescale_inplace(C, *out, bias ? cb.p : nullptr);
   out->scale = in.scale;
@@ -571,8 +568,7 @@ std::unique_ptr<CtSet> vr_conv2d(Ctx& C, const CtSet& in_any, const CtSet& S, co
       std::vector<const u64*> xs(kk);
       for (int t = 0; t < kk; t++) xs[t] = V->ct(t);
       DevBuf dxs((size_t)kk, C.stream);
-      // pageable source: the call returns once the pointers are staged
-      HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)kk * 8, cudaMemcpyHostToDevice, C.stream));
+      upload_async(C, dxs.p, xs.data(), (size_t)kk * 8);
       for (int t = 0; t < kk; t++)
         k_pack_blocks(C, (const u64* const*)dxs.p + t, masks + (size_t)t * mw, 1, 1, lp - 1, W->ct(t));
     }
@@ -601,8 +597,7 @@ std::unique_ptr<CtSet> vrot(Ctx& C, const CtSet& in_any, long r, int hw, const u
   const size_t cw = in.ct_words();
   const u64* xs[2] = {R->buf.p, R->buf.p + cw};
   DevBuf dxs(2, C.stream);
-  // pageable source: the call returns once the pointers are staged
-  HE_CUDA(cudaMemcpyAsync(dxs.p, xs, 16, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, dxs.p, xs, 16);
   auto out = new_set(C, in.n, 2, in.limbs, in.scale);
   k_pack_blocks(C, (const u64* const*)dxs.p, masks, 2, in.n, in.limbs, out->buf.p, 2 * cw);
   R.reset();
@@ -650,8 +645,7 @@ std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A_any, const CtSet& Bbar, 
   {
     const u64* x0 = T->buf.p;
     DevBuf dx(1, C.stream);
-    // pageable source: the call returns once the pointer is staged
-    HE_CUDA(cudaMemcpyAsync(dx.p, &x0, 8, cudaMemcpyHostToDevice, C.stream));
+    upload_async(C, dx.p, &x0, 8);
     k_pack_blocks(C, (const u64* const*)dx.p, E, 1, p, T->limbs, U->buf.p);
   }
   T.reset();
@@ -669,8 +663,7 @@ std::unique_ptr<CtSet> vr_matmul(Ctx& C, const CtSet& A_any, const CtSet& Bbar, 
     std::vector<const u64*> xs(p);
     for (int idx = 0; idx < p; idx++) xs[idx] = U->ct(idx);
     DevBuf dxs((size_t)p, C.stream);
-    // pageable source: the call returns once the pointers are staged
-    HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)p * 8, cudaMemcpyHostToDevice, C.stream));
+    upload_async(C, dxs.p, xs.data(), (size_t)p * 8);
     for (int idx = 0; idx < p; idx++)
       k_pack_blocks(C, (const u64* const*)dxs.p + idx, F + (size_t)idx * fw, 1, 1, U->limbs, D->ct(idx));
   }
@@ -700,8 +693,7 @@ std::unique_ptr<CtSet> reform(Ctx& C, const CtSet& in_any, int gap, int h, const
   std::vector<const u64*> xs(h);
   for (int i = 0; i < h; i++) xs[i] = R->buf.p + (size_t)i * cw;
   DevBuf dxs((size_t)h, C.stream);
-  // pageable source: the call returns once the pointers are staged
-  HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)h * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, dxs.p, xs.data(), (size_t)h * 8);
   auto out = new_set(C, in.n, 2, in.limbs, in.scale);
   k_pack_blocks(C, (const u64* const*)dxs.p, masks, h, in.n, in.limbs, out->buf.p, (size_t)h * cw);
   R.reset();
@@ -911,7 +903,7 @@ DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int li
   const size_t total = (size_t)out_dim * n_in;
   for (size_t c0 = 0; c0 < total; c0 += chunk) {
     const int cn = (int)std::min<size_t>(chunk, total - c0);
-    HE_CUDA(cudaMemcpyAsync(dm.p, pts_host + c0 * N, (size_t)cn * N * 8, cudaMemcpyHostToDevice, C.stream));
+    upload_async(C, dm.p, pts_host + c0 * N, (size_t)cn * N * 8);
     k_reduce_signed(C, (const int64_t*)dm.p, pts.p + c0 * per, cn, limbs_q(limbs, N));
     ntt_forward(C, pts.p + c0 * per, cn, limbs_q(limbs, N));
   }
@@ -946,8 +938,7 @@ std::unique_ptr<CtSet> pack_blocks(Ctx& C, const std::vector<const u64*>& xs, in
   if (T < 1 || n_ct < 1) throw Error(1, "nothing to pack");
   if (limbs < 2) throw Error(2, "packing needs one level");
   DevBuf dxs((size_t)T, C.stream);
-  // pageable source: the call returns once the pointers are staged
-  HE_CUDA(cudaMemcpyAsync(dxs.p, xs.data(), (size_t)T * 8, cudaMemcpyHostToDevice, C.stream));
+  upload_async(C, dxs.p, xs.data(), (size_t)T * 8);
   auto x = new_set(C, n_ct, 2, limbs, scale);
   k_pack_blocks(C, (const u64* const*)dxs.p, masks, T, n_ct, limbs, x->buf.p);
   rescale_inplace(C, *x);

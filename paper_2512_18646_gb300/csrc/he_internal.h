@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -82,6 +83,24 @@ struct LimbMap {
   }
 };
 
+// Page-locked staging for small host-to-device uploads (weight and constant tables, pointer
+// tables): a copy from it returns at once, where a copy from pageable memory can block the host
+// until the stream reaches it (and the GPU then idles while the host queues the next launches).
+// Slots are reused round-robin once their previous copy's event has completed.
+struct Staging {
+  static constexpr int kSlots = 16;
+  static constexpr size_t kSlotBytes = (size_t)1 << 20;
+  void* buf[kSlots] = {};
+  cudaEvent_t ev[kSlots] = {};
+  bool used[kSlots] = {};
+  int next = 0;
+  std::mutex mu;
+  Staging() = default;
+  Staging(const Staging&) = delete;
+  Staging& operator=(const Staging&) = delete;
+  ~Staging();
+};
+
 struct Ctx {
   int device = 0;
   int log_n = 0;
@@ -119,6 +138,8 @@ struct Ctx {
   bool capturing = false;
   uint64_t capture_gen = 0;
   std::vector<std::unique_ptr<CtSet>> deferred;
+
+  Staging staging;
 
   // keys
   bool has_keys = false;
@@ -326,6 +347,9 @@ std::vector<std::unique_ptr<CtSet>> matmul_batched(Ctx& C, const std::vector<con
                                                    const std::vector<const CtSet*>& Bs, const std::vector<int>& ps);
 std::unique_ptr<CtSet> square(Ctx& C, const CtSet& in);
 // degree-3 activation c0 + c1 x + c2 x^2 + c3 x^3 (coeffs c[0..3]); two levels, three components out
+// host -> device copy on the context stream through the staging slots (pageable copy during a
+// capture, which refuses it, or above a slot's size); src may be reused when the call returns
+void upload_async(Ctx& C, void* dst, const void* src, size_t bytes);
 std::unique_ptr<CtSet> drop_limbs(Ctx& C, const CtSet& x, int limbs);
 void add_plain(Ctx& C, CtSet& x, const int64_t* m, int n_vec);
 std::unique_ptr<CtSet> poly_act3(Ctx& C, const CtSet& x, const double* c);
