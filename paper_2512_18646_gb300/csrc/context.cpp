@@ -130,7 +130,12 @@ Staging::~Staging() {
 
 void upload_async(Ctx& C, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
-  if (C.capturing || bytes > Staging::kSlotBytes) {
+  // A capture of the context's stream, opened by he_graph_begin or by the caller directly (its own
+  // cudaStreamBeginCapture or a framework's graph capture), must not record a copy from a staging
+  // slot: a later call reuses the slot, so a replay would read another call's data.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HE_CUDA(cudaStreamIsCapturing(C.stream, &cs));
+  if (C.capturing || cs != cudaStreamCaptureStatusNone || bytes > Staging::kSlotBytes) {
     // pageable source: the call returns once the data is staged (a capture refuses it)
     HE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, C.stream));
     return;

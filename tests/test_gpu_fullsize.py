@@ -64,10 +64,15 @@ def test_conv_layer_n15_64x64(lib):
 
 
 def test_cnn_n16_128x128(lib):
-    """The CNN of bench.py at N = 2^16 on 256 images: conv-1 outputs sampled bit for bit, logits vs FP64."""
+    """The CNN of bench.py at N = 2^16 on 256 images: conv-1 and conv-2 outputs sampled bit for bit
+    (the oracle computes the conv-1 columns that conv-2 needs itself), logits vs FP64.
+
+    Conv-2 (8 input channels, 3x3: 72 terms per output) takes the 96-bit multiply-accumulate's
+    mid-sum reduction and its second pass of 8 output channels at the full size."""
     from paper_2512_18646_gb300 import api
     pre = synthetic.CNN_N16
     B, side, H = 256, 128, 128
+    h1, h2 = synthetic.cnn_shapes(side)
     o = Oracle.from_preset(pre, seed=301)
     g = api.Context.from_preset(pre, seed=301)
     o.keygen([1, 2, 3, 4])
@@ -77,25 +82,64 @@ def test_cnn_n16_128x128(lib):
     m = _columns(o, imgs, H)
     gx = g.encrypt_coeffs(m, o.L1, o.scale, 0)
     gy = g.conv2d(gx, 1, 1, w.conv1_w, w.conv1_b, 2)
-    got = gy.export().reshape(8, 62, 2, o.L1 - 1, o.N)
-    # oracle: conv-1 output columns 0 and 61 (inputs 0..4 and 122..126)
-    X = np.zeros((1, 128, 2, o.L1, o.N), np.uint64)
-    for j in list(range(5)) + list(range(122, 127)):
-        X[0, j] = o.encrypt(m[j], o.L1, j)
-    sel = [(c, jp) for c in range(8) for jp in (0, 61)]
-    oy = o.conv2d(X, 1, w.conv1_w, w.conv1_b, 2, o.scale, sel=sel)
-    for t, (c, jp) in enumerate(sel):
-        assert np.array_equal(got[c, jp], oy[t]), (c, jp)
-    # the rest of the network on the GPU, logits against the FP64 CNN
+    # conv-2's first and last output column (jp2 = 0 and h2 - 1) read conv-1 output columns
+    # 2 jp2 + b (b < 3) of every channel, which read input columns 4 jp2 .. 4 jp2 + 8
+    wins = (0, h2 - 1)
+    got1 = {(jp2, c, b): gy.slice(c * h1 + 2 * jp2 + b, 1).export()[0]
+            for jp2 in wins for c in range(8) for b in range(3)}
     g.square(gy)
+    sc = o.scale * o.scale / o.q[o.L1 - 2]
+    assert gy.scale == sc
     y = g.conv2d(gy, 8, 2, w.conv2_w, w.conv2_b, 2)
+    # the oracle from its own encryptions of each 9-column input window (the convolution is the same
+    # at every column offset, so a window's outputs are output columns 0..2 / 0 of the window)
+    for jp2 in wins:
+        X = np.stack([o.encrypt(m[j], o.L1, j) for j in range(4 * jp2, 4 * jp2 + 9)])[None]
+        sel = [(c, b) for c in range(8) for b in range(3)]
+        oy = o.conv2d(X, 1, w.conv1_w, w.conv1_b, 2, o.scale, sel=sel)
+        for t, (c, b) in enumerate(sel):
+            assert np.array_equal(got1[(jp2, c, b)], oy[t]), ("conv-1", jp2, c, b)
+        X2 = o.square(oy).reshape(8, 3, 3, o.L1 - 2, o.N)
+        oy2 = o.conv2d(X2, 2, w.conv2_w, w.conv2_b, 2, sc, sel=[(c, 0) for c in range(16)])
+        for c in range(16):
+            got = y.slice(c * h2 + jp2, 1).export()[0]
+            assert np.array_equal(got, oy2[c]), ("conv-2", c, jp2)
+        del X, oy, X2, oy2
+    del got1
+    # the rest of the network on the GPU, logits against the FP64 CNN
     g.square(y)
-    _, h2 = synthetic.cnn_shapes(side)
     pts = g.fc_prepare(w.fc_w, 16, h2, h2, 4, H, B, y.limbs)
     z = g.fc_apply(y, pts, w.fc_b)
     logits = layouts.logits_from_fc(g.decrypt_slots(z), B, H)
     ref = fp64_ref.cnn(imgs, w)
     assert np.abs(logits - ref).max() < 1e-4
+
+
+def test_fc_n16_480_columns(lib):
+    """The CNN's dense layer at its full size and level (N = 2^16, 9 limbs, 16 x 30 = 480 input
+    ciphertexts, rows at gap 4 in blocks of 128, 10 outputs) on seeded random residues and random
+    plaintexts: outputs 0 and 9 (the first and the second pass over outputs) bit for bit against the
+    oracle. 480 columns reduce the 96-bit sums of the 45-bit limbs several times per output."""
+    from paper_2512_18646_gb300 import api
+    pre = synthetic.CNN_N16
+    c_in, w_in, gap, H, out_dim, lp = 16, 30, 4, 128, 10, 9
+    o = Oracle.from_preset(pre, seed=303)
+    g = api.Context.from_preset(pre, seed=303)
+    steps = [4, 8, 16, 32, 64]
+    o.keygen(steps)
+    g.keygen(steps)
+    rng = np.random.default_rng(303)
+    X = np.empty((c_in * w_in, 2, lp, o.N), np.uint64)
+    for i in range(lp):
+        X[:, :, i, :] = rng.integers(0, o.primes[i], (c_in * w_in, 2, o.N), dtype=np.uint64)
+    pts = rng.integers(-(1 << 62), 1 << 62, (out_dim, c_in, w_in, o.N), dtype=np.int64)
+    bias = rng.normal(0, 0.05, out_dim)
+    gz = g.fc_apply(g.import_coeffs(X, o.scale), g.fc_prepare_coeffs(pts, gap, H, lp), bias)
+    sel = [0, out_dim - 1]
+    oz = o.fc(X.reshape(c_in, w_in, 2, lp, o.N), gap, H, pts[sel], bias, o.scale, sel)
+    got = gz.export()
+    for t, oi in enumerate(sel):
+        assert np.array_equal(got[oi], oz[t]), oi
 
 
 def test_conv_layer_encrypted_kernels_n15_64x64(lib):

@@ -268,6 +268,62 @@ def test_conv2d_matches_oracle_and_fp64(lib, stride, c_in, k, side):
     assert np.abs(got - ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("c_out,polys", [(16, 2), (11, 3)])
+def test_conv2d_96bit_sums_reduce_mid_sum_and_run_two_channel_passes(lib, c_out, polys):
+    """The second convolution's shape with 45-bit working primes: c_in = 8, k = 3 gives 72 terms per
+    output, more than the 63 products a 96-bit sum of 45-bit residues holds, so the multiply-
+    accumulate reduces in the middle of each sum; 16 (and a ragged 11) output channels run as two
+    passes of 8 over the same rotated inputs. Gap 2 and stride 2 as after a strided first layer;
+    the three-component case is the square's unrelinearised output. Bit-exact with the oracle."""
+    o, g = make_pair(10, (60,) + (45,) * 6, 2, 60, 2, 45.0, seed=41, steps=[2, 4])
+    H, side, Bn, c_in, k, stride, gap = 32, 13, 3, 8, 3, 2, 2
+    rng = np.random.default_rng(41 + c_out)
+    imgs = rng.uniform(-1, 1, (Bn, c_in, side, side))
+    K = rng.normal(0, 0.2, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.2, c_out)
+    z = np.concatenate([layouts.image_columns(imgs[:, c], o.slots, H, gap) for c in range(c_in)])
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=2000)
+    sc = o.scale
+    if polys == 3:
+        ox = o.square(ox)
+        g.square(gx)
+        sc = sc * sc / o.q[o.L1 - 1]
+        assert gx.scale == sc and gx.polys == 3
+    ox = ox.reshape(c_in, side, *ox.shape[1:])
+    gy = g.conv2d(gx, c_in, gap, K, bias, stride)
+    oy = o.conv2d(ox, gap, K, bias, stride, sc)
+    assert oy.shape[0] == c_out * ((side - k) // stride + 1)
+    assert np.array_equal(gy.export(), oy)
+    x = imgs ** 2 if polys == 3 else imgs
+    ref = fp64_ref.conv2d(x, K, bias, stride)
+    got = g.decrypt_image(gy, Bn, H, gap * stride, ref.shape[2])
+    got = got.reshape(Bn, c_out, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
+    assert np.abs(got - ref).max() < 1e-4
+
+
+def test_fc_96bit_sums_over_480_columns(lib):
+    """The dense layer's shape (16 channels x 30 columns = 480 input ciphertexts, rows at gap 4 in
+    blocks of 128) with 45-bit working primes: the 96-bit sums are reduced every ~63 columns, several
+    times per output, and the 10 outputs run as two passes. Bit-exact with the oracle, FP64 within 1e-4."""
+    o, g = make_pair(10, (60,) + (45,) * 4, 2, 60, 2, 45.0, seed=43, steps=[4, 8, 16, 32, 64])
+    c_in, hv, w_in, gap, H, out_dim = 16, 30, 30, 4, 128, 10
+    Bn = o.slots // H
+    rng = np.random.default_rng(43)
+    x = rng.uniform(-1, 1, (Bn, c_in, hv, w_in))
+    W = rng.normal(0, 0.05, (out_dim, c_in * hv * w_in))
+    b = rng.normal(0, 0.05, out_dim)
+    z = np.concatenate([layouts.image_columns(x[:, c], o.slots, H, gap) for c in range(c_in)])
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=0)
+    ox = ox.reshape(c_in, w_in, *ox.shape[1:])
+    lp = o.L1
+    pts = o.fc_plaintexts(lp, c_in, hv, w_in, gap, H, Bn, W, list(range(out_dim)))
+    oz = o.fc(ox, gap, H, pts, b, o.scale, list(range(out_dim)))
+    gz = g.fc_apply(gx, g.fc_prepare_coeffs(pts, gap, H, lp), b)
+    assert np.array_equal(gz.export(), oz)
+    logits = layouts.logits_from_fc(g.decrypt_slots(gz), Bn, H)
+    assert np.abs(logits - fp64_ref.dense(x, W, b)).max() < 1e-4
+
+
 @pytest.mark.parametrize("stride,c_in,k", [(1, 1, 3), (2, 3, 3), (2, 2, 5)])
 def test_conv2d_encrypted_kernels_matches_oracle_and_fp64(lib, stride, c_in, k):
     """Encrypted kernels (the model provider's ciphertexts): bit-exact with the oracle from the same
@@ -686,6 +742,59 @@ def test_graph_capture_failure_leaves_context_usable(lib):
     A, Bm = np.arange(6.0).reshape(2, 3) / 6, np.arange(6.0).reshape(3, 2) / 6
     C = g.decrypt_matrix(g.matmul(g.encrypt_matrix_a(A, 0), g.encrypt_matrix_b(Bm, 5), 2, 2), 2, 2)
     assert np.abs(C - A @ Bm).max() < 1e-5
+
+
+def test_direct_capture_of_the_context_stream_is_refused_loudly(lib):
+    """A capture the caller opens on the context's stream itself (torch's CUDA graph on that stream,
+    not he_graph_begin) must not record a copy from the context's page-locked staging slots, which
+    later calls reuse: a call that uploads host data (a convolution's weights) fails the capture
+    with an error instead, calls without uploads capture and replay like eager calls, and the
+    context keeps giving its eager results afterwards."""
+    import torch
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HeError
+    s = torch.cuda.Stream()
+    g = api.Context(10, (60, 40, 40, 40), 1, 60, 1, 40.0, seed=79, stream=s.cuda_stream)
+    g.keygen([1, 2])
+    rng = np.random.default_rng(79)
+    imgs = rng.uniform(0, 1, (2, 8, 8))
+    K, bias = rng.normal(0, 0.3, (2, 1, 3, 3)), rng.normal(0, 0.3, 2)
+    x = g.encrypt_image(imgs, 16, ct_id_base=0)
+    eager = g.conv2d(x, 1, 1, K, bias, 1).export()
+    g.synchronize()
+    # many uploads before the capture so that every staging slot holds some other call's data
+    for _ in range(20):
+        g.conv2d(x, 1, 1, K * 0.5, bias, 1)
+    g.synchronize()
+    refused = False
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gr.capture_begin()
+        try:
+            g.conv2d(x, 1, 1, K, bias, 1)
+        except HeError:
+            refused = True
+        finally:
+            try:
+                gr.capture_end()
+            except RuntimeError:
+                refused = True
+    assert refused
+    # a call without host uploads captures and replays bit-identically
+    y = g.conv2d(x, 1, 1, K, bias, 1)
+    g.synchronize()
+    want = g.add(y, y).export()
+    gr2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gr2.capture_begin()
+        z = g.add(y, y)
+        gr2.capture_end()
+    for _ in range(20):
+        g.conv2d(x, 1, 1, K * 0.25, bias, 1)
+    gr2.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(z.export(), want)
+    assert np.array_equal(g.conv2d(x, 1, 1, K, bias, 1).export(), eager)
 
 
 def test_work_budget_chunks_are_bit_identical(lib):

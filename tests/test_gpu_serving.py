@@ -9,6 +9,8 @@
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 
@@ -128,6 +130,58 @@ def test_server_results_same_alone_and_in_the_mix(served):
             assert np.abs(out[k][0] - ref).max() < TOL, k
         assert np.abs(out[2][0] - alone).max() < TOL
         assert np.abs(alone - fp64_ref.cnn(imgs[2][None], w[32])[0]).max() < TOL
+    finally:
+        srv.close()
+
+
+def test_server_admits_requests_that_arrive_while_a_batch_runs(served):
+    """Continuous batching on the GPU: requests submitted while another request's batch is on the GPU
+    (the server never paused) are admitted at once, while that batch still runs, and run together
+    in the next batch; each late request's logits equal its alone run within 1e-4 and the FP64 CNN."""
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_REQ_RUNNING
+    g, w = served
+    imgs = synthetic.images(4, 32, 32, seed=95)
+    reqs = [_request(g, imgs[k], 32, 7000 + 100 * k) for k in range(4)]
+    srv = api.Server(g, {32: w[32]}, hbm_budget_bytes=16 << 30, max_blocks=8)
+    try:
+        alone = {}
+        for k in (1, 2, 3):
+            rid = srv.submit(reqs[k], 32)
+            assert srv.wait(rid, 120_000)
+            z, blk, _ = srv.take(rid)
+            alone[k] = _logits(g, z, blk, 32)
+        for attempt in range(3):
+            b0 = srv.stats()["batches"]
+            first = srv.submit(reqs[0], 32)
+            deadline = time.monotonic() + 120
+            while srv.poll(first) < HE_REQ_RUNNING:
+                assert time.monotonic() < deadline
+                time.sleep(0.0002)
+            late = {k: srv.submit(reqs[k], 32) for k in (1, 2, 3)}
+            assert srv.wait(first, 120_000)
+            _, blk0, t0 = srv.take(first)
+            out = {}
+            for k, rid in late.items():
+                assert srv.wait(rid, 120_000)
+                z, blk, t = srv.take(rid)
+                out[k] = (_logits(g, z, blk, 32), blk, t)
+            if all(out[k][2][0] < t0[3] for k in out):
+                break  # every late request arrived while the first batch was on the GPU
+        else:
+            pytest.fail("the first batch ended before the late requests were submitted, three times")
+        assert blk0 == 0
+        for k, (logit, blk, t) in out.items():
+            assert t0[2] <= t[0] < t0[3], k          # submitted while the first batch ran
+            assert t[1] < t0[3], k                    # admitted (device budget reserved) during it
+            assert t[2] >= t0[3], k                   # run in a later batch
+            assert np.abs(logit - alone[k]).max() < TOL, k
+            ref = fp64_ref.cnn(imgs[k][None], w[32])[0]
+            assert np.abs(logit - ref).max() < TOL, k
+        # the three late requests shared one batch, in submission order
+        assert sorted(out[k][1] for k in out) == [0, 1, 2]
+        assert len({out[k][2][2] for k in out}) == 1
+        assert srv.stats()["batches"] == b0 + 2
     finally:
         srv.close()
 
