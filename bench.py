@@ -15,6 +15,16 @@ plaintext products and rotate-and-add of the dense layer, all on the NTT
 engine. Inputs are synthetic (seeded), already encrypted and resident in
 device memory when the timed region starts; they are larger than L2.
 
+The default run (N = 1) also measures the other configurations of the
+method, each in a process of its own before the CNN runs, and reports each
+JSON line whole under "workloads": 4096 small matmuls A(4x8) B(8x4) at
+N = 2^13 (plain calls, one batched call, its CUDA graph); one conv + x^2 layer
+on 64x64 images at N = 2^15; 64 matmuls of uneven m, n, p at N = 2^16
+(zero-rotation layout, baby-step giant-step, batched and plain revolver); a
+Poisson stream of CNN requests of sides 64/128/256 served by continuous
+batching against one request at a time (p50/p99). Each carries its own
+clock record and oracle baseline. --no-extra skips them.
+
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the
 same workload on the host cores and reports the same metric.
 """
@@ -410,6 +420,7 @@ def run_matmul(args, rank, world, local_rank):
     launches_b = launches_v = 0
     max_err = max_err_v = 0.0
     rng_seed = 402
+    clk = ClockSampler(local_rank).__enter__()
     for wave in waves:
         As, Bs, mats = [], [], []
         for i in wave:
@@ -464,6 +475,7 @@ def run_matmul(args, rank, world, local_rank):
         for t in range(len(wave)):
             max_err_v = max(max_err_v, float(np.abs(g.decrypt_matrix_volley(vouts[t], ms[t], ps[t]) - mats[t]).max()))
         del vouts, Vs, Bs
+    clk.__exit__()
     total = len(shapes)
     t_b = max_over_ranks(t_batched, world)
     t_p = max_over_ranks(t_plain, world)
@@ -476,7 +488,8 @@ def run_matmul(args, rank, world, local_rank):
             "bsgs_value": total * world / max_over_ranks(t_bsgs, world), "bsgs_ms": 1e3 * max_over_ranks(t_bsgs, world),
             "revolver_launches": launches_b, "revolver_max_abs_err": max_err, "keygen_s": keygen_s,
             "waves": len(waves), "revolver_rotations": rot, "revolver_tensors": sum(n * p for _, n, p in shapes),
-            "volley_tensors": sum(G * n for G, (_, n, _) in zip(groups, shapes)), "volley_rotations": 0}
+            "volley_tensors": sum(G * n for G, (_, n, _) in zip(groups, shapes)), "volley_rotations": 0,
+            "clocks": clk.summary(), "shapes": shapes}
 
 
 # ---------------------------------------------------------------------------
@@ -533,15 +546,16 @@ def run_matmul_small(args, rank, world, local_rank):
 
     for _ in range(max(1, args.warmup)):
         batched()
-    t_plain, l_plain = timed(plain, 1)
-    t_batched, l_batched = timed(batched, max(1, args.steps))
     g.synchronize()
     g.graph_begin()
     outs = g.matmul_batched(As, Bs, ms, ps)
     graph = g.graph_end()
     for _ in range(max(1, args.warmup)):
         graph.launch()
-    t_graph, l_graph = timed(graph.launch, max(1, args.steps))
+    with ClockSampler(local_rank) as clk:
+        t_plain, l_plain = timed(plain, 1)
+        t_batched, l_batched = timed(batched, max(1, args.steps))
+        t_graph, l_graph = timed(graph.launch, max(1, args.steps))
     g.synchronize()
     err = max(float(np.abs(g.decrypt_matrix(outs[t], m, p) - mats[t]).max()) for t in (0, count // 2, count - 1))
     graph.destroy()
@@ -549,7 +563,8 @@ def run_matmul_small(args, rank, world, local_rank):
     return {"value": count * world / t_g, "ms_per_step": 1e3 * t_g, "graph_kernel_launches": l_graph,
             "batched_value": count * world / max_over_ranks(t_batched, world), "batched_ms": 1e3 * t_batched,
             "batched_launches": l_batched, "plain_value": count * world / max_over_ranks(t_plain, world),
-            "plain_ms": 1e3 * t_plain, "plain_launches": l_plain, "max_abs_err": err, "count": count}
+            "plain_ms": 1e3 * t_plain, "plain_launches": l_plain, "max_abs_err": err, "count": count,
+            "clocks": clk.summary()}
 
 
 # ---------------------------------------------------------------------------
@@ -697,8 +712,9 @@ def run_layer(args, rank, world, local_rank):
         return ev0.elapsed_time(ev1) / 1e3 / reps, (lib.he_kernel_launches() - l0) // reps, ys[-1]
 
     reps = max(1, args.steps)
-    t1, l1, y1 = timed(x1, reps)
-    tb, lb, yb = timed(xb, reps)
+    with ClockSampler(local_rank) as clk:
+        t1, l1, y1 = timed(x1, reps)
+        tb, lb, yb = timed(xb, reps)
     # algorithmic bytes of one layer call from the library's per-kernel counts
     lib.he_profile_enable(1)
     layer(xb).free()
@@ -712,7 +728,7 @@ def run_layer(args, rank, world, local_rank):
     t1m, tbm = max_over_ranks(t1, world), max_over_ranks(tb, world)
     return {"value": n_batch * world / tbm, "ms_per_step": 1e3 * tbm, "launches": lb,
             "latency_ms": 1e3 * t1m, "plain_value": world / t1m, "plain_launches": l1,
-            "alg_bytes": alg_bytes, "GBps": alg_bytes / tbm / 1e9, "images_per_set": n_batch,
+            "alg_bytes": alg_bytes, "GBps": alg_bytes / tbm / 1e9, "images_per_set": n_batch, "clocks": clk.summary(),
             "checks": [(dec1, imgs[:1], K, bias), (decb, imgs[:4], K, bias)]}
 
 
@@ -910,6 +926,7 @@ def run_serve(args, rank, world, local_rank):
     out_words = 10 * 2 * (g.L1 - 6) * g.N
     out_buf = torch.empty(out_words, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
     res = {"encrypt_pool_s": t_enc}
+    clk = ClockSampler(local_rank).__enter__()
     for mode, max_blocks, n_req in (("batched", args.max_blocks, n_meas), ("plain", 1, args.plain_requests)):
         t_c = time.perf_counter()
         srv = api.Server(g, w, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_blocks=max_blocks)
@@ -938,6 +955,9 @@ def run_serve(args, rank, world, local_rank):
             "h2d_bytes": int(sum(int(s) * 2 * g.L1 * g.N * 8 for s in side[n_warm:n_warm + n_req])),
             "d2h_bytes": int(n_req * out_words * 8),
         }
+    clk.__exit__()
+    res["clocks"] = clk.summary()
+    res["sides"] = [int(x) for x in side[n_warm:n_warm + n_meas]]
     # accuracy: one request per side through the batched server, against the FP64 CNN (untimed)
     srv = api.Server(g, w, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_blocks=args.max_blocks,
                      start_paused=True)
@@ -963,30 +983,169 @@ def fp64_max_error(checks) -> float:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle: a bounded sample of the same workload
+# CPU oracle: bounded samples of the same workloads
 # ---------------------------------------------------------------------------
-KS_PER_INFERENCE = 128 * 4 + 496 + 496 * 2 + 480 + 10 * 5  # rotations + relinearisations of one step
+def ks_per_inference(side: int) -> int:
+    """Key switches of one CNN inference on a side x side image in the column layout: conv-1 rotates
+    each of the side input columns by 1..4; the square's output (8 h1 three-component ciphertexts) is
+    relinearised as conv-2's input and rotated by 2 and 4; the dense layer takes the second square's
+    three components, relinearises its 10 outputs and sums their blocks by rotations 4 .. side/2."""
+    h1 = (side - 5) // 2 + 1
+    return 4 * side + 8 * h1 + 16 * h1 + 10 + 10 * int(np.log2(side // 4))
 
 
-def oracle_sample(batch: int):
-    """Conv-1 output column 0 (all 8 channels) on the oracle at the full parameters.
+class OracleCnnSample:
+    """Conv-1 output column 0 (all 8 channels) of the CNN on the oracle at the full parameters.
 
-    The sample runs 20 hoisted rotations (5 ModUps) at the top level, 200
-    ciphertext-scalar products and 8 rescales; its time is scaled to one
-    inference by the number of key switches (KS_PER_INFERENCE / 20)."""
+    Set up once (keys, five encrypted input columns); each run() is 5 hoisted ModUps, 20 key switches
+    at the top level, 200 ciphertext-scalar products and 8 rescales, and stands for
+    20 / ks_per_inference(side) of one inference (the oracle's time is dominated by key switching)."""
+
+    def __init__(self, batch: int, side: int = SIDE, H: int = H):
+        from oracle import Oracle, layouts
+        pre = synthetic.CNN_N16
+        self.o = Oracle.from_preset(pre, seed=7)
+        self.o.keygen([1, 2, 3, 4])
+        imgs = synthetic.images(batch, side, 5, seed=301)
+        z = layouts.image_columns(imgs, self.o.slots, H)
+        self.X = np.stack([self.o.encrypt(self.o.encode(z[j]), self.o.L1, j) for j in range(5)])[None]
+        self.w = synthetic.cnn_weights(side, seed=302)
+        self.fraction = 20.0 / ks_per_inference(side)
+
+    def run(self) -> float:
+        t0 = time.perf_counter()
+        self.o.conv2d(self.X, 1, self.w.conv1_w, self.w.conv1_b, 2, self.o.scale, sel=[(c, 0) for c in range(8)])
+        return time.perf_counter() - t0
+
+
+def _cpu(value, unit, sample):
+    return {"value": value, "unit": unit, "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": sample}
+
+
+def oracle_cnn_baseline(batch: int):
+    s = OracleCnnSample(batch)
+    dt = s.run()
+    per_inference = dt / s.fraction
+    return _cpu(batch / per_inference, UNIT,
+                f"conv-1 output column 0 (8 channels, 20 top-level key switches) took {dt:.2f} s; scaled to one "
+                f"inference of {batch} images by key-switch count ({ks_per_inference(SIDE)}/20)")
+
+
+def oracle_matmul_small_baseline(budget_s: float = 10.0):
+    """The whole 4x8 . 8x4 product at N = 2^13 on the oracle (24 hoisted rotations, 32 tensor products,
+    4 relinearisations and rescales), repeated for about budget_s seconds."""
+    from oracle import Oracle, layouts
+    o = Oracle.from_preset(synthetic.MATMUL_SMALL, seed=5)
+    o.keygen([1, 2, 3])
+    A, Bm = synthetic.matmul_operands(4, 8, 4, seed=101)
+    Ac = np.stack([o.encrypt(o.encode(v), o.L1, i) for i, v in enumerate(layouts.matrix_a_columns(A, o.slots))])
+    Bc = np.stack([o.encrypt(o.encode(v), o.L1, 50 + i) for i, v in enumerate(layouts.matrix_b_rows(Bm, o.slots))])
+    reps, t0 = 0, time.perf_counter()
+    while reps == 0 or time.perf_counter() - t0 < budget_s:
+        o.matmul(Ac, Bc, 4)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return _cpu(reps / dt, "HE-matmul/s", f"{reps} whole products (A 4x8, B 8x4, N=2^13) in {dt:.2f} s")
+
+
+def oracle_layer_baseline():
+    """Output column 0 of the conv + x^2 + relinearisation layer (4 channels) at N = 2^15: 3 input columns
+    rotated by 1 and 2 (6 key switches), 36 scalar products, 4 squares and 4 relinearisations; scaled to
+    the whole layer (128 rotations + 248 relinearisations) by key-switch count."""
+    from oracle import Oracle, layouts
+    o = Oracle.from_preset(synthetic.CONV_LAYER, seed=201)
+    o.keygen([1, 2])
+    side, Hs = 64, 64
+    imgs = synthetic.images((o.slots // Hs), side, side, seed=201)
+    K, bias = synthetic.conv_weights(4, 1, 3, 0.1, seed=202)
+    z = layouts.image_columns(imgs[:, :, :3], o.slots, Hs)
+    X = np.stack([o.encrypt(o.encode(z[j]), o.L1, j) for j in range(3)])[None]
+    t0 = time.perf_counter()
+    y = o.square(o.conv2d(X, 1, K, bias, 1, o.scale, sel=[(c, 0) for c in range(4)]))
+    for t in range(4):
+        o.relin(y[t])
+    dt = time.perf_counter() - t0
+    per_layer = dt * (128 + 248) / (6 + 4)
+    return _cpu((o.slots // Hs) / per_layer, "images/s",
+                f"output column 0 of the 4 channels (10 key switches) took {dt:.2f} s; scaled to one layer of "
+                f"{o.slots // Hs} packed images by key-switch count (376/10)")
+
+
+def oracle_matmul_baseline(shapes):
+    """One zero-rotation product of the 64-product workload on the oracle (the one with the fewest tensor
+    products), scaled to all 64 by tensor-product count (sum of G n over the products)."""
     from oracle import Oracle, layouts
     pre = synthetic.CNN_N16
     o = Oracle.from_preset(pre, seed=7)
-    o.keygen([1, 2, 3, 4])
-    imgs = synthetic.images(batch, SIDE, 5, seed=301)
-    z = layouts.image_columns(imgs, o.slots, H)
-    X = np.stack([o.encrypt(o.encode(z[j]), o.L1, j) for j in range(5)])[None]
-    w = synthetic.cnn_weights(SIDE, seed=302)
+    o.keygen([])
+    S = (1 << pre.log_n) // 2
+    cost = [layouts.volley_geometry(S, m, p)[2] * n for m, n, p in shapes]
+    i = int(np.argmin(cost))
+    m, n, p = shapes[i]
+    A, Bm = synthetic.matmul_operands(m, n, p, seed=402 + i)
+    G = layouts.volley_geometry(S, m, p)[2]
+    za = layouts.matrix_a_volley(A, S, p).reshape(G * n, S)
+    Ac = np.stack([o.encrypt(o.encode(v), o.L1, t) for t, v in enumerate(za)]).reshape(G, n, 2, o.L1, o.N)
+    Bc = np.stack([o.encrypt(o.encode(v), o.L1, 10 ** 5 + t) for t, v in enumerate(layouts.matrix_b_rows(Bm, S))])
     t0 = time.perf_counter()
-    o.conv2d(X, 1, w.conv1_w, w.conv1_b, 2, o.scale, sel=[(c, 0) for c in range(8)])
+    o.matmul_volley(Ac, Bc)
     dt = time.perf_counter() - t0
-    per_inference = dt * KS_PER_INFERENCE / 20.0
-    return dt, per_inference
+    total = dt * sum(cost) / cost[i]
+    return _cpu(len(shapes) / total, "HE-matmul/s",
+                f"product {i} (m,n,p)=({m},{n},{p}), {cost[i]} tensor products, zero-rotation layout, took "
+                f"{dt:.2f} s; scaled to the {len(shapes)} products by tensor-product count ({sum(cost)}/{cost[i]})")
+
+
+def oracle_serve_baseline(sides):
+    """Requests served one at a time by the oracle: conv-1 output column 0 of a side-64 request timed,
+    each request's time scaled by its key-switch count (ks_per_inference(side) / 20)."""
+    s = OracleCnnSample(1, side=64, H=64)
+    dt = s.run()
+    per_ks = dt / 20.0
+    lat = np.array([per_ks * ks_per_inference(int(x)) for x in sides])
+    return _cpu(len(sides) / float(lat.sum()), "images/s",
+                f"conv-1 output column 0 of a side-64 request (20 key switches) took {dt:.2f} s; each request "
+                f"of the trace scaled by its key-switch count; serial latency p50 {np.percentile(lat, 50):.0f} s")
+
+
+# ---------------------------------------------------------------------------
+# the other configurations, reported beside the CNN in the default run
+# ---------------------------------------------------------------------------
+# (key, workload, extra arguments): the small matmul (4096 products, plain vs batched vs CUDA graph),
+# the conv + x^2 layer at N = 2^15, the 64 uneven matmuls at N = 2^16 (zero-rotation, baby-step
+# giant-step, batched and plain revolver), and the Poisson serving trace (continuous batching vs one
+# request at a time)
+EXTRA_WORKLOADS = (
+    ("matmul_4x8x4_n13", "matmul_small", ["--steps", "3", "--warmup", "3"]),
+    ("conv_layer_64x64_n15", "layer", ["--steps", "5", "--warmup", "3"]),
+    ("matmul64_uneven_n16", "matmul", []),
+    ("serving_poisson_n16", "serve", []),
+)
+
+
+def run_extra_workloads(args):
+    """Each configuration in a process of its own (its device memory is returned when it exits), before
+    the CNN touches the GPU; its JSON line (with its own clocks and oracle baseline) is kept whole."""
+    out = {}
+    for key, wl, extra in EXTRA_WORKLOADS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, *extra]
+        if args.no_cpu_baseline:
+            cmd.append("--no-cpu-baseline")
+        env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=1200, env=env)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode == 0 and lines:
+                out[key] = json.loads(lines[-1])
+            else:
+                out[key] = {"error": f"exit {r.returncode}: " + (r.stderr.strip().splitlines() or [""])[-1][:300]}
+        except subprocess.TimeoutExpired:
+            out[key] = {"error": "did not finish within 1200 s"}
+        out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+        sys.stderr.write(f"[bench] {key}: {out[key].get('value', out[key].get('error'))} ({out[key]['wall_s']} s)\n")
+    return out
 
 
 def cpu_cores():
@@ -1025,6 +1184,8 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="cnn workload: skip the other configurations (matmul, conv layer, batched matmul, serving)")
     ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "table1", "serve"],
                     default="cnn")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
@@ -1064,7 +1225,9 @@ def main():
                     "plain": {"value": res["plain_value"], "ms": res["latency_ms"], "images_per_set": 1,
                               "gpu_launches": res["plain_launches"]},
                     "algorithmic_bytes_per_layer": res["alg_bytes"], "GBps": res["GBps"],
-                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_square_layer_error(res["checks"])}
+                    "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_square_layer_error(res["checks"]),
+                    "clocks": res["clocks"],
+                    "cpu_baseline": None if args.no_cpu_baseline or world > 1 else oracle_layer_baseline()}
             print(json.dumps(line))
         return
 
@@ -1127,6 +1290,8 @@ def main():
                                "l2": "operands 25.8 GB, larger than L2"},
                     "path": "one he_matmul_batched call captured into a CUDA graph, replayed per step",
                     "gpu_launches": res["graph_kernel_launches"], "max_abs_err_vs_fp64": res["max_abs_err"],
+                    "clocks": res["clocks"],
+                    "cpu_baseline": None if args.no_cpu_baseline or world > 1 else oracle_matmul_small_baseline(),
                     "batched": {"value": res["batched_value"], "ms": res["batched_ms"],
                                 "gpu_launches": res["batched_launches"]},
                     "plain": {"value": res["plain_value"], "ms": res["plain_ms"],
@@ -1155,7 +1320,9 @@ def main():
                                  "max_abs_err_vs_fp64": res["revolver_max_abs_err"],
                                  "rotations": res["revolver_rotations"],
                                  "tensor_products": res["revolver_tensors"]},
-                    "keygen_s": res["keygen_s"], "waves": res["waves"]}
+                    "keygen_s": res["keygen_s"], "waves": res["waves"], "clocks": res["clocks"],
+                    "cpu_baseline": None if args.no_cpu_baseline or world > 1
+                    else oracle_matmul_baseline(res["shapes"])}
             print(json.dumps(line))
         return
 
@@ -1178,31 +1345,36 @@ def main():
                             "h2d_bytes_per_step": b["h2d_bytes"] // b["requests"],
                             "d2h_bytes_per_step": b["d2h_bytes"] // b["requests"]},
                     "max_abs_err_vs_fp64": None if args.no_cpu_baseline else fp64_max_error(res["checks"]),
-                    "encrypt_pool_s": res["encrypt_pool_s"]}
+                    "encrypt_pool_s": res["encrypt_pool_s"], "clocks": res["clocks"],
+                    "cpu_baseline": None if args.no_cpu_baseline or world > 1
+                    else oracle_serve_baseline(res["sides"])}
             print(json.dumps(line))
         return
 
     if args.impl == "reference":
         if rank != 0:
             return
-        steps = []
+        smp = OracleCnnSample(args.batch)
         for _ in range(args.warmup):
-            oracle_sample(args.batch)
-        for _ in range(args.steps):
-            steps.append(oracle_sample(args.batch))
-        per_inf = float(np.mean([s[1] for s in steps]))
-        val = args.batch / per_inf
+            smp.run()
+        times = [smp.run() for _ in range(args.steps)]
+        t_step = float(np.mean(times))
+        val = args.batch * smp.fraction / t_step
+        sample = (f"per step: conv-1 output column 0 of {args.batch} packed images (8 channels, 20 top-level key "
+                  f"switches), {smp.fraction:.5f} of one inference by key-switch count "
+                  f"(20/{ks_per_inference(SIDE)}); value = images represented / step time")
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_inf,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic", "config": cfg,
-                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
-                                 "sample": "conv-1 output column 0 (8 channels, 20 top-level key switches) per step, "
-                                           "scaled to one inference by key-switch count"},
+                "cpu_baseline": _cpu(val, UNIT, sample),
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
 
+    extras = None
+    if world == 1 and not args.no_extra:
+        extras = run_extra_workloads(args)
     res = run_gpu(args, rank, world, local_rank)
     if rank != 0:
         return
@@ -1211,10 +1383,7 @@ def main():
     if not args.no_cpu_baseline:
         max_err = fp64_max_error([(res["logits"], res["imgs"], res["weights"])])
     if not args.no_cpu_baseline and world == 1:
-        dt, per_inf = oracle_sample(args.batch)
-        cpu = {"value": args.batch / per_inf, "unit": UNIT, "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
-               "sample": f"conv-1 output column 0 (8 channels, 20 top-level key switches) took {dt:.2f} s; "
-                         f"scaled to one inference by key-switch count ({KS_PER_INFERENCE}/20)"}
+        cpu = oracle_cnn_baseline(args.batch)
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
@@ -1224,6 +1393,8 @@ def main():
             "plain": {"value": res["plain_value"], "ms_per_step": res["plain_ms"], "images_per_set": 1},
             "ntt_geometry": res["ntt_geometry"],
             "kernel_breakdown": res["breakdown"]}
+    if extras is not None:
+        line["workloads"] = extras
     print(json.dumps(line))
 
 
