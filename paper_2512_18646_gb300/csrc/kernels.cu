@@ -517,14 +517,16 @@ __global__ void __launch_bounds__(128, 6) k_conv_mac96_kernel(const u64* rot, u6
         pending++;
 #pragma unroll
         for (int t2 = 0; t2 < OB / 2; t2++) {
-          const ulonglong2 ww = reinterpret_cast<const ulonglong2*>(wr)[t2];
+          // a pair of channels exists in the weight row (cp words, cp even) only if its first
+          // channel does: the load stays inside the row, and inside the array at the last term
           if (o0 + 2 * t2 < c_out) {
+            const ulonglong2 ww = reinterpret_cast<const ulonglong2*>(wr)[t2];
             mac96(acc[2 * t2][0], x0, ww.x);
             mac96(acc[2 * t2][1], x1, ww.x);
-          }
-          if (o0 + 2 * t2 + 1 < c_out) {
-            mac96(acc[2 * t2 + 1][0], x0, ww.y);
-            mac96(acc[2 * t2 + 1][1], x1, ww.y);
+            if (o0 + 2 * t2 + 1 < c_out) {
+              mac96(acc[2 * t2 + 1][0], x0, ww.y);
+              mac96(acc[2 * t2 + 1][1], x1, ww.y);
+            }
           }
         }
         wr += cp;
