@@ -178,19 +178,24 @@ def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
 MAC96_KERNELS = ("k_conv_mac96_kernel", "k_fc_mac96_kernel")
 
 
-def alu_peak_for(name, modmul_peak, mac96_peak):
+def alu_peak_for(name, modmul_peak, mac96_peak, bfly_peak=None):
     """(products/s, unit, source) of the kernel's own product: the 96-bit multiply-accumulate for the
-    kernels built on it, else the Shoup product."""
+    kernels built on it, the growing-range butterfly of the 45-bit primes for the transforms (most of
+    their rows; the 60-bit rows run Harvey's slower butterfly, reported beside it), else the Shoup
+    product."""
     if name.startswith(MAC96_KERNELS):
         return mac96_peak, "Gmac96/s", "measured (he_calibrate_mac96: 96-bit multiply-accumulates in registers, all SMs)"
+    if bfly_peak and name.startswith("k_ntt_"):
+        return bfly_peak, "Gbfly/s", ("measured (he_calibrate_butterfly, narrow primes: growing-range butterflies in "
+                                      "registers, all SMs)")
     return modmul_peak, "Gmodmul/s", "measured (he_calibrate_modmul: Shoup products in registers, all SMs)"
 
 
-def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n, mac96_peak=None):
+def roofline_for(name, t, total_ms, hbm, measured, modmul_peak, log_n, mac96_peak=None, bfly_peak=None):
     """The kernel's bound is whichever takes longer at peak: its algorithmic bytes at the measured HBM
     bandwidth, or its products at the measured rate of that product (he_calibrate_modmul for Shoup
     products, he_calibrate_mac96 for 96-bit multiply-accumulates)."""
-    alu_peak, alu_unit, alu_src = alu_peak_for(name, modmul_peak, mac96_peak or modmul_peak)
+    alu_peak, alu_unit, alu_src = alu_peak_for(name, modmul_peak, mac96_peak or modmul_peak, bfly_peak)
     avg_s = t["ms"] / 1e3 / max(1, t["launches"])
     alg_per_launch = t["bytes"] / max(1, t["launches"])
     prod_per_launch = t.get("products", 0.0) / max(1, t["launches"])
@@ -302,17 +307,27 @@ def run_gpu(args, rank, world, local_rank):
     hbm = float(pk.get("hbm_gbs", 6800.0))
     import ctypes
     modmul_peak, mac96_peak = ctypes.c_double(), ctypes.c_double()
+    bfly_n, bfly_w = ctypes.c_double(), ctypes.c_double()
     lib.he_calibrate_modmul(g.h, ctypes.byref(modmul_peak))
     lib.he_calibrate_mac96(g.h, ctypes.byref(mac96_peak))
+    lib.he_calibrate_butterfly(g.h, 1, ctypes.byref(bfly_n))
+    lib.he_calibrate_butterfly(g.h, 0, ctypes.byref(bfly_w))
     roofline = roofline_for(top, prof[top], prof_total, hbm, "fallback" not in pk, modmul_peak.value, pre.log_n,
-                            mac96_peak.value)
-    breakdown = {k: {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
-                     "launches_per_step": v["launches"] // args.steps,
-                     "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
-                     "alu_frac": round(v["products"] / (v["ms"] / 1e3) /
-                                       alu_peak_for(k, modmul_peak.value, mac96_peak.value)[0], 3)
-                     if v["ms"] > 0 else 0.0}
-                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+                            mac96_peak.value, bfly_n.value)
+
+    def entry(k, v):
+        e = {"share": round(v["ms"] / prof_total, 4), "ms_per_step": round(v["ms"] / args.steps, 3),
+             "launches_per_step": v["launches"] // args.steps,
+             "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else 0.0,
+             "hbm_frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm, 3) if v["ms"] > 0 else 0.0,
+             "alu_frac": round(v["products"] / (v["ms"] / 1e3) /
+                               alu_peak_for(k, modmul_peak.value, mac96_peak.value, bfly_n.value)[0], 3)
+             if v["ms"] > 0 else 0.0}
+        if k.startswith("k_ntt_") and v["ms"] > 0:
+            # the same products against Harvey's butterfly of the 60-bit rows (the slower class)
+            e["alu_frac_wide_bfly"] = round(v["products"] / (v["ms"] / 1e3) / bfly_w.value, 3)
+        return e
+    breakdown = {k: entry(k, v) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     # end to end through the C ABI: host ciphertexts in (pinned), encrypted logits out
     e2e = None
@@ -343,6 +358,7 @@ def run_gpu(args, rank, world, local_rank):
             "ntt_geometry": {"column_stages": n1, "columns_per_block": cols, "tuned_on_limbs": tune_rows,
                              "fwd_inv_us": round(tune_us, 1)},
         "images_per_step": B, "modmul_peak": modmul_peak.value, "mac96_peak": mac96_peak.value,
+        "bfly_peak": {"narrow": bfly_n.value, "wide": bfly_w.value},
         "plain_value": job_throughput(1, args.steps, world, plain_ms / 1e3),
         "plain_ms": plain_ms / args.steps,
     }
@@ -1390,6 +1406,7 @@ def main():
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": res["launches"], "max_abs_err_vs_fp64": max_err,
             "alu_peak_modmul_per_s": res["modmul_peak"], "alu_peak_mac96_per_s": res["mac96_peak"],
+            "alu_peak_butterfly_per_s": res["bfly_peak"],
             "plain": {"value": res["plain_value"], "ms_per_step": res["plain_ms"], "images_per_set": 1},
             "ntt_geometry": res["ntt_geometry"],
             "kernel_breakdown": res["breakdown"]}

@@ -744,6 +744,16 @@ int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s);
  * measured like he_calibrate_modmul. */
 int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s);
 
+/* Measured peak of forward-transform butterflies per second on the context's
+ * GPU, in the form the transform kernels run them (the negacyclic NTT's
+ * Cooley-Tukey butterfly with the twiddle product of Shoup's method): narrow
+ * != 0 for primes below 2^54 (growing-range butterfly: the cheaper quotient
+ * estimate, no reduction between stages), 0 for the wider primes (Harvey's
+ * lazy butterfly). Independent chains in registers on every SM, timed like
+ * he_calibrate_modmul; the roofline of the transform kernels.
+ * Errors: HE_E_ARG (null pointers), HE_E_CUDA. */
+int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t he_kernel_launches(void);
 

@@ -138,6 +138,7 @@ SIGNATURES = {
     "he_ntt_autotune": (I, [V, I, P_I, P_I, P_D]),
     "he_calibrate_modmul": (I, [V, P_D]),
     "he_calibrate_mac96": (I, [V, P_D]),
+    "he_calibrate_butterfly": (I, [V, I, P_D]),
     "he_kernel_launches": (U64, []),
     "he_profile_enable": (I, [I]),
     "he_profile_read": (I, [ctypes.c_char_p, SZ, P_D, P_U64, P_D, P_D, I, P_I]),

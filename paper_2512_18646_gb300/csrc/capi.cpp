@@ -989,6 +989,30 @@ int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s) {
   });
 }
 
+int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s) {
+  return guard([&] {
+    REQUIRE(ctx && bfly_per_s, HE_E_ARG, "null argument");
+    Ctx& C = ctx->c;
+    int sms = 0;
+    HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
+    const int threads = 256, blocks = sms * 8, iters = 4096;
+    DevBuf sink((size_t)blocks * threads, C.stream);
+    k_calib_bfly(C, sink.p, blocks, threads, 64, narrow != 0);  // warm-up
+    cudaEvent_t a, b;
+    HE_CUDA(cudaEventCreate(&a));
+    HE_CUDA(cudaEventCreate(&b));
+    HE_CUDA(cudaEventRecord(a, C.stream));
+    k_calib_bfly(C, sink.p, blocks, threads, iters, narrow != 0);
+    HE_CUDA(cudaEventRecord(b, C.stream));
+    HE_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    HE_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *bfly_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+  });
+}
+
 int he_ntt_set_geometry(he_ctx* ctx, int n1, int cols) {
   return guard([&] {
     REQUIRE(ctx, HE_E_ARG, "null argument");

@@ -286,6 +286,8 @@ void k_mont_form(const Ctx& C, u64* data, int n_polys, const LimbMap& lm);
 // calibration: blocks x threads x 8 chains x iters Shoup products modulo q_0
 void k_calib_shoup(const Ctx& C, u64* sink, int blocks, int threads, int iters);
 void k_calib_mac96(const Ctx& C, u64* sink, int blocks, int threads, int iters);
+// calibration of the forward butterfly of the transforms (narrow: primes below kNarrowPrime)
+void k_calib_bfly(const Ctx& C, u64* sink, int blocks, int threads, int iters, bool narrow);
 // number of residues >= q_i in rows of limbs (limb = row % limbs), added to *bad
 void k_check_range(const Ctx& C, const u64* x, size_t rows, int limbs, unsigned long long* bad);
 // copy groups x rows_per_group limbs: row r of group g at src + g src_gs + r N

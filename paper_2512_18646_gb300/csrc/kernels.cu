@@ -926,6 +926,44 @@ __global__ void k_calib_mac96_kernel(u64* sink, u64 q, int iters) {
   sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
+// Calibration of the forward transform's butterfly as the transform kernels run it:
+// eight independent (X, Y) pairs per thread, each iteration one butterfly per pair
+// on its own output. NAR: the growing-range butterfly of primes below kNarrowPrime
+// (the cheaper quotient estimate, no reduction: X + T, X - T + 4q); otherwise
+// Harvey's (X reduced below 2q, Shoup's lazy product, X + T, X - T + 2q). The
+// values wrap; only the time is used.
+template <bool NAR>
+__global__ void k_calib_bfly_kernel(u64* sink, u64 q, u64 w, u64 wp, int iters) {
+  u64 x[8], y[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    x[c] = (blockIdx.x * 131ull + threadIdx.x * 7ull + c) % q;
+    y[c] = (blockIdx.x * 17ull + threadIdx.x * 29ull + 3 * c) % q;
+  }
+  const u64 q2 = 2 * q, q4 = 4 * q;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      if constexpr (NAR) {
+        const u64 T = shoup_approx(y[c], w, wp, q);
+        const u64 X = x[c];
+        x[c] = X + T;
+        y[c] = X - T + q4;
+      } else {
+        u64 X = x[c];
+        if (X >= q2) X -= q2;
+        const u64 T = shoup_lazy(y[c], w, wp, q);
+        x[c] = X + T;
+        y[c] = X - T + q2;
+      }
+    }
+  }
+  u64 r = 0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) r ^= x[c] ^ y[c];
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 // counts residues >= q_i in [n][limbs][N] rows (limb i of each polynomial)
 __global__ void k_check_range_kernel(const u64* x, size_t rows, int limbs, const PrimeTab* pt, int log_n,
                                      unsigned long long* bad) {
@@ -1224,6 +1262,24 @@ void k_calib_mac96(const Ctx& C, u64* sink, int blocks, int threads, int iters) 
     }
   void* tok = prof_begin("k_calib_mac96_kernel", C.stream, 0.0, 8.0 * blocks * threads * (double)iters);
   k_calib_mac96_kernel<<<blocks, threads, 0, C.stream>>>(sink, q, iters);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
+}
+void k_calib_bfly(const Ctx& C, u64* sink, int blocks, int threads, int iters, bool narrow) {
+  // a prime of the requested class from the context's chain (Q then P), else a stand-in of that size
+  u64 q = narrow ? (1ull << 45) - 55 : (1ull << 60) - 93;
+  for (u64 c : C.q)
+    if ((c < kNarrowPrime) == narrow) {
+      q = c;
+      break;
+    }
+  const u64 w = (q / 3) | 1, wp = (u64)(((unsigned __int128)w << 64) / q);
+  void* tok = prof_begin(narrow ? "k_calib_bfly_kernel<narrow>" : "k_calib_bfly_kernel<wide>", C.stream, 0.0,
+                         8.0 * blocks * threads * (double)iters);
+  if (narrow)
+    k_calib_bfly_kernel<true><<<blocks, threads, 0, C.stream>>>(sink, q, w, wp, iters);
+  else
+    k_calib_bfly_kernel<false><<<blocks, threads, 0, C.stream>>>(sink, q, w, wp, iters);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }
