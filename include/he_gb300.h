@@ -575,11 +575,14 @@ int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const h
  *  - in-place calls (he_rescale, he_relinearize, he_poly_act) and
  *    he_ctset_assign into sets made before the capture return HE_E_STATE;
  *  - calls that upload host data (encryption, convolution weights, biases,
- *    plaintext preparation) cannot be captured: the capture fails and
- *    he_graph_end returns HE_E_CUDA;
+ *    plaintext preparation) cannot be captured: they return HE_E_STATE (or
+ *    fail inside CUDA) and he_graph_end returns HE_E_CUDA;
  *  - he_ctset_free of a set made before the capture is deferred to he_graph_end.
  * Free the sets made during a capture after the graph's last replay. Kernel
- * launches of a replay are added to he_kernel_launches.
+ * launches of a replay are added to he_kernel_launches. A capture that the
+ * caller opens on the context's stream itself (cudaStreamBeginCapture, a
+ * framework's graph capture) refuses the calls that upload host data the
+ * same way: they return HE_E_STATE without recording the copy.
  */
 int he_graph_begin(he_ctx* ctx);
 int he_graph_end(he_ctx* ctx, he_graph** out);

@@ -862,6 +862,7 @@ int he_graph_begin(he_ctx* ctx) {
     HE_CUDA(cudaStreamSynchronize(C.stream));
     HE_CUDA(cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal));
     C.capturing = true;
+    C.capture_failed = false;
     C.capture_gen++;
   });
 }
@@ -875,6 +876,10 @@ int he_graph_end(he_ctx* ctx, he_graph** out) {
     const cudaError_t e = cudaStreamEndCapture(C.stream, &g);
     C.capturing = false;
     C.deferred.clear();  // sets made before the capture and freed during it
+    if (e == cudaSuccess && C.capture_failed) {
+      if (g) cudaGraphDestroy(g);
+      throw Error(HE_E_CUDA, "capture failed: a call inside it copies host data to the device");
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       if (g) cudaGraphDestroy(g);

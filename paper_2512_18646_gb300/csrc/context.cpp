@@ -131,12 +131,18 @@ Staging::~Staging() {
 void upload_async(Ctx& C, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
   // A capture of the context's stream, opened by he_graph_begin or by the caller directly (its own
-  // cudaStreamBeginCapture or a framework's graph capture), must not record a copy from a staging
-  // slot: a later call reuses the slot, so a replay would read another call's data.
+  // cudaStreamBeginCapture or a framework's graph capture), must not record a host-to-device copy:
+  // a replay would read a staging slot that later calls reuse, or host memory the call has freed.
+  // The call is refused instead (and a he_graph capture marked failed).
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   HE_CUDA(cudaStreamIsCapturing(C.stream, &cs));
-  if (C.capturing || cs != cudaStreamCaptureStatusNone || bytes > Staging::kSlotBytes) {
-    // pageable source: the call returns once the data is staged (a capture refuses it)
+  if (C.capturing || cs != cudaStreamCaptureStatusNone) {
+    C.capture_failed = C.capture_failed || C.capturing;
+    throw Error(9 /* HE_E_STATE */, "this call copies host data to the device and cannot run inside a capture of the "
+                            "context's stream");
+  }
+  if (bytes > Staging::kSlotBytes) {
+    // pageable source: the call returns once the data is staged
     HE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, C.stream));
     return;
   }

@@ -137,6 +137,8 @@ struct Ctx {
   // released after the capture ends (their memory is not the graph's to free)
   bool capturing = false;
   uint64_t capture_gen = 0;
+  // a call inside the capture needed a host upload (refused): he_graph_end then fails
+  bool capture_failed = false;
   std::vector<std::unique_ptr<CtSet>> deferred;
 
   Staging staging;
