@@ -51,6 +51,9 @@ UNIT = "images/s"
 SIDE = 128
 H = 128  # block stride (rows per image block)
 ROT_STEPS = [1, 2, 3, 4, 8, 16, 32, 64]
+CNN_PRESETS = {"cnn_n16": synthetic.CNN_N16, "cnn_n16_dnum3": synthetic.CNN_N16_DNUM3}
+KS_DESC = {"cnn_n16": "P=2x60, alpha=2 (7 digits)",
+           "cnn_n16_dnum3": "P=5x60, dnum=3 (alpha=5: the stated dnum with a special modulus above the digits)"}
 WORKLOAD = ("encrypted CNN conv5x5s2(8)->x^2->conv3x3s2(16)->x^2->fc10 on 128x128 grayscale images in the "
             "column layout (128 ciphertexts of 128 pixels); RNS-CKKS N=2^16, Q=60+12x45, P=2x60, alpha=2 (7 digits), "
             "scale 2^45")
@@ -235,7 +238,7 @@ def run_gpu(args, rank, world, local_rank):
     lib = load()
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
-    pre = synthetic.CNN_N16
+    pre = CNN_PRESETS[args.preset]
     seeds = rank_seeds(rank)
     g = api.Context.from_preset(pre, seed=seeds["ctx_seed"], stream=stream.cuda_stream)
     g.keygen(ROT_STEPS)
@@ -1017,9 +1020,9 @@ class OracleCnnSample:
     at the top level, 200 ciphertext-scalar products and 8 rescales, and stands for
     20 / ks_per_inference(side) of one inference (the oracle's time is dominated by key switching)."""
 
-    def __init__(self, batch: int, side: int = SIDE, H: int = H):
+    def __init__(self, batch: int, side: int = SIDE, H: int = H, preset=None):
         from oracle import Oracle, layouts
-        pre = synthetic.CNN_N16
+        pre = preset or synthetic.CNN_N16
         self.o = Oracle.from_preset(pre, seed=7)
         self.o.keygen([1, 2, 3, 4])
         imgs = synthetic.images(batch, side, 5, seed=301)
@@ -1039,8 +1042,8 @@ def _cpu(value, unit, sample):
             "sample": sample}
 
 
-def oracle_cnn_baseline(batch: int):
-    s = OracleCnnSample(batch)
+def oracle_cnn_baseline(batch: int, preset=None):
+    s = OracleCnnSample(batch, preset=preset)
     dt = s.run()
     per_inference = dt / s.fraction
     return _cpu(batch / per_inference, UNIT,
@@ -1137,6 +1140,8 @@ EXTRA_WORKLOADS = (
     ("conv_layer_64x64_n15", "layer", ["--steps", "5", "--warmup", "3"]),
     ("matmul64_uneven_n16", "matmul", []),
     ("serving_poisson_n16", "serve", []),
+    ("cnn_dnum3_5special_n16", "cnn", ["--preset", "cnn_n16_dnum3", "--steps", "5", "--warmup", "3", "--no-extra",
+                                       "--no-e2e"]),
 )
 
 
@@ -1200,6 +1205,8 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--preset", choices=sorted(CNN_PRESETS), default="cnn_n16",
+                    help="cnn workload: prime chain and key-switching digits")
     ap.add_argument("--no-extra", action="store_true",
                     help="cnn workload: skip the other configurations (matmul, conv layer, batched matmul, serving)")
     ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "table1", "serve"],
@@ -1218,7 +1225,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    cfg = {"workload": WORKLOAD, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
+    wl = WORKLOAD.replace(KS_DESC["cnn_n16"], KS_DESC[args.preset])
+    cfg = {"workload": wl, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
 
@@ -1399,7 +1407,7 @@ def main():
     if not args.no_cpu_baseline:
         max_err = fp64_max_error([(res["logits"], res["imgs"], res["weights"])])
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_cnn_baseline(args.batch)
+        cpu = oracle_cnn_baseline(args.batch, CNN_PRESETS[args.preset])
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,

@@ -67,9 +67,9 @@ typedef struct {
   int log_n;           /* ring degree N = 2^log_n, 4 <= log_n <= 16           */
   int n_q;             /* number of Q primes (levels + 1), 1..32             */
   const int* q_bits;   /* n_q bit sizes, each in [20, 61]                     */
-  int n_special;       /* K >= 1 special primes                               */
+  int n_special;       /* K special primes, 1..8                              */
   int special_bits;    /* bit size of each special prime, in [20, 61]         */
-  int alpha;           /* primes per key-switching digit, >= 1                */
+  int alpha;           /* primes per key-switching digit, 1..8                */
   double log_scale;    /* encoding scale = 2^log_scale                        */
   double sigma;        /* Gaussian error parameter (3.2)                      */
 } he_params_desc;
@@ -100,6 +100,17 @@ int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* al
  * columns each chunk needs) with the same per-ciphertext arithmetic, so the
  * results do not change. 0 (the default) means no bound. */
 int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes);
+
+/*
+ * Whether the convolution's ciphertext-scalar multiply-accumulate (Alg. 4's
+ * sum over channels and kernel offsets, he_conv2d) runs on the tensor cores
+ * (on != 0, the default) or on the CUDA cores. The tensor-core form splits
+ * the residues into 7-bit chunks whose products the tensor cores sum exactly
+ * in fp32 and recombines the sums modulo q; it is taken where those sums stay
+ * below 2^24 (c_in k^2 up to 148 terms for primes below 2^46, 115 above) and
+ * N >= 128. Both forms compute the same words. Errors: HE_E_ARG.
+ */
+int he_ctx_set_tensor_cores(he_ctx* ctx, int on);
 
 /*
  * he_keygen: draw the ternary secret s, the public key (-a s + e, a) over Q,

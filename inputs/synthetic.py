@@ -49,6 +49,9 @@ CONV_LAYER = ParamPreset("conv_n15", 15, (60,) + (40,) * 8, 1, 60, 1, 40.0)
 # Three-layer CNN on 128x128 images, N = 2^16, Q = 60 + 12 x 45, P = 2 x 60,
 # digits of alpha = 2 primes (beta = 7 digits at the top level).
 CNN_N16 = ParamPreset("cnn_n16", 16, (60,) + (45,) * 12, 2, 60, 2, 45.0)
+# The same chain with three key-switching digits (dnum = 3: alpha = 5 primes a digit) and
+# K = 5 special primes of 60 bits, so that P (300 bits) exceeds the largest digit (240 bits).
+CNN_N16_DNUM3 = ParamPreset("cnn_n16_dnum3", 16, (60,) + (45,) * 12, 5, 60, 5, 45.0)
 
 
 def small_preset(log_n: int, q_bits=(60, 40, 40, 40), n_special=1, special_bits=60,

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhegb300.so")
 BUILD = os.path.join(HERE, "_build")
 
-CU = ["ntt.cu", "kernels.cu", "noalloc.cu"]
+CU = ["ntt.cu", "kernels.cu", "conv_tc.cu", "noalloc.cu"]
 CPP = ["context.cpp", "eval.cpp", "encode.cpp", "capi.cpp", "profile.cpp", "server.cpp"]
 HEADERS = ["he_internal.h", "he_arith.cuh", "server_sched.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -59,6 +59,7 @@ SIGNATURES = {
     "he_ctx_primes": (I, [V, P_U64, I]),
     "he_ctx_info": (I, [V, P_I, P_I, P_I, P_I, P_D]),
     "he_ctx_set_work_budget": (I, [V, SZ]),
+    "he_ctx_set_tensor_cores": (I, [V, I]),
     "he_keygen": (I, [V, P_I32, I]),
     "he_encrypt_image": (I, [V, P_D, I, I, I, I, U64, PV]),
     "he_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),

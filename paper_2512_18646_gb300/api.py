@@ -171,6 +171,9 @@ class Context:
         """Bound the device temporaries of one operation (0 = none); results do not change."""
         check(load().he_ctx_set_work_budget(self.h, int(nbytes)))
 
+    def set_tensor_cores(self, on: bool):
+        check(load().he_ctx_set_tensor_cores(self.h, int(bool(on))))
+
     def synchronize(self):
         check(load().he_ctx_synchronize(self.h))
 

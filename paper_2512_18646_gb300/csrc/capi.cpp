@@ -90,6 +90,7 @@ int he_ctx_synchronize(he_ctx* ctx) {
   return guard([&] {
     REQUIRE(ctx, HE_E_ARG, "null context");
     HE_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    check_device_status(ctx->c);
   });
 }
 
@@ -725,6 +726,13 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
   return guard([&] {
     REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
     *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale));
+  });
+}
+
+int he_ctx_set_tensor_cores(he_ctx* ctx, int on) {
+  return guard([&] {
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    ctx->c.use_tc = on != 0;
   });
 }
 

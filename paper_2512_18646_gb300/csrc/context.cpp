@@ -173,7 +173,7 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
               double log_scale, double sigma, u64 seed, cudaStream_t st) {
   if (log_n < 4 || log_n > 16) throw Error(1, "log_n must be in [4, 16]");
   if (q_bits.empty() || q_bits.size() > 32) throw Error(1, "n_q must be in [1, 32]");
-  if (n_special < 1 || n_special > 4) throw Error(1, "n_special must be in [1, 4]");
+  if (n_special < 1 || n_special > 8) throw Error(1, "n_special must be in [1, 8]");
   if (alpha < 1 || alpha > 8) throw Error(1, "alpha must be in [1, 8]");
   if (special_bits < 20 || special_bits > 61) throw Error(1, "special_bits must be in [20, 61]");
   for (int b : q_bits)
@@ -346,6 +346,8 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
   }
   C.d_rs = DevBuf(rs.size(), st);
   upload(C, C.d_rs.p, rs.data(), rs.size() * 8);
+  C.d_status = DevBuf(1, st);
+  HE_CUDA(cudaMemsetAsync(C.d_status.p, 0, 8, st));
 
   // host FFT tables for encode / decode (M = N/2 point complex DFT)
   const size_t M = C.N / 2;
@@ -571,17 +573,30 @@ void decrypt_slots(Ctx& C, const CtSet& s_any, double* out) {
   });
 }
 
+// After a synchronisation: a kernel whose bounded device-side wait expired has set the status
+// word; report it (and clear it) instead of returning its words.
+void check_device_status(Ctx& C) {
+  u64 st = 0;
+  HE_CUDA(cudaMemcpy(&st, C.d_status.p, 8, cudaMemcpyDeviceToHost));
+  if (st) {
+    HE_CUDA(cudaMemset(C.d_status.p, 0, 8));
+    throw Error(6 /* HE_E_TIMEOUT */, "a device-side wait of a tensor-core kernel exceeded its limit");
+  }
+}
+
 void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
   DevBuf t(s.buf.words, C.stream);
   HE_CUDA(cudaMemcpyAsync(t.p, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
   ntt_inverse(C, t.p, s.n * s.polys, limbs_q(s.limbs, C.N));
   HE_CUDA(cudaMemcpyAsync(host, t.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
+  check_device_status(C);
 }
 
 void export_raw(Ctx& C, const CtSet& s, u64* host) {
   HE_CUDA(cudaMemcpyAsync(host, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
+  check_device_status(C);
 }
 
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale, bool ntt_domain) {

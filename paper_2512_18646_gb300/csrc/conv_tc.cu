@@ -1,0 +1,390 @@
+// conv_tc.cu - the convolution's multiply-accumulate on the 5th-generation
+// tensor cores (tcgen05, accumulators in tensor memory).
+//
+// The ciphertext-scalar multiply-accumulate of a convolution layer (Alg. 4 in
+// the column layout: output (o, j') = sum over (c, b, a) of the weight
+// K[o][c][a][b] times Rot(X_{c, s j' + b}, g a)) is, for one limb and one
+// component, a matrix product: out[o][n] = sum_t W[o][t] X_t[n] mod q, with
+// the c_out channels, T = c_in k^2 terms and the N coefficients of the limb as
+// its dimensions. Residues (below 2^46, resp. 2^62) are split into NC = 7
+// (resp. 9) chunks of 7 bits, x = sum_i x_i 2^(7i), which fp16 holds exactly;
+// the tensor cores sum the chunk products in fp32, which is exact while every
+// sum stays below 2^24:
+//   D_s[n][o] = sum_{i + j = s} sum_t x_i[t][n] w_j[o][t] <= NC T 127^2 < 2^24
+// (the host takes this path only for such T), s = 0 .. 2 NC - 2. Then
+//   out[o][n] = sum_s D_s[n][o] 2^(7s) mod q
+// on the CUDA cores (96-bit sums for the narrow primes, 128-bit otherwise,
+// one Barrett reduction). The result is the exact residue, the same word the
+// CUDA-core kernels compute.
+//
+// One CTA (four warps) owns a tile of 128 coefficients of one (component,
+// limb) and runs every output column j' of the layer over it. Per 16 terms
+// (one K step) each thread loads its coefficient's 16 input words (the next
+// step's are loaded while this step's are converted), writes their chunks as
+// row `thread` of NC fp16 tiles [128 x 16] in shared memory (K-major, 8 x 16-
+// byte core matrices, no swizzle), and one thread issues NC MMAs of
+// M = 128, N = NC * OBP, K = 16: MMA i multiplies chunk tile i by the weight
+// tile B = [chunk j][channel o] and accumulates at tensor-memory column
+// i * OBP, so that column s * OBP + o collects D_s[.][o]. The A tiles are
+// double-buffered; an mbarrier per buffer (tcgen05.commit) says when the MMAs
+// that read it have finished. Every wait is bounded: past the limit the CTA
+// records the failure in the context's status word (read by the host at its
+// next synchronisation), frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include "he_internal.h"
+
+namespace he {
+
+namespace {
+
+constexpr int kTcThreads = 128;  // four warps: warp w reads tensor-memory lanes 32 w .. 32 w + 31
+constexpr int kTcRows = 128;     // MMA M: coefficients of one tile (one per thread)
+
+template <int NC, int OBP>
+struct TcShape {
+  static constexpr int NS = 2 * NC - 1;                      // sums s = i + j
+  static constexpr int NMMA = (NC * OBP + 15) / 16 * 16;     // MMA N (rows of the weight tile)
+  static constexpr int COLS = (NC - 1) * OBP + NMMA;         // accumulator columns the MMAs touch
+  static constexpr int TMEM = COLS <= 64 ? 64 : COLS <= 128 ? 128 : 256;
+  static constexpr int A_TILE = kTcRows * 16 * 2;            // bytes of a [128 x 16] fp16 tile
+  static constexpr int B_TILE = NMMA * 16 * 2;               // bytes of an [NMMA x 16] fp16 tile
+  static_assert(COLS % 16 == 0 && COLS <= 256, "accumulators must fit 256 tensor-memory columns");
+  static_assert(NMMA >= 16 && NMMA <= 256, "MMA N for M = 128");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major tile without swizzle: core matrices of 8 rows x 16
+// bytes stored whole; the second core matrix along K (a row's fp16 8..15) 128 bytes after the first
+// (leading byte offset), the next group of 8 rows 256 bytes further (stride byte offset); descriptor
+// version 1 (bits 46-47), base offset 0, layout type 0 (no swizzle, bits 61-63).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D in f32 (bits 4-5 = 1), A and B fp16 (bits 7-9, 10-12 = 0),
+// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28, dense.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols) : "memory");
+}
+__device__ __forceinline__ void tc_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
+  // accumulate (the accumulators are zeroed before the first K step of a task)
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(1u)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the completion of the barrier's phase of this parity; false after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 30); it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+
+// zeros into 16 accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_zero16(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+// two 7-bit chunks (exact small integers) as one f16x2 word, the first in the low half
+__device__ __forceinline__ uint32_t chunk_pair(u64 x0, u64 x1, int sh) {
+  const __half h0 = __uint2half_rn((uint32_t)(x0 >> sh) & 127u);
+  const __half h1 = __uint2half_rn((uint32_t)(x1 >> sh) & 127u);
+  return (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+}
+
+// The input words of the 16 terms of K step ks at this thread's coefficient (0 for padding terms).
+__device__ __forceinline__ void load_step(u64 (&x)[16], const u64* xb, const u64* toff, int ks) {
+#pragma unroll
+  for (int v = 0; v < 16; v++) {
+    const u64 off = toff[16 * ks + v];
+    x[v] = off == ~0ull ? 0 : __ldg(xb + off);
+  }
+}
+
+// rot [c_in][w_in][k][2][limbs][N] (the hoisted rotations, term (c, b, a) of output column jp at
+// column stride jp + b, rotation a), w [c_out][c_in][k][k][limbs][2] (residue, Shoup companion),
+// out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
+// otherwise the others (9 chunks); blocks of the other class return at once.
+template <int NC, int OBP, bool NARROW>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_conv_mac_tc_kernel(const u64* __restrict__ rot, u64* __restrict__ out, const u64* __restrict__ w, int c_in,
+                         int w_in, int k, int stride, int c_out, int w_out, int limbs, const PrimeTab* __restrict__ pt,
+                         int log_n, u64* status) {
+  using S = TcShape<NC, OBP>;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  const size_t N = (size_t)1 << log_n;
+  const size_t LN = (size_t)limbs * N;
+  const int i = blockIdx.y % limbs, comp = blockIdx.y / limbs;
+  const Mod md = pt[i].mod;
+  if ((md.q < kMac96Prime) != NARROW) return;  // uniform across the block, before any allocation
+  const int kk2 = k * k, T = c_in * kk2, n_ks = (T + 15) >> 4;
+  unsigned char* A = tc_smem;                                                 // [2][NC][A_TILE]
+  unsigned char* B = A + 2 * NC * S::A_TILE;                                  // [n_ks][B_TILE]
+  u64* toff = reinterpret_cast<u64*>(B + (size_t)n_ks * S::B_TILE);          // [16 n_ks]
+  u64* csm = toff + 16 * n_ks;                                                // [NS] 2^(7 s) mod q
+  u64* bars = csm + S::NS;                                                    // [2] mbarriers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // word offset of each term's input in rot, relative to output column 0 (padding terms: none)
+  for (int t = tid; t < 16 * n_ks; t += kTcThreads) {
+    u64 off = ~0ull;
+    if (t < T) {
+      const int c = t / kk2, r = t - c * kk2, b = r / k, a = r - b * k;  // t = (c k + b) k + a
+      off = (((u64)c * w_in + b) * k + a) * 2 * LN;
+    }
+    toff[t] = off;
+  }
+  if (tid == 0) {
+    u64 c = 1;
+    for (int s = 0; s < S::NS; s++) {
+      csm[s] = c;
+      c = mulmod(c, 128, md);
+    }
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc_alloc(smem_u32(tslot), S::TMEM);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t lanes = (uint32_t)(warp * 32) << 16;  // this warp's lane quarter of tensor memory
+  const size_t io = (size_t)comp * LN + (size_t)i * N + (size_t)blockIdx.x * kTcRows + tid;
+  constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
+  // row `tid` of an A tile: core matrix (tid / 8, K half) at (tid / 8) 256 + half 128, row tid % 8 at 16 bytes
+  const int arow = (tid >> 3) * 256 + (tid & 7) * 16;
+  uint32_t uses[2] = {0, 0};
+  bool ok = true;
+  for (int o0 = 0; o0 < c_out; o0 += OBP) {
+    // weight tiles of this channel group: row r = j OBP + o holds chunk j of W[o0 + o][t], t = 16 ks + kk
+    for (int e = tid; e < n_ks * S::NMMA * 16; e += kTcThreads) {
+      const int ks = e / (S::NMMA * 16), rem = e - ks * (S::NMMA * 16), r = rem >> 4, kk = rem & 15;
+      const int t = ks * 16 + kk, j = r / OBP, o = r - j * OBP;
+      uint32_t v = 0;
+      if (j < NC && o0 + o < c_out && t < T) {
+        const int c = t / kk2, rr = t - c * kk2, b = rr / k, a = rr - b * k;
+        const u64 wv = w[(((size_t)(o0 + o) * T + (c * k + a) * k + b) * limbs + i) * 2];
+        v = (uint32_t)(wv >> (7 * j)) & 127u;
+      }
+      __half* dst = reinterpret_cast<__half*>(B + (size_t)ks * S::B_TILE + (r >> 3) * 256 + (kk >> 3) * 128 +
+                                              (r & 7) * 16) +
+                    (kk & 7);
+      *dst = __uint2half_rn(v);
+    }
+    for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
+#pragma unroll
+      for (int c = 0; c < S::COLS; c += 16) tc_zero16(tmem + lanes + c);
+      tc_wait_st();
+      const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + io;
+      u64 xc[16], xn[16];
+      load_step(xc, xb, toff, 0);
+      for (int ks = 0; ks < n_ks; ks++) {
+        if (ks + 1 < n_ks) load_step(xn, xb, toff, ks + 1);
+        const int b = ks & 1;
+        if (uses[b] > 0 && ok) ok = mbar_wait(smem_u32(&bars[b]), (uses[b] - 1) & 1);  // buffer b is free
+        unsigned char* Ab = A + (size_t)b * NC * S::A_TILE + arow;
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+          uint4 lo, hi;
+          lo.x = chunk_pair(xc[0], xc[1], 7 * c);
+          lo.y = chunk_pair(xc[2], xc[3], 7 * c);
+          lo.z = chunk_pair(xc[4], xc[5], 7 * c);
+          lo.w = chunk_pair(xc[6], xc[7], 7 * c);
+          hi.x = chunk_pair(xc[8], xc[9], 7 * c);
+          hi.y = chunk_pair(xc[10], xc[11], 7 * c);
+          hi.z = chunk_pair(xc[12], xc[13], 7 * c);
+          hi.w = chunk_pair(xc[14], xc[15], 7 * c);
+          *reinterpret_cast<uint4*>(Ab + c * S::A_TILE) = lo;
+          *reinterpret_cast<uint4*>(Ab + c * S::A_TILE + 128) = hi;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const uint64_t bdesc = tc_desc(smem_u32(B + (size_t)ks * S::B_TILE));
+#pragma unroll
+          for (int c = 0; c < NC; c++)
+            tc_mma(tmem + c * OBP, tc_desc(smem_u32(A + ((size_t)b * NC + c) * S::A_TILE)), bdesc, idesc);
+          tc_commit(smem_u32(&bars[b]));
+        }
+        uses[b]++;
+#pragma unroll
+        for (int v = 0; v < 16; v++) xc[v] = xn[v];
+      }
+      // the last commit covers every MMA of the task
+      {
+        const int b = (n_ks - 1) & 1;
+        if (ok) ok = mbar_wait(smem_u32(&bars[b]), (uses[b] - 1) & 1);
+      }
+      tc_fence_after();
+      // out[o] = sum_s D_s[o] 2^(7 s) mod q
+      u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + io;
+      const size_t ostep = (size_t)w_out * 2 * LN;
+      if constexpr (NARROW) {
+        Acc96 acc[OBP];
+#pragma unroll
+        for (int o = 0; o < OBP; o++) acc[o] = Acc96{0, 0, 0};
+        for (int s = 0; s < S::NS; s++) {
+          uint32_t d[OBP];
+          tc_ld(tmem + lanes + s * OBP, d);
+          tc_wait_ld();
+          const u64 cs = csm[s];
+#pragma unroll
+          for (int o = 0; o < OBP; o++) mac96(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+        }
+#pragma unroll
+        for (int o = 0; o < OBP; o++)
+          if (o0 + o < c_out) dst[o * ostep] = reduce96(acc[o], md);
+      } else {
+        Acc128 acc[OBP];
+#pragma unroll
+        for (int o = 0; o < OBP; o++) acc[o] = Acc128{0, 0};
+        for (int s = 0; s < S::NS; s++) {
+          uint32_t d[OBP];
+          tc_ld(tmem + lanes + s * OBP, d);
+          tc_wait_ld();
+          const u64 cs = csm[s];
+#pragma unroll
+          for (int o = 0; o < OBP; o++) mac128(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+        }
+#pragma unroll
+        for (int o = 0; o < OBP; o++)
+          if (o0 + o < c_out) dst[o * ostep] = reduce128(acc[o].hi, acc[o].lo, md);
+      }
+      // every warp has read its accumulators before the next task zeroes them (and before the
+      // next channel group rewrites the weight tiles)
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, S::TMEM);
+  if (!ok && tid == 0) atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
+}
+
+template <int NC, int OBP>
+size_t tc_smem_bytes(int T) {
+  using S = TcShape<NC, OBP>;
+  const int n_ks = (T + 15) / 16;
+  const size_t need = (size_t)2 * NC * S::A_TILE + (size_t)n_ks * S::B_TILE + 16 * n_ks * 8 + S::NS * 8 + 16 + 8;
+  // at most 512 / TMEM CTAs share an SM, so that every CTA's tensor-memory allocation is granted at
+  // once: request more than the SM's shared memory divided by one more CTA than that
+  const size_t floor_b = (size_t)(228 * 1024) / (512 / S::TMEM + 1) + 1024;
+  return need > floor_b ? need : floor_b;
+}
+
+template <int NC, int OBP, bool NARROW>
+void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+               int c_out, int w_out, int limbs, int n_class, const char* name) {
+  const int T = c_in * k * k;
+  const size_t smem = tc_smem_bytes<NC, OBP>(T);
+  static bool attr = false;
+  if (!attr) {
+    HE_CUDA(cudaFuncSetAttribute(k_conv_mac_tc_kernel<NC, OBP, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024));
+    attr = true;
+  }
+  const dim3 grid((unsigned)(C.N / kTcRows), (unsigned)(2 * limbs), 1);
+  const double per_limb_bytes =
+      8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
+  const double prods = 2.0 * C.N * (double)c_out * w_out * T * n_class;
+  void* tok = prof_begin(name, C.stream, per_limb_bytes * n_class, prods);
+  k_conv_mac_tc_kernel<NC, OBP, NARROW><<<grid, kTcThreads, smem, C.stream>>>(
+      rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, C.dev_ptab(), C.log_n, C.d_status.p);
+  prof_end(tok, C.stream);
+  HE_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+bool conv_mac_tc_fits(const Ctx& C, int c_in, int k, bool narrow) {
+  const long T = (long)c_in * k * k;
+  const long NC = narrow ? 7 : 9;
+  return C.log_n >= 7 && NC * T * 127 * 127 < (1L << 24);
+}
+
+void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                   int c_out, int w_out, int limbs, bool narrow) {
+  int n_class = 0;
+  for (int i = 0; i < limbs; i++) n_class += (C.q[i] < kMac96Prime) == narrow;
+  if (n_class == 0) return;
+  if (narrow) {
+    if (c_out <= 8)
+      launch_tc<7, 8, true>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                            "k_conv_mac_tc_kernel<7, 8>");
+    else
+      launch_tc<7, 16, true>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                             "k_conv_mac_tc_kernel<7, 16>");
+  } else {
+    launch_tc<9, 8, false>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                           "k_conv_mac_tc_kernel<9, 8>");
+  }
+}
+
+}  // namespace he

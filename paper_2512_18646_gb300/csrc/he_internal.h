@@ -125,6 +125,8 @@ struct Ctx {
   DevBuf d_up;                // ModUp constants, see modup_table()
   DevBuf d_down;              // ModDown constants
   DevBuf d_rs;                // rescale constants [L1][L1][3]
+  DevBuf d_status;            // device status word: nonzero after a bounded device-side wait expired
+  bool use_tc = true;         // convolution multiply-accumulate on the tensor cores where it fits
   // bound on the temporaries of one convolution, relinearisation, product or
   // rescale (bytes; 0 = none): larger sets are processed in ciphertext chunks
   // with the same per-ciphertext arithmetic
@@ -254,6 +256,12 @@ void k_mul_const(const Ctx& C, const u64* in, u64* out, size_t rows, int limbs, 
 // y[c][comp] += v[c][comp], comp < 2 (y with ypolys components, v with two)
 void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limbs);
 // conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
+// the same on the tensor cores (conv_tc.cu) for the limbs of one class (narrow: primes below
+// kMac96Prime); conv_mac_tc_fits: the chunk sums of this shape stay exact in fp32
+bool conv_mac_tc_fits(const Ctx& C, int c_in, int k, bool narrow);
+void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
+                   int c_out, int w_out, int limbs, bool narrow);
+void check_device_status(Ctx& C);
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs);
 // conv MAC with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a} tensor(W[o][c][a][b], R[c][s j' + b][a])

@@ -1113,13 +1113,22 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   // limbs by kernel: 96-bit sums below kMac96Prime, Shoup products above
   int wide = 0;
   for (int i = 0; i < limbs; i++) wide += C.q[i] >= kMac96Prime;
-  const int narrow = limbs - wide;
+  int narrow = limbs - wide;
   const double T = (double)c_in * k * k;
   auto per_limb_bytes = [&] {
     return 8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
   };
   const double prods_limb = 2.0 * C.N * (double)c_out * w_out * T;
   const unsigned gy = (unsigned)(2 * limbs);
+  // the tensor cores take each class of limbs whose chunk sums stay exact (conv_tc.cu)
+  if (wide > 0 && C.use_tc && conv_mac_tc_fits(C, c_in, k, false)) {
+    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, false);
+    wide = 0;
+  }
+  if (narrow > 0 && C.use_tc && conv_mac_tc_fits(C, c_in, k, true)) {
+    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, true);
+    narrow = 0;
+  }
   if (wide > 0) {
     const unsigned gx = (unsigned)((C.N / TN + TH - 1) / TH);
     unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * 2 * wide));

@@ -301,6 +301,65 @@ def test_conv2d_96bit_sums_reduce_mid_sum_and_run_two_channel_passes(lib, c_out,
     assert np.abs(got - ref).max() < 1e-4
 
 
+@pytest.mark.parametrize("c_in,k,stride,c_out,polys", [(8, 3, 2, 16, 3), (1, 5, 2, 8, 2), (2, 3, 1, 5, 2),
+                                                        (8, 3, 2, 11, 2)])
+def test_conv_tensor_cores_equal_cuda_cores_and_oracle(lib, c_in, k, stride, c_out, polys):
+    """The convolution's multiply-accumulate on the tensor cores (residues in 7-bit chunks whose
+    products the tensor cores sum exactly in fp32, recombined modulo q) and on the CUDA cores give
+    the same words, bit-exact with the oracle: 45-bit and 60-bit primes, 8, 16 and ragged channel
+    counts, 72, 25 and 18 terms, two- and three-component inputs."""
+    o, g = make_pair(10, (60,) + (45,) * 6, 2, 60, 2, 45.0, seed=47, steps=list(range(1, k)))
+    H, side, Bn, gap = 32, 13, 3, 1
+    rng = np.random.default_rng(47 + c_out + c_in)
+    imgs = rng.uniform(-1, 1, (Bn, c_in, side, side))
+    K = rng.normal(0, 0.2, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.2, c_out)
+    z = np.concatenate([layouts.image_columns(imgs[:, c], o.slots, H, gap) for c in range(c_in)])
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=3000)
+    sc = o.scale
+    if polys == 3:
+        ox = o.square(ox)
+        g.square(gx)
+        sc = sc * sc / o.q[o.L1 - 1]
+    ox = ox.reshape(c_in, side, *ox.shape[1:])
+    got = {}
+    for tc in (True, False):
+        g.set_tensor_cores(tc)
+        got[tc] = g.conv2d(gx, c_in, gap, K, bias, stride).export()
+    g.set_tensor_cores(True)
+    assert np.array_equal(got[True], got[False])
+    assert np.array_equal(got[True], o.conv2d(ox, gap, K, bias, stride, sc))
+
+
+def test_three_digits_and_five_special_primes_match_oracle(lib):
+    """The CNN's prime chain with dnum = 3 (digits of five primes) and five 60-bit special primes:
+    hoisted rotations, the square with its deferred relinearisation and a strided convolution over
+    it, bit-exact with the oracle, and decrypting to the FP64 convolution."""
+    o, g = make_pair(10, (60,) + (45,) * 12, 5, 60, 5, 45.0, seed=51, steps=[1, 2, 3])
+    assert len(o.primes) == 18
+    H, side, Bn, c_in, k, c_out = 32, 11, 3, 2, 3, 4
+    rng = np.random.default_rng(51)
+    imgs = rng.uniform(-1, 1, (Bn, c_in, side, side))
+    z = np.concatenate([layouts.image_columns(imgs[:, c], o.slots, H) for c in range(c_in)])
+    ox, gx = encrypt_both(o, g, encode_columns(o, z), ct_id_base=0)
+    r = g.rotate(gx.slice(0, 2), [1, 3]).export().reshape(2, 2, 2, o.L1, o.N)
+    for c in range(2):
+        want = o.rotate(ox[c], [1, 3])
+        assert np.array_equal(r[c], want), c
+    K = rng.normal(0, 0.2, (c_out, c_in, k, k))
+    bias = rng.normal(0, 0.2, c_out)
+    g.square(gx)
+    sq = o.square(ox)
+    sc = o.scale * o.scale / o.q[o.L1 - 1]
+    gy = g.conv2d(gx, c_in, 1, K, bias, 2)
+    oy = o.conv2d(sq.reshape(c_in, side, *sq.shape[1:]), 1, K, bias, 2, sc)
+    assert np.array_equal(gy.export(), oy)
+    ref = fp64_ref.conv2d(imgs ** 2, K, bias, 2)
+    got = g.decrypt_image(gy, Bn, H, 2, ref.shape[2])
+    got = got.reshape(Bn, c_out, ref.shape[3], ref.shape[2]).transpose(0, 1, 3, 2)
+    assert np.abs(got - ref).max() < 1e-4
+
+
 def test_fc_96bit_sums_over_480_columns(lib):
     """The dense layer's shape (16 channels x 30 columns = 480 input ciphertexts, rows at gap 4 in
     blocks of 128) with 45-bit working primes: the 96-bit sums are reduced every ~63 columns, several

@@ -802,3 +802,21 @@ def test_cnn_small_matches_fp64():
     x = fp64_ref.conv2d(x, c2w, c2b, 2) ** 2
     ref = fp64_ref.dense(x, fw, fb)
     assert np.abs(logits - ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("K,alpha,decrypts", [(2, 5, False), (5, 5, True), (2, 2, True)])
+def test_three_digits_need_a_special_modulus_above_the_digit(K, alpha, decrypts):
+    """The CNN configuration names 2 special primes and dnum = 3. With its 13 Q primes, three digits
+    hold 5 primes each (up to 60 + 4 x 45 = 240 bits) while P = 2 x 60 = 120 bits, and the key-switch
+    noise, about (digit / P) sigma sqrt(N) per coefficient, swamps the 2^45 scale: a rotation decrypts
+    with an error far above 1e-4. Five special primes (P = 300 bits, dnum = 3) or digits of two primes
+    with the two stated special primes (7 digits, the reading the CNN runs) decrypt within 1e-6."""
+    o = Oracle(11, (60,) + (45,) * 12, K, 60, alpha, 45.0, seed=9)
+    o.keygen([1])
+    z = np.random.default_rng(9).uniform(-1, 1, o.slots)
+    ct = o.encrypt(o.encode(z), o.L1, 0)
+    err = float(np.abs(o.decrypt(o.rotate(ct, [1])[0]) - np.roll(z, -1)).max())
+    if decrypts:
+        assert err < 1e-6
+    else:
+        assert err > 1e-4
