@@ -4,7 +4,9 @@
 // errors into status codes; all arithmetic runs in the kernels.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <thread>
 #include <vector>
 
@@ -17,6 +19,29 @@ static thread_local std::string g_err;
 
 namespace he {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+// the registry is never destroyed, so handles freed during process exit still find it
+static std::mutex& reg_mu() {
+  static std::mutex* m = new std::mutex;
+  return *m;
+}
+static std::unordered_map<const void*, int>& reg() {
+  static auto* r = new std::unordered_map<const void*, int>;
+  return *r;
+}
+void handle_add(const void* h, int kind) {
+  std::lock_guard<std::mutex> lk(reg_mu());
+  reg()[h] = kind;
+}
+void handle_remove(const void* h) {
+  std::lock_guard<std::mutex> lk(reg_mu());
+  reg().erase(h);
+}
+bool handle_is(const void* h, int kind) {
+  std::lock_guard<std::mutex> lk(reg_mu());
+  auto it = reg().find(h);
+  return it != reg().end() && it->second == kind;
+}
 }  // namespace he
 
 template <class F>
@@ -81,6 +106,7 @@ int he_ctx_create(const he_params_desc* d, uint64_t seed, void* cuda_stream, he_
 }
 
 void he_ctx_destroy(he_ctx* ctx) {
+  if (ctx && !handle_live(ctx)) return;
   if (!ctx) return;
   cudaStreamSynchronize(ctx->c.stream);
   delete ctx;
@@ -88,6 +114,7 @@ void he_ctx_destroy(he_ctx* ctx) {
 
 int he_ctx_synchronize(he_ctx* ctx) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null context");
     HE_CUDA(cudaStreamSynchronize(ctx->c.stream));
     check_device_status(ctx->c);
@@ -96,6 +123,7 @@ int he_ctx_synchronize(he_ctx* ctx) {
 
 int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && out, HE_E_ARG, "null argument");
     REQUIRE(n >= ctx->c.np(), HE_E_ARG, "output too small");
     for (int i = 0; i < ctx->c.np(); i++) out[i] = ctx->c.q[i];
@@ -104,6 +132,7 @@ int he_ctx_primes(const he_ctx* ctx, uint64_t* out, int n) {
 
 int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* alpha, double* scale) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null context");
     if (log_n) *log_n = ctx->c.log_n;
     if (n_q) *n_q = ctx->c.L1;
@@ -115,6 +144,7 @@ int he_ctx_info(const he_ctx* ctx, int* log_n, int* n_q, int* n_special, int* al
 
 int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && n_steps >= 0 && (n_steps == 0 || rot_steps), HE_E_ARG, "bad arguments");
     std::vector<long> st(rot_steps, rot_steps + n_steps);
     keygen(ctx->c, st);
@@ -124,6 +154,7 @@ int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps) {
 int he_encrypt_image(he_ctx* ctx, const double* px, int batch, int h, int w, int block_stride, uint64_t ct_id_base,
                      he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && px && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long M = (long)C.N / 2;
@@ -140,6 +171,7 @@ int he_encrypt_image(he_ctx* ctx, const double* px, int batch, int h, int w, int
 
 int he_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long M = (long)C.N / 2;
@@ -153,6 +185,7 @@ int he_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_
 
 int he_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && B && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long M = (long)C.N / 2;
@@ -174,6 +207,7 @@ int he_volley_geometry(int slots, int m, int p, int* M, int* per, int* groups) {
 int he_encrypt_matrix_a_volley(he_ctx* ctx, const double* A, int m, int n, int p, uint64_t ct_id_base,
                                he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -194,6 +228,7 @@ int he_encrypt_matrix_a_volley(he_ctx* ctx, const double* A, int m, int n, int p
 int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double scale, uint64_t ct_id_base,
                       he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && m && out, HE_E_ARG, "null argument");
     REQUIRE(scale > 0, HE_E_ARG, "scale must be positive");
     *out = wrap(encrypt_coeffs(ctx->c, m, n_ct, limbs, scale, ct_id_base));
@@ -202,6 +237,9 @@ int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double
 
 int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C_out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(B);
     REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
     REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
     REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
@@ -211,6 +249,9 @@ int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, h
 
 int he_matmul_bsgs(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int g, he_ctset** C_out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(B);
     REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
     REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
     REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
@@ -226,6 +267,9 @@ int he_matmul_bsgs(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int
 
 int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset** C_out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(B);
     REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
     REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
     *C_out = wrap(matmul_volley(ctx->c, *A->s, *B->s));
@@ -235,11 +279,14 @@ int he_matmul_volley(he_ctx* ctx, const he_ctset* A, const he_ctset* B, he_ctset
 int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he_ctset* const* B, const int* m,
                       const int* p, he_ctset** C_out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && count >= 0 && (count == 0 || (A && B && m && p && C_out)), HE_E_ARG, "null argument");
     std::vector<const CtSet*> As(count), Bs(count);
     std::vector<int> ps(p, p + count);
     for (int i = 0; i < count; i++) {
       REQUIRE(A[i] && B[i], HE_E_ARG, "null operand");
+      HANDLE(A[i]);
+      HANDLE(B[i]);
       REQUIRE(A[i]->s->scale == B[i]->s->scale, HE_E_SCALE, "operands at different scales");
       REQUIRE(m[i] >= 1 && (size_t)m[i] <= ctx->c.N / 2, HE_E_ARG, "bad m");
       As[i] = A[i]->s.get();
@@ -253,6 +300,8 @@ int he_matmul_batched(he_ctx* ctx, int count, const he_ctset* const* A, const he
 int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* weights, const double* bias, int c_out,
               int k, int stride, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && weights && out, HE_E_ARG, "null argument");
     *out = wrap(conv2d(ctx->c, *in->s, c_in, gap, weights, bias, c_out, k, stride));
   });
@@ -261,6 +310,7 @@ int he_conv2d(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const double* 
 int he_encrypt_conv_weights(he_ctx* ctx, const double* W, int c_out, int c_in, int k, int limbs, uint64_t ct_id_base,
                             he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && W && out, HE_E_ARG, "null argument");
     REQUIRE(c_out >= 1 && c_in >= 1 && k >= 1, HE_E_ARG, "bad kernel shape");
     Ctx& C = ctx->c;
@@ -276,6 +326,9 @@ int he_encrypt_conv_weights(he_ctx* ctx, const double* W, int c_out, int c_in, i
 int he_conv2d_enc(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const he_ctset* weights, const double* bias,
                   int c_out, int k, int stride, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
+    HANDLE(weights);
     REQUIRE(ctx && in && weights && out, HE_E_ARG, "null argument");
     *out = wrap(conv2d_enc(ctx->c, *in->s, c_in, gap, *weights->s, bias, c_out, k, stride));
   });
@@ -283,6 +336,8 @@ int he_conv2d_enc(he_ctx* ctx, const he_ctset* in, int c_in, int gap, const he_c
 
 int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(inout);
     REQUIRE(ctx && inout && coeffs, HE_E_ARG, "null argument");
     REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
             "in-place operation on a set made before the capture");
@@ -299,6 +354,7 @@ int he_poly_act(he_ctx* ctx, he_ctset* inout, const double* coeffs, int degree) 
 int he_fc_prepare(he_ctx* ctx, const double* W, int out_dim, int c_in, int h_valid, int w_in, int gap,
                   int block_stride, int batch, int limbs, he_ptset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && W && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long M = (long)C.N / 2;
@@ -335,6 +391,7 @@ int he_fc_prepare(he_ctx* ctx, const double* W, int out_dim, int c_in, int h_val
 int he_fc_prepare_coeffs(he_ctx* ctx, const int64_t* pts, int out_dim, int c_in, int w_in, int gap, int block_stride,
                          int limbs, he_ptset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && pts && out, HE_E_ARG, "null argument");
     REQUIRE(out_dim >= 1 && c_in >= 1 && w_in >= 1, HE_E_ARG, "bad shape");
     REQUIRE(pow2(block_stride) && pow2(gap), HE_E_ARG, "gap and block_stride must be powers of two");
@@ -352,10 +409,16 @@ int he_fc_prepare_coeffs(he_ctx* ctx, const int64_t* pts, int out_dim, int c_in,
   });
 }
 
-void he_ptset_free(he_ptset* pts) { delete pts; }
+void he_ptset_free(he_ptset* pts) {
+  if (pts && !handle_live(pts)) return;
+  delete pts;
+}
 
 int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const double* bias, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
+    HANDLE(pts);
     REQUIRE(ctx && in && pts && out, HE_E_ARG, "null argument");
     REQUIRE(in->s->n == pts->n_in, HE_E_ARG, "input size does not match the prepared weights");
     REQUIRE(in->s->limbs == pts->limbs, HE_E_LEVEL, "input level does not match the prepared weights");
@@ -366,6 +429,10 @@ int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const doub
 int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int out_dim, int c_in, int h_valid,
           int w_in, int gap, int block_stride, int batch, he_ctset** out) {
   he_ptset* pts = nullptr;
+  if ((ctx && !handle_live(ctx)) || (in && !handle_live(in))) {
+    set_last_error("invalid handle (unknown or freed)");
+    return HE_E_ARG;
+  }
   int rc = he_fc_prepare(ctx, W, out_dim, c_in, h_valid, w_in, gap, block_stride, batch, in ? in->s->limbs : 0, &pts);
   if (rc != HE_OK) return rc;
   rc = he_fc_apply(ctx, in, pts, b, out);
@@ -390,6 +457,7 @@ static void vr_check(const Ctx& C, int h, int w, int k, int Hb, int Wb) {
 int he_vr_encrypt_images(he_ctx* ctx, const double* px, int batch, int h, int w, int block_h, int block_w,
                          uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && px && out && batch >= 1, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     vr_check(C, h, w, 1, block_h, block_w);
@@ -408,6 +476,7 @@ int he_vr_encrypt_images(he_ctx* ctx, const double* px, int batch, int h, int w,
 int he_vr_encrypt_kernels(he_ctx* ctx, const double* K, int k, double k0, int h, int w, int block_h, int block_w,
                           int limbs, uint64_t ct_id_base, he_ctset** kernels, he_ctset** bias) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && K && kernels && bias, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     vr_check(C, h, w, k, block_h, block_w);
@@ -445,6 +514,10 @@ int he_vr_encrypt_kernels(he_ctx* ctx, const double* K, int k, double k0, int h,
 int he_vr_conv2d_coeffs(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int k,
                         int block_w, const int64_t* masks, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
+    HANDLE(kernels);
+    HANDLE(bias);
     REQUIRE(ctx && in && kernels && bias && masks && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const int lp = in->s->limbs;
@@ -457,6 +530,10 @@ int he_vr_conv2d_coeffs(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels
 int he_vr_conv2d(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const he_ctset* bias, int h, int w, int k,
                  int block_h, int block_w, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
+    HANDLE(kernels);
+    HANDLE(bias);
     REQUIRE(ctx && in && kernels && bias && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     vr_check(C, h, w, k, block_h, block_w);
@@ -483,6 +560,8 @@ int he_vr_conv2d(he_ctx* ctx, const he_ctset* in, const he_ctset* kernels, const
 
 int he_vrot_coeffs(he_ctx* ctx, const he_ctset* in, int r, int img_len, const int64_t* masks, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && masks && out, HE_E_ARG, "null argument");
     const int lp = in->s->limbs;
     REQUIRE(lp >= 2, HE_E_LEVEL, "no level left for vRot");
@@ -493,6 +572,8 @@ int he_vrot_coeffs(he_ctx* ctx, const he_ctset* in, int r, int img_len, const in
 
 int he_vrot(he_ctx* ctx, const he_ctset* in, int r, int row_len, int img_len, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -512,6 +593,7 @@ int he_vrot(he_ctx* ctx, const he_ctset* in, int r, int row_len, int img_len, he
 
 int he_vr_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && A && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -524,6 +606,7 @@ int he_vr_encrypt_matrix_a(he_ctx* ctx, const double* A, int m, int n, uint64_t 
 
 int he_vr_encrypt_matrix_b(he_ctx* ctx, const double* B, int n, int p, uint64_t ct_id_base, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && B && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -547,6 +630,9 @@ static std::unique_ptr<CtSet> vr_matmul_from_host(Ctx& C, const CtSet& A, const 
 int he_vr_matmul_coeffs(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, const int64_t* masks,
                         he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(Bbar);
     REQUIRE(ctx && A && Bbar && masks && out, HE_E_ARG, "null argument");
     REQUIRE(m >= 1 && (long)m * n <= (long)ctx->c.N / 2, HE_E_ARG, "bad shape");
     *out = wrap(vr_matmul_from_host(ctx->c, *A->s, *Bbar->s, n, p, masks));
@@ -555,6 +641,9 @@ int he_vr_matmul_coeffs(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, in
 
 int he_vr_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, int n, int p, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(Bbar);
     REQUIRE(ctx && A && Bbar && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -575,6 +664,8 @@ int he_vr_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* Bbar, int m, in
 
 int he_reform_coeffs(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, const int64_t* masks, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && masks && out, HE_E_ARG, "null argument");
     REQUIRE(gap >= 2 && h_valid >= 1, HE_E_ARG, "bad ReForm shape");
     Ctx& C = ctx->c;
@@ -587,6 +678,8 @@ int he_reform_coeffs(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, cons
 
 int he_reform(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, int block_stride, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     const long S = (long)C.N / 2;
@@ -609,7 +702,11 @@ int he_reform(he_ctx* ctx, const he_ctset* in, int gap, int h_valid, int block_s
 
 int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const he_ptset* masks, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(masks);
     REQUIRE(ctx && sets && masks && out && n_sets >= 1, HE_E_ARG, "null argument");
+    for (int t = 0; t < n_sets; t++) HANDLE(sets[t]);
+    REQUIRE(sets[0], HE_E_ARG, "null set");
     const CtSet& s0 = *sets[0]->s;
     std::vector<const u64*> xs;
     for (int t = 0; t < n_sets; t++) {
@@ -627,6 +724,8 @@ int he_pack_blocks(he_ctx* ctx, const he_ctset* const* sets, int n_sets, const h
 
 int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && steps && out && n_steps >= 1, HE_E_ARG, "bad arguments");
     std::vector<long> st(steps, steps + n_steps);
     *out = wrap(rotate(ctx->c, *in->s, st));
@@ -635,6 +734,9 @@ int he_rotate(he_ctx* ctx, const he_ctset* in, const int32_t* steps, int n_steps
 
 int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(a);
+    HANDLE(b);
     REQUIRE(ctx && a && b && out, HE_E_ARG, "null argument");
     *out = wrap(mul(ctx->c, *a->s, *b->s));
   });
@@ -642,6 +744,8 @@ int he_mul(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
 
 int he_rescale(he_ctx* ctx, he_ctset* inout) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(inout);
     REQUIRE(ctx && inout, HE_E_ARG, "null argument");
     REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
             "in-place operation on a set made before the capture");
@@ -651,6 +755,9 @@ int he_rescale(he_ctx* ctx, he_ctset* inout) {
 
 int he_add(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(a);
+    HANDLE(b);
     REQUIRE(ctx && a && b && out, HE_E_ARG, "null argument");
     *out = wrap(add(ctx->c, *a->s, *b->s));
   });
@@ -658,6 +765,8 @@ int he_add(he_ctx* ctx, const he_ctset* a, const he_ctset* b, he_ctset** out) {
 
 int he_decrypt_slots(he_ctx* ctx, const he_ctset* in, double* out, size_t out_len) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
     REQUIRE(out_len >= (size_t)in->s->n * (ctx->c.N / 2), HE_E_ARG, "output too small");
     decrypt_slots(ctx->c, *in->s, out);
@@ -666,6 +775,8 @@ int he_decrypt_slots(he_ctx* ctx, const he_ctset* in, double* out, size_t out_le
 
 int he_decrypt_matrix(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(Cs);
     REQUIRE(ctx && Cs && C_out, HE_E_ARG, "null argument");
     REQUIRE(Cs->s->n == p && m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "shape does not match");
     const size_t M = ctx->c.N / 2;
@@ -678,6 +789,8 @@ int he_decrypt_matrix(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_o
 
 int he_decrypt_matrix_volley(he_ctx* ctx, const he_ctset* Cs, int m, int p, double* C_out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(Cs);
     REQUIRE(ctx && Cs && C_out, HE_E_ARG, "null argument");
     const long S = (long)ctx->c.N / 2;
     int Mb, per, G;
@@ -698,6 +811,8 @@ int he_decrypt_matrix_volley(he_ctx* ctx, const he_ctset* Cs, int m, int p, doub
 int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_stride, int gap, int h_valid, double* out,
                      size_t out_len) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
     const size_t M = ctx->c.N / 2;
     const int n = in->s->n;
@@ -716,6 +831,7 @@ int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_strid
 
 int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words) {
   return guard([&] {
+    HANDLE(set);
     REQUIRE(set && host, HE_E_ARG, "null argument");
     REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
     export_coeffs(*set->s->ctx, *set->s, host);
@@ -724,6 +840,7 @@ int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words) {
 
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
     *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale));
   });
@@ -731,6 +848,7 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
 
 int he_ctx_set_tensor_cores(he_ctx* ctx, int on) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null context");
     ctx->c.use_tc = on != 0;
   });
@@ -738,6 +856,7 @@ int he_ctx_set_tensor_cores(he_ctx* ctx, int on) {
 
 int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null context");
     ctx->c.work_budget = bytes;
   });
@@ -745,6 +864,7 @@ int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes) {
 
 int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words) {
   return guard([&] {
+    HANDLE(set);
     REQUIRE(set && host, HE_E_ARG, "null argument");
     REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
     export_raw(*set->s->ctx, *set->s, host);
@@ -753,6 +873,7 @@ int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words) {
 
 int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
     *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale, true));
   });
@@ -760,6 +881,7 @@ int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, dou
 
 int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int* polys) {
   return guard([&] {
+    HANDLE(set);
     REQUIRE(set, HE_E_ARG, "null set");
     if (n_ct) *n_ct = set->s->n;
     if (limbs) *limbs = set->s->limbs;
@@ -770,6 +892,8 @@ int he_ctset_info(const he_ctset* set, int* n_ct, int* limbs, double* scale, int
 
 int he_ctset_drop_levels(he_ctx* ctx, const he_ctset* in, int limbs, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
     REQUIRE(ctx && in && out, HE_E_ARG, "null argument");
     REQUIRE(limbs >= 1 && limbs <= in->s->limbs, HE_E_LEVEL, "the target level must keep 1 .. limbs primes");
     *out = wrap(drop_limbs(ctx->c, *in->s, limbs));
@@ -778,6 +902,8 @@ int he_ctset_drop_levels(he_ctx* ctx, const he_ctset* in, int limbs, he_ctset** 
 
 int he_add_plain_coeffs(he_ctx* ctx, he_ctset* inout, const int64_t* m, int n_vec) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(inout);
     REQUIRE(ctx && inout && m, HE_E_ARG, "null argument");
     REQUIRE(n_vec == 1 || n_vec == inout->s->n, HE_E_ARG, "one plaintext, or one per ciphertext");
     REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
@@ -788,6 +914,8 @@ int he_add_plain_coeffs(he_ctx* ctx, he_ctset* inout, const int64_t* m, int n_ve
 
 int he_add_slots(he_ctx* ctx, he_ctset* inout, const double* v, int n_vec) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(inout);
     REQUIRE(ctx && inout && v, HE_E_ARG, "null argument");
     REQUIRE(n_vec == 1 || n_vec == inout->s->n, HE_E_ARG, "one slot vector, or one per ciphertext");
     REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
@@ -802,6 +930,8 @@ int he_add_slots(he_ctx* ctx, he_ctset* inout, const double* v, int n_vec) {
 
 int he_relinearize(he_ctx* ctx, he_ctset* inout) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(inout);
     REQUIRE(ctx && inout, HE_E_ARG, "null argument");
     REQUIRE(!ctx->c.capturing || inout->s->gen == ctx->c.capture_gen, HE_E_STATE,
             "in-place operation on a set made before the capture");
@@ -811,6 +941,7 @@ int he_relinearize(he_ctx* ctx, he_ctset* inout) {
 
 int he_ctset_device_ptr(const he_ctset* set, uint64_t** dptr) {
   return guard([&] {
+    HANDLE(set);
     REQUIRE(set && dptr, HE_E_ARG, "null argument");
     *dptr = set->s->buf.p;
   });
@@ -818,6 +949,8 @@ int he_ctset_device_ptr(const he_ctset* set, uint64_t** dptr) {
 
 int he_ctset_slice(he_ctx* ctx, const he_ctset* set, int first, int n, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(set);
     REQUIRE(ctx && set && out, HE_E_ARG, "null argument");
     const CtSet& s = *set->s;
     REQUIRE(first >= 0 && n >= 1 && first + n <= s.n, HE_E_ARG, "slice out of range");
@@ -830,7 +963,10 @@ int he_ctset_slice(he_ctx* ctx, const he_ctset* set, int first, int n, he_ctset*
 
 int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_ctset** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && sets && out && n_sets >= 1, HE_E_ARG, "null argument");
+    for (int i = 0; i < n_sets; i++) HANDLE(sets[i]);
+    REQUIRE(sets[0], HE_E_ARG, "null set");
     int total = 0;
     for (int i = 0; i < n_sets; i++) {
       REQUIRE(sets[i], HE_E_ARG, "null set");
@@ -852,6 +988,7 @@ int he_ctset_concat(he_ctx* ctx, const he_ctset* const* sets, int n_sets, he_cts
 }
 
 void he_ctset_free(he_ctset* set) {
+  if (set && !handle_live(set)) return;
   if (!set) return;
   Ctx* C = set->s ? set->s->ctx : nullptr;
   if (C && C->capturing && set->s->gen != C->capture_gen) {
@@ -863,6 +1000,7 @@ void he_ctset_free(he_ctset* set) {
 
 int he_graph_begin(he_ctx* ctx) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     REQUIRE(!C.capturing, HE_E_STATE, "a capture is already open on this context");
@@ -877,6 +1015,7 @@ int he_graph_begin(he_ctx* ctx) {
 
 int he_graph_end(he_ctx* ctx, he_graph** out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && out, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     REQUIRE(C.capturing, HE_E_STATE, "no capture is open on this context");
@@ -919,6 +1058,7 @@ int he_graph_end(he_ctx* ctx, he_graph** out) {
 
 int he_graph_launch(he_graph* g) {
   return guard([&] {
+    HANDLE(g);
     REQUIRE(g && g->exec, HE_E_ARG, "null graph");
     Ctx& C = g->ctx->c;
     REQUIRE(!C.capturing, HE_E_STATE, "a capture is open on this context");
@@ -929,12 +1069,14 @@ int he_graph_launch(he_graph* g) {
 
 int he_graph_info(const he_graph* g, uint64_t* kernel_nodes) {
   return guard([&] {
+    HANDLE(g);
     REQUIRE(g && kernel_nodes, HE_E_ARG, "null argument");
     *kernel_nodes = g->kernels;
   });
 }
 
 void he_graph_destroy(he_graph* g) {
+  if (g && !handle_live(g)) return;
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
@@ -943,6 +1085,9 @@ void he_graph_destroy(he_graph* g) {
 
 int he_ctset_assign(he_ctx* ctx, he_ctset* dst, const he_ctset* src) {
   return guard([&] {
+    HANDLE(ctx);
+    HANDLE(dst);
+    HANDLE(src);
     REQUIRE(ctx && dst && src, HE_E_ARG, "null argument");
     const CtSet& a = *src->s;
     CtSet& b = *dst->s;
@@ -956,6 +1101,7 @@ int he_ctset_assign(he_ctx* ctx, he_ctset* dst, const he_ctset* src) {
 
 int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && modmul_per_s, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     int sms = 0;
@@ -980,6 +1126,7 @@ int he_calibrate_modmul(he_ctx* ctx, double* modmul_per_s) {
 
 int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && mac_per_s, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     int sms = 0;
@@ -1004,6 +1151,7 @@ int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s) {
 
 int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && bfly_per_s, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     int sms = 0;
@@ -1028,6 +1176,7 @@ int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s) {
 
 int he_ntt_set_geometry(he_ctx* ctx, int n1, int cols) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx, HE_E_ARG, "null argument");
     Ctx& C = ctx->c;
     if (n1 == 0 && cols == 0) {
@@ -1042,6 +1191,7 @@ int he_ntt_set_geometry(he_ctx* ctx, int n1, int cols) {
 
 int he_ntt_autotune(he_ctx* ctx, int rows, int* n1_out, int* cols_out, double* us_out) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && rows >= 1, HE_E_ARG, "bad arguments");
     Ctx& C = ctx->c;
     REQUIRE(!C.capturing, HE_E_STATE, "a capture is open on this context");
@@ -1101,6 +1251,7 @@ int he_ntt_autotune(he_ctx* ctx, int rows, int* n1_out, int* cols_out, double* u
 
 int he_ntt(he_ctx* ctx, uint64_t* host, int n_polys, int limbs, int first_prime, int inverse) {
   return guard([&] {
+    HANDLE(ctx);
     REQUIRE(ctx && host && n_polys >= 1 && limbs >= 1, HE_E_ARG, "bad arguments");
     Ctx& C = ctx->c;
     REQUIRE(first_prime >= 0 && first_prime + limbs <= C.np(), HE_E_ARG, "prime range out of bounds");

@@ -398,22 +398,49 @@ void host_parallel(size_t n, F f) {
 void encode_real(const Ctx& C, const double* z, size_t nz, double scale, int64_t* m);
 void decode_real(const Ctx& C, const double* m, double scale, double* z);
 
+// Live handles of the C ABI (contexts, ciphertext sets, plaintext sets, graphs, servers): a
+// handle registers itself when it is made and leaves the registry when it is freed; every entry
+// point checks its handle arguments against the registry before it reads them, so an unknown,
+// corrupted or already freed handle is refused with HE_E_ARG instead of being dereferenced.
+enum HandleKind { kHCtx = 1, kHSet, kHPts, kHGraph, kHServer };
+void handle_add(const void* h, int kind);
+void handle_remove(const void* h);
+bool handle_is(const void* h, int kind);
+
 }  // namespace he
 
 struct he_ctx {
   he::Ctx c;
+  he_ctx() { he::handle_add(this, he::kHCtx); }
+  ~he_ctx() { he::handle_remove(this); }
 };
 struct he_ctset {
   std::unique_ptr<he::CtSet> s;
+  he_ctset() { he::handle_add(this, he::kHSet); }
+  ~he_ctset() { he::handle_remove(this); }
 };
 struct he_graph {
   he_ctx* ctx = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;  // kernel nodes, added to the launch counter per replay
+  he_graph() { he::handle_add(this, he::kHGraph); }
+  ~he_graph() { he::handle_remove(this); }
 };
 struct he_ptset {
   he::Ctx* ctx = nullptr;
   int out_dim = 0, n_in = 0, limbs = 0, gap = 1, block_stride = 1;
   he::DevBuf buf;  // [out_dim][n_in][limbs][N]
+  he_ptset() { he::handle_add(this, he::kHPts); }
+  ~he_ptset() { he::handle_remove(this); }
 };
+struct he_server;
+inline bool handle_live(const he_ctx* h) { return he::handle_is(h, he::kHCtx); }
+inline bool handle_live(const he_ctset* h) { return he::handle_is(h, he::kHSet); }
+inline bool handle_live(const he_graph* h) { return he::handle_is(h, he::kHGraph); }
+inline bool handle_live(const he_ptset* h) { return he::handle_is(h, he::kHPts); }
+inline bool handle_live(const he_server* h) { return he::handle_is(h, he::kHServer); }
+#define HANDLE(p)                                                                                   \
+  do {                                                                                              \
+    if ((p) && !handle_live(p)) throw he::Error(1 /* HE_E_ARG */, "invalid handle (unknown or freed): " #p); \
+  } while (0)

@@ -52,6 +52,7 @@ int he_rescale_noalloc(he_ctx* ctx, const uint64_t* in, int n_ct, int limbs, dou
                        double* out_scale) {
   try {
     if (!ctx || !in || !out) throw Error(HE_E_ARG, "null argument");
+    HANDLE(ctx);
     Ctx& C = ctx->c;
     if (n_ct < 1 || limbs < 2 || limbs > C.L1) throw Error(HE_E_ARG, "need n_ct >= 1 and 2 <= limbs <= n_q");
     const size_t N = C.N;

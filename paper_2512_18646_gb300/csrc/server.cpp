@@ -311,6 +311,8 @@ using namespace he;
 
 struct he_server {
   std::unique_ptr<Server> s;
+  he_server() { handle_add(this, kHServer); }
+  ~he_server() { handle_remove(this); }
 };
 
 template <class F>
@@ -340,6 +342,7 @@ extern "C" {
 
 int he_server_create(he_ctx* ctx, const he_server_desc* d, he_server** out) {
   return server_guard([&] {
+    HANDLE(ctx);
     SREQUIRE(ctx && d && out, HE_E_ARG, "null argument");
     SREQUIRE(d->conv1_w && d->conv1_b && d->conv2_w && d->conv2_b && d->sides && d->fc_w && d->fc_b, HE_E_ARG,
              "null weights");
@@ -412,6 +415,7 @@ int he_server_create(he_ctx* ctx, const he_server_desc* d, he_server** out) {
 
 int he_server_request_words(const he_server* srv, int side, size_t* n_words) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && n_words, HE_E_ARG, "null argument");
     SREQUIRE(srv->s->sides.count(side), HE_E_ARG, "no model for this image side");
     *n_words = (size_t)side * 2 * srv->s->C->L1 * srv->s->C->N;
@@ -420,6 +424,7 @@ int he_server_request_words(const he_server* srv, int side, size_t* n_words) {
 
 int he_server_submit(he_server* srv, const uint64_t* host_words, size_t n_words, int side, uint64_t* req_id) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && host_words && req_id, HE_E_ARG, "null argument");
     Server& s = *srv->s;
     SREQUIRE(s.sides.count(side), HE_E_ARG, "no model for this image side");
@@ -444,6 +449,7 @@ int he_server_submit(he_server* srv, const uint64_t* host_words, size_t n_words,
 
 int he_server_result_words(const he_server* srv, size_t* n_words) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && n_words, HE_E_ARG, "null argument");
     *n_words = (size_t)10 * 2 * (srv->s->C->L1 - 6) * srv->s->C->N;
   });
@@ -451,6 +457,7 @@ int he_server_result_words(const he_server* srv, size_t* n_words) {
 
 int he_server_poll(he_server* srv, uint64_t req_id, int* state) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && state, HE_E_ARG, "null argument");
     std::lock_guard<std::mutex> lk(srv->s->mu);
     auto it = srv->s->reqs.find(req_id);
@@ -461,6 +468,10 @@ int he_server_poll(he_server* srv, uint64_t req_id, int* state) {
 
 int he_server_wait(he_server* srv, uint64_t req_id, int timeout_ms, int* state) {
   if (!srv || !state) return HE_E_ARG;
+  if (!handle_live(srv)) {
+    set_last_error("invalid handle (unknown or freed): srv");
+    return HE_E_ARG;
+  }
   Server& s = *srv->s;
   std::unique_lock<std::mutex> lk(s.mu);
   auto it = s.reqs.find(req_id);
@@ -482,6 +493,7 @@ int he_server_wait(he_server* srv, uint64_t req_id, int timeout_ms, int* state) 
 
 int he_server_take(he_server* srv, uint64_t req_id, he_ctset** logits, int* block, double* times_ms) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && logits, HE_E_ARG, "null argument");
     Server& s = *srv->s;
     std::unique_ptr<Request> r;
@@ -515,6 +527,7 @@ int he_server_take(he_server* srv, uint64_t req_id, he_ctset** logits, int* bloc
 int he_server_take_host(he_server* srv, uint64_t req_id, uint64_t* host, size_t n_words, int* block,
                         double* times_ms) {
   return server_guard([&] {
+    HANDLE(srv);
     SREQUIRE(srv && host, HE_E_ARG, "null argument");
     Server& s = *srv->s;
     SREQUIRE(n_words >= (size_t)10 * 2 * (s.C->L1 - 6) * s.C->N, HE_E_ARG, "output too small");
@@ -536,6 +549,10 @@ int he_server_take_host(he_server* srv, uint64_t req_id, uint64_t* host, size_t 
 
 int he_server_pause(he_server* srv, int paused) {
   if (!srv) return HE_E_ARG;
+  if (!handle_live(srv)) {
+    set_last_error("invalid handle (unknown or freed): srv");
+    return HE_E_ARG;
+  }
   {
     std::lock_guard<std::mutex> lk(srv->s->mu);
     srv->s->paused = paused != 0;
@@ -546,6 +563,10 @@ int he_server_pause(he_server* srv, int paused) {
 
 int he_server_stats(he_server* srv, uint64_t* counts, size_t* bytes) {
   if (!srv) return HE_E_ARG;
+  if (!handle_live(srv)) {
+    set_last_error("invalid handle (unknown or freed): srv");
+    return HE_E_ARG;
+  }
   Server& s = *srv->s;
   std::lock_guard<std::mutex> lk(s.mu);
   if (counts) {
@@ -565,7 +586,10 @@ int he_server_stats(he_server* srv, uint64_t* counts, size_t* bytes) {
   return HE_OK;
 }
 
-void he_server_destroy(he_server* srv) { delete srv; }
+void he_server_destroy(he_server* srv) {
+  if (srv && !handle_live(srv)) return;
+  delete srv;
+}
 
 // Discrete-event run of the scheduler: one GPU whose batch of a side with T
 // requests takes base_ms + per_request_ms * T of that side; results are

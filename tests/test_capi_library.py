@@ -67,3 +67,34 @@ def test_volley_geometry_matches_oracle_layout():
     for slots, m, p in [(64, 5, 3), (16, 20, 4), (16, 10, 8)]:  # p does not divide, or no block fits
         with pytest.raises(HeError):
             api.volley_geometry(slots, m, p)
+
+
+def test_corrupted_or_freed_handles_are_refused_without_touching_them():
+    """Every entry point checks its handle arguments against the library's registry of live handles
+    before it reads them: a pointer that is no handle (here a zeroed host buffer, and a stray address)
+    gets HE_E_ARG, and the free / destroy calls ignore it. No CUDA call is reached."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import _lib
+    lib = _lib.load()
+    fake = ctypes.create_string_buffer(4096)
+    for bogus in (ctypes.cast(fake, ctypes.c_void_p), ctypes.c_void_p(0x1000)):
+        n, lv, polys = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        sc = ctypes.c_double()
+        assert lib.he_ctset_info(bogus, ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc),
+                                 ctypes.byref(polys)) == _lib.HE_E_ARG
+        assert b"invalid handle" in lib.he_last_error()
+        assert lib.he_ctx_synchronize(bogus) == _lib.HE_E_ARG
+        assert lib.he_keygen(bogus, None, 0) == _lib.HE_E_ARG
+        st = ctypes.c_int()
+        assert lib.he_server_poll(bogus, ctypes.c_uint64(1), ctypes.byref(st)) == _lib.HE_E_ARG
+        assert lib.he_server_wait(bogus, ctypes.c_uint64(1), 10, ctypes.byref(st)) == _lib.HE_E_ARG
+        out = ctypes.c_void_p()
+        assert lib.he_rotate(bogus, bogus, None, 0, ctypes.byref(out)) == _lib.HE_E_ARG
+        # freeing what is no handle does nothing
+        lib.he_ctset_free(bogus)
+        lib.he_ptset_free(bogus)
+        lib.he_graph_destroy(bogus)
+        lib.he_server_destroy(bogus)
+        lib.he_ctx_destroy(bogus)
+    assert fake.raw == b"\0" * 4096  # never written
