@@ -613,6 +613,7 @@ typedef struct he_server he_server;
 #define HE_REQ_RUNNING 2   /* in the batch on the GPU           */
 #define HE_REQ_DONE 3      /* result ready for he_server_take   */
 #define HE_REQ_FAILED 4    /* he_server_take reports the error  */
+#define HE_REQ_CANCELLED 5 /* withdrawn by he_server_cancel      */
 
 typedef struct {
   const double* conv1_w;         /* [8][1][5][5]                               */
@@ -660,8 +661,8 @@ int he_server_submit(he_server* srv, const uint64_t* host_words, size_t n_words,
 /* Current HE_REQ_* state of a request not yet taken. */
 int he_server_poll(he_server* srv, uint64_t req_id, int* state);
 
-/* Wait up to timeout_ms for a request to be DONE or FAILED (*state gets its
- * state). HE_E_TIMEOUT if it is not. */
+/* Wait up to timeout_ms for a request to be DONE, FAILED or CANCELLED
+ * (*state gets its state). HE_E_TIMEOUT if it is not. */
 int he_server_wait(he_server* srv, uint64_t req_id, int timeout_ms, int* state);
 
 /*
@@ -692,8 +693,18 @@ int he_server_take_host(he_server* srv, uint64_t req_id, uint64_t* host, size_t 
 int he_server_pause(he_server* srv, int paused);
 
 /*
- * counts[6]: submitted, waiting (host), admitted (on the device, not
- * running), done, failed, batches started. bytes[4]: budgeted bytes held now,
+ * he_server_cancel: withdraw a request. Not yet in a batch: it leaves the
+ * queue at once and its device memory and budget are released (requests
+ * behind it may be admitted). In a running batch: the batch finishes and the
+ * request's share of the result is dropped. Done: its share of the result is
+ * released. The request then reads HE_REQ_CANCELLED; he_server_take returns
+ * HE_E_STATE for it and forgets it. Errors: HE_E_ARG (unknown request).
+ */
+int he_server_cancel(he_server* srv, uint64_t req_id);
+
+/*
+ * counts[7]: submitted, waiting (host), admitted (on the device, not
+ * running), done, failed, batches started, cancelled. bytes[4]: budgeted bytes held now,
  * the most ever held, the batch reserve, the allocator's high-water mark
  * (including keys and tables). Either may be NULL.
  */
@@ -767,6 +778,12 @@ int he_calibrate_mac96(he_ctx* ctx, double* mac_per_s);
  * he_calibrate_modmul; the roofline of the transform kernels.
  * Errors: HE_E_ARG (null pointers), HE_E_CUDA. */
 int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s);
+
+/* Fault injection on the host, for tests of the error paths: the next n
+ * device allocations of the library (any context, any thread) fail as if the
+ * device were out of memory (HE_E_OOM); n = 0 disarms it. No GPU fault is
+ * involved. The paper has no counterpart. */
+int he_debug_fail_allocations(int n);
 
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t he_kernel_launches(void);

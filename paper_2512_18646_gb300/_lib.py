@@ -37,7 +37,7 @@ class ServerDesc(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_blocks", ctypes.c_int), ("start_paused", ctypes.c_int)]
 
 
-HE_REQ_WAITING, HE_REQ_ADMITTED, HE_REQ_RUNNING, HE_REQ_DONE, HE_REQ_FAILED = range(5)
+HE_REQ_WAITING, HE_REQ_ADMITTED, HE_REQ_RUNNING, HE_REQ_DONE, HE_REQ_FAILED, HE_REQ_CANCELLED = range(6)
 
 V = ctypes.c_void_p
 PV = ctypes.POINTER(ctypes.c_void_p)
@@ -131,6 +131,8 @@ SIGNATURES = {
     "he_server_take_host": (I, [V, U64, V, SZ, P_I, P_D]),
     "he_server_pause": (I, [V, I]),
     "he_server_stats": (I, [V, P_U64, ctypes.POINTER(SZ)]),
+    "he_server_cancel": (I, [V, U64]),
+    "he_debug_fail_allocations": (I, [I]),
     "he_server_destroy": (None, [V]),
     "he_sched_simulate": (I, [I, P_D, P_I, ctypes.POINTER(SZ), I, P_I, P_D, P_D, SZ, SZ, I, SZ, P_I64, P_I, P_D,
                               P_D, P_D, ctypes.POINTER(SZ)]),

@@ -539,11 +539,16 @@ class Server:
     def pause(self, on: bool):
         check(load().he_server_pause(self.h, int(on)))
 
+    def cancel(self, rid: int):
+        """Withdraw a request (include/he_gb300.h he_server_cancel); its host words may be reused
+        once it reads HE_REQ_CANCELLED and is not running."""
+        check(load().he_server_cancel(self.h, rid))
+
     def stats(self):
-        c = np.zeros(6, np.uint64)
+        c = np.zeros(7, np.uint64)
         b = (ctypes.c_size_t * 4)()
         check(load().he_server_stats(self.h, _ptr(c, P_U64), b))
-        keys = ("submitted", "waiting", "admitted", "done", "failed", "batches")
+        keys = ("submitted", "waiting", "admitted", "done", "failed", "batches", "cancelled")
         out = {k: int(v) for k, v in zip(keys, c)}
         out.update(held_bytes=b[0], max_held_bytes=b[1], reserve_bytes=b[2], pool_high_bytes=b[3])
         return out

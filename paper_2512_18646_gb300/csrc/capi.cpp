@@ -846,6 +846,13 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
   });
 }
 
+int he_debug_fail_allocations(int n) {
+  return guard([&] {
+    REQUIRE(n >= 0, HE_E_ARG, "n must be >= 0");
+    g_fail_allocs.store(n);
+  });
+}
+
 int he_ctx_set_tensor_cores(he_ctx* ctx, int on) {
   return guard([&] {
     HANDLE(ctx);

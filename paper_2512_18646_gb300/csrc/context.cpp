@@ -17,6 +17,7 @@
 // digits in place and the single permutation is applied to its result
 // (sum_j phi_k(d_j) evk_j = phi_k(sum_j d_j phi_{k^-1}(evk_j))).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -34,8 +35,15 @@ void cuda_check(cudaError_t e, const char* what) {
   throw Error(7, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// armed by he_debug_fail_allocations: that many of the next allocations fail
+std::atomic<int> g_fail_allocs{0};
+
 DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), st(s) {
   if (w == 0) return;
+  if (g_fail_allocs.load() > 0 && g_fail_allocs.fetch_sub(1) > 0) {
+    words = 0;
+    throw Error(5, "device allocation of " + std::to_string(w * 8) + " bytes failed (injected)");
+  }
   void* ptr = nullptr;
   cudaError_t e = cudaMallocAsync(&ptr, w * 8, s);
   if (e != cudaSuccess) {

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -262,6 +263,7 @@ bool conv_mac_tc_fits(const Ctx& C, int c_in, int k, bool narrow);
 void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                    int c_out, int w_out, int limbs, bool narrow);
 void check_device_status(Ctx& C);
+extern std::atomic<int> g_fail_allocs;
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                 int c_out, int w_out, int limbs);
 // conv MAC with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a} tensor(W[o][c][a][b], R[c][s j' + b][a])

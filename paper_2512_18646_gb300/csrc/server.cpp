@@ -17,6 +17,7 @@
 // a third stream, so both overlap the batch running on the context stream;
 // submitting a request is host work only. One worker thread runs the batches.
 // All waits are bounded.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <map>
@@ -62,6 +63,7 @@ struct Request : SchedReq {
   DevBuf dev;
   cudaEvent_t uploaded = nullptr;
   bool issued = false;  // the upload and its event are enqueued
+  bool cancel = false;  // cancelled while its upload was being enqueued or its batch ran
   int state = HE_REQ_WAITING;
   std::shared_ptr<BatchOut> out;
 };
@@ -81,7 +83,7 @@ struct Server {
   bool stop = false, paused = false;
   u64 next_id = 1;
   std::map<u64, std::unique_ptr<Request>> reqs;
-  uint64_t n_submitted = 0, n_done = 0, n_failed = 0;
+  uint64_t n_submitted = 0, n_done = 0, n_failed = 0, n_cancelled = 0;
   size_t pool_high = 0;
   std::string error;
 
@@ -91,6 +93,7 @@ struct Server {
   void run_uploads();
   const BatchOut& claim(uint64_t req_id, std::unique_ptr<Request>& r, std::shared_ptr<BatchOut>& out);
   void release(Request& r, const std::shared_ptr<BatchOut>& out);
+  void cancel_locked(Request& r);
   ~Server();
 };
 
@@ -144,6 +147,7 @@ void Server::run_uploads() {
       error = err;
       r->state = HE_REQ_FAILED;
     }
+    if (r->cancel && r->state == HE_REQ_ADMITTED) cancel_locked(*r);
     cv.notify_all();
   }
 }
@@ -181,7 +185,7 @@ void Server::run() {
     std::vector<Request*> live;
     for (SchedReq* s : b) {
       Request* r = static_cast<Request*>(s);
-      if (r->state != HE_REQ_RUNNING) continue;
+      if (r->state != HE_REQ_RUNNING || r->cancel) continue;
       live.push_back(r);
       xs.push_back(r->dev.p);
     }
@@ -214,6 +218,15 @@ void Server::run() {
     sch->finish(b, now_ms(), err.empty() ? out->bytes : 0);
     for (SchedReq* s : b) {
       Request* r = static_cast<Request*>(s);
+      if (r->cancel) {  // cancelled before or while its batch ran: its share of the result is dropped
+        const bool was_live = r->state == HE_REQ_RUNNING && err.empty() && out->logits &&
+                              std::find(live.begin(), live.end(), r) != live.end();
+        if (was_live) out->unclaimed--;
+        r->dev.reset();
+        r->state = HE_REQ_CANCELLED;
+        n_cancelled++;
+        continue;
+      }
       if (r->state == HE_REQ_FAILED || !err.empty()) {
         r->state = HE_REQ_FAILED;
         n_failed++;
@@ -224,8 +237,56 @@ void Server::run() {
       n_done++;
     }
     if (!err.empty()) error = err;
+    if (out->logits && out->unclaimed == 0) {  // every request of the batch was cancelled
+      sch->release(out->bytes);
+      out->logits.reset();
+    }
     admit_locked();
     cv.notify_all();
+  }
+}
+
+// Cancel a request (mu held): withdrawn from the queues with its device memory and budget if no
+// batch has taken it; marked for the worker if its upload is being enqueued or its batch runs;
+// a finished request's share of its batch's result is released.
+void Server::cancel_locked(Request& r) {
+  switch (r.state) {
+    case HE_REQ_WAITING:
+    case HE_REQ_ADMITTED: {
+      if (r.state == HE_REQ_ADMITTED && !r.issued) {
+        auto it = std::find(to_upload.begin(), to_upload.end(), &r);
+        if (it == to_upload.end()) {  // the uploader is enqueueing its copy: finish there
+          r.cancel = true;
+          return;
+        }
+        to_upload.erase(it);
+      }
+      if (!sch->withdraw(&r)) {  // taken into a batch that has not started yet
+        r.cancel = true;
+        return;
+      }
+      r.dev.reset();  // after its upload, in the upload stream's order
+      r.state = HE_REQ_CANCELLED;
+      n_cancelled++;
+      admit_locked();
+      return;
+    }
+    case HE_REQ_RUNNING:
+      r.cancel = true;
+      return;
+    case HE_REQ_DONE: {
+      std::shared_ptr<BatchOut> out = std::move(r.out);
+      if (--out->unclaimed == 0) {
+        sch->release(out->bytes);
+        out->logits.reset();
+        admit_locked();
+      }
+      r.state = HE_REQ_CANCELLED;
+      n_cancelled++;
+      return;
+    }
+    default:
+      return;
   }
 }
 
@@ -264,6 +325,11 @@ const BatchOut& Server::claim(uint64_t req_id, std::unique_ptr<Request>& r, std:
     if (it->second->uploaded) cudaEventDestroy(it->second->uploaded);
     reqs.erase(it);
     throw Error(HE_E_CUDA, "request failed: " + why);
+  }
+  if (it->second->state == HE_REQ_CANCELLED) {
+    if (it->second->uploaded) cudaEventDestroy(it->second->uploaded);
+    reqs.erase(it);
+    throw Error(HE_E_STATE, "request was cancelled");
   }
   if (it->second->state != HE_REQ_DONE) throw Error(HE_E_STATE, "request not finished");
   r = std::move(it->second);
@@ -481,7 +547,7 @@ int he_server_wait(he_server* srv, uint64_t req_id, int timeout_ms, int* state) 
   }
   Request* r = it->second.get();
   s.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
-                [&] { return r->state >= HE_REQ_DONE; });
+                [&] { return r->state >= HE_REQ_DONE; });  // DONE, FAILED or CANCELLED
   *state = r->state;
   if (r->state < HE_REQ_DONE) {
     set_last_error("request not finished before the timeout");
@@ -561,6 +627,19 @@ int he_server_pause(he_server* srv, int paused) {
   return HE_OK;
 }
 
+int he_server_cancel(he_server* srv, uint64_t req_id) {
+  return server_guard([&] {
+    HANDLE(srv);
+    SREQUIRE(srv, HE_E_ARG, "null argument");
+    Server& s = *srv->s;
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.reqs.find(req_id);
+    SREQUIRE(it != s.reqs.end(), HE_E_ARG, "unknown request");
+    s.cancel_locked(*it->second);
+    s.cv.notify_all();
+  });
+}
+
 int he_server_stats(he_server* srv, uint64_t* counts, size_t* bytes) {
   if (!srv) return HE_E_ARG;
   if (!handle_live(srv)) {
@@ -576,6 +655,7 @@ int he_server_stats(he_server* srv, uint64_t* counts, size_t* bytes) {
     counts[3] = s.n_done;
     counts[4] = s.n_failed;
     counts[5] = (uint64_t)s.sch->batches();
+    counts[6] = s.n_cancelled;
   }
   if (bytes) {
     bytes[0] = s.sch->held();

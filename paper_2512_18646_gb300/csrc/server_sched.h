@@ -89,6 +89,23 @@ class Scheduler {
   // the result of a finished batch was released
   void release(size_t out_bytes) { held_ -= out_bytes; }
 
+  // withdraw a request no batch has taken: from the waiting queue (it held nothing) or from the
+  // admitted list (its bytes are released); false if it is in neither (in a batch, or finished)
+  bool withdraw(SchedReq* r) {
+    for (auto it = waiting_.begin(); it != waiting_.end(); ++it)
+      if (*it == r) {
+        waiting_.erase(it);
+        return true;
+      }
+    for (auto it = ready_.begin(); it != ready_.end(); ++it)
+      if (*it == r) {
+        ready_.erase(it);
+        held_ -= r->bytes;
+        return true;
+      }
+    return false;
+  }
+
   size_t held() const { return held_; }
   size_t max_held() const { return max_held_; }
   size_t reserve() const { return reserve_; }
