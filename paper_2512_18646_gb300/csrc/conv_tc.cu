@@ -38,8 +38,10 @@ namespace he {
 
 namespace {
 
-constexpr int kTcThreads = 128;  // four warps: warp w reads tensor-memory lanes 32 w .. 32 w + 31
-constexpr int kTcRows = 128;     // MMA M: coefficients of one tile (one per thread)
+constexpr int kTcThreads = 256;  // eight warps, two threads a tile row
+constexpr int kTcRows = 128;     // MMA M: coefficients of one tile
+constexpr int kStages = 4;       // input stages in the bulk-copy ring
+constexpr int kStageBytes = 16 * kTcRows * 8;  // one K step: 16 terms x 128 words
 
 template <int NC, int OBP>
 struct TcShape {
@@ -146,26 +148,47 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 
-// two 7-bit chunks (exact small integers) as one f16x2 word, the first in the low half
+// Two 7-bit chunks (exact small integers) as one f16x2 word, the first in the low half: the fp16
+// words 0x6400 | v are 1024 + v exactly (unit spacing in [1024, 2048)), and one f16x2 subtraction of
+// 1024 leaves v exactly, without a conversion instruction per chunk.
 __device__ __forceinline__ uint32_t chunk_pair(u64 x0, u64 x1, int sh) {
-  const __half h0 = __uint2half_rn((uint32_t)(x0 >> sh) & 127u);
-  const __half h1 = __uint2half_rn((uint32_t)(x1 >> sh) & 127u);
-  return (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+  const uint32_t a = (uint32_t)(x0 >> sh) & 127u, b = (uint32_t)(x1 >> sh) & 127u;
+  const uint32_t biased = a | (b << 16) | 0x64006400u;
+  __half2 h;
+  memcpy(&h, &biased, 4);
+  const __half2 r = __hsub2(h, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+  uint32_t out;
+  memcpy(&out, &r, 4);
+  return out;
 }
 
-// The input words of the 16 terms of K step ks at this thread's coefficient (0 for padding terms).
-__device__ __forceinline__ void load_step(u64 (&x)[16], const u64* xb, const u64* toff, int ks) {
-#pragma unroll
-  for (int v = 0; v < 16; v++) {
-    const u64 off = toff[16 * ks + v];
-    x[v] = off == ~0ull ? 0 : __ldg(xb + off);
-  }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bulk copy (untiled TMA) of `bytes` from global memory into this CTA's shared memory; the
+// barrier counts the bytes as they land. Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 // rot [c_in][w_in][k][2][limbs][N] (the hoisted rotations, term (c, b, a) of output column jp at
 // column stride jp + b, rotation a), w [c_out][c_in][k][k][limbs][2] (residue, Shoup companion),
 // out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
 // otherwise the others (9 chunks); blocks of the other class return at once.
+//
+// Roles: thread 0 issues the bulk copies of the input words (the 16 terms of a K step, 1 KB each
+// for the tile's 128 coefficients) kStages - 1 steps ahead into a ring of stages, and the MMAs;
+// every thread converts chunks: the two threads of tile row r = tid % 128 convert the first and
+// the second half of the NC chunks. In the recombination warp w reads tensor-memory lanes
+// 32 (w % 4) .. (its tile rows) for half w / 4 of the channels.
 template <int NC, int OBP, bool NARROW>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv_mac_tc_kernel(const u64* __restrict__ rot, u64* __restrict__ out, const u64* __restrict__ w, int c_in,
@@ -179,13 +202,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const Mod md = pt[i].mod;
   if ((md.q < kMac96Prime) != NARROW) return;  // uniform across the block, before any allocation
   const int kk2 = k * k, T = c_in * kk2, n_ks = (T + 15) >> 4;
-  unsigned char* A = tc_smem;                                                 // [2][NC][A_TILE]
+  unsigned char* X = tc_smem;                                                 // [kStages][16][128] words
+  unsigned char* A = X + kStages * kStageBytes;                               // [2][NC][A_TILE]
   unsigned char* B = A + 2 * NC * S::A_TILE;                                  // [n_ks][B_TILE]
   u64* toff = reinterpret_cast<u64*>(B + (size_t)n_ks * S::B_TILE);          // [16 n_ks]
   u64* csm = toff + 16 * n_ks;                                                // [NS] 2^(7 s) mod q
-  u64* bars = csm + S::NS;                                                    // [2] mbarriers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  u64* bars = csm + S::NS;                                                    // full[kStages], mma[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kStages + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), half = tid >> 7;
   // word offset of each term's input in rot, relative to output column 0 (padding terms: none)
   for (int t = tid; t < 16 * n_ks; t += kTcThreads) {
     u64 off = ~0ull;
@@ -201,8 +225,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       csm[s] = c;
       c = mulmod(c, 128, md);
     }
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
+    for (int b = 0; b < kStages + 2; b++) mbar_init(smem_u32(&bars[b]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -213,13 +236,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t lanes = (uint32_t)(warp * 32) << 16;  // this warp's lane quarter of tensor memory
-  const size_t io = (size_t)comp * LN + (size_t)i * N + (size_t)blockIdx.x * kTcRows + tid;
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // this warp's lane quarter of tensor memory
+  const size_t tile = (size_t)comp * LN + (size_t)i * N + (size_t)blockIdx.x * kTcRows;  // word of row 0
   constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
-  // row `tid` of an A tile: core matrix (tid / 8, K half) at (tid / 8) 256 + half 128, row tid % 8 at 16 bytes
-  const int arow = (tid >> 3) * 256 + (tid & 7) * 16;
-  uint32_t uses[2] = {0, 0};
+  constexpr int C0 = (NC + 1) / 2;  // chunks of the first half of the threads
+  const int c_lo = half ? C0 : 0, c_hi = half ? NC : C0;
+  // row `row` of an A tile: core matrix (row / 8, K half) at (row / 8) 256 + half 128, row % 8 at 16 bytes
+  const int arow = (row >> 3) * 256 + (row & 7) * 16;
+  const int n_jp = (w_out - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
+  uint32_t mma_uses[2] = {0, 0};
+  long gs0 = 0;  // steps of earlier channel groups (the stage ring and its barriers run on)
   bool ok = true;
+  // thread 0: the bulk copies of step g of this channel group into its stage
+  auto issue = [&](int g) {
+    const int jp = (int)blockIdx.z + (g / n_ks) * (int)gridDim.z, ks = g % n_ks;
+    const long gs = gs0 + g;
+    const int st = (int)(gs % kStages);
+    const int nreal = min(16, T - 16 * ks);
+    const uint32_t bar = smem_u32(&bars[st]);
+    mbar_expect_tx(bar, (uint32_t)nreal * kTcRows * 8);
+    const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + tile;
+    const uint32_t dst = smem_u32(X + (size_t)st * kStageBytes);
+    for (int v = 0; v < nreal; v++) bulk_g2s(dst + v * kTcRows * 8, xb + toff[16 * ks + v], kTcRows * 8, bar);
+  };
   for (int o0 = 0; o0 < c_out; o0 += OBP) {
     // weight tiles of this channel group: row r = j OBP + o holds chunk j of W[o0 + o][t], t = 16 ks + kk
     for (int e = tid; e < n_ks * S::NMMA * 16; e += kTcThreads) {
@@ -236,92 +275,105 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     (kk & 7);
       *dst = __uint2half_rn(v);
     }
-    for (int jp = blockIdx.z; jp < w_out; jp += gridDim.z) {
+    const int G = n_jp * n_ks;
+    if (tid == 0)
+      for (int g = 0; g < kStages - 1 && g < G; g++) issue(g);
+    for (int g = 0; g < G; g++) {
+      const int ks = g % n_ks;
+      const long gs = gs0 + g;
+      if (ks == 0 && warp < 4) {  // this task's accumulators start at zero
 #pragma unroll
-      for (int c = 0; c < S::COLS; c += 16) tc_zero16(tmem + lanes + c);
-      tc_wait_st();
-      const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + io;
-      u64 xc[16], xn[16];
-      load_step(xc, xb, toff, 0);
-      for (int ks = 0; ks < n_ks; ks++) {
-        if (ks + 1 < n_ks) load_step(xn, xb, toff, ks + 1);
-        const int b = ks & 1;
-        if (uses[b] > 0 && ok) ok = mbar_wait(smem_u32(&bars[b]), (uses[b] - 1) & 1);  // buffer b is free
+        for (int c = 0; c < S::COLS; c += 16) tc_zero16(tmem + lanes + c);
+        tc_wait_st();
+      }
+      // this step's input words have landed
+      if (ok) ok = mbar_wait(smem_u32(&bars[gs % kStages]), (uint32_t)((gs / kStages) & 1));
+      // A buffer b is free once the MMAs of two steps ago have finished
+      const int b = (int)(gs & 1);
+      if (mma_uses[b] > 0 && ok) ok = mbar_wait(smem_u32(&bars[kStages + b]), (mma_uses[b] - 1) & 1);
+      {
+        const u64* xs = reinterpret_cast<const u64*>(X + (size_t)(gs % kStages) * kStageBytes) + row;
+        const int nreal = min(16, T - 16 * ks);
+        u64 x[16];
+#pragma unroll
+        for (int v = 0; v < 16; v++) x[v] = v < nreal ? xs[v * kTcRows] : 0;
         unsigned char* Ab = A + (size_t)b * NC * S::A_TILE + arow;
 #pragma unroll
         for (int c = 0; c < NC; c++) {
+          if (c < c_lo || c >= c_hi) continue;
           uint4 lo, hi;
-          lo.x = chunk_pair(xc[0], xc[1], 7 * c);
-          lo.y = chunk_pair(xc[2], xc[3], 7 * c);
-          lo.z = chunk_pair(xc[4], xc[5], 7 * c);
-          lo.w = chunk_pair(xc[6], xc[7], 7 * c);
-          hi.x = chunk_pair(xc[8], xc[9], 7 * c);
-          hi.y = chunk_pair(xc[10], xc[11], 7 * c);
-          hi.z = chunk_pair(xc[12], xc[13], 7 * c);
-          hi.w = chunk_pair(xc[14], xc[15], 7 * c);
+          lo.x = chunk_pair(x[0], x[1], 7 * c);
+          lo.y = chunk_pair(x[2], x[3], 7 * c);
+          lo.z = chunk_pair(x[4], x[5], 7 * c);
+          lo.w = chunk_pair(x[6], x[7], 7 * c);
+          hi.x = chunk_pair(x[8], x[9], 7 * c);
+          hi.y = chunk_pair(x[10], x[11], 7 * c);
+          hi.z = chunk_pair(x[12], x[13], 7 * c);
+          hi.w = chunk_pair(x[14], x[15], 7 * c);
           *reinterpret_cast<uint4*>(Ab + c * S::A_TILE) = lo;
           *reinterpret_cast<uint4*>(Ab + c * S::A_TILE + 128) = hi;
         }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-          tc_fence_after();
-          const uint64_t bdesc = tc_desc(smem_u32(B + (size_t)ks * S::B_TILE));
-#pragma unroll
-          for (int c = 0; c < NC; c++)
-            tc_mma(tmem + c * OBP, tc_desc(smem_u32(A + ((size_t)b * NC + c) * S::A_TILE)), bdesc, idesc);
-          tc_commit(smem_u32(&bars[b]));
-        }
-        uses[b]++;
-#pragma unroll
-        for (int v = 0; v < 16; v++) xc[v] = xn[v];
       }
-      // the last commit covers every MMA of the task
-      {
-        const int b = (n_ks - 1) & 1;
-        if (ok) ok = mbar_wait(smem_u32(&bars[b]), (uses[b] - 1) & 1);
-      }
-      tc_fence_after();
-      // out[o] = sum_s D_s[o] 2^(7 s) mod q
-      u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + io;
-      const size_t ostep = (size_t)w_out * 2 * LN;
-      if constexpr (NARROW) {
-        Acc96 acc[OBP];
-#pragma unroll
-        for (int o = 0; o < OBP; o++) acc[o] = Acc96{0, 0, 0};
-        for (int s = 0; s < S::NS; s++) {
-          uint32_t d[OBP];
-          tc_ld(tmem + lanes + s * OBP, d);
-          tc_wait_ld();
-          const u64 cs = csm[s];
-#pragma unroll
-          for (int o = 0; o < OBP; o++) mac96(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
-        }
-#pragma unroll
-        for (int o = 0; o < OBP; o++)
-          if (o0 + o < c_out) dst[o * ostep] = reduce96(acc[o], md);
-      } else {
-        Acc128 acc[OBP];
-#pragma unroll
-        for (int o = 0; o < OBP; o++) acc[o] = Acc128{0, 0};
-        for (int s = 0; s < S::NS; s++) {
-          uint32_t d[OBP];
-          tc_ld(tmem + lanes + s * OBP, d);
-          tc_wait_ld();
-          const u64 cs = csm[s];
-#pragma unroll
-          for (int o = 0; o < OBP; o++) mac128(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
-        }
-#pragma unroll
-        for (int o = 0; o < OBP; o++)
-          if (o0 + o < c_out) dst[o * ostep] = reduce128(acc[o].hi, acc[o].lo, md);
-      }
-      // every warp has read its accumulators before the next task zeroes them (and before the
-      // next channel group rewrites the weight tiles)
+      fence_async_smem();
       tc_fence_before();
       __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint64_t bdesc = tc_desc(smem_u32(B + (size_t)ks * S::B_TILE));
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+          tc_mma(tmem + c * OBP, tc_desc(smem_u32(A + ((size_t)b * NC + c) * S::A_TILE)), bdesc, idesc);
+        tc_commit(smem_u32(&bars[kStages + b]));
+        // the stage of step g - 1 has been read by every thread: refill it with step g + kStages - 1
+        if (g + kStages - 1 < G) issue(g + kStages - 1);
+      }
+      mma_uses[b]++;
+      if (ks == n_ks - 1) {
+        // the last commit covers every MMA of the task
+        if (ok) ok = mbar_wait(smem_u32(&bars[kStages + b]), (mma_uses[b] - 1) & 1);
+        tc_fence_after();
+        const int jp = (int)blockIdx.z + (g / n_ks) * (int)gridDim.z;
+        constexpr int OH = OBP / 2;  // channels of this thread's half
+        const int oh = half * OH;
+        u64* dst = out + ((size_t)(o0 + oh) * w_out + jp) * 2 * LN + tile + row;
+        const size_t ostep = (size_t)w_out * 2 * LN;
+        if constexpr (NARROW) {
+          Acc96 acc[OH];
+#pragma unroll
+          for (int o = 0; o < OH; o++) acc[o] = Acc96{0, 0, 0};
+          for (int s = 0; s < S::NS; s++) {
+            uint32_t d[OH];
+            tc_ld(tmem + lanes + s * OBP + oh, d);
+            tc_wait_ld();
+            const u64 cs = csm[s];
+#pragma unroll
+            for (int o = 0; o < OH; o++) mac96(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+          }
+#pragma unroll
+          for (int o = 0; o < OH; o++)
+            if (o0 + oh + o < c_out) dst[o * ostep] = reduce96(acc[o], md);
+        } else {
+          Acc128 acc[OH];
+#pragma unroll
+          for (int o = 0; o < OH; o++) acc[o] = Acc128{0, 0};
+          for (int s = 0; s < S::NS; s++) {
+            uint32_t d[OH];
+            tc_ld(tmem + lanes + s * OBP + oh, d);
+            tc_wait_ld();
+            const u64 cs = csm[s];
+#pragma unroll
+            for (int o = 0; o < OH; o++) mac128(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+          }
+#pragma unroll
+          for (int o = 0; o < OH; o++)
+            if (o0 + oh + o < c_out) dst[o * ostep] = reduce128(acc[o].hi, acc[o].lo, md);
+        }
+        // every warp has read its accumulators before the next task zeroes them
+        tc_fence_before();
+        __syncthreads();
+      }
     }
+    gs0 += G;
   }
   tc_fence_after();
   if (warp == 0) tc_dealloc(tmem, S::TMEM);
@@ -332,11 +384,8 @@ template <int NC, int OBP>
 size_t tc_smem_bytes(int T) {
   using S = TcShape<NC, OBP>;
   const int n_ks = (T + 15) / 16;
-  const size_t need = (size_t)2 * NC * S::A_TILE + (size_t)n_ks * S::B_TILE + 16 * n_ks * 8 + S::NS * 8 + 16 + 8;
-  // at most 512 / TMEM CTAs share an SM, so that every CTA's tensor-memory allocation is granted at
-  // once: request more than the SM's shared memory divided by one more CTA than that
-  const size_t floor_b = (size_t)(228 * 1024) / (512 / S::TMEM + 1) + 1024;
-  return need > floor_b ? need : floor_b;
+  return (size_t)kStages * kStageBytes + (size_t)2 * NC * S::A_TILE + (size_t)n_ks * S::B_TILE + 16 * n_ks * 8 +
+         S::NS * 8 + (kStages + 2) * 8 + 8;
 }
 
 template <int NC, int OBP, bool NARROW>

@@ -237,3 +237,121 @@ def test_server_admission_by_budget(served):
         assert e.value.code == HE_E_OOM
     finally:
         tiny.close()
+
+
+def test_server_wait_times_out_while_nothing_runs(served):
+    """A request whose batch cannot start (the server is held, as a stalled producer would leave it)
+    makes he_server_wait return HE_E_TIMEOUT after its limit; the request is unharmed and finishes
+    once batches resume."""
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_REQ_ADMITTED, HE_REQ_DONE
+    g, w = served
+    img = synthetic.images(1, 32, 32, seed=97)[0]
+    srv = api.Server(g, {32: w[32]}, hbm_budget_bytes=16 << 30, max_blocks=4, start_paused=True)
+    try:
+        rid = srv.submit(_request(g, img, 32, 7500), 32)
+        t0 = time.monotonic()
+        assert not srv.wait(rid, 200)  # HE_E_TIMEOUT
+        assert time.monotonic() - t0 >= 0.19
+        assert srv.poll(rid) == HE_REQ_ADMITTED
+        srv.pause(False)
+        assert srv.wait(rid, 120_000) and srv.poll(rid) == HE_REQ_DONE
+        z, blk, _ = srv.take(rid)
+        assert np.abs(_logits(g, z, blk, 32) - fp64_ref.cnn(img[None], w[32])[0]).max() < TOL
+    finally:
+        srv.close()
+
+
+def test_server_cancel_releases_budget_in_every_state(served):
+    """he_server_cancel: a waiting request leaves the queue, an admitted one gives back its device
+    budget at once (the next waiting request is admitted), a running one's share is dropped when its
+    batch ends, a finished one's result share is released; a cancelled request reads
+    HE_REQ_CANCELLED and he_server_take refuses it (HE_E_STATE) and forgets it. The other requests'
+    results are unchanged."""
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import (HE_E_ARG, HE_E_STATE, HE_REQ_CANCELLED, HE_REQ_RUNNING, HE_REQ_WAITING,
+                                             HeError)
+    g, w = served
+    req_bytes = 32 * 2 * g.L1 * g.N * 8
+    probe = api.Server(g, {32: w[32]}, hbm_budget_bytes=16 << 30, max_blocks=8)
+    reserve = probe.stats()["reserve_bytes"]
+    probe.close()
+    imgs = synthetic.images(5, 32, 32, seed=98)
+    reqs = [_request(g, imgs[k], 32, 8000 + 100 * k) for k in range(5)]
+    # room for two requests beside the reserve
+    srv = api.Server(g, {32: w[32]}, hbm_budget_bytes=reserve + int(2.5 * req_bytes), max_blocks=8,
+                     start_paused=True)
+    try:
+        ids = [srv.submit(reqs[k], 32) for k in range(4)]
+        st = srv.stats()
+        assert st["admitted"] == 2 and st["waiting"] == 2
+        srv.cancel(ids[3])  # waiting
+        assert srv.poll(ids[3]) == HE_REQ_CANCELLED
+        st = srv.stats()
+        assert st["waiting"] == 1 and st["cancelled"] == 1 and st["held_bytes"] == 2 * req_bytes
+        srv.cancel(ids[1])  # admitted: its budget goes to the waiting request 2
+        st = srv.stats()
+        assert srv.poll(ids[1]) == HE_REQ_CANCELLED
+        assert st["admitted"] == 2 and st["waiting"] == 0 and st["held_bytes"] == 2 * req_bytes
+        with pytest.raises(HeError) as e:
+            srv.take(ids[3])
+        assert e.value.code == HE_E_STATE
+        with pytest.raises(HeError) as e:
+            srv.poll(ids[3])  # forgotten
+        assert e.value.code == HE_E_ARG
+        srv.pause(False)
+        for k in (0, 2):
+            assert srv.wait(ids[k], 120_000)
+        # a finished request cancelled: its share of the batch result is released
+        srv.cancel(ids[0])
+        z, blk, _ = srv.take(ids[2])
+        assert np.abs(_logits(g, z, blk, 32) - fp64_ref.cnn(imgs[2][None], w[32])[0]).max() < TOL
+        assert srv.stats()["held_bytes"] == 0
+        # a running request cancelled: the batch ends, the share is dropped, nothing stays held
+        rid = srv.submit(reqs[4], 32)
+        deadline = time.monotonic() + 120
+        while srv.poll(rid) < HE_REQ_RUNNING:
+            assert time.monotonic() < deadline
+            time.sleep(0.0005)
+        srv.cancel(rid)
+        assert srv.wait(rid, 120_000) and srv.poll(rid) == HE_REQ_CANCELLED
+        st = srv.stats()
+        assert st["held_bytes"] == 0 and st["cancelled"] == 4
+        # the server keeps serving
+        rid = srv.submit(reqs[4], 32)
+        assert srv.wait(rid, 120_000)
+        z, blk, _ = srv.take(rid)
+        assert np.abs(_logits(g, z, blk, 32) - fp64_ref.cnn(imgs[4][None], w[32])[0]).max() < TOL
+        assert srv.poll(ids[1]) == HE_REQ_CANCELLED and HE_REQ_WAITING == 0
+    finally:
+        srv.close()
+
+
+def test_server_rolls_back_a_request_whose_allocation_fails(served):
+    """An admitted request whose device allocation fails (injected on the host: the next allocation
+    reports out-of-memory) ends FAILED; he_server_take reports the error and forgets it, its budget
+    is released, and the next request is served normally."""
+    from paper_2512_18646_gb300 import api, load
+    from paper_2512_18646_gb300._lib import HE_E_CUDA, HE_REQ_FAILED, HeError
+    g, w = served
+    imgs = synthetic.images(2, 32, 32, seed=99)
+    srv = api.Server(g, {32: w[32]}, hbm_budget_bytes=16 << 30, max_blocks=4)
+    try:
+        words = _request(g, imgs[0], 32, 9000)  # (encryption allocates: before arming)
+        g.synchronize()
+        assert load().he_debug_fail_allocations(1) == 0
+        rid = srv.submit(words, 32)
+        assert srv.wait(rid, 120_000) and srv.poll(rid) == HE_REQ_FAILED
+        assert load().he_debug_fail_allocations(0) == 0
+        with pytest.raises(HeError) as e:
+            srv.take(rid)
+        assert e.value.code == HE_E_CUDA and "injected" in str(e.value)
+        st = srv.stats()
+        assert st["failed"] == 1 and st["held_bytes"] == 0
+        rid = srv.submit(_request(g, imgs[1], 32, 9100), 32)
+        assert srv.wait(rid, 120_000)
+        z, blk, _ = srv.take(rid)
+        assert np.abs(_logits(g, z, blk, 32) - fp64_ref.cnn(imgs[1][None], w[32])[0]).max() < TOL
+    finally:
+        load().he_debug_fail_allocations(0)
+        srv.close()
