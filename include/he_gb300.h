@@ -123,6 +123,25 @@ int he_ctx_set_tensor_cores(he_ctx* ctx, int on);
  */
 int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps);
 
+/*
+ * he_keys_export: a checkpoint of the context's keys in n_words 64-bit words
+ * (host memory, caller-owned): a header with the ring degree, the prime chain
+ * and the digit size, then the secret and public keys and every switching key
+ * (relinearisation and Galois keys), coefficient words in the NTT domain.
+ * *needed (may be NULL) gets the size; words == NULL only asks for it.
+ * A client keeps its secret: strip it before handing keys to a server. The
+ * paper has no counterpart (it assumes the keys exist, Sec. II-A).
+ * Errors: HE_E_STATE (no keys), HE_E_ARG (output too small).
+ *
+ * he_keys_import: load such a checkpoint into a context made with the same
+ * parameters (ring degree, primes, special primes, digits), replacing its
+ * keys; ciphertexts of the exporting context then decrypt and rotate here.
+ * The words are checked (header, primes, sizes, residues below their
+ * primes). Errors: HE_E_ARG (other parameters, malformed or truncated).
+ */
+int he_keys_export(he_ctx* ctx, uint64_t* words, size_t n_words, size_t* needed);
+int he_keys_import(he_ctx* ctx, const uint64_t* words, size_t n_words);
+
 /* ---- encryption into the paper's layouts (Enc_pk, Sec. II-A) ---- */
 
 /*

@@ -61,6 +61,8 @@ SIGNATURES = {
     "he_ctx_set_work_budget": (I, [V, SZ]),
     "he_ctx_set_tensor_cores": (I, [V, I]),
     "he_keygen": (I, [V, P_I32, I]),
+    "he_keys_export": (I, [V, P_U64, SZ, ctypes.POINTER(SZ)]),
+    "he_keys_import": (I, [V, P_U64, SZ]),
     "he_encrypt_image": (I, [V, P_D, I, I, I, I, U64, PV]),
     "he_encrypt_matrix_a": (I, [V, P_D, I, I, U64, PV]),
     "he_encrypt_matrix_b": (I, [V, P_D, I, I, U64, PV]),

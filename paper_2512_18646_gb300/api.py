@@ -198,6 +198,18 @@ class Context:
         st = (ctypes.c_int32 * max(1, len(steps)))(*steps)
         check(load().he_keygen(self.h, st, len(steps)))
 
+    def export_keys(self) -> np.ndarray:
+        """The key checkpoint (include/he_gb300.h he_keys_export) as uint64 words."""
+        n = ctypes.c_size_t()
+        check(load().he_keys_export(self.h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.uint64)
+        check(load().he_keys_export(self.h, _ptr(out, P_U64), out.size, None))
+        return out
+
+    def import_keys(self, words):
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        check(load().he_keys_import(self.h, _ptr(words, P_U64), words.size))
+
     def encrypt_image(self, px, block_stride: int, ct_id_base: int = 0) -> CtSet:
         px = _f64(px)
         b, h, w = px.shape

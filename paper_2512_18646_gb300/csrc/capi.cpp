@@ -151,6 +151,24 @@ int he_keygen(he_ctx* ctx, const int32_t* rot_steps, int n_steps) {
   });
 }
 
+int he_keys_export(he_ctx* ctx, uint64_t* words, size_t n_words, size_t* needed) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx && (words || needed), HE_E_ARG, "null argument");
+    const size_t need = keys_export(ctx->c, nullptr, 0);
+    if (needed) *needed = need;
+    if (words) keys_export(ctx->c, words, n_words);
+  });
+}
+
+int he_keys_import(he_ctx* ctx, const uint64_t* words, size_t n_words) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx && words, HE_E_ARG, "null argument");
+    keys_import(ctx->c, words, n_words);
+  });
+}
+
 int he_encrypt_image(he_ctx* ctx, const double* px, int batch, int h, int w, int block_stride, uint64_t ct_id_base,
                      he_ctset** out) {
   return guard([&] {

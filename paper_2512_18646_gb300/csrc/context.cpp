@@ -466,6 +466,87 @@ DevBuf make_ksk(Ctx& C, u64 key_id, const u64* d_sprime) {
 
 }  // namespace
 
+// Checkpoint of the keys: header [magic, version, log_n, n_q, K, alpha, primes...], the secret
+// [L1+K][N] and public key [2][L1][N] (NTT domain), then per switching key its Galois element
+// (1: relinearisation), its word count and its words.
+static const u64 kKeyMagic = 0x4845474233303031ull;  // "HEGB3001"
+
+size_t keys_export(Ctx& C, u64* out, size_t cap) {
+  if (!C.has_keys) throw Error(9, "no keys to export (call he_keygen)");
+  const size_t NPN = (size_t)C.np() * C.N, PK = (size_t)2 * C.L1 * C.N;
+  size_t need = 6 + C.np() + NPN + PK + 1;
+  for (auto& kv : C.ksk) need += 2 + kv.second.words;
+  if (!out) return need;
+  if (cap < need) throw Error(1, "output too small for the keys (" + std::to_string(need) + " words)");
+  size_t o = 0;
+  out[o++] = kKeyMagic;
+  out[o++] = 1;
+  out[o++] = (u64)C.log_n;
+  out[o++] = (u64)C.L1;
+  out[o++] = (u64)C.K;
+  out[o++] = (u64)C.alpha;
+  for (int i = 0; i < C.np(); i++) out[o++] = C.q[i];
+  HE_CUDA(cudaMemcpyAsync(out + o, C.d_s.p, NPN * 8, cudaMemcpyDeviceToHost, C.stream));
+  o += NPN;
+  HE_CUDA(cudaMemcpyAsync(out + o, C.d_pk.p, PK * 8, cudaMemcpyDeviceToHost, C.stream));
+  o += PK;
+  out[o++] = (u64)C.ksk.size();
+  for (auto& kv : C.ksk) {
+    out[o++] = kv.first;
+    out[o++] = (u64)kv.second.words;
+    HE_CUDA(cudaMemcpyAsync(out + o, kv.second.p, kv.second.words * 8, cudaMemcpyDeviceToHost, C.stream));
+    o += kv.second.words;
+  }
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  return need;
+}
+
+void keys_import(Ctx& C, const u64* in, size_t n) {
+  auto need = [&](size_t at, size_t words) {
+    if (at + words > n) throw Error(1, "truncated key checkpoint");
+  };
+  need(0, 6);
+  if (in[0] != kKeyMagic || in[1] != 1) throw Error(1, "not a key checkpoint of this library");
+  if (in[2] != (u64)C.log_n || in[3] != (u64)C.L1 || in[4] != (u64)C.K || in[5] != (u64)C.alpha)
+    throw Error(1, "key checkpoint of other parameters (ring degree, primes or digits)");
+  size_t o = 6;
+  need(o, C.np());
+  for (int i = 0; i < C.np(); i++)
+    if (in[o + i] != C.q[i]) throw Error(1, "key checkpoint of another prime chain");
+  o += C.np();
+  const size_t NPN = (size_t)C.np() * C.N, PK = (size_t)2 * C.L1 * C.N;
+  const size_t key_words = (size_t)C.beta_at(C.L1) * 2 * C.np() * C.N;
+  need(o, NPN + PK + 1);
+  // residues in range: every word below its prime
+  for (size_t r = 0; r < (size_t)C.np(); r++)
+    for (size_t j = 0; j < C.N; j++)
+      if (in[o + r * C.N + j] >= C.q[r]) throw Error(1, "key checkpoint holds a residue out of range");
+  DevBuf s(NPN, C.stream), pk(PK, C.stream);
+  HE_CUDA(cudaMemcpyAsync(s.p, in + o, NPN * 8, cudaMemcpyHostToDevice, C.stream));
+  o += NPN;
+  HE_CUDA(cudaMemcpyAsync(pk.p, in + o, PK * 8, cudaMemcpyHostToDevice, C.stream));
+  o += PK;
+  const u64 nk = in[o++];
+  std::map<u64, DevBuf> keys;
+  for (u64 t = 0; t < nk; t++) {
+    need(o, 2);
+    const u64 k = in[o], words = in[o + 1];
+    o += 2;
+    if (words != key_words || (k != 1 && (k % 2 == 0 || k >= 2 * (u64)C.N)))
+      throw Error(1, "key checkpoint holds a malformed switching key");
+    need(o, words);
+    DevBuf d(words, C.stream);
+    HE_CUDA(cudaMemcpyAsync(d.p, in + o, words * 8, cudaMemcpyHostToDevice, C.stream));
+    o += words;
+    keys[k] = std::move(d);
+  }
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  C.d_s = std::move(s);
+  C.d_pk = std::move(pk);
+  C.ksk = std::move(keys);
+  C.has_keys = true;
+}
+
 void keygen(Ctx& C, const std::vector<long>& steps) {
   const int np = C.np();
   const size_t NPN = (size_t)np * C.N;

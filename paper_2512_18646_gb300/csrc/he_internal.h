@@ -310,6 +310,9 @@ void k_copy_limbs(const Ctx& C, const u64* src, size_t src_gs, u64* dst, size_t 
 void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, int special_bits, int alpha,
               double log_scale, double sigma, u64 seed, cudaStream_t st);
 void keygen(Ctx& C, const std::vector<long>& steps);
+// key checkpoint (he_keys_export / he_keys_import); out == nullptr: the size in words
+size_t keys_export(Ctx& C, u64* out, size_t cap);
+void keys_import(Ctx& C, const u64* in, size_t n);
 std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale);
 std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs, double scale, u64 id_base);
 void decrypt_slots(Ctx& C, const CtSet& s, double* out);

@@ -1022,3 +1022,42 @@ def test_plaintext_add_and_drop_levels(lib):
     with pytest.raises(HeError) as e:
         g.add_plain_coeffs(y, mv[:2])  # two plaintexts for three ciphertexts
     assert e.value.code == HE_E_ARG
+
+
+def test_key_checkpoint_moves_keys_between_contexts(lib):
+    """he_keys_export / he_keys_import: a context with the same parameters but another seed takes the
+    first one's keys from the checkpoint, then decrypts the first one's ciphertexts and rotates and
+    multiplies them to the same words. Other parameters, a truncated checkpoint and a residue out of
+    range are refused (HE_E_ARG), and the refused context keeps its own keys."""
+    from paper_2512_18646_gb300 import api
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_STATE, HeError
+    params = (10, (60, 45, 45, 45), 2, 60, 2, 45.0)
+    a = api.Context(*params, seed=61)
+    with pytest.raises(HeError) as e:
+        a.export_keys()
+    assert e.value.code == HE_E_STATE
+    a.keygen([1, 5])
+    words = a.export_keys()
+    b = api.Context(*params, seed=62)
+    b.import_keys(words)
+    assert np.array_equal(b.export_keys(), words)
+    A = np.random.default_rng(61).uniform(-1, 1, (7, 3))
+    xa = a.encrypt_matrix_a(A, 0)
+    xb = b.import_coeffs(xa.export(), xa.scale)
+    assert np.abs(b.decrypt_slots(xb)[:, :7] - A.T).max() < 1e-6
+    assert np.array_equal(b.rotate(xb, [1, 5]).export(), a.rotate(xa, [1, 5]).export())
+    assert np.array_equal(b.relinearize(b.mul(xb, xb)).export(), a.relinearize(a.mul(xa, xa)).export())
+    # refusals
+    c = api.Context(10, (60, 45, 45, 45), 2, 60, 1, 45.0, seed=63)
+    c.keygen([])
+    own = c.export_keys()
+    for bad in (words, words[:-5]):
+        with pytest.raises(HeError) as e:
+            c.import_keys(bad)
+        assert e.value.code == HE_E_ARG
+    bad = words.copy()
+    bad[6 + len(a.primes) + 3] = np.uint64(1 << 63)  # a secret-key residue above its prime
+    with pytest.raises(HeError) as e:
+        b.import_keys(bad)
+    assert e.value.code == HE_E_ARG
+    assert np.array_equal(c.export_keys(), own)
