@@ -1129,6 +1129,58 @@ def oracle_serve_baseline(sides):
 
 
 # ---------------------------------------------------------------------------
+# small cases of the hot kernels, sized for profiler captures (--workload case --case NAME)
+# ---------------------------------------------------------------------------
+# Each runs one layer of the CNN at its parameters (N = 2^16, Q = 60 + 12 x 45, P = 2 x 60,
+# digits of two primes) on a narrow slab, so that every launch has the shape of the full workload's
+# launches per limb while the device holds a few GB and each launch's data exceeds L2; the body runs
+# inside the NVTX range "case" (ncu --nvtx --nvtx-include "case/"):
+#   conv1   16 image columns (256 images): hoisted rotations by 1..4, the 8-channel 5x5 stride-2
+#           multiply-accumulate, rescale;
+#   square  x^2 of 64 ciphertexts at the top level (tensor, rescale, relinearisation);
+#   conv2   the second convolution (16 x 3 x 3, stride 2, 8 channels of 16 columns, row gap 2) on
+#           128 ciphertexts at 11 limbs;
+#   fc      the dense layer on 16 x 4 input ciphertexts at 9 limbs, 10 outputs.
+CASES = ("conv1", "conv2", "square", "fc")
+
+
+def run_case(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_18646_gb300 import api
+    pre = synthetic.CNN_N16
+    g = api.Context.from_preset(pre, seed=5)
+    g.keygen([1, 2, 3, 4])
+    w = synthetic.cnn_weights(128, seed=302)
+    if args.case == "conv2":
+        rng = np.random.default_rng(4)
+        x = g.encrypt_coeffs(rng.integers(-(1 << 40), 1 << 40, size=(8 * 16, g.N), dtype=np.int64), 11, g.scale)
+    elif args.case == "fc":
+        g.keygen([4, 8, 16, 32, 64])
+        rng = np.random.default_rng(3)
+        x = g.encrypt_coeffs(rng.integers(-(1 << 40), 1 << 40, size=(64, g.N), dtype=np.int64), 9, g.scale)
+        pts = g.fc_prepare(rng.normal(0, 0.05, (10, 16 * 30 * 4)), 16, 30, 4, 4, 128, 256, 9)
+    else:
+        x = g.encrypt_image(synthetic.images(256, 128, 16 if args.case == "conv1" else 64, seed=301), 128)
+    g.synchronize()
+    torch.cuda.nvtx.range_push("case")
+    for _ in range(max(1, args.steps)):
+        if args.case == "conv1":
+            y = g.conv2d(x, 1, 1, w.conv1_w, w.conv1_b, 2)
+        elif args.case == "conv2":
+            y = g.conv2d(x, 8, 2, w.conv2_w, w.conv2_b, 2)
+        elif args.case == "fc":
+            y = g.fc_apply(x, pts, None)
+        else:
+            y = g.relinearize(g.mul(x, x))
+        del y
+    g.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"case": args.case, "repeats": max(1, args.steps), "done": True}))
+
+
+# ---------------------------------------------------------------------------
 # the other configurations, reported beside the CNN in the default run
 # ---------------------------------------------------------------------------
 # (key, workload, extra arguments): the small matmul (4096 products, plain vs batched vs CUDA graph),
@@ -1209,8 +1261,9 @@ def main():
                     help="cnn workload: prime chain and key-switching digits")
     ap.add_argument("--no-extra", action="store_true",
                     help="cnn workload: skip the other configurations (matmul, conv layer, batched matmul, serving)")
-    ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "table1", "serve"],
-                    default="cnn")
+    ap.add_argument("--workload", choices=["cnn", "layer", "matmul", "matmul_small", "layer28", "table1", "serve",
+                                           "case"], default="cnn")
+    ap.add_argument("--case", choices=CASES, default="conv2", help="case workload: the kernel case to run")
     ap.add_argument("--count", type=int, default=0, help="matmul workload: first COUNT products only")
     ap.add_argument("--requests", type=int, default=600, help="serve workload: measured requests")
     ap.add_argument("--serve-warmup", type=int, default=20, help="serve workload: warm-up requests")
@@ -1229,6 +1282,10 @@ def main():
     cfg = {"workload": wl, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+
+    if args.workload == "case":
+        run_case(args)
+        return
 
     if args.workload == "layer" and args.impl == "gpu":
         res = run_layer(args, rank, world, local_rank)
