@@ -17,19 +17,15 @@
 // one Barrett reduction). The result is the exact residue, the same word the
 // CUDA-core kernels compute.
 //
-// One CTA (four warps) owns a tile of 128 coefficients of one (component,
-// limb) and runs every output column j' of the layer over it. Per 16 terms
-// (one K step) each thread loads its coefficient's 16 input words (the next
-// step's are loaded while this step's are converted), writes their chunks as
-// row `thread` of NC fp16 tiles [128 x 16] in shared memory (K-major, 8 x 16-
-// byte core matrices, no swizzle), and one thread issues NC MMAs of
-// M = 128, N = NC * OBP, K = 16: MMA i multiplies chunk tile i by the weight
-// tile B = [chunk j][channel o] and accumulates at tensor-memory column
-// i * OBP, so that column s * OBP + o collects D_s[.][o]. The A tiles are
-// double-buffered; an mbarrier per buffer (tcgen05.commit) says when the MMAs
-// that read it have finished. Every wait is bounded: past the limit the CTA
-// records the failure in the context's status word (read by the host at its
-// next synchronisation), frees its tensor memory and returns.
+// One CTA owns a tile of 128 coefficients of one (component, limb) and runs every output column
+// j' of the layer over it, 16 terms (one K step) at a time: the input words of a step arrive by
+// bulk copies (untiled TMA) in a ring of stages; converting warps write their 7-bit chunks as NC
+// fp16 tiles [128 x 16] (K-major, 8 x 16-byte core matrices, no swizzle); one thread issues NC
+// MMAs of M = 128, N = NC * OBP, K = 16: MMA i multiplies chunk tile i by the weight tile
+// B = [chunk j][channel o] and accumulates at tensor-memory column i * OBP, so that column
+// s * OBP + o collects D_s[.][o]. The roles hand work over through mbarriers (see the kernel).
+// Every wait is bounded: past the limit the CTA records the failure in the context's status word
+// (read by the host at its next synchronisation), frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include "he_internal.h"
@@ -38,20 +34,22 @@ namespace he {
 
 namespace {
 
-constexpr int kTcThreads = 256;  // eight warps, two threads a tile row
-constexpr int kTcRows = 128;     // MMA M: coefficients of one tile
-constexpr int kStages = 4;       // input stages in the bulk-copy ring
-constexpr int kStageBytes = 16 * kTcRows * 8;  // one K step: 16 terms x 128 words
+constexpr int kTcConvWarps = 8;                      // warps converting chunks and recombining
+constexpr int kTcThreads = 32 * (2 + kTcConvWarps);  // + warp 0 (MMA issue), warp 1 (bulk copies)
+constexpr int kTcRows = 128;                         // MMA M: coefficients of one tile
+constexpr int kStages = 4;                           // input stages in the bulk-copy ring
+constexpr int kABufs = 3;                            // chunk-tile buffers between conversion and MMA
+constexpr int kStageBytes = 16 * kTcRows * 8;        // one K step: 16 terms x 128 words
+constexpr int kAccCols = 256;                        // tensor-memory columns of one accumulator buffer
 
 template <int NC, int OBP>
 struct TcShape {
   static constexpr int NS = 2 * NC - 1;                      // sums s = i + j
   static constexpr int NMMA = (NC * OBP + 15) / 16 * 16;     // MMA N (rows of the weight tile)
   static constexpr int COLS = (NC - 1) * OBP + NMMA;         // accumulator columns the MMAs touch
-  static constexpr int TMEM = COLS <= 64 ? 64 : COLS <= 128 ? 128 : 256;
   static constexpr int A_TILE = kTcRows * 16 * 2;            // bytes of a [128 x 16] fp16 tile
   static constexpr int B_TILE = NMMA * 16 * 2;               // bytes of an [NMMA x 16] fp16 tile
-  static_assert(COLS % 16 == 0 && COLS <= 256, "accumulators must fit 256 tensor-memory columns");
+  static_assert(COLS % 16 == 0 && COLS <= kAccCols, "accumulators must fit one buffer of 256 columns");
   static_assert(NMMA >= 16 && NMMA <= 256, "MMA N for M = 128");
 };
 
@@ -105,8 +103,9 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the completion of the barrier's phase of this parity; false after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the completion of the barrier's phase of this parity; false after about two seconds, or
+// at once when another role of the CTA has given up (*abort set).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 30); it++) {
     uint32_t done;
@@ -117,9 +116,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 255) == 255 && global_ns() - t0 > 2000000000ull) return false;
+    if ((it & 255) == 255 && (*abort || global_ns() - t0 > 2000000000ull)) {
+      *abort = 1;
+      return false;
+    }
   }
+  *abort = 1;
   return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // zeros into 16 accumulator columns of this warp's 32 lanes
@@ -131,17 +137,15 @@ __device__ __forceinline__ void tc_zero16(uint32_t taddr) {
       "r"(z)
       : "memory");
 }
+// zeros into 8 accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_zero8(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
 __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -184,11 +188,16 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 // out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
 // otherwise the others (9 chunks); blocks of the other class return at once.
 //
-// Roles: thread 0 issues the bulk copies of the input words (the 16 terms of a K step, 1 KB each
-// for the tile's 128 coefficients) kStages - 1 steps ahead into a ring of stages, and the MMAs;
-// every thread converts chunks: the two threads of tile row r = tid % 128 convert the first and
-// the second half of the NC chunks. In the recombination warp w reads tensor-memory lanes
-// 32 (w % 4) .. (its tile rows) for half w / 4 of the channels.
+// A CTA runs every task (channel group og, output column jp) of its tile, K step by K step, with
+// its warps in three roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
+//  - warp 1, one thread: bulk copies (untiled TMA, 1 KB a term) of each step's input words into a
+//    ring of kStages stages ("full" barriers count the bytes; "xfree" says a stage was read);
+//  - warps 2 .. 9: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
+//    (two threads a tile row, half of the chunks each; "afull" when written), and recombine the
+//    accumulators of the previous task while the MMAs of the current one run;
+//  - warp 0, one thread: per step NC MMAs into the task's accumulator buffer (two buffers of 256
+//    columns alternate between tasks), committed to "aempty" (buffer free) and, after a task's
+//    last step, to "accfull". The recombining warps zero the buffer after reading it ("accempty").
 template <int NC, int OBP, bool NARROW>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv_mac_tc_kernel(const u64* __restrict__ rot, u64* __restrict__ out, const u64* __restrict__ w, int c_in,
@@ -202,15 +211,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const Mod md = pt[i].mod;
   if ((md.q < kMac96Prime) != NARROW) return;  // uniform across the block, before any allocation
   const int kk2 = k * k, T = c_in * kk2, n_ks = (T + 15) >> 4;
+  const int n_og = (c_out + OBP - 1) / OBP;
+  const int n_jp = (w_out - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int n_tasks = n_og * n_jp, G = n_tasks * n_ks;
   unsigned char* X = tc_smem;                                                 // [kStages][16][128] words
-  unsigned char* A = X + kStages * kStageBytes;                               // [2][NC][A_TILE]
-  unsigned char* B = A + 2 * NC * S::A_TILE;                                  // [n_ks][B_TILE]
-  u64* toff = reinterpret_cast<u64*>(B + (size_t)n_ks * S::B_TILE);          // [16 n_ks]
+  unsigned char* A = X + kStages * kStageBytes;                               // [kABufs][NC][A_TILE]
+  unsigned char* B = A + kABufs * NC * S::A_TILE;                             // [n_og][n_ks][B_TILE]
+  u64* toff = reinterpret_cast<u64*>(B + (size_t)n_og * n_ks * S::B_TILE);   // [16 n_ks]
   u64* csm = toff + 16 * n_ks;                                                // [NS] 2^(7 s) mod q
-  u64* bars = csm + S::NS;                                                    // full[kStages], mma[2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kStages + 2);
-  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), half = tid >> 7;
-  // word offset of each term's input in rot, relative to output column 0 (padding terms: none)
+  u64* bars = csm + S::NS;
+  u64* full = bars;                      // [kStages]
+  u64* xfree = full + kStages;           // [kStages]
+  u64* afull = xfree + kStages;          // [kABufs]
+  u64* aempty = afull + kABufs;          // [kABufs]
+  u64* accfull = aempty + kABufs;        // [2]
+  u64* accempty = accfull + 2;           // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int t = tid; t < 16 * n_ks; t += kTcThreads) {
     u64 off = ~0ull;
     if (t < T) {
@@ -219,180 +237,216 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     toff[t] = off;
   }
+  // weight tiles of every channel group: row r = j OBP + o holds chunk j of W[og OBP + o][t]
+  for (int e = tid; e < n_og * n_ks * S::NMMA * 16; e += kTcThreads) {
+    const int og = e / (n_ks * S::NMMA * 16), e2 = e - og * (n_ks * S::NMMA * 16);
+    const int ks = e2 / (S::NMMA * 16), rem = e2 - ks * (S::NMMA * 16), r = rem >> 4, kk = rem & 15;
+    const int t = ks * 16 + kk, j = r / OBP, o = og * OBP + (r - j * OBP);
+    uint32_t v = 0;
+    if (j < NC && o < c_out && t < T) {
+      const int c = t / kk2, rr = t - c * kk2, b = rr / k, a = rr - b * k;
+      const u64 wv = w[(((size_t)o * T + (c * k + a) * k + b) * limbs + i) * 2];
+      v = (uint32_t)(wv >> (7 * j)) & 127u;
+    }
+    __half* dst = reinterpret_cast<__half*>(B + ((size_t)og * n_ks + ks) * S::B_TILE + (r >> 3) * 256 +
+                                            (kk >> 3) * 128 + (r & 7) * 16) +
+                  (kk & 7);
+    *dst = __uint2half_rn(v);
+  }
   if (tid == 0) {
     u64 c = 1;
     for (int s = 0; s < S::NS; s++) {
       csm[s] = c;
       c = mulmod(c, 128, md);
     }
-    for (int b = 0; b < kStages + 2; b++) mbar_init(smem_u32(&bars[b]), 1);
+    for (int b = 0; b < kStages; b++) {
+      mbar_init(smem_u32(&full[b]), 1);
+      mbar_init(smem_u32(&xfree[b]), kTcConvWarps);
+    }
+    for (int b = 0; b < kABufs; b++) {
+      mbar_init(smem_u32(&afull[b]), kTcConvWarps);
+      mbar_init(smem_u32(&aempty[b]), 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&accfull[b]), 1);
+      mbar_init(smem_u32(&accempty[b]), kTcConvWarps);
+    }
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    tc_alloc(smem_u32(tslot), S::TMEM);
+    tc_alloc(smem_u32(tslot), 2 * kAccCols);
     tc_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // this warp's lane quarter of tensor memory
   const size_t tile = (size_t)comp * LN + (size_t)i * N + (size_t)blockIdx.x * kTcRows;  // word of row 0
-  constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
-  constexpr int C0 = (NC + 1) / 2;  // chunks of the first half of the threads
-  const int c_lo = half ? C0 : 0, c_hi = half ? NC : C0;
-  // row `row` of an A tile: core matrix (row / 8, K half) at (row / 8) 256 + half 128, row % 8 at 16 bytes
-  const int arow = (row >> 3) * 256 + (row & 7) * 16;
-  const int n_jp = (w_out - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
-  uint32_t mma_uses[2] = {0, 0};
-  long gs0 = 0;  // steps of earlier channel groups (the stage ring and its barriers run on)
-  bool ok = true;
-  // thread 0: the bulk copies of step g of this channel group into its stage
-  auto issue = [&](int g) {
-    const int jp = (int)blockIdx.z + (g / n_ks) * (int)gridDim.z, ks = g % n_ks;
-    const long gs = gs0 + g;
-    const int st = (int)(gs % kStages);
-    const int nreal = min(16, T - 16 * ks);
-    const uint32_t bar = smem_u32(&bars[st]);
-    mbar_expect_tx(bar, (uint32_t)nreal * kTcRows * 8);
-    const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + tile;
-    const uint32_t dst = smem_u32(X + (size_t)st * kStageBytes);
-    for (int v = 0; v < nreal; v++) bulk_g2s(dst + v * kTcRows * 8, xb + toff[16 * ks + v], kTcRows * 8, bar);
-  };
-  for (int o0 = 0; o0 < c_out; o0 += OBP) {
-    // weight tiles of this channel group: row r = j OBP + o holds chunk j of W[o0 + o][t], t = 16 ks + kk
-    for (int e = tid; e < n_ks * S::NMMA * 16; e += kTcThreads) {
-      const int ks = e / (S::NMMA * 16), rem = e - ks * (S::NMMA * 16), r = rem >> 4, kk = rem & 15;
-      const int t = ks * 16 + kk, j = r / OBP, o = r - j * OBP;
-      uint32_t v = 0;
-      if (j < NC && o0 + o < c_out && t < T) {
-        const int c = t / kk2, rr = t - c * kk2, b = rr / k, a = rr - b * k;
-        const u64 wv = w[(((size_t)(o0 + o) * T + (c * k + a) * k + b) * limbs + i) * 2];
-        v = (uint32_t)(wv >> (7 * j)) & 127u;
-      }
-      __half* dst = reinterpret_cast<__half*>(B + (size_t)ks * S::B_TILE + (r >> 3) * 256 + (kk >> 3) * 128 +
-                                              (r & 7) * 16) +
-                    (kk & 7);
-      *dst = __uint2half_rn(v);
-    }
-    const int G = n_jp * n_ks;
-    if (tid == 0)
-      for (int g = 0; g < kStages - 1 && g < G; g++) issue(g);
-    for (int g = 0; g < G; g++) {
-      const int ks = g % n_ks;
-      const long gs = gs0 + g;
-      if (ks == 0 && warp < 4) {  // this task's accumulators start at zero
+  if (warp >= 2 && warp < 6) {
+    // both accumulator buffers start at zero (one warp per lane quarter)
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    for (int c = 0; c < 2 * kAccCols; c += 16) tc_zero16(tmem + lanes + c);
+    tc_wait_st();
+  }
+  fence_async_smem();  // the weight tiles, written by every thread, before the first MMA reads them
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == 0) {
+    // ---- MMA issue ----
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
+      for (int t = 0; t < n_tasks; t++) {
+        const int acc = t & 1, og = t / n_jp;
+        if (t >= 2 && !mbar_wait(smem_u32(&accempty[acc]), ((t >> 1) - 1) & 1, abort)) break;
+        tc_fence_after();
+        const uint32_t tacc = tmem + acc * kAccCols;
+        bool ok = true;
+        for (int ks = 0; ks < n_ks; ks++) {
+          const int g = t * n_ks + ks, ab = g % kABufs;
+          if (!(ok = mbar_wait(smem_u32(&afull[ab]), (uint32_t)((g / kABufs) & 1), abort))) break;
+          tc_fence_after();
+          const uint64_t bdesc = tc_desc(smem_u32(B + ((size_t)og * n_ks + ks) * S::B_TILE));
 #pragma unroll
-        for (int c = 0; c < S::COLS; c += 16) tc_zero16(tmem + lanes + c);
-        tc_wait_st();
-      }
-      // this step's input words have landed
-      if (ok) ok = mbar_wait(smem_u32(&bars[gs % kStages]), (uint32_t)((gs / kStages) & 1));
-      // A buffer b is free once the MMAs of two steps ago have finished
-      const int b = (int)(gs & 1);
-      if (mma_uses[b] > 0 && ok) ok = mbar_wait(smem_u32(&bars[kStages + b]), (mma_uses[b] - 1) & 1);
-      {
-        const u64* xs = reinterpret_cast<const u64*>(X + (size_t)(gs % kStages) * kStageBytes) + row;
-        const int nreal = min(16, T - 16 * ks);
-        u64 x[16];
-#pragma unroll
-        for (int v = 0; v < 16; v++) x[v] = v < nreal ? xs[v * kTcRows] : 0;
-        unsigned char* Ab = A + (size_t)b * NC * S::A_TILE + arow;
-#pragma unroll
-        for (int c = 0; c < NC; c++) {
-          if (c < c_lo || c >= c_hi) continue;
-          uint4 lo, hi;
-          lo.x = chunk_pair(x[0], x[1], 7 * c);
-          lo.y = chunk_pair(x[2], x[3], 7 * c);
-          lo.z = chunk_pair(x[4], x[5], 7 * c);
-          lo.w = chunk_pair(x[6], x[7], 7 * c);
-          hi.x = chunk_pair(x[8], x[9], 7 * c);
-          hi.y = chunk_pair(x[10], x[11], 7 * c);
-          hi.z = chunk_pair(x[12], x[13], 7 * c);
-          hi.w = chunk_pair(x[14], x[15], 7 * c);
-          *reinterpret_cast<uint4*>(Ab + c * S::A_TILE) = lo;
-          *reinterpret_cast<uint4*>(Ab + c * S::A_TILE + 128) = hi;
+          for (int c = 0; c < NC; c++)
+            tc_mma(tacc + c * OBP, tc_desc(smem_u32(A + ((size_t)ab * NC + c) * S::A_TILE)), bdesc, idesc);
+          tc_commit(smem_u32(&aempty[ab]));
         }
+        if (!ok) break;
+        tc_commit(smem_u32(&accfull[acc]));
+      }
+    }
+  } else if (warp == 1) {
+    // ---- bulk copies of the input words ----
+    if (lane == 0) {
+      for (int g = 0; g < G; g++) {
+        const int st = g % kStages;
+        if (g >= kStages && !mbar_wait(smem_u32(&xfree[st]), (uint32_t)(((g / kStages) - 1) & 1), abort)) break;
+        const int t = g / n_ks, ks = g - t * n_ks;
+        const int jp = (int)blockIdx.z + (t % n_jp) * (int)gridDim.z;
+        const int nreal = min(16, T - 16 * ks);
+        const uint32_t bar = smem_u32(&full[st]);
+        mbar_expect_tx(bar, (uint32_t)nreal * kTcRows * 8);
+        const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + tile;
+        const uint32_t dst = smem_u32(X + (size_t)st * kStageBytes);
+        for (int v = 0; v < nreal; v++) bulk_g2s(dst + v * kTcRows * 8, xb + toff[16 * ks + v], kTcRows * 8, bar);
+      }
+    }
+  } else {
+    // ---- chunk conversion and recombination ----
+    const int ci = tid - 64, row = ci & (kTcRows - 1), half = ci >> 7;
+    constexpr int C0 = (NC + 1) / 2;  // chunks of the first half of the threads
+    const int c_lo = half ? C0 : 0, c_hi = half ? NC : C0;
+    const int arow = (row >> 3) * 256 + (row & 7) * 16;
+    // recombination: lane quarter of this warp (its tile rows) and its half of the channels
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
+    constexpr int OH = OBP / 2;
+    auto recombine = [&](int tt) {
+      const int acc = tt & 1, og = tt / n_jp, jp = (int)blockIdx.z + (tt % n_jp) * (int)gridDim.z;
+      if (!mbar_wait(smem_u32(&accfull[acc]), (uint32_t)((tt >> 1) & 1), abort)) return false;
+      tc_fence_after();
+      const uint32_t tacc = tmem + acc * kAccCols + lanes;
+      const int o0 = og * OBP + eh * OH;
+      u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
+      const size_t ostep = (size_t)w_out * 2 * LN;
+      if constexpr (NARROW) {
+        Acc96 acc96[OH];
+#pragma unroll
+        for (int o = 0; o < OH; o++) acc96[o] = Acc96{0, 0, 0};
+        for (int s = 0; s < S::NS; s++) {
+          uint32_t d[OH];
+          tc_ld(tacc + s * OBP + eh * OH, d);
+          tc_wait_ld();
+          const u64 cs = csm[s];
+#pragma unroll
+          for (int o = 0; o < OH; o++) mac96(acc96[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+        }
+#pragma unroll
+        for (int o = 0; o < OH; o++)
+          if (o0 + o < c_out) dst[o * ostep] = reduce96(acc96[o], md);
+      } else {
+        Acc128 a128[OH];
+#pragma unroll
+        for (int o = 0; o < OH; o++) a128[o] = Acc128{0, 0};
+        for (int s = 0; s < S::NS; s++) {
+          uint32_t d[OH];
+          tc_ld(tacc + s * OBP + eh * OH, d);
+          tc_wait_ld();
+          const u64 cs = csm[s];
+#pragma unroll
+          for (int o = 0; o < OH; o++) mac128(a128[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+        }
+#pragma unroll
+        for (int o = 0; o < OH; o++)
+          if (o0 + o < c_out) dst[o * ostep] = reduce128(a128[o].hi, a128[o].lo, md);
+      }
+      // zero this warp's half of the buffer's columns for the task after next, then hand it back
+      for (int c = eh * (S::COLS / 2); c < (eh + 1) * (S::COLS / 2); c += 8) tc_zero8(tacc + c);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&accempty[acc]));
+      return true;
+    };
+    bool ok = true;
+    for (int g = 0; g < G && ok; g++) {
+      const int t = g / n_ks, ks = g - t * n_ks, st = g % kStages, ab = g % kABufs;
+      if (!(ok = mbar_wait(smem_u32(&full[st]), (uint32_t)((g / kStages) & 1), abort))) break;
+      const u64* xs = reinterpret_cast<const u64*>(X + (size_t)st * kStageBytes) + row;
+      const int nreal = min(16, T - 16 * ks);
+      u64 x[16];
+#pragma unroll
+      for (int v = 0; v < 16; v++) x[v] = v < nreal ? xs[v * kTcRows] : 0;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&xfree[st]));
+      if (g >= kABufs && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / kABufs) - 1) & 1), abort))) break;
+      unsigned char* Ab = A + (size_t)ab * NC * S::A_TILE + arow;
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        if (c < c_lo || c >= c_hi) continue;
+        uint4 lo, hi;
+        lo.x = chunk_pair(x[0], x[1], 7 * c);
+        lo.y = chunk_pair(x[2], x[3], 7 * c);
+        lo.z = chunk_pair(x[4], x[5], 7 * c);
+        lo.w = chunk_pair(x[6], x[7], 7 * c);
+        hi.x = chunk_pair(x[8], x[9], 7 * c);
+        hi.y = chunk_pair(x[10], x[11], 7 * c);
+        hi.z = chunk_pair(x[12], x[13], 7 * c);
+        hi.w = chunk_pair(x[14], x[15], 7 * c);
+        *reinterpret_cast<uint4*>(Ab + c * S::A_TILE) = lo;
+        *reinterpret_cast<uint4*>(Ab + c * S::A_TILE + 128) = hi;
       }
       fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint64_t bdesc = tc_desc(smem_u32(B + (size_t)ks * S::B_TILE));
-#pragma unroll
-        for (int c = 0; c < NC; c++)
-          tc_mma(tmem + c * OBP, tc_desc(smem_u32(A + ((size_t)b * NC + c) * S::A_TILE)), bdesc, idesc);
-        tc_commit(smem_u32(&bars[kStages + b]));
-        // the stage of step g - 1 has been read by every thread: refill it with step g + kStages - 1
-        if (g + kStages - 1 < G) issue(g + kStages - 1);
-      }
-      mma_uses[b]++;
-      if (ks == n_ks - 1) {
-        // the last commit covers every MMA of the task
-        if (ok) ok = mbar_wait(smem_u32(&bars[kStages + b]), (mma_uses[b] - 1) & 1);
-        tc_fence_after();
-        const int jp = (int)blockIdx.z + (g / n_ks) * (int)gridDim.z;
-        constexpr int OH = OBP / 2;  // channels of this thread's half
-        const int oh = half * OH;
-        u64* dst = out + ((size_t)(o0 + oh) * w_out + jp) * 2 * LN + tile + row;
-        const size_t ostep = (size_t)w_out * 2 * LN;
-        if constexpr (NARROW) {
-          Acc96 acc[OH];
-#pragma unroll
-          for (int o = 0; o < OH; o++) acc[o] = Acc96{0, 0, 0};
-          for (int s = 0; s < S::NS; s++) {
-            uint32_t d[OH];
-            tc_ld(tmem + lanes + s * OBP + oh, d);
-            tc_wait_ld();
-            const u64 cs = csm[s];
-#pragma unroll
-            for (int o = 0; o < OH; o++) mac96(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
-          }
-#pragma unroll
-          for (int o = 0; o < OH; o++)
-            if (o0 + oh + o < c_out) dst[o * ostep] = reduce96(acc[o], md);
-        } else {
-          Acc128 acc[OH];
-#pragma unroll
-          for (int o = 0; o < OH; o++) acc[o] = Acc128{0, 0};
-          for (int s = 0; s < S::NS; s++) {
-            uint32_t d[OH];
-            tc_ld(tmem + lanes + s * OBP + oh, d);
-            tc_wait_ld();
-            const u64 cs = csm[s];
-#pragma unroll
-            for (int o = 0; o < OH; o++) mac128(acc[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
-          }
-#pragma unroll
-          for (int o = 0; o < OH; o++)
-            if (o0 + oh + o < c_out) dst[o * ostep] = reduce128(acc[o].hi, acc[o].lo, md);
-        }
-        // every warp has read its accumulators before the next task zeroes them
-        tc_fence_before();
-        __syncthreads();
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&afull[ab]));
+      // the previous task's accumulators, while this task's MMAs run
+      if (ks == 0 && t >= 1) ok = recombine(t - 1);
     }
-    gs0 += G;
+    if (ok) ok = recombine(n_tasks - 1);
   }
+  __syncthreads();
   tc_fence_after();
-  if (warp == 0) tc_dealloc(tmem, S::TMEM);
-  if (!ok && tid == 0) atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
+  if (warp == 0) tc_dealloc(tmem, 2 * kAccCols);
+  if (*abort && tid == 0) atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
 }
 
 template <int NC, int OBP>
-size_t tc_smem_bytes(int T) {
+size_t tc_smem_bytes(int T, int c_out) {
   using S = TcShape<NC, OBP>;
-  const int n_ks = (T + 15) / 16;
-  return (size_t)kStages * kStageBytes + (size_t)2 * NC * S::A_TILE + (size_t)n_ks * S::B_TILE + 16 * n_ks * 8 +
-         S::NS * 8 + (kStages + 2) * 8 + 8;
+  const int n_ks = (T + 15) / 16, n_og = (c_out + OBP - 1) / OBP;
+  return (size_t)kStages * kStageBytes + (size_t)kABufs * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE +
+         16 * n_ks * 8 + S::NS * 8 + (2 * kStages + 2 * kABufs + 4) * 8 + 16;
 }
 
 template <int NC, int OBP, bool NARROW>
 void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                int c_out, int w_out, int limbs, int n_class, const char* name) {
   const int T = c_in * k * k;
-  const size_t smem = tc_smem_bytes<NC, OBP>(T);
+  const size_t smem = tc_smem_bytes<NC, OBP>(T, c_out);
+  if (smem > 227 * 1024) throw Error(8, "convolution too large for the tensor-core multiply-accumulate");
   static bool attr = false;
   if (!attr) {
     HE_CUDA(cudaFuncSetAttribute(k_conv_mac_tc_kernel<NC, OBP, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
