@@ -137,11 +137,15 @@ __device__ __forceinline__ void tc_zero16(uint32_t taddr) {
       "r"(z)
       : "memory");
 }
-// zeros into 8 accumulator columns of this warp's 32 lanes
-__device__ __forceinline__ void tc_zero8(uint32_t taddr) {
+// zeros into W = 4 or 8 accumulator columns of this warp's 32 lanes
+template <int W>
+__device__ __forceinline__ void tc_zero_cols(uint32_t taddr) {
   const uint32_t z = 0;
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
-               : "memory");
+  if constexpr (W == 8)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
+                 : "memory");
+  else
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};" ::"r"(taddr), "r"(z) : "memory");
 }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -383,8 +387,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int o = 0; o < OH; o++)
           if (o0 + o < c_out) dst[o * ostep] = reduce128(a128[o].hi, a128[o].lo, md);
       }
-      // zero this warp's half of the buffer's columns for the task after next, then hand it back
-      for (int c = eh * (S::COLS / 2); c < (eh + 1) * (S::COLS / 2); c += 8) tc_zero8(tacc + c);
+      // zero the columns this warp read (and only those: its partner warp on the same lanes may
+      // still be reading the other half), for the task after next, then hand the buffer back; the
+      // columns past NS OBP only ever gain zeros (padding rows of the weight tile)
+      for (int s = 0; s < S::NS; s++) tc_zero_cols<OH>(tacc + s * OBP + eh * OH);
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
