@@ -356,36 +356,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int o0 = og * OBP + eh * OH;
       u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
       const size_t ostep = (size_t)w_out * 2 * LN;
-      if constexpr (NARROW) {
-        Acc96 acc96[OH];
+      // sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo: two independent 64-bit sums of
+      // 32 x 32-bit products (below 2^60 for the up to 17 sums), joined into 128 bits at the end
+      u64 slo[OH], shi[OH];
 #pragma unroll
-        for (int o = 0; o < OH; o++) acc96[o] = Acc96{0, 0, 0};
-        for (int s = 0; s < S::NS; s++) {
-          uint32_t d[OH];
-          tc_ld(tacc + s * OBP + eh * OH, d);
-          tc_wait_ld();
-          const u64 cs = csm[s];
+      for (int o = 0; o < OH; o++) slo[o] = shi[o] = 0;
+      for (int s = 0; s < S::NS; s++) {
+        uint32_t d[OH];
+        tc_ld(tacc + s * OBP + eh * OH, d);
+        tc_wait_ld();
+        const u64 cs = csm[s];
+        const uint32_t clo = (uint32_t)cs, chi = (uint32_t)(cs >> 32);
 #pragma unroll
-          for (int o = 0; o < OH; o++) mac96(acc96[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
+        for (int o = 0; o < OH; o++) {
+          const uint32_t dv = __float2uint_rn(__uint_as_float(d[o]));
+          slo[o] += (u64)dv * clo;
+          shi[o] += (u64)dv * chi;
         }
+      }
 #pragma unroll
-        for (int o = 0; o < OH; o++)
-          if (o0 + o < c_out) dst[o * ostep] = reduce96(acc96[o], md);
-      } else {
-        Acc128 a128[OH];
-#pragma unroll
-        for (int o = 0; o < OH; o++) a128[o] = Acc128{0, 0};
-        for (int s = 0; s < S::NS; s++) {
-          uint32_t d[OH];
-          tc_ld(tacc + s * OBP + eh * OH, d);
-          tc_wait_ld();
-          const u64 cs = csm[s];
-#pragma unroll
-          for (int o = 0; o < OH; o++) mac128(a128[o], (u64)__float2uint_rn(__uint_as_float(d[o])), cs);
-        }
-#pragma unroll
-        for (int o = 0; o < OH; o++)
-          if (o0 + o < c_out) dst[o * ostep] = reduce128(a128[o].hi, a128[o].lo, md);
+      for (int o = 0; o < OH; o++) {
+        if (o0 + o >= c_out) continue;
+        const u64 vlo = slo[o] + (shi[o] << 32);
+        const u64 vhi = (shi[o] >> 32) + (vlo < slo[o]);
+        dst[o * ostep] = reduce128(vhi, vlo, md);
       }
       // zero the columns this warp read (and only those: its partner warp on the same lanes may
       // still be reading the other half), for the task after next, then hand the buffer back; the
