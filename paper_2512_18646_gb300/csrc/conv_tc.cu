@@ -34,7 +34,7 @@ namespace he {
 
 namespace {
 
-constexpr int kTcConvWarps = 8;                      // warps converting chunks and recombining
+constexpr int kTcConvWarps = 16;                     // warps converting chunks and recombining
 constexpr int kTcThreads = 32 * (2 + kTcConvWarps);  // + warp 0 (MMA issue), warp 1 (bulk copies)
 constexpr int kTcRows = 128;                         // MMA M: coefficients of one tile
 constexpr int kStages = 4;                           // input stages in the bulk-copy ring
@@ -137,24 +137,21 @@ __device__ __forceinline__ void tc_zero16(uint32_t taddr) {
       "r"(z)
       : "memory");
 }
-// zeros into W = 4 or 8 accumulator columns of this warp's 32 lanes
+// zeros into W = 2, 4 or 8 accumulator columns of this warp's 32 lanes
 template <int W>
 __device__ __forceinline__ void tc_zero_cols(uint32_t taddr) {
   const uint32_t z = 0;
   if constexpr (W == 8)
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
                  : "memory");
-  else
+  else if constexpr (W == 4)
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};" ::"r"(taddr), "r"(z) : "memory");
+  else
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %1};" ::"r"(taddr), "r"(z) : "memory");
 }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
 
 // Two 7-bit chunks (exact small integers) as one f16x2 word, the first in the low half: the fp16
 // words 0x6400 | v are 1024 + v exactly (unit spacing in [1024, 2048)), and one f16x2 subtraction of
@@ -181,6 +178,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
 __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -196,9 +196,9 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 // its warps in three roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
 //  - warp 1, one thread: bulk copies (untiled TMA, 1 KB a term) of each step's input words into a
 //    ring of kStages stages ("full" barriers count the bytes; "xfree" says a stage was read);
-//  - warps 2 .. 9: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
-//    (two threads a tile row, half of the chunks each; "afull" when written), and recombine the
-//    accumulators of the previous task while the MMAs of the current one run;
+//  - warps 2 .. 17: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
+//    (four threads a tile row, a quarter of the chunks each; "afull" when written), and recombine
+//    the accumulators of the previous task while the MMAs of the current one run;
 //  - warp 0, one thread: per step NC MMAs into the task's accumulator buffer (two buffers of 256
 //    columns alternate between tasks), committed to "aempty" (buffer free) and, after a task's
 //    last step, to "accfull". The recombining warps zero the buffer after reading it ("accempty").
@@ -340,14 +340,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ---- chunk conversion and recombination ----
-    const int ci = tid - 64, row = ci & (kTcRows - 1), half = ci >> 7;
-    constexpr int C0 = (NC + 1) / 2;  // chunks of the first half of the threads
-    const int c_lo = half ? C0 : 0, c_hi = half ? NC : C0;
+    constexpr int NQ = kTcConvWarps / 4;  // threads a tile row (each converts its share of the chunks)
+    const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;
+    const int c_lo = part * NC / NQ, c_hi = (part + 1) * NC / NQ;
     const int arow = (row >> 3) * 256 + (row & 7) * 16;
-    // recombination: lane quarter of this warp (its tile rows) and its half of the channels
+    // recombination: lane quarter of this warp (its tile rows) and its share of the channels
     const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
     const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
-    constexpr int OH = OBP / 2;
+    constexpr int OH = OBP / NQ;
     auto recombine = [&](int tt) {
       const int acc = tt & 1, og = tt / n_jp, jp = (int)blockIdx.z + (tt % n_jp) * (int)gridDim.z;
       if (!mbar_wait(smem_u32(&accfull[acc]), (uint32_t)((tt >> 1) & 1), abort)) return false;
