@@ -104,19 +104,21 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 // Wait for the completion of the barrier's phase of this parity; false after about two seconds, or
-// at once when another role of the CTA has given up (*abort set).
+// soon after another role of the CTA has given up (*abort set). Each try suspends the thread until
+// the phase completes or 20 us pass (the suspend-time hint), so waiting warps do not take issue
+// slots from the working ones.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
   const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < (1u << 30); it++) {
+  for (uint32_t it = 0; it < (1u << 24); it++) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     if (done) return true;
-    if ((it & 255) == 255 && (*abort || global_ns() - t0 > 2000000000ull)) {
+    if (*abort || global_ns() - t0 > 2000000000ull) {
       *abort = 1;
       return false;
     }
