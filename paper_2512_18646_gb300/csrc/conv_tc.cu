@@ -169,6 +169,27 @@ __device__ __forceinline__ uint32_t chunk_pair(u64 x0, u64 x1, int sh) {
   return out;
 }
 
+// Row `row` of chunk tiles C in [LO, HI) (tile C at Ab + C A_TILE) from the 16 input words x of the
+// row: chunk indexes and shifts are compile-time, so every extraction is a constant shift and mask.
+template <int A_TILE, int C, int HI>
+__device__ __forceinline__ void write_chunks(const u64 (&x)[16], unsigned char* Ab) {
+  if constexpr (C < HI) {
+    constexpr int sh = 7 * C;
+    uint4 lo, hi;
+    lo.x = chunk_pair(x[0], x[1], sh);
+    lo.y = chunk_pair(x[2], x[3], sh);
+    lo.z = chunk_pair(x[4], x[5], sh);
+    lo.w = chunk_pair(x[6], x[7], sh);
+    hi.x = chunk_pair(x[8], x[9], sh);
+    hi.y = chunk_pair(x[10], x[11], sh);
+    hi.z = chunk_pair(x[12], x[13], sh);
+    hi.w = chunk_pair(x[14], x[15], sh);
+    *reinterpret_cast<uint4*>(Ab + C * A_TILE) = lo;
+    *reinterpret_cast<uint4*>(Ab + C * A_TILE + 128) = hi;
+    write_chunks<A_TILE, C + 1, HI>(x, Ab);
+  }
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -343,8 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     // ---- chunk conversion and recombination ----
     constexpr int NQ = kTcConvWarps / 4;  // threads a tile row (each converts its share of the chunks)
-    const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;
-    const int c_lo = part * NC / NQ, c_hi = (part + 1) * NC / NQ;
+    const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;  // chunks [part NC / 4, (part + 1) NC / 4)
     const int arow = (row >> 3) * 256 + (row & 7) * 16;
     // recombination: lane quarter of this warp (its tile rows) and its share of the channels
     const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
@@ -406,20 +426,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) mbar_arrive(smem_u32(&xfree[st]));
       if (g >= kABufs && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / kABufs) - 1) & 1), abort))) break;
       unsigned char* Ab = A + (size_t)ab * NC * S::A_TILE + arow;
-#pragma unroll
-      for (int c = 0; c < NC; c++) {
-        if (c < c_lo || c >= c_hi) continue;
-        uint4 lo, hi;
-        lo.x = chunk_pair(x[0], x[1], 7 * c);
-        lo.y = chunk_pair(x[2], x[3], 7 * c);
-        lo.z = chunk_pair(x[4], x[5], 7 * c);
-        lo.w = chunk_pair(x[6], x[7], 7 * c);
-        hi.x = chunk_pair(x[8], x[9], 7 * c);
-        hi.y = chunk_pair(x[10], x[11], 7 * c);
-        hi.z = chunk_pair(x[12], x[13], 7 * c);
-        hi.w = chunk_pair(x[14], x[15], 7 * c);
-        *reinterpret_cast<uint4*>(Ab + c * S::A_TILE) = lo;
-        *reinterpret_cast<uint4*>(Ab + c * S::A_TILE + 128) = hi;
+      static_assert(NQ == 4, "four chunk shares");
+      switch (part) {  // warp-uniform
+        case 0: write_chunks<S::A_TILE, 0, NC / 4>(x, Ab); break;
+        case 1: write_chunks<S::A_TILE, NC / 4, 2 * NC / 4>(x, Ab); break;
+        case 2: write_chunks<S::A_TILE, 2 * NC / 4, 3 * NC / 4>(x, Ab); break;
+        default: write_chunks<S::A_TILE, 3 * NC / 4, NC>(x, Ab); break;
       }
       fence_async_smem();
       __syncwarp();
