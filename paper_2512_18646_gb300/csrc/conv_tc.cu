@@ -37,8 +37,6 @@ namespace {
 constexpr int kTcConvWarps = 16;                     // warps converting chunks and recombining
 constexpr int kTcThreads = 32 * (2 + kTcConvWarps);  // + warp 0 (MMA issue), warp 1 (bulk copies)
 constexpr int kTcRows = 128;                         // MMA M: coefficients of one tile
-constexpr int kStages = 4;                           // input stages in the bulk-copy ring
-constexpr int kABufs = 3;                            // chunk-tile buffers between conversion and MMA
 constexpr int kStageBytes = 16 * kTcRows * 8;        // one K step: 16 terms x 128 words
 constexpr int kAccCols = 256;                        // tensor-memory columns of one accumulator buffer
 
@@ -215,7 +213,7 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 // out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
 // otherwise the others (9 chunks); blocks of the other class return at once.
 //
-// A CTA runs every task (channel group og, output column jp) of its tile, K step by K step, with
+// A CTA runs every task (channel group og, output column jp) of its tiles, K step by K step, with
 // its warps in three roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
 //  - warp 1, one thread: bulk copies (untiled TMA, 1 KB a term) of each step's input words into a
 //    ring of kStages stages ("full" barriers count the bytes; "xfree" says a stage was read);
@@ -225,7 +223,7 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 //  - warp 0, one thread: per step NC MMAs into the task's accumulator buffer (two buffers of 256
 //    columns alternate between tasks), committed to "aempty" (buffer free) and, after a task's
 //    last step, to "accfull". The recombining warps zero the buffer after reading it ("accempty").
-template <int NC, int OBP, bool NARROW>
+template <int NC, int OBP, bool NARROW, int ST, int AB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv_mac_tc_kernel(const u64* __restrict__ rot, u64* __restrict__ out, const u64* __restrict__ w, int c_in,
                          int w_in, int k, int stride, int c_out, int w_out, int limbs, const PrimeTab* __restrict__ pt,
@@ -239,19 +237,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if ((md.q < kMac96Prime) != NARROW) return;  // uniform across the block, before any allocation
   const int kk2 = k * k, T = c_in * kk2, n_ks = (T + 15) >> 4;
   const int n_og = (c_out + OBP - 1) / OBP;
-  const int n_jp = (w_out - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
-  const int n_tasks = n_og * n_jp, G = n_tasks * n_ks;
-  unsigned char* X = tc_smem;                                                 // [kStages][16][128] words
-  unsigned char* A = X + kStages * kStageBytes;                               // [kABufs][NC][A_TILE]
-  unsigned char* B = A + kABufs * NC * S::A_TILE;                             // [n_og][n_ks][B_TILE]
+  // the CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ... of the limb's N / 128; per tile the
+  // tasks (channel group, output column), each n_ks K steps; the pipeline runs across them all
+  const int n_tiles = (int)(N / kTcRows);
+  const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int per_tile = n_og * w_out;
+  const int n_tasks = my_tiles * per_tile, G = n_tasks * n_ks;
+  const size_t row0 = (size_t)comp * LN + (size_t)i * N;
+  auto task_of = [&](int t, int& og, int& jp, size_t& tile) {
+    const int m = t / per_tile, r = t - m * per_tile;
+    og = r / w_out;
+    jp = r - og * w_out;
+    tile = row0 + (size_t)((int)blockIdx.x + m * (int)gridDim.x) * kTcRows;  // word of the tile's row 0
+  };
+  unsigned char* X = tc_smem;                                                 // [ST][16][128] words
+  unsigned char* A = X + ST * kStageBytes;                               // [AB][NC][A_TILE]
+  unsigned char* B = A + AB * NC * S::A_TILE;                             // [n_og][n_ks][B_TILE]
   u64* toff = reinterpret_cast<u64*>(B + (size_t)n_og * n_ks * S::B_TILE);   // [16 n_ks]
   u64* csm = toff + 16 * n_ks;                                                // [NS] 2^(7 s) mod q
   u64* bars = csm + S::NS;
-  u64* full = bars;                      // [kStages]
-  u64* xfree = full + kStages;           // [kStages]
-  u64* afull = xfree + kStages;          // [kABufs]
-  u64* aempty = afull + kABufs;          // [kABufs]
-  u64* accfull = aempty + kABufs;        // [2]
+  u64* full = bars;                      // [ST]
+  u64* xfree = full + ST;           // [ST]
+  u64* afull = xfree + ST;          // [AB]
+  u64* aempty = afull + AB;          // [AB]
+  u64* accfull = aempty + AB;        // [2]
   u64* accempty = accfull + 2;           // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
@@ -286,11 +295,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       csm[s] = c;
       c = mulmod(c, 128, md);
     }
-    for (int b = 0; b < kStages; b++) {
+    for (int b = 0; b < ST; b++) {
       mbar_init(smem_u32(&full[b]), 1);
       mbar_init(smem_u32(&xfree[b]), kTcConvWarps);
     }
-    for (int b = 0; b < kABufs; b++) {
+    for (int b = 0; b < AB; b++) {
       mbar_init(smem_u32(&afull[b]), kTcConvWarps);
       mbar_init(smem_u32(&aempty[b]), 1);
     }
@@ -309,7 +318,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const size_t tile = (size_t)comp * LN + (size_t)i * N + (size_t)blockIdx.x * kTcRows;  // word of row 0
   if (warp >= 2 && warp < 6) {
     // both accumulator buffers start at zero (one warp per lane quarter)
     const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
@@ -326,14 +334,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
       for (int t = 0; t < n_tasks; t++) {
-        const int acc = t & 1, og = t / n_jp;
+        const int acc = t & 1;
+        int og, jp_unused;
+        size_t tile_unused;
+        task_of(t, og, jp_unused, tile_unused);
         if (t >= 2 && !mbar_wait(smem_u32(&accempty[acc]), ((t >> 1) - 1) & 1, abort)) break;
         tc_fence_after();
         const uint32_t tacc = tmem + acc * kAccCols;
         bool ok = true;
         for (int ks = 0; ks < n_ks; ks++) {
-          const int g = t * n_ks + ks, ab = g % kABufs;
-          if (!(ok = mbar_wait(smem_u32(&afull[ab]), (uint32_t)((g / kABufs) & 1), abort))) break;
+          const int g = t * n_ks + ks, ab = g % AB;
+          if (!(ok = mbar_wait(smem_u32(&afull[ab]), (uint32_t)((g / AB) & 1), abort))) break;
           tc_fence_after();
           const uint64_t bdesc = tc_desc(smem_u32(B + ((size_t)og * n_ks + ks) * S::B_TILE));
 #pragma unroll
@@ -349,10 +360,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- bulk copies of the input words ----
     if (lane == 0) {
       for (int g = 0; g < G; g++) {
-        const int st = g % kStages;
-        if (g >= kStages && !mbar_wait(smem_u32(&xfree[st]), (uint32_t)(((g / kStages) - 1) & 1), abort)) break;
+        const int st = g % ST;
+        if (g >= ST && !mbar_wait(smem_u32(&xfree[st]), (uint32_t)(((g / ST) - 1) & 1), abort)) break;
         const int t = g / n_ks, ks = g - t * n_ks;
-        const int jp = (int)blockIdx.z + (t % n_jp) * (int)gridDim.z;
+        int og_unused, jp;
+        size_t tile;
+        task_of(t, og_unused, jp, tile);
         const int nreal = min(16, T - 16 * ks);
         const uint32_t bar = smem_u32(&full[st]);
         mbar_expect_tx(bar, (uint32_t)nreal * kTcRows * 8);
@@ -371,7 +384,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
     constexpr int OH = OBP / NQ;
     auto recombine = [&](int tt) {
-      const int acc = tt & 1, og = tt / n_jp, jp = (int)blockIdx.z + (tt % n_jp) * (int)gridDim.z;
+      const int acc = tt & 1;
+      int og, jp;
+      size_t tile;
+      task_of(tt, og, jp, tile);
       if (!mbar_wait(smem_u32(&accfull[acc]), (uint32_t)((tt >> 1) & 1), abort)) return false;
       tc_fence_after();
       const uint32_t tacc = tmem + acc * kAccCols + lanes;
@@ -415,8 +431,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     };
     bool ok = true;
     for (int g = 0; g < G && ok; g++) {
-      const int t = g / n_ks, ks = g - t * n_ks, st = g % kStages, ab = g % kABufs;
-      if (!(ok = mbar_wait(smem_u32(&full[st]), (uint32_t)((g / kStages) & 1), abort))) break;
+      const int t = g / n_ks, ks = g - t * n_ks, st = g % ST, ab = g % AB;
+      if (!(ok = mbar_wait(smem_u32(&full[st]), (uint32_t)((g / ST) & 1), abort))) break;
       const u64* xs = reinterpret_cast<const u64*>(X + (size_t)st * kStageBytes) + row;
       const int nreal = min(16, T - 16 * ks);
       u64 x[16];
@@ -424,7 +440,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int v = 0; v < 16; v++) x[v] = v < nreal ? xs[v * kTcRows] : 0;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&xfree[st]));
-      if (g >= kABufs && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / kABufs) - 1) & 1), abort))) break;
+      if (g >= AB && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / AB) - 1) & 1), abort))) break;
       unsigned char* Ab = A + (size_t)ab * NC * S::A_TILE + arow;
       static_assert(NQ == 4, "four chunk shares");
       switch (part) {  // warp-uniform
@@ -447,32 +463,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (*abort && tid == 0) atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
 }
 
-template <int NC, int OBP>
+template <int NC, int OBP, int ST, int AB>
 size_t tc_smem_bytes(int T, int c_out) {
   using S = TcShape<NC, OBP>;
   const int n_ks = (T + 15) / 16, n_og = (c_out + OBP - 1) / OBP;
-  return (size_t)kStages * kStageBytes + (size_t)kABufs * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE +
-         16 * n_ks * 8 + S::NS * 8 + (2 * kStages + 2 * kABufs + 4) * 8 + 16;
+  return (size_t)ST * kStageBytes + (size_t)AB * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE + 16 * n_ks * 8 +
+         S::NS * 8 + (2 * ST + 2 * AB + 4) * 8 + 16;
 }
 
-template <int NC, int OBP, bool NARROW>
+template <int NC, int OBP, bool NARROW, int ST, int AB>
 void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                int c_out, int w_out, int limbs, int n_class, const char* name) {
   const int T = c_in * k * k;
-  const size_t smem = tc_smem_bytes<NC, OBP>(T, c_out);
+  const size_t smem = tc_smem_bytes<NC, OBP, ST, AB>(T, c_out);
   if (smem > 227 * 1024) throw Error(8, "convolution too large for the tensor-core multiply-accumulate");
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
-    HE_CUDA(cudaFuncSetAttribute(k_conv_mac_tc_kernel<NC, OBP, NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024));
+    HE_CUDA(cudaFuncSetAttribute(k_conv_mac_tc_kernel<NC, OBP, NARROW, ST, AB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
     attr = true;
   }
-  const dim3 grid((unsigned)(C.N / kTcRows), (unsigned)(2 * limbs), 1);
+  // one CTA per SM at a time (its shared memory and all tensor memory): the (component, limb)
+  // pairs of this class share the SMs, each CTA looping over tiles of its pair
+  const int pairs = 2 * n_class;
+  const int gx = std::max(1, std::min((int)(C.N / kTcRows), sms / pairs));
+  const dim3 grid((unsigned)gx, (unsigned)(2 * limbs), 1);
   const double per_limb_bytes =
       8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
   const double prods = 2.0 * C.N * (double)c_out * w_out * T * n_class;
   void* tok = prof_begin(name, C.stream, per_limb_bytes * n_class, prods);
-  k_conv_mac_tc_kernel<NC, OBP, NARROW><<<grid, kTcThreads, smem, C.stream>>>(
+  k_conv_mac_tc_kernel<NC, OBP, NARROW, ST, AB><<<grid, kTcThreads, smem, C.stream>>>(
       rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, C.dev_ptab(), C.log_n, C.d_status.p);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
@@ -493,14 +515,14 @@ void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_i
   if (n_class == 0) return;
   if (narrow) {
     if (c_out <= 8)
-      launch_tc<7, 8, true>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
-                            "k_conv_mac_tc_kernel<7, 8>");
+      launch_tc<7, 8, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                                  "k_conv_mac_tc_kernel<7, 8>");
     else
-      launch_tc<7, 16, true>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
-                             "k_conv_mac_tc_kernel<7, 16>");
+      launch_tc<7, 16, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                                   "k_conv_mac_tc_kernel<7, 16>");
   } else {
-    launch_tc<9, 8, false>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
-                           "k_conv_mac_tc_kernel<9, 8>");
+    launch_tc<9, 8, false, 6, 2>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                                 "k_conv_mac_tc_kernel<9, 8>");
   }
 }
 
