@@ -383,50 +383,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
     const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
     constexpr int OH = OBP / NQ;
-    auto recombine = [&](int tt) {
-      const int acc = tt & 1;
-      int og, jp;
-      size_t tile;
-      task_of(tt, og, jp, tile);
-      if (!mbar_wait(smem_u32(&accfull[acc]), (uint32_t)((tt >> 1) & 1), abort)) return false;
-      tc_fence_after();
-      const uint32_t tacc = tmem + acc * kAccCols + lanes;
-      const int o0 = og * OBP + eh * OH;
-      u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
-      const size_t ostep = (size_t)w_out * 2 * LN;
-      // sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo: two independent 64-bit sums of
-      // 32 x 32-bit products (below 2^60 for the up to 17 sums), joined into 128 bits at the end
-      u64 slo[OH], shi[OH];
+    // Recombination of a finished task, spread over the K steps of the next one so that the
+    // tensor-memory loads overlap other warps' conversion: step ks of the next task takes the sums
+    // s in [ks NS / n_ks, (ks + 1) NS / n_ks), loaded four at a time before one wait. Per channel
+    // of this warp: sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo, as two independent
+    // 64-bit sums of 32 x 32-bit products (below 2^60 for up to 17 sums), joined at the end.
+    int pend = -1;  // task being recombined
+    u64 slo[OH], shi[OH];
+    auto recombine_part = [&](int s_lo, int s_hi) {
+      const uint32_t tacc = tmem + (pend & 1) * kAccCols + lanes + eh * OH;
+      if (s_lo == 0) {
+        if (!mbar_wait(smem_u32(&accfull[pend & 1]), (uint32_t)((pend >> 1) & 1), abort)) return false;
+        tc_fence_after();
 #pragma unroll
-      for (int o = 0; o < OH; o++) slo[o] = shi[o] = 0;
-      for (int s = 0; s < S::NS; s++) {
-        uint32_t d[OH];
-        tc_ld(tacc + s * OBP + eh * OH, d);
+        for (int o = 0; o < OH; o++) slo[o] = shi[o] = 0;
+      }
+      for (int s0 = s_lo; s0 < s_hi; s0 += 4) {
+        uint32_t d[4][OH];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (s0 + q < s_hi) tc_ld(tacc + (s0 + q) * OBP, d[q]);
         tc_wait_ld();
-        const u64 cs = csm[s];
-        const uint32_t clo = (uint32_t)cs, chi = (uint32_t)(cs >> 32);
 #pragma unroll
-        for (int o = 0; o < OH; o++) {
-          const uint32_t dv = __float2uint_rn(__uint_as_float(d[o]));
-          slo[o] += (u64)dv * clo;
-          shi[o] += (u64)dv * chi;
+        for (int q = 0; q < 4; q++) {
+          if (s0 + q >= s_hi) break;
+          const u64 cs = csm[s0 + q];
+          const uint32_t clo = (uint32_t)cs, chi = (uint32_t)(cs >> 32);
+#pragma unroll
+          for (int o = 0; o < OH; o++) {
+            const uint32_t dv = __float2uint_rn(__uint_as_float(d[q][o]));
+            slo[o] += (u64)dv * clo;
+            shi[o] += (u64)dv * chi;
+          }
+          // zero the columns this warp read (only those: its partner warps on the same lanes read
+          // the other channels), for the task after next; the columns past NS OBP only ever gain
+          // zeros (padding rows of the weight tile)
+          tc_zero_cols<OH>(tacc + (s0 + q) * OBP);
         }
       }
+      if (s_hi == S::NS) {
+        int og, jp;
+        size_t tile;
+        task_of(pend, og, jp, tile);
+        const int o0 = og * OBP + eh * OH;
+        u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
+        const size_t ostep = (size_t)w_out * 2 * LN;
 #pragma unroll
-      for (int o = 0; o < OH; o++) {
-        if (o0 + o >= c_out) continue;
-        const u64 vlo = slo[o] + (shi[o] << 32);
-        const u64 vhi = (shi[o] >> 32) + (vlo < slo[o]);
-        dst[o * ostep] = reduce128(vhi, vlo, md);
+        for (int o = 0; o < OH; o++) {
+          if (o0 + o >= c_out) continue;
+          const u64 vlo = slo[o] + (shi[o] << 32);
+          const u64 vhi = (shi[o] >> 32) + (vlo < slo[o]);
+          dst[o * ostep] = reduce128(vhi, vlo, md);
+        }
+        tc_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&accempty[pend & 1]));
+        pend = -1;
       }
-      // zero the columns this warp read (and only those: its partner warp on the same lanes may
-      // still be reading the other half), for the task after next, then hand the buffer back; the
-      // columns past NS OBP only ever gain zeros (padding rows of the weight tile)
-      for (int s = 0; s < S::NS; s++) tc_zero_cols<OH>(tacc + s * OBP + eh * OH);
-      tc_wait_st();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&accempty[acc]));
       return true;
     };
     bool ok = true;
@@ -452,10 +466,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&afull[ab]));
-      // the previous task's accumulators, while this task's MMAs run
-      if (ks == 0 && t >= 1) ok = recombine(t - 1);
+      // a share of the previous task's recombination, while this task's MMAs run
+      if (ks == 0 && t >= 1) pend = t - 1;
+      if (pend >= 0) ok = recombine_part(ks * S::NS / n_ks, (ks + 1) * S::NS / n_ks);
     }
-    if (ok) ok = recombine(n_tasks - 1);
+    if (ok && n_tasks > 0) {
+      if (pend < 0) pend = n_tasks - 1;  // the last task (or the rest of a pending one)
+      ok = recombine_part(0, S::NS);
+    }
   }
   __syncthreads();
   tc_fence_after();
