@@ -26,6 +26,8 @@
 // s * OBP + o collects D_s[.][o]. The roles hand work over through mbarriers (see the kernel).
 // Every wait is bounded: past the limit the CTA records the failure in the context's status word
 // (read by the host at its next synchronisation), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "he_internal.h"
@@ -191,13 +193,16 @@ __device__ __forceinline__ void write_chunks(const u64 (&x)[16], unsigned char* 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// bulk copy (untiled TMA) of `bytes` from global memory into this CTA's shared memory; the
-// barrier counts the bytes as they land. Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+// tiled TMA load of one box of the 2-D tensor map at coordinates (x, y) into this CTA's shared memory
+// (box rows one after another); the barrier counts the bytes as they land
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
+
 
 __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[2]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
@@ -208,8 +213,10 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
                : "r"(taddr));
 }
 
-// rot [c_in][w_in][k][2][limbs][N] (the hoisted rotations, term (c, b, a) of output column jp at
-// column stride jp + b, rotation a), w [c_out][c_in][k][k][limbs][2] (residue, Shoup companion),
+// rot_map: the tensor map of the hoisted rotations stored column-major, [w_in][c_in][k][2][limbs][N]
+// (ciphertext (j c_in + c) k + a is the rotation by g a of column j of channel c), so that the terms
+// (b, c, a) of output column jp are the consecutive ciphertexts stride jp c_in k + (b c_in + c) k + a;
+// w [c_out][c_in][k][k][limbs][2] (residue, Shoup companion),
 // out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
 // otherwise the others (9 chunks); blocks of the other class return at once.
 //
@@ -225,9 +232,9 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 //    last step, to "accfull". The recombining warps zero the buffer after reading it ("accempty").
 template <int NC, int OBP, bool NARROW, int ST, int AB>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_conv_mac_tc_kernel(const u64* __restrict__ rot, u64* __restrict__ out, const u64* __restrict__ w, int c_in,
-                         int w_in, int k, int stride, int c_out, int w_out, int limbs, const PrimeTab* __restrict__ pt,
-                         int log_n, u64* status) {
+    k_conv_mac_tc_kernel(const __grid_constant__ CUtensorMap rot_map, u64* __restrict__ out,
+                         const u64* __restrict__ w, int c_in, int w_in, int k, int stride, int c_out, int w_out,
+                         int limbs, const PrimeTab* __restrict__ pt, int log_n, u64* status) {
   using S = TcShape<NC, OBP>;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   const size_t N = (size_t)1 << log_n;
@@ -253,8 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* X = tc_smem;                                                 // [ST][16][128] words
   unsigned char* A = X + ST * kStageBytes;                               // [AB][NC][A_TILE]
   unsigned char* B = A + AB * NC * S::A_TILE;                             // [n_og][n_ks][B_TILE]
-  u64* toff = reinterpret_cast<u64*>(B + (size_t)n_og * n_ks * S::B_TILE);   // [16 n_ks]
-  u64* csm = toff + 16 * n_ks;                                                // [NS] 2^(7 s) mod q
+  u64* csm = reinterpret_cast<u64*>(B + (size_t)n_og * n_ks * S::B_TILE);    // [NS] 2^(7 s) mod q
   u64* bars = csm + S::NS;
   u64* full = bars;                      // [ST]
   u64* xfree = full + ST;           // [ST]
@@ -265,22 +271,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int t = tid; t < 16 * n_ks; t += kTcThreads) {
-    u64 off = ~0ull;
-    if (t < T) {
-      const int c = t / kk2, r = t - c * kk2, b = r / k, a = r - b * k;  // t = (c k + b) k + a
-      off = (((u64)c * w_in + b) * k + a) * 2 * LN;
-    }
-    toff[t] = off;
-  }
-  // weight tiles of every channel group: row r = j OBP + o holds chunk j of W[og OBP + o][t]
+  // term t of an output column: (b, c, a) with t = (b c_in + c) k + a, the rotation by g a of input
+  // column stride jp + b of channel c, at ciphertext stride jp c_in k + t of the column-major
+  // rotations; weight tiles of every channel group: row r = j OBP + o holds chunk j of W[og OBP + o][t]
+  const int ck = c_in * k;
   for (int e = tid; e < n_og * n_ks * S::NMMA * 16; e += kTcThreads) {
     const int og = e / (n_ks * S::NMMA * 16), e2 = e - og * (n_ks * S::NMMA * 16);
     const int ks = e2 / (S::NMMA * 16), rem = e2 - ks * (S::NMMA * 16), r = rem >> 4, kk = rem & 15;
     const int t = ks * 16 + kk, j = r / OBP, o = og * OBP + (r - j * OBP);
     uint32_t v = 0;
     if (j < NC && o < c_out && t < T) {
-      const int c = t / kk2, rr = t - c * kk2, b = rr / k, a = rr - b * k;
+      const int b = t / ck, rr = t - b * ck, c = rr / k, a = rr - c * k;
       const u64 wv = w[(((size_t)o * T + (c * k + a) * k + b) * limbs + i) * 2];
       v = (uint32_t)(wv >> (7 * j)) & 127u;
     }
@@ -366,12 +367,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int og_unused, jp;
         size_t tile;
         task_of(t, og_unused, jp, tile);
-        const int nreal = min(16, T - 16 * ks);
+        // one box: 128 words of each of the step's 16 consecutive ciphertexts (past the column's
+        // last term it reads the next column's, or zeros past the array; those rows go unused)
         const uint32_t bar = smem_u32(&full[st]);
-        mbar_expect_tx(bar, (uint32_t)nreal * kTcRows * 8);
-        const u64* xb = rot + (size_t)stride * jp * k * 2 * LN + tile;
-        const uint32_t dst = smem_u32(X + (size_t)st * kStageBytes);
-        for (int v = 0; v < nreal; v++) bulk_g2s(dst + v * kTcRows * 8, xb + toff[16 * ks + v], kTcRows * 8, bar);
+        mbar_expect_tx(bar, (uint32_t)kStageBytes);
+        tma_load_2d(smem_u32(X + (size_t)st * kStageBytes), &rot_map, (int)tile,
+                    stride * jp * ck + 16 * ks, bar);
       }
     }
   } else {
@@ -485,8 +486,32 @@ template <int NC, int OBP, int ST, int AB>
 size_t tc_smem_bytes(int T, int c_out) {
   using S = TcShape<NC, OBP>;
   const int n_ks = (T + 15) / 16, n_og = (c_out + OBP - 1) / OBP;
-  return (size_t)ST * kStageBytes + (size_t)AB * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE + 16 * n_ks * 8 +
-         S::NS * 8 + (2 * ST + 2 * AB + 4) * 8 + 16;
+  return (size_t)ST * kStageBytes + (size_t)AB * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE + S::NS * 8 +
+         (2 * ST + 2 * AB + 4) * 8 + 16;
+}
+
+// The tensor map of the column-major rotations: dimension 0 the words of a ciphertext (2 limbs N,
+// contiguous), dimension 1 the ciphertexts (2 limbs N words apart); boxes of 128 words by 16
+// ciphertexts, one K step of one tile. Reads past the last ciphertext fill zeros.
+static CUtensorMap rot_tensor_map(const u64* rot, size_t ct_words, size_t n_cts) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    HE_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) throw Error(7, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)ct_words, (cuuint64_t)n_cts};
+  const cuuint64_t strides[1] = {(cuuint64_t)ct_words * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcRows, 16u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<u64*>(rot), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(7, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return map;
 }
 
 template <int NC, int OBP, bool NARROW, int ST, int AB>
@@ -512,18 +537,24 @@ void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, i
       8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
   const double prods = 2.0 * C.N * (double)c_out * w_out * T * n_class;
   void* tok = prof_begin(name, C.stream, per_limb_bytes * n_class, prods);
+  const size_t ct_words = (size_t)2 * limbs * C.N;
+  if ((reinterpret_cast<uintptr_t>(rot) & 15) || ct_words % 2) throw Error(1, "rotations not 16-byte aligned");
+  const CUtensorMap map = rot_tensor_map(rot, ct_words, (size_t)w_in * c_in * k);
   k_conv_mac_tc_kernel<NC, OBP, NARROW, ST, AB><<<grid, kTcThreads, smem, C.stream>>>(
-      rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, C.dev_ptab(), C.log_n, C.d_status.p);
+      map, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, C.dev_ptab(), C.log_n, C.d_status.p);
   prof_end(tok, C.stream);
   HE_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
-bool conv_mac_tc_fits(const Ctx& C, int c_in, int k, bool narrow) {
+bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int lp) {
+  if (!C.use_tc || C.log_n < 7) return false;
   const long T = (long)c_in * k * k;
-  const long NC = narrow ? 7 : 9;
-  return C.log_n >= 7 && NC * T * 127 * 127 < (1L << 24);
+  bool narrow = false, wide = false;
+  for (int i = 0; i < lp; i++) (C.q[i] < kMac96Prime ? narrow : wide) = true;
+  // the chunk sums below 2^24: NC T 127^2 (NC = 7 below kMac96Prime, 9 above)
+  return (!narrow || 7 * T * 127 * 127 < (1L << 24)) && (!wide || 9 * T * 127 * 127 < (1L << 24));
 }
 
 void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,

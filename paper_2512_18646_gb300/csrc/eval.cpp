@@ -179,6 +179,36 @@ static const CtSet& two_comp(Ctx& C, const CtSet& in, std::unique_ptr<CtSet>& ho
   return *hold;
 }
 
+// Rotations of the input columns of c_in channels (in: [c][j], w_in columns each), stored for the
+// tensor-core convolution: the rotation by steps[a] of column j of channel c at ciphertext
+// (j c_in + c) k + a, so that the c_in k^2 terms of one output column are consecutive
+// ciphertexts. One ModUp for all inputs; the key switches run per channel on views of it.
+static std::unique_ptr<CtSet> rotate_colmajor(Ctx& C, const CtSet& in, int c_in, const std::vector<long>& steps) {
+  const int w_in = in.n / c_in, k = (int)steps.size();
+  for (long s : steps)
+    if (C.galois_elt(s) != 1) C.key(C.galois_elt(s));
+  auto out = new_set(C, in.n * k, 2, in.limbs, in.scale);
+  bool any = false;
+  for (long s : steps) any |= C.galois_elt(s) != 1;
+  DevBuf ext;
+  if (any) ext = modup_c1(C, in);
+  const size_t ext_ct = (size_t)C.beta_at(in.limbs) * (in.limbs + C.K) * C.N;
+  const size_t cw = in.ct_words();
+  for (int c = 0; c < c_in; c++) {
+    SetView v(in, c * w_in, w_in);
+    DevBuf ev;  // a view of channel c's digits (not owned)
+    if (ext.p) {
+      ev.p = ext.p + (size_t)c * w_in * ext_ct;
+      ev.words = (size_t)w_in * ext_ct;
+      ev.st = ext.st;
+    }
+    rotate_from_ext(C, v.s, ev, steps, out->buf.p + (size_t)c * k * cw, c_in * k);
+    ev.p = nullptr;
+    ev.words = 0;
+  }
+  return out;
+}
+
 std::unique_ptr<CtSet> rotate(Ctx& C, const CtSet& in_any, const std::vector<long>& steps) {
   std::unique_ptr<CtSet> hold;
   const CtSet& in = two_comp(C, in_any, hold);
@@ -393,9 +423,12 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
   // output columns per chunk: a chunk of wc columns reads (wc - 1) stride + k input columns per channel
   const int max_span = chunk_items(C, w_in, per_ct * c_in);
   const int wc = max_span >= w_in ? w_out : std::max(1, (max_span - k) / stride + 1);
+  // the tensor-core multiply-accumulate reads the rotations column-major ([j][c][a]), the CUDA-core
+  // kernels channel-major ([c][j][a])
+  const bool tc = conv_mac_tc_all(C, c_in, k, lp);
   if (wc >= w_out) {
-    auto rot = rotate(C, in, steps);  // [c][j][a]
-    k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp);
+    auto rot = tc ? rotate_colmajor(C, in, c_in, steps) : rotate(C, in, steps);
+    k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp, tc);
   } else {
     const size_t cw = in.ct_words();
     for (int j0 = 0; j0 < w_out; j0 += wc) {
@@ -404,10 +437,10 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
       for (int c = 0; c < c_in; c++)
         HE_CUDA(cudaMemcpyAsync(part->ct(c * span), in.ct(c * w_in + first), (size_t)span * cw * 8,
                                 cudaMemcpyDeviceToDevice, C.stream));
-      auto rot = rotate(C, *part, steps);
+      auto rot = tc ? rotate_colmajor(C, *part, c_in, steps) : rotate(C, *part, steps);
       part.reset();
       DevBuf oc((size_t)c_out * jn * cw, C.stream);
-      k_conv_mac(C, rot->buf.p, oc.p, dw.p, c_in, span, k, stride, c_out, jn, lp);
+      k_conv_mac(C, rot->buf.p, oc.p, dw.p, c_in, span, k, stride, c_out, jn, lp, tc);
       rot.reset();
       for (int o = 0; o < c_out; o++)
         HE_CUDA(cudaMemcpyAsync(out->ct(o * w_out + j0), oc.p + (size_t)o * jn * cw, (size_t)jn * cw * 8,

@@ -258,14 +258,17 @@ void k_mul_const(const Ctx& C, const u64* in, u64* out, size_t rows, int limbs, 
 void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limbs);
 // conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
 // the same on the tensor cores (conv_tc.cu) for the limbs of one class (narrow: primes below
-// kMac96Prime); conv_mac_tc_fits: the chunk sums of this shape stay exact in fp32
-bool conv_mac_tc_fits(const Ctx& C, int c_in, int k, bool narrow);
+// kMac96Prime), reading the rotations column-major ([j][c][a]); conv_mac_tc_all: the context
+// allows it and the chunk sums of this shape stay exact in fp32 for every class of the lp limbs
+bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int lp);
 void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                    int c_out, int w_out, int limbs, bool narrow);
 void check_device_status(Ctx& C);
 extern std::atomic<int> g_fail_allocs;
+// colmajor: rot in the tensor-core order [j][c][a] (the tensor cores then run every class of
+// limbs), else [c][j][a] for the CUDA-core kernels
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
-                int c_out, int w_out, int limbs);
+                int c_out, int w_out, int limbs, bool colmajor);
 // conv MAC with encrypted kernels: out[o][j'] (3 components) = sum_{c,b,a} tensor(W[o][c][a][b], R[c][s j' + b][a])
 void k_conv_enc_mac(const Ctx& C, const u64* rot, const u64* W, u64* out, int c_in, int w_in, int k, int stride,
                     int c_out, int w_out, int limbs);

@@ -1106,7 +1106,12 @@ void k_add_const(const Ctx& C, u64* ct, int n, int limbs, const u64* c_dev, int 
   HE_LAUNCH(k_add_const_kernel, (size_t)n * limbs * C.N, 8.0 * (double)C.N * 2.0 * n * limbs, ct, n, limbs, c_dev, per_group, C.dev_ptab(), C.log_n);
 }
 void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
-                int c_out, int w_out, int limbs) {
+                int c_out, int w_out, int limbs, bool colmajor) {
+  if (colmajor) {  // the tensor cores, every class of limbs (conv_mac_tc_all held)
+    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, false);
+    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, true);
+    return;
+  }
   constexpr int TN = 2, TH = 128;
   const size_t smem = (size_t)c_out * c_in * k * k * 16;
   if (smem > 200 * 1024) throw Error(8, "convolution weights exceed shared memory");
@@ -1120,15 +1125,6 @@ void k_conv_mac(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, 
   };
   const double prods_limb = 2.0 * C.N * (double)c_out * w_out * T;
   const unsigned gy = (unsigned)(2 * limbs);
-  // the tensor cores take each class of limbs whose chunk sums stay exact (conv_tc.cu)
-  if (wide > 0 && C.use_tc && conv_mac_tc_fits(C, c_in, k, false)) {
-    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, false);
-    wide = 0;
-  }
-  if (narrow > 0 && C.use_tc && conv_mac_tc_fits(C, c_in, k, true)) {
-    k_conv_mac_tc(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, true);
-    narrow = 0;
-  }
   if (wide > 0) {
     const unsigned gx = (unsigned)((C.N / TN + TH - 1) / TH);
     unsigned gz = (unsigned)std::max<size_t>(1, (size_t)152 * 16 / ((size_t)gx * 2 * wide));
