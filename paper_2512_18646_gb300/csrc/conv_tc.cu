@@ -36,7 +36,7 @@ namespace he {
 
 namespace {
 
-constexpr int kTcConvWarps = 16;                     // warps converting chunks and recombining
+constexpr int kTcConvWarps = 8;                      // warps converting chunks and recombining
 constexpr int kTcThreads = 32 * (2 + kTcConvWarps);  // + warp 0 (MMA issue), warp 1 (bulk copies)
 constexpr int kTcRows = 128;                         // MMA M: coefficients of one tile
 constexpr int kStageBytes = 16 * kTcRows * 8;        // one K step: 16 terms x 128 words
@@ -204,8 +204,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 
 
-__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[2]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
@@ -224,8 +226,8 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 // its warps in three roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
 //  - warp 1, one thread: bulk copies (untiled TMA, 1 KB a term) of each step's input words into a
 //    ring of kStages stages ("full" barriers count the bytes; "xfree" says a stage was read);
-//  - warps 2 .. 17: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
-//    (four threads a tile row, a quarter of the chunks each; "afull" when written), and recombine
+//  - warps 2 .. 9: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
+//    (two threads a tile row, half of the chunks each; "afull" when written), and recombine
 //    the accumulators of the previous task while the MMAs of the current one run;
 //  - warp 0, one thread: per step NC MMAs into the task's accumulator buffer (two buffers of 256
 //    columns alternate between tasks), committed to "aempty" (buffer free) and, after a task's
@@ -378,16 +380,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     // ---- chunk conversion and recombination ----
     constexpr int NQ = kTcConvWarps / 4;  // threads a tile row (each converts its share of the chunks)
-    const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;  // chunks [part NC / 4, (part + 1) NC / 4)
+    const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;  // first or second half of the chunks
     const int arow = (row >> 3) * 256 + (row & 7) * 16;
     // recombination: lane quarter of this warp (its tile rows) and its share of the channels
     const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
     const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
     constexpr int OH = OBP / NQ;
-    // Recombination of a finished task, spread over the K steps of the next one so that the
-    // tensor-memory loads overlap other warps' conversion: step ks of the next task takes the sums
-    // s in [ks NS / n_ks, (ks + 1) NS / n_ks), loaded four at a time before one wait. Per channel
-    // of this warp: sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo, as two independent
+    // Recombination of a finished task after the first K step of the next one (so that the next
+    // task's MMAs run meanwhile): the sums s loaded four at a time before one wait. Per channel of
+    // this warp: sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo, as two independent
     // 64-bit sums of 32 x 32-bit products (below 2^60 for up to 17 sums), joined at the end.
     int pend = -1;  // task being recombined
     u64 slo[OH], shi[OH];
@@ -457,19 +458,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) mbar_arrive(smem_u32(&xfree[st]));
       if (g >= AB && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / AB) - 1) & 1), abort))) break;
       unsigned char* Ab = A + (size_t)ab * NC * S::A_TILE + arow;
-      static_assert(NQ == 4, "four chunk shares");
-      switch (part) {  // warp-uniform
-        case 0: write_chunks<S::A_TILE, 0, NC / 4>(x, Ab); break;
-        case 1: write_chunks<S::A_TILE, NC / 4, 2 * NC / 4>(x, Ab); break;
-        case 2: write_chunks<S::A_TILE, 2 * NC / 4, 3 * NC / 4>(x, Ab); break;
-        default: write_chunks<S::A_TILE, 3 * NC / 4, NC>(x, Ab); break;
-      }
+      static_assert(NQ == 2, "two chunk shares");
+      if (part == 0)  // warp-uniform
+        write_chunks<S::A_TILE, 0, (NC + 1) / 2>(x, Ab);
+      else
+        write_chunks<S::A_TILE, (NC + 1) / 2, NC>(x, Ab);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&afull[ab]));
-      // a share of the previous task's recombination, while this task's MMAs run
-      if (ks == 0 && t >= 1) pend = t - 1;
-      if (pend >= 0) ok = recombine_part(ks * S::NS / n_ks, (ks + 1) * S::NS / n_ks);
+      // the previous task's recombination, while this task's MMAs run
+      if (ks == 0 && t >= 1) {
+        pend = t - 1;
+        ok = recombine_part(0, S::NS);
+      }
     }
     if (ok && n_tasks > 0) {
       if (pend < 0) pend = n_tasks - 1;  // the last task (or the rest of a pending one)
@@ -528,10 +529,10 @@ void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, i
     HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
     attr = true;
   }
-  // one CTA per SM at a time (its shared memory and all tensor memory): the (component, limb)
-  // pairs of this class share the SMs, each CTA looping over tiles of its pair
-  const int pairs = 2 * n_class;
-  const int gx = std::max(1, std::min((int)(C.N / kTcRows), sms / pairs));
+  // one CTA per SM at a time (its shared memory and all tensor memory), one tile of one
+  // (component, limb) each
+  (void)sms;
+  const int gx = (int)(C.N / kTcRows);  // one tile a CTA
   const dim3 grid((unsigned)gx, (unsigned)(2 * limbs), 1);
   const double per_limb_bytes =
       8.0 * (double)C.N * 2.0 * ((double)c_in * (stride * (w_out - 1) + k) * k + (double)c_out * w_out);
