@@ -208,6 +208,18 @@ int he_encrypt_coeffs(he_ctx* ctx, const int64_t* m, int n_ct, int limbs, double
 int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, he_ctset** C);
 
 /*
+ * he_matmul_range: the diagonals idx_lo <= idx < idx_hi of he_matmul's result
+ * (idx_hi - idx_lo ciphertexts, ciphertext t equal to he_matmul's ciphertext
+ * idx_lo + t, word for word). Sec. IV-A splits the product across the columns
+ * of B, one diagonal per worker; this is one worker's share, so that a matmul
+ * can be sharded over GPUs by diagonal index with A and B replicated and no
+ * exchange. Needs rotation keys for the steps of the range (step 0 needs none).
+ * Errors: as he_matmul; HE_E_ARG if the range is empty or outside [0, p).
+ */
+int he_matmul_range(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int idx_lo, int idx_hi,
+                    he_ctset** C);
+
+/*
  * he_matmul_bsgs: he_matmul's result (same operands, same p diagonal
  * ciphertexts, decoded by he_decrypt_matrix) with the rotations of Alg. 3 split
  * into baby and giant steps: idx = g i + j, j < g, and
@@ -414,6 +426,26 @@ void he_ptset_free(he_ptset* pts);
  */
 int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const double* bias, he_ctset** out);
 
+/*
+ * he_fc_partial / he_fc_finish: he_fc_apply in two halves, so that a dense
+ * layer can be sharded over its input columns (Sec. IV-B: the products of
+ * different channels and columns are independent and meet only in a sum).
+ * he_fc_partial: `in` holds the n input ciphertexts of columns first ..
+ * first + n - 1 of the layout `pts` was prepared for (two or three
+ * components); out receives out_dim ciphertexts, the sums
+ * sum_{first <= cj < first + n} pt_{o,cj} (x) in_cj mod q, before the rescale
+ * (same components as the input; the scale field is the input's while the
+ * sums still carry the plaintexts' factor q_l). Partial sums of disjoint
+ * column ranges add (he_add, mod q) to the full sums exactly.
+ * he_fc_finish: from the full sums (out_dim ciphertexts at the prepared level):
+ * rescale, relinearisation, rotate-and-add inside blocks, bias; the result
+ * equals he_fc_apply's word for word. `sums` is not modified.
+ * Errors: HE_E_ARG (columns outside the prepared range, count), HE_E_LEVEL,
+ * HE_E_NOKEY (finish).
+ */
+int he_fc_partial(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, int first, he_ctset** out);
+int he_fc_finish(he_ctx* ctx, const he_ctset* sums, const he_ptset* pts, const double* bias, he_ctset** out);
+
 /* he_fc: he_fc_prepare + he_fc_apply + he_ptset_free. Inputs may have two or
  * three components; the outputs are relinearised before the rotations. */
 int he_fc(he_ctx* ctx, const he_ctset* in, const double* W, const double* b, int out_dim, int c_in, int h_valid,
@@ -498,6 +530,24 @@ int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words);
  * [n][2][limbs][N] as he_ctset_export_raw writes them; every residue is
  * checked to be below its prime (HE_E_ARG otherwise). */
 int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
+
+/*
+ * Word exchange between processes (a sharded layer's all-gather or halo
+ * exchange): he_ctset_export_words copies the words as held, [n][polys][limbs][N]
+ * in the NTT domain, into dst -- HOST memory (dst_on_device = 0) or DEVICE
+ * memory of the context's GPU (dst_on_device = 1, e.g. a communication
+ * library's buffer) -- and returns when the copy is complete. n_words must be
+ * at least n * polys * limbs * N. he_ctset_import_words builds a set of n
+ * ciphertexts of `polys` (2 or 3) components at `limbs` limbs and the given
+ * scale from such words in host or device memory (src_on_device); the source
+ * is read on the context's stream, so device writes to it must be complete (or
+ * ordered before the call on that stream) when the call is made, and it may be
+ * reused when the call returns. Every residue is checked against its prime
+ * (HE_E_ARG otherwise).
+ */
+int he_ctset_export_words(const he_ctset* set, uint64_t* dst, int dst_on_device, size_t n_words);
+int he_ctset_import_words(he_ctx* ctx, const uint64_t* src, int src_on_device, int n, int polys, int limbs,
+                          double scale, he_ctset** out);
 
 /* Number of ciphertexts, limbs (level + 1), scale, components per ciphertext
  * (2, or 3 for an unrelinearised product). Any pointer may be NULL. */

@@ -70,6 +70,7 @@ SIGNATURES = {
     "he_encrypt_matrix_a_volley": (I, [V, P_D, I, I, I, U64, PV]),
     "he_encrypt_coeffs": (I, [V, P_I64, I, I, D, U64, PV]),
     "he_matmul": (I, [V, V, V, I, I, PV]),
+    "he_matmul_range": (I, [V, V, V, I, I, I, I, PV]),
     "he_matmul_batched": (I, [V, I, PV, PV, P_I, P_I, PV]),
     "he_matmul_volley": (I, [V, V, V, PV]),
     "he_matmul_bsgs": (I, [V, V, V, I, I, I, PV]),
@@ -93,6 +94,8 @@ SIGNATURES = {
     "he_fc_prepare_coeffs": (I, [V, P_I64, I, I, I, I, I, I, PV]),
     "he_ptset_free": (None, [V]),
     "he_fc_apply": (I, [V, V, V, P_D, PV]),
+    "he_fc_partial": (I, [V, V, V, I, PV]),
+    "he_fc_finish": (I, [V, V, V, P_D, PV]),
     "he_fc": (I, [V, V, P_D, P_D, I, I, I, I, I, I, I, PV]),
     "he_pack_blocks": (I, [V, PV, I, V, PV]),
     "he_rotate": (I, [V, V, P_I32, I, PV]),
@@ -113,6 +116,8 @@ SIGNATURES = {
     "he_ctset_import_raw": (I, [V, P_U64, I, I, D, PV]),
     "he_ctset_info": (I, [V, P_I, P_I, P_D, P_I]),
     "he_ctset_device_ptr": (I, [V, ctypes.POINTER(P_U64)]),
+    "he_ctset_export_words": (I, [V, P_U64, I, SZ]),
+    "he_ctset_import_words": (I, [V, P_U64, I, I, I, I, D, PV]),
     "he_ctset_slice": (I, [V, V, I, I, PV]),
     "he_ctset_concat": (I, [V, PV, I, PV]),
     "he_ctset_free": (None, [V]),

@@ -18,6 +18,15 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _words_buffer(buf):
+    """(pointer, on_device, words) of a uint64 numpy array or a 64-bit torch tensor."""
+    if isinstance(buf, np.ndarray):
+        assert buf.dtype == np.uint64 and buf.flags.c_contiguous
+        return _ptr(buf, P_U64), 0, buf.size
+    assert buf.element_size() == 8 and buf.is_contiguous(), "64-bit contiguous tensor expected"
+    return ctypes.cast(ctypes.c_void_p(buf.data_ptr()), P_U64), int(buf.is_cuda), buf.numel()
+
+
 def volley_geometry(slots: int, m: int, p: int):
     """(M, per, groups) of the zero-rotation matmul layout (he_volley_geometry)."""
     M, per, G = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -84,6 +93,15 @@ class CtSet:
         assert out.dtype == np.uint64 and out.flags.c_contiguous and out.size >= n * polys * limbs * self.ctx.N
         check(load().he_ctset_export_raw(self.h, _ptr(out, P_U64), out.size))
         return out
+
+    def export_words(self, dst) -> None:
+        """The words as held, [n][polys][limbs][N] in the NTT domain, into `dst`: a C-contiguous
+        numpy uint64 array (host) or a contiguous 64-bit torch CUDA tensor on the context's GPU."""
+        n, limbs, _, polys = self.info4()
+        need = n * polys * limbs * self.ctx.N
+        ptr, on_dev, size = _words_buffer(dst)
+        assert size >= need, "destination too small"
+        check(load().he_ctset_export_words(self.h, ptr, on_dev, size))
 
     def device_ptr(self) -> int:
         p = P_U64()
@@ -263,6 +281,10 @@ class Context:
     def matmul(self, A: CtSet, B: CtSet, m: int, p: int) -> CtSet:
         return self._set(load().he_matmul, self.h, A.h, B.h, m, p)
 
+    def matmul_range(self, A: CtSet, B: CtSet, m: int, p: int, lo: int, hi: int) -> CtSet:
+        """Diagonals lo .. hi - 1 of matmul(A, B, m, p)."""
+        return self._set(load().he_matmul_range, self.h, A.h, B.h, m, p, lo, hi)
+
     def matmul_bsgs(self, A: CtSet, B: CtSet, m: int, p: int, g: int = 0) -> CtSet:
         return self._set(load().he_matmul_bsgs, self.h, A.h, B.h, m, p, g)
 
@@ -376,6 +398,15 @@ class Context:
         b = None if bias is None else _f64(bias)
         return self._set(load().he_fc_apply, self.h, x.h, pts.h, None if b is None else _ptr(b, P_D))
 
+    def fc_partial(self, x: CtSet, pts: PtSet, first: int) -> CtSet:
+        """Sums over input columns first .. first + x.n - 1, before the rescale (he_fc_partial)."""
+        return self._set(load().he_fc_partial, self.h, x.h, pts.h, first)
+
+    def fc_finish(self, sums: CtSet, pts: PtSet, bias) -> CtSet:
+        """Rescale, relinearisation, rotate-and-add and bias of full sums (he_fc_finish)."""
+        b = None if bias is None else _f64(bias)
+        return self._set(load().he_fc_finish, self.h, sums.h, pts.h, None if b is None else _ptr(b, P_D))
+
     def pack_blocks(self, sets: Sequence[CtSet], masks: PtSet) -> CtSet:
         """rescale(sum_t masks_t * sets_t) (he_pack_blocks)."""
         arr = (ctypes.c_void_p * len(sets))(*[s.h.value for s in sets])
@@ -432,6 +463,18 @@ class Context:
         a = np.ascontiguousarray(words, dtype=np.uint64)
         n = a.size // (2 * limbs * self.N)
         return self._set(load().he_ctset_import_raw, self.h, _ptr(a, P_U64), n, limbs, float(scale))
+
+    def concat(self, sets: Sequence[CtSet]) -> CtSet:
+        """One set of the given sets' ciphertexts in order (same level, scale and components)."""
+        arr = (ctypes.c_void_p * len(sets))(*[s.h.value for s in sets])
+        return self._set(load().he_ctset_concat, self.h, arr, len(sets))
+
+    def import_words(self, src, n: int, polys: int, limbs: int, scale: float) -> CtSet:
+        """A set of n ciphertexts of `polys` components from NTT-domain words [n][polys][limbs][N]
+        in a numpy uint64 array or a 64-bit torch tensor (host or the context's GPU)."""
+        ptr, on_dev, size = _words_buffer(src)
+        assert size >= n * polys * limbs * self.N, "source too small"
+        return self._set(load().he_ctset_import_words, self.h, ptr, on_dev, n, polys, limbs, float(scale))
 
     def decrypt_matrix(self, C: CtSet, m: int, p: int) -> np.ndarray:
         out = np.zeros((m, p), np.float64)

@@ -265,6 +265,20 @@ int he_matmul(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, h
   });
 }
 
+int he_matmul_range(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int idx_lo, int idx_hi,
+                    he_ctset** C_out) {
+  return guard([&] {
+    HANDLE(ctx);
+    HANDLE(A);
+    HANDLE(B);
+    REQUIRE(ctx && A && B && C_out, HE_E_ARG, "null argument");
+    REQUIRE(m >= 1 && (size_t)m <= ctx->c.N / 2, HE_E_ARG, "bad m");
+    REQUIRE(idx_lo >= 0 && idx_lo < idx_hi && idx_hi <= p, HE_E_ARG, "diagonal range outside [0, p)");
+    REQUIRE(A->s->scale == B->s->scale, HE_E_SCALE, "operands at different scales");
+    *C_out = wrap(matmul(ctx->c, *A->s, *B->s, p, idx_lo, idx_hi));
+  });
+}
+
 int he_matmul_bsgs(he_ctx* ctx, const he_ctset* A, const he_ctset* B, int m, int p, int g, he_ctset** C_out) {
   return guard([&] {
     HANDLE(ctx);
@@ -441,6 +455,34 @@ int he_fc_apply(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, const doub
     REQUIRE(in->s->n == pts->n_in, HE_E_ARG, "input size does not match the prepared weights");
     REQUIRE(in->s->limbs == pts->limbs, HE_E_LEVEL, "input level does not match the prepared weights");
     *out = wrap(fc_apply(ctx->c, *in->s, pts->buf.p, pts->out_dim, pts->gap, pts->block_stride, bias));
+  });
+}
+
+int he_fc_partial(he_ctx* ctx, const he_ctset* in, const he_ptset* pts, int first, he_ctset** out) {
+  return guard([&] {
+    HANDLE(ctx);
+    HANDLE(in);
+    HANDLE(pts);
+    REQUIRE(ctx && in && pts && out, HE_E_ARG, "null argument");
+    REQUIRE(first >= 0 && first + in->s->n <= pts->n_in, HE_E_ARG, "input columns outside the prepared weights");
+    REQUIRE(in->s->limbs == pts->limbs, HE_E_LEVEL, "input level does not match the prepared weights");
+    *out = wrap(fc_partial(ctx->c, *in->s, pts->buf.p, pts->out_dim, pts->n_in, first));
+  });
+}
+
+int he_fc_finish(he_ctx* ctx, const he_ctset* sums, const he_ptset* pts, const double* bias, he_ctset** out) {
+  return guard([&] {
+    HANDLE(ctx);
+    HANDLE(sums);
+    HANDLE(pts);
+    REQUIRE(ctx && sums && pts && out, HE_E_ARG, "null argument");
+    const CtSet& z = *sums->s;
+    REQUIRE(z.n == pts->out_dim, HE_E_ARG, "one sum per output expected");
+    REQUIRE(z.limbs == pts->limbs, HE_E_LEVEL, "sums at a level other than the prepared weights'");
+    auto r = new_set(ctx->c, z.n, z.polys, z.limbs, z.scale);
+    HE_CUDA(cudaMemcpyAsync(r->buf.p, z.buf.p, z.buf.words * 8, cudaMemcpyDeviceToDevice, ctx->c.stream));
+    fc_finish(ctx->c, *r, pts->gap, pts->block_stride, bias);
+    *out = wrap(std::move(r));
   });
 }
 
@@ -901,6 +943,25 @@ int he_ctset_import_raw(he_ctx* ctx, const uint64_t* host, int n, int limbs, dou
     HANDLE(ctx);
     REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
     *out = wrap(import_coeffs(ctx->c, host, n, limbs, scale, true));
+  });
+}
+
+int he_ctset_export_words(const he_ctset* set, uint64_t* dst, int dst_on_device, size_t n_words) {
+  return guard([&] {
+    HANDLE(set);
+    REQUIRE(set && dst, HE_E_ARG, "null argument");
+    REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
+    export_words(*set->s->ctx, *set->s, dst, dst_on_device != 0);
+  });
+}
+
+int he_ctset_import_words(he_ctx* ctx, const uint64_t* src, int src_on_device, int n, int polys, int limbs,
+                          double scale, he_ctset** out) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx && src && out, HE_E_ARG, "null argument");
+    REQUIRE(scale > 0, HE_E_ARG, "scale must be positive");
+    *out = wrap(import_words(ctx->c, src, src_on_device != 0, n, polys, limbs, scale));
   });
 }
 

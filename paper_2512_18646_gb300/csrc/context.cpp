@@ -688,19 +688,44 @@ void export_raw(Ctx& C, const CtSet& s, u64* host) {
   check_device_status(C);
 }
 
+void export_words(Ctx& C, const CtSet& s, u64* dst, bool on_device) {
+  HE_CUDA(cudaMemcpyAsync(dst, s.buf.p, s.buf.words * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  check_device_status(C);
+}
+
+// residues of rows [n_rows][limbs][N] checked against their primes on the device
+static void check_residues(Ctx& C, const u64* p, size_t n_rows, int limbs) {
+  DevBuf bad(1, C.stream);
+  HE_CUDA(cudaMemsetAsync(bad.p, 0, 8, C.stream));
+  k_check_range(C, p, n_rows, limbs, (unsigned long long*)bad.p);
+  unsigned long long nbad = 0;
+  HE_CUDA(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, C.stream));
+  HE_CUDA(cudaStreamSynchronize(C.stream));
+  if (nbad) throw Error(1, std::to_string(nbad) + " residues out of range");
+}
+
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale, bool ntt_domain) {
   if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
   auto s = new_set(C, n, 2, limbs, scale);
   upload(C, s->buf.p, host, s->buf.words * 8);
   // residues are checked on the device before the transform
-  DevBuf bad(1, C.stream);
-  HE_CUDA(cudaMemsetAsync(bad.p, 0, 8, C.stream));
-  k_check_range(C, s->buf.p, (size_t)n * 2 * limbs, limbs, (unsigned long long*)bad.p);
-  unsigned long long nbad = 0;
-  HE_CUDA(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, C.stream));
-  HE_CUDA(cudaStreamSynchronize(C.stream));
-  if (nbad) throw Error(1, std::to_string(nbad) + " residues out of range");
+  check_residues(C, s->buf.p, (size_t)n * 2, limbs);
   if (!ntt_domain) ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
+  return s;
+}
+
+std::unique_ptr<CtSet> import_words(Ctx& C, const u64* src, bool on_device, int n, int polys, int limbs,
+                                    double scale) {
+  if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
+  if (polys != 2 && polys != 3) throw Error(1, "ciphertexts have two or three components");
+  auto s = new_set(C, n, polys, limbs, scale);
+  if (on_device)
+    HE_CUDA(cudaMemcpyAsync(s->buf.p, src, s->buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+  else
+    upload(C, s->buf.p, src, s->buf.words * 8);
+  check_residues(C, s->buf.p, (size_t)n * polys, limbs);
   return s;
 }
 

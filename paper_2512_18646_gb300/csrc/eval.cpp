@@ -503,31 +503,33 @@ std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in_any, int c_in, int gap
   return out;
 }
 
-std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, int p) {
+std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A_any, const CtSet& B_any, int p, int lo, int hi) {
   std::unique_ptr<CtSet> ha, hb;
   const CtSet& A = two_comp(C, A_any, ha);
   const CtSet& B = two_comp(C, B_any, hb);
   if (A.n != B.n || A.n < 1) throw Error(1, "A and B must have the same number n of ciphertexts");
   if (p < 1 || (C.N / 2) % (size_t)p) throw Error(1, "p must divide the slot count");
+  if (hi <= 0) hi = p;
+  if (lo < 0 || lo >= hi || hi > p) throw Error(1, "diagonal range outside [0, p)");
   if (A.limbs != B.limbs) throw Error(4, "operands at different levels");
   if (A.limbs < 2) throw Error(2, "no level left for the product");
-  for (int s = 1; s < p; s++) C.key(C.galois_elt(s));
-  const int n = A.n, lp = A.limbs;
+  for (int s = std::max(lo, 1); s < hi; s++) C.key(C.galois_elt(s));
+  const int n = A.n, lp = A.limbs, nd = hi - lo;
   const size_t cw = (size_t)2 * lp * C.N;
   DevBuf ext;
-  if (p > 1) ext = modup_c1(C, B);
+  if (hi > 1) ext = modup_c1(C, B);
   // rotations by idx in chunks that bound the memory of the rotated operands
   const size_t budget_words = (size_t)1 << 30;  // 8 GiB
   int chunk = (int)std::max<size_t>(1, budget_words / ((size_t)n * cw));
-  if (chunk > p) chunk = p;
-  auto d = new_set(C, p, 3, lp, A.scale * B.scale);
+  if (chunk > nd) chunk = nd;
+  auto d = new_set(C, nd, 3, lp, A.scale * B.scale);
   DevBuf R((size_t)n * chunk * cw, C.stream);
-  for (int i0 = 0; i0 < p; i0 += chunk) {
-    const int ci = std::min(chunk, p - i0);
+  for (int i0 = lo; i0 < hi; i0 += chunk) {
+    const int ci = std::min(chunk, hi - i0);
     std::vector<long> steps(ci);
     for (int t = 0; t < ci; t++) steps[t] = i0 + t;
     rotate_from_ext(C, B, ext, steps, R.p, ci);
-    k_matmul_acc(C, A.buf.p, R.p, d->ct(i0), n, ci, lp);
+    k_matmul_acc(C, A.buf.p, R.p, d->ct(i0 - lo), n, ci, lp);
   }
   R.reset();
   ext.reset();
@@ -944,24 +946,38 @@ DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int li
   return pts;
 }
 
-std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
-                                const double* bias) {
+std::unique_ptr<CtSet> fc_partial(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int pt_cols, int first) {
   const int lp = in.limbs;
   if (lp < 2) throw Error(2, "no level left for the dense layer");
-  for (int t = gap; t < block_stride; t *= 2) C.key(C.galois_elt(t));
+  if (first < 0 || first + in.n > pt_cols) throw Error(1, "input columns outside the prepared weights");
   auto z = new_set(C, out_dim, in.polys, lp, in.scale);
-  k_fc_mac(C, in.buf.p, pts, z->buf.p, in.n, out_dim, lp, in.polys);
-  rescale_inplace(C, *z);
-  z->scale = in.scale;  // plaintexts were encoded at scale q_l
-  relinearize(C, *z);
+  k_fc_mac(C, in.buf.p, pts + (size_t)first * lp * C.N, z->buf.p, in.n, pt_cols, out_dim, lp, in.polys);
+  return z;
+}
+
+void fc_finish(Ctx& C, CtSet& z, int gap, int block_stride, const double* bias) {
+  if (z.limbs < 2) throw Error(2, "no level left for the dense layer");
+  for (int t = gap; t < block_stride; t *= 2) C.key(C.galois_elt(t));
+  const double scale = z.scale;
+  rescale_inplace(C, z);
+  z.scale = scale;  // plaintexts were encoded at scale q_l
+  relinearize(C, z);
   for (int t = gap; t < block_stride; t *= 2) {
-    auto r = rotate(C, *z, {(long)t});
-    k_add(C, z->buf.p, r->buf.p, z->buf.p, z->n * 2, z->limbs);
+    auto r = rotate(C, z, {(long)t});
+    k_add(C, z.buf.p, r->buf.p, z.buf.p, z.n * 2, z.limbs);
   }
   if (bias) {
-    DevBuf cb = const_table(C, bias, out_dim, z->limbs, z->scale);
-    k_add_const(C, z->buf.p, z->n, z->limbs, cb.p, 1);
+    DevBuf cb = const_table(C, bias, z.n, z.limbs, z.scale);
+    k_add_const(C, z.buf.p, z.n, z.limbs, cb.p, 1);
   }
+}
+
+std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
+                                const double* bias) {
+  if (in.limbs < 2) throw Error(2, "no level left for the dense layer");
+  for (int t = gap; t < block_stride; t *= 2) C.key(C.galois_elt(t));
+  auto z = fc_partial(C, in, pts, out_dim, in.n, 0);
+  fc_finish(C, *z, gap, block_stride, bias);
   return z;
 }
 

@@ -291,7 +291,9 @@ void k_move_words(const Ctx& C, const SetPtrs& P, u64* base, int T, int dir);
 // zero-rotation matmul accumulate: d[g] = sum_k tensor(Ahat[g][k], B[k]), g < G
 void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int G, int limbs);
 // fc MAC: out[o] = sum_{cj} pt[o][cj] * X[cj], every one of the `polys` components
-void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys);
+// pt: [out_dim][pt_cols][limbs][N]; the n_in input columns are the first n_in of each row of pt
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int pt_cols, int out_dim, int limbs,
+              int polys);
 // slot-block packing: out[j] = sum_t masks[t] * xs[t][j] ([n_ct][2][limbs][N]); xs is a device array of T pointers
 // (ct_stride: words between the ciphertexts of one set, 0 = contiguous)
 void k_pack_blocks(const Ctx& C, const u64* const* xs, const u64* masks, int T, int n_ct, int limbs, u64* out,
@@ -322,6 +324,12 @@ void decrypt_slots(Ctx& C, const CtSet& s, double* out);
 void export_coeffs(Ctx& C, const CtSet& s, u64* host);
 // device words as held (NTT domain) to host
 void export_raw(Ctx& C, const CtSet& s, u64* host);
+// the words as held to a host or device buffer (completed on return)
+void export_words(Ctx& C, const CtSet& s, u64* dst, bool on_device);
+// n ciphertexts of `polys` components from NTT-domain words [n][polys][limbs][N] in a host or device
+// buffer, range-checked
+std::unique_ptr<CtSet> import_words(Ctx& C, const u64* src, bool on_device, int n, int polys, int limbs,
+                                    double scale);
 // [n][2][limbs][N] residues, coefficient domain (or already NTT domain), range-checked
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale,
                                      bool ntt_domain = false);
@@ -345,7 +353,8 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in, int c_in, int gap, const 
 // convolution with encrypted kernels Wct [c_out][c_in][k][k] (constants at scale q_{limbs-1})
 std::unique_ptr<CtSet> conv2d_enc(Ctx& C, const CtSet& in, int c_in, int gap, const CtSet& Wct, const double* bias,
                                   int c_out, int k, int stride);
-std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p);
+// diagonals idx in [lo, hi) of the revolver product (hi <= 0: up to p); hi - lo ciphertexts
+std::unique_ptr<CtSet> matmul(Ctx& C, const CtSet& A, const CtSet& B, int p, int lo = 0, int hi = 0);
 // vRot (Alg. 5) by r inside rows of images of hw slots; masks [2][lp][N] (F1, F2; NTT domain); one level
 std::unique_ptr<CtSet> vrot(Ctx& C, const CtSet& in, long r, int hw, const u64* masks);
 // Alg. 3 with one ciphertext per operand: E [lp-1][N] column-0 mask, F [p][lp-2][N] (NTT domain); three levels
@@ -378,6 +387,11 @@ std::unique_ptr<CtSet> mul(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> add(Ctx& C, const CtSet& a, const CtSet& b);
 std::unique_ptr<CtSet> fc_apply(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int gap, int block_stride,
                                 const double* bias);
+// the dense layer's sums over input columns [first, first + in.n) of pts [out_dim][pt_cols][limbs][N],
+// before the rescale (scale field: the input's; the sums carry the plaintexts' factor q_l)
+std::unique_ptr<CtSet> fc_partial(Ctx& C, const CtSet& in, const u64* pts, int out_dim, int pt_cols, int first);
+// the rest of the dense layer on full sums, in place: rescale, relinearisation, rotate-and-add, bias
+void fc_finish(Ctx& C, CtSet& z, int gap, int block_stride, const double* bias);
 DevBuf fc_prepare(Ctx& C, const int64_t* pts_host, int out_dim, int n_in, int limbs);
 // rescale(sum_t masks[t] * X_t): T sets of n_ct two-component ciphertexts at `limbs` limbs
 // (device pointers xs[t]), masks [T][limbs][N] encoded at scale q_{limbs-1}; result at `scale`

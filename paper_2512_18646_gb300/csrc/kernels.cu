@@ -746,8 +746,8 @@ __global__ void k_volley_acc_kernel(const u64* Ah, const u64* B, u64* d, int n, 
 // enough reads are in flight to stream the plaintexts at memory speed; sums
 // are reduced every 8 columns.
 template <int OB, int UN, int P>
-__global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim, int limbs,
-                                const PrimeTab* pt, int log_n) {
+__global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int pt_cols,
+                                                       int out_dim, int limbs, const PrimeTab* pt, int log_n) {
   static_assert(8 % UN == 0, "reduction every 8 columns");
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* 
           for (int c = 0; c < P; c++) xv[v][c] = ok ? X[((size_t)cj * P + c) * LN + w] : 0;
 #pragma unroll
           for (int t = 0; t < OB; t++)
-            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * n_in + cj) * LN + w] : 0;
+            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * pt_cols + cj) * LN + w] : 0;
         }
 #pragma unroll
         for (int v = 0; v < UN; v++)
@@ -800,8 +800,9 @@ __global__ void __launch_bounds__(128) k_fc_mac_kernel(const u64* X, const u64* 
 // 96-bit sums (seven 32-bit multiplies a product), reduced once every `room`
 // columns and at the end. Same layout and tiling as k_fc_mac_kernel.
 template <int OB, int UN, int P>
-__global__ void __launch_bounds__(128) k_fc_mac96_kernel(const u64* X, const u64* ptx, u64* out, int n_in, int out_dim,
-                                                         int limbs, const PrimeTab* pt, int log_n) {
+__global__ void __launch_bounds__(128) k_fc_mac96_kernel(const u64* X, const u64* ptx, u64* out, int n_in,
+                                                         int pt_cols, int out_dim, int limbs, const PrimeTab* pt,
+                                                         int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
   HE_GRID_LOOP(w, LN) {
@@ -826,7 +827,7 @@ __global__ void __launch_bounds__(128) k_fc_mac96_kernel(const u64* X, const u64
           for (int c = 0; c < P; c++) xv[v][c] = ok ? X[((size_t)cj * P + c) * LN + w] : 0;
 #pragma unroll
           for (int t = 0; t < OB; t++)
-            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * n_in + cj) * LN + w] : 0;
+            pv[v][t] = (ok && o0 + t < out_dim) ? ptx[((size_t)(o0 + t) * pt_cols + cj) * LN + w] : 0;
         }
         if (pending + UN > room) {  // uniform across the block
 #pragma unroll
@@ -1215,7 +1216,8 @@ void k_volley_acc(const Ctx& C, const u64* Ah, const u64* B, u64* d, int n, int 
               8.0 * (double)C.N * limbs * (2.0 * n * G + 2.0 * n + 3.0 * G), 4.0 * C.N * limbs * n * G, Ah, B, d, n,
               G, limbs, C.dev_ptab(), C.log_n);
 }
-void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int out_dim, int limbs, int polys) {
+void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int pt_cols, int out_dim, int limbs,
+              int polys) {
   if (polys != 2 && polys != 3) throw Error(1, "dense layer inputs have two or three components");
   const size_t total = (size_t)limbs * C.N;
   // 128-thread blocks: at 126-156 registers a thread, three or four blocks fit an SM
@@ -1229,18 +1231,22 @@ void k_fc_mac(const Ctx& C, const u64* X, const u64* pt, u64* out, int n_in, int
   if (wide > 0) {
     void* tok = prof_begin("k_fc_mac_kernel", C.stream, limb_bytes * wide, limb_prods * wide);
     if (polys == 2)
-      k_fc_mac_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+      k_fc_mac_kernel<5, 2, 2>
+          <<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, pt_cols, out_dim, limbs, C.dev_ptab(), C.log_n);
     else
-      k_fc_mac_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+      k_fc_mac_kernel<5, 2, 3>
+          <<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, pt_cols, out_dim, limbs, C.dev_ptab(), C.log_n);
     prof_end(tok, C.stream);
     HE_CUDA(cudaGetLastError());
   }
   if (narrow > 0) {
     void* tok = prof_begin("k_fc_mac96_kernel", C.stream, limb_bytes * narrow, limb_prods * narrow);
     if (polys == 2)
-      k_fc_mac96_kernel<5, 2, 2><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+      k_fc_mac96_kernel<5, 2, 2>
+          <<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, pt_cols, out_dim, limbs, C.dev_ptab(), C.log_n);
     else
-      k_fc_mac96_kernel<5, 2, 3><<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, out_dim, limbs, C.dev_ptab(), C.log_n);
+      k_fc_mac96_kernel<5, 2, 3>
+          <<<grid_fc, 128, 0, C.stream>>>(X, pt, out, n_in, pt_cols, out_dim, limbs, C.dev_ptab(), C.log_n);
     prof_end(tok, C.stream);
     HE_CUDA(cudaGetLastError());
   }
