@@ -166,9 +166,11 @@ def _free_port() -> int:
 
 
 def _worker(rank, world, port, seed, q):
+    import datetime
+
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
     try:
         from paper_2512_18646_gb300 import shard
         comm = shard.Comm()
@@ -185,6 +187,8 @@ def _worker(rank, world, port, seed, q):
         q.put((rank, (y1.lo, y1.hi, None if y1.cts is None else y1.cts.w),
                (y2.lo, y2.hi, None if y2.cts is None else y2.cts.w), z.w, d.w, yc.w))
         dist.barrier()
+    except Exception as e:  # reported to the test, which fails with it
+        q.put((rank, "error", repr(e)))
     finally:
         dist.destroy_process_group()
 
@@ -195,12 +199,19 @@ def test_sharded_layers_equal_the_one_process_result(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, 7, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, 7, q), daemon=True) for r in range(world)]
     for p in procs:
         p.start()
-    res = sorted((q.get(timeout=180) for _ in procs), key=lambda t: t[0])
+    try:
+        res = sorted((q.get(timeout=180) for _ in procs), key=lambda t: t[0])
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    for r in res:
+        assert r[1] != "error", r[2]
     for p in procs:
-        p.join(timeout=60)
         assert p.exitcode == 0
     c1, c2 = 3, 4
     w1, w2 = y1_ref.shape[0] // c1, y2_ref.shape[0] // c2
