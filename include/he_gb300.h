@@ -854,6 +854,15 @@ int he_calibrate_butterfly(he_ctx* ctx, int narrow, double* bfly_per_s);
  * involved. The paper has no counterpart. */
 int he_debug_fail_allocations(int n);
 
+/* Device-side fault path, for tests: enqueue on the context's stream one
+ * thread that waits on a barrier nothing arrives on, gives up after limit_us
+ * microseconds (1 .. 2,000,000) and records the failure in the context's
+ * status word -- the path every bounded wait of the tensor-core kernels takes.
+ * The next he_ctx_synchronize (or export) returns HE_E_TIMEOUT once and clears
+ * the word; the context stays usable. No GPU fault is involved. The paper has
+ * no counterpart. Errors: HE_E_ARG. */
+int he_debug_wait_timeout(he_ctx* ctx, int limit_us);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t he_kernel_launches(void);
 

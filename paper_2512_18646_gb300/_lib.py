@@ -140,6 +140,7 @@ SIGNATURES = {
     "he_server_stats": (I, [V, P_U64, ctypes.POINTER(SZ)]),
     "he_server_cancel": (I, [V, U64]),
     "he_debug_fail_allocations": (I, [I]),
+    "he_debug_wait_timeout": (I, [V, I]),
     "he_server_destroy": (None, [V]),
     "he_sched_simulate": (I, [I, P_D, P_I, ctypes.POINTER(SZ), I, P_I, P_D, P_D, SZ, SZ, I, SZ, P_I64, P_I, P_D,
                               P_D, P_D, ctypes.POINTER(SZ)]),

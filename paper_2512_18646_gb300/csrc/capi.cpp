@@ -906,6 +906,15 @@ int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double 
   });
 }
 
+int he_debug_wait_timeout(he_ctx* ctx, int limit_us) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    REQUIRE(limit_us >= 1 && limit_us <= 2000000, HE_E_ARG, "limit outside 1 .. 2,000,000 us");
+    k_wait_expires(ctx->c, (uint64_t)limit_us * 1000);
+  });
+}
+
 int he_debug_fail_allocations(int n) {
   return guard([&] {
     REQUIRE(n >= 0, HE_E_ARG, "n must be >= 0");

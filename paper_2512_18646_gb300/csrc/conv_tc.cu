@@ -103,11 +103,12 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the completion of the barrier's phase of this parity; false after about two seconds, or
-// soon after another role of the CTA has given up (*abort set). Each try suspends the thread until
-// the phase completes or 20 us pass (the suspend-time hint), so waiting warps do not take issue
-// slots from the working ones.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Wait for the completion of the barrier's phase of this parity; false after limit_ns (about two
+// seconds unless given), or soon after another role of the CTA has given up (*abort set). Each try
+// suspends the thread until the phase completes or 20 us pass (the suspend-time hint), so waiting
+// warps do not take issue slots from the working ones.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns = 2000000000ull) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 24); it++) {
     uint32_t done;
@@ -118,7 +119,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     if (done) return true;
-    if (*abort || global_ns() - t0 > 2000000000ull) {
+    if (*abort || global_ns() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }
@@ -483,6 +484,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (*abort && tid == 0) atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
 }
 
+// A wait that nothing ends, for tests of the failure path: one thread waits on a barrier of its CTA
+// that no thread arrives on, gives up after limit_ns, records the failure in the status word (as the
+// tensor-core kernels do) and returns; the host reports it at its next synchronisation.
+__global__ void k_wait_expires_kernel(u64* status, uint64_t limit_ns) {
+  __shared__ __align__(8) u64 bar;
+  __shared__ int give_up;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    give_up = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, &give_up, limit_ns))
+    atomicOr(reinterpret_cast<unsigned long long*>(status), 2ull);
+}
+
 template <int NC, int OBP, int ST, int AB>
 size_t tc_smem_bytes(int T, int c_out) {
   using S = TcShape<NC, OBP>;
@@ -548,6 +565,11 @@ void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, i
 }
 
 }  // namespace
+
+void k_wait_expires(const Ctx& C, uint64_t limit_ns) {
+  k_wait_expires_kernel<<<1, 32, 0, C.stream>>>(C.d_status.p, limit_ns);
+  HE_CUDA(cudaGetLastError());
+}
 
 bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int lp) {
   if (!C.use_tc || C.log_n < 7) return false;

@@ -803,6 +803,26 @@ def test_graph_capture_failure_leaves_context_usable(lib):
     assert np.abs(C - A @ Bm).max() < 1e-5
 
 
+def test_device_wait_that_runs_out_is_reported_and_the_context_stays_usable(lib):
+    """A device-side wait that nothing ends (he_debug_wait_timeout: a barrier no thread arrives on)
+    gives up after its limit and records the failure in the context's status word; the next
+    synchronisation reports HE_E_TIMEOUT once, and the context keeps computing exact results."""
+    from paper_2512_18646_gb300 import HeError, load
+    from paper_2512_18646_gb300._lib import HE_E_ARG, HE_E_TIMEOUT, check
+    o, g = make_pair(10, (60, 45, 45), 2, 60, 2, 45.0, seed=9, steps=[1])
+    rng = np.random.default_rng(9)
+    m = rng.integers(-(1 << 30), 1 << 30, size=(2, o.N), dtype=np.int64)
+    oc, gc = encrypt_both(o, g, m)
+    check(load().he_debug_wait_timeout(g.h, 2000))  # 2 ms
+    with pytest.raises(HeError) as e:
+        g.synchronize()
+    assert e.value.code == HE_E_TIMEOUT
+    g.synchronize()  # reported once
+    assert np.array_equal(g.rotate(gc, [1]).export(), np.stack([o.rotate(c, [1])[0] for c in oc]))
+    for bad in (0, 2000001):
+        assert load().he_debug_wait_timeout(g.h, bad) == HE_E_ARG
+
+
 def test_direct_capture_of_the_context_stream_is_refused_loudly(lib):
     """A capture the caller opens on the context's stream itself (torch's CUDA graph on that stream,
     not he_graph_begin) must not record a copy from the context's page-locked staging slots, which
