@@ -241,6 +241,8 @@ def run_gpu(args, rank, world, local_rank):
     pre = CNN_PRESETS[args.preset]
     seeds = rank_seeds(rank)
     g = api.Context.from_preset(pre, seed=seeds["ctx_seed"], stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     g.keygen(ROT_STEPS)
     B = args.batch
     h1, h2 = synthetic.cnn_shapes(SIDE)
@@ -392,6 +394,8 @@ def run_matmul(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     pre = synthetic.CNN_N16
     g = api.Context.from_preset(pre, seed=4000 + rank, stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     shapes = synthetic.batched_matmul_shapes(64, seed=401)
     if args.count:
         shapes = shapes[: args.count]
@@ -532,6 +536,8 @@ def run_matmul_small(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     pre = synthetic.MATMUL_SMALL
     g = api.Context.from_preset(pre, seed=5000 + rank, stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     g.keygen([1, 2, 3])
     count = args.count or 4096
     m, n, p = 4, 8, 4
@@ -611,6 +617,8 @@ def run_layer28(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     pre = synthetic.CNN_N16
     g = api.Context.from_preset(pre, seed=6000 + rank, stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     side, k, Hb = 28, 3, 32
     g.keygen([1, 2, Hb, 2 * Hb])
     K, bias = synthetic.conv_weights(4, 1, k, 0.1, seed=202)
@@ -701,6 +709,8 @@ def run_layer(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     pre = synthetic.CONV_LAYER
     g = api.Context.from_preset(pre, seed=201 + 1000 * rank, stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     g.keygen([1, 2])
     side, Hs = 64, 64
     K, bias = synthetic.conv_weights(4, 1, 3, 0.1, seed=202)
@@ -781,6 +791,8 @@ def run_table1(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     g = api.Context.from_preset(synthetic.CNN_N16, seed=7000 + rank, stream=stream.cuda_stream)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     geo = table1.Geometry(h=28, w=28, k=3, Hb=32, Wb=32, channels=4, fc1_out=64, fc2_out=10, slots=g.N // 2)
     t0 = time.perf_counter()
     g.keygen(table1.rotation_steps(geo))
@@ -922,6 +934,8 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     pre = synthetic.CNN_N16
     g = api.Context.from_preset(pre, seed=5000 + rank)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     g.keygen([])
     w = {s: synthetic.cnn_weights(s, seed=302) for s in SERVE_SIDES}
     n_warm, n_meas = args.serve_warmup, args.requests
@@ -1151,6 +1165,8 @@ def run_case(args):
     from paper_2512_18646_gb300 import api
     pre = synthetic.CNN_N16
     g = api.Context.from_preset(pre, seed=5)
+    if getattr(args, 'no_tensor_cores', False):
+        g.set_tensor_cores(False)  # the convolutions' multiply-accumulate on the CUDA cores
     g.keygen([1, 2, 3, 4])
     w = synthetic.cnn_weights(128, seed=302)
     if args.case == "conv2":
@@ -1256,6 +1272,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--batch", type=int, default=256, help="images per ciphertext set (block stride 128)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tensor-cores", action="store_true",
+                    help="run the convolutions' multiply-accumulate on the CUDA cores (96-bit sums)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preset", choices=sorted(CNN_PRESETS), default="cnn_n16",
                     help="cnn workload: prime chain and key-switching digits")
@@ -1281,7 +1299,9 @@ def main():
     wl = WORKLOAD.replace(KS_DESC["cnn_n16"], KS_DESC[args.preset])
     cfg = {"workload": wl, "images_per_step": args.batch, "image_side": SIDE, "log_n": 16,
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
-           "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed"}
+           "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed",
+           "conv_mac": "CUDA cores (96-bit sums)" if args.no_tensor_cores else
+           "tensor cores (tcgen05, 7-bit chunks summed exactly in fp32)"}
 
     if args.workload == "case":
         run_case(args)
