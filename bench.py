@@ -1301,7 +1301,7 @@ def main():
            "parallelism": f"replicas x{world} (independent inferences, no collective)",
            "l2": "inputs (128 ciphertexts, 1.7 GB) larger than L2; no flush needed",
            "conv_mac": "CUDA cores (96-bit sums)" if args.no_tensor_cores else
-           "tensor cores (tcgen05, 7-bit chunks summed exactly in fp32)"}
+           "tensor cores (tcgen05: residues in byte or 7-bit chunks, products summed exactly in fp32)"}
 
     if args.workload == "case":
         run_case(args)

@@ -6,26 +6,32 @@
 // K[o][c][a][b] times Rot(X_{c, s j' + b}, g a)) is, for one limb and one
 // component, a matrix product: out[o][n] = sum_t W[o][t] X_t[n] mod q, with
 // the c_out channels, T = c_in k^2 terms and the N coefficients of the limb as
-// its dimensions. Residues (below 2^46, resp. 2^62) are split into NC = 7
-// (resp. 9) chunks of 7 bits, x = sum_i x_i 2^(7i), which fp16 holds exactly;
-// the tensor cores sum the chunk products in fp32, which is exact while every
-// sum stays below 2^24:
-//   D_s[n][o] = sum_{i + j = s} sum_t x_i[t][n] w_j[o][t] <= NC T 127^2 < 2^24
-// (the host takes this path only for such T), s = 0 .. 2 NC - 2. Then
-//   out[o][n] = sum_s D_s[n][o] 2^(7s) mod q
-// on the CUDA cores (96-bit sums for the narrow primes, 128-bit otherwise,
-// one Barrett reduction). The result is the exact residue, the same word the
-// CUDA-core kernels compute.
+// its dimensions. Residues are cut into chunks that fp16 holds exactly and the
+// tensor cores sum the chunk products in fp32, which is exact while every sum
+// stays below 2^24:
+//  - primes below 2^46: NC = 6 bytes; the input chunks are taken signed,
+//    x = sum_i (b_i - 128) 256^i + K0 with K0 = 128 (256^6 - 1) / 255, the
+//    weight chunks unsigned, so |D_s| <= 6 T 128 255 < 2^24 for T <= 85;
+//  - primes below 2^62: NC = 9 chunks of 7 bits, both unsigned,
+//    D_s <= 9 T 127^2 < 2^24 for T <= 115;
+//   D_s[n][o] = sum_{i + j = s} sum_t x_i[t][n] w_j[o][t], s = 0 .. 2 NC - 2
+// (the host takes this path only for such T). Then on the CUDA cores
+//   out[o][n] = sum_s D_s[n][o] r^s (+ K0 sum_t W[o][t] for bytes) mod q
+// (r = 256 or 128; two 64-bit sums of 32 x 32-bit products, one Barrett
+// reduction). The result is the exact residue, the same word the CUDA-core
+// kernels compute.
 //
 // One CTA owns a tile of 128 coefficients of one (component, limb) and runs every output column
-// j' of the layer over it, 16 terms (one K step) at a time: the input words of a step arrive by
-// bulk copies (untiled TMA) in a ring of stages; converting warps write their 7-bit chunks as NC
-// fp16 tiles [128 x 16] (K-major, 8 x 16-byte core matrices, no swizzle); one thread issues NC
-// MMAs of M = 128, N = NC * OBP, K = 16: MMA i multiplies chunk tile i by the weight tile
+// j' of the layer over it, 16 terms (one K step) at a time: the input words of a step arrive by one
+// tiled TMA box in a ring of stages; converting warps write their chunks as NC fp16 tiles
+// [128 x 16] (K-major, 8 x 16-byte core matrices, no swizzle); one thread issues NC MMAs of
+// M = 128, N = NC * OBP, K = 16: MMA i multiplies chunk tile i by the weight tile
 // B = [chunk j][channel o] and accumulates at tensor-memory column i * OBP, so that column
-// s * OBP + o collects D_s[.][o]. The roles hand work over through mbarriers (see the kernel).
-// Every wait is bounded: past the limit the CTA records the failure in the context's status word
-// (read by the host at its next synchronisation), frees its tensor memory and returns.
+// s * OBP + o collects D_s[.][o]; recombining warps, two per lane quarter of the accumulator, turn
+// the finished sums of a task into residues while the next task's MMAs run. The roles hand work
+// over through mbarriers (see the kernel). Every wait is bounded: past the limit the CTA records
+// the failure in the context's status word (read by the host at its next synchronisation), frees
+// its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -36,8 +42,12 @@ namespace he {
 
 namespace {
 
-constexpr int kTcConvWarps = 8;                      // warps converting chunks and recombining
-constexpr int kTcThreads = 32 * (2 + kTcConvWarps);  // + warp 0 (MMA issue), warp 1 (bulk copies)
+constexpr int kTcConvWarps = 8;  // warps converting chunks
+constexpr int kTcRecWarps = 8;   // warps recombining the accumulators (a multiple of 4: whole lane quarters)
+// + warp 0 (MMA issue) and warp 1 (TMA loads)
+constexpr int kTcThreads = 32 * (2 + kTcConvWarps + kTcRecWarps);
+constexpr int kZeroBytes = 256 * 16 * 2;  // an all-zero fp16 tile of up to 256 rows x 16 (K-major)
+constexpr size_t kTcSmemMax = 227 * 1024;  // dynamic shared memory a CTA may opt in to
 constexpr int kTcRows = 128;                         // MMA M: coefficients of one tile
 constexpr int kStageBytes = 16 * kTcRows * 8;        // one K step: 16 terms x 128 words
 constexpr int kAccCols = 256;                        // tensor-memory columns of one accumulator buffer
@@ -47,9 +57,10 @@ struct TcShape {
   static constexpr int NS = 2 * NC - 1;                      // sums s = i + j
   static constexpr int NMMA = (NC * OBP + 15) / 16 * 16;     // MMA N (rows of the weight tile)
   static constexpr int COLS = (NC - 1) * OBP + NMMA;         // accumulator columns the MMAs touch
+  static constexpr int ZCOLS = (COLS + 15) / 16 * 16;         // columns the clearing MMA writes
   static constexpr int A_TILE = kTcRows * 16 * 2;            // bytes of a [128 x 16] fp16 tile
   static constexpr int B_TILE = NMMA * 16 * 2;               // bytes of an [NMMA x 16] fp16 tile
-  static_assert(COLS % 16 == 0 && COLS <= kAccCols, "accumulators must fit one buffer of 256 columns");
+  static_assert(ZCOLS <= kAccCols, "accumulators must fit one buffer of 256 columns");
   static_assert(NMMA >= 16 && NMMA <= 256, "MMA N for M = 128");
 };
 
@@ -83,12 +94,12 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
-  // accumulate (the accumulators are zeroed before the first K step of a task)
+// D (+)= A B; acc = 0 overwrites D (used with an all-zero A to clear a task's accumulators)
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc = 1u) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(1u)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -131,28 +142,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// zeros into 16 accumulator columns of this warp's 32 lanes
-__device__ __forceinline__ void tc_zero16(uint32_t taddr) {
-  const uint32_t z = 0;
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-      "%1};" ::"r"(taddr),
-      "r"(z)
-      : "memory");
-}
-// zeros into W = 2, 4 or 8 accumulator columns of this warp's 32 lanes
-template <int W>
-__device__ __forceinline__ void tc_zero_cols(uint32_t taddr) {
-  const uint32_t z = 0;
-  if constexpr (W == 8)
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
-                 : "memory");
-  else if constexpr (W == 4)
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};" ::"r"(taddr), "r"(z) : "memory");
-  else
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %1};" ::"r"(taddr), "r"(z) : "memory");
-}
-__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
@@ -191,6 +180,42 @@ __device__ __forceinline__ void write_chunks(const u64 (&x)[16], unsigned char* 
   }
 }
 
+// Bytes of two words as one f16x2 word of signed values b - 128 (b the byte `bi` of the 32-bit
+// halves w0, w1): one byte permutation places the bytes, a mask and the bias 0x6400 make the fp16
+// words 1024 + b exactly, and one f16x2 subtraction of 1152 leaves b - 128 exactly.
+__device__ __forceinline__ uint32_t byte_pair(uint32_t w0, uint32_t w1, uint32_t sel) {
+  const uint32_t biased = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;
+  __half2 h;
+  memcpy(&h, &biased, 4);
+  const __half2 r = __hsub2(h, __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+  uint32_t out;
+  memcpy(&out, &r, 4);
+  return out;
+}
+
+// Row `row` of byte tiles C in [C, HI) from the 16 input words (residues below 2^48): tile C holds
+// byte C of each word, less 128.
+template <int A_TILE, int C, int HI>
+__device__ __forceinline__ void write_bytes(const u64 (&x)[16], unsigned char* Ab) {
+  if constexpr (C < HI) {
+    constexpr int bi = C & 3;
+    constexpr uint32_t sel = (uint32_t)bi | ((uint32_t)(4 + bi) << 8);  // result bytes 0, 2: w0.bi, w1.bi
+    auto half = [](u64 v) { return C < 4 ? (uint32_t)v : (uint32_t)(v >> 32); };
+    uint4 lo, hi;
+    lo.x = byte_pair(half(x[0]), half(x[1]), sel);
+    lo.y = byte_pair(half(x[2]), half(x[3]), sel);
+    lo.z = byte_pair(half(x[4]), half(x[5]), sel);
+    lo.w = byte_pair(half(x[6]), half(x[7]), sel);
+    hi.x = byte_pair(half(x[8]), half(x[9]), sel);
+    hi.y = byte_pair(half(x[10]), half(x[11]), sel);
+    hi.z = byte_pair(half(x[12]), half(x[13]), sel);
+    hi.w = byte_pair(half(x[14]), half(x[15]), sel);
+    *reinterpret_cast<uint4*>(Ab + C * A_TILE) = lo;
+    *reinterpret_cast<uint4*>(Ab + C * A_TILE + 128) = hi;
+    write_bytes<A_TILE, C + 1, HI>(x, Ab);
+  }
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -205,6 +230,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 
 
+__device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -223,16 +256,18 @@ __device__ __forceinline__ void tc_ld(uint32_t taddr, uint32_t (&r)[4]) {
 // out [c_out][w_out][2][limbs][N]. NARROW: the limbs whose prime is below kMac96Prime (7 chunks),
 // otherwise the others (9 chunks); blocks of the other class return at once.
 //
-// A CTA runs every task (channel group og, output column jp) of its tiles, K step by K step, with
-// its warps in three roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
-//  - warp 1, one thread: bulk copies (untiled TMA, 1 KB a term) of each step's input words into a
-//    ring of kStages stages ("full" barriers count the bytes; "xfree" says a stage was read);
-//  - warps 2 .. 9: read a stage, convert the words into fp16 chunk tiles in one of kABufs buffers
-//    (two threads a tile row, half of the chunks each; "afull" when written), and recombine
-//    the accumulators of the previous task while the MMAs of the current one run;
-//  - warp 0, one thread: per step NC MMAs into the task's accumulator buffer (two buffers of 256
-//    columns alternate between tasks), committed to "aempty" (buffer free) and, after a task's
-//    last step, to "accfull". The recombining warps zero the buffer after reading it ("accempty").
+// A CTA runs every task (channel group og, output column jp) of its tile, K step by K step, with
+// its warps in four roles that hand work over through mbarriers (no CTA-wide barrier in the loop):
+//  - warp 1, one thread: one tiled TMA box (128 words of 16 consecutive ciphertexts) per step into
+//    a ring of ST stages ("full" barriers count the bytes; "xfree" says a stage was read);
+//  - warps 2 .. 9: read a stage, convert the words into fp16 chunk tiles in one of AB buffers
+//    (two threads a tile row, half of the chunks each; "afull" when written);
+//  - warp 0, one thread: per task, one MMA with an all-zero A and accumulation off clears the
+//    task's accumulator buffer (two buffers of 256 columns alternate between tasks), then per step
+//    NC MMAs, committed to "aempty" (chunk buffer free) and, after the last step, to "accfull";
+//  - warps 10 .. 17, two per lane quarter (half of the channels each): read a finished buffer,
+//    recombine and store the task's residues, and release the buffer ("accempty") while the next
+//    task's MMAs run.
 template <int NC, int OBP, bool NARROW, int ST, int AB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv_mac_tc_kernel(const __grid_constant__ CUtensorMap rot_map, u64* __restrict__ out,
@@ -263,8 +298,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* X = tc_smem;                                                 // [ST][16][128] words
   unsigned char* A = X + ST * kStageBytes;                               // [AB][NC][A_TILE]
   unsigned char* B = A + AB * NC * S::A_TILE;                             // [n_og][n_ks][B_TILE]
-  u64* csm = reinterpret_cast<u64*>(B + (size_t)n_og * n_ks * S::B_TILE);    // [NS] 2^(7 s) mod q
-  u64* bars = csm + S::NS;
+  unsigned char* Z = B + (size_t)n_og * n_ks * S::B_TILE;                   // kZeroBytes of zeros
+  u64* csm = reinterpret_cast<u64*>(Z + kZeroBytes);                         // [NS] 2^(7 s) or 2^(8 s) mod q
+  u64* corr = csm + S::NS;                                                    // [n_og OBP] (byte chunks)
+  u64* bars = corr + n_og * OBP;
   u64* full = bars;                      // [ST]
   u64* xfree = full + ST;           // [ST]
   u64* afull = xfree + ST;          // [AB]
@@ -286,18 +323,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (j < NC && o < c_out && t < T) {
       const int b = t / ck, rr = t - b * ck, c = rr / k, a = rr - c * k;
       const u64 wv = w[(((size_t)o * T + (c * k + a) * k + b) * limbs + i) * 2];
-      v = (uint32_t)(wv >> (7 * j)) & 127u;
+      v = NARROW ? (uint32_t)(wv >> (8 * j)) & 255u : (uint32_t)(wv >> (7 * j)) & 127u;
     }
     __half* dst = reinterpret_cast<__half*>(B + ((size_t)og * n_ks + ks) * S::B_TILE + (r >> 3) * 256 +
                                             (kk >> 3) * 128 + (r & 7) * 16) +
                   (kk & 7);
     *dst = __uint2half_rn(v);
   }
+  for (int e = tid; e < kZeroBytes / 16; e += kTcThreads) reinterpret_cast<uint4*>(Z)[e] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     u64 c = 1;
     for (int s = 0; s < S::NS; s++) {
       csm[s] = c;
-      c = mulmod(c, 128, md);
+      c = mulmod(c, NARROW ? 256 : 128, md);
     }
     for (int b = 0; b < ST; b++) {
       mbar_init(smem_u32(&full[b]), 1);
@@ -309,10 +347,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(smem_u32(&accfull[b]), 1);
-      mbar_init(smem_u32(&accempty[b]), kTcConvWarps);
+      mbar_init(smem_u32(&accempty[b]), kTcRecWarps);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (NARROW && tid < n_og * OBP) {
+    // byte chunks: x = sum_i (b_i - 128) 256^i + K0, K0 = 128 (256^6 - 1) / 255, so channel o's
+    // sum gains K0 sum_t W[o][t]; the recombination adds 2^24 to each signed D_s, so it loses
+    // 2^24 sum_s 256^s. corr[o] = K0 sum_t W[o][t] - 2^24 sum_s 256^s mod q (0 past c_out).
+    u64 wsum = 0;
+    if (tid < c_out)
+      for (int t = 0; t < T; t++) wsum = addmod(wsum, w[((size_t)tid * T + t) * limbs * 2 + (size_t)i * 2], md.q);
+    u64 c = 1, cs = 0;
+    for (int s = 0; s < S::NS; s++) {
+      cs = addmod(cs, c, md.q);
+      c = mulmod(c, 256, md);
+    }
+    const u64 k0 = 0x808080808080ull % md.q, two24 = (1ull << 24) % md.q;
+    const u64 v = addmod(mulmod(k0, wsum, md), (md.q - mulmod(two24, cs, md)) % md.q, md.q);
+    corr[tid] = tid < c_out ? v : 0;
   }
   if (warp == 0) {
     tc_alloc(smem_u32(tslot), 2 * kAccCols);
@@ -322,13 +376,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  if (warp >= 2 && warp < 6) {
-    // both accumulator buffers start at zero (one warp per lane quarter)
-    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-    for (int c = 0; c < 2 * kAccCols; c += 16) tc_zero16(tmem + lanes + c);
-    tc_wait_st();
-  }
-  fence_async_smem();  // the weight tiles, written by every thread, before the first MMA reads them
+  fence_async_smem();  // the weight and zero tiles, written by every thread, before the first MMA reads them
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -337,6 +385,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- MMA issue ----
     if (lane == 0) {
       constexpr uint32_t idesc = tc_idesc(kTcRows, S::NMMA);
+      constexpr uint32_t idesc_zero = tc_idesc(kTcRows, S::ZCOLS);
+      const uint64_t zdesc = tc_desc(smem_u32(Z));
       for (int t = 0; t < n_tasks; t++) {
         const int acc = t & 1;
         int og, jp_unused;
@@ -345,6 +395,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (t >= 2 && !mbar_wait(smem_u32(&accempty[acc]), ((t >> 1) - 1) & 1, abort)) break;
         tc_fence_after();
         const uint32_t tacc = tmem + acc * kAccCols;
+        tc_mma(tacc, zdesc, zdesc, idesc_zero, 0u);  // the buffer's ZCOLS columns := 0
         bool ok = true;
         for (int ks = 0; ks < n_ks; ks++) {
           const int g = t * n_ks + ks, ab = g % AB;
@@ -378,78 +429,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     stride * jp * ck + 16 * ks, bar);
       }
     }
-  } else {
-    // ---- chunk conversion and recombination ----
+  } else if (warp < 2 + kTcConvWarps) {
+    // ---- chunk conversion ----
     constexpr int NQ = kTcConvWarps / 4;  // threads a tile row (each converts its share of the chunks)
     const int ci = tid - 64, row = ci & (kTcRows - 1), part = ci >> 7;  // first or second half of the chunks
     const int arow = (row >> 3) * 256 + (row & 7) * 16;
-    // recombination: lane quarter of this warp (its tile rows) and its share of the channels
-    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-    const int erow = (warp & 3) * 32 + lane, eh = (warp - 2) >> 2;
-    constexpr int OH = OBP / NQ;
-    // Recombination of a finished task after the first K step of the next one (so that the next
-    // task's MMAs run meanwhile): the sums s loaded four at a time before one wait. Per channel of
-    // this warp: sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo, as two independent
-    // 64-bit sums of 32 x 32-bit products (below 2^60 for up to 17 sums), joined at the end.
-    int pend = -1;  // task being recombined
-    u64 slo[OH], shi[OH];
-    auto recombine_part = [&](int s_lo, int s_hi) {
-      const uint32_t tacc = tmem + (pend & 1) * kAccCols + lanes + eh * OH;
-      if (s_lo == 0) {
-        if (!mbar_wait(smem_u32(&accfull[pend & 1]), (uint32_t)((pend >> 1) & 1), abort)) return false;
-        tc_fence_after();
-#pragma unroll
-        for (int o = 0; o < OH; o++) slo[o] = shi[o] = 0;
-      }
-      for (int s0 = s_lo; s0 < s_hi; s0 += 4) {
-        uint32_t d[4][OH];
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-          if (s0 + q < s_hi) tc_ld(tacc + (s0 + q) * OBP, d[q]);
-        tc_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          if (s0 + q >= s_hi) break;
-          const u64 cs = csm[s0 + q];
-          const uint32_t clo = (uint32_t)cs, chi = (uint32_t)(cs >> 32);
-#pragma unroll
-          for (int o = 0; o < OH; o++) {
-            const uint32_t dv = __float2uint_rn(__uint_as_float(d[q][o]));
-            slo[o] += (u64)dv * clo;
-            shi[o] += (u64)dv * chi;
-          }
-          // zero the columns this warp read (only those: its partner warps on the same lanes read
-          // the other channels), for the task after next; the columns past NS OBP only ever gain
-          // zeros (padding rows of the weight tile)
-          tc_zero_cols<OH>(tacc + (s0 + q) * OBP);
-        }
-      }
-      if (s_hi == S::NS) {
-        int og, jp;
-        size_t tile;
-        task_of(pend, og, jp, tile);
-        const int o0 = og * OBP + eh * OH;
-        u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
-        const size_t ostep = (size_t)w_out * 2 * LN;
-#pragma unroll
-        for (int o = 0; o < OH; o++) {
-          if (o0 + o >= c_out) continue;
-          const u64 vlo = slo[o] + (shi[o] << 32);
-          const u64 vhi = (shi[o] >> 32) + (vlo < slo[o]);
-          dst[o * ostep] = reduce128(vhi, vlo, md);
-        }
-        tc_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&accempty[pend & 1]));
-        pend = -1;
-      }
-      return true;
-    };
-    bool ok = true;
-    for (int g = 0; g < G && ok; g++) {
-      const int t = g / n_ks, ks = g - t * n_ks, st = g % ST, ab = g % AB;
-      if (!(ok = mbar_wait(smem_u32(&full[st]), (uint32_t)((g / ST) & 1), abort))) break;
+    static_assert(NQ == 2, "two chunk shares");
+    for (int g = 0; g < G; g++) {
+      const int ks = g % n_ks, st = g % ST, ab = g % AB;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / ST) & 1), abort)) break;
       const u64* xs = reinterpret_cast<const u64*>(X + (size_t)st * kStageBytes) + row;
       const int nreal = min(16, T - 16 * ks);
       u64 x[16];
@@ -457,25 +445,82 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int v = 0; v < 16; v++) x[v] = v < nreal ? xs[v * kTcRows] : 0;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&xfree[st]));
-      if (g >= AB && !(ok = mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / AB) - 1) & 1), abort))) break;
+      if (g >= AB && !mbar_wait(smem_u32(&aempty[ab]), (uint32_t)(((g / AB) - 1) & 1), abort)) break;
       unsigned char* Ab = A + (size_t)ab * NC * S::A_TILE + arow;
-      static_assert(NQ == 2, "two chunk shares");
-      if (part == 0)  // warp-uniform
-        write_chunks<S::A_TILE, 0, (NC + 1) / 2>(x, Ab);
-      else
-        write_chunks<S::A_TILE, (NC + 1) / 2, NC>(x, Ab);
+      if constexpr (NARROW) {
+        if (part == 0)  // warp-uniform
+          write_bytes<S::A_TILE, 0, (NC + 1) / 2>(x, Ab);
+        else
+          write_bytes<S::A_TILE, (NC + 1) / 2, NC>(x, Ab);
+      } else {
+        if (part == 0)
+          write_chunks<S::A_TILE, 0, (NC + 1) / 2>(x, Ab);
+        else
+          write_chunks<S::A_TILE, (NC + 1) / 2, NC>(x, Ab);
+      }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&afull[ab]));
-      // the previous task's recombination, while this task's MMAs run
-      if (ks == 0 && t >= 1) {
-        pend = t - 1;
-        ok = recombine_part(0, S::NS);
-      }
     }
-    if (ok && n_tasks > 0) {
-      if (pend < 0) pend = n_tasks - 1;  // the last task (or the rest of a pending one)
-      ok = recombine_part(0, S::NS);
+  } else {
+    // ---- recombination: kTcRecWarps / 4 warps per lane quarter, each a share of the channels ----
+    // Per channel: sum_s D_s c_s with D_s < 2^24 and c_s = c_hi 2^32 + c_lo, as two independent
+    // 64-bit sums of 32 x 32-bit products (below 2^60 for up to 17 sums), joined at the end.
+    constexpr int RQ = kTcRecWarps / 4;  // warps per lane quarter
+    constexpr int OH = OBP / RQ;         // channels of one warp
+    const int rw = warp - 2 - kTcConvWarps, q4 = warp & 3, oh0 = (rw / 4) * OH;
+    const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+    const int erow = q4 * 32 + lane;
+    constexpr int LB = OH >= 16 ? 2 : OH == 8 ? 4 : 7;  // sums loaded before one wait
+    for (int t = 0; t < n_tasks; t++) {
+      const int acc = t & 1;
+      if (!mbar_wait(smem_u32(&accfull[acc]), (uint32_t)((t >> 1) & 1), abort)) break;
+      tc_fence_after();
+      const uint32_t tacc = tmem + acc * kAccCols + lanes + oh0;
+      u64 slo[OH], shi[OH];
+#pragma unroll
+      for (int o = 0; o < OH; o++) slo[o] = shi[o] = 0;
+#pragma unroll
+      for (int s0 = 0; s0 < S::NS; s0 += LB) {
+        uint32_t d[LB][OH];
+#pragma unroll
+        for (int q = 0; q < LB; q++)
+          if (s0 + q < S::NS) tc_ld(tacc + (s0 + q) * OBP, d[q]);
+        tc_wait_ld();
+#pragma unroll
+        for (int q = 0; q < LB; q++) {
+          if (s0 + q < S::NS) {
+            const u64 cs = csm[s0 + q];
+            const uint32_t clo = (uint32_t)cs, chi = (uint32_t)(cs >> 32);
+#pragma unroll
+            for (int o = 0; o < OH; o++) {
+              // byte chunks: D_s signed, below 2^24 in magnitude, taken as D_s + 2^24
+              const uint32_t dv = NARROW ? (uint32_t)(__float2int_rn(__uint_as_float(d[q][o])) + (1 << 24))
+                                         : __float2uint_rn(__uint_as_float(d[q][o]));
+              slo[o] += (u64)dv * clo;
+              shi[o] += (u64)dv * chi;
+            }
+          }
+        }
+      }
+      // the buffer is read: the MMAs of the task after next may clear it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&accempty[acc]));
+      int og, jp;
+      size_t tile;
+      task_of(t, og, jp, tile);
+      const int o0 = og * OBP + oh0;
+      u64* dst = out + ((size_t)o0 * w_out + jp) * 2 * LN + tile + erow;
+      const size_t ostep = (size_t)w_out * 2 * LN;
+#pragma unroll
+      for (int o = 0; o < OH; o++) {
+        if (o0 + o >= c_out) continue;
+        if constexpr (NARROW) slo[o] += corr[o0 + o];  // below 2^62 with it
+        const u64 vlo = slo[o] + (shi[o] << 32);
+        const u64 vhi = (shi[o] >> 32) + (vlo < slo[o]);
+        dst[o * ostep] = reduce128(vhi, vlo, md);
+      }
     }
   }
   __syncthreads();
@@ -504,8 +549,8 @@ template <int NC, int OBP, int ST, int AB>
 size_t tc_smem_bytes(int T, int c_out) {
   using S = TcShape<NC, OBP>;
   const int n_ks = (T + 15) / 16, n_og = (c_out + OBP - 1) / OBP;
-  return (size_t)ST * kStageBytes + (size_t)AB * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE + S::NS * 8 +
-         (2 * ST + 2 * AB + 4) * 8 + 16;
+  return (size_t)ST * kStageBytes + (size_t)AB * NC * S::A_TILE + (size_t)n_og * n_ks * S::B_TILE + kZeroBytes +
+         S::NS * 8 + (size_t)n_og * OBP * 8 + (2 * ST + 2 * AB + 4) * 8 + 16;
 }
 
 // The tensor map of the column-major rotations: dimension 0 the words of a ciphertext (2 limbs N,
@@ -537,12 +582,12 @@ void launch_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, i
                int c_out, int w_out, int limbs, int n_class, const char* name) {
   const int T = c_in * k * k;
   const size_t smem = tc_smem_bytes<NC, OBP, ST, AB>(T, c_out);
-  if (smem > 227 * 1024) throw Error(8, "convolution too large for the tensor-core multiply-accumulate");
+  if (smem > kTcSmemMax) throw Error(8, "convolution too large for the tensor-core multiply-accumulate");
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
     HE_CUDA(cudaFuncSetAttribute(k_conv_mac_tc_kernel<NC, OBP, NARROW, ST, AB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
     HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
     attr = true;
   }
@@ -571,13 +616,22 @@ void k_wait_expires(const Ctx& C, uint64_t limit_ns) {
   HE_CUDA(cudaGetLastError());
 }
 
-bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int lp) {
+// shared memory of the launch k_conv_mac_tc makes for a class of limbs
+static size_t tc_smem_for(int T, int c_out, bool narrow) {
+  if (!narrow) return tc_smem_bytes<9, 8, 6, 2>(T, c_out);
+  return c_out <= 8 ? tc_smem_bytes<6, 8, 6, 3>(T, c_out) : tc_smem_bytes<6, 16, 6, 3>(T, c_out);
+}
+
+bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int c_out, int lp) {
   if (!C.use_tc || C.log_n < 7) return false;
   const long T = (long)c_in * k * k;
   bool narrow = false, wide = false;
   for (int i = 0; i < lp; i++) (C.q[i] < kMac96Prime ? narrow : wide) = true;
-  // the chunk sums below 2^24: NC T 127^2 (NC = 7 below kMac96Prime, 9 above)
-  return (!narrow || 7 * T * 127 * 127 < (1L << 24)) && (!wide || 9 * T * 127 * 127 < (1L << 24));
+  // the chunk sums below 2^24: NC T 127^2 (NC = 7 below kMac96Prime, 9 above); every channel
+  // group's weight tiles held in shared memory
+  const bool ok_n = !narrow || (6 * T * 128 * 255 < (1L << 24) && tc_smem_for((int)T, c_out, true) <= kTcSmemMax);
+  const bool ok_w = !wide || (9 * T * 127 * 127 < (1L << 24) && tc_smem_for((int)T, c_out, false) <= kTcSmemMax);
+  return ok_n && ok_w;
 }
 
 void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
@@ -587,11 +641,11 @@ void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_i
   if (n_class == 0) return;
   if (narrow) {
     if (c_out <= 8)
-      launch_tc<7, 8, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
-                                  "k_conv_mac_tc_kernel<7, 8>");
+      launch_tc<6, 8, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                                  "k_conv_mac_tc_kernel<6, 8>");
     else
-      launch_tc<7, 16, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
-                                   "k_conv_mac_tc_kernel<7, 16>");
+      launch_tc<6, 16, true, 6, 3>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
+                                   "k_conv_mac_tc_kernel<6, 16>");
   } else {
     launch_tc<9, 8, false, 6, 2>(C, rot, out, w, c_in, w_in, k, stride, c_out, w_out, limbs, n_class,
                                  "k_conv_mac_tc_kernel<9, 8>");

@@ -425,7 +425,7 @@ std::unique_ptr<CtSet> conv2d(Ctx& C, const CtSet& in_any, int c_in, int gap, co
   const int wc = max_span >= w_in ? w_out : std::max(1, (max_span - k) / stride + 1);
   // the tensor-core multiply-accumulate reads the rotations column-major ([j][c][a]), the CUDA-core
   // kernels channel-major ([c][j][a])
-  const bool tc = conv_mac_tc_all(C, c_in, k, lp);
+  const bool tc = conv_mac_tc_all(C, c_in, k, c_out, lp);
   if (wc >= w_out) {
     auto rot = tc ? rotate_colmajor(C, in, c_in, steps) : rotate(C, in, steps);
     k_conv_mac(C, rot->buf.p, out->buf.p, dw.p, c_in, w_in, k, stride, c_out, w_out, lp, tc);

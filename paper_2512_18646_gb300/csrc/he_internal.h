@@ -259,10 +259,11 @@ void k_add_comps(const Ctx& C, u64* y, const u64* v, int n, int ypolys, int limb
 // conv MAC: out[o][j'] = sum_{c,b,a} W * R[c][s j' + b][a]
 // the same on the tensor cores (conv_tc.cu) for the limbs of one class (narrow: primes below
 // kMac96Prime), reading the rotations column-major ([j][c][a]); conv_mac_tc_all: the context
-// allows it and the chunk sums of this shape stay exact in fp32 for every class of the lp limbs
+// allows it, the chunk sums of this shape stay exact in fp32 and the weight tiles fit shared
+// memory, for every class of the lp limbs
 // one CTA waits on a barrier nothing arrives on for limit_ns, then records the failure in the status word
 void k_wait_expires(const Ctx& C, uint64_t limit_ns);
-bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int lp);
+bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int c_out, int lp);
 void k_conv_mac_tc(const Ctx& C, const u64* rot, u64* out, const u64* w, int c_in, int w_in, int k, int stride,
                    int c_out, int w_out, int limbs, bool narrow);
 void check_device_status(Ctx& C);

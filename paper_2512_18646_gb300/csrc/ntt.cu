@@ -610,7 +610,13 @@ void launch_rows(bool inv, u64* base, const LimbMap& lm, int rows, const Ctx& C,
   // a fused rescale also reads the limbs being rescaled and multiplies by q_l^{-1}
   const bool fused = !inv && (MODE == 1 || MODE == 2);
   const double bytes = (fused ? (MODE == 2 ? 32.0 : 24.0) : 16.0) * rows * (double)C.N;
-  const double prods = (double)rows * C.N * ((C.log_n - n1) / 2.0 + (fused ? 1.0 : 0.0));
+  // products: the butterflies, plus one Shoup product per element that ends the transform: the
+  // fused epilogue's, or else (growing-range path, primes below kNarrowPrime) the reduction of the
+  // result to [0, q) (forward) or [0, 2q) (inverse)
+  int narrow = 0;
+  for (int i = 0; i < lm.lpp; i++) narrow += C.q[lm.prime(i)] < kNarrowPrime;
+  const double last = fused ? 1.0 : (double)narrow / lm.lpp;
+  const double prods = (double)rows * C.N * ((C.log_n - n1) / 2.0 + last);
   const char* name = inv ? "k_ntt_inv_rows"
                          : MODE == 1 ? "k_ntt_fwd_rows<rescale>" : MODE == 2 ? "k_ntt_fwd_rows<moddown>" : "k_ntt_fwd_rows";
   static_assert(MODE >= 0 && MODE <= 4, "transform modes 0..4");
