@@ -346,10 +346,14 @@ def run_gpu(args, rank, world, local_rank):
         from paper_2512_18646_gb300._lib import P_U64, check
         g.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            xin = g.import_coeffs(pin_arr, g.scale)
+        # each step's ciphertexts are uploaded while the previous step computes (he_ctset_import_async
+        # copies on a stream of its own), and each step's logits are exported before the next begins
+        xin = g.import_coeffs_async(pin_arr, g.scale)
+        for i in range(args.steps):
             zz = cnn_step(g, xin, w, pts)
+            xnext = g.import_coeffs_async(pin_arr, g.scale) if i + 1 < args.steps else None
             check(lib.he_ctset_export(zz.h, pin_out.ctypes.data_as(P_U64), pin_out.size))
+            xin = xnext
         g.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": round(job_throughput(B, args.steps, world, t_e2e), 3), "unit": UNIT,

@@ -521,6 +521,23 @@ int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words);
 /* Build a set from coefficient-domain limbs [n][2][limbs][N] (residues < q_i). */
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
 
+/*
+ * he_ctset_import_async: he_ctset_import that does not wait for the copy, so
+ * that a caller streaming inputs can upload the next batch while the GPU still
+ * computes the current one. The host words [n][2][limbs][N] (coefficient
+ * domain) are copied on a copy stream of the context into one of two device
+ * staging buffers the context keeps (allocated on first use and grown to the
+ * largest import, freed with the context); the context's stream waits for the
+ * copy, range-checks the residues, takes them into the new set and transforms
+ * them. The host words must stay unchanged until the copy has completed, which
+ * is certain once the context has been synchronised (he_ctx_synchronize, an
+ * export, a decryption); page-locked host memory lets the copy overlap the
+ * computation. Out-of-range residues are reported as HE_E_ARG by that
+ * synchronisation. Refused (HE_E_STATE) inside a capture of the context's
+ * stream. The paper has no counterpart (an interface for streaming callers).
+ */
+int he_ctset_import_async(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
+
 /* Copy out the device words as held, [n][polys][limbs][N] in the NTT domain
  * (no transform). n_words must be at least n * polys * limbs * N.
  * Synchronises. */

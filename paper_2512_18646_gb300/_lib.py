@@ -116,6 +116,7 @@ SIGNATURES = {
     "he_ctset_import_raw": (I, [V, P_U64, I, I, D, PV]),
     "he_ctset_info": (I, [V, P_I, P_I, P_D, P_I]),
     "he_ctset_device_ptr": (I, [V, ctypes.POINTER(P_U64)]),
+    "he_ctset_import_async": (I, [V, P_U64, I, I, D, PV]),
     "he_ctset_export_words": (I, [V, P_U64, I, SZ]),
     "he_ctset_import_words": (I, [V, P_U64, I, I, I, I, D, PV]),
     "he_ctset_slice": (I, [V, V, I, I, PV]),

@@ -277,6 +277,13 @@ class Context:
         n, _, limbs, _ = host.shape
         return self._set(load().he_ctset_import, self.h, _ptr(host, P_U64), n, limbs, scale)
 
+    def import_coeffs_async(self, host, scale: float) -> CtSet:
+        """import_coeffs without waiting for the copy (he_ctset_import_async): `host` (page-locked
+        for overlap) must stay unchanged until the context is next synchronised."""
+        assert host.dtype == np.uint64 and host.flags.c_contiguous
+        n, _, limbs, _ = host.shape
+        return self._set(load().he_ctset_import_async, self.h, _ptr(host, P_U64), n, limbs, scale)
+
     # ---- evaluation ----
     def matmul(self, A: CtSet, B: CtSet, m: int, p: int) -> CtSet:
         return self._set(load().he_matmul, self.h, A.h, B.h, m, p)

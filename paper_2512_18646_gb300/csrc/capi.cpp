@@ -938,6 +938,15 @@ int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes) {
   });
 }
 
+int he_ctset_import_async(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx && host && out, HE_E_ARG, "null argument");
+    REQUIRE(scale > 0, HE_E_ARG, "scale must be positive");
+    *out = wrap(import_async(ctx->c, host, n, limbs, scale));
+  });
+}
+
 int he_ctset_export_raw(const he_ctset* set, uint64_t* host, size_t n_words) {
   return guard([&] {
     HANDLE(set);

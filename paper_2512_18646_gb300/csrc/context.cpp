@@ -136,6 +136,19 @@ Staging::~Staging() {
   }
 }
 
+ImportRing::~ImportRing() {
+  if (!copy) return;
+  cudaStreamSynchronize(copy);
+  for (int k = 0; k < 2; k++) {
+    if (pending[k]) cudaEventSynchronize(consumed[k]);
+    if (buf[k]) cudaFree(buf[k]);
+    cudaEventDestroy(copied[k]);
+    cudaEventDestroy(consumed[k]);
+  }
+  if (bad) cudaFree(bad);
+  cudaStreamDestroy(copy);
+}
+
 void upload_async(Ctx& C, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
   // A capture of the context's stream, opened by he_graph_begin or by the caller directly (its own
@@ -671,6 +684,14 @@ void check_device_status(Ctx& C) {
     HE_CUDA(cudaMemset(C.d_status.p, 0, 8));
     throw Error(6 /* HE_E_TIMEOUT */, "a device-side wait of a tensor-core kernel exceeded its limit");
   }
+  if (C.imports.bad) {
+    unsigned long long nbad = 0;
+    HE_CUDA(cudaMemcpy(&nbad, C.imports.bad, 8, cudaMemcpyDeviceToHost));
+    if (nbad) {
+      HE_CUDA(cudaMemset(C.imports.bad, 0, 8));
+      throw Error(1, std::to_string(nbad) + " residues out of range in an asynchronous import");
+    }
+  }
 }
 
 void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
@@ -695,11 +716,11 @@ void export_words(Ctx& C, const CtSet& s, u64* dst, bool on_device) {
   check_device_status(C);
 }
 
-// residues of rows [n_rows][limbs][N] checked against their primes on the device
-static void check_residues(Ctx& C, const u64* p, size_t n_rows, int limbs) {
+// residues of n_polys polynomials [n_polys][limbs][N] checked against their primes on the device
+static void check_residues(Ctx& C, const u64* p, size_t n_polys, int limbs) {
   DevBuf bad(1, C.stream);
   HE_CUDA(cudaMemsetAsync(bad.p, 0, 8, C.stream));
-  k_check_range(C, p, n_rows, limbs, (unsigned long long*)bad.p);
+  k_check_range(C, p, n_polys * limbs, limbs, (unsigned long long*)bad.p);
   unsigned long long nbad = 0;
   HE_CUDA(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
@@ -713,6 +734,49 @@ std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, 
   // residues are checked on the device before the transform
   check_residues(C, s->buf.p, (size_t)n * 2, limbs);
   if (!ntt_domain) ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
+  return s;
+}
+
+std::unique_ptr<CtSet> import_async(Ctx& C, const u64* host, int n, int limbs, double scale) {
+  if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HE_CUDA(cudaStreamIsCapturing(C.stream, &cs));
+  if (C.capturing || cs != cudaStreamCaptureStatusNone) {
+    C.capture_failed = C.capture_failed || C.capturing;
+    throw Error(9 /* HE_E_STATE */, "an import copies host data and cannot run inside a capture of the context's stream");
+  }
+  ImportRing& R = C.imports;
+  if (!R.copy) {
+    HE_CUDA(cudaStreamCreateWithFlags(&R.copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+      HE_CUDA(cudaEventCreateWithFlags(&R.copied[k], cudaEventDisableTiming));
+      HE_CUDA(cudaEventCreateWithFlags(&R.consumed[k], cudaEventDisableTiming));
+    }
+    HE_CUDA(cudaMalloc(&R.bad, 8));
+    HE_CUDA(cudaMemset(R.bad, 0, 8));
+  }
+  const size_t words = (size_t)n * 2 * limbs * C.N;
+  const int k = R.next;
+  R.next ^= 1;
+  if (R.words[k] < words) {  // grow the buffer once its last reader is done
+    if (R.pending[k]) HE_CUDA(cudaEventSynchronize(R.consumed[k]));
+    if (R.buf[k]) HE_CUDA(cudaFree(R.buf[k]));
+    R.buf[k] = nullptr;
+    R.words[k] = 0;
+    HE_CUDA(cudaMalloc(&R.buf[k], words * 8));
+    R.words[k] = words;
+  }
+  // the copy waits for the previous reader of the buffer only, not for the context's stream
+  if (R.pending[k]) HE_CUDA(cudaStreamWaitEvent(R.copy, R.consumed[k], 0));
+  HE_CUDA(cudaMemcpyAsync(R.buf[k], host, words * 8, cudaMemcpyHostToDevice, R.copy));
+  HE_CUDA(cudaEventRecord(R.copied[k], R.copy));
+  HE_CUDA(cudaStreamWaitEvent(C.stream, R.copied[k], 0));
+  auto s = new_set(C, n, 2, limbs, scale);
+  k_check_range(C, R.buf[k], (size_t)n * 2 * limbs, limbs, R.bad);  // every limb row
+  HE_CUDA(cudaMemcpyAsync(s->buf.p, R.buf[k], words * 8, cudaMemcpyDeviceToDevice, C.stream));
+  HE_CUDA(cudaEventRecord(R.consumed[k], C.stream));
+  R.pending[k] = true;
+  ntt_forward(C, s->buf.p, n * 2, limbs_q(limbs, C.N));
   return s;
 }
 

@@ -102,6 +102,25 @@ struct Staging {
   ~Staging();
 };
 
+// Device staging of overlapped imports (he_ctset_import_async): host words are copied into one of
+// two device buffers on a copy stream of their own, so that the copy runs while the context's
+// stream still computes; the context's stream waits for the copy, checks and takes the words, and
+// marks the buffer free for the import after next. Out-of-range residues are counted in `bad` and
+// reported at the next synchronisation.
+struct ImportRing {
+  cudaStream_t copy = nullptr;
+  u64* buf[2] = {};
+  size_t words[2] = {};
+  cudaEvent_t copied[2] = {}, consumed[2] = {};
+  bool pending[2] = {};  // consumed[k] recorded since buffer k was last filled
+  int next = 0;
+  unsigned long long* bad = nullptr;
+  ImportRing() = default;
+  ImportRing(const ImportRing&) = delete;
+  ImportRing& operator=(const ImportRing&) = delete;
+  ~ImportRing();
+};
+
 struct Ctx {
   int device = 0;
   int log_n = 0;
@@ -145,6 +164,7 @@ struct Ctx {
   std::vector<std::unique_ptr<CtSet>> deferred;
 
   Staging staging;
+  ImportRing imports;
 
   // keys
   bool has_keys = false;
@@ -333,6 +353,9 @@ void export_words(Ctx& C, const CtSet& s, u64* dst, bool on_device);
 // buffer, range-checked
 std::unique_ptr<CtSet> import_words(Ctx& C, const u64* src, bool on_device, int n, int polys, int limbs,
                                     double scale);
+// he_ctset_import without waiting: the copy overlaps the work already queued on the context's
+// stream; range errors are reported at the next synchronisation
+std::unique_ptr<CtSet> import_async(Ctx& C, const u64* host, int n, int limbs, double scale);
 // [n][2][limbs][N] residues, coefficient domain (or already NTT domain), range-checked
 std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, double scale,
                                      bool ntt_domain = false);

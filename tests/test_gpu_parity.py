@@ -824,6 +824,44 @@ def test_device_wait_that_runs_out_is_reported_and_the_context_stays_usable(lib)
         assert load().he_debug_wait_timeout(g.h, bad) == HE_E_ARG
 
 
+def test_overlapped_import_equals_import_and_reports_bad_residues_later(lib):
+    """he_ctset_import_async (the copy on a stream of its own, two staging buffers taken in turn)
+    gives the same words as he_ctset_import over three imports interleaved with computation; an
+    out-of-range residue is reported as HE_E_ARG by the next synchronisation, after which the
+    context keeps working."""
+    import torch
+    from paper_2512_18646_gb300 import HeError
+    from paper_2512_18646_gb300._lib import HE_E_ARG
+    o, g = make_pair(10, (60, 45, 45), 2, 60, 2, 45.0, seed=13, steps=[1])
+    rng = np.random.default_rng(13)
+    hosts = []
+    for t in range(3):
+        a = np.stack([np.stack([rng.integers(0, q, g.N, dtype=np.uint64) for q in g.primes[:3]]) for _ in range(2)])
+        buf = torch.empty(a.size, dtype=torch.int64).pin_memory().numpy().view(np.uint64).reshape(1, 2, 3, g.N)
+        buf[...] = a[None]
+        hosts.append(buf)
+    outs = []
+    for t in range(3):
+        x = g.import_coeffs_async(hosts[t], g.scale)
+        outs.append((x, g.rotate(x, [1])))  # computation queued behind the import
+    for t in range(3):
+        ref = g.import_coeffs(hosts[t], g.scale)
+        assert np.array_equal(outs[t][0].export_raw(), ref.export_raw())
+        assert np.array_equal(outs[t][1].export_raw(), g.rotate(ref, [1]).export_raw())
+    for at in ((0, 1, 2, 5), (0, 1, 2, g.N - 1), (0, 0, 0, 0)):
+        bad = hosts[0].copy()
+        bad[at] = np.uint64(g.primes[at[2]])  # a residue equal to its prime
+        g.import_coeffs_async(bad, g.scale)
+        with pytest.raises(HeError) as e:
+            g.synchronize()
+        assert e.value.code == HE_E_ARG
+        g.synchronize()  # reported once
+        with pytest.raises(HeError) as e:
+            g.import_coeffs(bad, g.scale)
+        assert e.value.code == HE_E_ARG
+    assert np.array_equal(g.import_coeffs_async(hosts[1], g.scale).export_raw(), outs[1][0].export_raw())
+
+
 def test_direct_capture_of_the_context_stream_is_refused_loudly(lib):
     """A capture the caller opens on the context's stream itself (torch's CUDA graph on that stream,
     not he_graph_begin) must not record a copy from the context's page-locked staging slots, which

@@ -108,14 +108,15 @@ def test_words_move_through_host_and_device_buffers(lib):
         y = g.import_words(src, n, polys, limbs, scale)
         assert y.info4() == (n, limbs, scale, polys)
         assert np.array_equal(y.export_raw(), raw)
-    bad = host.copy()
-    bad[g.N + 3] = np.uint64(g.primes[1])  # limb 1 of component 0 holds its own prime
-    with pytest.raises(HeError) as e:
-        g.import_words(bad, n, polys, limbs, scale)
-    assert e.value.code == HE_E_ARG
-    with pytest.raises(HeError) as e:
-        g.import_words(torch.from_numpy(bad.view(np.int64)).cuda(), n, polys, limbs, scale)
-    assert e.value.code == HE_E_ARG
+    for at, prime in ((g.N + 3, 1), (raw.size - 1, limbs - 1)):  # an early row; the very last word
+        bad = host.copy()
+        bad[at] = np.uint64(g.primes[prime])  # a residue equal to its prime
+        with pytest.raises(HeError) as e:
+            g.import_words(bad, n, polys, limbs, scale)
+        assert e.value.code == HE_E_ARG
+        with pytest.raises(HeError) as e:
+            g.import_words(torch.from_numpy(bad.view(np.int64)).cuda(), n, polys, limbs, scale)
+        assert e.value.code == HE_E_ARG
 
 
 # ---------------------------------------------------------------------------
