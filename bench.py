@@ -445,6 +445,7 @@ def run_matmul(args, rank, world, local_rank):
     g.matmul_volley(g.encrypt_matrix_a_volley(np.ones((4, 4)), 4, 0), wb)
     t_batched = t_plain = t_volley = t_bsgs = 0.0
     launches_b = launches_v = 0
+    wave0_prof = {}
     max_err = max_err_v = 0.0
     rng_seed = 402
     clk = ClockSampler(local_rank).__enter__()
@@ -474,6 +475,22 @@ def run_matmul(args, rank, world, local_rank):
             return None
         _, dt = timed(plain)
         t_plain += dt
+        if wave is waves[0]:
+            # where the time goes in both revolver modes: per-kernel device time (CUDA events per
+            # launch) against the elapsed time of the same call, repeated once with the profiler on
+            for mode, fn in (("batched", lambda: g.matmul_batched(As, Bs, ms, ps)), ("plain", plain)):
+                profile_read(lib)
+                lib.he_profile_enable(1)
+                r_, dt_ = timed(fn)
+                del r_
+                prof = profile_read(lib)
+                lib.he_profile_enable(0)
+                dev = sum(v["ms"] for v in prof.values())
+                top = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:4]
+                wave0_prof[mode] = {"products": len(wave), "elapsed_ms": round(1e3 * dt_, 1),
+                                    "kernel_ms": round(dev, 1), "busy_frac": round(dev / (1e3 * dt_), 3),
+                                    "launches": int(sum(v["launches"] for v in prof.values())),
+                                    "top_kernels_ms": {k: round(v["ms"], 1) for k, v in top}}
 
         def bsgs():
             for t in range(len(wave)):
@@ -516,7 +533,7 @@ def run_matmul(args, rank, world, local_rank):
             "revolver_launches": launches_b, "revolver_max_abs_err": max_err, "keygen_s": keygen_s,
             "waves": len(waves), "revolver_rotations": rot, "revolver_tensors": sum(n * p for _, n, p in shapes),
             "volley_tensors": sum(G * n for G, (_, n, _) in zip(groups, shapes)), "volley_rotations": 0,
-            "clocks": clk.summary(), "shapes": shapes}
+            "clocks": clk.summary(), "shapes": shapes, "revolver_wave0_profile": wave0_prof}
 
 
 # ---------------------------------------------------------------------------
@@ -1424,7 +1441,8 @@ def main():
                                  "gpu_launches": res["revolver_launches"],
                                  "max_abs_err_vs_fp64": res["revolver_max_abs_err"],
                                  "rotations": res["revolver_rotations"],
-                                 "tensor_products": res["revolver_tensors"]},
+                                 "tensor_products": res["revolver_tensors"],
+                                 "wave0_profile": res["revolver_wave0_profile"]},
                     "keygen_s": res["keygen_s"], "waves": res["waves"], "clocks": res["clocks"],
                     "cpu_baseline": None if args.no_cpu_baseline or world > 1
                     else oracle_matmul_baseline(res["shapes"])}

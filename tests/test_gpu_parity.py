@@ -732,6 +732,24 @@ def test_matmul_batched_equals_single_matmuls(lib):
 
 
 
+def test_matmul_batched_matches_oracle_on_ragged_shapes(lib):
+    """he_matmul_batched over ragged shapes (some sharing p, so their B operands share launches),
+    each product bit-exact against the oracle's revolver matmul on the same ciphertexts."""
+    o, g = make_pair(10, (60, 40, 40), 1, 60, 1, 40.0, seed=17, steps=list(range(1, 8)))
+    rng = np.random.default_rng(17)
+    shapes = [(5, 3, 8), (8, 5, 4), (3, 2, 8), (16, 1, 1), (7, 6, 4), (1, 4, 2)]
+    ga_s, gb_s, oa_s, ob_s, mats = [], [], [], [], []
+    for t, (m, n, p) in enumerate(shapes):
+        A, Bm = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (n, p))
+        oa, ga = encrypt_both(o, g, encode_columns(o, layouts.matrix_a_columns(A, o.slots)), ct_id_base=1000 * t)
+        ob, gb = encrypt_both(o, g, encode_columns(o, layouts.matrix_b_rows(Bm, o.slots)), ct_id_base=1000 * t + 500)
+        ga_s.append(ga), gb_s.append(gb), oa_s.append(oa), ob_s.append(ob), mats.append(A @ Bm)
+    outs = g.matmul_batched(ga_s, gb_s, [s[0] for s in shapes], [s[2] for s in shapes])
+    for t, (m, n, p) in enumerate(shapes):
+        assert np.array_equal(outs[t].export(), o.matmul(oa_s[t], ob_s[t], p)), t
+        assert np.abs(g.decrypt_matrix(outs[t], m, p) - mats[t]).max() < 1e-5
+
+
 def test_graph_replays_batched_matmuls(lib):
     """A batched call captured into a CUDA graph: each replay recomputes the products from the
     current contents of the input sets, bit-identical to eager calls; in-place calls on sets made
