@@ -344,6 +344,9 @@ def run_gpu(args, rank, world, local_rank):
         pin_out = torch.empty(out_words, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
         import ctypes
         from paper_2512_18646_gb300._lib import P_U64, check
+        # the context's two import staging buffers are allocated by its first overlapped imports
+        for _ in range(2):
+            g.import_coeffs_async(pin_arr, g.scale).free()
         g.synchronize()
         t0 = time.perf_counter()
         # each step's ciphertexts are uploaded while the previous step computes (he_ctset_import_async

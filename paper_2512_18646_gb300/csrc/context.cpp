@@ -257,6 +257,10 @@ void ctx_init(Ctx& C, int log_n, const std::vector<int>& q_bits, int n_special, 
     u64 qi = 1;  // q^{-1} mod 2^64 by Newton iteration (q odd): each step doubles the correct bits
     for (int it = 0; it < 6; it++) qi *= 2 - q * qi;
     T.qinv_neg = (u64)0 - qi;
+    int qbits = 0;
+    while (qbits < 64 && (q >> qbits)) qbits++;
+    T.frd_sh = std::max(0, qbits + 9 - 32);
+    T.frd = (float)(std::ldexp(1.0, T.frd_sh) / (double)q);
     // psi = x^((q-1)/2N), x the smallest quadratic non-residue
     u64 x = 2;
     while (pow_h(x, (q - 1) / 2, q) != q - 1) x++;

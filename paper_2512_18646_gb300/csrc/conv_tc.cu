@@ -625,6 +625,11 @@ static size_t tc_smem_for(int T, int c_out, bool narrow) {
 bool conv_mac_tc_all(const Ctx& C, int c_in, int k, int c_out, int lp) {
   if (!C.use_tc || C.log_n < 7) return false;
   const long T = (long)c_in * k * k;
+  // below about 128 products per output column and word the CUDA-core kernels are faster: their
+  // cost is a few multiplies per product, the tensor path's a conversion per input word and a
+  // recombination per output (measured: 4 channels of 9 terms 20.5 ms on the CUDA cores against
+  // 22.7 ms here; 8 channels of 25 terms 13.0 against 11.9; 16 of 72, 28.2 against 10.7)
+  if (T * c_out < 128) return false;
   bool narrow = false, wide = false;
   for (int i = 0; i < lp; i++) (C.q[i] < kMac96Prime ? narrow : wide) = true;
   // the chunk sums below 2^24: NC T 127^2 (NC = 7 below kMac96Prime, 9 above); every channel

@@ -227,6 +227,22 @@ HE_HD u64 reduce4q(u64 a, u64 q) {
 }
 
 #if defined(__CUDACC__)
+// v mod q for v < 2^9 q, q < 2^54 (frd = 2^sh / q rounded to fp32, sh = max(0, bitlen(q) + 9 - 32)):
+// the quotient is estimated in fp32 from the top 32 bits of v. The estimate x of v / q has
+// |x - v / q| < 2^-13 (three fp32 roundings of a value below 512, and the dropped low bits worth
+// below 2^-22), so trunc(x) is floor(v / q) or one off either side; v - trunc(x) q is then in
+// [-q, 2q) and one correction makes it exact. One 32 x 64-bit product instead of a Shoup product.
+__device__ __forceinline__ u64 reduce_fp32(u64 v, u64 q, float frd, int sh) {
+  const u32 hi = (u32)(v >> sh);
+  const u32 t = __float2uint_rz(__fmul_rn(__uint2float_rn(hi), frd));
+  u64 r = v - (u64)t * q;
+  if ((long long)r < 0)
+    r += q;
+  else if (r >= q)
+    r -= q;
+  return r;
+}
+
 __device__ __forceinline__ u32 brv_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
 
 // Index j' with NTT(phi_k(a))[j] = NTT(a)[j'] for the bit-reversed evaluation

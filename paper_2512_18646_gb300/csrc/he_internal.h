@@ -67,6 +67,8 @@ struct PrimeTab {
   u64 one_sh;         // floor(2^64 / q): Shoup companion of 1 (x mod q in [0, 2q) for any word x)
   u64 mont_r, mont_r_sh;  // R = 2^64 mod q (Montgomery radix) and its Shoup companion
   u64 qinv_neg;           // -q^{-1} mod 2^64
+  float frd;              // 2^frd_sh / q in fp32: quotient estimates of reduce_fp32
+  int frd_sh;             // max(0, bitlen(q) + 9 - 32): the top 32 bits of a value below 2^9 q
 };
 
 // Constants of one launch over a batch of limbs. Limb i of each polynomial

@@ -287,7 +287,7 @@ constexpr int kRowThreads = 256;
 // kernel's growing range); outputs in [0, q).
 template <int LOGM, int MODE, bool NAR>
 __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, const u64* tw, int n, int n1, u64 run,
-                                              u64 q, u64 one_sh, const LimbMap& lm, const Fuse& fz) {
+                                              u64 q, float frd, int frd_sh, const LimbMap& lm, const Fuse& fz) {
   using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   const size_t N = (size_t)1 << n;
@@ -295,7 +295,8 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
   auto sync = [] { __syncwarp(__activemask()); };
   // the transform's result reduced to [0, q) (growing range: the cheaper quotient estimate
   // leaves [0, 4q), as the lazy butterflies do)
-  auto fin = [q, one_sh](u64 v) { return reduce4q(NAR ? shoup_approx(v, 1, one_sh, q) : v, q); };
+  // (growing range: values below 72 q, reduced by an fp32 quotient estimate; Harvey: [0, 4q))
+  auto fin = [q, frd, frd_sh](u64 v) { return NAR ? reduce_fp32(v, q, frd, frd_sh) : reduce4q(v, q); };
   // exact products of the fused epilogues, by way of [0, 4q)
   auto mulq = [q](u64 v, u64 w, u64 wp) { return reduce4q(shoup_approx(v, w, wp, q), q); };
   // a multiple of q above every transform output (72q growing range, 4q Harvey), so that
@@ -375,7 +376,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, Limb
   const size_t N = (size_t)1 << n;
   int prime;
   u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q, one_sh = pt[prime].one_sh;
+  const u64 q = pt[prime].mod.q;
+  const float frd = pt[prime].frd;
+  const int frd_sh = pt[prime].frd_sh;
   const u64* tw = tw_all + (size_t)prime * 2 * N;
   const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
   const u64 run = (u64)blockIdx.x * RUNS + r_cta;
@@ -386,16 +389,16 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_fwd_rows(u64* data, Limb
   const int rw = (threadIdx.x & 31) / P::T;  // run index inside the warp
   u64* smw = sm + warp * 32 * P::E;
   if (q < kNarrowPrime)
-    fwd_rows_body<LOGM, MODE, true>(xr, smw, rw, u, tw, n, n1, run, q, one_sh, lm, fz);
+    fwd_rows_body<LOGM, MODE, true>(xr, smw, rw, u, tw, n, n1, run, q, frd, frd_sh, lm, fz);
   else
-    fwd_rows_body<LOGM, MODE, false>(xr, smw, rw, u, tw, n, n1, run, q, one_sh, lm, fz);
+    fwd_rows_body<LOGM, MODE, false>(xr, smw, rw, u, tw, n, n1, run, q, frd, frd_sh, lm, fz);
 }
 
 // inverse, first n2 stages (smallest distances) inside runs; inputs below 2q,
 // outputs in [0, 2q)
 template <int LOGM, bool NAR>
 __device__ __forceinline__ void inv_rows_body(const u64* xs, u64* xr, u64* smw, int rw, int u, const u64* tw, int n1,
-                                              u64 run, u64 q, u64 one_sh) {
+                                              u64 run, u64 q, float frd, int frd_sh) {
   using P = Plan<LOGM, kRowKB>;
   constexpr int M = 1 << LOGM;
   auto addr = [rw](int e) { return swz(rw * M + e); };
@@ -412,7 +415,8 @@ __device__ __forceinline__ void inv_rows_body(const u64* xs, u64* xr, u64* smw, 
   using M0 = RMap<LOGM, 0, kRowKB>;
   const int x0 = M0::upart(u);
 #pragma unroll
-  for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = NAR ? shoup_lazy(a[k], 1, one_sh, q) : a[k];
+  // growing range: below 2^9 q after these stages, reduced to [0, q) (within the next kernel's [0, 2q) inputs)
+  for (int k = 0; k < P::E; k++) xr[x0 | M0::kbits(k)] = NAR ? reduce_fp32(a[k], q, frd, frd_sh) : a[k];
 }
 
 template <int LOGM>
@@ -425,7 +429,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, Limb
   const size_t N = (size_t)1 << n;
   int prime;
   u64* x = row_ptr(data, lm, blockIdx.y, N, prime);
-  const u64 q = pt[prime].mod.q, one_sh = pt[prime].one_sh;
+  const u64 q = pt[prime].mod.q;
+  const float frd = pt[prime].frd;
+  const int frd_sh = pt[prime].frd_sh;
   const u64* tw = tw_all + (size_t)prime * 2 * N;
   const int r_cta = threadIdx.x / P::T, u = threadIdx.x - r_cta * P::T;
   const u64 run = (u64)blockIdx.x * RUNS + r_cta;
@@ -440,9 +446,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_ntt_inv_rows(u64* data, Limb
   const int rw = (threadIdx.x & 31) / P::T;
   u64* smw = sm + warp * 32 * P::E;
   if (q < kNarrowPrime)
-    inv_rows_body<LOGM, true>(xs, xr, smw, rw, u, tw, n1, run, q, one_sh);
+    inv_rows_body<LOGM, true>(xs, xr, smw, rw, u, tw, n1, run, q, frd, frd_sh);
   else
-    inv_rows_body<LOGM, false>(xs, xr, smw, rw, u, tw, n1, run, q, one_sh);
+    inv_rows_body<LOGM, false>(xs, xr, smw, rw, u, tw, n1, run, q, frd, frd_sh);
 }
 
 // ---------------------------------------------------------------------------

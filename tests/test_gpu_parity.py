@@ -301,14 +301,16 @@ def test_conv2d_96bit_sums_reduce_mid_sum_and_run_two_channel_passes(lib, c_out,
     assert np.abs(got - ref).max() < 1e-4
 
 
-@pytest.mark.parametrize("c_in,k,stride,c_out,polys", [(8, 3, 2, 16, 3), (1, 5, 2, 8, 2), (2, 3, 1, 5, 2),
-                                                        (8, 3, 2, 11, 2), (9, 3, 1, 4, 2), (10, 3, 2, 3, 2)])
+@pytest.mark.parametrize("c_in,k,stride,c_out,polys", [(8, 3, 2, 16, 3), (1, 5, 2, 8, 2), (2, 3, 1, 8, 2),
+                                                        (8, 3, 2, 11, 2), (9, 3, 1, 4, 2), (10, 3, 2, 3, 2),
+                                                        (2, 3, 1, 5, 2)])
 def test_conv_tensor_cores_equal_cuda_cores_and_oracle(lib, c_in, k, stride, c_out, polys):
     """The convolution's multiply-accumulate on the tensor cores (residues cut into bytes (45-bit
     primes) or 7-bit chunks (60-bit primes) whose products the tensor cores sum exactly in fp32,
     recombined modulo q) and on the CUDA cores give the same words, bit-exact with the oracle:
     8, 16 and ragged channel counts, 72, 25 and 18 terms, 81 (the last term count the byte chunks
-    take) and 90 (past it: the CUDA cores), two- and three-component inputs."""
+    take) and 90 (past it: the CUDA cores), a layer too small for the tensor path (5 channels of 18
+    terms: the CUDA cores), two- and three-component inputs."""
     o, g = make_pair(10, (60,) + (45,) * 6, 2, 60, 2, 45.0, seed=47, steps=list(range(1, k)))
     H, side, Bn, gap = 32, 13, 3, 1
     rng = np.random.default_rng(47 + c_out + c_in)
