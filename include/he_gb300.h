@@ -105,10 +105,13 @@ int he_ctx_set_work_budget(he_ctx* ctx, size_t bytes);
  * Whether the convolution's ciphertext-scalar multiply-accumulate (Alg. 4's
  * sum over channels and kernel offsets, he_conv2d) runs on the tensor cores
  * (on != 0, the default) or on the CUDA cores. The tensor-core form splits
- * the residues into 7-bit chunks whose products the tensor cores sum exactly
- * in fp32 and recombines the sums modulo q; it is taken where those sums stay
- * below 2^24 (c_in k^2 up to 148 terms for primes below 2^46, 115 above) and
- * N >= 128. Both forms compute the same words. Errors: HE_E_ARG.
+ * the residues into chunks (bytes for primes below 2^46, 7 bits above) whose
+ * products the tensor cores sum exactly in fp32 and recombines the sums modulo
+ * q; it is taken where those sums stay below 2^24 (c_in k^2 up to 85 terms
+ * below 2^46, 115 above), the weight tiles fit shared memory, the layer has
+ * at least 128 products per output column and coefficient (c_in k^2 c_out; the
+ * CUDA cores are faster below) and N >= 128. Both forms compute the same
+ * words. Errors: HE_E_ARG.
  */
 int he_ctx_set_tensor_cores(he_ctx* ctx, int on);
 
