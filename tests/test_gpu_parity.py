@@ -918,6 +918,23 @@ def test_direct_capture_of_the_context_stream_is_refused_loudly(lib):
             except RuntimeError:
                 refused = True
     assert refused
+    # the overlapped import is refused inside such a capture too (its copy reads host memory)
+    host = np.ascontiguousarray(x.export())
+    refused = False
+    gr1 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gr1.capture_begin()
+        try:
+            g.import_coeffs_async(host, g.scale)
+        except HeError:
+            refused = True
+        finally:
+            try:
+                gr1.capture_end()
+            except RuntimeError:
+                refused = True
+    assert refused
+    assert np.array_equal(g.import_coeffs_async(host, g.scale).export(), host)  # usable afterwards
     # a call without host uploads captures and replays bit-identically
     y = g.conv2d(x, 1, 1, K, bias, 1)
     g.synchronize()
