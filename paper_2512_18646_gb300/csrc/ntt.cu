@@ -351,14 +351,23 @@ __device__ __forceinline__ void fwd_rows_body(u64* xr, u64* smw, int rw, int u, 
     // brv_L(xl) | brv_L(kbits(k)) (disjoint bits), so only a constant is or-ed per element
     const u32 hb = (brv_bits((u32)xl, LOGM) << (n - LOGM)) | (n > LOGM ? brv_bits((u32)run, n - LOGM) : 0u);
     const u32 mask = (2u << n) - 1, gk = (u32)fz.gk;
+    // (2 (hb | c) + 1) gk = (2 hb + 1) gk + 2 c gk (disjoint bits): one product per thread, and per
+    // element the constant 2 c gk, c = brv(kbits(k)) 2^(n-L), as a sum of the products for its bits
+    const u32 e0 = (2 * hb + 1) * gk;
+    u32 gbit[P::KB];
+#pragma unroll
+    for (int b = 0; b < P::KB; b++) gbit[b] = (2 * gk * brv_const(ML::kbits(1 << b), LOGM)) << (n - LOGM);
 #pragma unroll
     for (int k = 0; k < P::E; k++) {
       const u32 j = (u32)(run * M) + (u32)(xl | ML::kbits(k));
       u32 src = j;
       if (gk != 1) {
-        const u32 bj = hb | (brv_const(ML::kbits(k), LOGM) << (n - LOGM));
-        const u32 e2 = ((2 * bj + 1) * gk) & mask;
-        src = brv_bits((e2 - 1) >> 1, n);
+        u32 e2 = e0;
+#pragma unroll
+        for (int b = 0; b < P::KB; b++)
+          if ((k >> b) & 1) e2 += gbit[b];
+        // brv_n((e2 - 1) / 2) = brev32(e2 - 1) >> (31 - n): e2 is odd, so bit 0 of e2 - 1 is clear
+        src = __brev((e2 & mask) - 1) >> (31 - n);
       }
       const u64 v = mulq(ui[src] + zq - a[k], pv, ps);
       oi[j] = add ? addmod(v, bi[fz.kmode == 0 ? j : src], q) : v;
