@@ -151,6 +151,9 @@ __global__ void k_add_kernel(const u64* a, const u64* b, u64* out, int n_polys, 
 
 // d[c] = (a0 b0, a0 b1 + a1 b0, a1 b1) for ciphertext c = blockIdx.y; a square (a = b)
 // takes one cross product, doubled, and reads one operand.
+// d = (a0 b0, a0 b1 + a1 b0, a1 b1) per word. Products by Montgomery's reduction (Math. Comp.
+// 1985): one operand is first put in Montgomery form by a Shoup product with R = 2^64 mod q, so
+// that redc(aR * b) = a b mod q exactly, cheaper than a 128-bit Barrett reduction per product.
 __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int limbs, const PrimeTab* pt, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const size_t LN = (size_t)limbs * N;
@@ -159,22 +162,33 @@ __global__ void k_tensor_kernel(const u64* a, const u64* b, u64* d, int n, int l
   const u64* B = b + c * 2 * LN;
   u64* D = d + c * 3 * LN;
   const bool square = a == b;
+  int limb = -1;  // the prime's constants are reloaded only when the stride crosses into another limb
+  u64 q = 0, R = 0, Rs = 0, qneg = 0;
   for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < LN; w += (size_t)gridDim.x * blockDim.x) {
-    const Mod md = pt[(int)(w >> log_n)].mod;
+    if ((int)(w >> log_n) != limb) {
+      limb = (int)(w >> log_n);
+      q = pt[limb].mod.q;
+      R = pt[limb].mont_r;
+      Rs = pt[limb].mont_r_sh;
+      qneg = pt[limb].qinv_neg;
+    }
+    auto mont = [&](u64 xr, u64 y) {  // xr y 2^-64 mod q for xr, y < q
+      u64 h, l;
+      mul128(xr, y, h, l);
+      return redc128(h, l, q, qneg);
+    };
     const u64 a0 = A[w], a1 = A[LN + w];
+    const u64 a0r = shoup(a0, R, Rs, q), a1r = shoup(a1, R, Rs, q);
     if (square) {
-      D[w] = mulmod(a0, a0, md);
-      const u64 t = mulmod(a0, a1, md);
-      D[LN + w] = addmod(t, t, md.q);
-      D[2 * LN + w] = mulmod(a1, a1, md);
+      D[w] = mont(a0r, a0);
+      const u64 t = mont(a0r, a1);
+      D[LN + w] = addmod(t, t, q);
+      D[2 * LN + w] = mont(a1r, a1);
     } else {
       const u64 b0 = B[w], b1 = B[LN + w];
-      D[w] = mulmod(a0, b0, md);
-      Acc128 acc{0, 0};
-      mac128(acc, a0, b1);
-      mac128(acc, a1, b0);
-      D[LN + w] = reduce128(acc.hi, acc.lo, md);
-      D[2 * LN + w] = mulmod(a1, b1, md);
+      D[w] = mont(a0r, b0);
+      D[LN + w] = addmod(mont(a0r, b1), mont(a1r, b0), q);
+      D[2 * LN + w] = mont(a1r, b1);
     }
   }
 }
