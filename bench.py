@@ -16,7 +16,8 @@ engine. Inputs are synthetic (seeded), already encrypted and resident in
 device memory when the timed region starts; they are larger than L2.
 
 The default run (N = 1) also measures the other configurations of the
-method, each in a process of its own before the CNN runs, and reports each
+method, each in a process of its own after the CNN's measurement (which
+releases its device memory first), and reports each
 JSON line whole under "workloads": 4096 small matmuls A(4x8) B(8x4) at
 N = 2^13 (plain calls, one batched call, its CUDA graph); one conv + x^2 layer
 on 64x64 images at N = 2^15; 64 matmuls of uneven m, n, p at N = 2^16
@@ -1241,8 +1242,9 @@ EXTRA_WORKLOADS = (
 
 
 def run_extra_workloads(args):
-    """Each configuration in a process of its own (its device memory is returned when it exits), before
-    the CNN touches the GPU; its JSON line (with its own clocks and oracle baseline) is kept whole."""
+    """Each configuration in a process of its own (its device memory is returned when it exits), after
+    the CNN's measurement has released its device memory; its JSON line (with its own clocks and
+    oracle baseline) is kept whole."""
     out = {}
     for key, wl, extra in EXTRA_WORKLOADS:
         cmd = [sys.executable, os.path.abspath(__file__), "--workload", wl, *extra]
@@ -1501,12 +1503,22 @@ def main():
         print(json.dumps(line))
         return
 
-    extras = None
-    if world == 1 and not args.no_extra:
-        extras = run_extra_workloads(args)
     res = run_gpu(args, rank, world, local_rank)
     if rank != 0:
         return
+    extras = None
+    if world == 1 and not args.no_extra:
+        # the CNN's context went out of scope with run_gpu: release its device memory first
+        import gc
+
+        import torch
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free, total = torch.cuda.mem_get_info()
+        sys.stderr.write(f"[bench] device memory free before the extra workloads: {free / 2**30:.1f} of "
+                         f"{total / 2**30:.1f} GiB\n")
+        extras = run_extra_workloads(args)
     cpu = None
     max_err = None
     if not args.no_cpu_baseline:

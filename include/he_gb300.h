@@ -83,6 +83,13 @@ typedef struct {
  * HE_E_OOM on device failures.
  */
 int he_ctx_create(const he_params_desc* desc, uint64_t seed, void* cuda_stream, he_ctx** out);
+/*
+ * he_ctx_destroy: wait for the context's stream, free its keys, tables and
+ * staging buffers, then return the unused part of the device's default memory
+ * pool to the driver (a context keeps freed pool memory cached while it lives;
+ * memory still held by other contexts' ciphertexts is not touched). A null or
+ * already destroyed handle is ignored.
+ */
 void he_ctx_destroy(he_ctx* ctx);
 
 /* Block until all work enqueued on the context's stream has finished. */

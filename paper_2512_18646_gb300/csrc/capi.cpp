@@ -108,8 +108,16 @@ int he_ctx_create(const he_params_desc* d, uint64_t seed, void* cuda_stream, he_
 void he_ctx_destroy(he_ctx* ctx) {
   if (ctx && !handle_live(ctx)) return;
   if (!ctx) return;
-  cudaStreamSynchronize(ctx->c.stream);
+  const cudaStream_t st = ctx->c.stream;
+  const int dev = ctx->c.device;
+  cudaStreamSynchronize(st);
   delete ctx;
+  // the buffers were freed in stream order: once the stream has passed the frees, hand the pool's
+  // cached memory back (the release threshold set at creation keeps it otherwise)
+  cudaStreamSynchronize(st);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  cudaGetLastError();
 }
 
 int he_ctx_synchronize(he_ctx* ctx) {

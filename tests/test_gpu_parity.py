@@ -987,6 +987,27 @@ def test_work_budget_chunks_are_bit_identical(lib):
         assert np.array_equal(a, b)
 
 
+def test_destroy_returns_cached_pool_memory(lib):
+    """Freed ciphertexts stay cached in the device's memory pool while their context lives; destroying
+    the context hands that memory back to the driver, so a later process or context can use it."""
+    import torch
+    from paper_2512_18646_gb300 import api
+    torch.cuda.init()
+    api.Context(14, (60, 45, 45, 45), 2, 60, 2, 45.0, seed=3).close()  # start from a trimmed pool
+    free0, _ = torch.cuda.mem_get_info()
+    g = api.Context(14, (60, 45, 45, 45), 2, 60, 2, 45.0, seed=3)
+    g.keygen([])
+    x = g.encrypt_coeffs(np.zeros((256, g.N), np.int64), 4, g.scale)   # 256 MiB of ciphertexts
+    x.free()
+    g.synchronize()
+    held, _ = torch.cuda.mem_get_info()
+    assert held < free0 - (200 << 20)       # still cached after the free
+    g.close()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 > held + (200 << 20)
+    assert free1 > free0 - (64 << 20)
+
+
 def test_table1_network_single_ciphertext(lib):
     """Table I's CNN (CONV, ACT-1, FC-1, ACT-2, FC-2) in the paper's single-ciphertext layout at a
     reduced size (N = 2^11: 16 images of 6 x 6 in 8 x 8 blocks, 2 kernels 3 x 3, FC-1 from 2 x 4 x 4
