@@ -528,6 +528,30 @@ int he_decrypt_image(he_ctx* ctx, const he_ctset* in, int batch, int block_strid
  * n * polys * limbs * N. Synchronises. */
 int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words);
 
+/*
+ * he_ctset_export_async: he_ctset_export that does not wait, so that a caller
+ * streaming results can queue the next batch while this one is still on the
+ * GPU. The inverse transform and the copy into `host` ([n][polys][limbs][N],
+ * coefficient domain, n_words as for he_ctset_export) are queued on the
+ * context's stream after the work already there; *ticket receives a number
+ * above 0 that grows with every export of the context. The words may be read
+ * once he_ctset_export_wait has returned for that ticket (or the context has
+ * been synchronised). The set may be freed right after the call: its release
+ * is ordered after the copy. Page-locked host memory lets the call return at
+ * once; with pageable memory the copy completes before the call returns.
+ * Refused (HE_E_STATE) inside a capture of the context's stream. The paper
+ * has no counterpart (an interface for streaming callers).
+ */
+int he_ctset_export_async(const he_ctset* set, uint64_t* host, size_t n_words, uint64_t* ticket);
+
+/*
+ * he_ctset_export_wait: block until the export with this ticket, and every
+ * earlier export of the context, has reached host memory; a device error
+ * raised meanwhile is reported as by he_ctx_synchronize. HE_E_ARG for 0 or a
+ * ticket the context has not issued.
+ */
+int he_ctset_export_wait(he_ctx* ctx, uint64_t ticket);
+
 /* Build a set from coefficient-domain limbs [n][2][limbs][N] (residues < q_i). */
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out);
 

@@ -111,6 +111,8 @@ SIGNATURES = {
     "he_decrypt_matrix_volley": (I, [V, V, I, I, P_D]),
     "he_decrypt_image": (I, [V, V, I, I, I, I, P_D, SZ]),
     "he_ctset_export": (I, [V, P_U64, SZ]),
+    "he_ctset_export_async": (I, [V, P_U64, SZ, P_U64]),
+    "he_ctset_export_wait": (I, [V, U64]),
     "he_ctset_import": (I, [V, P_U64, I, I, D, PV]),
     "he_ctset_export_raw": (I, [V, P_U64, SZ]),
     "he_ctset_import_raw": (I, [V, P_U64, I, I, D, PV]),

@@ -85,6 +85,16 @@ class CtSet:
         check(load().he_ctset_export(self.h, _ptr(out, P_U64), out.size))
         return out
 
+    def export_async(self, out: np.ndarray) -> int:
+        """Queue export() into `out` ([n][polys][limbs][N] uint64, page-locked for overlap) without
+        waiting (he_ctset_export_async); returns the ticket Context.export_wait takes. `out` must
+        not be read before that wait."""
+        n, limbs, _, polys = self.info4()
+        assert out.dtype == np.uint64 and out.flags.c_contiguous and out.size >= n * polys * limbs * self.ctx.N
+        t = ctypes.c_uint64()
+        check(load().he_ctset_export_async(self.h, _ptr(out, P_U64), out.size, ctypes.byref(t)))
+        return t.value
+
     def export_raw(self, out: Optional[np.ndarray] = None) -> np.ndarray:
         """The device words as held, [n][polys][limbs][N] uint64 in the NTT domain."""
         n, limbs, _, polys = self.info4()
@@ -194,6 +204,10 @@ class Context:
 
     def synchronize(self):
         check(load().he_ctx_synchronize(self.h))
+
+    def export_wait(self, ticket: int):
+        """Block until CtSet.export_async's copy with this ticket (and every earlier one) is on the host."""
+        check(load().he_ctset_export_wait(self.h, int(ticket)))
 
     def close(self):
         if getattr(self, "h", None):

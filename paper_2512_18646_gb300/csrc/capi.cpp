@@ -906,6 +906,23 @@ int he_ctset_export(const he_ctset* set, uint64_t* host, size_t n_words) {
   });
 }
 
+int he_ctset_export_async(const he_ctset* set, uint64_t* host, size_t n_words, uint64_t* ticket) {
+  return guard([&] {
+    HANDLE(set);
+    REQUIRE(set && host && ticket, HE_E_ARG, "null argument");
+    REQUIRE(n_words >= set->s->buf.words, HE_E_ARG, "output too small");
+    *ticket = export_async(*set->s->ctx, *set->s, host);
+  });
+}
+
+int he_ctset_export_wait(he_ctx* ctx, uint64_t ticket) {
+  return guard([&] {
+    HANDLE(ctx);
+    REQUIRE(ctx, HE_E_ARG, "null context");
+    export_wait(ctx->c, ticket);
+  });
+}
+
 int he_ctset_import(he_ctx* ctx, const uint64_t* host, int n, int limbs, double scale, he_ctset** out) {
   return guard([&] {
     HANDLE(ctx);

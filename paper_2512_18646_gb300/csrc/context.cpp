@@ -149,6 +149,14 @@ ImportRing::~ImportRing() {
   cudaStreamDestroy(copy);
 }
 
+ExportRing::~ExportRing() {
+  for (int k = 0; k < kSlots; k++)
+    if (done[k]) {
+      cudaEventSynchronize(done[k]);
+      cudaEventDestroy(done[k]);
+    }
+}
+
 void upload_async(Ctx& C, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
   // A capture of the context's stream, opened by he_graph_begin or by the caller directly (its own
@@ -707,6 +715,46 @@ void export_coeffs(Ctx& C, const CtSet& s, u64* host) {
   check_device_status(C);
 }
 
+// copies into host memory cannot be replayed from a graph of the context's stream
+static void refuse_under_capture(Ctx& C, const char* what) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HE_CUDA(cudaStreamIsCapturing(C.stream, &cs));
+  if (C.capturing || cs != cudaStreamCaptureStatusNone) {
+    C.capture_failed = C.capture_failed || C.capturing;
+    throw Error(9 /* HE_E_STATE */, std::string(what) + " cannot run inside a capture of the context's stream");
+  }
+}
+
+uint64_t export_async(Ctx& C, const CtSet& s, u64* host) {
+  refuse_under_capture(C, "an export copies to host memory and");
+  ExportRing& E = C.exports;
+  const uint64_t ticket = E.issued + 1;
+  const int k = (int)(ticket % ExportRing::kSlots);
+  if (!E.done[k]) HE_CUDA(cudaEventCreateWithFlags(&E.done[k], cudaEventDisableTiming));
+  {
+    DevBuf t(s.buf.words, C.stream);  // released in stream order after the copy below
+    HE_CUDA(cudaMemcpyAsync(t.p, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToDevice, C.stream));
+    ntt_inverse(C, t.p, s.n * s.polys, limbs_q(s.limbs, C.N));
+    HE_CUDA(cudaMemcpyAsync(host, t.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
+  }
+  HE_CUDA(cudaEventRecord(E.done[k], C.stream));
+  E.seq[k] = ticket;
+  E.issued = ticket;
+  return ticket;
+}
+
+void export_wait(Ctx& C, uint64_t ticket) {
+  ExportRing& E = C.exports;
+  if (ticket == 0 || ticket > E.issued) throw Error(1, "export ticket not issued by this context");
+  if (ticket > E.completed) {
+    // the slot holds this ticket or a newer one, which completes after it
+    const int k = (int)(ticket % ExportRing::kSlots);
+    HE_CUDA(cudaEventSynchronize(E.done[k]));
+    E.completed = std::max(E.completed, E.seq[k]);
+  }
+  check_device_status(C);
+}
+
 void export_raw(Ctx& C, const CtSet& s, u64* host) {
   HE_CUDA(cudaMemcpyAsync(host, s.buf.p, s.buf.words * 8, cudaMemcpyDeviceToHost, C.stream));
   HE_CUDA(cudaStreamSynchronize(C.stream));
@@ -743,12 +791,7 @@ std::unique_ptr<CtSet> import_coeffs(Ctx& C, const u64* host, int n, int limbs, 
 
 std::unique_ptr<CtSet> import_async(Ctx& C, const u64* host, int n, int limbs, double scale) {
   if (n < 1 || limbs < 1 || limbs > C.L1) throw Error(1, "bad ciphertext count or level");
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  HE_CUDA(cudaStreamIsCapturing(C.stream, &cs));
-  if (C.capturing || cs != cudaStreamCaptureStatusNone) {
-    C.capture_failed = C.capture_failed || C.capturing;
-    throw Error(9 /* HE_E_STATE */, "an import copies host data and cannot run inside a capture of the context's stream");
-  }
+  refuse_under_capture(C, "an import copies host data and");
   ImportRing& R = C.imports;
   if (!R.copy) {
     HE_CUDA(cudaStreamCreateWithFlags(&R.copy, cudaStreamNonBlocking));

@@ -123,6 +123,20 @@ struct ImportRing {
   ~ImportRing();
 };
 
+// Exports queued by he_ctset_export_async: one event per ticket in a small ring. The context's
+// stream runs the exports in order, so a slot re-recorded for a newer ticket still covers the
+// older one.
+struct ExportRing {
+  static constexpr int kSlots = 4;
+  cudaEvent_t done[kSlots] = {};
+  uint64_t seq[kSlots] = {};  // the ticket last recorded in each slot
+  uint64_t issued = 0, completed = 0;
+  ExportRing() = default;
+  ExportRing(const ExportRing&) = delete;
+  ExportRing& operator=(const ExportRing&) = delete;
+  ~ExportRing();
+};
+
 struct Ctx {
   int device = 0;
   int log_n = 0;
@@ -167,6 +181,7 @@ struct Ctx {
 
   Staging staging;
   ImportRing imports;
+  ExportRing exports;
 
   // keys
   bool has_keys = false;
@@ -347,6 +362,10 @@ std::unique_ptr<CtSet> new_set(Ctx& C, int n, int polys, int limbs, double scale
 std::unique_ptr<CtSet> encrypt_coeffs(Ctx& C, const int64_t* m, int n, int limbs, double scale, u64 id_base);
 void decrypt_slots(Ctx& C, const CtSet& s, double* out);
 void export_coeffs(Ctx& C, const CtSet& s, u64* host);
+// export_coeffs without waiting: returns the ticket export_wait takes
+uint64_t export_async(Ctx& C, const CtSet& s, u64* host);
+// block until the export with this ticket (and every earlier one) has reached the host
+void export_wait(Ctx& C, uint64_t ticket);
 // device words as held (NTT domain) to host
 void export_raw(Ctx& C, const CtSet& s, u64* host);
 // the words as held to a host or device buffer (completed on return)

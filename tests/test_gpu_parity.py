@@ -882,6 +882,68 @@ def test_overlapped_import_equals_import_and_reports_bad_residues_later(lib):
     assert np.array_equal(g.import_coeffs_async(hosts[1], g.scale).export_raw(), outs[1][0].export_raw())
 
 
+def test_export_async_equals_export_and_waits_by_ticket(lib):
+    """he_ctset_export_async queued behind computation writes the words he_ctset_export gives; six
+    exports (more than the context's four event slots) from sets freed right after the call are
+    waited by ticket, the oldest first; tickets grow; 0 and a ticket not yet issued are refused; the
+    call is refused inside a capture of the context's stream, which stays usable."""
+    import torch
+    from paper_2512_18646_gb300 import HeError, api
+    from paper_2512_18646_gb300._lib import HE_E_ARG
+    _, g = make_pair(10, (60, 45, 45), 2, 60, 2, 45.0, seed=14, steps=[1])
+    m = np.random.default_rng(14).integers(-(1 << 40), 1 << 40, size=(3, g.N), dtype=np.int64)
+    x = g.encrypt_coeffs(m, 3, g.scale)
+    ops = (lambda: g.add(x, x), lambda: g.rotate(x, [1]))
+    want = [op().export() for op in ops]
+
+    def pinned(shape):
+        n = int(np.prod(shape))
+        return torch.empty(n, dtype=torch.int64).pin_memory().numpy().view(np.uint64).reshape(shape)
+
+    bufs, tickets = [], []
+    for t in range(6):
+        y = ops[t % 2]()
+        bufs.append(pinned(want[t % 2].shape))
+        tickets.append(y.export_async(bufs[-1]))
+        y.free()  # its release is ordered after the copy
+    assert tickets[0] > 0 and all(b > a for a, b in zip(tickets, tickets[1:]))
+    g.export_wait(tickets[0])  # its event slot was re-recorded by a later export
+    assert np.array_equal(bufs[0], want[0])
+    g.export_wait(tickets[4])
+    for t in range(1, 5):
+        assert np.array_equal(bufs[t], want[t % 2]), t
+    g.export_wait(tickets[2])  # already complete
+    g.export_wait(tickets[5])
+    assert np.array_equal(bufs[5], want[1])
+    for bad in (0, tickets[-1] + 1):
+        with pytest.raises(HeError) as e:
+            g.export_wait(bad)
+        assert e.value.code == HE_E_ARG
+
+    s = torch.cuda.Stream()
+    g2 = api.Context(10, (60, 45, 45), 2, 60, 2, 45.0, seed=15, stream=s.cuda_stream)
+    g2.keygen([])
+    x2 = g2.encrypt_coeffs(m, 3, g2.scale)
+    g2.synchronize()
+    refused = False
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        gr.capture_begin()
+        try:
+            x2.export_async(bufs[0])
+        except HeError:
+            refused = True
+        finally:
+            try:
+                gr.capture_end()
+            except RuntimeError:
+                refused = True
+    assert refused
+    t2 = x2.export_async(bufs[0])
+    g2.export_wait(t2)
+    assert np.array_equal(bufs[0], x2.export())
+
+
 def test_direct_capture_of_the_context_stream_is_refused_loudly(lib):
     """A capture the caller opens on the context's stream itself (torch's CUDA graph on that stream,
     not he_graph_begin) must not record a copy from the context's page-locked staging slots, which
